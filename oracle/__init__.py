@@ -1,0 +1,214 @@
+"""FP64 CPU oracle for the l1-regularised Cox proximal-gradient iteration.
+
+TEST INFRASTRUCTURE.  Only the test suite, the package smoke check and the
+benchmark's CPU-baseline leg may import this package.  It shares no code
+with the CUDA solver (``paper_2010_16114_gb300``), and neither imports the
+other.
+
+The arithmetic lives in ``cox_oracle.c`` (plain loops, FP64, no FMA
+contraction); this module only marshals numpy arrays.  Every function cites
+the passage of arXiv 2010.16114 (DistStat.jl) it follows:
+
+* ``risk`` / ``risk_bruteforce`` -- Section 5.3, W_j, pi_ij and P delta;
+  Breslow ties per Section 6.
+* ``eta`` / ``grad`` -- Section 5.3, X beta and Delta = X^T (I - P) delta
+  (divided by n; the 1/n normalisation is this build's reading).
+* ``prox`` / ``soft_threshold`` -- Section 4.2 soft threshold, applied as
+  S(beta + sigma g, sigma lambda) (Section 5.3 iteration).
+* ``opnorm2`` -- Section 4.4 power method; ``lipschitz`` = 2 ||X_c||_2^2 / n
+  from the step-size remark in Section 5.3.
+* ``ista`` -- the Section 5.3 iteration repeated.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cox_oracle.c")
+_LIBS = {False: os.path.join(_HERE, "liboracle.so"), True: os.path.join(_HERE, "liboracle_ld.so")}
+
+_p = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_f64 = ctypes.c_double
+
+
+def build(force: bool = False) -> None:
+    """Compile the FP64 oracle and its long-double twin with gcc."""
+    for ld, path in _LIBS.items():
+        if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+            tmp = path + ".tmp"
+            cmd = ["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
+            if ld:
+                cmd.append("-DORC_LONG_DOUBLE")
+            subprocess.check_call(cmd + ["-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, path)
+
+
+_loaded: dict = {}
+
+
+def _lib(long_double: bool = False):
+    if long_double not in _loaded:
+        build()
+        lib = ctypes.CDLL(_LIBS[long_double])
+        for name in ("orc_risk", "orc_risk_bruteforce"):
+            f = getattr(lib, name)
+            f.restype = ctypes.c_int
+            f.argtypes = [_i64, _p, _p, _p, _p, _p, _p]
+        lib.orc_argsort.restype = ctypes.c_int
+        lib.orc_argsort.argtypes = [_i64, _p, _p]
+        lib.orc_eta.restype = None
+        lib.orc_eta.argtypes = [_i64, _i64, _p, _p, _p, _p]
+        lib.orc_grad.restype = None
+        lib.orc_grad.argtypes = [_i64, _i64, _p, _p, _p, _p, _p]
+        lib.orc_soft_threshold.restype = _f64
+        lib.orc_soft_threshold.argtypes = [_f64, _f64]
+        lib.orc_prox.restype = None
+        lib.orc_prox.argtypes = [_i64, _p, _p, _f64, _f64, _p]
+        lib.orc_objective.restype = ctypes.c_int
+        lib.orc_objective.argtypes = [_i64, _i64, _p, _p, _p, _p, _p, _f64, _p]
+        lib.orc_ista.restype = ctypes.c_int
+        lib.orc_ista.argtypes = [_i64, _i64, _p, _p, _p, _p, _f64, _f64, _i64, _p, _p, _p]
+        lib.orc_opnorm2.restype = _f64
+        lib.orc_opnorm2.argtypes = [_i64, _i64, _p, _p, _p, _f64, _i64, _p]
+        _loaded[long_double] = lib
+    return _loaded[long_double]
+
+
+def _f(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _u8(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.uint8)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _cols(X) -> np.ndarray:
+    """(n, m) matrix -> column-major float64 buffer."""
+    return np.asfortranarray(X, dtype=np.float64)
+
+
+def argsort(y) -> np.ndarray:
+    """Stable ascending order of the observed times (Section 5.3 sorting)."""
+    y = _f(y)
+    ord_ = np.zeros(len(y), np.int64)
+    _lib().orc_argsort(len(y), _ptr(y), _ptr(ord_))
+    return ord_
+
+
+def risk(y, delta, eta, long_double: bool = False):
+    """(W, u, f) by sorted cumulative sums: W_i = sum_{y_j >= y_i} exp(eta_j - c),
+    u = P delta, f = -l(beta)/n (Section 5.3; Breslow ties, Section 6)."""
+    y, delta, eta = _f(y), _u8(delta), _f(eta)
+    n = len(y)
+    W, u, loss = np.zeros(n), np.zeros(n), _f64()
+    rc = _lib(long_double).orc_risk(n, _ptr(y), _ptr(delta), _ptr(eta), _ptr(W), _ptr(u),
+                                    ctypes.byref(loss))
+    if rc != 0:
+        raise FloatingPointError(f"orc_risk returned {rc}")
+    return W, u, loss.value
+
+
+def risk_bruteforce(y, delta, eta, long_double: bool = False):
+    """Same as ``risk`` from the O(n^2) definitions of W_j and pi_ij
+    (Section 5.3; Appendix B's P delta double loop).  Tiny n only."""
+    y, delta, eta = _f(y), _u8(delta), _f(eta)
+    n = len(y)
+    W, u, loss = np.zeros(n), np.zeros(n), _f64()
+    rc = _lib(long_double).orc_risk_bruteforce(n, _ptr(y), _ptr(delta), _ptr(eta), _ptr(W),
+                                               _ptr(u), ctypes.byref(loss))
+    if rc != 0:
+        raise FloatingPointError(f"orc_risk_bruteforce returned {rc}")
+    return W, u, loss.value
+
+
+def eta(Xcols, mu, beta, long_double: bool = False) -> np.ndarray:
+    """eta = X_c beta over the given columns (Section 5.3, X beta)."""
+    Xc = _cols(Xcols)
+    n, m = Xc.shape
+    beta = _f(beta)
+    mu = None if mu is None else _f(mu)
+    out = np.zeros(n)
+    _lib(long_double).orc_eta(n, m, _ptr(Xc), _ptr(mu), _ptr(beta), _ptr(out))
+    return out
+
+
+def grad(Xcols, mu, delta, u, long_double: bool = False) -> np.ndarray:
+    """g = X_c^T (delta - u) / n over the given columns (Section 5.3, Delta / n)."""
+    Xc = _cols(Xcols)
+    n, m = Xc.shape
+    mu = None if mu is None else _f(mu)
+    g = np.zeros(m)
+    _lib(long_double).orc_grad(n, m, _ptr(Xc), _ptr(mu), _ptr(_u8(delta)), _ptr(_f(u)), _ptr(g))
+    return g
+
+
+def soft_threshold(x: float, t: float) -> float:
+    """Section 4.2 soft threshold."""
+    return _lib().orc_soft_threshold(float(x), float(t))
+
+
+def prox(beta, g, sigma: float, lam: float) -> np.ndarray:
+    """S(beta + sigma g, sigma lambda) elementwise (Section 5.3)."""
+    beta, g = _f(beta), _f(g)
+    out = np.zeros_like(beta)
+    _lib().orc_prox(len(beta), _ptr(beta), _ptr(g), sigma, lam, _ptr(out))
+    return out
+
+
+def objective(X, mu, y, delta, beta, lam: float) -> float:
+    """F_lambda(beta) = f(beta) + lambda ||beta||_1."""
+    Xc = _cols(X)
+    n, p = Xc.shape
+    F = _f64()
+    rc = _lib().orc_objective(n, p, _ptr(Xc), _ptr(None if mu is None else _f(mu)), _ptr(_f(y)),
+                              _ptr(_u8(delta)), _ptr(_f(beta)), lam, ctypes.byref(F))
+    if rc != 0:
+        raise FloatingPointError(f"orc_objective returned {rc}")
+    return F.value
+
+
+def ista(X, mu, y, delta, sigma: float, lam: float, iters: int, beta0=None):
+    """ISTA (Section 5.3) for ``iters`` iterations from beta0 (default 0).
+    Returns (beta, F_trace, g_last): F_trace[t] = F_lambda(beta_t)."""
+    Xc = _cols(X)
+    n, p = Xc.shape
+    beta = np.zeros(p) if beta0 is None else _f(beta0).copy()
+    F = np.zeros(max(iters, 1))
+    g = np.zeros(p)
+    rc = _lib().orc_ista(n, p, _ptr(Xc), _ptr(None if mu is None else _f(mu)), _ptr(_f(y)),
+                         _ptr(_u8(delta)), sigma, lam, iters, _ptr(beta), _ptr(F), _ptr(g))
+    if rc != 0:
+        raise FloatingPointError(f"orc_ista returned {rc}")
+    return beta, F[:iters], g
+
+
+def opnorm2(X, mu, v0, tol: float = 1e-6, maxiter: int = 1000):
+    """||X_c||_2 by the power method (Section 4.4).  Returns (norm, iterations)."""
+    Xc = _cols(X)
+    n, p = Xc.shape
+    it = _i64()
+    v = _lib().orc_opnorm2(n, p, _ptr(Xc), _ptr(None if mu is None else _f(mu)), _ptr(_f(v0)),
+                           tol, maxiter, ctypes.byref(it))
+    return v, it.value
+
+
+def lipschitz(X, mu, v0, tol: float = 1e-6, maxiter: int = 1000) -> float:
+    """L = 2 ||X_c||_2^2 / n: the Section 5.3 step sigma = 1 / (2 ||X||_2^2)
+    rescaled to the 1/n-normalised loss, with the centred design."""
+    nrm, _ = opnorm2(X, mu, v0, tol, maxiter)
+    return 2.0 * nrm * nrm / X.shape[0]
+
+
+def lambda_max(X, mu, y, delta) -> float:
+    """Smallest lambda with beta = 0 optimal: ||g(0)||_inf."""
+    W, u, _ = risk(y, delta, np.zeros(len(y)))
+    return float(np.max(np.abs(grad(X, mu, delta, u))))

@@ -1,0 +1,331 @@
+/*
+ * cox_oracle.c -- plain, slow FP64 CPU oracle for the l1-regularised Cox
+ * proportional-hazards proximal-gradient iteration of Ko, Zhou, Zhou & Won,
+ * "DistStat.jl" (arXiv 2010.16114), Section 5.3 and Appendix B.
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the package smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or constant with the CUDA solver, and the solver never calls
+ * it.
+ *
+ * Notation (the paper writes X in R^{m x n}; here n subjects, p predictors):
+ *   y_i observed time, delta_i = 1 for an event, 0 for censoring.
+ *   eta = X_c beta, X_c = X - 1 mu^T (mu = column means, or 0 when uncentred).
+ *   Log partial likelihood (Section 5.3, first display; the minus sign inside
+ *   the bracket is lost in the source and restored here):
+ *     l(beta) = sum_i delta_i [ eta_i - log sum_{j: y_j >= y_i} exp(eta_j) ].
+ *   f(beta) = -l(beta)/n,   F_lambda(beta) = f(beta) + lambda ||beta||_1.
+ *   Iteration (Section 5.3, second display):
+ *     w_i = exp(eta_i);  W_j = sum_{i: y_i >= y_j} w_i;
+ *     pi_ij = I(y_i >= y_j) w_i / W_j;  u = P delta,
+ *       i.e. u_i = w_i sum_{j: y_j <= y_i} delta_j / W_j;
+ *     g = X_c^T (delta - u) / n   (= -grad f);
+ *     beta <- S(beta + sigma g, sigma lambda)   (soft threshold, Section 4.2).
+ *   Ties (Section 6): Breslow -- every subject with y_j >= t is at risk at t,
+ *   tied events share one W.  exp is evaluated as exp(eta - max eta); the
+ *   common factor cancels in w/W and in the loss.
+ *
+ * Compiled with -ffp-contract=off.  Built a second time with
+ * -DORC_LONG_DOUBLE, which carries every intermediate in long double; the
+ * two builds are compared to bound the FP64 build's own rounding.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef ORC_LONG_DOUBLE
+typedef long double real;
+#define EXP expl
+#define LOG logl
+#define SQRT sqrtl
+#define FABS fabsl
+#else
+typedef double real;
+#define EXP exp
+#define LOG log
+#define SQRT sqrt
+#define FABS fabs
+#endif
+
+/* ---- sorting ---------------------------------------------------------- */
+
+static void merge_pass(int64_t n, const double *y, int64_t *a, int64_t *tmp)
+{
+    for (int64_t width = 1; width < n; width *= 2) {
+        for (int64_t lo = 0; lo < n; lo += 2 * width) {
+            int64_t mid = lo + width < n ? lo + width : n;
+            int64_t hi = lo + 2 * width < n ? lo + 2 * width : n;
+            int64_t i = lo, j = mid, k = lo;
+            while (i < mid && j < hi) tmp[k++] = (y[a[j]] < y[a[i]]) ? a[j++] : a[i++];
+            while (i < mid) tmp[k++] = a[i++];
+            while (j < hi) tmp[k++] = a[j++];
+        }
+        memcpy(a, tmp, (size_t)n * sizeof(int64_t));
+    }
+}
+
+/* Stable ascending argsort of y (merge sort). Returns 0, or -2 on OOM. */
+int orc_argsort(int64_t n, const double *y, int64_t *ord)
+{
+    int64_t *tmp = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    if (!tmp) return -2;
+    for (int64_t i = 0; i < n; ++i) ord[i] = i;
+    merge_pass(n, y, ord, tmp);
+    free(tmp);
+    return 0;
+}
+
+/* ---- risk sets -------------------------------------------------------- */
+
+/*
+ * Risk-set sums by sorting (Section 5.3: once subjects are ordered by time,
+ * the sum over {j: y_j >= y_i} is a cumulative sum).  Sorted ascending, so
+ * W is a reverse cumulative sum read at the first member of each tie group
+ * (Breslow), and C_i = sum_{j: y_j <= y_i} delta_j / W_j is a forward
+ * cumulative sum read at the last member of the tie group.
+ * Outputs in subject order: W, u = P delta, and *loss = f(beta).
+ * Returns 0, -1 on bad arguments, -2 on OOM, -4 on a non-finite value.
+ */
+int orc_risk(int64_t n, const double *y, const uint8_t *delta, const double *eta,
+             double *W_out, double *u_out, double *loss)
+{
+    if (n <= 0) return -1;
+    int64_t *ord = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    real *w = (real *)malloc((size_t)n * sizeof(real));
+    real *R = (real *)malloc((size_t)n * sizeof(real));
+    real *Ws = (real *)malloc((size_t)n * sizeof(real));
+    real *F = (real *)malloc((size_t)n * sizeof(real));
+    if (!ord || !w || !R || !Ws || !F) {
+        free(ord); free(w); free(R); free(Ws); free(F);
+        return -2;
+    }
+    orc_argsort(n, y, ord);
+
+    real c = (real)eta[0];
+    for (int64_t i = 1; i < n; ++i)
+        if ((real)eta[i] > c) c = (real)eta[i];
+    for (int64_t r = 0; r < n; ++r) w[r] = EXP((real)eta[ord[r]] - c);
+
+    /* R[r] = sum_{s >= r} w[s] */
+    R[n - 1] = w[n - 1];
+    for (int64_t r = n - 2; r >= 0; --r) R[r] = R[r + 1] + w[r];
+
+    /* W at each position = R at the first position of its tie group */
+    for (int64_t r = 0; r < n;) {
+        int64_t e = r;
+        while (e + 1 < n && y[ord[e + 1]] == y[ord[r]]) ++e;
+        for (int64_t s = r; s <= e; ++s) Ws[s] = R[r];
+        r = e + 1;
+    }
+
+    /* F[r] = sum_{s <= r} delta_s / W_s */
+    real acc = 0;
+    for (int64_t r = 0; r < n; ++r) {
+        if (delta[ord[r]]) acc += (real)1 / Ws[r];
+        F[r] = acc;
+    }
+
+    /* C at each position = F at the last position of its tie group; u = w C */
+    real lsum = 0;
+    int bad = 0;
+    for (int64_t r = 0; r < n;) {
+        int64_t e = r;
+        while (e + 1 < n && y[ord[e + 1]] == y[ord[r]]) ++e;
+        for (int64_t s = r; s <= e; ++s) {
+            int64_t i = ord[s];
+            real u = w[s] * F[e];
+            W_out[i] = (double)Ws[s];
+            u_out[i] = (double)u;
+            if (delta[i]) lsum += LOG(Ws[s]) - ((real)eta[i] - c);
+            if (!isfinite((double)u) || !isfinite((double)Ws[s])) bad = 1;
+        }
+        r = e + 1;
+    }
+    if (loss) *loss = (double)(lsum / (real)n);
+
+    free(ord); free(w); free(R); free(Ws); free(F);
+    return bad ? -4 : 0;
+}
+
+/*
+ * The same quantities from the literal definitions, O(n^2), no sorting
+ * (Section 5.3 display for W_j and pi_ij; Appendix B computes P delta with
+ * the same double loop).  For tiny n only.
+ */
+int orc_risk_bruteforce(int64_t n, const double *y, const uint8_t *delta, const double *eta,
+                        double *W_out, double *u_out, double *loss)
+{
+    if (n <= 0) return -1;
+    real *w = (real *)malloc((size_t)n * sizeof(real));
+    real *W = (real *)malloc((size_t)n * sizeof(real));
+    if (!w || !W) { free(w); free(W); return -2; }
+    real c = (real)eta[0];
+    for (int64_t i = 1; i < n; ++i)
+        if ((real)eta[i] > c) c = (real)eta[i];
+    for (int64_t i = 0; i < n; ++i) w[i] = EXP((real)eta[i] - c);
+    for (int64_t j = 0; j < n; ++j) {
+        real s = 0;
+        for (int64_t i = 0; i < n; ++i)
+            if (y[i] >= y[j]) s += w[i];
+        W[j] = s;
+    }
+    real lsum = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        real s = 0; /* (P delta)_i = sum_j pi_ij delta_j */
+        for (int64_t j = 0; j < n; ++j)
+            if (y[i] >= y[j] && delta[j]) s += w[i] / W[j];
+        u_out[i] = (double)s;
+        W_out[i] = (double)W[i];
+        if (delta[i]) lsum += LOG(W[i]) - ((real)eta[i] - c);
+    }
+    if (loss) *loss = (double)(lsum / (real)n);
+    free(w); free(W);
+    return 0;
+}
+
+/* ---- products with the centred design -------------------------------- */
+
+/* eta_i = sum_t (x_{i,t} - mu_t) beta_t over the m given columns, t in order.
+ * Xcols is column-major n x m; mu may be NULL (uncentred). */
+void orc_eta(int64_t n, int64_t m, const double *Xcols, const double *mu, const double *beta,
+             double *eta)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        real s = 0;
+        for (int64_t t = 0; t < m; ++t) {
+            real xc = (real)Xcols[t * n + i] - (mu ? (real)mu[t] : (real)0);
+            s += xc * (real)beta[t];
+        }
+        eta[i] = (double)s;
+    }
+}
+
+/* g_t = (1/n) sum_i (x_{i,t} - mu_t)(delta_i - u_i): the t-th entry of
+ * X_c^T (I - P) delta / n (Section 5.3, Delta), i.e. minus the gradient of f. */
+void orc_grad(int64_t n, int64_t m, const double *Xcols, const double *mu, const uint8_t *delta,
+              const double *u, double *g)
+{
+    for (int64_t t = 0; t < m; ++t) {
+        real s = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            real xc = (real)Xcols[t * n + i] - (mu ? (real)mu[t] : (real)0);
+            s += xc * ((real)delta[i] - (real)u[i]);
+        }
+        g[t] = (double)(s / (real)n);
+    }
+}
+
+/* Soft threshold (Section 4.2): x - t if x > t, x + t if x < -t, else 0. */
+double orc_soft_threshold(double x, double t)
+{
+    if (x > t) return x - t;
+    if (x < -t) return x + t;
+    return 0.0;
+}
+
+/* beta_out = S(beta + sigma g, sigma lambda) elementwise (Section 5.3). */
+void orc_prox(int64_t m, const double *beta, const double *g, double sigma, double lam,
+              double *beta_out)
+{
+    for (int64_t t = 0; t < m; ++t)
+        beta_out[t] = orc_soft_threshold((double)((real)beta[t] + (real)sigma * (real)g[t]),
+                                         (double)((real)sigma * (real)lam));
+}
+
+/* F_lambda(beta) = f(beta) + lambda ||beta||_1 on a dense column-major X. */
+int orc_objective(int64_t n, int64_t p, const double *X, const double *mu, const double *y,
+                  const uint8_t *delta, const double *beta, double lam, double *F)
+{
+    double *eta = (double *)malloc((size_t)n * sizeof(double));
+    double *W = (double *)malloc((size_t)n * sizeof(double));
+    double *u = (double *)malloc((size_t)n * sizeof(double));
+    if (!eta || !W || !u) { free(eta); free(W); free(u); return -2; }
+    orc_eta(n, p, X, mu, beta, eta);
+    double f;
+    int rc = orc_risk(n, y, delta, eta, W, u, &f);
+    real l1 = 0;
+    for (int64_t j = 0; j < p; ++j) l1 += FABS((real)beta[j]);
+    *F = (double)((real)f + (real)lam * l1);
+    free(eta); free(W); free(u);
+    return rc;
+}
+
+/*
+ * Proximal gradient (ISTA) from the given beta for `iters` iterations on a
+ * dense column-major X (Section 5.3).  F_trace[t] = F_lambda(beta_t) for the
+ * iterate entering iteration t; g_last (may be NULL) = g at the last entering
+ * iterate.  beta is updated in place.
+ */
+int orc_ista(int64_t n, int64_t p, const double *X, const double *mu, const double *y,
+             const uint8_t *delta, double sigma, double lam, int64_t iters, double *beta,
+             double *F_trace, double *g_last)
+{
+    double *eta = (double *)malloc((size_t)n * sizeof(double));
+    double *W = (double *)malloc((size_t)n * sizeof(double));
+    double *u = (double *)malloc((size_t)n * sizeof(double));
+    double *g = (double *)malloc((size_t)p * sizeof(double));
+    if (!eta || !W || !u || !g) { free(eta); free(W); free(u); free(g); return -2; }
+    int rc = 0;
+    for (int64_t t = 0; t < iters; ++t) {
+        orc_eta(n, p, X, mu, beta, eta);
+        double f;
+        rc = orc_risk(n, y, delta, eta, W, u, &f);
+        if (rc) break;
+        if (F_trace) {
+            real l1 = 0;
+            for (int64_t j = 0; j < p; ++j) l1 += FABS((real)beta[j]);
+            F_trace[t] = (double)((real)f + (real)lam * l1);
+        }
+        orc_grad(n, p, X, mu, delta, u, g);
+        if (g_last) memcpy(g_last, g, (size_t)p * sizeof(double));
+        orc_prox(p, beta, g, sigma, lam, beta);
+    }
+    free(eta); free(W); free(u); free(g);
+    return rc;
+}
+
+/*
+ * ||X_c||_2 by power iteration on X_c^T X_c (Section 4.4, operator norms:
+ * power method with a tolerance and an iteration cap).  v0 is the start
+ * vector (drawn by the caller).  Stops when the Rayleigh estimate changes by
+ * at most tol relative.  Returns the norm; *iters_out = iterations used.
+ */
+double orc_opnorm2(int64_t n, int64_t p, const double *X, const double *mu, const double *v0,
+                   double tol, int64_t maxiter, int64_t *iters_out)
+{
+    real *v = (real *)malloc((size_t)p * sizeof(real));
+    real *a = (real *)malloc((size_t)n * sizeof(real));
+    real *b = (real *)malloc((size_t)p * sizeof(real));
+    if (!v || !a || !b) { free(v); free(a); free(b); return -1.0; }
+    real nv = 0;
+    for (int64_t j = 0; j < p; ++j) { v[j] = (real)v0[j]; nv += v[j] * v[j]; }
+    nv = SQRT(nv);
+    for (int64_t j = 0; j < p; ++j) v[j] /= nv;
+    real s_prev = 0, s = 0;
+    int64_t it = 0;
+    for (it = 1; it <= maxiter; ++it) {
+        for (int64_t i = 0; i < n; ++i) {
+            real acc = 0;
+            for (int64_t j = 0; j < p; ++j)
+                acc += ((real)X[j * n + i] - (mu ? (real)mu[j] : (real)0)) * v[j];
+            a[i] = acc;
+        }
+        real nb = 0;
+        for (int64_t j = 0; j < p; ++j) {
+            real acc = 0;
+            for (int64_t i = 0; i < n; ++i)
+                acc += ((real)X[j * n + i] - (mu ? (real)mu[j] : (real)0)) * a[i];
+            b[j] = acc;
+            nb += acc * acc;
+        }
+        nb = SQRT(nb);          /* ||X_c^T X_c v|| -> sigma_max^2 */
+        s = nb;
+        for (int64_t j = 0; j < p; ++j) v[j] = b[j] / nb;
+        if (it > 1 && FABS(s - s_prev) <= (real)tol * s) break;
+        s_prev = s;
+    }
+    if (iters_out) *iters_out = it > maxiter ? maxiter : it;
+    free(v); free(a); free(b);
+    return (double)SQRT(s);
+}

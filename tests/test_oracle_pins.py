@@ -1,0 +1,304 @@
+"""Pins for the FP64 oracle against facts fixed outside it.
+
+Each test checks the oracle against a brute-force definition, exact rational
+arithmetic, a closed form, a textbook estimator, calculus (finite
+differences), optimality conditions, or a library routine -- never against
+a retyped copy of its own formula.  Paper references are to arXiv 2010.16114
+(Section 5.3 iteration and likelihood, Section 4.2 soft threshold, Section 4.4
+power method, Section 6 Breslow ties and stopping rule).
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import synth
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def _tiny(n, ties, seed):
+    r = _rng(seed)
+    if ties:
+        y = r.integers(1, max(2, n // 3), size=n).astype(float)
+    else:
+        y = r.permutation(n).astype(float) + r.random(n) * 0.5
+    delta = (r.random(n) < 0.6).astype(np.uint8)
+    eta = r.normal(0, 1.0, n)
+    return y, delta, eta
+
+
+# --- risk sets: brute force O(n^2) and exact rationals ----------------------
+
+@pytest.mark.parametrize("ties", [False, True])
+@pytest.mark.parametrize("n", [1, 2, 7, 33, 64])
+def test_sorted_scans_match_bruteforce(orc, n, ties):
+    """Section 5.3 W_j / pi_ij by literal double loops == sorted cumsums."""
+    for seed in range(4):
+        y, delta, eta = _tiny(n, ties, 100 * n + seed)
+        W, u, f = orc.risk(y, delta, eta)
+        Wb, ub, fb = orc.risk_bruteforce(y, delta, eta)
+        np.testing.assert_allclose(W, Wb, rtol=1e-14, atol=0)
+        np.testing.assert_allclose(u, ub, rtol=1e-13, atol=1e-15)
+        assert abs(f - fb) <= 1e-13 * max(1.0, abs(fb))
+
+
+def _exact_risk(y, delta):
+    """u and f at eta = 0 in exact rationals, from the risk-set definitions."""
+    n = len(y)
+    W = [Fraction(sum(1 for j in range(n) if y[j] >= y[i])) for i in range(n)]
+    u = [sum((Fraction(1) / W[j] for j in range(n) if y[j] <= y[i] and delta[j]), Fraction(0))
+         for i in range(n)]
+    return W, u
+
+
+def test_exact_rational_breslow_example(orc):
+    """eta = 0 makes every w_i = 1, so W and u are exact rationals; tie groups
+    of sizes 1, 3, 2 with mixed events check the Breslow reading."""
+    y = np.array([5.0, 2.0, 2.0, 9.0, 2.0, 5.0, 1.0])
+    delta = np.array([1, 1, 0, 0, 1, 0, 1], np.uint8)
+    W, u, f = orc.risk(y, delta, np.zeros(7))
+    We, ue = _exact_risk(list(y), list(delta))
+    np.testing.assert_allclose(W, [float(x) for x in We], rtol=1e-15)
+    np.testing.assert_allclose(u, [float(x) for x in ue], rtol=1e-15)
+    # hand values: times 1 (1 event, 7 at risk), 2 (2 events, 6 at risk), 5 (1 event, 3 at risk)
+    assert W[6] == 7 and W[1] == 6 and W[2] == 6 and W[0] == 3 and W[3] == 1
+    np.testing.assert_allclose(u[1], 1 / 7 + 2 / 6, rtol=1e-15)
+    np.testing.assert_allclose(u[3], 1 / 7 + 2 / 6 + 1 / 3, rtol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_exact_rationals_random_ties(orc, seed):
+    r = _rng(seed)
+    n = 25
+    y = r.integers(1, 6, size=n).astype(float)
+    delta = (r.random(n) < 0.5).astype(np.uint8)
+    W, u, f = orc.risk(y, delta, np.zeros(n))
+    We, ue = _exact_risk(list(y), list(delta))
+    np.testing.assert_allclose(W, [float(x) for x in We], rtol=1e-15)
+    np.testing.assert_allclose(u, [float(x) for x in ue], rtol=1e-14)
+
+
+# --- invariants ---------------------------------------------------------------
+
+@pytest.mark.parametrize("ties", [False, True])
+def test_sum_u_equals_sum_delta(orc, ties):
+    """1^T P delta = 1^T delta for any beta (each event's pi column sums to 1)."""
+    for seed in range(5):
+        y, delta, eta = _tiny(500, ties, seed)
+        _, u, _ = orc.risk(y, delta, 3 * eta)
+        assert abs(u.sum() - delta.sum()) <= 1e-11 * max(1, delta.sum())
+
+
+@pytest.mark.parametrize("ties", [False, True])
+def test_subject_permutation_invariance(orc, ties):
+    """Relabelling subjects (including the order inside tie groups) permutes
+    W and u and leaves the loss unchanged."""
+    y, delta, eta = _tiny(300, ties, 7)
+    W, u, f = orc.risk(y, delta, eta)
+    perm = _rng(8).permutation(300)
+    W2, u2, f2 = orc.risk(y[perm], delta[perm], eta[perm])
+    np.testing.assert_allclose(W2, W[perm], rtol=1e-12)
+    np.testing.assert_allclose(u2, u[perm], rtol=1e-12, atol=1e-14)
+    assert abs(f2 - f) <= 1e-12 * abs(f)
+
+
+def test_shift_invariance(orc):
+    """A common shift of eta cancels in w/W and in the partial likelihood."""
+    y, delta, eta = _tiny(200, True, 3)
+    _, u, f = orc.risk(y, delta, eta)
+    _, u2, f2 = orc.risk(y, delta, eta + 37.25)
+    np.testing.assert_allclose(u2, u, rtol=1e-12, atol=1e-14)
+    assert abs(f2 - f) <= 1e-12 * abs(f)
+
+
+def test_overflow_guard(orc):
+    """eta of order 1e3 would overflow exp() without the max shift."""
+    y, delta, eta = _tiny(100, True, 4)
+    _, u, f = orc.risk(y, delta, eta + 900.0)
+    _, u0, f0 = orc.risk(y, delta, eta)
+    assert np.all(np.isfinite(u)) and np.isfinite(f)
+    np.testing.assert_allclose(u, u0, rtol=1e-10, atol=1e-13)
+
+
+# --- closed forms and textbook estimators ------------------------------------
+
+def test_loss_at_zero_distinct_times(orc):
+    """f(0) = (1/n) sum_i delta_i log |R_i| with |R_i| = n - rank_i."""
+    n = 400
+    y, delta, _ = _tiny(n, False, 11)
+    rank = np.argsort(np.argsort(y, kind="stable"), kind="stable")
+    expect = np.sum(delta * np.log(n - rank)) / n
+    _, _, f = orc.risk(y, delta, np.zeros(n))
+    assert abs(f - expect) <= 1e-13 * abs(expect)
+
+
+def test_loss_at_zero_with_ties(orc):
+    """With ties |R(t)| is the number at risk at t (Breslow)."""
+    n = 400
+    y, delta, _ = _tiny(n, True, 12)
+    at_risk = np.array([(y >= t).sum() for t in y])
+    expect = np.sum(delta * np.log(at_risk)) / n
+    _, _, f = orc.risk(y, delta, np.zeros(n))
+    assert abs(f - expect) <= 1e-13 * abs(expect)
+
+
+@pytest.mark.parametrize("ties", [False, True])
+def test_u_at_zero_is_nelson_aalen(orc, ties):
+    """At beta = 0, u_i is the Nelson-Aalen cumulative hazard at y_i."""
+    y, delta, _ = _tiny(600, ties, 13)
+    times = np.unique(y)
+    d = np.array([delta[y == t].sum() for t in times], float)
+    r = np.array([(y >= t).sum() for t in times], float)
+    H = np.cumsum(d / r)
+    expect = H[np.searchsorted(times, y)]
+    _, u, _ = orc.risk(y, delta, np.zeros(len(y)))
+    np.testing.assert_allclose(u, expect, rtol=1e-13)
+
+
+def test_logrank_score_p1(orc):
+    """p = 1, beta = 0: n g = sum over events of (x_i - mean of x over R(y_i)),
+    the log-rank score (with Breslow ties)."""
+    r = _rng(21)
+    n = 300
+    y = r.integers(1, 60, n).astype(float)
+    delta = (r.random(n) < 0.4).astype(np.uint8)
+    x = r.integers(0, 3, n).astype(float)
+    _, u, _ = orc.risk(y, delta, np.zeros(n))
+    g = orc.grad(x[:, None], None, delta, u)[0]
+    score = sum(x[i] - x[y >= y[i]].mean() for i in range(n) if delta[i])
+    assert abs(n * g - score) <= 1e-11 * max(1, abs(score))
+
+
+# --- calculus -------------------------------------------------------------------
+
+@pytest.mark.parametrize("center", [False, True])
+def test_gradient_central_differences(orc, center):
+    """g = -grad f: central differences of the FP64 loss, h = 1e-5."""
+    w = synth.workload(1, n=400, p=12)
+    X = w.dense().astype(float)
+    mu = X.mean(0) if center else None
+    beta = _rng(5).normal(0, 0.3, w.p)
+    eta = orc.eta(X, mu, beta)
+    _, u, f = orc.risk(w.y, w.delta, eta)
+    g = orc.grad(X, mu, w.delta, u)
+    h = 1e-5
+    fd = np.zeros(w.p)
+    for j in range(w.p):
+        e = np.zeros(w.p)
+        e[j] = h
+        fp = orc.risk(w.y, w.delta, orc.eta(X, mu, beta + e))[2]
+        fm = orc.risk(w.y, w.delta, orc.eta(X, mu, beta - e))[2]
+        fd[j] = (fp - fm) / (2 * h)
+    np.testing.assert_allclose(-fd, g, rtol=1e-7, atol=1e-9 * np.abs(g).max())
+
+
+def test_centering_leaves_loss_unchanged(orc):
+    """X_c beta differs from X beta by a constant, which the loss ignores."""
+    w = synth.workload(1, n=300, p=20)
+    X = w.dense().astype(float)
+    beta = _rng(6).normal(0, 0.2, w.p)
+    f_c = orc.risk(w.y, w.delta, orc.eta(X, X.mean(0), beta))[2]
+    f_u = orc.risk(w.y, w.delta, orc.eta(X, None, beta))[2]
+    assert abs(f_c - f_u) <= 1e-12 * abs(f_u)
+
+
+# --- optimisation: KKT, monotone objective, Newton root ------------------------
+
+def test_soft_threshold_cases(orc):
+    """Section 4.2: strict inequalities, so |x| == t maps to exactly 0."""
+    st = orc.soft_threshold
+    assert st(3.0, 1.0) == 2.0 and st(-3.0, 1.0) == -2.0
+    assert st(1.0, 1.0) == 0.0 and st(-1.0, 1.0) == 0.0 and st(0.5, 1.0) == 0.0
+    assert st(0.0, 0.0) == 0.0 and st(2.5, 0.0) == 2.5
+
+
+def _small_problem(seed=0, n=150, p=30):
+    w = synth.workload(1, n=n, p=p)
+    X = w.dense().astype(float)
+    mu = X.mean(0)
+    return w, X, mu
+
+
+def test_ista_kkt_and_monotone(orc):
+    """ISTA fixed point <=> KKT: |g_j| <= lambda where beta_j = 0 and
+    g_j = lambda sign(beta_j) elsewhere; F_lambda never increases."""
+    w, X, mu = _small_problem()
+    v0 = synth.normal_vec(95376, 7, w.p)
+    L = orc.lipschitz(X, mu, v0, tol=1e-10, maxiter=5000)
+    lmax = orc.lambda_max(X, mu, w.y, w.delta)
+    lam = 0.3 * lmax
+    beta = np.zeros(w.p)
+    Ftr = []
+    for _ in range(200):
+        beta_new, F, g = orc.ista(X, mu, w.y, w.delta, 1.0 / L, lam, 200, beta)
+        Ftr.extend(F)
+        if np.max(np.abs(beta_new - beta)) < 1e-13:
+            beta = beta_new
+            break
+        beta = beta_new
+    Ftr = np.array(Ftr)
+    assert np.all(np.diff(Ftr) <= 1e-14 * np.abs(Ftr[1:]))
+    eta = orc.eta(X, mu, beta)
+    _, u, _ = orc.risk(w.y, w.delta, eta)
+    g = orc.grad(X, mu, w.delta, u)
+    zero = beta == 0
+    assert zero.any() and (~zero).any()
+    assert np.all(np.abs(g[zero]) <= lam * (1 + 1e-6))
+    np.testing.assert_allclose(g[~zero], lam * np.sign(beta[~zero]), rtol=0, atol=1e-6 * lam)
+
+
+def test_unpenalised_p1_matches_newton(orc):
+    """p = 1, lambda = 0: the ISTA limit is the root of the Cox score,
+    found here by Newton's method on score and information written from the
+    partial likelihood in numpy."""
+    r = _rng(31)
+    n = 250
+    y = r.integers(1, 40, n).astype(float)
+    x = r.normal(0, 1, n)
+    delta = (r.random(n) < 0.5).astype(np.uint8)
+    b = 0.0
+    for _ in range(50):
+        e = np.exp(b * x)
+        U = I = 0.0
+        for i in np.nonzero(delta)[0]:
+            R = y >= y[i]
+            s0, s1, s2 = e[R].sum(), (e[R] * x[R]).sum(), (e[R] * x[R] ** 2).sum()
+            U += x[i] - s1 / s0
+            I += s2 / s0 - (s1 / s0) ** 2
+        b += U / I
+    L = 2 * np.sum((x - x.mean()) ** 2) / n
+    beta, F, g = orc.ista(x[:, None], x[None, :].mean(1), y, delta, 1.0 / L, 0.0, 20000)
+    assert abs(beta[0] - b) <= 1e-9 * max(1, abs(b))
+
+
+def test_power_method_matches_svd(orc):
+    """Section 4.4 power method vs LAPACK's largest singular value."""
+    w, X, mu = _small_problem(n=200, p=40)
+    v0 = synth.normal_vec(95376, 7, w.p)
+    nrm, it = orc.opnorm2(X, mu, v0, tol=1e-12, maxiter=10000)
+    ref = np.linalg.norm(X - mu, 2)
+    assert abs(nrm - ref) <= 1e-8 * ref
+    nrm6, _ = orc.opnorm2(X, mu, v0)  # the paper's defaults: tol 1e-6, 1000 iterations
+    assert abs(nrm6 - ref) <= 1e-5 * ref
+
+
+# --- the oracle's own rounding ------------------------------------------------------
+
+def test_long_double_twin_agrees(orc):
+    """The same source carried in long double agrees to ~1e-13: the FP64
+    build's summation order is not a source of error at the test sizes."""
+    w, X, mu = _small_problem(n=500, p=25)
+    beta = _rng(9).normal(0, 0.3, w.p)
+    eta = orc.eta(X, mu, beta)
+    eta_ld = orc.eta(X, mu, beta, long_double=True)
+    np.testing.assert_allclose(eta, eta_ld, rtol=1e-13, atol=1e-14)
+    W, u, f = orc.risk(w.y, w.delta, eta)
+    Wl, ul, fl = orc.risk(w.y, w.delta, eta_ld, long_double=True)
+    np.testing.assert_allclose(u, ul, rtol=1e-12, atol=1e-14)
+    assert abs(f - fl) <= 1e-13 * abs(fl)
+    g = orc.grad(X, mu, w.delta, u)
+    gl = orc.grad(X, mu, w.delta, ul, long_double=True)
+    np.testing.assert_allclose(g, gl, rtol=1e-10, atol=1e-13 * np.abs(gl).max())
