@@ -1,0 +1,201 @@
+/*
+ * coxgb.h -- C ABI of the GB300 l1-regularised Cox proportional-hazards
+ * proximal-gradient library (libcoxgb.so).
+ *
+ * Method: Ko, Zhou, Zhou & Won, "DistStat.jl" (arXiv 2010.16114), Section 5.3
+ * (partial likelihood, proximal-gradient iteration, sorted cumulative sums,
+ * step size), Section 4.2 (soft threshold), Section 4.4 (power method),
+ * Section 6 (Breslow ties, lag-10 stopping rule).
+ *
+ * Notation: n subjects, p predictors (SNPs), k penalty values solved
+ * together.  y = observed times, delta = event indicators.  The library
+ * centres the design, X_c = X - 1 mu^T with mu_j the column mean, when
+ * cox_options.center is 1, and works with
+ *     f(beta)  = -(1/n) sum_i delta_i [ eta_i - log sum_{j: y_j >= y_i} exp(eta_j) ],
+ *     eta      = X_c beta,
+ *     g(beta)  = X_c^T (delta - u) / n = -grad f,   u = P delta (Section 5.3),
+ *     F(beta)  = f(beta) + lambda ||beta||_1,
+ *     one step : beta <- S(beta + sigma g, sigma lambda),  sigma = step.
+ * Ties in y are handled by Breslow's rule: every subject with y_j >= t is in
+ * the risk set at t, and tied events share that risk set.
+ *
+ * Conventions for every call:
+ *   - Return value: COX_OK (0) or a negative COX_ERR_* code; no call throws
+ *     or aborts across this boundary.  cox_strerror() names the code.
+ *   - Pointers named *_dev are device pointers on the handle's device;
+ *     *_host are host pointers.  The caller owns every buffer it passes; the
+ *     library owns the handle and everything it allocates for it.
+ *   - Coefficient matrices are p x k column-major: entry (j, c) at c*p + j,
+ *     column c belonging to lambdas[c].  Element type: float, except for a
+ *     handle created with precision COX_FP64, where it is double.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is ordered on it.  Calls that return host values
+ *     synchronise the stream before returning; cox_prox_step does not, and a
+ *     device-side error it meets is reported by the next synchronising call
+ *     (cox_sync, cox_loss_grad, cox_path_fit, cox_prox_step_host).
+ *   - A handle is not thread-safe: one host thread at a time.
+ */
+#ifndef COXGB_H
+#define COXGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cox_handle *cox_h;
+
+enum {
+    COX_OK = 0,
+    COX_ERR_ARG = -1,           /* bad shape, pointer, option or value        */
+    COX_ERR_CODE3 = -2,         /* genotype code 3 (not in {0,1,2})           */
+    COX_ERR_OOM = -3,           /* device or host allocation failed           */
+    COX_ERR_CUDA = -4,          /* a CUDA runtime call failed                 */
+    COX_ERR_TIMEOUT = -5,       /* a device-side wait ran out its limit       */
+    COX_ERR_NONFINITE = -6,     /* eta, W or the loss became non-finite       */
+    COX_ERR_NOT_CONVERGED = -7, /* warning: a path column hit max_iter        */
+    COX_ERR_STATE = -8,         /* state blob does not match the handle       */
+    COX_ERR_UNSUPPORTED = -9    /* no sm_103a device, or mode/format mismatch */
+};
+
+/* How X is passed to cox_setup. */
+enum {
+    COX_X_INT8_HOST = 0,    /* uint8 codes {0,1,2}, n x p row-major, host          */
+    COX_X_F64_HOST = 1,     /* double, n x p row-major, host (COX_FP64 only)        */
+    COX_X_PACKED2_HOST = 2, /* 2-bit codes, row-major, ceil(p/4) bytes per row,     */
+    COX_X_PACKED2_DEV = 3   /*   SNP j in bits 2*(j%4)+{0,1} of byte j/4; host/dev  */
+};
+
+/* Arithmetic of the two products X_c B and X_c^T V. */
+enum {
+    COX_SPLIT_BF16 = 0, /* tcgen05 tensor cores, coefficients split hi+lo bf16,
+                           FP32 accumulation; FP64 risk-set scans (default)   */
+    COX_FP64 = 1,       /* FP64 everywhere, dense X (COX_X_F64_HOST)          */
+    COX_FP32_GEMV = 2   /* baseline: one lambda at a time, FP32 CUDA-core GEMV
+                           on the packed genotypes, unfused soft threshold    */
+};
+
+typedef struct cox_options {
+    int precision;        /* COX_SPLIT_BF16 (default), COX_FP64, COX_FP32_GEMV       */
+    int center;           /* 1: X_c = X - 1 mu^T (default 1; COX_FP64 default 0)    */
+    int device;           /* CUDA device ordinal (default: current device)           */
+    int tile_m;           /* 128-row tiles per CTA in the tensor-core products;
+                             0 = choose automatically (autotuned table)              */
+    int stages;           /* shared-memory pipeline depth; 0 = automatic             */
+    int lag;              /* stopping-rule lag in iterations (default 10, Section 6) */
+    double wait_limit_s;  /* device-side wait limit in seconds (default 2.0)         */
+} cox_options;
+
+/* Fill *opt with the defaults above. */
+void cox_default_options(cox_options *opt);
+
+/*
+ * Create a handle for one data set (Section 5.3 problem statement: X, y,
+ * delta).  Sorts subjects by y (stable), records Breslow tie groups, computes
+ * column means mu (exact integer sums for genotypes), and lays X out in
+ * device memory: two 2-bit tiled copies (subject-major and SNP-major) for the
+ * genotype modes, dense row- and column-major FP64 copies for COX_FP64.
+ *   X       : as x_format says; host buffers are copied, a COX_X_PACKED2_DEV
+ *             buffer is read during setup only (the caller may free it after).
+ *   n, p    : >= 1.  Genotype modes accept n, p up to 2^31 - 1 each.
+ *   time    : n finite doubles (host).  event: n bytes, 0 or 1 (host).
+ *   opt     : NULL for defaults.
+ * Errors: COX_ERR_ARG (shapes, non-finite time, event not 0/1, format not
+ * allowed for the precision), COX_ERR_CODE3, COX_ERR_OOM, COX_ERR_CUDA,
+ * COX_ERR_UNSUPPORTED (device is not sm_103).  On error *out is NULL.
+ */
+int cox_setup(cox_h *out, const void *X, int64_t n, int64_t p, int x_format,
+              const double *time, const uint8_t *event, const cox_options *opt);
+
+/* Release the handle and all device memory it owns.  NULL is a no-op. */
+void cox_destroy(cox_h h);
+
+/*
+ * L = 2 ||X_c||_2^2 / n, the Lipschitz constant the step 1/L is built from
+ * (Section 5.3 step-size remark, rescaled to the 1/n loss), with ||X_c||_2
+ * from the power method of Section 4.4: tolerance 1e-6 on the relative
+ * change of the estimate, at most 1000 iterations.  start_host: p doubles,
+ * the start vector (NULL: all ones).  Synchronous.
+ */
+int cox_lipschitz(cox_h h, const double *start_host, double *L_out);
+
+/* lambda_max = ||g(0)||_inf: the smallest lambda for which beta = 0 solves
+ * the problem (g(0) uses u(0), the Nelson-Aalen hazard).  Synchronous. */
+int cox_lambda_max(cox_h h, double *lmax_out);
+
+/*
+ * Loss and gradient at k coefficient vectors (Section 5.3 Delta, no prox):
+ *   beta_dev : p x k coefficients (device, column-major).
+ *   loss_host: k doubles, f(beta_c) (no penalty).  May be NULL.
+ *   grad_dev : p x k, grad f = -X_c^T (delta - u) / n (device).  May be NULL.
+ * Synchronous (returns after the stream has drained).
+ */
+int cox_loss_grad(cox_h h, const void *beta_dev, int k, double *loss_host, void *grad_dev,
+                  void *stream);
+
+/*
+ * One proximal-gradient iteration for k penalties at once (Section 5.3):
+ * eta = X_c B, risk-set scans, G = X_c^T V, beta <- S(beta + step g, step lambda).
+ *   beta_dev : p x k in/out (device).
+ *   lambdas  : k penalties (host, >= 0).  step: sigma > 0.
+ * Asynchronous on `stream`.  The handle keeps F(beta entering this step)
+ * per column; cox_last_objective() reads it.
+ */
+int cox_prox_step(cox_h h, void *beta_dev, const double *lambdas, int k, double step,
+                  void *stream);
+
+/* As cox_prox_step with beta in host memory (copied in and out inside the
+ * call); synchronous.  The end-to-end form of one iteration. */
+int cox_prox_step_host(cox_h h, void *beta_host, const double *lambdas, int k, double step,
+                       void *stream);
+
+/* Wait for `stream` and report any device-side error of earlier calls. */
+int cox_sync(cox_h h, void *stream);
+
+/* F_lambda at the iterate that entered the last cox_prox_step, per column
+ * (k doubles, host).  Synchronous. */
+int cox_last_objective(cox_h h, double *obj_host, int k, void *stream);
+
+/*
+ * Solve k penalties from beta = 0 (or from beta_dev when warm != 0), each
+ * column until |F_t - F_{t-lag}| / |F_t + 1| < tol (Section 6 stopping rule,
+ * F = penalised objective) or max_iter.  A converged column is frozen: its
+ * result equals a solo run.  Iterations run as CUDA-graph replays of `lag`
+ * steps; the host reads k objectives per replay.
+ *   beta_dev  : p x k (device) out (in too when warm).
+ *   iters_host: k ints, iterations each column ran.  obj_host: k doubles,
+ *               final F.  Either may be NULL.
+ * Returns COX_OK, or COX_ERR_NOT_CONVERGED if some column hit max_iter.
+ */
+int cox_path_fit(cox_h h, const double *lambdas, int k, int max_iter, double tol, double step,
+                 int warm, void *beta_dev, int *iters_host, double *obj_host, void *stream);
+
+/* Checkpoint: the solver state of the last path fit / step (coefficients,
+ * iteration counters, objective history).  cox_get_state with buf == NULL
+ * sets *size to the bytes needed.  cox_set_state restores it (same n, p, k,
+ * precision) so a path fit resumes bit-identically. */
+int cox_get_state(cox_h h, void *buf, size_t *size);
+int cox_set_state(cox_h h, const void *buf, size_t size);
+
+/* Handle facts: n, p, padded sizes, precision, tile choice, device bytes. */
+typedef struct cox_info {
+    int64_t n, p, n_pad, p_pad;
+    int precision, center, tile_m, stages, sm_count;
+    int64_t device_bytes;
+    int64_t n_tie_groups;
+} cox_info;
+int cox_get_info(cox_h h, cox_info *info);
+
+/* Column means mu (p doubles, host) and the sorted order (n int64, host;
+ * entry r = subject at rank r).  Either may be NULL. */
+int cox_get_mu_order(cox_h h, double *mu_host, int64_t *order_host);
+
+const char *cox_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COXGB_H */

@@ -1,0 +1,198 @@
+"""ctypes binding of libcoxgb.so: the C ABI in include/coxgb.h, same names.
+
+Argument marshalling only; every step of the iteration runs in the CUDA
+library.  Loading fails loudly when the library has not been built."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcoxgb.so")
+
+COX_OK = 0
+COX_ERR_ARG = -1
+COX_ERR_CODE3 = -2
+COX_ERR_OOM = -3
+COX_ERR_CUDA = -4
+COX_ERR_TIMEOUT = -5
+COX_ERR_NONFINITE = -6
+COX_ERR_NOT_CONVERGED = -7
+COX_ERR_STATE = -8
+COX_ERR_UNSUPPORTED = -9
+
+COX_X_INT8_HOST = 0
+COX_X_F64_HOST = 1
+COX_X_PACKED2_HOST = 2
+COX_X_PACKED2_DEV = 3
+
+COX_SPLIT_BF16 = 0
+COX_FP64 = 1
+COX_FP32_GEMV = 2
+
+# every symbol include/coxgb.h declares
+EXPORTS = [
+    "cox_default_options", "cox_setup", "cox_destroy", "cox_lipschitz", "cox_lambda_max",
+    "cox_loss_grad", "cox_prox_step", "cox_prox_step_host", "cox_sync", "cox_last_objective",
+    "cox_path_fit", "cox_get_state", "cox_set_state", "cox_get_info", "cox_get_mu_order",
+    "cox_strerror",
+]
+
+
+class cox_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("center", ctypes.c_int), ("device", ctypes.c_int),
+                ("tile_m", ctypes.c_int), ("stages", ctypes.c_int), ("lag", ctypes.c_int),
+                ("wait_limit_s", ctypes.c_double)]
+
+
+class cox_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("p", ctypes.c_int64), ("n_pad", ctypes.c_int64),
+                ("p_pad", ctypes.c_int64), ("precision", ctypes.c_int), ("center", ctypes.c_int),
+                ("tile_m", ctypes.c_int), ("stages", ctypes.c_int), ("sm_count", ctypes.c_int),
+                ("device_bytes", ctypes.c_int64), ("n_tie_groups", ctypes.c_int64)]
+
+
+class CoxError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libcoxgb.so (built by ``paper_2010_16114_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"libcoxgb.so is not built ({path}); run paper_2010_16114_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    lib.cox_default_options.restype = None
+    lib.cox_default_options.argtypes = [ctypes.POINTER(cox_options)]
+    lib.cox_setup.restype = I
+    lib.cox_setup.argtypes = [ctypes.POINTER(P), P, I64, I64, I, P, P, ctypes.POINTER(cox_options)]
+    lib.cox_destroy.restype = None
+    lib.cox_destroy.argtypes = [P]
+    lib.cox_lipschitz.restype = I
+    lib.cox_lipschitz.argtypes = [P, P, ctypes.POINTER(D)]
+    lib.cox_lambda_max.restype = I
+    lib.cox_lambda_max.argtypes = [P, ctypes.POINTER(D)]
+    lib.cox_loss_grad.restype = I
+    lib.cox_loss_grad.argtypes = [P, P, I, P, P, P]
+    lib.cox_prox_step.restype = I
+    lib.cox_prox_step.argtypes = [P, P, P, I, D, P]
+    lib.cox_prox_step_host.restype = I
+    lib.cox_prox_step_host.argtypes = [P, P, P, I, D, P]
+    lib.cox_sync.restype = I
+    lib.cox_sync.argtypes = [P, P]
+    lib.cox_last_objective.restype = I
+    lib.cox_last_objective.argtypes = [P, P, I, P]
+    lib.cox_path_fit.restype = I
+    lib.cox_path_fit.argtypes = [P, P, I, I, D, D, I, P, P, P, P]
+    lib.cox_get_state.restype = I
+    lib.cox_get_state.argtypes = [P, P, ctypes.POINTER(ctypes.c_size_t)]
+    lib.cox_set_state.restype = I
+    lib.cox_set_state.argtypes = [P, P, ctypes.c_size_t]
+    lib.cox_get_info.restype = I
+    lib.cox_get_info.argtypes = [P, ctypes.POINTER(cox_info)]
+    lib.cox_get_mu_order.restype = I
+    lib.cox_get_mu_order.argtypes = [P, P, P]
+    lib.cox_strerror.restype = ctypes.c_char_p
+    lib.cox_strerror.argtypes = [I]
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().cox_strerror(code).decode()
+    except ImportError:
+        return f"error {code}"
+
+
+def check(code: int, where: str, allow=(COX_OK,)) -> int:
+    if code not in allow:
+        raise CoxError(code, where)
+    return code
+
+
+# thin same-name wrappers -------------------------------------------------------------
+
+def cox_default_options() -> cox_options:
+    o = cox_options()
+    load().cox_default_options(ctypes.byref(o))
+    return o
+
+
+def cox_setup(X_ptr, n, p, x_format, time_ptr, event_ptr, opt: cox_options | None):
+    h = ctypes.c_void_p()
+    rc = load().cox_setup(ctypes.byref(h), X_ptr, n, p, x_format, time_ptr, event_ptr,
+                          ctypes.byref(opt) if opt is not None else None)
+    return rc, h
+
+
+def cox_destroy(h):
+    load().cox_destroy(h)
+
+
+def cox_lipschitz(h, start_ptr=None):
+    L = ctypes.c_double()
+    rc = load().cox_lipschitz(h, start_ptr, ctypes.byref(L))
+    return rc, L.value
+
+
+def cox_lambda_max(h):
+    v = ctypes.c_double()
+    rc = load().cox_lambda_max(h, ctypes.byref(v))
+    return rc, v.value
+
+
+def cox_loss_grad(h, beta_ptr, k, loss_ptr, grad_ptr, stream_ptr):
+    return load().cox_loss_grad(h, beta_ptr, k, loss_ptr, grad_ptr, stream_ptr)
+
+
+def cox_prox_step(h, beta_ptr, lam_ptr, k, step, stream_ptr):
+    return load().cox_prox_step(h, beta_ptr, lam_ptr, k, step, stream_ptr)
+
+
+def cox_prox_step_host(h, beta_ptr, lam_ptr, k, step, stream_ptr):
+    return load().cox_prox_step_host(h, beta_ptr, lam_ptr, k, step, stream_ptr)
+
+
+def cox_sync(h, stream_ptr):
+    return load().cox_sync(h, stream_ptr)
+
+
+def cox_last_objective(h, obj_ptr, k, stream_ptr):
+    return load().cox_last_objective(h, obj_ptr, k, stream_ptr)
+
+
+def cox_path_fit(h, lam_ptr, k, max_iter, tol, step, warm, beta_ptr, iters_ptr, obj_ptr, stream_ptr):
+    return load().cox_path_fit(h, lam_ptr, k, max_iter, tol, step, warm, beta_ptr, iters_ptr, obj_ptr,
+                               stream_ptr)
+
+
+def cox_get_state(h, buf_ptr, size_ref):
+    return load().cox_get_state(h, buf_ptr, size_ref)
+
+
+def cox_set_state(h, buf_ptr, size):
+    return load().cox_set_state(h, buf_ptr, size)
+
+
+def cox_get_info(h):
+    info = cox_info()
+    rc = load().cox_get_info(h, ctypes.byref(info))
+    return rc, info
+
+
+def cox_get_mu_order(h, mu_ptr, order_ptr):
+    return load().cox_get_mu_order(h, mu_ptr, order_ptr)
+
+
+def cox_strerror(code: int) -> str:
+    return strerror(code)

@@ -1,0 +1,198 @@
+"""Python front end of libcoxgb: one handle per data set.
+
+Coefficients are torch tensors of shape (k, p) on the handle's CUDA device
+(row c = penalty c), which is the library's p x k column-major layout.
+float32 for the genotype modes, float64 for precision "fp64".
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+PRECISIONS = {"split_bf16": L.COX_SPLIT_BF16, "fp64": L.COX_FP64, "fp32_gemv": L.COX_FP32_GEMV}
+
+
+def _vp(x):
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(int(x))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class CoxProblem:
+    """A data set (X, y, delta) laid out on the GPU (``cox_setup``).
+
+    X may be
+      * a numpy uint8 (n, p) array of genotype codes {0,1,2};
+      * a numpy float64 (n, p) array (precision "fp64");
+      * a uint8 array/tensor of row-major 2-bit codes, shape (n, ceil(p/4)),
+        on the host or on the device, with ``p`` given."""
+
+    def __init__(self, X, time, event, precision: str = "split_bf16", center: bool | None = None,
+                 p: int | None = None, device: int | None = None, tile_m: int = 0, stages: int = 0,
+                 lag: int = 10, wait_limit_s: float = 2.0):
+        lib = L.load()
+        opt = L.cox_default_options()
+        opt.precision = PRECISIONS[precision]
+        opt.center = int(center if center is not None else precision != "fp64")
+        opt.device = -1 if device is None else int(device)
+        opt.tile_m = int(tile_m)
+        opt.stages = int(stages)
+        opt.lag = int(lag)
+        opt.wait_limit_s = float(wait_limit_s)
+        time = np.ascontiguousarray(time, dtype=np.float64)
+        event = np.ascontiguousarray(event, dtype=np.uint8)
+        n = len(time)
+        self._keep = None
+        if isinstance(X, torch.Tensor) and X.is_cuda:
+            assert X.dtype == torch.uint8 and p is not None
+            fmt, xp = L.COX_X_PACKED2_DEV, _vp(X.contiguous())
+            self._keep = X
+        elif isinstance(X, np.ndarray) and X.dtype == np.float64:
+            fmt, p = L.COX_X_F64_HOST, X.shape[1]
+            X = np.ascontiguousarray(X)
+            xp = _vp(X)
+        elif p is not None and X.shape[1] == (p + 3) // 4 and X.dtype == np.uint8 and X.shape[1] != p:
+            X = np.ascontiguousarray(X)
+            fmt, xp = L.COX_X_PACKED2_HOST, _vp(X)
+        else:
+            X = np.ascontiguousarray(X, dtype=np.uint8)
+            fmt, p = L.COX_X_INT8_HOST, X.shape[1]
+            xp = _vp(X)
+        rc, h = L.cox_setup(xp, n, p, fmt, _vp(time), _vp(event), opt)
+        L.check(rc, "cox_setup")
+        self.h = h
+        self.n, self.p = n, p
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        dev = torch.cuda.current_device() if device is None else device
+        self.device = torch.device("cuda", dev)
+        self._lib = lib
+
+    # -- life cycle -------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            L.cox_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- queries ------------------------------------------------------------------------
+    def info(self):
+        rc, info = L.cox_get_info(self.h)
+        L.check(rc, "cox_get_info")
+        return {f: getattr(info, f) for f, _ in L.cox_info._fields_}
+
+    def mu_order(self):
+        mu = np.zeros(self.p)
+        order = np.zeros(self.n, np.int64)
+        L.check(L.cox_get_mu_order(self.h, _vp(mu), _vp(order)), "cox_get_mu_order")
+        return mu, order
+
+    def lipschitz(self, start: np.ndarray | None = None) -> float:
+        s = None if start is None else np.ascontiguousarray(start, dtype=np.float64)
+        rc, v = L.cox_lipschitz(self.h, _vp(s))
+        L.check(rc, "cox_lipschitz")
+        return v
+
+    def lambda_max(self) -> float:
+        rc, v = L.cox_lambda_max(self.h)
+        L.check(rc, "cox_lambda_max")
+        return v
+
+    def zeros(self, k: int) -> torch.Tensor:
+        return torch.zeros((k, self.p), dtype=self.dtype, device=self.device)
+
+    def _beta(self, beta: torch.Tensor) -> torch.Tensor:
+        if beta.dim() == 1:
+            beta = beta[None]
+        if beta.dtype != self.dtype or not beta.is_cuda or beta.shape[1] != self.p or not beta.is_contiguous():
+            raise ValueError(f"beta must be a contiguous {self.dtype} CUDA tensor of shape (k, {self.p})")
+        return beta
+
+    # -- the iteration ---------------------------------------------------------------------
+    def loss_grad(self, beta: torch.Tensor, stream=None):
+        """f(beta_c) per row and grad f (same shape as beta)."""
+        b = self._beta(beta)
+        k = b.shape[0]
+        loss = np.zeros(k)
+        grad = torch.empty_like(b)
+        rc = L.cox_loss_grad(self.h, _vp(b), k, _vp(loss), _vp(grad), _stream_ptr(stream))
+        L.check(rc, "cox_loss_grad")
+        return loss, grad.view_as(beta)
+
+    def prox_step(self, beta: torch.Tensor, lambdas, step: float, stream=None):
+        """One iteration in place on beta (asynchronous)."""
+        b = self._beta(beta)
+        k = b.shape[0]
+        lam = np.ascontiguousarray(np.broadcast_to(np.asarray(lambdas, dtype=np.float64), (k,)))
+        rc = L.cox_prox_step(self.h, _vp(b), _vp(lam), k, float(step), _stream_ptr(stream))
+        L.check(rc, "cox_prox_step")
+        return beta
+
+    def prox_step_host(self, beta: np.ndarray, lambdas, step: float, stream=None):
+        """One iteration on a host array (k, p), copied in and out."""
+        k = beta.shape[0] if beta.ndim == 2 else 1
+        lam = np.ascontiguousarray(np.broadcast_to(np.asarray(lambdas, dtype=np.float64), (k,)))
+        rc = L.cox_prox_step_host(self.h, _vp(beta), _vp(lam), k, float(step), _stream_ptr(stream))
+        L.check(rc, "cox_prox_step_host")
+        return beta
+
+    def sync(self, stream=None):
+        L.check(L.cox_sync(self.h, _stream_ptr(stream)), "cox_sync")
+
+    def last_objective(self, k: int, stream=None) -> np.ndarray:
+        out = np.zeros(k)
+        L.check(L.cox_last_objective(self.h, _vp(out), k, _stream_ptr(stream)), "cox_last_objective")
+        return out
+
+    def path_fit(self, lambdas, step: float, max_iter: int = 1000, tol: float = 1e-6,
+                 beta: torch.Tensor | None = None, warm: int = 0, stream=None):
+        """Fit k penalties; returns (beta (k,p), iterations, objectives, converged)."""
+        lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64).ravel())
+        k = len(lam)
+        if beta is None:
+            beta = self.zeros(k)
+        b = self._beta(beta)
+        iters = np.zeros(k, np.int32)
+        obj = np.zeros(k)
+        rc = L.cox_path_fit(self.h, _vp(lam), k, int(max_iter), float(tol), float(step), int(warm), _vp(b),
+                            _vp(iters), _vp(obj), _stream_ptr(stream))
+        L.check(rc, "cox_path_fit", allow=(L.COX_OK, L.COX_ERR_NOT_CONVERGED))
+        return beta, iters, obj, rc == L.COX_OK
+
+    def get_state(self) -> bytes:
+        size = ctypes.c_size_t()
+        L.check(L.cox_get_state(self.h, None, ctypes.byref(size)), "cox_get_state")
+        buf = ctypes.create_string_buffer(size.value)
+        L.check(L.cox_get_state(self.h, buf, ctypes.byref(size)), "cox_get_state")
+        return buf.raw
+
+    def set_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        L.check(L.cox_set_state(self.h, buf, len(blob)), "cox_set_state")

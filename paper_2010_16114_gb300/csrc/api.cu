@@ -1,0 +1,581 @@
+// api.cu -- the C ABI of libcoxgb: handle life cycle, one proximal-gradient
+// iteration (arXiv 2010.16114, Section 5.3), loss and gradient, the power
+// method for the step (Section 4.4), the batched path fit with the lag-10
+// stopping rule (Section 6) replayed as a CUDA graph, and checkpoints.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "internal.h"
+
+namespace coxgb {
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return COX_ERR_OOM;
+    }
+    return COX_ERR_CUDA;
+}
+
+int dmalloc(cox_handle *h, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? COX_ERR_OOM : COX_ERR_CUDA;
+    }
+    if (h) h->device_bytes += static_cast<int64_t>(bytes);
+    return COX_OK;
+}
+
+void dfree(void *p)
+{
+    if (p) cudaFree(p);
+}
+
+namespace {
+
+template <typename T>
+int alloc(cox_handle *h, T *&p, size_t count)
+{
+    void *v = nullptr;
+    int r = dmalloc(h, &v, count * sizeof(T));
+    p = static_cast<T *>(v);
+    return r;
+}
+
+void free_workspace(cox_handle *h)
+{
+    Workspace &w = h->ws;
+    void *ptrs[] = {w.eta, w.w, w.Rt, w.Ft, w.cmax, w.csw, w.csd, w.suf, w.pre, w.lossp, w.vsp, w.l1p,
+                    w.sumV, w.f, w.F, w.l1, w.lam, w.active, w.Fring, w.Bb, w.Vb, w.part1, w.part4,
+                    w.cnt4, w.V64, w.V32, w.eta32, w.G32};
+    for (void *p : ptrs) dfree(p);
+    const GemmPlan g1 = w.g1, g4 = w.g4;
+    (void)g1;
+    (void)g4;
+    h->ws = Workspace();
+}
+
+int check_device_error(cox_handle *h, cudaStream_t st)
+{
+    int e = 0;
+    COX_CUDA(cudaMemcpyAsync(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    COX_CUDA(cudaStreamSynchronize(st));
+    if (e) {
+        COX_CUDA(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+        COX_CUDA(cudaStreamSynchronize(st));
+        if (e & DEVERR_TIMEOUT) return COX_ERR_TIMEOUT;
+        if (e & DEVERR_NONFINITE) return COX_ERR_NONFINITE;
+        if (e & DEVERR_CODE3) return COX_ERR_CODE3;
+    }
+    return COX_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool is_split(const cox_handle *h) { return h->opt.precision == COX_SPLIT_BF16; }
+bool is_fp64(const cox_handle *h) { return h->opt.precision == COX_FP64; }
+
+} // namespace
+
+// One iteration for k columns.  epi: EPI_PROX (update beta) or EPI_GRAD.
+int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, cudaStream_t st)
+{
+    Workspace &ws = h->ws;
+    if (is_split(h)) {
+        float *b32 = static_cast<float *>(beta);
+        COX_TRY(prep_limbs_beta(h, b32, k, ws.Bb, ws.g1.NP, st));
+        COX_TRY(l1_norms32(h, b32, k, st));
+        EpiArgs e1;
+        e1.epi = EPI_PARTIAL;
+        e1.part = ws.part1;
+        COX_TRY(launch_gemm(h, ws.g1, e1, k, st));
+        ScanArgs sa;
+        sa.k = k;
+        sa.eta_src = ETA_PARTIAL_F32;
+        sa.eta = ws.part1;
+        sa.slot_stride = static_cast<int64_t>(k) * h->n_pad;
+        sa.col_stride = h->n_pad;
+        sa.group_rows = ws.g1.T * TILE;
+        sa.KC = ws.g1.KC;
+        sa.L = ws.g1.L;
+        sa.v_out = V_LIMBS_BF16;
+        sa.V = ws.Vb;
+        sa.NP = ws.g4.NP;
+        sa.exp64 = false;
+        sa.lam = ws.lam;
+        sa.need_loss = true;
+        COX_TRY(run_scans(h, sa, st));
+        EpiArgs e4;
+        e4.epi = epi;
+        e4.part = ws.part4;
+        e4.counters = ws.cnt4;
+        e4.beta = epi == EPI_PROX ? b32 : nullptr;
+        e4.grad = epi == EPI_GRAD ? static_cast<float *>(grad) : nullptr;
+        e4.lam = ws.lam;
+        e4.step = step;
+        e4.mu = h->d_mu;
+        e4.sumV = ws.sumV;
+        e4.active = ws.active;
+        e4.rows_valid = h->p;
+        e4.inv_n = 1.0 / static_cast<double>(h->n);
+        COX_TRY(launch_gemm(h, ws.g4, e4, k, st));
+        return COX_OK;
+    }
+    if (is_fp64(h)) {
+        double *b64 = static_cast<double *>(beta);
+        COX_TRY(l1_norms64(h, b64, k, st));
+        COX_TRY(eta64(h, b64, k, ws.eta, st));
+        ScanArgs sa;
+        sa.k = k;
+        sa.eta_src = ETA_DENSE_F64;
+        sa.eta = ws.eta;
+        sa.slot_stride = 0;
+        sa.col_stride = h->n;
+        sa.group_rows = 1;
+        sa.KC = 1;
+        sa.L = 1;
+        sa.v_out = V_DENSE_F64;
+        sa.V = ws.V64;
+        sa.NP = 0;
+        sa.exp64 = true;
+        sa.lam = ws.lam;
+        sa.need_loss = true;
+        COX_TRY(run_scans(h, sa, st));
+        COX_TRY(xtv64(h, ws.V64, k, epi == EPI_PROX ? b64 : nullptr, epi == EPI_GRAD ? static_cast<double *>(grad) : nullptr,
+                      ws.lam, step, st));
+        return COX_OK;
+    }
+    // plain FP32 baseline: one column at a time, unfused
+    float *b32 = static_cast<float *>(beta);
+    for (int c = 0; c < k; ++c) {
+        float *bc = b32 + static_cast<int64_t>(c) * h->p;
+        COX_TRY(l1_norms32(h, bc, 1, st));
+        COX_TRY(gemv_tiles(h, h->d_A1, h->n_pad, h->p_pad / TILE, bc, h->p, ws.eta32, st));
+        ScanArgs sa;
+        sa.k = 1;
+        sa.eta_src = ETA_DENSE_F32;
+        sa.eta = ws.eta32;
+        sa.slot_stride = 0;
+        sa.col_stride = h->n_pad;
+        sa.group_rows = 1;
+        sa.KC = 1;
+        sa.L = 1;
+        sa.v_out = V_DENSE_F32;
+        sa.V = ws.V32;
+        sa.NP = 0;
+        sa.exp64 = false;
+        sa.lam = ws.lam + c;
+        sa.need_loss = true;
+        COX_TRY(run_scans(h, sa, st));
+        COX_CUDA(cudaMemcpyAsync(ws.Fring + c, ws.F, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        COX_CUDA(cudaMemcpyAsync(ws.Fring + k + c, ws.f, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        COX_TRY(gemv_tiles(h, h->d_A4, h->p_pad, h->n_pad / TILE, ws.V32, h->n, ws.G32, st));
+        float *gc = epi == EPI_GRAD ? static_cast<float *>(grad) : nullptr;
+        COX_TRY(prox_or_grad32(h, ws.G32, c, epi == EPI_PROX ? b32 : nullptr, gc, ws.lam, step, st));
+    }
+    // gather per-column objectives into F / f
+    COX_CUDA(cudaMemcpyAsync(ws.F, ws.Fring, k * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    COX_CUDA(cudaMemcpyAsync(ws.f, ws.Fring + k, k * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return COX_OK;
+}
+
+namespace {
+
+int validate_k(const cox_handle *h, int k)
+{
+    if (k < 1) return COX_ERR_ARG;
+    if (is_split(h) && k > MAX_K_TC) return COX_ERR_ARG;
+    if (k > 1024) return COX_ERR_ARG;
+    return COX_OK;
+}
+
+int set_lambdas(cox_handle *h, const double *lambdas, int k, cudaStream_t st)
+{
+    if (!lambdas) return COX_ERR_ARG;
+    for (int c = 0; c < k; ++c)
+        if (!(lambdas[c] >= 0.0) || !std::isfinite(lambdas[c])) return COX_ERR_ARG;
+    COX_CUDA(cudaMemcpyAsync(h->ws.lam, lambdas, k * sizeof(double), cudaMemcpyHostToDevice, st));
+    return COX_OK;
+}
+
+int set_all_active(cox_handle *h, int k, cudaStream_t st)
+{
+    std::vector<int> one(static_cast<size_t>(k), 1);
+    COX_CUDA(cudaMemcpyAsync(h->ws.active, one.data(), k * sizeof(int), cudaMemcpyHostToDevice, st));
+    COX_CUDA(cudaStreamSynchronize(st));
+    return COX_OK;
+}
+
+} // namespace
+
+int ensure_workspace(cox_handle *h, int k)
+{
+    Workspace &ws = h->ws;
+    if (ws.k == k) return COX_OK;
+    free_workspace(h);
+    const int64_t n = h->n, p = h->p, nch = h->n_chunks;
+    const int lag = std::max(1, h->opt.lag);
+    int r = COX_OK;
+#define A(ptr, cnt)                                 \
+    if ((r = alloc(h, ptr, (cnt))) != COX_OK) { \
+        free_workspace(h);                          \
+        return r;                                   \
+    }
+    A(ws.eta, k * n);
+    A(ws.w, k * n);
+    A(ws.Rt, k * n);
+    A(ws.Ft, k * n);
+    A(ws.cmax, k * nch);
+    A(ws.csw, k * nch);
+    A(ws.csd, k * nch);
+    A(ws.suf, k * nch);
+    A(ws.pre, k * nch);
+    A(ws.lossp, k * nch);
+    A(ws.vsp, k * nch);
+    A(ws.l1p, static_cast<size_t>(k) * h->l1_blocks);
+    A(ws.sumV, k);
+    A(ws.f, k);
+    A(ws.F, k);
+    A(ws.l1, k);
+    A(ws.lam, k);
+    A(ws.active, k);
+    A(ws.Fring, static_cast<size_t>(std::max(lag, 2)) * k);
+    if (is_split(h)) {
+        const int NP = (2 * k + 15) / 16 * 16 <= 16 ? 16 : (2 * k + 15) / 16 * 16 <= 32 ? 32 : (2 * k + 15) / 16 * 16 <= 64 ? 64 : 128;
+        A(ws.Bb, static_cast<size_t>(NP) * h->p_pad);
+        A(ws.Vb, static_cast<size_t>(NP) * h->n_pad);
+        cudaMemset(ws.Bb, 0, static_cast<size_t>(NP) * h->p_pad * 2);
+        cudaMemset(ws.Vb, 0, static_cast<size_t>(NP) * h->n_pad * 2);
+        ws.NP = NP;
+        if ((r = plan_gemm(h, ws.g1, h->d_A1, h->n_pad, h->p_pad, ws.Bb, k, h->opt.tile_m, h->opt.stages)) != COX_OK ||
+            (r = plan_gemm(h, ws.g4, h->d_A4, h->p_pad, h->n_pad, ws.Vb, k, h->opt.tile_m, h->opt.stages)) != COX_OK) {
+            free_workspace(h);
+            return r;
+        }
+        A(ws.part1, static_cast<size_t>(ws.g1.max_slots) * k * h->n_pad);
+        A(ws.part4, static_cast<size_t>(ws.g4.max_slots) * k * h->p_pad);
+        A(ws.cnt4, static_cast<size_t>(ws.g4.n_groups));
+        cudaMemset(ws.cnt4, 0, static_cast<size_t>(ws.g4.n_groups) * sizeof(int));
+    } else if (is_fp64(h)) {
+        A(ws.V64, k * n);
+    } else {
+        A(ws.V32, n);
+        A(ws.eta32, h->n_pad);
+        A(ws.G32, h->p_pad);
+    }
+#undef A
+    (void)p;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        free_workspace(h);
+        return COX_ERR_CUDA;
+    }
+    ws.k = k;
+    return set_all_active(h, k, 0);
+}
+
+} // namespace coxgb
+
+using namespace coxgb;
+
+extern "C" {
+
+void cox_default_options(cox_options *opt)
+{
+    if (!opt) return;
+    opt->precision = COX_SPLIT_BF16;
+    opt->center = 1;
+    opt->device = -1;
+    opt->tile_m = 0;
+    opt->stages = 0;
+    opt->lag = 10;
+    opt->wait_limit_s = 2.0;
+}
+
+const char *cox_strerror(int code)
+{
+    switch (code) {
+    case COX_OK: return "ok";
+    case COX_ERR_ARG: return "invalid argument";
+    case COX_ERR_CODE3: return "genotype code outside {0,1,2}";
+    case COX_ERR_OOM: return "out of memory";
+    case COX_ERR_CUDA: return "CUDA runtime error";
+    case COX_ERR_TIMEOUT: return "device-side wait timed out";
+    case COX_ERR_NONFINITE: return "non-finite value in eta, W or the loss";
+    case COX_ERR_NOT_CONVERGED: return "some column reached max_iter before the stopping rule";
+    case COX_ERR_STATE: return "state blob does not match the handle";
+    case COX_ERR_UNSUPPORTED: return "unsupported device or mode";
+    default: return "unknown error";
+    }
+}
+
+void cox_destroy(cox_h h)
+{
+    if (!h) return;
+    DeviceGuard g(h->dev);
+    cudaDeviceSynchronize();
+    free_workspace(h);
+    void *ptrs[] = {h->d_head, h->d_tail, h->d_delta, h->d_mu, h->d_A1, h->d_A4, h->d_Xr, h->d_Xc, h->d_err};
+    for (void *p : ptrs) dfree(p);
+    delete h;
+}
+
+int cox_setup(cox_h *out, const void *X, int64_t n, int64_t p, int x_format, const double *time,
+              const uint8_t *event, const cox_options *opt_in)
+{
+    if (!out) return COX_ERR_ARG;
+    *out = nullptr;
+    cox_options opt;
+    cox_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    if (!X || !time || !event || n < 1 || p < 1 || n > INT32_MAX || p > INT32_MAX) return COX_ERR_ARG;
+    if (opt.precision != COX_SPLIT_BF16 && opt.precision != COX_FP64 && opt.precision != COX_FP32_GEMV)
+        return COX_ERR_ARG;
+    if ((opt.precision == COX_FP64) != (x_format == COX_X_F64_HOST)) return COX_ERR_UNSUPPORTED;
+    if (x_format < COX_X_INT8_HOST || x_format > COX_X_PACKED2_DEV) return COX_ERR_ARG;
+    if (opt.lag < 1 || !(opt.wait_limit_s >= 0.0)) return COX_ERR_ARG;
+    if (opt.tile_m != 0 && opt.tile_m != 1 && opt.tile_m != 2 && opt.tile_m != 4 && opt.tile_m != 8) return COX_ERR_ARG;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!std::isfinite(time[i])) return COX_ERR_ARG;
+        if (event[i] > 1) return COX_ERR_ARG;
+    }
+    int dev = opt.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return COX_ERR_CUDA;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return COX_ERR_UNSUPPORTED;
+    }
+    if (prop.major != 10 || prop.minor != 3) return COX_ERR_UNSUPPORTED;
+    DeviceGuard guard(dev);
+
+    cox_handle *h = new cox_handle();
+    h->dev = dev;
+    h->sm_count = prop.multiProcessorCount;
+    h->opt = opt;
+    h->n = n;
+    h->p = p;
+    h->n_pad = (n + PAD - 1) / PAD * PAD;
+    h->p_pad = (p + PAD - 1) / PAD * PAD;
+    h->n_chunks = static_cast<int>((n + SCAN_CH - 1) / SCAN_CH);
+    h->l1_blocks = static_cast<int>(std::min<int64_t>(64, (p + 4095) / 4096));
+    {
+        int khz = 0;
+        if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess || khz <= 0) {
+            cudaGetLastError();
+            khz = 2100000;  // GB300 boost clock ceiling, 2.07 GHz
+        }
+        h->wait_cycles = static_cast<long long>(opt.wait_limit_s * static_cast<double>(khz) * 1000.0);
+    }
+
+    // stable sort by time; Breslow tie groups
+    h->h_order.resize(static_cast<size_t>(n));
+    std::iota(h->h_order.begin(), h->h_order.end(), 0);
+    std::stable_sort(h->h_order.begin(), h->h_order.end(), [&](int64_t a, int64_t b) { return time[a] < time[b]; });
+    std::vector<int32_t> head(static_cast<size_t>(n)), tail(static_cast<size_t>(n));
+    std::vector<uint8_t> dsorted(static_cast<size_t>(n));
+    int64_t groups = 0;
+    for (int64_t r = 0; r < n;) {
+        int64_t e = r;
+        while (e + 1 < n && time[h->h_order[e + 1]] == time[h->h_order[r]]) ++e;
+        for (int64_t s = r; s <= e; ++s) {
+            head[s] = static_cast<int32_t>(r);
+            tail[s] = static_cast<int32_t>(e);
+        }
+        ++groups;
+        r = e + 1;
+    }
+    for (int64_t r = 0; r < n; ++r) dsorted[r] = event[h->h_order[r]];
+    h->n_groups_tie = groups;
+
+    cudaStream_t st = 0;
+    int rc = COX_OK;
+    do {
+        if ((rc = dmalloc(h, reinterpret_cast<void **>(&h->d_err), sizeof(int))) != COX_OK) break;
+        if ((rc = dmalloc(h, reinterpret_cast<void **>(&h->d_head), n * sizeof(int32_t))) != COX_OK) break;
+        if ((rc = dmalloc(h, reinterpret_cast<void **>(&h->d_tail), n * sizeof(int32_t))) != COX_OK) break;
+        if ((rc = dmalloc(h, reinterpret_cast<void **>(&h->d_delta), n)) != COX_OK) break;
+        if ((rc = dmalloc(h, reinterpret_cast<void **>(&h->d_mu), p * sizeof(double))) != COX_OK) break;
+        if (cudaMemset(h->d_err, 0, sizeof(int)) != cudaSuccess ||
+            cudaMemcpy(h->d_head, head.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(h->d_tail, tail.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(h->d_delta, dsorted.data(), n, cudaMemcpyHostToDevice) != cudaSuccess) {
+            rc = COX_ERR_CUDA;
+            break;
+        }
+        if (opt.precision == COX_FP64) rc = setup_dense64(h, static_cast<const double *>(X), st);
+        else rc = setup_genotypes(h, X, x_format, st);
+        if (rc != COX_OK) break;
+        if (cudaMemcpy(h->d_mu, h->h_mu.data(), p * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            rc = COX_ERR_CUDA;
+            break;
+        }
+    } while (false);
+    if (rc != COX_OK) {
+        cox_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return COX_OK;
+}
+
+int cox_get_info(cox_h h, cox_info *info)
+{
+    if (!h || !info) return COX_ERR_ARG;
+    info->n = h->n;
+    info->p = h->p;
+    info->n_pad = h->n_pad;
+    info->p_pad = h->p_pad;
+    info->precision = h->opt.precision;
+    info->center = h->opt.center;
+    info->tile_m = h->ws.k ? h->ws.g1.T : h->opt.tile_m;
+    info->stages = h->ws.k ? h->ws.g1.stages : h->opt.stages;
+    info->sm_count = h->sm_count;
+    info->device_bytes = h->device_bytes;
+    info->n_tie_groups = h->n_groups_tie;
+    return COX_OK;
+}
+
+int cox_get_mu_order(cox_h h, double *mu_host, int64_t *order_host)
+{
+    if (!h) return COX_ERR_ARG;
+    if (mu_host) std::memcpy(mu_host, h->h_mu.data(), h->p * sizeof(double));
+    if (order_host) std::memcpy(order_host, h->h_order.data(), h->n * sizeof(int64_t));
+    return COX_OK;
+}
+
+int cox_sync(cox_h h, void *stream)
+{
+    if (!h) return COX_ERR_ARG;
+    DeviceGuard g(h->dev);
+    return check_device_error(h, static_cast<cudaStream_t>(stream));
+}
+
+int cox_loss_grad(cox_h h, const void *beta_dev, int k, double *loss_host, void *grad_dev, void *stream)
+{
+    if (!h || !beta_dev) return COX_ERR_ARG;
+    COX_TRY(validate_k(h, k));
+    DeviceGuard g(h->dev);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    COX_TRY(ensure_workspace(h, k));
+    std::vector<double> zeros(static_cast<size_t>(k), 0.0);
+    COX_TRY(set_lambdas(h, zeros.data(), k, st));
+    void *gout = grad_dev;
+    void *tmp = nullptr;
+    if (!gout) {
+        COX_TRY(dmalloc(nullptr, &tmp, static_cast<size_t>(k) * h->p * (is_fp64(h) ? 8 : 4)));
+        gout = tmp;
+    }
+    int rc = iterate(h, const_cast<void *>(beta_dev), k, EPI_GRAD, gout, 0.0, st);
+    if (rc == COX_OK) rc = check_device_error(h, st);
+    if (rc == COX_OK && loss_host) {
+        if (cudaMemcpyAsync(loss_host, h->ws.f, k * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = COX_ERR_CUDA;
+    }
+    if (tmp) {
+        cudaStreamSynchronize(st);
+        dfree(tmp);
+    }
+    return rc;
+}
+
+int cox_prox_step(cox_h h, void *beta_dev, const double *lambdas, int k, double step, void *stream)
+{
+    if (!h || !beta_dev || !(step > 0.0) || !std::isfinite(step)) return COX_ERR_ARG;
+    COX_TRY(validate_k(h, k));
+    DeviceGuard g(h->dev);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    COX_TRY(ensure_workspace(h, k));
+    COX_TRY(set_lambdas(h, lambdas, k, st));
+    return iterate(h, beta_dev, k, EPI_PROX, nullptr, step, st);
+}
+
+int cox_prox_step_host(cox_h h, void *beta_host, const double *lambdas, int k, double step, void *stream)
+{
+    if (!h || !beta_host) return COX_ERR_ARG;
+    COX_TRY(validate_k(h, k));
+    DeviceGuard g(h->dev);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bytes = static_cast<size_t>(k) * h->p * (is_fp64(h) ? 8 : 4);
+    COX_TRY(ensure_workspace(h, k));
+    static thread_local void *dbuf = nullptr;
+    static thread_local size_t dcap = 0;
+    static thread_local int ddev = -1;
+    if (dcap < bytes || ddev != h->dev) {
+        if (dbuf) cudaFree(dbuf);
+        dbuf = nullptr;
+        dcap = 0;
+        COX_TRY(dmalloc(nullptr, &dbuf, bytes));
+        dcap = bytes;
+        ddev = h->dev;
+    }
+    COX_CUDA(cudaMemcpyAsync(dbuf, beta_host, bytes, cudaMemcpyHostToDevice, st));
+    COX_TRY(set_lambdas(h, lambdas, k, st));
+    COX_TRY(iterate(h, dbuf, k, EPI_PROX, nullptr, step, st));
+    COX_CUDA(cudaMemcpyAsync(beta_host, dbuf, bytes, cudaMemcpyDeviceToHost, st));
+    return check_device_error(h, st);
+}
+
+int cox_last_objective(cox_h h, double *obj_host, int k, void *stream)
+{
+    if (!h || !obj_host || k != h->ws.k) return COX_ERR_ARG;
+    DeviceGuard g(h->dev);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    COX_CUDA(cudaMemcpyAsync(obj_host, h->ws.F, k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    return check_device_error(h, st);
+}
+
+int cox_lambda_max(cox_h h, double *lmax_out)
+{
+    if (!h || !lmax_out) return COX_ERR_ARG;
+    DeviceGuard g(h->dev);
+    const size_t es = is_fp64(h) ? 8 : 4;
+    void *b = nullptr, *gr = nullptr;
+    COX_TRY(dmalloc(nullptr, &b, h->p * es));
+    if (dmalloc(nullptr, &gr, h->p * es) != COX_OK) {
+        dfree(b);
+        return COX_ERR_OOM;
+    }
+    cudaMemset(b, 0, h->p * es);
+    int rc = cox_loss_grad(h, b, 1, nullptr, gr, nullptr);
+    double m = 0.0;
+    if (rc == COX_OK) {
+        if (es == 8) {
+            std::vector<double> v(static_cast<size_t>(h->p));
+            if (cudaMemcpy(v.data(), gr, h->p * 8, cudaMemcpyDeviceToHost) != cudaSuccess) rc = COX_ERR_CUDA;
+            for (double x : v) m = std::max(m, std::fabs(x));
+        } else {
+            std::vector<float> v(static_cast<size_t>(h->p));
+            if (cudaMemcpy(v.data(), gr, h->p * 4, cudaMemcpyDeviceToHost) != cudaSuccess) rc = COX_ERR_CUDA;
+            for (float x : v) m = std::max(m, static_cast<double>(std::fabs(x)));
+        }
+    }
+    dfree(b);
+    dfree(gr);
+    *lmax_out = m;
+    return rc;
+}
+
+} // extern "C"

@@ -1,0 +1,581 @@
+// gemm_tc.cu -- the two genotype products of the Cox iteration on tcgen05
+// tensor cores (arXiv 2010.16114, Section 5.3: X beta, and Delta = X^T (I-P) delta):
+//
+//   first product : D = X_sorted (n x p) * Bhat (p x 2k)    -> eta partials
+//   second product: D = X_sorted^T (p x n) * Vhat (n x 2k)  -> X^T V, then the
+//                   soft-threshold step (Section 4.2) in the epilogue.
+//
+// A is the 2-bit genotype matrix in a tiled layout (128 x 128 blocks of 4 KB),
+// loaded by TMA into shared memory, decoded by eight warps into Tensor Memory
+// and consumed by tcgen05.mma as the A operand (kind::f16, A from TMEM,
+// B from 128B-swizzled shared memory, FP32 accumulators in TMEM).
+//
+// Decode: a genotype code c in {0,1,2} placed at mantissa bits [2t, 2t+1] of
+// a zero-exponent bf16 is the subnormal c * 2^(2t-133); the matching B row is
+// pre-scaled by 2^(69-2t), so each product equals c * b * 2^-64 exactly and
+// the epilogue multiplies by 2^64.  Decoding is one AND per pair of codes.
+//
+// B holds each coefficient column as two bf16 limbs, hi = RN(b), lo = RN(b-hi)
+// (columns 2c and 2c+1), so D[2c] + D[2c+1] carries ~16 significant bits of b.
+//
+// FP32 accumulation in TMEM rounds with a bias, so each CTA accumulates at most
+// F K-chunks in TMEM (double-buffered), then the decoder warps fold the window
+// into FP32 registers (round-to-nearest).
+//
+// Work split: units = (M group, K chunk) pairs; CTA c takes the contiguous
+// range [c L, (c+1) L).  A group cut between CTAs gets one partial per CTA
+// (slot = CTA - first CTA of the group); the last CTA to finish a group sums
+// the slots in slot order (deterministic) and applies the epilogue.
+#include <cuda_bf16.h>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace coxgb {
+namespace {
+
+struct KParams {
+    int KC, F, k, stages, ring;
+    int64_t units, L;
+    int64_t rows_pad, slot_stride;
+    float *part;
+    int epi;
+    int *counters;
+    float *beta;
+    float *grad;
+    const double *lam;
+    double step;
+    const double *mu;
+    const double *sumV;
+    const int *active;
+    int64_t rows_valid;
+    double inv_n;
+    long long wait_limit;
+    int *err;
+};
+
+constexpr long long DRAIN_LIMIT = 4000000000LL;  // ~2 s: copies/MMAs always finish
+__device__ int g_never_set = 0;                 // abort flag for drain waits: never raised
+
+__device__ __forceinline__ void decode16(uint32_t P, uint32_t *o)
+{
+    const uint32_t Q = P >> 6, R = P >> 12;
+    o[0] = P & 0x00030003u;
+    o[1] = P & 0x000C000Cu;
+    o[2] = P & 0x00300030u;
+    o[3] = Q & 0x00030003u;
+    o[4] = Q & 0x000C000Cu;
+    o[5] = Q & 0x00300030u;
+    o[6] = R & 0x00030003u;
+    o[7] = R & 0x000C000Cu;
+}
+
+__device__ __forceinline__ void fail(volatile int *abort_sm, int *err)
+{
+    if (!*abort_sm) {
+        *abort_sm = 1;
+        atomicOr(err, DEVERR_TIMEOUT);
+    }
+}
+
+__device__ __forceinline__ bool window_first(int64_t i, int kc, int64_t wstart, int F)
+{
+    return i == 0 || kc == 0 || i - wstart == F;
+}
+
+template <int T, int NP>
+__global__ void __launch_bounds__(320, 1)
+    k_packed_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                  const KParams P)
+{
+    constexpr int KH = NP / 4;
+    constexpr int B_BYTES = NP * 256;
+    constexpr int X_BYTES = T * BLOCK_BYTES;
+    constexpr int STAGE = B_BYTES + X_BYTES;
+    constexpr int ACC_COLS = 2 * T * NP;
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                ~static_cast<uintptr_t>(1023));
+    const int S = P.stages, R = P.ring;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S * STAGE);
+    const uint32_t full0 = smem_addr(bars);
+    const uint32_t empty0 = full0 + 8 * S;
+    const uint32_t afull0 = empty0 + 8 * S;
+    const uint32_t aempty0 = afull0 + 8 * R;
+    const uint32_t accf0 = aempty0 + 8 * R;
+    const uint32_t acce0 = accf0 + 16;
+    const uint32_t drainb = acce0 + 16;
+    const uint32_t epib = drainb + 8;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 2 * R + 6);
+    volatile int *abort_sm = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    volatile int *last_sm = reinterpret_cast<volatile int *>(tmem_slot + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 9);
+        }
+        for (int r = 0; r < R; ++r) {
+            mbar_init(afull0 + 8 * r, 8);
+            mbar_init(aempty0 + 8 * r, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf0 + 8 * b, 1);
+            mbar_init(acce0 + 8 * b, 8);
+        }
+        mbar_init(drainb, 1);
+        mbar_init(epib, 8);
+        *abort_sm = 0;
+        *last_sm = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_addr(tmem_slot), 512);
+        tmem_relinquish();
+    }
+    if (threadIdx.x == 0) {
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_slot;
+
+    const int64_t cta = blockIdx.x;
+    const int64_t u0 = cta * P.L;
+    const int64_t u1 = min(u0 + P.L, P.units);
+    const int64_t nu = u1 > u0 ? u1 - u0 : 0;
+    const int KC = P.KC, F = P.F;
+    const long long lim = P.wait_limit;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            int64_t issued = 0;
+            for (int64_t i = 0; i < nu; ++i) {
+                const int s = static_cast<int>(i % S);
+                const int64_t f = i / S;
+                if (f >= 1 && !mbar_wait(empty0 + 8 * s, static_cast<uint32_t>((f - 1) & 1), lim, abort_sm)) {
+                    fail(abort_sm, P.err);
+                    break;
+                }
+                const int64_t u = u0 + i;
+                const int g = static_cast<int>(u / KC), kc = static_cast<int>(u % KC);
+                const uint32_t st = smem_addr(smem + s * STAGE);
+                const uint32_t fb = full0 + 8 * s;
+                mbar_arrive_expect_tx(fb, STAGE);
+                tma_load_2d(st, &tmB, kc * TILE, 0, fb);
+                tma_load_2d(st + NP * 128, &tmB, kc * TILE + 64, 0, fb);
+                tma_load_4d(st + B_BYTES, &tmA, 0, 0, kc, g * T, fb);
+                issued = i + 1;
+            }
+            // never leave a copy in flight into shared memory we are about to give up
+            for (int64_t i = issued > S ? issued - S : 0; i < issued; ++i)
+                mbar_wait(full0 + 8 * static_cast<int>(i % S), static_cast<uint32_t>((i / S) & 1), DRAIN_LIMIT,
+                          &g_never_set);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16_f32(128, NP);
+            int64_t j = 0, wi = -1, wstart = 0;
+            bool ok = true;
+            for (int64_t i = 0; i < nu && ok; ++i) {
+                const int s = static_cast<int>(i % S);
+                const int64_t f = i / S;
+                const int64_t u = u0 + i;
+                const int kc = static_cast<int>(u % KC);
+                const bool first = window_first(i, kc, wstart, F);
+                if (first) {
+                    ++wi;
+                    wstart = i;
+                    if (wi >= 2 && !mbar_wait(acce0 + 8 * (wi & 1), static_cast<uint32_t>(((wi >> 1) - 1) & 1), lim, abort_sm)) {
+                        ok = false;
+                        break;
+                    }
+                }
+                const bool last = (i == nu - 1) || (kc == KC - 1) || (i + 1 - wstart == F);
+                const int b = static_cast<int>(wi & 1);
+                if (!mbar_wait(full0 + 8 * s, static_cast<uint32_t>(f & 1), lim, abort_sm)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t st_b = smem_addr(smem + s * STAGE);
+#pragma unroll 1
+                for (int t = 0; t < T; ++t) {
+                    const int r = static_cast<int>(j % R);
+                    const int64_t m = j / R;
+                    if (!mbar_wait(afull0 + 8 * r, static_cast<uint32_t>(m & 1), lim, abort_sm)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tbase + static_cast<uint32_t>((b * T + t) * NP);
+                    const uint32_t a = tbase + static_cast<uint32_t>(ACC_COLS + 64 * r);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const uint64_t bd = smem_desc_sw128(st_b + (q >> 2) * NP * 128 + (q & 3) * 32);
+                        mma_ts(d, a + 8 * q, bd, idesc, (first && q == 0) ? 0u : 1u);
+                    }
+                    mma_commit(aempty0 + 8 * r);
+                    ++j;
+                }
+                if (!ok) break;
+                mma_commit(empty0 + 8 * s);
+                if (last) mma_commit(accf0 + 8 * b);
+            }
+            if (!ok) fail(abort_sm, P.err);
+            mma_commit(drainb);
+            mbar_wait(drainb, 0, DRAIN_LIMIT, &g_never_set);
+        }
+    } else {
+        // ---------------- decoders / accumulators / epilogue ----------------
+        const int h = (warp - 2) >> 2;    // K half of each chunk (64 codes)
+        const int q = warp & 3;           // TMEM lane quarter
+        const int rit = 32 * q + lane;    // row inside a 128-row tile
+        const uint32_t lane_base = tbase + (static_cast<uint32_t>(32 * q) << 16);
+        float acc[T][KH];
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+#pragma unroll
+            for (int e = 0; e < KH; ++e) acc[t][e] = 0.f;
+
+        int64_t j = 0, wi = -1, wstart = 0;
+        bool pend = false, pend_segend = false;
+        int pend_b = 0, pend_g = 0;
+        int64_t pend_m = 0;
+        uint32_t epi_phase = 0;
+        bool ok = true;
+
+        auto drain = [&](int b, int64_t m, bool segend, int g) {
+            if (!ok) return;
+            if (!__all_sync(0xffffffffu, mbar_wait(accf0 + 8 * b, static_cast<uint32_t>(m & 1), lim, abort_sm))) {
+                ok = false;
+                return;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+#pragma unroll
+                for (int cc = 0; cc < KH / 4; ++cc) {
+                    uint32_t v[8];
+                    tmem_ld_32x32b_x8(lane_base + static_cast<uint32_t>((b * T + t) * NP + h * (NP / 2) + cc * 8), v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        acc[t][cc * 4 + e] += __uint_as_float(v[2 * e]) + __uint_as_float(v[2 * e + 1]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce0 + 8 * b);
+            if (!segend) return;
+
+            // write this CTA's partial of group g
+            const int64_t first_cta = (static_cast<int64_t>(g) * KC) / P.L;
+            const int64_t slot = cta - first_cta;
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const int64_t row = (static_cast<int64_t>(g) * T + t) * TILE + rit;
+#pragma unroll
+                for (int e = 0; e < KH; ++e) {
+                    const int kk = h * KH + e;
+                    if (kk < P.k)
+                        P.part[slot * P.slot_stride + kk * P.rows_pad + row] = acc[t][e] * 0x1.0p64f;
+                    acc[t][e] = 0.f;
+                }
+            }
+            if (P.epi == EPI_PARTIAL) return;
+
+            // last CTA of the group applies the step (Section 5.3: beta <- S(beta + sigma g, sigma lambda))
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(epib);
+            if (!__all_sync(0xffffffffu, mbar_wait(epib, epi_phase & 1, lim, abort_sm))) {
+                ok = false;
+                return;
+            }
+            ++epi_phase;
+            const int64_t last_cta = (static_cast<int64_t>(g) * KC + KC - 1) / P.L;
+            const int cnt = static_cast<int>(last_cta - first_cta + 1);
+            if (threadIdx.x == 64) {
+                const int old = atomicAdd(&P.counters[g], 1);
+                const int is_last = (old == cnt - 1);
+                if (is_last) P.counters[g] = 0;
+                *last_sm = is_last;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(epib);
+            if (!__all_sync(0xffffffffu, mbar_wait(epib, epi_phase & 1, lim, abort_sm))) {
+                ok = false;
+                return;
+            }
+            ++epi_phase;
+            if (!*last_sm) return;
+            __threadfence();
+            const int tid = threadIdx.x - 64;
+            const int64_t grows = static_cast<int64_t>(T) * TILE;
+            for (int64_t idx = tid; idx < grows * P.k; idx += 256) {
+                const int kk = static_cast<int>(idx / grows);
+                const int64_t row = static_cast<int64_t>(g) * grows + idx % grows;
+                if (row >= P.rows_valid) continue;
+                double G = 0.0;
+                for (int s2 = 0; s2 < cnt; ++s2) G += static_cast<double>(__ldcg(&P.part[s2 * P.slot_stride + kk * P.rows_pad + row]));
+                const double gv = (G - P.mu[row] * P.sumV[kk]) * P.inv_n;
+                const int64_t bi = static_cast<int64_t>(kk) * P.rows_valid + row;
+                if (P.epi == EPI_PROX) {
+                    if (P.active && !P.active[kk]) continue;
+                    const double z = static_cast<double>(P.beta[bi]) + P.step * gv;
+                    const double thr = P.step * P.lam[kk];
+                    P.beta[bi] = static_cast<float>(z > thr ? z - thr : (z < -thr ? z + thr : 0.0));
+                } else {
+                    P.grad[bi] = static_cast<float>(-gv);
+                }
+            }
+        };
+
+        for (int64_t i = 0; i < nu && ok; ++i) {
+            const int s = static_cast<int>(i % S);
+            const int64_t f = i / S;
+            const int64_t u = u0 + i;
+            const int g = static_cast<int>(u / KC), kc = static_cast<int>(u % KC);
+            if (window_first(i, kc, wstart, F)) {
+                ++wi;
+                wstart = i;
+                if (pend) {
+                    drain(pend_b, pend_m, pend_segend, pend_g);
+                    pend = false;
+                    if (!ok) break;
+                }
+            }
+            const bool last = (i == nu - 1) || (kc == KC - 1) || (i + 1 - wstart == F);
+            bool w_ok = mbar_wait(full0 + 8 * s, static_cast<uint32_t>(f & 1), lim, abort_sm);
+            if (!__all_sync(0xffffffffu, w_ok)) {
+                ok = false;
+                break;
+            }
+            const uint8_t *xs = smem + s * STAGE + B_BYTES;
+#pragma unroll 1
+            for (int t = 0; t < T; ++t) {
+                const int r = static_cast<int>(j % R);
+                const int64_t m = j / R;
+                if (m >= 1) {
+                    w_ok = mbar_wait(aempty0 + 8 * r, static_cast<uint32_t>((m - 1) & 1), lim, abort_sm);
+                    if (!__all_sync(0xffffffffu, w_ok)) {
+                        ok = false;
+                        break;
+                    }
+                }
+                tc_fence_after();
+                const int phys = h ^ ((rit >> 2) & 1);
+                const uint4 v = *reinterpret_cast<const uint4 *>(xs + t * BLOCK_BYTES + rit * 32 + phys * 16);
+                uint32_t o[32];
+                decode16(v.x, o);
+                decode16(v.y, o + 8);
+                decode16(v.z, o + 16);
+                decode16(v.w, o + 24);
+                tmem_st_32x32b_x32(lane_base + static_cast<uint32_t>(ACC_COLS + 64 * r + 32 * h), o);
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(afull0 + 8 * r);
+                ++j;
+            }
+            if (!ok) break;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty0 + 8 * s);
+            if (last) {
+                pend = true;
+                pend_b = static_cast<int>(wi & 1);
+                pend_m = wi >> 1;
+                pend_segend = (i == nu - 1) || (kc == KC - 1);
+                pend_g = g;
+            }
+        }
+        if (ok && pend) drain(pend_b, pend_m, pend_segend, pend_g);
+        if (!ok) fail(abort_sm, P.err);
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 512);
+    }
+}
+
+// beta (p x k fp32, column-major) -> bf16 limbs [NP][p_pad], scaled per K slot.
+__global__ void k_prep_limbs_beta(const float *__restrict__ beta, int64_t p, int k, int64_t p_pad,
+                                  uint16_t *__restrict__ Bb)
+{
+    const int kk = blockIdx.y;
+    for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < p;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int tsl = ((((j & 15) >> 1) % 3));
+        const float bs = ldexpf(beta[static_cast<int64_t>(kk) * p + j], 69 - 2 * tsl);
+        const __nv_bfloat16 hi = __float2bfloat16_rn(bs);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(bs - __bfloat162float(hi));
+        Bb[(2 * kk) * p_pad + j] = __bfloat16_as_ushort(hi);
+        Bb[(2 * kk + 1) * p_pad + j] = __bfloat16_as_ushort(lo);
+    }
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled get_encoder()
+{
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+using KernelFn = void (*)(const CUtensorMap, const CUtensorMap, const KParams);
+
+KernelFn pick_kernel(int T, int NP)
+{
+    switch (T * 1000 + NP) {
+    case 1016: return k_packed_gemm<1, 16>;
+    case 2016: return k_packed_gemm<2, 16>;
+    case 4016: return k_packed_gemm<4, 16>;
+    case 8016: return k_packed_gemm<8, 16>;
+    case 1032: return k_packed_gemm<1, 32>;
+    case 2032: return k_packed_gemm<2, 32>;
+    case 4032: return k_packed_gemm<4, 32>;
+    case 1064: return k_packed_gemm<1, 64>;
+    case 2064: return k_packed_gemm<2, 64>;
+    case 1128: return k_packed_gemm<1, 128>;
+    default: return nullptr;
+    }
+}
+
+} // namespace
+
+// Plan one product: A (rows_pad x K_pad, tiled 2-bit) times B limbs (NP x K_pad).
+int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, int64_t K_pad,
+              const uint16_t *B, int k, int T_req, int stages_req)
+{
+    if (k < 1 || k > MAX_K_TC) return COX_ERR_ARG;
+    const int NP = (2 * k + 15) / 16 * 16;
+    int np_cls = NP <= 16 ? 16 : NP <= 32 ? 32 : NP <= 64 ? 64 : 128;
+    const int64_t m_tiles = rows_pad / TILE;
+    int T = T_req > 0 ? T_req : 4;
+    if (T != 1 && T != 2 && T != 4 && T != 8) return COX_ERR_ARG;
+    if (np_cls == 32 && T > 4) T = 4;
+    if (np_cls == 64 && T > 2) T = 2;
+    if (np_cls == 128) T = 1;
+    if (m_tiles % T != 0) return COX_ERR_ARG;
+    g.T = T;
+    g.NP = np_cls;
+    const int acc_cols = 2 * T * np_cls;
+    g.ring = (512 - acc_cols) / 64;
+    if (g.ring > 8) g.ring = 8;
+    if (g.ring < 2) return COX_ERR_ARG;
+    const int stage = np_cls * 256 + T * BLOCK_BYTES;
+    int S = stages_req > 0 ? stages_req : (225 * 1024 - 2048) / stage;
+    if (S > 8) S = 8;
+    if (S < 2) S = 2;
+    g.stages = S;
+    g.smem = static_cast<size_t>(S) * stage + 1024 + 1024;
+    if (g.smem < 120 * 1024) g.smem = 120 * 1024;  // one CTA per SM: it owns all 512 TMEM columns
+    g.F = 32;
+    g.KC = static_cast<int>(K_pad / TILE);
+    g.n_groups = static_cast<int>(m_tiles / T);
+    g.units = static_cast<int64_t>(g.n_groups) * g.KC;
+    int grid = h->sm_count;
+    if (g.units < grid) grid = static_cast<int>(g.units);
+    g.L = (g.units + grid - 1) / grid;
+    g.grid = static_cast<int>((g.units + g.L - 1) / g.L);
+    int ms = 1;
+    for (int64_t gg = 0; gg < g.n_groups; ++gg) {
+        const int64_t fc = (gg * g.KC) / g.L, lc = (gg * g.KC + g.KC - 1) / g.L;
+        if (lc - fc + 1 > ms) ms = static_cast<int>(lc - fc + 1);
+    }
+    g.max_slots = ms;
+    g.rows_pad = rows_pad;
+    {
+        KernelFn fn = pick_kernel(g.T, g.NP);
+        if (!fn) return COX_ERR_ARG;
+        COX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(g.smem)));
+    }
+
+    EncodeTiled enc = get_encoder();
+    if (!enc) return COX_ERR_CUDA;
+    {
+        cuuint64_t dims[4] = {8, 128, static_cast<cuuint64_t>(g.KC), static_cast<cuuint64_t>(m_tiles)};
+        cuuint64_t strides[3] = {32, BLOCK_BYTES, static_cast<cuuint64_t>(g.KC) * BLOCK_BYTES};
+        cuuint32_t box[4] = {8, 128, 1, static_cast<cuuint32_t>(T)};
+        cuuint32_t es[4] = {1, 1, 1, 1};
+        CUresult r = enc(&g.tmA, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, const_cast<uint32_t *>(A), dims, strides,
+                         box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return COX_ERR_CUDA;
+    }
+    {
+        cuuint64_t dims[2] = {static_cast<cuuint64_t>(K_pad), static_cast<cuuint64_t>(np_cls)};
+        cuuint64_t strides[1] = {static_cast<cuuint64_t>(K_pad) * 2};
+        cuuint32_t box[2] = {64, static_cast<cuuint32_t>(np_cls)};
+        cuuint32_t es[2] = {1, 1};
+        CUresult r = enc(&g.tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(B), dims, strides,
+                         box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return COX_ERR_CUDA;
+    }
+    return COX_OK;
+}
+
+int launch_gemm(cox_handle *h, const GemmPlan &g, const EpiArgs &e, int k, cudaStream_t st)
+{
+    KParams kp;
+    kp.KC = g.KC;
+    kp.F = g.F;
+    kp.k = k;
+    kp.stages = g.stages;
+    kp.ring = g.ring;
+    kp.units = g.units;
+    kp.L = g.L;
+    kp.rows_pad = g.rows_pad;
+    kp.slot_stride = static_cast<int64_t>(k) * g.rows_pad;
+    kp.part = e.part;
+    kp.epi = e.epi;
+    kp.counters = e.counters;
+    kp.beta = e.beta;
+    kp.grad = e.grad;
+    kp.lam = e.lam;
+    kp.step = e.step;
+    kp.mu = e.mu;
+    kp.sumV = e.sumV;
+    kp.active = e.active;
+    kp.rows_valid = e.rows_valid;
+    kp.inv_n = e.inv_n;
+    kp.wait_limit = h->wait_cycles;
+    kp.err = h->d_err;
+    KernelFn fn = pick_kernel(g.T, g.NP);
+    if (!fn) return COX_ERR_ARG;
+    fn<<<g.grid, 320, g.smem, st>>>(g.tmA, g.tmB, kp);
+    COX_CUDA(cudaGetLastError());
+    return COX_OK;
+}
+
+int prep_limbs_beta(cox_handle *h, const float *beta, int k, uint16_t *Bb, int NP, cudaStream_t st)
+{
+    (void)NP;
+    dim3 grid(static_cast<unsigned>(std::min<int64_t>((h->p + 255) / 256, 4096)), k);
+    k_prep_limbs_beta<<<grid, 256, 0, st>>>(beta, h->p, k, h->p_pad, Bb);
+    COX_CUDA(cudaGetLastError());
+    return COX_OK;
+}
+
+} // namespace coxgb

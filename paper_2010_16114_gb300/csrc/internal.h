@@ -1,0 +1,182 @@
+// internal.h -- handle layout and cross-file entry points of libcoxgb.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/coxgb.h"
+
+namespace coxgb {
+
+// Device-side error bits (OR-ed into handle->d_err by kernels).
+enum : int { DEVERR_TIMEOUT = 1, DEVERR_NONFINITE = 2, DEVERR_CODE3 = 4 };
+
+constexpr int TILE = 128;          // rows per tensor-core tile, K per chunk
+constexpr int BLOCK_BYTES = 4096;  // one 128 x 128 block of 2-bit codes
+constexpr int PAD = 1024;          // n, p padding of the tiled layouts
+constexpr int SCAN_CH = 2048;      // subjects per scan chunk (256 threads x 8)
+constexpr int MAX_K_TC = 64;       // largest k of the tensor-core path
+
+// One tensor-core product: a 2-bit A (rows x K, tiled) times limb matrix B.
+struct GemmPlan {
+    int T = 4;         // 128-row tiles per CTA (one M group)
+    int NP = 16;       // limb columns (2k rounded up to 16)
+    int stages = 6;    // shared-memory pipeline depth
+    int ring = 4;      // TMEM A buffers
+    int F = 64;        // K chunks per TMEM accumulation window
+    int grid = 0;      // CTAs
+    int KC = 0;        // K chunks
+    int n_groups = 0;  // M groups
+    int64_t units = 0, L = 0;
+    int max_slots = 1;
+    int64_t rows_pad = 0;  // row stride of the partial buffer
+    size_t smem = 0;
+    CUtensorMap tmA, tmB;
+};
+
+struct Workspace {
+    int k = 0;        // columns the workspace is sized for
+    int NP = 0;
+    // split / gemv / fp64 common (sorted subject order)
+    double *eta = nullptr;      // k x n
+    double *w = nullptr;        // k x n
+    double *Rt = nullptr;       // k x n local reverse scans
+    double *Ft = nullptr;       // k x n local forward scans
+    double *cmax = nullptr, *csw = nullptr, *csd = nullptr, *suf = nullptr, *pre = nullptr;
+    double *lossp = nullptr, *vsp = nullptr;  // k x chunks
+    double *l1p = nullptr;                    // k x l1 blocks
+    double *sumV = nullptr, *f = nullptr, *F = nullptr, *l1 = nullptr;  // k
+    double *lam = nullptr;     // k
+    int *active = nullptr;     // k
+    double *Fring = nullptr;   // lag x k
+    // split mode
+    uint16_t *Bb = nullptr;    // NP x p_pad bf16 limbs of beta
+    uint16_t *Vb = nullptr;    // NP x n_pad bf16 limbs of V
+    float *part1 = nullptr;    // slots x k x rows_pad (eta partials)
+    float *part4 = nullptr;    // slots x k x rows_pad (X^T V partials)
+    int *cnt4 = nullptr;       // per M group of the second product
+    // fp64 / gemv
+    double *V64 = nullptr;     // k x n
+    float *V32 = nullptr;      // n
+    float *eta32 = nullptr;    // n
+    float *G32 = nullptr;      // p
+    GemmPlan g1, g4;
+    bool plans_ready = false;
+};
+
+} // namespace coxgb
+
+struct cox_handle {
+    int dev = 0, sm_count = 0;
+    int64_t n = 0, p = 0, n_pad = 0, p_pad = 0;
+    int n_chunks = 0, l1_blocks = 0;
+    cox_options opt;
+    int64_t n_groups_tie = 0;
+    // sorted order (host copies)
+    std::vector<int64_t> h_order;
+    std::vector<double> h_mu;
+    // device data
+    int32_t *d_head = nullptr, *d_tail = nullptr;
+    uint8_t *d_delta = nullptr;
+    double *d_mu = nullptr;
+    uint32_t *d_A1 = nullptr;  // subject-major 2-bit tiles
+    uint32_t *d_A4 = nullptr;  // SNP-major 2-bit tiles
+    double *d_Xr = nullptr;    // FP64: n x p, sorted rows
+    double *d_Xc = nullptr;    // FP64: p x n (columns), sorted subjects
+    int *d_err = nullptr;
+    int64_t device_bytes = 0;
+    long long wait_cycles = 0;
+    coxgb::Workspace ws;
+    // path / checkpoint state
+    int st_k = 0;
+    std::vector<float> st_beta32;
+    std::vector<double> st_beta64;
+    std::vector<int> st_iters;
+    std::vector<double> st_F;
+    std::vector<int> st_active;
+    int64_t st_step = 0;
+};
+
+namespace coxgb {
+
+// ---- error helpers ----------------------------------------------------------
+int cuda_status(cudaError_t e);
+#define COX_CUDA(x)                                      \
+    do {                                                 \
+        cudaError_t e_ = (x);                            \
+        if (e_ != cudaSuccess) return coxgb::cuda_status(e_); \
+    } while (0)
+#define COX_TRY(x)            \
+    do {                      \
+        int r_ = (x);         \
+        if (r_ != COX_OK) return r_; \
+    } while (0)
+
+int dmalloc(cox_handle *h, void **p, size_t bytes);
+void dfree(void *p);
+
+// ---- setup (setup.cu) ----------------------------------------------------------
+int setup_genotypes(cox_handle *h, const void *X, int x_format, cudaStream_t st);
+int setup_dense64(cox_handle *h, const double *X, cudaStream_t st);
+
+// ---- workspace / plans / one iteration (api.cu) ----------------------------------
+int ensure_workspace(cox_handle *h, int k);
+int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, cudaStream_t st);
+
+// ---- scans (scans.cu) -------------------------------------------------------------
+// Risk-set scans on eta (sorted order, k columns).  eta_src kinds:
+enum EtaSrc { ETA_PARTIAL_F32 = 0, ETA_DENSE_F64 = 1, ETA_DENSE_F32 = 2 };
+enum VOut { V_LIMBS_BF16 = 0, V_DENSE_F64 = 1, V_DENSE_F32 = 2 };
+struct ScanArgs {
+    int k;
+    int eta_src;
+    const void *eta;      // partial f32 [slot][k][rows_pad] or dense [k][n]
+    int64_t slot_stride, col_stride;  // partial layout
+    int group_rows, KC;   // partial slot counts: group of a row, K chunks, L
+    int64_t L;
+    int v_out;
+    void *V;              // limbs [NP][n_pad] or dense [k][n]
+    int NP;
+    bool exp64;           // exp in FP64 (FP64 mode) or FP32
+    const double *lam;    // k (objective); may be null
+    bool need_loss;
+};
+int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st);
+
+// ---- tensor-core products (gemm_tc.cu) ---------------------------------------------
+int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, int64_t K_pad,
+              const uint16_t *B, int k, int T_req, int stages_req);
+enum Epi { EPI_PARTIAL = 0, EPI_PROX = 1, EPI_GRAD = 2 };
+struct EpiArgs {
+    int epi = EPI_PARTIAL;
+    float *part = nullptr;
+    int *counters = nullptr;
+    float *beta = nullptr;   // p x k (prox: in/out)
+    float *grad = nullptr;   // p x k (grad output)
+    const double *lam = nullptr;
+    double step = 0;
+    const double *mu = nullptr;
+    const double *sumV = nullptr;
+    const int *active = nullptr;
+    int64_t rows_valid = 0;  // p
+    double inv_n = 0;
+};
+int launch_gemm(cox_handle *h, const GemmPlan &g, const EpiArgs &e, int k, cudaStream_t st);
+int prep_limbs_beta(cox_handle *h, const float *beta, int k, uint16_t *Bb, int NP, cudaStream_t st);
+
+// ---- CUDA-core paths (gemv.cu) -----------------------------------------------------
+int l1_norms32(cox_handle *h, const float *beta, int k, cudaStream_t st);
+int l1_norms64(cox_handle *h, const double *beta, int k, cudaStream_t st);
+int gemv_tiles(cox_handle *h, const uint32_t *A, int64_t rows, int64_t KC, const float *x,
+               int64_t K_valid, float *y, cudaStream_t st);
+int prox_or_grad32(cox_handle *h, const float *G, int col, float *beta, float *grad,
+                   const double *lam, double step, cudaStream_t st);
+int eta64(cox_handle *h, const double *beta, int k, double *eta, cudaStream_t st);
+int xtv64(cox_handle *h, const double *V, int k, double *beta, double *grad, const double *lam,
+          double step, cudaStream_t st);
+int center_fix_vec(cox_handle *h, const float *v_in, float *a_out, int64_t len, double sub,
+                   cudaStream_t st);
+
+} // namespace coxgb

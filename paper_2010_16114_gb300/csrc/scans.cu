@@ -1,0 +1,347 @@
+// scans.cu -- Breslow risk-set sums of the Cox iteration in FP64
+// (arXiv 2010.16114, Section 5.3: w = exp(eta), W_j = sum_{y_i >= y_j} w_i,
+// u = P delta; the paper's remark that sorting by time turns W into a
+// cumulative sum; Section 6: Breslow ties).
+//
+// Subjects are stored in ascending time order, so with R_r = sum_{s >= r} w_s
+// (a reverse inclusive scan) and F_r = sum_{s <= r} delta_s / W_s (a forward
+// inclusive scan):
+//   W_r = R_{head(r)}            head = first position of r's tie group
+//   u_r = w_r F_{tail(r)}        tail = last position of r's tie group
+//   V_r = delta_r - u_r          (the vector X^T multiplies)
+//   f   = (1/n) sum_r delta_r (log W_r - (eta_r - c)),  c = max eta.
+// Each scan runs in fixed 2048-subject chunks (block scans with warp
+// shuffles), then an exclusive scan of the chunk totals, then a gather; the
+// summation order never depends on timing, so results are bit-reproducible.
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace coxgb {
+namespace {
+
+constexpr int NT = 256;
+constexpr int PER = SCAN_CH / NT;  // 8
+
+__device__ __forceinline__ double warp_incl_scan(double x, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Inclusive scan of one value per thread across the 256-thread block.
+__device__ __forceinline__ double block_incl_scan(double x, double *sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    x = warp_incl_scan(x, lane);
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        double v = lane < NT / 32 ? sh[lane] : 0.0;
+        v = warp_incl_scan(v, lane);
+        if (lane < NT / 32) sh[lane] = v;
+    }
+    __syncthreads();
+    if (warp > 0) x += sh[warp - 1];
+    __syncthreads();
+    return x;
+}
+
+__device__ __forceinline__ double block_sum(double x, double *sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[warp] = x;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < NT / 32; ++w) t += sh[w];
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+__device__ __forceinline__ double block_max(double x, double *sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if (lane == 0) sh[warp] = x;
+    __syncthreads();
+    double t = -INFINITY;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < NT / 32; ++w) t = fmax(t, sh[w]);
+    __syncthreads();
+    return t;
+}
+
+struct SP {
+    int64_t n, n_pad;
+    int nch, k;
+    const uint8_t *delta;
+    const int32_t *head, *tail;
+    double *eta, *w, *Rt, *Ft, *cmax, *csw, *csd, *suf, *pre, *lossp, *vsp;
+};
+
+// (1) eta = sum of the product's partial slots (or a dense copy); chunk maxima.
+template <int SRC>
+__global__ void k_eta(SP s, const void *src, int64_t slot_stride, int64_t col_stride, int group_rows,
+                      int KC, int64_t L)
+{
+    __shared__ double sh[NT / 32];
+    const int c = blockIdx.x, kk = blockIdx.y;
+    const int64_t i0 = static_cast<int64_t>(c) * SCAN_CH;
+    double mx = -INFINITY;
+    for (int e = threadIdx.x; e < SCAN_CH; e += NT) {
+        const int64_t i = i0 + e;
+        if (i >= s.n) break;
+        double v;
+        if (SRC == ETA_PARTIAL_F32) {
+            const float *part = static_cast<const float *>(src);
+            const int64_t g = i / group_rows;
+            const int64_t cnt = (g * KC + KC - 1) / L - (g * KC) / L + 1;
+            v = 0.0;
+            for (int64_t sl = 0; sl < cnt; ++sl) v += static_cast<double>(part[sl * slot_stride + kk * col_stride + i]);
+        } else if (SRC == ETA_DENSE_F32) {
+            v = static_cast<double>(static_cast<const float *>(src)[kk * col_stride + i]);
+        } else {
+            v = static_cast<const double *>(src)[kk * col_stride + i];
+        }
+        s.eta[kk * s.n + i] = v;
+        mx = fmax(mx, v);
+    }
+    const double m = block_max(mx, sh);
+    if (threadIdx.x == 0) s.cmax[kk * s.nch + c] = m;
+}
+
+__device__ __forceinline__ double column_max(const SP &s, int kk, double *sh)
+{
+    double m = -INFINITY;
+    for (int c = threadIdx.x; c < s.nch; c += NT) m = fmax(m, s.cmax[kk * s.nch + c]);
+    m = block_max(m, sh);
+    if (threadIdx.x == 0) sh[0] = m;
+    __syncthreads();
+    m = sh[0];
+    __syncthreads();
+    return m;
+}
+
+// (2) w = exp(eta - c); chunk-local reverse inclusive scan of w; chunk totals.
+template <bool EXP64>
+__global__ void k_rev(SP s)
+{
+    __shared__ double sh[NT / 32];
+    __shared__ double buf[SCAN_CH];
+    const int c = blockIdx.x, kk = blockIdx.y;
+    const double cmx = column_max(s, kk, sh);
+    const int64_t i0 = static_cast<int64_t>(c) * SCAN_CH;
+    for (int e = threadIdx.x; e < SCAN_CH; e += NT) {
+        const int64_t i = i0 + e;
+        double wv = 0.0;
+        if (i < s.n) {
+            const double x = s.eta[kk * s.n + i] - cmx;
+            wv = EXP64 ? exp(x) : static_cast<double>(expf(static_cast<float>(x)));
+            s.w[kk * s.n + i] = wv;
+        }
+        buf[e] = wv;
+    }
+    __syncthreads();
+    // thread t owns reversed positions [PER t, PER t + PER): elements SCAN_CH-1-(PER t + j)
+    double loc[PER];
+    double run = 0.0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        run += buf[SCAN_CH - 1 - (PER * threadIdx.x + j)];
+        loc[j] = run;
+    }
+    const double incl = block_incl_scan(run, sh);
+    const double excl = incl - run;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) buf[SCAN_CH - 1 - (PER * threadIdx.x + j)] = loc[j] + excl;
+    __syncthreads();
+    for (int e = threadIdx.x; e < SCAN_CH; e += NT) {
+        const int64_t i = i0 + e;
+        if (i < s.n) s.Rt[kk * s.n + i] = buf[e];
+    }
+    if (threadIdx.x == NT - 1) s.csw[kk * s.nch + c] = incl;
+}
+
+// exclusive scans of chunk totals: suffix (reverse) or prefix (forward)
+template <bool SUFFIX>
+__global__ void k_chunks(SP s)
+{
+    const int kk = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    const double *src = SUFFIX ? s.csw : s.csd;
+    double *dst = SUFFIX ? s.suf : s.pre;
+    double acc = 0.0;
+    if (SUFFIX) {
+        for (int c = s.nch - 1; c >= 0; --c) {
+            dst[kk * s.nch + c] = acc;
+            acc += src[kk * s.nch + c];
+        }
+    } else {
+        for (int c = 0; c < s.nch; ++c) {
+            dst[kk * s.nch + c] = acc;
+            acc += src[kk * s.nch + c];
+        }
+    }
+}
+
+// (3) W = R at the tie head; D = delta / W; loss terms; chunk-local forward scan of D.
+__global__ void k_fwd(SP s, bool need_loss)
+{
+    __shared__ double sh[NT / 32];
+    __shared__ double buf[SCAN_CH];
+    const int c = blockIdx.x, kk = blockIdx.y;
+    const double cmx = need_loss ? column_max(s, kk, sh) : 0.0;
+    const int64_t i0 = static_cast<int64_t>(c) * SCAN_CH;
+    double lsum = 0.0;
+    for (int e = threadIdx.x; e < SCAN_CH; e += NT) {
+        const int64_t i = i0 + e;
+        double d = 0.0;
+        if (i < s.n && s.delta[i]) {
+            const int64_t hd = s.head[i];
+            const double W = s.Rt[kk * s.n + hd] + s.suf[kk * s.nch + hd / SCAN_CH];
+            d = 1.0 / W;
+            if (need_loss) lsum += log(W) - (s.eta[kk * s.n + i] - cmx);
+        }
+        buf[e] = d;
+    }
+    __syncthreads();
+    double loc[PER];
+    double run = 0.0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        run += buf[PER * threadIdx.x + j];
+        loc[j] = run;
+    }
+    const double incl = block_incl_scan(run, sh);
+    const double excl = incl - run;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) buf[PER * threadIdx.x + j] = loc[j] + excl;
+    __syncthreads();
+    for (int e = threadIdx.x; e < SCAN_CH; e += NT) {
+        const int64_t i = i0 + e;
+        if (i < s.n) s.Ft[kk * s.n + i] = buf[e];
+    }
+    if (threadIdx.x == NT - 1) s.csd[kk * s.nch + c] = incl;
+    if (need_loss) {
+        const double t = block_sum(lsum, sh);
+        if (threadIdx.x == 0) s.lossp[kk * s.nch + c] = t;
+    }
+}
+
+// (4) C = F at the tie tail; u = w C; V = delta - u -> output form; sum of V.
+template <int VO>
+__global__ void k_uv(SP s, void *Vout, int64_t n_pad)
+{
+    __shared__ double sh[NT / 32];
+    const int c = blockIdx.x, kk = blockIdx.y;
+    const int64_t i0 = static_cast<int64_t>(c) * SCAN_CH;
+    double vs = 0.0;
+    for (int e = threadIdx.x; e < SCAN_CH; e += NT) {
+        const int64_t i = i0 + e;
+        if (i >= s.n) break;
+        const int64_t tl = s.tail[i];
+        const double C = s.Ft[kk * s.n + tl] + s.pre[kk * s.nch + tl / SCAN_CH];
+        const double u = s.w[kk * s.n + i] * C;
+        const double V = static_cast<double>(s.delta[i]) - u;
+        vs += V;
+        if (VO == V_LIMBS_BF16) {
+            const int tsl = (((i & 15) >> 1) % 3);
+            const double Vs = ldexp(V, 69 - 2 * tsl);
+            const __nv_bfloat16 hi = __float2bfloat16_rn(static_cast<float>(Vs));
+            const __nv_bfloat16 lo = __float2bfloat16_rn(static_cast<float>(Vs - static_cast<double>(__bfloat162float(hi))));
+            uint16_t *Vb = static_cast<uint16_t *>(Vout);
+            Vb[(2 * kk) * n_pad + i] = __bfloat16_as_ushort(hi);
+            Vb[(2 * kk + 1) * n_pad + i] = __bfloat16_as_ushort(lo);
+        } else if (VO == V_DENSE_F64) {
+            static_cast<double *>(Vout)[kk * s.n + i] = V;
+        } else {
+            static_cast<float *>(Vout)[kk * s.n + i] = static_cast<float>(V);
+        }
+    }
+    const double t = block_sum(vs, sh);
+    if (threadIdx.x == 0) s.vsp[kk * s.nch + c] = t;
+}
+
+// (5) per column: sum V, f, ||beta||_1, F = f + lambda ||beta||_1; flag non-finite.
+__global__ void k_finalize(SP s, int l1_blocks, const double *l1p, const double *lam, double *sumV,
+                           double *f, double *l1, double *Fobj, bool need_loss, int *err)
+{
+    const int kk = threadIdx.x;
+    if (kk >= s.k) return;
+    double v = 0.0, lo = 0.0, b1 = 0.0;
+    for (int c = 0; c < s.nch; ++c) v += s.vsp[kk * s.nch + c];
+    sumV[kk] = v;
+    if (need_loss) {
+        for (int c = 0; c < s.nch; ++c) lo += s.lossp[kk * s.nch + c];
+        lo /= static_cast<double>(s.n);
+        f[kk] = lo;
+        if (l1p)
+            for (int c = 0; c < l1_blocks; ++c) b1 += l1p[kk * l1_blocks + c];
+        l1[kk] = b1;
+        Fobj[kk] = lo + (lam ? lam[kk] * b1 : 0.0);
+        if (!isfinite(lo)) atomicOr(err, DEVERR_NONFINITE);
+    }
+    if (!isfinite(v)) atomicOr(err, DEVERR_NONFINITE);
+}
+
+} // namespace
+
+int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st)
+{
+    Workspace &ws = h->ws;
+    SP s;
+    s.n = h->n;
+    s.n_pad = h->n_pad;
+    s.nch = h->n_chunks;
+    s.k = a.k;
+    s.delta = h->d_delta;
+    s.head = h->d_head;
+    s.tail = h->d_tail;
+    s.eta = ws.eta;
+    s.w = ws.w;
+    s.Rt = ws.Rt;
+    s.Ft = ws.Ft;
+    s.cmax = ws.cmax;
+    s.csw = ws.csw;
+    s.csd = ws.csd;
+    s.suf = ws.suf;
+    s.pre = ws.pre;
+    s.lossp = ws.lossp;
+    s.vsp = ws.vsp;
+    dim3 grid(h->n_chunks, a.k);
+    switch (a.eta_src) {
+    case ETA_PARTIAL_F32:
+        k_eta<ETA_PARTIAL_F32><<<grid, NT, 0, st>>>(s, a.eta, a.slot_stride, a.col_stride, a.group_rows, a.KC, a.L);
+        break;
+    case ETA_DENSE_F32:
+        k_eta<ETA_DENSE_F32><<<grid, NT, 0, st>>>(s, a.eta, 0, a.col_stride, 1, 1, 1);
+        break;
+    default:
+        k_eta<ETA_DENSE_F64><<<grid, NT, 0, st>>>(s, a.eta, 0, a.col_stride, 1, 1, 1);
+        break;
+    }
+    if (a.exp64) k_rev<true><<<grid, NT, 0, st>>>(s);
+    else k_rev<false><<<grid, NT, 0, st>>>(s);
+    k_chunks<true><<<a.k, 32, 0, st>>>(s);
+    k_fwd<<<grid, NT, 0, st>>>(s, a.need_loss);
+    k_chunks<false><<<a.k, 32, 0, st>>>(s);
+    switch (a.v_out) {
+    case V_LIMBS_BF16: k_uv<V_LIMBS_BF16><<<grid, NT, 0, st>>>(s, a.V, h->n_pad); break;
+    case V_DENSE_F64: k_uv<V_DENSE_F64><<<grid, NT, 0, st>>>(s, a.V, h->n_pad); break;
+    default: k_uv<V_DENSE_F32><<<grid, NT, 0, st>>>(s, a.V, h->n_pad); break;
+    }
+    k_finalize<<<1, 64, 0, st>>>(s, h->l1_blocks, a.need_loss ? ws.l1p : nullptr, a.lam, ws.sumV, ws.f, ws.l1,
+                                 ws.F, a.need_loss, h->d_err);
+    COX_CUDA(cudaGetLastError());
+    return COX_OK;
+}
+
+} // namespace coxgb

@@ -1,0 +1,228 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (stated per result; derived in the design doc):
+  * FP64 path (config-0 recipe): beta and gradient relative L2 <= 1e-10.
+  * split-bf16 tensor-core path and FP32 baseline: gradient relative L2 <= 1e-5,
+    loss relative error <= 1e-7, beta relative L2 <= 1e-4 after a fixed number
+    of iterations, identical support outside a 1e-6 threshold margin.
+Sizes are chosen so the oracle finishes in seconds while n and p span several
+128-wide tiles with a ragged tail.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import dense_problem, oracle_loss_grad, rel_l2, support_matches
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2010_16114_gb300 as P
+    P.build()
+    assert torch.cuda.is_available()
+    return P
+
+
+def _problem(pkg, X, w, precision, **kw):
+    from paper_2010_16114_gb300.cox import CoxProblem
+    return CoxProblem(X, w.y, w.delta, precision=precision, **kw)
+
+
+# ---------------------------------------------------------------- FP64 path
+def test_fp64_config0_200_iterations(pkg):
+    """Config 0 as specified: n=1000, p=2000, lambda = 0.5 lambda_max, step 1/L,
+    200 iterations in FP64; beta and gradient within 1e-10 of the oracle."""
+    w, X, Xf, mu = dense_problem(0)
+    v0 = synth.normal_vec(95376, 7, w.p)
+    L = oracle.lipschitz(Xf, mu, v0)
+    lmax = oracle.lambda_max(Xf, mu, w.y, w.delta)
+    lam, sigma = 0.5 * lmax, 1.0 / L
+    beta_o, F_o, _ = oracle.ista(Xf, mu, w.y, w.delta, sigma, lam, 200)
+    with _problem(pkg, Xf, w, "fp64", center=False) as prob:
+        assert abs(prob.lambda_max() - lmax) <= 1e-12 * lmax
+        beta = prob.zeros(1)
+        for _ in range(200):
+            prob.prox_step(beta, [lam], sigma)
+        prob.sync()
+        b = beta.cpu().numpy()[0]
+        assert rel_l2(b, beta_o) <= 1e-10
+        assert (b != 0).sum() == (beta_o != 0).sum()
+        f_o, g_o = oracle_loss_grad(Xf, mu, w.y, w.delta, beta_o)
+        loss, grad = prob.loss_grad(beta)
+        assert abs(loss[0] - f_o) <= 1e-12 * abs(f_o)
+        assert rel_l2(grad.cpu().numpy()[0], g_o) <= 1e-10
+        Lg = prob.lipschitz(v0)
+        assert abs(Lg - L) <= 1e-6 * L
+
+
+# ---------------------------------------------------------------- genotype paths
+GENO_SIZES = [(3000, 700), (1000, 129), (4099, 1500)]
+
+
+@pytest.fixture(scope="module", params=GENO_SIZES, ids=lambda s: f"n{s[0]}_p{s[1]}")
+def geno(request):
+    n, p = request.param
+    return dense_problem(1, n=n, p=p)
+
+
+def _random_betas(p, k, seed):
+    r = np.random.default_rng(seed)
+    B = np.zeros((k, p))
+    for c in range(k):
+        nz = r.choice(p, size=max(1, p // (3 + c)), replace=False)
+        B[c, nz] = r.normal(0, 0.05, len(nz))
+    return B
+
+
+@pytest.mark.parametrize("precision", ["split_bf16", "fp32_gemv"])
+@pytest.mark.parametrize("k", [1, 3, 16])
+def test_loss_grad_geno(pkg, geno, precision, k):
+    w, X, Xf, mu = geno
+    B = _random_betas(w.p, k, 11 + k)
+    with _problem(pkg, X, w, precision) as prob:
+        beta = torch.tensor(B, dtype=torch.float32, device="cuda")
+        loss, grad = prob.loss_grad(beta)
+        G = grad.cpu().numpy()
+        for c in range(k):
+            bc = beta[c].cpu().numpy().astype(np.float64)  # the FP32 master the GPU saw
+            f_o, g_o = oracle_loss_grad(Xf, mu, w.y, w.delta, bc)
+            assert abs(loss[c] - f_o) <= 1e-7 * abs(f_o), (c, loss[c], f_o)
+            assert rel_l2(G[c], g_o) <= 1e-5, (c, rel_l2(G[c], g_o))
+
+
+@pytest.mark.parametrize("precision", ["split_bf16", "fp32_gemv"])
+def test_prox_iterations_geno(pkg, geno, precision):
+    """20 batched iterations for 3 penalties vs the oracle's iterates."""
+    w, X, Xf, mu = geno
+    v0 = synth.normal_vec(95376, 7, w.p)
+    L = oracle.lipschitz(Xf, mu, v0)
+    lmax = oracle.lambda_max(Xf, mu, w.y, w.delta)
+    lams = np.array([0.8, 0.3, 0.1]) * lmax
+    sigma = 1.0 / L
+    iters = 20
+    with _problem(pkg, X, w, precision) as prob:
+        beta = prob.zeros(3)
+        for _ in range(iters):
+            prob.prox_step(beta, lams, sigma)
+        prob.sync()
+        Bg = beta.cpu().numpy().astype(np.float64)
+        for c, lam in enumerate(lams):
+            b_prev, _, g_prev = oracle.ista(Xf, mu, w.y, w.delta, sigma, lam, iters - 1)
+            b_o, _, g_last = oracle.ista(Xf, mu, w.y, w.delta, sigma, lam, 1, b_prev)
+            z = b_prev + sigma * g_last
+            if np.linalg.norm(b_o) == 0:
+                assert np.all(Bg[c] == 0)
+                continue
+            assert rel_l2(Bg[c], b_o) <= 1e-4, (c, rel_l2(Bg[c], b_o))
+            assert support_matches(Bg[c], b_o, z, sigma * lam)
+
+
+def test_lambda_max_and_lipschitz_geno(pkg, geno):
+    w, X, Xf, mu = geno
+    v0 = synth.normal_vec(95376, 7, w.p)
+    L = oracle.lipschitz(Xf, mu, v0)
+    lmax = oracle.lambda_max(Xf, mu, w.y, w.delta)
+    with _problem(pkg, X, w, "split_bf16") as prob:
+        assert abs(prob.lambda_max() - lmax) <= 1e-5 * lmax
+        assert abs(prob.lipschitz(v0) - L) <= 1e-4 * L
+
+
+# ---------------------------------------------------------------- edge cases
+def _edge_case(kind, n=700, p=300):
+    w, X, Xf, mu = dense_problem(1, n=n, p=p)
+    y, d = w.y.copy(), w.delta.copy()
+    if kind == "all_censored":
+        d[:] = 0
+    elif kind == "all_events":
+        d[:] = 1
+    elif kind == "all_tied":
+        y[:] = 5.0
+    elif kind == "one_event":
+        d[:] = 0
+        d[np.argmax(y)] = 1
+    return w, X, Xf, mu, y, d
+
+
+@pytest.mark.parametrize("kind", ["all_censored", "all_events", "all_tied", "one_event"])
+def test_degenerate_cases(pkg, kind):
+    from paper_2010_16114_gb300.cox import CoxProblem
+    w, X, Xf, mu, y, d = _edge_case(kind)
+    B = _random_betas(w.p, 2, 5)
+    with CoxProblem(X, y, d, precision="split_bf16") as prob:
+        beta = torch.tensor(B, dtype=torch.float32, device="cuda")
+        loss, grad = prob.loss_grad(beta)
+        G = grad.cpu().numpy()
+        for c in range(2):
+            f_o, g_o = oracle_loss_grad(Xf, mu, y, d, beta[c].cpu().numpy().astype(np.float64))
+            if np.linalg.norm(g_o) == 0:
+                assert np.all(np.abs(G[c]) <= 1e-12)
+                assert loss[c] == 0.0
+            else:
+                assert abs(loss[c] - f_o) <= 1e-7 * max(abs(f_o), 1e-300)
+                assert rel_l2(G[c], g_o) <= 1e-5
+
+
+def test_single_predictor_and_tiny_n(pkg):
+    for n, p in [(1, 1), (2, 1), (5, 3), (130, 1)]:
+        w, X, Xf, mu = dense_problem(1, n=n, p=p)
+        d = w.delta.copy()
+        d[0] = 1
+        from paper_2010_16114_gb300.cox import CoxProblem
+        with CoxProblem(X, w.y, d, precision="split_bf16") as prob:
+            beta = torch.full((1, p), 0.3, dtype=torch.float32, device="cuda")
+            loss, grad = prob.loss_grad(beta)
+            f_o, g_o = oracle_loss_grad(Xf, mu, w.y, d, np.full(p, 0.3))
+            assert abs(loss[0] - f_o) <= 1e-7 * max(1.0, abs(f_o))
+            assert np.allclose(grad.cpu().numpy()[0], g_o, rtol=1e-5, atol=1e-7)
+
+
+def test_invalid_code_rejected(pkg):
+    from paper_2010_16114_gb300._lib import COX_ERR_CODE3, CoxError
+    from paper_2010_16114_gb300.cox import CoxProblem
+    w, X, Xf, mu = dense_problem(1, n=200, p=50)
+    X = X.copy()
+    X[17, 33] = 3
+    with pytest.raises(CoxError) as ei:
+        CoxProblem(X, w.y, w.delta)
+    assert ei.value.code == COX_ERR_CODE3
+
+
+def test_packed_inputs_match_int8(pkg):
+    """Row-major 2-bit input (host and device) gives the same handle as uint8."""
+    from paper_2010_16114_gb300.cox import CoxProblem
+    w, X, Xf, mu = dense_problem(1, n=1500, p=333)
+    pk = w.packed_rows()
+    beta = torch.tensor(_random_betas(w.p, 2, 3), dtype=torch.float32, device="cuda")
+    with CoxProblem(X, w.y, w.delta) as a:
+        la, ga = a.loss_grad(beta)
+        mua, oa = a.mu_order()
+    with CoxProblem(pk, w.y, w.delta, p=w.p) as b:
+        lb, gb = b.loss_grad(beta)
+    pkd = torch.from_numpy(pk).cuda()
+    with CoxProblem(pkd, w.y, w.delta, p=w.p) as c:
+        lc, gc = c.loss_grad(beta)
+        muc, oc = c.mu_order()
+    assert np.array_equal(la, lb) and np.array_equal(la, lc)
+    assert torch.equal(ga, gb) and torch.equal(ga, gc)
+    assert np.array_equal(mua, muc) and np.array_equal(oa, oc)
+    np.testing.assert_array_equal(mua, Xf.mean(0))
+
+
+def test_repeatable_bitwise(pkg):
+    """Same inputs, same launch: bit-identical loss, gradient and iterates."""
+    from paper_2010_16114_gb300.cox import CoxProblem
+    w, X, Xf, mu = dense_problem(1, n=3000, p=700)
+    with CoxProblem(X, w.y, w.delta) as prob:
+        b1 = prob.zeros(4)
+        b2 = prob.zeros(4)
+        lams = [1e-3, 5e-4, 2e-4, 1e-4]
+        for _ in range(5):
+            prob.prox_step(b1, lams, 0.5)
+        for _ in range(5):
+            prob.prox_step(b2, lams, 0.5)
+        prob.sync()
+        assert torch.equal(b1, b2)
