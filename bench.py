@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark: l1-Cox proximal-gradient iterations/s on one GB300.
+
+Workload (default): the paper-scale genotype problem -- n = 400,000 subjects,
+p = 500,000 SNPs (2-bit packed, MAF ~ U(0.01, 0.5)), 500 causal SNPs, integer
+days 1..5000 with ties, ~5% events, 16 penalties log-spaced from lambda_max to
+0.01 lambda_max solved together.  A step is one proximal-gradient iteration
+for all 16 penalties: X_c B, Breslow risk-set scans, X_c^T V, soft threshold.
+
+The JSON line carries the device-timed throughput (inputs resident in HBM),
+the end-to-end throughput through the C ABI with host buffers, the roofline
+of the dominant kernel (the tensor-core genotype product), the plain FP32
+GEMV path on the same resident data, and the FP64 oracle timed on a bounded
+sample on the host cores.  ``--impl reference`` times only that oracle.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "l1-Cox prox-grad iters/s & HBM GB/s: batched-lambda split-BF16 vs plain FP32"
+UNIT = "iter/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=4)
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--p", type=int, default=None)
+    ap.add_argument("--k", type=int, default=None)
+    ap.add_argument("--tile-m", type=int, default=0)
+    ap.add_argument("--stages", type=int, default=0)
+    ap.add_argument("--gemv-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-gemv", action="store_true")
+    ap.add_argument("--cpu-sample-cols", type=int, default=400)
+    ap.add_argument("--cpu-sample-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def recipe(args):
+    import synth
+    r = synth.CONFIGS[args.config]
+    if args.n or args.p or args.k:
+        r = r.scaled(n=args.n, p=args.p, k=args.k)
+    return r
+
+
+def workload_name(r) -> str:
+    return (f"config {r.config}: n={r.n} subjects x p={r.p} SNPs 2-bit packed, MAF~U({r.maf_lo},{r.maf_hi}), "
+            f"{r.n_causal} causal, days 1..{r.dmax} (ties), {r.event_frac:.0%} events, k={r.k} lambdas "
+            f"log-spaced lambda_max..{r.lam_lo} lambda_max")
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ distributed plumbing
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+def oracle_sample(r, cols: int, steps: int):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: all n
+    subjects, `cols` SNP columns, one penalty; returns seconds per sample step
+    and the scale factor to one full iteration (p / cols columns, k penalties)."""
+    import oracle
+    import synth
+    w = synth.Workload(r)
+    cols = min(cols, r.p)
+    idx = np.arange(cols, dtype=np.int64)
+    Xs = w.cols(idx)
+    mu = Xs.mean(axis=0)
+    beta = np.zeros(cols)
+    lam = 0.0
+    sigma = 1e-3
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        beta, _, _ = oracle.ista(Xs, mu, w.y, w.delta, sigma, lam, 1, beta)
+        times.append(time.perf_counter() - t0)
+    t = float(np.median(times))
+    scale = (r.p / cols) * r.k
+    return t, scale, cols
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    r = recipe(args)
+    import oracle
+    oracle.build()
+    cols = args.cpu_sample_cols
+    # warm-up steps run inside oracle_sample's loop are not separated: run them first, untimed
+    if args.warmup > 0:
+        oracle_sample(r, min(cols, 50), 1)
+    t_step, scale, cols = oracle_sample(r, cols, max(1, args.steps))
+    full = t_step * scale
+    value = 1.0 / full
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": full * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(r)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"one FP64 oracle iteration on all {r.n} subjects x {cols} SNP columns, one "
+                                   f"penalty, {args.steps} timed steps; scaled by p/{cols} columns x {r.k} penalties"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world):
+    import torch
+
+    import synth
+    from paper_2010_16114_gb300 import build
+    from paper_2010_16114_gb300.cox import CoxProblem
+
+    build()
+    synth.build_device()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    r = recipe(args)
+    n, p, k = r.n, r.p, r.k
+    stream = torch.cuda.current_stream()
+
+    t_setup0 = time.perf_counter()
+    w = synth.Workload(r)
+    thr = torch.from_numpy(w.thr.view(np.int32).copy()).cuda()
+    packed = torch.empty((n, (p + 3) // 4), dtype=torch.uint8, device="cuda")
+    w.packed_rows_device(packed.data_ptr(), stream.cuda_stream, thr.data_ptr())
+    torch.cuda.synchronize()
+    prob = CoxProblem(packed, w.y, w.delta, p=p, precision="split_bf16", tile_m=args.tile_m, stages=args.stages)
+    del packed, thr
+    torch.cuda.empty_cache()
+    lmax = prob.lambda_max()
+    L = prob.lipschitz(tol=1e-4, maxiter=100)
+    step = 1.0 / L
+    lams = lmax * r.lambda_fracs()
+    t_setup = time.perf_counter() - t_setup0
+
+    beta = prob.zeros(k)
+    for _ in range(args.warmup):
+        prob.prox_step(beta, lams, step)
+    prob.sync()
+    launches0 = prob.info()["launches"]
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks.start()
+    prob.profile(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        prob.prox_step(beta, lams, step)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    ck = clocks.stop()
+    prob.profile(False)
+    prob.sync()
+    cls_ms, cls_n = prob.profile_read()
+    launches = prob.info()["launches"] - launches0
+    F_last = prob.last_objective(k)
+    ms_max = max_over_ranks(ms, world)
+    ms_step = ms_max / args.steps
+    value = world * args.steps / (ms_max / 1e3)
+
+    # algorithmic bytes (packed X padded to 128 per dimension, as streamed by each product)
+    xb = (-(-n // 128) * 128) * (-(-p // 128) * 128) / 4.0
+    b1 = xb + p * 2 * k * 2 + k * n * 4           # X, beta limbs, eta partials
+    b4 = xb + n * 2 * k * 2 + 8 * k * p           # X, V limbs, beta read+write
+    scan_bytes = k * n * 8 * 12                     # FP64 scan passes (eta, w, R, F, gathers, V)
+    iter_bytes = b1 + b4 + scan_bytes + 12 * k * p  # + beta limbs / l1 pass
+    gemm_ms = cls_ms[0] + cls_ms[1]
+    gemm_n = cls_n[0] + cls_n[1]
+    avg_launch_s = (gemm_ms / max(gemm_n, 1)) / 1e3
+    achieved = ((b1 + b4) / 2.0) / avg_launch_s / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    traffic = None
+    prof_file = os.path.join(ROOT, "profiles", "gemm_traffic.json")
+    if os.path.exists(prof_file):
+        try:
+            with open(prof_file) as fh:
+                tj = json.load(fh)
+            if tj.get("n") and tj.get("p") and tj.get("k") == k:
+                traffic = tj["bytes_per_launch_per_entry"] * n * p
+        except Exception:
+            traffic = None
+
+    # end to end: host buffers through the C ABI, copies inside the timed region
+    beta_h = torch.zeros((k, p), dtype=torch.float32).pin_memory().numpy()
+    beta_h[:] = beta.cpu().numpy()
+    prob.prox_step_host(beta_h, lams, step)  # warm
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        prob.prox_step_host(beta_h, lams, step)
+    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(e2e_s, world)
+    e2e_val = world * args.e2e_steps / e2e_s
+
+    # plain FP32 GEMV path on the same resident data
+    gemv = None
+    if not args.no_gemv and args.gemv_steps > 0:
+        b0 = beta.clone()
+        b_split = b0.clone()
+        prob.prox_step(b_split, lams, step)
+        prob.set_precision("fp32_gemv")
+        b_gemv = b0.clone()
+        prob.prox_step(b_gemv, lams, step)
+        prob.sync()
+        diff = float(torch.linalg.vector_norm(b_gemv - b_split) / max(torch.linalg.vector_norm(b_split), 1e-30))
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        g0.record(stream)
+        for _ in range(args.gemv_steps):
+            prob.prox_step(b_gemv, lams, step)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        gms = g0.elapsed_time(g1) / args.gemv_steps
+        gemv = {"iters_per_s": 1e3 / gms, "ms_per_step": gms, "steps": args.gemv_steps,
+                "lambda_iters_per_s": k * 1e3 / gms, "speedup_of_batched": (1e3 / ms_step) / (1e3 / gms),
+                "hbm_gbs": 2 * k * xb / (gms / 1e3) / 1e9,
+                "rel_l2_vs_batched_one_step": diff}
+        prob.set_precision("split_bf16")
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t_s, scale, cols = oracle_sample(r, args.cpu_sample_cols, args.cpu_sample_steps)
+        cpu = {"value": 1.0 / (t_s * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one FP64 oracle iteration on all {n} subjects x {cols} SNP columns, one penalty "
+                         f"(median of {args.cpu_sample_steps}); scaled by p/{cols} columns x {k} penalties"}
+
+    prob.close()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": workload_name(r), "n": n, "p": p, "k": k,
+                   "l2": "inputs larger than L2: 2 x ~50 GB of packed genotypes streamed per step",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "step_size": step, "lambda_max": lmax},
+        "lambda_iters_per_s": value * k,
+        "hbm_gbs": iter_bytes / (ms_step / 1e3) / 1e9,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_packed_gemm (tensor-core genotype product, both launches per step)",
+                     "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_launch": (b1 + b4) / 2.0,
+                     "avg_launch_ms": avg_launch_s * 1e3},
+        "kernel_ms_per_step": {"x_b_product": cls_ms[0] / args.steps, "xt_v_product_step": cls_ms[1] / args.steps,
+                               "scans": cls_ms[2] / args.steps, "other": cls_ms[3] / args.steps},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(k * p * 4 + k * 8),
+                "d2h_bytes_per_step": int(k * p * 4 + 4), "steps": args.e2e_steps},
+        "gpu_launches": int(launches),
+        "clocks": ck,
+        "fp32_gemv": gemv,
+        "objective_last": [float(x) for x in F_last[:4]],
+        "setup_s": t_setup,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world = dist_init(args)
+    if args.impl == "reference":
+        rc = run_reference(args, rank, world)
+    else:
+        rc = run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -115,11 +115,12 @@ void cox_destroy(cox_h h);
 /*
  * L = 2 ||X_c||_2^2 / n, the Lipschitz constant the step 1/L is built from
  * (Section 5.3 step-size remark, rescaled to the 1/n loss), with ||X_c||_2
- * from the power method of Section 4.4: tolerance 1e-6 on the relative
- * change of the estimate, at most 1000 iterations.  start_host: p doubles,
- * the start vector (NULL: all ones).  Synchronous.
+ * from the power method of Section 4.4: stop when the estimate changes by at
+ * most tol relative (tol <= 0: the paper's 1e-6) or after maxiter iterations
+ * (maxiter <= 0: the paper's 1000).  start_host: p doubles, the start vector
+ * (NULL: all ones).  Synchronous.
  */
-int cox_lipschitz(cox_h h, const double *start_host, double *L_out);
+int cox_lipschitz(cox_h h, const double *start_host, double tol, int maxiter, double *L_out);
 
 /* lambda_max = ||g(0)||_inf: the smallest lambda for which beta = 0 solves
  * the problem (g(0) uses u(0), the Nelson-Aalen hazard).  Synchronous. */
@@ -179,14 +180,33 @@ int cox_path_fit(cox_h h, const double *lambdas, int k, int max_iter, double tol
 int cox_get_state(cox_h h, void *buf, size_t *size);
 int cox_set_state(cox_h h, const void *buf, size_t size);
 
-/* Handle facts: n, p, padded sizes, precision, tile choice, device bytes. */
+/* Handle facts: n, p, padded sizes, precision, tile choice, device bytes,
+ * and the number of kernels the library has launched on this handle. */
 typedef struct cox_info {
     int64_t n, p, n_pad, p_pad;
     int precision, center, tile_m, stages, sm_count;
     int64_t device_bytes;
     int64_t n_tie_groups;
+    int64_t launches;
 } cox_info;
 int cox_get_info(cox_h h, cox_info *info);
+
+/* Switch a genotype handle between COX_SPLIT_BF16 and COX_FP32_GEMV; both
+ * read the same resident tiles.  Drops the per-k workspace.  Errors:
+ * COX_ERR_UNSUPPORTED for COX_FP64 handles or targets. */
+int cox_set_precision(cox_h h, int precision);
+
+/*
+ * Per-kernel timing with CUDA events recorded on the launching stream around
+ * each kernel class of an iteration: 0 = X_c B product, 1 = X_c^T V product
+ * with the fused step, 2 = risk-set scans (all their launches), 3 = other
+ * (coefficient limbs, ||beta||_1).  cox_profile(h, 1) clears and starts
+ * recording; cox_profile(h, 0) stops.  cox_profile_read synchronises, then
+ * fills total_ms[4] and launches[4] for the recorded iterations.  Recording
+ * is off inside cox_path_fit graphs.
+ */
+int cox_profile(cox_h h, int enable);
+int cox_profile_read(cox_h h, double *total_ms, int64_t *launches);
 
 /* Column means mu (p doubles, host) and the sorted order (n int64, host;
  * entry r = subject at rank r).  Either may be NULL. */

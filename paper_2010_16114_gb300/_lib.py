@@ -35,7 +35,7 @@ EXPORTS = [
     "cox_default_options", "cox_setup", "cox_destroy", "cox_lipschitz", "cox_lambda_max",
     "cox_loss_grad", "cox_prox_step", "cox_prox_step_host", "cox_sync", "cox_last_objective",
     "cox_path_fit", "cox_get_state", "cox_set_state", "cox_get_info", "cox_get_mu_order",
-    "cox_strerror",
+    "cox_strerror", "cox_set_precision", "cox_profile", "cox_profile_read",
 ]
 
 
@@ -49,7 +49,8 @@ class cox_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("p", ctypes.c_int64), ("n_pad", ctypes.c_int64),
                 ("p_pad", ctypes.c_int64), ("precision", ctypes.c_int), ("center", ctypes.c_int),
                 ("tile_m", ctypes.c_int), ("stages", ctypes.c_int), ("sm_count", ctypes.c_int),
-                ("device_bytes", ctypes.c_int64), ("n_tie_groups", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("n_tie_groups", ctypes.c_int64),
+                ("launches", ctypes.c_int64)]
 
 
 class CoxError(RuntimeError):
@@ -78,7 +79,7 @@ def load(path: str | None = None):
     lib.cox_destroy.restype = None
     lib.cox_destroy.argtypes = [P]
     lib.cox_lipschitz.restype = I
-    lib.cox_lipschitz.argtypes = [P, P, ctypes.POINTER(D)]
+    lib.cox_lipschitz.argtypes = [P, P, D, I, ctypes.POINTER(D)]
     lib.cox_lambda_max.restype = I
     lib.cox_lambda_max.argtypes = [P, ctypes.POINTER(D)]
     lib.cox_loss_grad.restype = I
@@ -101,6 +102,12 @@ def load(path: str | None = None):
     lib.cox_get_info.argtypes = [P, ctypes.POINTER(cox_info)]
     lib.cox_get_mu_order.restype = I
     lib.cox_get_mu_order.argtypes = [P, P, P]
+    lib.cox_set_precision.restype = I
+    lib.cox_set_precision.argtypes = [P, I]
+    lib.cox_profile.restype = I
+    lib.cox_profile.argtypes = [P, I]
+    lib.cox_profile_read.restype = I
+    lib.cox_profile_read.argtypes = [P, P, P]
     lib.cox_strerror.restype = ctypes.c_char_p
     lib.cox_strerror.argtypes = [I]
     _lib = lib
@@ -139,9 +146,9 @@ def cox_destroy(h):
     load().cox_destroy(h)
 
 
-def cox_lipschitz(h, start_ptr=None):
+def cox_lipschitz(h, start_ptr=None, tol=0.0, maxiter=0):
     L = ctypes.c_double()
-    rc = load().cox_lipschitz(h, start_ptr, ctypes.byref(L))
+    rc = load().cox_lipschitz(h, start_ptr, tol, maxiter, ctypes.byref(L))
     return rc, L.value
 
 
@@ -192,6 +199,18 @@ def cox_get_info(h):
 
 def cox_get_mu_order(h, mu_ptr, order_ptr):
     return load().cox_get_mu_order(h, mu_ptr, order_ptr)
+
+
+def cox_set_precision(h, precision: int) -> int:
+    return load().cox_set_precision(h, precision)
+
+
+def cox_profile(h, enable: int) -> int:
+    return load().cox_profile(h, enable)
+
+
+def cox_profile_read(h, ms_ptr, launches_ptr) -> int:
+    return load().cox_profile_read(h, ms_ptr, launches_ptr)
 
 
 def cox_strerror(code: int) -> str:

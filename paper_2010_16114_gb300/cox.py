@@ -114,9 +114,25 @@ class CoxProblem:
         L.check(L.cox_get_mu_order(self.h, _vp(mu), _vp(order)), "cox_get_mu_order")
         return mu, order
 
-    def lipschitz(self, start: np.ndarray | None = None) -> float:
+    def set_precision(self, precision: str):
+        """Switch between "split_bf16" and "fp32_gemv" on the same resident data."""
+        L.check(L.cox_set_precision(self.h, PRECISIONS[precision]), "cox_set_precision")
+        self.precision = precision
+
+    def profile(self, enable: bool):
+        L.check(L.cox_profile(self.h, int(enable)), "cox_profile")
+
+    def profile_read(self):
+        """(total ms, launches) per kernel class: X B, X^T V (+step), scans, other."""
+        ms = np.zeros(4)
+        n = np.zeros(4, np.int64)
+        L.check(L.cox_profile_read(self.h, _vp(ms), _vp(n)), "cox_profile_read")
+        return ms, n
+
+    def lipschitz(self, start: np.ndarray | None = None, tol: float = 0.0, maxiter: int = 0) -> float:
+        """L = 2 ||X_c||_2^2 / n by the power method (defaults: tol 1e-6, 1000 iterations)."""
         s = None if start is None else np.ascontiguousarray(start, dtype=np.float64)
-        rc, v = L.cox_lipschitz(self.h, _vp(s))
+        rc, v = L.cox_lipschitz(self.h, _vp(s), float(tol), int(maxiter))
         L.check(rc, "cox_lipschitz")
         return v
 

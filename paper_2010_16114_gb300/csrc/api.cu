@@ -97,6 +97,38 @@ struct DeviceGuard {
 bool is_split(const cox_handle *h) { return h->opt.precision == COX_SPLIT_BF16; }
 bool is_fp64(const cox_handle *h) { return h->opt.precision == COX_FP64; }
 
+cudaEvent_t get_event(cox_handle *h)
+{
+    if (h->ev_used == h->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        h->ev_pool.push_back(e);
+    }
+    return h->ev_pool[h->ev_used++];
+}
+
+// Counts the kernels of one launch site and, when profiling, brackets them
+// with events on the launching stream.
+struct Site {
+    cox_handle *h;
+    int cls, nk;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    Site(cox_handle *h_, int cls_, int nk_, cudaStream_t st_) : h(h_), cls(cls_), nk(nk_), st(st_)
+    {
+        h->launches += nk;
+        if (h->prof && (a = get_event(h))) cudaEventRecord(a, st);
+    }
+    ~Site()
+    {
+        if (!h->prof || !a) return;
+        cudaEvent_t b = get_event(h);
+        if (!b) return;
+        cudaEventRecord(b, st);
+        h->prof_recs.push_back({cls * 1000 + nk, a, b});
+    }
+};
+
 } // namespace
 
 // One iteration for k columns.  epi: EPI_PROX (update beta) or EPI_GRAD.
@@ -105,12 +137,18 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
     Workspace &ws = h->ws;
     if (is_split(h)) {
         float *b32 = static_cast<float *>(beta);
-        COX_TRY(prep_limbs_beta(h, b32, k, ws.Bb, ws.g1.NP, st));
-        COX_TRY(l1_norms32(h, b32, k, st));
+        {
+            Site s_(h, 3, 2, st);
+            COX_TRY(prep_limbs_beta(h, b32, k, ws.Bb, ws.g1.NP, st));
+            COX_TRY(l1_norms32(h, b32, k, st));
+        }
         EpiArgs e1;
         e1.epi = EPI_PARTIAL;
         e1.part = ws.part1;
-        COX_TRY(launch_gemm(h, ws.g1, e1, k, st));
+        {
+            Site s_(h, 0, 1, st);
+            COX_TRY(launch_gemm(h, ws.g1, e1, k, st));
+        }
         ScanArgs sa;
         sa.k = k;
         sa.eta_src = ETA_PARTIAL_F32;
@@ -126,7 +164,10 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
         sa.exp64 = false;
         sa.lam = ws.lam;
         sa.need_loss = true;
-        COX_TRY(run_scans(h, sa, st));
+        {
+            Site s_(h, 2, 7, st);
+            COX_TRY(run_scans(h, sa, st));
+        }
         EpiArgs e4;
         e4.epi = epi;
         e4.part = ws.part4;
@@ -140,13 +181,22 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
         e4.active = ws.active;
         e4.rows_valid = h->p;
         e4.inv_n = 1.0 / static_cast<double>(h->n);
-        COX_TRY(launch_gemm(h, ws.g4, e4, k, st));
+        {
+            Site s_(h, 1, 1, st);
+            COX_TRY(launch_gemm(h, ws.g4, e4, k, st));
+        }
         return COX_OK;
     }
     if (is_fp64(h)) {
         double *b64 = static_cast<double *>(beta);
-        COX_TRY(l1_norms64(h, b64, k, st));
-        COX_TRY(eta64(h, b64, k, ws.eta, st));
+        {
+            Site s_(h, 3, 1, st);
+            COX_TRY(l1_norms64(h, b64, k, st));
+        }
+        {
+            Site s_(h, 0, 1, st);
+            COX_TRY(eta64(h, b64, k, ws.eta, st));
+        }
         ScanArgs sa;
         sa.k = k;
         sa.eta_src = ETA_DENSE_F64;
@@ -162,7 +212,11 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
         sa.exp64 = true;
         sa.lam = ws.lam;
         sa.need_loss = true;
-        COX_TRY(run_scans(h, sa, st));
+        {
+            Site s_(h, 2, 7, st);
+            COX_TRY(run_scans(h, sa, st));
+        }
+        Site s4_(h, 1, 1, st);
         COX_TRY(xtv64(h, ws.V64, k, epi == EPI_PROX ? b64 : nullptr, epi == EPI_GRAD ? static_cast<double *>(grad) : nullptr,
                       ws.lam, step, st));
         return COX_OK;
@@ -171,8 +225,14 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
     float *b32 = static_cast<float *>(beta);
     for (int c = 0; c < k; ++c) {
         float *bc = b32 + static_cast<int64_t>(c) * h->p;
-        COX_TRY(l1_norms32(h, bc, 1, st));
-        COX_TRY(gemv_tiles(h, h->d_A1, h->n_pad, h->p_pad / TILE, bc, h->p, ws.eta32, st));
+        {
+            Site s_(h, 3, 1, st);
+            COX_TRY(l1_norms32(h, bc, 1, st));
+        }
+        {
+            Site s_(h, 0, 1, st);
+            COX_TRY(gemv_tiles(h, h->d_A1, h->n_pad, h->p_pad / TILE, bc, h->p, ws.eta32, st));
+        }
         ScanArgs sa;
         sa.k = 1;
         sa.eta_src = ETA_DENSE_F32;
@@ -188,12 +248,18 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
         sa.exp64 = false;
         sa.lam = ws.lam + c;
         sa.need_loss = true;
-        COX_TRY(run_scans(h, sa, st));
+        {
+            Site s_(h, 2, 7, st);
+            COX_TRY(run_scans(h, sa, st));
+        }
         COX_CUDA(cudaMemcpyAsync(ws.Fring + c, ws.F, sizeof(double), cudaMemcpyDeviceToDevice, st));
         COX_CUDA(cudaMemcpyAsync(ws.Fring + k + c, ws.f, sizeof(double), cudaMemcpyDeviceToDevice, st));
-        COX_TRY(gemv_tiles(h, h->d_A4, h->p_pad, h->n_pad / TILE, ws.V32, h->n, ws.G32, st));
-        float *gc = epi == EPI_GRAD ? static_cast<float *>(grad) : nullptr;
-        COX_TRY(prox_or_grad32(h, ws.G32, c, epi == EPI_PROX ? b32 : nullptr, gc, ws.lam, step, st));
+        {
+            Site s_(h, 1, 2, st);
+            COX_TRY(gemv_tiles(h, h->d_A4, h->p_pad, h->n_pad / TILE, ws.V32, h->n, ws.G32, st));
+            float *gc = epi == EPI_GRAD ? static_cast<float *>(grad) : nullptr;
+            COX_TRY(prox_or_grad32(h, ws.G32, c, epi == EPI_PROX ? b32 : nullptr, gc, ws.lam, step, st));
+        }
     }
     // gather per-column objectives into F / f
     COX_CUDA(cudaMemcpyAsync(ws.F, ws.Fring, k * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -336,6 +402,7 @@ void cox_destroy(cox_h h)
     DeviceGuard g(h->dev);
     cudaDeviceSynchronize();
     free_workspace(h);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     void *ptrs[] = {h->d_head, h->d_tail, h->d_delta, h->d_mu, h->d_A1, h->d_A4, h->d_Xr, h->d_Xc, h->d_err};
     for (void *p : ptrs) dfree(p);
     delete h;
@@ -454,6 +521,52 @@ int cox_get_info(cox_h h, cox_info *info)
     info->sm_count = h->sm_count;
     info->device_bytes = h->device_bytes;
     info->n_tie_groups = h->n_groups_tie;
+    info->launches = h->launches;
+    return COX_OK;
+}
+
+int cox_set_precision(cox_h h, int precision)
+{
+    if (!h) return COX_ERR_ARG;
+    if (h->opt.precision == COX_FP64 || (precision != COX_SPLIT_BF16 && precision != COX_FP32_GEMV))
+        return COX_ERR_UNSUPPORTED;
+    if (precision == h->opt.precision) return COX_OK;
+    DeviceGuard g(h->dev);
+    cudaDeviceSynchronize();
+    free_workspace(h);
+    h->opt.precision = precision;
+    return COX_OK;
+}
+
+int cox_profile(cox_h h, int enable)
+{
+    if (!h) return COX_ERR_ARG;
+    DeviceGuard g(h->dev);
+    if (enable) {
+        cudaDeviceSynchronize();
+        h->prof_recs.clear();
+        h->ev_used = 0;
+    }
+    h->prof = enable != 0;
+    return COX_OK;
+}
+
+int cox_profile_read(cox_h h, double *total_ms, int64_t *launches)
+{
+    if (!h || !total_ms || !launches) return COX_ERR_ARG;
+    DeviceGuard g(h->dev);
+    for (int c = 0; c < 4; ++c) {
+        total_ms[c] = 0.0;
+        launches[c] = 0;
+    }
+    for (const auto &r : h->prof_recs) {
+        COX_CUDA(cudaEventSynchronize(r.b));
+        float ms = 0.f;
+        COX_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+        const int cls = r.cls / 1000;
+        total_ms[cls] += ms;
+        launches[cls] += r.cls % 1000;
+    }
     return COX_OK;
 }
 

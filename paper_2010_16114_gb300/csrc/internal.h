@@ -97,6 +97,16 @@ struct cox_handle {
     std::vector<double> st_F;
     std::vector<int> st_active;
     int64_t st_step = 0;
+    // launch accounting and optional per-kernel-class event timing
+    int64_t launches = 0;
+    bool prof = false;
+    struct ProfRec {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
 };
 
 namespace coxgb {

@@ -112,7 +112,7 @@ struct DeviceGuard {
 };
 
 template <typename TV>
-int power_method(cox_handle *h, const double *start, double *L_out)
+int power_method(cox_handle *h, const double *start, double tol, int maxiter, double *L_out)
 {
     const int64_t n = h->n, p = h->p;
     const bool f64 = h->opt.precision == COX_FP64;
@@ -133,7 +133,7 @@ int power_method(cox_handle *h, const double *start, double *L_out)
     double s = 0.0, s_prev = 0.0;
     do {
         if (cudaMemcpy(v, v0.data(), p * sizeof(TV), cudaMemcpyHostToDevice) != cudaSuccess) { rc = COX_ERR_CUDA; break; }
-        for (int it = 1; it <= 1000; ++it) {
+        for (int it = 1; it <= maxiter; ++it) {
             k_dot_mu<TV><<<1, RB, 0, st>>>(h->d_mu, v, p, sc);
             if (f64) {
                 rc = eta64(h, reinterpret_cast<const double *>(v), 1, reinterpret_cast<double *>(a), st);
@@ -158,7 +158,7 @@ int power_method(cox_handle *h, const double *start, double *L_out)
             if (!(nb2 > 0.0) || !std::isfinite(nb2)) { s = 0.0; break; }
             s = std::sqrt(nb2);  // ||X_c^T X_c v|| -> largest eigenvalue of X_c^T X_c
             k_scale<TV><<<static_cast<unsigned>((p + 255) / 256), 256, 0, st>>>(b, v, p, 1.0 / s);
-            if (it > 1 && std::fabs(s - s_prev) <= 1e-6 * s) break;
+            if (it > 1 && std::fabs(s - s_prev) <= tol * s) break;
             s_prev = s;
         }
         if (cudaDeviceSynchronize() != cudaSuccess && rc == COX_OK) rc = COX_ERR_CUDA;
@@ -178,12 +178,14 @@ using namespace coxgb;
 
 extern "C" {
 
-int cox_lipschitz(cox_h h, const double *start_host, double *L_out)
+int cox_lipschitz(cox_h h, const double *start_host, double tol, int maxiter, double *L_out)
 {
     if (!h || !L_out) return COX_ERR_ARG;
     DeviceGuard g(h->dev);
-    if (h->opt.precision == COX_FP64) return power_method<double>(h, start_host, L_out);
-    return power_method<float>(h, start_host, L_out);
+    if (!(tol > 0.0)) tol = 1e-6;
+    if (maxiter <= 0) maxiter = 1000;
+    if (h->opt.precision == COX_FP64) return power_method<double>(h, start_host, tol, maxiter, L_out);
+    return power_method<float>(h, start_host, tol, maxiter, L_out);
 }
 
 int cox_path_fit(cox_h h, const double *lambdas, int k, int max_iter, double tol, double step, int warm,

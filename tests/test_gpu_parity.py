@@ -162,7 +162,13 @@ def test_degenerate_cases(pkg, kind):
                 assert np.all(np.abs(G[c]) <= 1e-12)
                 assert loss[c] == 0.0
             else:
-                assert abs(loss[c] - f_o) <= 1e-7 * max(abs(f_o), 1e-300)
+                # f = (1/n) sum_i delta_i (log W_i - eta_i): a difference of O(|eta|)
+                # terms, so its error follows the split-bf16 error of eta (~2^-17 of
+                # sum_j |x_ij beta_j|), not |f| -- with one event f is nearly zero.
+                eta_o = oracle.eta(Xf, mu, beta[c].cpu().numpy().astype(np.float64))
+                eta_scale = np.abs(X.astype(np.float64)) @ np.abs(beta[c].cpu().numpy().astype(np.float64))
+                atol = 2.0 ** -16 * d.mean() * max(eta_scale.max(), np.abs(eta_o).max())
+                assert abs(loss[c] - f_o) <= 1e-7 * abs(f_o) + atol
                 assert rel_l2(G[c], g_o) <= 1e-5
 
 
