@@ -18,15 +18,25 @@
 // B holds each coefficient column as two bf16 limbs, hi = RN(b), lo = RN(b-hi)
 // (columns 2c and 2c+1), so D[2c] + D[2c+1] carries ~16 significant bits of b.
 //
+// Pipeline per CTA (one per SM): a TMA warp fills a ring of shared-memory
+// stages (B chunk + T A blocks); eight decoder warps turn a stage into bf16 in
+// a ring of TMEM stage slots, issuing all of a stage's tcgen05.st before one
+// wait; one thread issues T x 8 MMAs per stage and commits.  The TMEM slot
+// ring lets decoding run several stages ahead of the MMAs, which hides the
+// MMA-to-commit round trip.
+//
 // FP32 accumulation in TMEM rounds with a bias, so each CTA accumulates at most
 // F K-chunks in TMEM (double-buffered), then the decoder warps fold the window
-// into FP32 registers (round-to-nearest).
+// into FP32 registers (round-to-nearest); the fold of a window is deferred by a
+// few stages so it never stalls decoding.
 //
 // Work split: units = (M group, K chunk) pairs; CTA c takes the contiguous
 // range [c L, (c+1) L).  A group cut between CTAs gets one partial per CTA
 // (slot = CTA - first CTA of the group); the last CTA to finish a group sums
 // the slots in slot order (deterministic) and applies the epilogue.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "internal.h"
 #include "ptx.cuh"
@@ -35,7 +45,7 @@ namespace coxgb {
 namespace {
 
 struct KParams {
-    int KC, F, k, stages, ring;
+    int KC, F, k, stages, ring, defer;
     int64_t units, L;
     int64_t rows_pad, slot_stride;
     float *part;
@@ -83,6 +93,12 @@ __device__ __forceinline__ bool window_first(int64_t i, int kc, int64_t wstart, 
     return i == 0 || kc == 0 || i - wstart == F;
 }
 
+// all lanes wait; the warp agrees on the outcome
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, long long lim, volatile int *abort)
+{
+    return __all_sync(0xffffffffu, mbar_wait(bar, parity, lim, abort));
+}
+
 template <int T, int NP>
 __global__ void __launch_bounds__(320, 1)
     k_packed_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -93,6 +109,7 @@ __global__ void __launch_bounds__(320, 1)
     constexpr int X_BYTES = T * BLOCK_BYTES;
     constexpr int STAGE = B_BYTES + X_BYTES;
     constexpr int ACC_COLS = 2 * T * NP;
+    constexpr int SLOT_COLS = T * 64;
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -181,11 +198,13 @@ __global__ void __launch_bounds__(320, 1)
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_bf16_f32(128, NP);
-            int64_t j = 0, wi = -1, wstart = 0;
+            int64_t wi = -1, wstart = 0;
             bool ok = true;
-            for (int64_t i = 0; i < nu && ok; ++i) {
+            for (int64_t i = 0; i < nu; ++i) {
                 const int s = static_cast<int>(i % S);
                 const int64_t f = i / S;
+                const int r = static_cast<int>(i % R);
+                const int64_t m = i / R;
                 const int64_t u = u0 + i;
                 const int kc = static_cast<int>(u % KC);
                 const bool first = window_first(i, kc, wstart, F);
@@ -199,32 +218,24 @@ __global__ void __launch_bounds__(320, 1)
                 }
                 const bool last = (i == nu - 1) || (kc == KC - 1) || (i + 1 - wstart == F);
                 const int b = static_cast<int>(wi & 1);
-                if (!mbar_wait(full0 + 8 * s, static_cast<uint32_t>(f & 1), lim, abort_sm)) {
+                if (!mbar_wait(full0 + 8 * s, static_cast<uint32_t>(f & 1), lim, abort_sm) ||
+                    !mbar_wait(afull0 + 8 * r, static_cast<uint32_t>(m & 1), lim, abort_sm)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t st_b = smem_addr(smem + s * STAGE);
-#pragma unroll 1
+#pragma unroll
                 for (int t = 0; t < T; ++t) {
-                    const int r = static_cast<int>(j % R);
-                    const int64_t m = j / R;
-                    if (!mbar_wait(afull0 + 8 * r, static_cast<uint32_t>(m & 1), lim, abort_sm)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
                     const uint32_t d = tbase + static_cast<uint32_t>((b * T + t) * NP);
-                    const uint32_t a = tbase + static_cast<uint32_t>(ACC_COLS + 64 * r);
+                    const uint32_t a = tbase + static_cast<uint32_t>(ACC_COLS + r * SLOT_COLS + t * 64);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const uint64_t bd = smem_desc_sw128(st_b + (q >> 2) * NP * 128 + (q & 3) * 32);
                         mma_ts(d, a + 8 * q, bd, idesc, (first && q == 0) ? 0u : 1u);
                     }
-                    mma_commit(aempty0 + 8 * r);
-                    ++j;
                 }
-                if (!ok) break;
+                mma_commit(aempty0 + 8 * r);
                 mma_commit(empty0 + 8 * s);
                 if (last) mma_commit(accf0 + 8 * b);
             }
@@ -237,6 +248,7 @@ __global__ void __launch_bounds__(320, 1)
         const int h = (warp - 2) >> 2;    // K half of each chunk (64 codes)
         const int q = warp & 3;           // TMEM lane quarter
         const int rit = 32 * q + lane;    // row inside a 128-row tile
+        const int phys = h ^ ((rit >> 2) & 1);
         const uint32_t lane_base = tbase + (static_cast<uint32_t>(32 * q) << 16);
         float acc[T][KH];
 #pragma unroll
@@ -244,16 +256,16 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll
             for (int e = 0; e < KH; ++e) acc[t][e] = 0.f;
 
-        int64_t j = 0, wi = -1, wstart = 0;
+        int64_t wi = -1, wstart = 0;
         bool pend = false, pend_segend = false;
         int pend_b = 0, pend_g = 0;
-        int64_t pend_m = 0;
+        int64_t pend_m = 0, pend_due = 0;
         uint32_t epi_phase = 0;
         bool ok = true;
 
         auto drain = [&](int b, int64_t m, bool segend, int g) {
             if (!ok) return;
-            if (!__all_sync(0xffffffffu, mbar_wait(accf0 + 8 * b, static_cast<uint32_t>(m & 1), lim, abort_sm))) {
+            if (!warp_wait(accf0 + 8 * b, static_cast<uint32_t>(m & 1), lim, abort_sm)) {
                 ok = false;
                 return;
             }
@@ -295,7 +307,7 @@ __global__ void __launch_bounds__(320, 1)
             __threadfence();
             __syncwarp();
             if (lane == 0) mbar_arrive(epib);
-            if (!__all_sync(0xffffffffu, mbar_wait(epib, epi_phase & 1, lim, abort_sm))) {
+            if (!warp_wait(epib, epi_phase & 1, lim, abort_sm)) {
                 ok = false;
                 return;
             }
@@ -310,7 +322,7 @@ __global__ void __launch_bounds__(320, 1)
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(epib);
-            if (!__all_sync(0xffffffffu, mbar_wait(epib, epi_phase & 1, lim, abort_sm))) {
+            if (!warp_wait(epib, epi_phase & 1, lim, abort_sm)) {
                 ok = false;
                 return;
             }
@@ -341,59 +353,60 @@ __global__ void __launch_bounds__(320, 1)
         for (int64_t i = 0; i < nu && ok; ++i) {
             const int s = static_cast<int>(i % S);
             const int64_t f = i / S;
+            const int r = static_cast<int>(i % R);
+            const int64_t m = i / R;
             const int64_t u = u0 + i;
             const int g = static_cast<int>(u / KC), kc = static_cast<int>(u % KC);
             if (window_first(i, kc, wstart, F)) {
                 ++wi;
                 wstart = i;
-                if (pend) {
-                    drain(pend_b, pend_m, pend_segend, pend_g);
-                    pend = false;
-                    if (!ok) break;
-                }
+            }
+            // fold the previous window once `defer` stages have passed (by then the
+            // MMAs of that window have completed, so the wait is short)
+            if (pend && i >= pend_due) {
+                drain(pend_b, pend_m, pend_segend, pend_g);
+                pend = false;
+                if (!ok) break;
             }
             const bool last = (i == nu - 1) || (kc == KC - 1) || (i + 1 - wstart == F);
-            bool w_ok = mbar_wait(full0 + 8 * s, static_cast<uint32_t>(f & 1), lim, abort_sm);
-            if (!__all_sync(0xffffffffu, w_ok)) {
+            if (!warp_wait(full0 + 8 * s, static_cast<uint32_t>(f & 1), lim, abort_sm) ||
+                (m >= 1 && !warp_wait(aempty0 + 8 * r, static_cast<uint32_t>((m - 1) & 1), lim, abort_sm))) {
                 ok = false;
                 break;
             }
-            const uint8_t *xs = smem + s * STAGE + B_BYTES;
-#pragma unroll 1
+            tc_fence_after();
+            const uint8_t *xs = smem + s * STAGE + B_BYTES + rit * 32 + phys * 16;
+            const uint32_t acol = lane_base + static_cast<uint32_t>(ACC_COLS + r * SLOT_COLS + 32 * h);
+#pragma unroll
             for (int t = 0; t < T; ++t) {
-                const int r = static_cast<int>(j % R);
-                const int64_t m = j / R;
-                if (m >= 1) {
-                    w_ok = mbar_wait(aempty0 + 8 * r, static_cast<uint32_t>((m - 1) & 1), lim, abort_sm);
-                    if (!__all_sync(0xffffffffu, w_ok)) {
-                        ok = false;
-                        break;
-                    }
-                }
-                tc_fence_after();
-                const int phys = h ^ ((rit >> 2) & 1);
-                const uint4 v = *reinterpret_cast<const uint4 *>(xs + t * BLOCK_BYTES + rit * 32 + phys * 16);
+                const uint4 v = *reinterpret_cast<const uint4 *>(xs + t * BLOCK_BYTES);
                 uint32_t o[32];
                 decode16(v.x, o);
                 decode16(v.y, o + 8);
                 decode16(v.z, o + 16);
                 decode16(v.w, o + 24);
-                tmem_st_32x32b_x32(lane_base + static_cast<uint32_t>(ACC_COLS + 64 * r + 32 * h), o);
-                tmem_wait_st();
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(afull0 + 8 * r);
-                ++j;
+                tmem_st_32x32b_x32(acol + t * 64, o);
             }
-            if (!ok) break;
+            tmem_wait_st();
+            tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(empty0 + 8 * s);
+            if (lane == 0) {
+                mbar_arrive(afull0 + 8 * r);
+                mbar_arrive(empty0 + 8 * s);
+            }
             if (last) {
+                // a window shorter than `defer`: fold the older one now, so at most one
+                // fold is ever owed and it always precedes the window that reuses its buffer
+                if (pend) {
+                    drain(pend_b, pend_m, pend_segend, pend_g);
+                    if (!ok) break;
+                }
                 pend = true;
                 pend_b = static_cast<int>(wi & 1);
                 pend_m = wi >> 1;
                 pend_segend = (i == nu - 1) || (kc == KC - 1);
                 pend_g = g;
+                pend_due = i + 1 + P.defer;
             }
         }
         if (ok && pend) drain(pend_b, pend_m, pend_segend, pend_g);
@@ -450,10 +463,8 @@ KernelFn pick_kernel(int T, int NP)
     case 1016: return k_packed_gemm<1, 16>;
     case 2016: return k_packed_gemm<2, 16>;
     case 4016: return k_packed_gemm<4, 16>;
-    case 8016: return k_packed_gemm<8, 16>;
     case 1032: return k_packed_gemm<1, 32>;
     case 2032: return k_packed_gemm<2, 32>;
-    case 4032: return k_packed_gemm<4, 32>;
     case 1064: return k_packed_gemm<1, 64>;
     case 2064: return k_packed_gemm<2, 64>;
     case 1128: return k_packed_gemm<1, 128>;
@@ -464,33 +475,36 @@ KernelFn pick_kernel(int T, int NP)
 } // namespace
 
 // Plan one product: A (rows_pad x K_pad, tiled 2-bit) times B limbs (NP x K_pad).
+// TMEM budget (512 columns): 2 T NP accumulator columns + ring x T x 64 A columns.
 int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, int64_t K_pad,
               const uint16_t *B, int k, int T_req, int stages_req)
 {
     if (k < 1 || k > MAX_K_TC) return COX_ERR_ARG;
     const int NP = (2 * k + 15) / 16 * 16;
-    int np_cls = NP <= 16 ? 16 : NP <= 32 ? 32 : NP <= 64 ? 64 : 128;
+    const int np_cls = NP <= 16 ? 16 : NP <= 32 ? 32 : NP <= 64 ? 64 : 128;
     const int64_t m_tiles = rows_pad / TILE;
-    int T = T_req > 0 ? T_req : 4;
-    if (T != 1 && T != 2 && T != 4 && T != 8) return COX_ERR_ARG;
-    if (np_cls == 32 && T > 4) T = 4;
-    if (np_cls == 64 && T > 2) T = 2;
+    int T = T_req > 0 ? T_req : 2;
+    if (T > 4) T = 4;
+    if (T != 1 && T != 2 && T != 4) return COX_ERR_ARG;
+    if (np_cls >= 32 && T > 2) T = 2;
     if (np_cls == 128) T = 1;
+    while (T > 1 && (512 - 2 * T * np_cls) / (T * 64) < 2) T >>= 1;
     if (m_tiles % T != 0) return COX_ERR_ARG;
+    int ring = (512 - 2 * T * np_cls) / (T * 64);
+    if (ring > 8) ring = 8;
+    if (ring < 2) return COX_ERR_ARG;
     g.T = T;
     g.NP = np_cls;
-    const int acc_cols = 2 * T * np_cls;
-    g.ring = (512 - acc_cols) / 64;
-    if (g.ring > 8) g.ring = 8;
-    if (g.ring < 2) return COX_ERR_ARG;
+    g.ring = ring;
     const int stage = np_cls * 256 + T * BLOCK_BYTES;
     int S = stages_req > 0 ? stages_req : (225 * 1024 - 2048) / stage;
-    if (S > 8) S = 8;
+    if (S > 12) S = 12;
     if (S < 2) S = 2;
     g.stages = S;
     g.smem = static_cast<size_t>(S) * stage + 1024 + 1024;
     if (g.smem < 120 * 1024) g.smem = 120 * 1024;  // one CTA per SM: it owns all 512 TMEM columns
     g.F = 32;
+    g.defer = std::min(ring, g.F - 1);
     g.KC = static_cast<int>(K_pad / TILE);
     g.n_groups = static_cast<int>(m_tiles / T);
     g.units = static_cast<int64_t>(g.n_groups) * g.KC;
@@ -514,9 +528,10 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
     EncodeTiled enc = get_encoder();
     if (!enc) return COX_ERR_CUDA;
     {
-        cuuint64_t dims[4] = {8, 128, static_cast<cuuint64_t>(g.KC), static_cast<cuuint64_t>(m_tiles)};
-        cuuint64_t strides[3] = {32, BLOCK_BYTES, static_cast<cuuint64_t>(g.KC) * BLOCK_BYTES};
-        cuuint32_t box[4] = {8, 128, 1, static_cast<cuuint32_t>(T)};
+        // a 4 KB block viewed as 4 rows of 1 KB; T consecutive row tiles per box
+        cuuint64_t dims[4] = {256, 4, static_cast<cuuint64_t>(g.KC), static_cast<cuuint64_t>(m_tiles)};
+        cuuint64_t strides[3] = {1024, BLOCK_BYTES, static_cast<cuuint64_t>(g.KC) * BLOCK_BYTES};
+        cuuint32_t box[4] = {256, 4, 1, static_cast<cuuint32_t>(T)};
         cuuint32_t es[4] = {1, 1, 1, 1};
         CUresult r = enc(&g.tmA, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, const_cast<uint32_t *>(A), dims, strides,
                          box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -544,6 +559,7 @@ int launch_gemm(cox_handle *h, const GemmPlan &g, const EpiArgs &e, int k, cudaS
     kp.k = k;
     kp.stages = g.stages;
     kp.ring = g.ring;
+    kp.defer = g.defer;
     kp.units = g.units;
     kp.L = g.L;
     kp.rows_pad = g.rows_pad;

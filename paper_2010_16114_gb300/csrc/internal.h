@@ -25,7 +25,8 @@ struct GemmPlan {
     int NP = 16;       // limb columns (2k rounded up to 16)
     int stages = 6;    // shared-memory pipeline depth
     int ring = 4;      // TMEM A buffers
-    int F = 64;        // K chunks per TMEM accumulation window
+    int F = 32;        // K chunks per TMEM accumulation window
+    int defer = 3;     // stages between a window's end and its fold into registers
     int grid = 0;      // CTAs
     int KC = 0;        // K chunks
     int n_groups = 0;  // M groups
