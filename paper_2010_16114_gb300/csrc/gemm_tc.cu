@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(320, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 9);
+            mbar_init(empty0 + 8 * s, 1);  // the MMA commit: decoders are done with a stage before its MMAs issue
         }
         for (int r = 0; r < R; ++r) {
             mbar_init(afull0 + 8 * r, 8);
@@ -167,20 +167,21 @@ __global__ void __launch_bounds__(320, 1)
     const int64_t nu = u1 > u0 ? u1 - u0 : 0;
     const int KC = P.KC, F = P.F;
     const long long lim = P.wait_limit;
+    // position of the first unit; every loop below advances its counters by
+    // increments only (no division on the per-stage path)
+    const int g0 = static_cast<int>(u0 / KC), kc0 = static_cast<int>(u0 - static_cast<int64_t>(g0) * KC);
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
+            int s = 0, kc = kc0, g = g0;
+            uint32_t ph = 0;
             int64_t issued = 0;
             for (int64_t i = 0; i < nu; ++i) {
-                const int s = static_cast<int>(i % S);
-                const int64_t f = i / S;
-                if (f >= 1 && !mbar_wait(empty0 + 8 * s, static_cast<uint32_t>((f - 1) & 1), lim, abort_sm)) {
+                if (i >= S && !mbar_wait(empty0 + 8 * s, ph ^ 1u, lim, abort_sm)) {
                     fail(abort_sm, P.err);
                     break;
                 }
-                const int64_t u = u0 + i;
-                const int g = static_cast<int>(u / KC), kc = static_cast<int>(u % KC);
                 const uint32_t st = smem_addr(smem + s * STAGE);
                 const uint32_t fb = full0 + 8 * s;
                 mbar_arrive_expect_tx(fb, STAGE);
@@ -188,56 +189,75 @@ __global__ void __launch_bounds__(320, 1)
                 tma_load_2d(st + NP * 128, &tmB, kc * TILE + 64, 0, fb);
                 tma_load_4d(st + B_BYTES, &tmA, 0, 0, kc, g * T, fb);
                 issued = i + 1;
+                if (++s == S) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+                if (++kc == KC) {
+                    kc = 0;
+                    ++g;
+                }
             }
             // never leave a copy in flight into shared memory we are about to give up
-            for (int64_t i = issued > S ? issued - S : 0; i < issued; ++i)
-                mbar_wait(full0 + 8 * static_cast<int>(i % S), static_cast<uint32_t>((i / S) & 1), DRAIN_LIMIT,
-                          &g_never_set);
+            const int64_t from = issued > S ? issued - S : 0;
+            int sd = static_cast<int>(from % S);
+            uint32_t pd = static_cast<uint32_t>((from / S) & 1);
+            for (int64_t i = from; i < issued; ++i) {
+                mbar_wait(full0 + 8 * sd, pd, DRAIN_LIMIT, &g_never_set);
+                if (++sd == S) {
+                    sd = 0;
+                    pd ^= 1u;
+                }
+            }
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_bf16_f32(128, NP);
-            int64_t wi = -1, wstart = 0;
+            int s = 0, r = 0, kc = kc0, wlen = 0, b = 1;
+            uint32_t aph = 0, eph = 1;  // afull phase; acce phase of buffer b (flips per reuse)
+            int64_t wi = -1;
             bool ok = true;
+            const uint64_t desc0 = smem_desc_sw128(smem_addr(smem));
             for (int64_t i = 0; i < nu; ++i) {
-                const int s = static_cast<int>(i % S);
-                const int64_t f = i / S;
-                const int r = static_cast<int>(i % R);
-                const int64_t m = i / R;
-                const int64_t u = u0 + i;
-                const int kc = static_cast<int>(u % KC);
-                const bool first = window_first(i, kc, wstart, F);
+                const bool first = (i == 0) || (kc == 0) || (wlen == F);
                 if (first) {
                     ++wi;
-                    wstart = i;
-                    if (wi >= 2 && !mbar_wait(acce0 + 8 * (wi & 1), static_cast<uint32_t>(((wi >> 1) - 1) & 1), lim, abort_sm)) {
+                    wlen = 0;
+                    b ^= 1;
+                    if (b == 0) eph ^= 1u;
+                    if (wi >= 2 && !mbar_wait(acce0 + 8 * b, eph ^ 1u, lim, abort_sm)) {
                         ok = false;
                         break;
                     }
                 }
-                const bool last = (i == nu - 1) || (kc == KC - 1) || (i + 1 - wstart == F);
-                const int b = static_cast<int>(wi & 1);
-                if (!mbar_wait(full0 + 8 * s, static_cast<uint32_t>(f & 1), lim, abort_sm) ||
-                    !mbar_wait(afull0 + 8 * r, static_cast<uint32_t>(m & 1), lim, abort_sm)) {
+                ++wlen;
+                const bool last = (i == nu - 1) || (kc == KC - 1) || (wlen == F);
+                if (!mbar_wait(afull0 + 8 * r, aph, lim, abort_sm)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t st_b = smem_addr(smem + s * STAGE);
+                const uint64_t dstage = desc0 + static_cast<uint64_t>((s * STAGE) >> 4);
 #pragma unroll
                 for (int t = 0; t < T; ++t) {
                     const uint32_t d = tbase + static_cast<uint32_t>((b * T + t) * NP);
                     const uint32_t a = tbase + static_cast<uint32_t>(ACC_COLS + r * SLOT_COLS + t * 64);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
-                        const uint64_t bd = smem_desc_sw128(st_b + (q >> 2) * NP * 128 + (q & 3) * 32);
+                        const uint64_t bd = dstage + static_cast<uint64_t>(((q >> 2) * NP * 128 + (q & 3) * 32) >> 4);
                         mma_ts(d, a + 8 * q, bd, idesc, (first && q == 0) ? 0u : 1u);
                     }
                 }
                 mma_commit(aempty0 + 8 * r);
                 mma_commit(empty0 + 8 * s);
                 if (last) mma_commit(accf0 + 8 * b);
+                if (++s == S) s = 0;
+                if (++r == R) {
+                    r = 0;
+                    aph ^= 1u;
+                }
+                if (++kc == KC) kc = 0;
             }
             if (!ok) fail(abort_sm, P.err);
             mma_commit(drainb);
@@ -256,16 +276,16 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll
             for (int e = 0; e < KH; ++e) acc[t][e] = 0.f;
 
-        int64_t wi = -1, wstart = 0;
         bool pend = false, pend_segend = false;
         int pend_b = 0, pend_g = 0;
-        int64_t pend_m = 0, pend_due = 0;
+        uint32_t pend_ph = 0;
+        int64_t pend_due = 0;
         uint32_t epi_phase = 0;
         bool ok = true;
 
-        auto drain = [&](int b, int64_t m, bool segend, int g) {
+        auto drain = [&](int b, uint32_t ph, bool segend, int g) {
             if (!ok) return;
-            if (!warp_wait(accf0 + 8 * b, static_cast<uint32_t>(m & 1), lim, abort_sm)) {
+            if (!warp_wait(accf0 + 8 * b, ph, lim, abort_sm)) {
                 ok = false;
                 return;
             }
@@ -350,27 +370,25 @@ __global__ void __launch_bounds__(320, 1)
             }
         };
 
+        int s = 0, r = 0, kc = kc0, g = g0, wlen = 0, b = 1;
+        uint32_t fph = 0, aph = 0, bph = 1;  // full, aempty, accf phases
         for (int64_t i = 0; i < nu && ok; ++i) {
-            const int s = static_cast<int>(i % S);
-            const int64_t f = i / S;
-            const int r = static_cast<int>(i % R);
-            const int64_t m = i / R;
-            const int64_t u = u0 + i;
-            const int g = static_cast<int>(u / KC), kc = static_cast<int>(u % KC);
-            if (window_first(i, kc, wstart, F)) {
-                ++wi;
-                wstart = i;
+            if ((i == 0) || (kc == 0) || (wlen == F)) {
+                wlen = 0;
+                b ^= 1;
+                if (b == 0) bph ^= 1u;
             }
+            ++wlen;
             // fold the previous window once `defer` stages have passed (by then the
             // MMAs of that window have completed, so the wait is short)
             if (pend && i >= pend_due) {
-                drain(pend_b, pend_m, pend_segend, pend_g);
+                drain(pend_b, pend_ph, pend_segend, pend_g);
                 pend = false;
                 if (!ok) break;
             }
-            const bool last = (i == nu - 1) || (kc == KC - 1) || (i + 1 - wstart == F);
-            if (!warp_wait(full0 + 8 * s, static_cast<uint32_t>(f & 1), lim, abort_sm) ||
-                (m >= 1 && !warp_wait(aempty0 + 8 * r, static_cast<uint32_t>((m - 1) & 1), lim, abort_sm))) {
+            const bool last = (i == nu - 1) || (kc == KC - 1) || (wlen == F);
+            if (!warp_wait(full0 + 8 * s, fph, lim, abort_sm) ||
+                (i >= R && !warp_wait(aempty0 + 8 * r, aph ^ 1u, lim, abort_sm))) {
                 ok = false;
                 break;
             }
@@ -390,26 +408,35 @@ __global__ void __launch_bounds__(320, 1)
             tmem_wait_st();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(afull0 + 8 * r);
-                mbar_arrive(empty0 + 8 * s);
-            }
+            if (lane == 0) mbar_arrive(afull0 + 8 * r);
             if (last) {
                 // a window shorter than `defer`: fold the older one now, so at most one
                 // fold is ever owed and it always precedes the window that reuses its buffer
                 if (pend) {
-                    drain(pend_b, pend_m, pend_segend, pend_g);
+                    drain(pend_b, pend_ph, pend_segend, pend_g);
                     if (!ok) break;
                 }
                 pend = true;
-                pend_b = static_cast<int>(wi & 1);
-                pend_m = wi >> 1;
+                pend_b = b;
+                pend_ph = bph;
                 pend_segend = (i == nu - 1) || (kc == KC - 1);
                 pend_g = g;
                 pend_due = i + 1 + P.defer;
             }
+            if (++s == S) {
+                s = 0;
+                fph ^= 1u;
+            }
+            if (++r == R) {
+                r = 0;
+                aph ^= 1u;
+            }
+            if (++kc == KC) {
+                kc = 0;
+                ++g;
+            }
         }
-        if (ok && pend) drain(pend_b, pend_m, pend_segend, pend_g);
+        if (ok && pend) drain(pend_b, pend_ph, pend_segend, pend_g);
         if (!ok) fail(abort_sm, P.err);
     }
 
