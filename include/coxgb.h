@@ -122,6 +122,29 @@ void cox_destroy(cox_h h);
  */
 int cox_lipschitz(cox_h h, const double *start_host, double tol, int maxiter, double *L_out);
 
+/*
+ * cox_lipschitz without any device allocation.  The paper has no counterpart;
+ * this entry point exists for callers that cannot allocate device memory at
+ * call time: a process whose GPU memory is already reserved by another
+ * allocator (a framework's caching pool, a fixed arena), so that cudaMalloc
+ * fails or must not be used, and latency-sensitive loops that cannot afford
+ * the device-wide synchronisation cudaFree implies.
+ *
+ * Same arguments, result and power method as cox_lipschitz.  The work
+ * vectors live in a 16 MiB array built into the library (every GPU that loads
+ * the library holds it until the process exits).  Limit: with e = 4 bytes
+ * (genotype handles) or 8 (COX_FP64 handles), the call needs
+ *   e * (p + n_pad + p_pad) + 256 (+ 8 p when start_host is given)
+ * bytes, each term rounded up to 256; larger problems get COX_ERR_ARG
+ * (n_pad, p_pad from cox_get_info; for COX_FP64 n_pad, p_pad read n, p).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Calls share the array: calls that overlap on
+ * the GPU race; each call writes everything it reads.  Calls no cudaMalloc,
+ * cudaFree or allocating library routine.  Synchronous (legacy stream).
+ */
+int cox_lipschitz_noalloc(cox_h h, const double *start_host, double tol, int maxiter, double *L_out);
+
 /* lambda_max = ||g(0)||_inf: the smallest lambda for which beta = 0 solves
  * the problem (g(0) uses u(0), the Nelson-Aalen hazard).  Synchronous. */
 int cox_lambda_max(cox_h h, double *lmax_out);

@@ -35,7 +35,7 @@ EXPORTS = [
     "cox_default_options", "cox_setup", "cox_destroy", "cox_lipschitz", "cox_lambda_max",
     "cox_loss_grad", "cox_prox_step", "cox_prox_step_host", "cox_sync", "cox_last_objective",
     "cox_path_fit", "cox_get_state", "cox_set_state", "cox_get_info", "cox_get_mu_order",
-    "cox_strerror", "cox_set_precision", "cox_profile", "cox_profile_read",
+    "cox_strerror", "cox_set_precision", "cox_profile", "cox_profile_read", "cox_lipschitz_noalloc",
 ]
 
 
@@ -80,6 +80,8 @@ def load(path: str | None = None):
     lib.cox_destroy.argtypes = [P]
     lib.cox_lipschitz.restype = I
     lib.cox_lipschitz.argtypes = [P, P, D, I, ctypes.POINTER(D)]
+    lib.cox_lipschitz_noalloc.restype = I
+    lib.cox_lipschitz_noalloc.argtypes = [P, P, D, I, ctypes.POINTER(D)]
     lib.cox_lambda_max.restype = I
     lib.cox_lambda_max.argtypes = [P, ctypes.POINTER(D)]
     lib.cox_loss_grad.restype = I
@@ -149,6 +151,12 @@ def cox_destroy(h):
 def cox_lipschitz(h, start_ptr=None, tol=0.0, maxiter=0):
     L = ctypes.c_double()
     rc = load().cox_lipschitz(h, start_ptr, tol, maxiter, ctypes.byref(L))
+    return rc, L.value
+
+
+def cox_lipschitz_noalloc(h, start_ptr=None, tol=0.0, maxiter=0):
+    L = ctypes.c_double()
+    rc = load().cox_lipschitz_noalloc(h, start_ptr, tol, maxiter, ctypes.byref(L))
     return rc, L.value
 
 

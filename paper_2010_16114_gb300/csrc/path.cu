@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -397,3 +398,137 @@ int cox_set_state(cox_h h, const void *buf, size_t size)
 }
 
 } // extern "C"
+
+// ---- step size without device allocation ------------------------------------
+//
+// cox_lipschitz_noalloc runs the same power method as cox_lipschitz, but its
+// work vectors live in one file-scope device array instead of memory taken
+// with cudaMalloc.  The array is part of the library image: every GPU that
+// loads the library holds it until the process exits.  Host code only ever
+// sees a host-side stand-in for it under its name, so the device address is
+// looked up once per device with cudaGetSymbolAddress (with that device
+// current) and passed to the kernels.  All calls share the array; calls that
+// overlap on the GPU race on it.  Each call writes every element it later
+// reads, so nothing left by an earlier call leaks into a result.
+namespace coxgb {
+namespace {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = static_cast<size_t>(16) << 20;  // 16 MiB
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_BYTES / sizeof(double)];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on device `dev` (current).  First call
+// per device performs the lookup.
+int noalloc_scratch(int dev, void **out)
+{
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return COX_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return COX_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return COX_OK;
+}
+
+// v = start / ||start|| (start == null: all entries 1/sqrt(p)); one block.
+template <typename TV>
+__global__ void k_start_vector(const double *__restrict__ start, int64_t p, TV *__restrict__ v)
+{
+    __shared__ double sh[RB];
+    double s = 0.0;
+    for (int64_t j = threadIdx.x; j < p; j += RB) s += start ? start[j] * start[j] : 1.0;
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = RB / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double inv = 1.0 / sqrt(sh[0]);
+    for (int64_t j = threadIdx.x; j < p; j += RB) v[j] = static_cast<TV>((start ? start[j] : 1.0) * inv);
+}
+
+template <typename TV>
+int power_method_noalloc(cox_handle *h, const double *start, double tol, int maxiter, double *L_out)
+{
+    const int64_t n = h->n, p = h->p;
+    const bool f64 = h->opt.precision == COX_FP64;
+    const int64_t alen = f64 ? n : h->n_pad, blen = f64 ? p : h->p_pad;
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t off_a = up(p * sizeof(TV));
+    const size_t off_b = off_a + up(alen * sizeof(TV));
+    const size_t off_sc = off_b + up(blen * sizeof(TV));
+    const size_t off_st = off_sc + 256;
+    const size_t need = off_st + (start ? up(p * sizeof(double)) : 0);
+    if (need > NOALLOC_SCRATCH_BYTES) return COX_ERR_ARG;
+    void *base = nullptr;
+    COX_TRY(noalloc_scratch(h->dev, &base));
+    uint8_t *b8 = static_cast<uint8_t *>(base);
+    TV *v = reinterpret_cast<TV *>(b8);
+    TV *a = reinterpret_cast<TV *>(b8 + off_a);
+    TV *b = reinterpret_cast<TV *>(b8 + off_b);
+    double *sc = reinterpret_cast<double *>(b8 + off_sc);
+    double *st_dev = start ? reinterpret_cast<double *>(b8 + off_st) : nullptr;
+    cudaStream_t st = 0;
+    if (start) COX_CUDA(cudaMemcpyAsync(st_dev, start, p * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_start_vector<TV><<<1, RB, 0, st>>>(st_dev, p, v);
+    COX_CUDA(cudaGetLastError());
+    double s = 0.0, s_prev = 0.0;
+    int rc = COX_OK;
+    for (int it = 1; it <= maxiter; ++it) {
+        k_dot_mu<TV><<<1, RB, 0, st>>>(h->d_mu, v, p, sc);
+        if (f64) {
+            rc = eta64(h, reinterpret_cast<const double *>(v), 1, reinterpret_cast<double *>(a), st);
+        } else {
+            rc = gemv_tiles(h, h->d_A1, h->n_pad, h->p_pad / TILE, reinterpret_cast<const float *>(v), p,
+                            reinterpret_cast<float *>(a), st);
+        }
+        if (rc != COX_OK) break;
+        k_center_sum<TV><<<1, RB, 0, st>>>(a, n, alen, sc, sc + 1);
+        if (f64) {
+            k_xta64<<<static_cast<unsigned>((p * 32 + 255) / 256), 256, 0, st>>>(
+                h->d_Xc, n, p, reinterpret_cast<const double *>(a), reinterpret_cast<double *>(b));
+        } else {
+            rc = gemv_tiles(h, h->d_A4, h->p_pad, h->n_pad / TILE, reinterpret_cast<const float *>(a), n,
+                            reinterpret_cast<float *>(b), st);
+            if (rc != COX_OK) break;
+        }
+        k_center_norm<TV><<<1, RB, 0, st>>>(b, h->d_mu, p, sc + 1, sc + 2);
+        double nb2 = 0.0;
+        if (cudaMemcpy(&nb2, sc + 2, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            rc = COX_ERR_CUDA;
+            break;
+        }
+        if (!(nb2 > 0.0) || !std::isfinite(nb2)) {
+            s = 0.0;
+            break;
+        }
+        s = std::sqrt(nb2);
+        k_scale<TV><<<static_cast<unsigned>((p + 255) / 256), 256, 0, st>>>(b, v, p, 1.0 / s);
+        if (it > 1 && std::fabs(s - s_prev) <= tol * s) break;
+        s_prev = s;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == COX_OK) rc = COX_ERR_CUDA;
+    if (rc == COX_OK) *L_out = 2.0 * s / static_cast<double>(n);
+    return rc;
+}
+
+} // namespace
+} // namespace coxgb
+
+extern "C" int cox_lipschitz_noalloc(cox_h h, const double *start_host, double tol, int maxiter, double *L_out)
+{
+    if (!h || !L_out) return COX_ERR_ARG;
+    DeviceGuard g(h->dev);
+    if (!(tol > 0.0)) tol = 1e-6;
+    if (maxiter <= 0) maxiter = 1000;
+    if (h->opt.precision == COX_FP64) return power_method_noalloc<double>(h, start_host, tol, maxiter, L_out);
+    return power_method_noalloc<float>(h, start_host, tol, maxiter, L_out);
+}
