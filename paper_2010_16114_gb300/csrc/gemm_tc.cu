@@ -99,17 +99,32 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, long lo
     return __all_sync(0xffffffffu, mbar_wait(bar, parity, lim, abort));
 }
 
-template <int T, int NP>
-__global__ void __launch_bounds__(320, 1)
+// Warp roles (WARPS = 1 + I + 4 G):
+//   warp 0            TMA producer (lane 0); allocates TMEM
+//   warps 1 .. I      MMA issuers: issuer j owns row tile t = j / H and K part
+//                     h = j % H of every stage, accumulating into its own TMEM
+//                     accumulator (a single thread issues at most one MMA per
+//                     ~50 cycles, so I issuers keep the tensor pipe fed)
+//   warps I+1 ..      G decoder groups of four warps (one per TMEM lane
+//                     quarter); group gamma decodes stages i = gamma (mod G), so
+//                     the latency of one stage's waits and stores overlaps with
+//                     the other groups' work.  Group 0 also folds the
+//                     accumulators into registers at window ends and runs the
+//                     epilogue.
+template <int T, int H, int NP, int G>
+__global__ void __launch_bounds__(32 * (1 + T * H + 4 * G), 1)
     k_packed_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const KParams P)
 {
-    constexpr int KH = NP / 4;
+    constexpr int I = T * H;              // MMA issuers
+    constexpr int QH = 8 / H;             // K16 MMAs per issuer per stage
+    constexpr int KH = NP / 2;            // lambda columns a decoder thread folds (NP/2 >= k)
     constexpr int B_BYTES = NP * 256;
     constexpr int X_BYTES = T * BLOCK_BYTES;
     constexpr int STAGE = B_BYTES + X_BYTES;
-    constexpr int ACC_COLS = 2 * T * NP;
+    constexpr int ACC_COLS = I * NP;      // single-buffered accumulators
     constexpr int SLOT_COLS = T * 64;
+    constexpr int DEC0 = 1 + I;           // first decoder warp
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -120,11 +135,11 @@ __global__ void __launch_bounds__(320, 1)
     const uint32_t empty0 = full0 + 8 * S;
     const uint32_t afull0 = empty0 + 8 * S;
     const uint32_t aempty0 = afull0 + 8 * R;
-    const uint32_t accf0 = aempty0 + 8 * R;
-    const uint32_t acce0 = accf0 + 16;
-    const uint32_t drainb = acce0 + 16;
+    const uint32_t accf = aempty0 + 8 * R;
+    const uint32_t acce = accf + 8;
+    const uint32_t drainb = acce + 8;
     const uint32_t epib = drainb + 8;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 2 * R + 6);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 2 * R + 4);
     volatile int *abort_sm = reinterpret_cast<volatile int *>(tmem_slot + 1);
     volatile int *last_sm = reinterpret_cast<volatile int *>(tmem_slot + 2);
 
@@ -132,23 +147,21 @@ __global__ void __launch_bounds__(320, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);  // the MMA commit: decoders are done with a stage before its MMAs issue
+            mbar_init(empty0 + 8 * s, I);
         }
         for (int r = 0; r < R; ++r) {
-            mbar_init(afull0 + 8 * r, 8);
-            mbar_init(aempty0 + 8 * r, 1);
+            mbar_init(afull0 + 8 * r, 4);
+            mbar_init(aempty0 + 8 * r, I);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(accf0 + 8 * b, 1);
-            mbar_init(acce0 + 8 * b, 8);
-        }
-        mbar_init(drainb, 1);
-        mbar_init(epib, 8);
+        mbar_init(accf, I);
+        mbar_init(acce, 4);
+        mbar_init(drainb, I);
+        mbar_init(epib, 4);
         *abort_sm = 0;
         *last_sm = 0;
         mbar_fence_init();
     }
-    if (warp == 1) {
+    if (warp == 0) {
         tmem_alloc(smem_addr(tmem_slot), 512);
         tmem_relinquish();
     }
@@ -167,7 +180,7 @@ __global__ void __launch_bounds__(320, 1)
     const int64_t nu = u1 > u0 ? u1 - u0 : 0;
     const int KC = P.KC, F = P.F;
     const long long lim = P.wait_limit;
-    // position of the first unit; every loop below advances its counters by
+    // position of the first unit; the loops below advance their counters by
     // increments only (no division on the per-stage path)
     const int g0 = static_cast<int>(u0 / KC), kc0 = static_cast<int>(u0 - static_cast<int64_t>(g0) * KC);
 
@@ -210,12 +223,15 @@ __global__ void __launch_bounds__(320, 1)
                 }
             }
         }
-    } else if (warp == 1) {
-        // ---------------- MMA issuer ----------------
+    } else if (warp <= I) {
+        // ---------------- MMA issuers ----------------
         if (lane == 0) {
+            const int j = warp - 1;
+            const int t = j / H, h = j % H;
             constexpr uint32_t idesc = idesc_bf16_f32(128, NP);
-            int s = 0, r = 0, kc = kc0, wlen = 0, b = 1;
-            uint32_t aph = 0, eph = 1;  // afull phase; acce phase of buffer b (flips per reuse)
+            const uint32_t d = tbase + static_cast<uint32_t>(j * NP);
+            int s = 0, r = 0, kc = kc0, wlen = 0;
+            uint32_t aph = 0, eph = 0;
             int64_t wi = -1;
             bool ok = true;
             const uint64_t desc0 = smem_desc_sw128(smem_addr(smem));
@@ -224,11 +240,13 @@ __global__ void __launch_bounds__(320, 1)
                 if (first) {
                     ++wi;
                     wlen = 0;
-                    b ^= 1;
-                    if (b == 0) eph ^= 1u;
-                    if (wi >= 2 && !mbar_wait(acce0 + 8 * b, eph ^ 1u, lim, abort_sm)) {
-                        ok = false;
-                        break;
+                    // the accumulator is reused: wait until group 0 has folded the previous window
+                    if (wi >= 1) {
+                        if (!mbar_wait(acce, eph, lim, abort_sm)) {
+                            ok = false;
+                            break;
+                        }
+                        eph ^= 1u;
                     }
                 }
                 ++wlen;
@@ -239,19 +257,16 @@ __global__ void __launch_bounds__(320, 1)
                 }
                 tc_fence_after();
                 const uint64_t dstage = desc0 + static_cast<uint64_t>((s * STAGE) >> 4);
+                const uint32_t a = tbase + static_cast<uint32_t>(ACC_COLS + r * SLOT_COLS + t * 64);
 #pragma unroll
-                for (int t = 0; t < T; ++t) {
-                    const uint32_t d = tbase + static_cast<uint32_t>((b * T + t) * NP);
-                    const uint32_t a = tbase + static_cast<uint32_t>(ACC_COLS + r * SLOT_COLS + t * 64);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const uint64_t bd = dstage + static_cast<uint64_t>(((q >> 2) * NP * 128 + (q & 3) * 32) >> 4);
-                        mma_ts(d, a + 8 * q, bd, idesc, (first && q == 0) ? 0u : 1u);
-                    }
+                for (int qq = 0; qq < QH; ++qq) {
+                    const int q = h * QH + qq;
+                    const uint64_t bd = dstage + static_cast<uint64_t>(((q >> 2) * NP * 128 + (q & 3) * 32) >> 4);
+                    mma_ts(d, a + 8 * q, bd, idesc, (first && qq == 0) ? 0u : 1u);
                 }
                 mma_commit(aempty0 + 8 * r);
                 mma_commit(empty0 + 8 * s);
-                if (last) mma_commit(accf0 + 8 * b);
+                if (last) mma_commit(accf);
                 if (++s == S) s = 0;
                 if (++r == R) {
                     r = 0;
@@ -264,50 +279,51 @@ __global__ void __launch_bounds__(320, 1)
             mbar_wait(drainb, 0, DRAIN_LIMIT, &g_never_set);
         }
     } else {
-        // ---------------- decoders / accumulators / epilogue ----------------
-        const int h = (warp - 2) >> 2;    // K half of each chunk (64 codes)
+        // ---------------- decoders (group gamma), folds and epilogue (group 0) ----------------
+        const int dw = warp - DEC0;
+        const int gamma = dw >> 2;        // decoder group
         const int q = warp & 3;           // TMEM lane quarter
         const int rit = 32 * q + lane;    // row inside a 128-row tile
-        const int phys = h ^ ((rit >> 2) & 1);
+        const int swp = (rit >> 2) & 1;   // row halves stored swapped
         const uint32_t lane_base = tbase + (static_cast<uint32_t>(32 * q) << 16);
         float acc[T][KH];
 #pragma unroll
         for (int t = 0; t < T; ++t)
 #pragma unroll
             for (int e = 0; e < KH; ++e) acc[t][e] = 0.f;
-
-        bool pend = false, pend_segend = false;
-        int pend_b = 0, pend_g = 0;
-        uint32_t pend_ph = 0;
-        int64_t pend_due = 0;
-        uint32_t epi_phase = 0;
+        uint32_t epi_phase = 0, fold_phase = 0;
         bool ok = true;
 
-        auto drain = [&](int b, uint32_t ph, bool segend, int g) {
+        // group 0: fold the finished window into registers; at a segment end write
+        // this CTA's partial of group g and, for the last CTA, apply the epilogue
+        auto fold = [&](bool segend, int g) {
             if (!ok) return;
-            if (!warp_wait(accf0 + 8 * b, ph, lim, abort_sm)) {
+            if (!warp_wait(accf, fold_phase, lim, abort_sm)) {
                 ok = false;
                 return;
             }
+            fold_phase ^= 1u;
             tc_fence_after();
 #pragma unroll
             for (int t = 0; t < T; ++t) {
 #pragma unroll
-                for (int cc = 0; cc < KH / 4; ++cc) {
-                    uint32_t v[8];
-                    tmem_ld_32x32b_x8(lane_base + static_cast<uint32_t>((b * T + t) * NP + h * (NP / 2) + cc * 8), v);
-                    tmem_wait_ld();
+                for (int hh = 0; hh < H; ++hh) {
 #pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        acc[t][cc * 4 + e] += __uint_as_float(v[2 * e]) + __uint_as_float(v[2 * e + 1]);
+                    for (int cc = 0; cc < NP / 8; ++cc) {
+                        uint32_t v[8];
+                        tmem_ld_32x32b_x8(lane_base + static_cast<uint32_t>((t * H + hh) * NP + cc * 8), v);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            acc[t][cc * 4 + e] += __uint_as_float(v[2 * e]) + __uint_as_float(v[2 * e + 1]);
+                    }
                 }
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(acce0 + 8 * b);
+            if (lane == 0) mbar_arrive(acce);
             if (!segend) return;
 
-            // write this CTA's partial of group g
             const int64_t first_cta = (static_cast<int64_t>(g) * KC) / P.L;
             const int64_t slot = cta - first_cta;
 #pragma unroll
@@ -315,26 +331,24 @@ __global__ void __launch_bounds__(320, 1)
                 const int64_t row = (static_cast<int64_t>(g) * T + t) * TILE + rit;
 #pragma unroll
                 for (int e = 0; e < KH; ++e) {
-                    const int kk = h * KH + e;
-                    if (kk < P.k)
-                        P.part[slot * P.slot_stride + kk * P.rows_pad + row] = acc[t][e] * 0x1.0p64f;
+                    if (e < P.k) P.part[slot * P.slot_stride + e * P.rows_pad + row] = acc[t][e] * 0x1.0p64f;
                     acc[t][e] = 0.f;
                 }
             }
             if (P.epi == EPI_PARTIAL) return;
 
-            // last CTA of the group applies the step (Section 5.3: beta <- S(beta + sigma g, sigma lambda))
+            // the last CTA of the group applies the step (Section 5.3: beta <- S(beta + sigma g, sigma lambda))
             __threadfence();
             __syncwarp();
             if (lane == 0) mbar_arrive(epib);
-            if (!warp_wait(epib, epi_phase & 1, lim, abort_sm)) {
+            if (!warp_wait(epib, epi_phase, lim, abort_sm)) {
                 ok = false;
                 return;
             }
-            ++epi_phase;
+            epi_phase ^= 1u;
             const int64_t last_cta = (static_cast<int64_t>(g) * KC + KC - 1) / P.L;
             const int cnt = static_cast<int>(last_cta - first_cta + 1);
-            if (threadIdx.x == 64) {
+            if (threadIdx.x == 32 * DEC0) {
                 const int old = atomicAdd(&P.counters[g], 1);
                 const int is_last = (old == cnt - 1);
                 if (is_last) P.counters[g] = 0;
@@ -342,22 +356,22 @@ __global__ void __launch_bounds__(320, 1)
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(epib);
-            if (!warp_wait(epib, epi_phase & 1, lim, abort_sm)) {
+            if (!warp_wait(epib, epi_phase, lim, abort_sm)) {
                 ok = false;
                 return;
             }
-            ++epi_phase;
+            epi_phase ^= 1u;
             if (!*last_sm) return;
             __threadfence();
-            const int tid = threadIdx.x - 64;
+            const int tid = threadIdx.x - 32 * DEC0;
             const int64_t grows = static_cast<int64_t>(T) * TILE;
-            for (int64_t idx = tid; idx < grows * P.k; idx += 256) {
+            for (int64_t idx = tid; idx < grows * P.k; idx += 128) {
                 const int kk = static_cast<int>(idx / grows);
                 const int64_t row = static_cast<int64_t>(g) * grows + idx % grows;
                 if (row >= P.rows_valid) continue;
-                double G = 0.0;
-                for (int s2 = 0; s2 < cnt; ++s2) G += static_cast<double>(__ldcg(&P.part[s2 * P.slot_stride + kk * P.rows_pad + row]));
-                const double gv = (G - P.mu[row] * P.sumV[kk]) * P.inv_n;
+                double Gs = 0.0;
+                for (int s2 = 0; s2 < cnt; ++s2) Gs += static_cast<double>(__ldcg(&P.part[s2 * P.slot_stride + kk * P.rows_pad + row]));
+                const double gv = (Gs - P.mu[row] * P.sumV[kk]) * P.inv_n;
                 const int64_t bi = static_cast<int64_t>(kk) * P.rows_valid + row;
                 if (P.epi == EPI_PROX) {
                     if (P.active && !P.active[kk]) continue;
@@ -370,79 +384,87 @@ __global__ void __launch_bounds__(320, 1)
             }
         };
 
-        int s = 0, r = 0, kc = kc0, g = g0, wlen = 0, b = 1;
-        uint32_t fph = 0, aph = 0, bph = 1;  // full, aempty, accf phases
-        for (int64_t i = 0; i < nu && ok; ++i) {
-            if ((i == 0) || (kc == 0) || (wlen == F)) {
-                wlen = 0;
-                b ^= 1;
-                if (b == 0) bph ^= 1u;
+        // group 0 tracks windows of every stage (it owes the folds); all groups
+        // advance their stage counters by G per iteration
+        int s = gamma % S, r = gamma % R;
+        uint32_t fph = static_cast<uint32_t>((gamma / S) & 1), aph = static_cast<uint32_t>((gamma / R) & 1);
+        int kc = kc0 + gamma, g = g0;
+        while (kc >= KC) {
+            kc -= KC;
+            ++g;
+        }
+        // window bookkeeping (group 0): walk every stage in order and fold each
+        // window as soon as its last stage lies behind the stage being decoded
+        int wkc = kc0, wg = g0, wlen = 0;
+        int64_t wnext = 0;
+        auto fold_until = [&](int64_t upto) {  // stages [wnext, upto)
+            for (; wnext < upto && wnext < nu && ok; ++wnext) {
+                if (wnext == 0 || wkc == 0 || wlen == F) wlen = 0;
+                ++wlen;
+                const bool seg = (wnext == nu - 1) || (wkc == KC - 1);
+                if (seg || wlen == F) fold(seg, wg);
+                if (++wkc == KC) {
+                    wkc = 0;
+                    ++wg;
+                }
             }
-            ++wlen;
-            // fold the previous window once `defer` stages have passed (by then the
-            // MMAs of that window have completed, so the wait is short)
-            if (pend && i >= pend_due) {
-                drain(pend_b, pend_ph, pend_segend, pend_g);
-                pend = false;
+        };
+
+        for (int64_t i = gamma; i < nu && ok; i += G) {
+            if (gamma == 0) {
+                // windows ending before stage i: every stage of theirs is decoded
+                // or owned by another group, so their MMAs complete without us
+                fold_until(i);
                 if (!ok) break;
             }
-            const bool last = (i == nu - 1) || (kc == KC - 1) || (wlen == F);
             if (!warp_wait(full0 + 8 * s, fph, lim, abort_sm) ||
                 (i >= R && !warp_wait(aempty0 + 8 * r, aph ^ 1u, lim, abort_sm))) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            const uint8_t *xs = smem + s * STAGE + B_BYTES + rit * 32 + phys * 16;
-            const uint32_t acol = lane_base + static_cast<uint32_t>(ACC_COLS + r * SLOT_COLS + 32 * h);
+            const uint8_t *xs = smem + s * STAGE + B_BYTES + rit * 32;
+            const uint32_t acol = lane_base + static_cast<uint32_t>(ACC_COLS + r * SLOT_COLS);
 #pragma unroll
             for (int t = 0; t < T; ++t) {
-                const uint4 v = *reinterpret_cast<const uint4 *>(xs + t * BLOCK_BYTES);
-                uint32_t o[32];
-                decode16(v.x, o);
-                decode16(v.y, o + 8);
-                decode16(v.z, o + 16);
-                decode16(v.w, o + 24);
-                tmem_st_32x32b_x32(acol + t * 64, o);
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(xs + t * BLOCK_BYTES + 16 * (hh ^ swp));
+                    uint32_t o[32];
+                    decode16(v.x, o);
+                    decode16(v.y, o + 8);
+                    decode16(v.z, o + 16);
+                    decode16(v.w, o + 24);
+                    tmem_st_32x32b_x32(acol + t * 64 + 32 * hh, o);
+                }
             }
             tmem_wait_st();
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(afull0 + 8 * r);
-            if (last) {
-                // a window shorter than `defer`: fold the older one now, so at most one
-                // fold is ever owed and it always precedes the window that reuses its buffer
-                if (pend) {
-                    drain(pend_b, pend_ph, pend_segend, pend_g);
-                    if (!ok) break;
-                }
-                pend = true;
-                pend_b = b;
-                pend_ph = bph;
-                pend_segend = (i == nu - 1) || (kc == KC - 1);
-                pend_g = g;
-                pend_due = i + 1 + P.defer;
-            }
-            if (++s == S) {
-                s = 0;
+            s += G;
+            if (s >= S) {
+                s -= S;
                 fph ^= 1u;
             }
-            if (++r == R) {
-                r = 0;
+            r += G;
+            while (r >= R) {
+                r -= R;
                 aph ^= 1u;
             }
-            if (++kc == KC) {
-                kc = 0;
+            kc += G;
+            while (kc >= KC) {
+                kc -= KC;
                 ++g;
             }
         }
-        if (ok && pend) drain(pend_b, pend_ph, pend_segend, pend_g);
+        if (gamma == 0 && ok) fold_until(nu);
         if (!ok) fail(abort_sm, P.err);
     }
 
     tc_fence_before();
     __syncthreads();
-    if (warp == 1) {
+    if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tbase, 512);
     }
@@ -484,20 +506,28 @@ EncodeTiled get_encoder()
 
 using KernelFn = void (*)(const CUtensorMap, const CUtensorMap, const KParams);
 
-KernelFn pick_kernel(int T, int NP)
+constexpr int DEC_GROUPS = 3;
+
+// (T row tiles, H K parts per stage) for a limb-column class NP
+void shape_for(int NP, int *T, int *H)
 {
-    switch (T * 1000 + NP) {
-    case 1016: return k_packed_gemm<1, 16>;
-    case 2016: return k_packed_gemm<2, 16>;
-    case 4016: return k_packed_gemm<4, 16>;
-    case 1032: return k_packed_gemm<1, 32>;
-    case 2032: return k_packed_gemm<2, 32>;
-    case 1064: return k_packed_gemm<1, 64>;
-    case 2064: return k_packed_gemm<2, 64>;
-    case 1128: return k_packed_gemm<1, 128>;
+    if (NP <= 32) { *T = 2; *H = 2; }
+    else if (NP == 64) { *T = 2; *H = 1; }
+    else { *T = 1; *H = 2; }
+}
+
+KernelFn pick_kernel(int T, int H, int NP)
+{
+    switch ((T * 10 + H) * 1000 + NP) {
+    case 22016: return k_packed_gemm<2, 2, 16, DEC_GROUPS>;
+    case 22032: return k_packed_gemm<2, 2, 32, DEC_GROUPS>;
+    case 21064: return k_packed_gemm<2, 1, 64, DEC_GROUPS>;
+    case 12128: return k_packed_gemm<1, 2, 128, DEC_GROUPS>;
     default: return nullptr;
     }
 }
+
+int threads_for(int T, int H) { return 32 * (1 + T * H + 4 * DEC_GROUPS); }
 
 } // namespace
 
@@ -510,28 +540,26 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
     const int NP = (2 * k + 15) / 16 * 16;
     const int np_cls = NP <= 16 ? 16 : NP <= 32 ? 32 : NP <= 64 ? 64 : 128;
     const int64_t m_tiles = rows_pad / TILE;
-    int T = T_req > 0 ? T_req : 2;
-    if (T > 4) T = 4;
-    if (T != 1 && T != 2 && T != 4) return COX_ERR_ARG;
-    if (np_cls >= 32 && T > 2) T = 2;
-    if (np_cls == 128) T = 1;
-    while (T > 1 && (512 - 2 * T * np_cls) / (T * 64) < 2) T >>= 1;
+    (void)T_req;  // the row-tile count follows from the limb-column class
+    int T = 2, H = 2;
+    shape_for(np_cls, &T, &H);
     if (m_tiles % T != 0) return COX_ERR_ARG;
-    int ring = (512 - 2 * T * np_cls) / (T * 64);
+    int ring = (512 - T * H * np_cls) / (T * 64);
     if (ring > 8) ring = 8;
     if (ring < 2) return COX_ERR_ARG;
+    g.H = H;
     g.T = T;
     g.NP = np_cls;
     g.ring = ring;
     const int stage = np_cls * 256 + T * BLOCK_BYTES;
     int S = stages_req > 0 ? stages_req : (225 * 1024 - 2048) / stage;
     if (S > 12) S = 12;
-    if (S < 2) S = 2;
+    if (S < DEC_GROUPS + 1) S = DEC_GROUPS + 1;  // decoder groups step through the stage ring by DEC_GROUPS
     g.stages = S;
     g.smem = static_cast<size_t>(S) * stage + 1024 + 1024;
     if (g.smem < 120 * 1024) g.smem = 120 * 1024;  // one CTA per SM: it owns all 512 TMEM columns
-    g.F = 32;
-    g.defer = std::min(ring, g.F - 1);
+    g.F = 64;  // K chunks per accumulation window: 64 x 8 / H MMAs into one accumulator
+    g.defer = 0;
     g.KC = static_cast<int>(K_pad / TILE);
     g.n_groups = static_cast<int>(m_tiles / T);
     g.units = static_cast<int64_t>(g.n_groups) * g.KC;
@@ -547,7 +575,7 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
     g.max_slots = ms;
     g.rows_pad = rows_pad;
     {
-        KernelFn fn = pick_kernel(g.T, g.NP);
+        KernelFn fn = pick_kernel(g.T, g.H, g.NP);
         if (!fn) return COX_ERR_ARG;
         COX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(g.smem)));
     }
@@ -605,9 +633,9 @@ int launch_gemm(cox_handle *h, const GemmPlan &g, const EpiArgs &e, int k, cudaS
     kp.inv_n = e.inv_n;
     kp.wait_limit = h->wait_cycles;
     kp.err = h->d_err;
-    KernelFn fn = pick_kernel(g.T, g.NP);
+    KernelFn fn = pick_kernel(g.T, g.H, g.NP);
     if (!fn) return COX_ERR_ARG;
-    fn<<<g.grid, 320, g.smem, st>>>(g.tmA, g.tmB, kp);
+    fn<<<g.grid, threads_for(g.T, g.H), g.smem, st>>>(g.tmA, g.tmB, kp);
     COX_CUDA(cudaGetLastError());
     return COX_OK;
 }

@@ -21,7 +21,8 @@ constexpr int MAX_K_TC = 64;       // largest k of the tensor-core path
 
 // One tensor-core product: a 2-bit A (rows x K, tiled) times limb matrix B.
 struct GemmPlan {
-    int T = 4;         // 128-row tiles per CTA (one M group)
+    int T = 2;         // 128-row tiles per CTA (one M group)
+    int H = 2;         // K parts per stage, one MMA-issuing warp per (tile, part)
     int NP = 16;       // limb columns (2k rounded up to 16)
     int stages = 6;    // shared-memory pipeline depth
     int ring = 4;      // TMEM A buffers
