@@ -132,11 +132,11 @@ int cox_lipschitz(cox_h h, const double *start_host, double tol, int maxiter, do
  *
  * Same arguments, result and power method as cox_lipschitz.  The work
  * vectors live in a 16 MiB array built into the library (every GPU that loads
- * the library holds it until the process exits).  Limit: with e = 4 bytes
- * (genotype handles) or 8 (COX_FP64 handles), the call needs
- *   e * (p + n_pad + p_pad) + 256 (+ 8 p when start_host is given)
- * bytes, each term rounded up to 256; larger problems get COX_ERR_ARG
- * (n_pad, p_pad from cox_get_info; for COX_FP64 n_pad, p_pad read n, p).
+ * the library holds it until the process exits).  Limit: the call needs
+ *   4 (p + 2 n_pad + p_pad) + 256   bytes (genotype handles),
+ *   8 (2 p + n) + 256               bytes (COX_FP64 handles),
+ * plus 8 p when start_host is given, each term rounded up to 256; larger
+ * problems get COX_ERR_ARG (n_pad, p_pad from cox_get_info).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  Calls share the array: calls that overlap on

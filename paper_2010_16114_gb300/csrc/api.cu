@@ -256,7 +256,7 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
         COX_CUDA(cudaMemcpyAsync(ws.Fring + k + c, ws.f, sizeof(double), cudaMemcpyDeviceToDevice, st));
         {
             Site s_(h, 1, 2, st);
-            COX_TRY(gemv_tiles(h, h->d_A4, h->p_pad, h->n_pad / TILE, ws.V32, h->n, ws.G32, st));
+            COX_TRY(gemv_tiles(h, h->d_A4, h->p_pad, h->n_pad / TILE, ws.V32, h->n_pad, ws.G32, st));
             float *gc = epi == EPI_GRAD ? static_cast<float *>(grad) : nullptr;
             COX_TRY(prox_or_grad32(h, ws.G32, c, epi == EPI_PROX ? b32 : nullptr, gc, ws.lam, step, st));
         }
@@ -347,7 +347,8 @@ int ensure_workspace(cox_handle *h, int k)
     } else if (is_fp64(h)) {
         A(ws.V64, k * n);
     } else {
-        A(ws.V32, n);
+        A(ws.V32, h->n_pad);  // A4 K order; positions of padding stay zero
+        cudaMemset(ws.V32, 0, h->n_pad * sizeof(float));
         A(ws.eta32, h->n_pad);
         A(ws.G32, h->p_pad);
     }
@@ -446,6 +447,14 @@ int cox_setup(cox_h *out, const void *X, int64_t n, int64_t p, int x_format, con
     h->n_pad = (n + PAD - 1) / PAD * PAD;
     h->p_pad = (p + PAD - 1) / PAD * PAD;
     h->n_chunks = static_cast<int>((n + SCAN_CH - 1) / SCAN_CH);
+    {
+        // A4 K order: multiplier near nb (sqrt 5 - 1) / 2, odd, prime to nb
+        const int64_t nb = h->n_pad / 16;
+        int64_t a = static_cast<int64_t>(std::llround(0.6180339887498949 * static_cast<double>(nb))) | 1;
+        while (std::gcd(a, nb) != 1) a += 2;
+        h->kperm_nb = nb;
+        h->kperm_a = a % nb;
+    }
     h->l1_blocks = static_cast<int>(std::min<int64_t>(64, (p + 4095) / 4096));
     {
         int khz = 0;

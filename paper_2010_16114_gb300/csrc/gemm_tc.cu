@@ -558,6 +558,7 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
     g.stages = S;
     g.smem = static_cast<size_t>(S) * stage + 1024 + 1024;
     if (g.smem < 120 * 1024) g.smem = 120 * 1024;  // one CTA per SM: it owns all 512 TMEM columns
+    if (g.smem > 227 * 1024) return COX_ERR_ARG;    // too many stages requested
     g.F = 64;  // K chunks per accumulation window: 64 x 8 / H MMAs into one accumulator
     g.defer = 0;
     g.KC = static_cast<int>(K_pad / TILE);

@@ -19,6 +19,18 @@ constexpr int PAD = 1024;          // n, p padding of the tiled layouts
 constexpr int SCAN_CH = 2048;      // subjects per scan chunk (256 threads x 8)
 constexpr int MAX_K_TC = 64;       // largest k of the tensor-core path
 
+// K order of the SNP-major copy (A4).  Sorted subjects are kept in blocks of
+// 16 (one packed word), and sorted block b is stored at block (a b) mod nb,
+// nb = n_pad / 16, a odd and prime to nb, near nb (sqrt 5 - 1) / 2.  Any run
+// of consecutive K positions then holds subjects spread evenly over the time
+// order, so the running sums of x_ij V_i that the tensor cores accumulate do
+// not drift with the time trend of V (V = delta - u sums to zero only over all
+// subjects); the positions inside a block, and so the K-slot scales, are kept.
+__host__ __device__ inline int64_t a4_pos(int64_t i, int64_t a, int64_t nb)
+{
+    return ((a * (i >> 4)) % nb) * 16 + (i & 15);
+}
+
 // One tensor-core product: a 2-bit A (rows x K, tiled) times limb matrix B.
 struct GemmPlan {
     int T = 2;         // 128-row tiles per CTA (one M group)
@@ -55,13 +67,13 @@ struct Workspace {
     double *Fring = nullptr;   // lag x k
     // split mode
     uint16_t *Bb = nullptr;    // NP x p_pad bf16 limbs of beta
-    uint16_t *Vb = nullptr;    // NP x n_pad bf16 limbs of V
+    uint16_t *Vb = nullptr;    // NP x n_pad bf16 limbs of V, A4 K order
     float *part1 = nullptr;    // slots x k x rows_pad (eta partials)
     float *part4 = nullptr;    // slots x k x rows_pad (X^T V partials)
     int *cnt4 = nullptr;       // per M group of the second product
     // fp64 / gemv
     double *V64 = nullptr;     // k x n
-    float *V32 = nullptr;      // n
+    float *V32 = nullptr;      // n_pad, A4 K order
     float *eta32 = nullptr;    // n
     float *G32 = nullptr;      // p
     GemmPlan g1, g4;
@@ -73,6 +85,7 @@ struct Workspace {
 struct cox_handle {
     int dev = 0, sm_count = 0;
     int64_t n = 0, p = 0, n_pad = 0, p_pad = 0;
+    int64_t kperm_a = 1, kperm_nb = 1;  // K order of A4 (a4_pos)
     int n_chunks = 0, l1_blocks = 0;
     cox_options opt;
     int64_t n_groups_tie = 0;

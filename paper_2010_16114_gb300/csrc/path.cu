@@ -56,6 +56,15 @@ __global__ void k_center_sum(TV *a, int64_t n, int64_t len, const double *s, dou
     if (threadIdx.x == 0) *out = sh[0];
 }
 
+// out[a4_pos(i)] = a[i], i < len: a vector over sorted subjects put in the K
+// order of the SNP-major genotype copy
+__global__ void k_to_a4(const float *__restrict__ a, int64_t len, int64_t pa, int64_t pnb, float *__restrict__ out)
+{
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < len;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        out[a4_pos(i, pa, pnb)] = a[i];
+}
+
 // b_j -= mu_j s (j < p); out = ||b||^2
 template <typename TV>
 __global__ void k_center_norm(TV *b, const double *__restrict__ mu, int64_t p, const double *s, double *out)
@@ -118,13 +127,17 @@ int power_method(cox_handle *h, const double *start, double tol, int maxiter, do
     const int64_t n = h->n, p = h->p;
     const bool f64 = h->opt.precision == COX_FP64;
     const int64_t alen = f64 ? n : h->n_pad, blen = f64 ? p : h->p_pad;
-    TV *v = nullptr, *a = nullptr, *b = nullptr;
+    TV *v = nullptr, *a = nullptr, *b = nullptr, *a4 = nullptr;
     double *sc = nullptr;
     int rc = COX_OK;
     if ((rc = dmalloc(nullptr, reinterpret_cast<void **>(&v), p * sizeof(TV))) != COX_OK) return rc;
     if ((rc = dmalloc(nullptr, reinterpret_cast<void **>(&a), alen * sizeof(TV))) != COX_OK) { dfree(v); return rc; }
     if ((rc = dmalloc(nullptr, reinterpret_cast<void **>(&b), blen * sizeof(TV))) != COX_OK) { dfree(v); dfree(a); return rc; }
     if ((rc = dmalloc(nullptr, reinterpret_cast<void **>(&sc), 4 * sizeof(double))) != COX_OK) { dfree(v); dfree(a); dfree(b); return rc; }
+    if (!f64 && (rc = dmalloc(nullptr, reinterpret_cast<void **>(&a4), alen * sizeof(TV))) != COX_OK) {
+        dfree(v); dfree(a); dfree(b); dfree(sc);
+        return rc;
+    }
     std::vector<TV> v0(static_cast<size_t>(p));
     double nv = 0.0;
     for (int64_t j = 0; j < p; ++j) nv += (start ? start[j] * start[j] : 1.0);
@@ -149,7 +162,9 @@ int power_method(cox_handle *h, const double *start, double tol, int maxiter, do
                                                                                      reinterpret_cast<const double *>(a),
                                                                                      reinterpret_cast<double *>(b));
             } else {
-                rc = gemv_tiles(h, h->d_A4, h->p_pad, h->n_pad / TILE, reinterpret_cast<const float *>(a), n,
+                k_to_a4<<<static_cast<unsigned>((alen + 255) / 256), 256, 0, st>>>(
+                    reinterpret_cast<const float *>(a), alen, h->kperm_a, h->kperm_nb, reinterpret_cast<float *>(a4));
+                rc = gemv_tiles(h, h->d_A4, h->p_pad, h->n_pad / TILE, reinterpret_cast<const float *>(a4), alen,
                                 reinterpret_cast<float *>(b), st);
                 if (rc != COX_OK) break;
             }
@@ -168,6 +183,7 @@ int power_method(cox_handle *h, const double *start, double tol, int maxiter, do
     dfree(a);
     dfree(b);
     dfree(sc);
+    dfree(a4);
     if (rc == COX_OK) *L_out = 2.0 * s / static_cast<double>(n);
     return rc;
 }
@@ -465,7 +481,8 @@ int power_method_noalloc(cox_handle *h, const double *start, double tol, int max
     const size_t off_a = up(p * sizeof(TV));
     const size_t off_b = off_a + up(alen * sizeof(TV));
     const size_t off_sc = off_b + up(blen * sizeof(TV));
-    const size_t off_st = off_sc + 256;
+    const size_t off_a4 = off_sc + 256;
+    const size_t off_st = off_a4 + (f64 ? 0 : up(alen * sizeof(TV)));
     const size_t need = off_st + (start ? up(p * sizeof(double)) : 0);
     if (need > NOALLOC_SCRATCH_BYTES) return COX_ERR_ARG;
     void *base = nullptr;
@@ -475,6 +492,7 @@ int power_method_noalloc(cox_handle *h, const double *start, double tol, int max
     TV *a = reinterpret_cast<TV *>(b8 + off_a);
     TV *b = reinterpret_cast<TV *>(b8 + off_b);
     double *sc = reinterpret_cast<double *>(b8 + off_sc);
+    TV *a4 = reinterpret_cast<TV *>(b8 + off_a4);
     double *st_dev = start ? reinterpret_cast<double *>(b8 + off_st) : nullptr;
     cudaStream_t st = 0;
     if (start) COX_CUDA(cudaMemcpyAsync(st_dev, start, p * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -496,7 +514,9 @@ int power_method_noalloc(cox_handle *h, const double *start, double tol, int max
             k_xta64<<<static_cast<unsigned>((p * 32 + 255) / 256), 256, 0, st>>>(
                 h->d_Xc, n, p, reinterpret_cast<const double *>(a), reinterpret_cast<double *>(b));
         } else {
-            rc = gemv_tiles(h, h->d_A4, h->p_pad, h->n_pad / TILE, reinterpret_cast<const float *>(a), n,
+            k_to_a4<<<static_cast<unsigned>((alen + 255) / 256), 256, 0, st>>>(
+                reinterpret_cast<const float *>(a), alen, h->kperm_a, h->kperm_nb, reinterpret_cast<float *>(a4));
+            rc = gemv_tiles(h, h->d_A4, h->p_pad, h->n_pad / TILE, reinterpret_cast<const float *>(a4), alen,
                             reinterpret_cast<float *>(b), st);
             if (rc != COX_OK) break;
         }

@@ -82,6 +82,7 @@ __device__ __forceinline__ double block_max(double x, double *sh)
 struct SP {
     int64_t n, n_pad;
     int nch, k;
+    int64_t pa, pnb;  // K order of the SNP-major genotype copy (a4_pos)
     const uint8_t *delta;
     const int32_t *head, *tail;
     double *eta, *w, *Rt, *Ft, *cmax, *csw, *csd, *suf, *pre, *lossp, *vsp;
@@ -237,6 +238,8 @@ __global__ void k_fwd(SP s, bool need_loss)
 }
 
 // (4) C = F at the tie tail; u = w C; V = delta - u -> output form; sum of V.
+// The limb and FP32 forms feed products over the SNP-major copy and are
+// written at its K positions (a4_pos); the FP64 form stays in sorted order.
 template <int VO>
 __global__ void k_uv(SP s, void *Vout, int64_t n_pad)
 {
@@ -251,19 +254,28 @@ __global__ void k_uv(SP s, void *Vout, int64_t n_pad)
         const double C = s.Ft[kk * s.n + tl] + s.pre[kk * s.nch + tl / SCAN_CH];
         const double u = s.w[kk * s.n + i] * C;
         const double V = static_cast<double>(s.delta[i]) - u;
-        vs += V;
+        const int64_t pos = a4_pos(i, s.pa, s.pnb);
+        // sum V in the form the product reads: X^T V - mu sum V is then
+        // exactly the centred product of that V.  (Censored subjects between
+        // two event times share one V, so their rounding errors do not
+        // cancel; with the exact sum, mu times their sum would remain.)
         if (VO == V_LIMBS_BF16) {
             const int tsl = (((i & 15) >> 1) % 3);
             const double Vs = ldexp(V, 69 - 2 * tsl);
             const __nv_bfloat16 hi = __float2bfloat16_rn(static_cast<float>(Vs));
-            const __nv_bfloat16 lo = __float2bfloat16_rn(static_cast<float>(Vs - static_cast<double>(__bfloat162float(hi))));
+            const double hd = static_cast<double>(__bfloat162float(hi));
+            const __nv_bfloat16 lo = __float2bfloat16_rn(static_cast<float>(Vs - hd));
             uint16_t *Vb = static_cast<uint16_t *>(Vout);
-            Vb[(2 * kk) * n_pad + i] = __bfloat16_as_ushort(hi);
-            Vb[(2 * kk + 1) * n_pad + i] = __bfloat16_as_ushort(lo);
+            Vb[(2 * kk) * n_pad + pos] = __bfloat16_as_ushort(hi);
+            Vb[(2 * kk + 1) * n_pad + pos] = __bfloat16_as_ushort(lo);
+            vs += ldexp(hd + static_cast<double>(__bfloat162float(lo)), 2 * tsl - 69);
         } else if (VO == V_DENSE_F64) {
             static_cast<double *>(Vout)[kk * s.n + i] = V;
+            vs += V;
         } else {
-            static_cast<float *>(Vout)[kk * s.n + i] = static_cast<float>(V);
+            const float v32 = static_cast<float>(V);
+            static_cast<float *>(Vout)[kk * n_pad + pos] = v32;
+            vs += static_cast<double>(v32);
         }
     }
     const double t = block_sum(vs, sh);
@@ -302,6 +314,8 @@ int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st)
     s.n_pad = h->n_pad;
     s.nch = h->n_chunks;
     s.k = a.k;
+    s.pa = h->kperm_a;
+    s.pnb = h->kperm_nb;
     s.delta = h->d_delta;
     s.head = h->d_head;
     s.tail = h->d_tail;

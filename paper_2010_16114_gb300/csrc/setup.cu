@@ -5,8 +5,9 @@
 // Subjects are put in ascending time order (stable), so the risk sets become
 // suffixes of the order.  Genotypes are stored twice as 2-bit codes in
 // 128 x 128 blocks of 4 KB: subject-major (A1: rows = sorted subjects,
-// K = SNPs, for X beta) and SNP-major (A4: rows = SNPs, K = sorted subjects,
-// for X^T V), each streamed once per iteration by its own product.
+// K = SNPs, for X beta) and SNP-major (A4: rows = SNPs, K = sorted subjects in
+// 16-subject blocks spread by a4_pos, for X^T V), each streamed once per
+// iteration by its own product.
 //
 // Block layout (both copies): row r of a block is 32 bytes = two 16-byte
 // halves (K 0-63 and 64-127 of the chunk); the halves of rows with bit 2 of r
@@ -62,10 +63,11 @@ __global__ void k_pack_a1(const uint8_t *__restrict__ in, int64_t rb, int64_t n,
     }
 }
 
-// A4: thread per (SNP j, 16 sorted subjects); column sums for mu.
+// A4: thread per (SNP j, 16 sorted subjects), stored at the block's K position
+// a4_pos; column sums for mu.
 __global__ void k_pack_a4(const uint8_t *__restrict__ in, int64_t rb, int64_t n, int64_t p,
                           const int32_t *__restrict__ order, uint32_t *__restrict__ A4, int64_t KC4,
-                          unsigned long long *__restrict__ colsum)
+                          int64_t pa, int64_t pnb, unsigned long long *__restrict__ colsum)
 {
     const int64_t R16 = (n + 15) / 16;
     const int64_t total = R16 * p;
@@ -84,7 +86,8 @@ __global__ void k_pack_a4(const uint8_t *__restrict__ in, int64_t rb, int64_t n,
                 s += c;
             }
         }
-        A4[word_offset(j / TILE, KC4, r0 / TILE, static_cast<int>(j % TILE), static_cast<int>(r0 % TILE))] = P;
+        const int64_t k0 = a4_pos(r0, pa, pnb);
+        A4[word_offset(j / TILE, KC4, k0 / TILE, static_cast<int>(j % TILE), static_cast<int>(k0 % TILE))] = P;
         if (s) atomicAdd(&colsum[j], static_cast<unsigned long long>(s));
     }
 }
@@ -177,7 +180,8 @@ int setup_genotypes(cox_handle *h, const void *X, int x_format, cudaStream_t st)
         k_pack_a1<<<grid_for(n * ((p + 15) / 16), h->sm_count), 256, 0, st>>>(d_in, rb, n, p, d_order, h->d_A1,
                                                                                 h->p_pad / TILE, h->d_err);
         k_pack_a4<<<grid_for(((n + 15) / 16) * p, h->sm_count), 256, 0, st>>>(d_in, rb, n, p, d_order, h->d_A4,
-                                                                                h->n_pad / TILE, d_colsum);
+                                                                                h->n_pad / TILE, h->kperm_a,
+                                                                                h->kperm_nb, d_colsum);
         if (cudaGetLastError() != cudaSuccess) {
             rc = COX_ERR_CUDA;
             break;
