@@ -18,17 +18,19 @@
 // B holds each coefficient column as two bf16 limbs, hi = RN(b), lo = RN(b-hi)
 // (columns 2c and 2c+1), so D[2c] + D[2c+1] carries ~16 significant bits of b.
 //
-// Pipeline per CTA (one per SM): a TMA warp fills a ring of shared-memory
-// stages (B chunk + T A blocks); eight decoder warps turn a stage into bf16 in
-// a ring of TMEM stage slots, issuing all of a stage's tcgen05.st before one
-// wait; one thread issues T x 8 MMAs per stage and commits.  The TMEM slot
-// ring lets decoding run several stages ahead of the MMAs, which hides the
-// MMA-to-commit round trip.
+// Pipeline per CTA (one per SM): two TMA warps fill a ring of shared-memory
+// stages (B chunk + T A blocks); groups of four decoder warps turn a stage into
+// bf16 in a ring of TMEM slots, issuing all of a stage's tcgen05.st before one
+// wait; issuer warps (a tile and every Q-th stage each) issue the stage's MMAs
+// into their own accumulators and commit.  Decoders hand a slot to the issuers
+// through a hardware named barrier (tens of cycles, against a few hundred for
+// an mbarrier arrive and wait), and every wait or commit serves a whole stage.
 //
 // FP32 accumulation in TMEM rounds with a bias, so each CTA accumulates at most
-// F K-chunks in TMEM (double-buffered), then the decoder warps fold the window
-// into FP32 registers (round-to-nearest); the fold of a window is deferred by a
-// few stages so it never stalls decoding.
+// F K-chunks in TMEM, then decoder group 0 adds the window's accumulators into
+// FP32 registers (round-to-nearest).  The K order of the X^T V product spreads
+// the time order (setup.cu), so these running sums stay near the size of the
+// result instead of drifting with the time trend of V.
 //
 // Work split: units = (M group, K chunk) pairs; CTA c takes the contiguous
 // range [c L, (c+1) L).  A group cut between CTAs gets one partial per CTA
@@ -45,7 +47,7 @@ namespace coxgb {
 namespace {
 
 struct KParams {
-    int KC, F, k, stages, ring, defer;
+    int KC, F, k, stages, ring, nb_period;
     int64_t units, L;
     int64_t rows_pad, slot_stride;
     float *part;
@@ -99,60 +101,70 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, long lo
     return __all_sync(0xffffffffu, mbar_wait(bar, parity, lim, abort));
 }
 
-// Warp roles (WARPS = 1 + I + 4 G):
-//   warp 0            TMA producer (lane 0); allocates TMEM
-//   warps 1 .. I      MMA issuers: issuer j owns row tile t = j / H and K part
-//                     h = j % H of every stage, accumulating into its own TMEM
-//                     accumulator (a single thread issues at most one MMA per
-//                     ~50 cycles, so I issuers keep the tensor pipe fed)
-//   warps I+1 ..      G decoder groups of four warps (one per TMEM lane
-//                     quarter); group gamma decodes stages i = gamma (mod G), so
-//                     the latency of one stage's waits and stores overlaps with
-//                     the other groups' work.  Group 0 also folds the
-//                     accumulators into registers at window ends and runs the
-//                     epilogue.
-template <int T, int H, int NP, int G>
-__global__ void __launch_bounds__(32 * (1 + T * H + 4 * G), 1)
+// Warp roles (WARPS = 2 + I + 4 G, I = T Q):
+//   warps 0, 1     TMA producers (lane 0): warp w loads the stages i = w (mod 2);
+//                  warp 0 also allocates TMEM
+//   warps 2..I+1   MMA issuers: issuer j owns row tile t = j / Q and the stages
+//                  i = c (mod Q), c = j % Q, and accumulates them into its own
+//                  TMEM accumulator.  One thread issues at most one MMA per ~50
+//                  cycles and each barrier wait or commit costs it a few hundred,
+//                  so an issuer takes whole stages: 8 MMAs per wait and commit.
+//   warps I+2..    G decoder groups of four warps (one per TMEM lane quarter);
+//                  group gamma decodes the stages i = gamma (mod G) into TMEM
+//                  slot i mod R.  Group 0 also adds the accumulators up at window
+//                  ends and runs the epilogue.
+// Hand-offs of stage i (shared-memory slot s = i mod S, TMEM slot r = i mod R):
+//   full[s]        mbarrier, TMA transaction bytes           producer -> decoders
+//   named 1+i%PB   hardware barrier: A slot written          decoders -> T issuers
+//   aempty[r]      tcgen05.commit of the T issuers           -> decoders of stage i+R
+//   empty[s]       one arrival by the decoders of stage i+R once they have seen
+//                  aempty for stage i (its MMAs, which read B and follow the
+//                  decoders' reads of X, are complete)       -> producer
+// PB = lcm(G, Q, R): each use of a named barrier has the same warps, and the
+// decoders of stage i+PB cannot arrive before the issuers of stage i have
+// passed it (they first wait, through the TMEM slot chain, for MMAs that those
+// issuers issue after it).  Decoders arrive on every path, so an issuer's
+// (unbounded) hardware-barrier wait always ends.
+template <int T, int Q, int NP, int G>
+__global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
     k_packed_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const KParams P)
 {
-    constexpr int I = T * H;              // MMA issuers
-    constexpr int QH = 8 / H;             // K16 MMAs per issuer per stage
+    constexpr int I = T * Q;              // MMA issuers
     constexpr int KH = NP / 2;            // lambda columns a decoder thread folds (NP/2 >= k)
     constexpr int B_BYTES = NP * 256;
     constexpr int X_BYTES = T * BLOCK_BYTES;
     constexpr int STAGE = B_BYTES + X_BYTES;
-    constexpr int ACC_COLS = I * NP;      // single-buffered accumulators
+    constexpr int ACC_COLS = I * NP;      // one accumulator per issuer
     constexpr int SLOT_COLS = T * 64;
-    constexpr int DEC0 = 1 + I;           // first decoder warp
+    constexpr int DEC0 = 2 + I;           // first decoder warp
+    constexpr int NB_COUNT = 32 * (4 + T);  // a decoder group and the stage's T issuer warps
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                 ~static_cast<uintptr_t>(1023));
-    const int S = P.stages, R = P.ring;
+    const int S = P.stages, R = P.ring, PB = P.nb_period;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S * STAGE);
     const uint32_t full0 = smem_addr(bars);
     const uint32_t empty0 = full0 + 8 * S;
-    const uint32_t afull0 = empty0 + 8 * S;
-    const uint32_t aempty0 = afull0 + 8 * R;
+    const uint32_t aempty0 = empty0 + 8 * S;
     const uint32_t accf = aempty0 + 8 * R;
     const uint32_t acce = accf + 8;
     const uint32_t drainb = acce + 8;
     const uint32_t epib = drainb + 8;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 2 * R + 4);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + R + 4);
     volatile int *abort_sm = reinterpret_cast<volatile int *>(tmem_slot + 1);
     volatile int *last_sm = reinterpret_cast<volatile int *>(tmem_slot + 2);
+    volatile int *armed = reinterpret_cast<volatile int *>(tmem_slot + 4);  // [S] parity of the last TMA into a slot
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, I);
+            mbar_init(empty0 + 8 * s, 1);
+            armed[s] = -1;
         }
-        for (int r = 0; r < R; ++r) {
-            mbar_init(afull0 + 8 * r, 4);
-            mbar_init(aempty0 + 8 * r, I);
-        }
+        for (int r = 0; r < R; ++r) mbar_init(aempty0 + 8 * r, T);
         mbar_init(accf, I);
         mbar_init(acce, 4);
         mbar_init(drainb, I);
@@ -165,7 +177,7 @@ __global__ void __launch_bounds__(32 * (1 + T * H + 4 * G), 1)
         tmem_alloc(smem_addr(tmem_slot), 512);
         tmem_relinquish();
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 32) {
         tma_prefetch_desc(&tmA);
         tma_prefetch_desc(&tmB);
     }
@@ -184,97 +196,93 @@ __global__ void __launch_bounds__(32 * (1 + T * H + 4 * G), 1)
     // increments only (no division on the per-stage path)
     const int g0 = static_cast<int>(u0 / KC), kc0 = static_cast<int>(u0 - static_cast<int64_t>(g0) * KC);
 
-    if (warp == 0) {
-        // ---------------- TMA producer ----------------
+    if (warp < 2) {
+        // ---------------- TMA producers ----------------
         if (lane == 0) {
-            int s = 0, kc = kc0, g = g0;
+            const int w = warp;
+            int s = w, kc = kc0 + w, g = g0;
+            if (kc >= KC) {
+                kc -= KC;
+                ++g;
+            }
             uint32_t ph = 0;
-            int64_t issued = 0;
-            for (int64_t i = 0; i < nu; ++i) {
+            for (int64_t i = w; i < nu; i += 2) {
                 if (i >= S && !mbar_wait(empty0 + 8 * s, ph ^ 1u, lim, abort_sm)) {
                     fail(abort_sm, P.err);
                     break;
                 }
                 const uint32_t st = smem_addr(smem + s * STAGE);
                 const uint32_t fb = full0 + 8 * s;
+                armed[s] = static_cast<int>(ph);
                 mbar_arrive_expect_tx(fb, STAGE);
                 tma_load_2d(st, &tmB, kc * TILE, 0, fb);
                 tma_load_2d(st + NP * 128, &tmB, kc * TILE + 64, 0, fb);
                 tma_load_4d(st + B_BYTES, &tmA, 0, 0, kc, g * T, fb);
-                issued = i + 1;
-                if (++s == S) {
-                    s = 0;
+                s += 2;
+                if (s >= S) {
+                    s -= S;
                     ph ^= 1u;
                 }
-                if (++kc == KC) {
-                    kc = 0;
+                kc += 2;
+                if (kc >= KC) {
+                    kc -= KC;
                     ++g;
                 }
             }
-            // never leave a copy in flight into shared memory we are about to give up
-            const int64_t from = issued > S ? issued - S : 0;
-            int sd = static_cast<int>(from % S);
-            uint32_t pd = static_cast<uint32_t>((from / S) & 1);
-            for (int64_t i = from; i < issued; ++i) {
-                mbar_wait(full0 + 8 * sd, pd, DRAIN_LIMIT, &g_never_set);
-                if (++sd == S) {
-                    sd = 0;
-                    pd ^= 1u;
-                }
-            }
         }
-    } else if (warp <= I) {
-        // ---------------- MMA issuers ----------------
-        if (lane == 0) {
-            const int j = warp - 1;
-            const int t = j / H, h = j % H;
-            constexpr uint32_t idesc = idesc_bf16_f32(128, NP);
-            const uint32_t d = tbase + static_cast<uint32_t>(j * NP);
-            int s = 0, r = 0, kc = kc0, wlen = 0;
-            uint32_t aph = 0, eph = 0;
-            int64_t wi = -1;
-            bool ok = true;
-            const uint64_t desc0 = smem_desc_sw128(smem_addr(smem));
-            for (int64_t i = 0; i < nu; ++i) {
-                const bool first = (i == 0) || (kc == 0) || (wlen == F);
-                if (first) {
-                    ++wi;
-                    wlen = 0;
-                    // the accumulator is reused: wait until group 0 has folded the previous window
-                    if (wi >= 1) {
-                        if (!mbar_wait(acce, eph, lim, abort_sm)) {
-                            ok = false;
-                            break;
-                        }
-                        eph ^= 1u;
+    } else if (warp < DEC0) {
+        // ---------------- MMA issuers (whole warp; lane 0 issues) ----------------
+        const int j = warp - 2;
+        const int t = j / Q, c = j % Q;
+        constexpr uint32_t idesc = idesc_bf16_f32(128, NP);
+        const uint32_t d = tbase + static_cast<uint32_t>(j * NP);
+        const uint64_t desc0 = smem_desc_sw128(smem_addr(smem));
+        int s = 0, r = 0, kc = kc0, wlen = 0, own = 0, nbid = 0;
+        uint32_t eph = 0;
+        int64_t wi = -1;
+        bool ok = true, firstown = true;
+        for (int64_t i = 0; i < nu; ++i) {
+            if (i == 0 || kc == 0 || wlen == F) {
+                // window start: the accumulator is reused once group 0 has added
+                // up the previous window
+                ++wi;
+                wlen = 0;
+                firstown = true;
+                if (wi >= 1) {
+                    if (ok && !warp_wait(acce, eph, lim, abort_sm)) {
+                        ok = false;
+                        if (lane == 0) fail(abort_sm, P.err);
                     }
+                    eph ^= 1u;
                 }
-                ++wlen;
-                const bool last = (i == nu - 1) || (kc == KC - 1) || (wlen == F);
-                if (!mbar_wait(afull0 + 8 * r, aph, lim, abort_sm)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint64_t dstage = desc0 + static_cast<uint64_t>((s * STAGE) >> 4);
-                const uint32_t a = tbase + static_cast<uint32_t>(ACC_COLS + r * SLOT_COLS + t * 64);
-#pragma unroll
-                for (int qq = 0; qq < QH; ++qq) {
-                    const int q = h * QH + qq;
-                    const uint64_t bd = dstage + static_cast<uint64_t>(((q >> 2) * NP * 128 + (q & 3) * 32) >> 4);
-                    mma_ts(d, a + 8 * q, bd, idesc, (first && qq == 0) ? 0u : 1u);
-                }
-                mma_commit(aempty0 + 8 * r);
-                mma_commit(empty0 + 8 * s);
-                if (last) mma_commit(accf);
-                if (++s == S) s = 0;
-                if (++r == R) {
-                    r = 0;
-                    aph ^= 1u;
-                }
-                if (++kc == KC) kc = 0;
             }
-            if (!ok) fail(abort_sm, P.err);
+            ++wlen;
+            const bool last = (i == nu - 1) || (kc == KC - 1) || (wlen == F);
+            if (own == c) {
+                __syncwarp();
+                named_sync(1 + nbid, NB_COUNT);
+                if (ok && lane == 0) {
+                    tc_fence_after();
+                    const uint64_t dstage = desc0 + static_cast<uint64_t>((s * STAGE) >> 4);
+                    const uint32_t a = tbase + static_cast<uint32_t>(ACC_COLS + r * SLOT_COLS + t * 64);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const uint64_t bd = dstage + static_cast<uint64_t>(((q >> 2) * NP * 128 + (q & 3) * 32) >> 4);
+                        mma_ts(d, a + 8 * q, bd, idesc, (firstown && q == 0) ? 0u : 1u);
+                    }
+                    mma_commit(aempty0 + 8 * r);
+                }
+                firstown = false;
+            }
+            if (last && ok && lane == 0) mma_commit(accf);
+            if (++s == S) s = 0;
+            if (++r == R) r = 0;
+            if (++kc == KC) kc = 0;
+            if (++own == Q) own = 0;
+            if (++nbid == PB) nbid = 0;
+        }
+        __syncwarp();
+        if (lane == 0) {
             mma_commit(drainb);
             mbar_wait(drainb, 0, DRAIN_LIMIT, &g_never_set);
         }
@@ -286,17 +294,20 @@ __global__ void __launch_bounds__(32 * (1 + T * H + 4 * G), 1)
         const int rit = 32 * q + lane;    // row inside a 128-row tile
         const int swp = (rit >> 2) & 1;   // row halves stored swapped
         const uint32_t lane_base = tbase + (static_cast<uint32_t>(32 * q) << 16);
-        float acc[T][KH];
-#pragma unroll
-        for (int t = 0; t < T; ++t)
-#pragma unroll
-            for (int e = 0; e < KH; ++e) acc[t][e] = 0.f;
+        // group 0's running sums of the windows, in shared memory ([column][thread]):
+        // registers are the scarce resource of the decoders
+        float *accs = reinterpret_cast<float *>(smem + S * STAGE + 1024) + (threadIdx.x - 32 * DEC0);
+        auto acc = [&](int tt, int e) -> float & { return accs[(tt * KH + e) * 128]; };
+        if (gamma == 0)
+            for (int e = 0; e < T * KH; ++e) accs[e * 128] = 0.f;
         uint32_t epi_phase = 0, fold_phase = 0;
         bool ok = true;
 
-        // group 0: fold the finished window into registers; at a segment end write
-        // this CTA's partial of group g and, for the last CTA, apply the epilogue
-        auto fold = [&](bool segend, int g) {
+        // group 0: add the finished window's accumulators into registers; at a
+        // segment end write this CTA's partial of group g and, for the last
+        // CTA, apply the epilogue.  Accumulator (t, c) holds the window's
+        // stages i = c (mod Q); one the window did not reach is skipped.
+        auto fold = [&](bool segend, int g, int64_t wst, int wl) {
             if (!ok) return;
             if (!warp_wait(accf, fold_phase, lim, abort_sm)) {
                 ok = false;
@@ -305,17 +316,19 @@ __global__ void __launch_bounds__(32 * (1 + T * H + 4 * G), 1)
             fold_phase ^= 1u;
             tc_fence_after();
 #pragma unroll
-            for (int t = 0; t < T; ++t) {
+            for (int cq = 0; cq < Q; ++cq) {
+                const int m = (cq - static_cast<int>(wst % Q) + Q) % Q;
+                if (m >= wl) continue;
 #pragma unroll
-                for (int hh = 0; hh < H; ++hh) {
+                for (int tt = 0; tt < T; ++tt) {
 #pragma unroll
                     for (int cc = 0; cc < NP / 8; ++cc) {
                         uint32_t v[8];
-                        tmem_ld_32x32b_x8(lane_base + static_cast<uint32_t>((t * H + hh) * NP + cc * 8), v);
+                        tmem_ld_32x32b_x8(lane_base + static_cast<uint32_t>((tt * Q + cq) * NP + cc * 8), v);
                         tmem_wait_ld();
 #pragma unroll
                         for (int e = 0; e < 4; ++e)
-                            acc[t][cc * 4 + e] += __uint_as_float(v[2 * e]) + __uint_as_float(v[2 * e + 1]);
+                            acc(tt, cc * 4 + e) += __uint_as_float(v[2 * e]) + __uint_as_float(v[2 * e + 1]);
                     }
                 }
             }
@@ -327,16 +340,15 @@ __global__ void __launch_bounds__(32 * (1 + T * H + 4 * G), 1)
             const int64_t first_cta = (static_cast<int64_t>(g) * KC) / P.L;
             const int64_t slot = cta - first_cta;
 #pragma unroll
-            for (int t = 0; t < T; ++t) {
-                const int64_t row = (static_cast<int64_t>(g) * T + t) * TILE + rit;
+            for (int tt = 0; tt < T; ++tt) {
+                const int64_t row = (static_cast<int64_t>(g) * T + tt) * TILE + rit;
 #pragma unroll
                 for (int e = 0; e < KH; ++e) {
-                    if (e < P.k) P.part[slot * P.slot_stride + e * P.rows_pad + row] = acc[t][e] * 0x1.0p64f;
-                    acc[t][e] = 0.f;
+                    if (e < P.k) P.part[slot * P.slot_stride + e * P.rows_pad + row] = acc(tt, e) * 0x1.0p64f;
+                    acc(tt, e) = 0.f;
                 }
             }
             if (P.epi == EPI_PARTIAL) return;
-
             // the last CTA of the group applies the step (Section 5.3: beta <- S(beta + sigma g, sigma lambda))
             __threadfence();
             __syncwarp();
@@ -384,25 +396,19 @@ __global__ void __launch_bounds__(32 * (1 + T * H + 4 * G), 1)
             }
         };
 
-        // group 0 tracks windows of every stage (it owes the folds); all groups
-        // advance their stage counters by G per iteration
-        int s = gamma % S, r = gamma % R;
-        uint32_t fph = static_cast<uint32_t>((gamma / S) & 1), aph = static_cast<uint32_t>((gamma / R) & 1);
-        int kc = kc0 + gamma, g = g0;
-        while (kc >= KC) {
-            kc -= KC;
-            ++g;
-        }
         // window bookkeeping (group 0): walk every stage in order and fold each
         // window as soon as its last stage lies behind the stage being decoded
         int wkc = kc0, wg = g0, wlen = 0;
-        int64_t wnext = 0;
+        int64_t wnext = 0, wst = 0;
         auto fold_until = [&](int64_t upto) {  // stages [wnext, upto)
             for (; wnext < upto && wnext < nu && ok; ++wnext) {
-                if (wnext == 0 || wkc == 0 || wlen == F) wlen = 0;
+                if (wnext == 0 || wkc == 0 || wlen == F) {
+                    wlen = 0;
+                    wst = wnext;
+                }
                 ++wlen;
                 const bool seg = (wnext == nu - 1) || (wkc == KC - 1);
-                if (seg || wlen == F) fold(seg, wg);
+                if (seg || wlen == F) fold(seg, wg, wst, wlen);
                 if (++wkc == KC) {
                     wkc = 0;
                     ++wg;
@@ -410,38 +416,50 @@ __global__ void __launch_bounds__(32 * (1 + T * H + 4 * G), 1)
             }
         };
 
-        for (int64_t i = gamma; i < nu && ok; i += G) {
-            if (gamma == 0) {
+        int s = gamma % S, r = gamma % R, nbid = gamma % PB;
+        uint32_t fph = static_cast<uint32_t>((gamma / S) & 1), aph = static_cast<uint32_t>((gamma / R) & 1);
+        for (int64_t i = gamma; i < nu; i += G) {
+            bool go = ok;
+            if (go && gamma == 0) {
                 // windows ending before stage i: every stage of theirs is decoded
                 // or owned by another group, so their MMAs complete without us
                 fold_until(i);
-                if (!ok) break;
+                go = ok;
             }
-            if (!warp_wait(full0 + 8 * s, fph, lim, abort_sm) ||
-                (i >= R && !warp_wait(aempty0 + 8 * r, aph ^ 1u, lim, abort_sm))) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            const uint8_t *xs = smem + s * STAGE + B_BYTES + rit * 32;
-            const uint32_t acol = lane_base + static_cast<uint32_t>(ACC_COLS + r * SLOT_COLS);
-#pragma unroll
-            for (int t = 0; t < T; ++t) {
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(xs + t * BLOCK_BYTES + 16 * (hh ^ swp));
-                    uint32_t o[32];
-                    decode16(v.x, o);
-                    decode16(v.y, o + 8);
-                    decode16(v.z, o + 16);
-                    decode16(v.w, o + 24);
-                    tmem_st_32x32b_x32(acol + t * 64 + 32 * hh, o);
+            if (go && !warp_wait(full0 + 8 * s, fph, lim, abort_sm)) go = false;
+            // TMEM slot r is free once the MMAs of stage i - R are complete
+            if (go && i >= R && !warp_wait(aempty0 + 8 * r, aph ^ 1u, lim, abort_sm)) go = false;
+            if (go) {
+                if (i >= R && q == (DEC0 & 3) && lane == 0) {
+                    int se = s - R;
+                    if (se < 0) se += S;
+                    mbar_arrive(empty0 + 8 * se);
                 }
+                tc_fence_after();
+                const uint8_t *xs = smem + s * STAGE + B_BYTES + rit * 32;
+                const uint32_t acol = lane_base + static_cast<uint32_t>(ACC_COLS + r * SLOT_COLS);
+#pragma unroll
+                for (int tt = 0; tt < T; ++tt) {
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const uint4 v = *reinterpret_cast<const uint4 *>(xs + tt * BLOCK_BYTES + 16 * (hh ^ swp));
+                        uint32_t o[32];
+                        decode16(v.x, o);
+                        decode16(v.y, o + 8);
+                        decode16(v.z, o + 16);
+                        decode16(v.w, o + 24);
+                        tmem_st_32x32b_x32(acol + tt * 64 + 32 * hh, o);
+                    }
+                }
+                tmem_wait_st();
             }
-            tmem_wait_st();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(afull0 + 8 * r);
+            named_arrive(1 + nbid, NB_COUNT);
+            if (!go && ok) {
+                ok = false;
+                if (lane == 0) fail(abort_sm, P.err);
+            }
             s += G;
             if (s >= S) {
                 s -= S;
@@ -452,19 +470,22 @@ __global__ void __launch_bounds__(32 * (1 + T * H + 4 * G), 1)
                 r -= R;
                 aph ^= 1u;
             }
-            kc += G;
-            while (kc >= KC) {
-                kc -= KC;
-                ++g;
-            }
+            nbid += G;
+            if (nbid >= PB) nbid -= PB;
         }
         if (gamma == 0 && ok) fold_until(nu);
-        if (!ok) fail(abort_sm, P.err);
+        if (!ok && lane == 0) fail(abort_sm, P.err);
     }
 
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
+        // never leave a copy in flight into shared memory we are about to give
+        // up (after an abort, stages may have been loaded that nobody waited for)
+        if (lane == 0)
+            for (int s = 0; s < S; ++s)
+                if (armed[s] >= 0) mbar_wait(full0 + 8 * s, static_cast<uint32_t>(armed[s]), DRAIN_LIMIT, &g_never_set);
+        __syncwarp();
         tc_fence_after();
         tmem_dealloc(tbase, 512);
     }
@@ -508,26 +529,32 @@ using KernelFn = void (*)(const CUtensorMap, const CUtensorMap, const KParams);
 
 constexpr int DEC_GROUPS = 3;
 
-// (T row tiles, H K parts per stage) for a limb-column class NP
-void shape_for(int NP, int *T, int *H)
+// (T row tiles per stage, Q issuers per tile) for a limb-column class NP.
+// Up to N = 32 an MMA is issue-bound (~50 cycles per instruction from one
+// thread), so two issuers per tile take alternate stages; from N = 64 on the
+// tensor pipe itself is the bound and one issuer per tile keeps up.
+void shape_for(int NP, int *T, int *Q)
 {
-    if (NP <= 32) { *T = 2; *H = 2; }
-    else if (NP == 64) { *T = 2; *H = 1; }
-    else { *T = 1; *H = 2; }
+    if (NP <= 32) { *T = 2; *Q = 2; }
+    else if (NP == 64) { *T = 2; *Q = 1; }
+    else { *T = 1; *Q = 1; }
 }
 
-KernelFn pick_kernel(int T, int H, int NP)
+KernelFn pick_kernel(int T, int Q, int NP)
 {
-    switch ((T * 10 + H) * 1000 + NP) {
+    switch ((T * 10 + Q) * 1000 + NP) {
     case 22016: return k_packed_gemm<2, 2, 16, DEC_GROUPS>;
     case 22032: return k_packed_gemm<2, 2, 32, DEC_GROUPS>;
     case 21064: return k_packed_gemm<2, 1, 64, DEC_GROUPS>;
-    case 12128: return k_packed_gemm<1, 2, 128, DEC_GROUPS>;
+    case 11128: return k_packed_gemm<1, 1, 128, DEC_GROUPS>;
     default: return nullptr;
     }
 }
 
-int threads_for(int T, int H) { return 32 * (1 + T * H + 4 * DEC_GROUPS); }
+int threads_for(int T, int Q) { return 32 * (2 + T * Q + 4 * DEC_GROUPS); }
+
+int gcd_i(int a, int b) { return b ? gcd_i(b, a % b) : a; }
+int lcm_i(int a, int b) { return a / gcd_i(a, b) * b; }
 
 } // namespace
 
@@ -541,26 +568,32 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
     const int np_cls = NP <= 16 ? 16 : NP <= 32 ? 32 : NP <= 64 ? 64 : 128;
     const int64_t m_tiles = rows_pad / TILE;
     (void)T_req;  // the row-tile count follows from the limb-column class
-    int T = 2, H = 2;
-    shape_for(np_cls, &T, &H);
+    int T = 2, Q = 2;
+    shape_for(np_cls, &T, &Q);
     if (m_tiles % T != 0) return COX_ERR_ARG;
-    int ring = (512 - T * H * np_cls) / (T * 64);
+    const int stage = np_cls * 256 + T * BLOCK_BYTES;
+    const int fold_bytes = T * (np_cls / 2) * 128 * 4;  // group 0's window sums
+    int S = stages_req > 0 ? stages_req : (225 * 1024 - 2048 - fold_bytes) / stage;
+    if (S > 12) S = 12;
+    if (S < DEC_GROUPS + 1) S = DEC_GROUPS + 1;  // decoder groups step through the stage ring by DEC_GROUPS
+    // TMEM: T Q accumulators of NP columns, the rest A slots of T x 64 columns;
+    // a slot's previous stage must still be in shared memory (ring <= S), and
+    // the named-barrier period lcm(G, Q, ring) must fit barriers 1..15
+    int ring = (512 - T * Q * np_cls) / (T * 64);
     if (ring > 8) ring = 8;
+    if (ring > S) ring = S;
+    while (ring >= 2 && lcm_i(lcm_i(DEC_GROUPS, Q), ring) > 15) --ring;
     if (ring < 2) return COX_ERR_ARG;
-    g.H = H;
+    g.H = Q;
     g.T = T;
     g.NP = np_cls;
     g.ring = ring;
-    const int stage = np_cls * 256 + T * BLOCK_BYTES;
-    int S = stages_req > 0 ? stages_req : (225 * 1024 - 2048) / stage;
-    if (S > 12) S = 12;
-    if (S < DEC_GROUPS + 1) S = DEC_GROUPS + 1;  // decoder groups step through the stage ring by DEC_GROUPS
+    g.nb_period = lcm_i(lcm_i(DEC_GROUPS, Q), ring);
     g.stages = S;
-    g.smem = static_cast<size_t>(S) * stage + 1024 + 1024;
+    g.smem = static_cast<size_t>(S) * stage + 1024 + 1024 + fold_bytes;
     if (g.smem < 120 * 1024) g.smem = 120 * 1024;  // one CTA per SM: it owns all 512 TMEM columns
     if (g.smem > 227 * 1024) return COX_ERR_ARG;    // too many stages requested
     g.F = 64;  // K chunks per accumulation window: 64 x 8 / H MMAs into one accumulator
-    g.defer = 0;
     g.KC = static_cast<int>(K_pad / TILE);
     g.n_groups = static_cast<int>(m_tiles / T);
     g.units = static_cast<int64_t>(g.n_groups) * g.KC;
@@ -615,7 +648,7 @@ int launch_gemm(cox_handle *h, const GemmPlan &g, const EpiArgs &e, int k, cudaS
     kp.k = k;
     kp.stages = g.stages;
     kp.ring = g.ring;
-    kp.defer = g.defer;
+    kp.nb_period = g.nb_period;
     kp.units = g.units;
     kp.L = g.L;
     kp.rows_pad = g.rows_pad;

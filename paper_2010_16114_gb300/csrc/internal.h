@@ -34,12 +34,12 @@ __host__ __device__ inline int64_t a4_pos(int64_t i, int64_t a, int64_t nb)
 // One tensor-core product: a 2-bit A (rows x K, tiled) times limb matrix B.
 struct GemmPlan {
     int T = 2;         // 128-row tiles per CTA (one M group)
-    int H = 2;         // K parts per stage, one MMA-issuing warp per (tile, part)
+    int H = 2;         // MMA-issuing warps per tile (each takes every H-th stage)
     int NP = 16;       // limb columns (2k rounded up to 16)
     int stages = 6;    // shared-memory pipeline depth
     int ring = 4;      // TMEM A buffers
+    int nb_period = 6; // named barriers in use: lcm(decoder groups, H, ring)
     int F = 32;        // K chunks per TMEM accumulation window
-    int defer = 3;     // stages between a window's end and its fold into registers
     int grid = 0;      // CTAs
     int KC = 0;        // K chunks
     int n_groups = 0;  // M groups

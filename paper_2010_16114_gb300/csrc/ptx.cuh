@@ -48,18 +48,51 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
+// Non-blocking probe of the same condition.
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}\n"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
 // Wait for the phase with the given parity to complete, for at most `limit`
 // clock cycles, or until *abort becomes non-zero.  Returns false on either.
+// The first probe does not block and the limit is checked before every
+// (briefly suspending) try_wait, so with limit 0 any wait that is not already
+// satisfied gives up.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit,
                                           volatile int *abort)
 {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_test_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
         if (*abort) return false;
         if (clock64() - t0 > limit) return false;
+        if (mbar_try_wait(bar, parity)) return true;
     }
+}
+
+// ---- named (hardware) barriers ------------------------------------------------
+// `count` threads (a multiple of 32, whole warps) take part in one use of
+// barrier `id` (1..15; 0 is __syncthreads).  Warp-collective: every lane of a
+// warp executes the same instruction.  Arrive does not wait; sync waits until
+// the count is reached.  These waits cannot time out, so a caller must make
+// sure that every arrival a sync depends on is made on every path.
+
+__device__ __forceinline__ void named_arrive(int id, int count)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void named_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 // ---- TMA (bulk tensor copies, global -> shared) ------------------------------
