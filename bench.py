@@ -243,7 +243,7 @@ def run_ours(args, rank, world):
     packed = torch.empty((n, (p + 3) // 4), dtype=torch.uint8, device="cuda")
     w.packed_rows_device(packed.data_ptr(), stream.cuda_stream, thr.data_ptr())
     torch.cuda.synchronize()
-    prob = CoxProblem(packed, w.y, w.delta, p=p, precision="split_bf16", tile_m=args.tile_m, stages=args.stages)
+    prob = CoxProblem(packed, w.y, w.delta, p=p, precision="split_e4m3", tile_m=args.tile_m, stages=args.stages)
     del packed, thr
     torch.cuda.empty_cache()
     lmax = prob.lambda_max()
@@ -334,7 +334,7 @@ def run_ours(args, rank, world):
                 "lambda_iters_per_s": k * 1e3 / gms, "speedup_of_batched": (1e3 / ms_step) / (1e3 / gms),
                 "hbm_gbs": 2 * k * xb / (gms / 1e3) / 1e9,
                 "rel_l2_vs_batched_one_step": diff}
-        prob.set_precision("split_bf16")
+        prob.set_precision("split_e4m3")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -70,15 +70,17 @@ enum {
 
 /* Arithmetic of the two products X_c B and X_c^T V. */
 enum {
-    COX_SPLIT_BF16 = 0, /* tcgen05 tensor cores, coefficients split hi+lo bf16,
-                           FP32 accumulation; FP64 risk-set scans (default)   */
+    COX_SPLIT_E4M3 = 0, /* tcgen05 tensor cores (kind::f8f6f4): genotype codes as
+                           e4m3, coefficients split into 4 e4m3 limbs under a
+                           power-of-two column scale, FP32 accumulation; FP64
+                           risk-set scans (default)                            */
     COX_FP64 = 1,       /* FP64 everywhere, dense X (COX_X_F64_HOST)          */
     COX_FP32_GEMV = 2   /* baseline: one lambda at a time, FP32 CUDA-core GEMV
                            on the packed genotypes, unfused soft threshold    */
 };
 
 typedef struct cox_options {
-    int precision;        /* COX_SPLIT_BF16 (default), COX_FP64, COX_FP32_GEMV       */
+    int precision;        /* COX_SPLIT_E4M3 (default), COX_FP64, COX_FP32_GEMV       */
     int center;           /* 1: X_c = X - 1 mu^T (default 1; COX_FP64 default 0)    */
     int device;           /* CUDA device ordinal (default: current device)           */
     int tile_m;           /* 128-row tiles per CTA in the tensor-core products;
@@ -214,7 +216,7 @@ typedef struct cox_info {
 } cox_info;
 int cox_get_info(cox_h h, cox_info *info);
 
-/* Switch a genotype handle between COX_SPLIT_BF16 and COX_FP32_GEMV; both
+/* Switch a genotype handle between COX_SPLIT_E4M3 and COX_FP32_GEMV; both
  * read the same resident tiles.  Drops the per-k workspace.  Errors:
  * COX_ERR_UNSUPPORTED for COX_FP64 handles or targets. */
 int cox_set_precision(cox_h h, int precision);

@@ -26,7 +26,7 @@ COX_X_F64_HOST = 1
 COX_X_PACKED2_HOST = 2
 COX_X_PACKED2_DEV = 3
 
-COX_SPLIT_BF16 = 0
+COX_SPLIT_E4M3 = 0
 COX_FP64 = 1
 COX_FP32_GEMV = 2
 

@@ -13,7 +13,7 @@ import torch
 
 from . import _lib as L
 
-PRECISIONS = {"split_bf16": L.COX_SPLIT_BF16, "fp64": L.COX_FP64, "fp32_gemv": L.COX_FP32_GEMV}
+PRECISIONS = {"split_e4m3": L.COX_SPLIT_E4M3, "fp64": L.COX_FP64, "fp32_gemv": L.COX_FP32_GEMV}
 
 
 def _vp(x):
@@ -43,7 +43,7 @@ class CoxProblem:
       * a uint8 array/tensor of row-major 2-bit codes, shape (n, ceil(p/4)),
         on the host or on the device, with ``p`` given."""
 
-    def __init__(self, X, time, event, precision: str = "split_bf16", center: bool | None = None,
+    def __init__(self, X, time, event, precision: str = "split_e4m3", center: bool | None = None,
                  p: int | None = None, device: int | None = None, tile_m: int = 0, stages: int = 0,
                  lag: int = 10, wait_limit_s: float = 2.0):
         lib = L.load()
@@ -115,7 +115,7 @@ class CoxProblem:
         return mu, order
 
     def set_precision(self, precision: str):
-        """Switch between "split_bf16" and "fp32_gemv" on the same resident data."""
+        """Switch between "split_e4m3" and "fp32_gemv" on the same resident data."""
         L.check(L.cox_set_precision(self.h, PRECISIONS[precision]), "cox_set_precision")
         self.precision = precision
 

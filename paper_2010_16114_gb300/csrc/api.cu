@@ -55,8 +55,8 @@ void free_workspace(cox_handle *h)
 {
     Workspace &w = h->ws;
     void *ptrs[] = {w.eta, w.w, w.Rt, w.Ft, w.cmax, w.csw, w.csd, w.suf, w.pre, w.lossp, w.vsp, w.l1p,
-                    w.sumV, w.f, w.F, w.l1, w.lam, w.active, w.Fring, w.Bb, w.Vb, w.part1, w.part4,
-                    w.cnt4, w.V64, w.V32, w.eta32, w.G32};
+                    w.sumV, w.f, w.F, w.l1, w.lam, w.active, w.Fring, w.Bq, w.Vq, w.bs1, w.bs4, w.bmaxp,
+                    w.vmaxp, w.part1, w.part4, w.cnt4, w.V64, w.V32, w.eta32, w.G32};
     for (void *p : ptrs) dfree(p);
     const GemmPlan g1 = w.g1, g4 = w.g4;
     (void)g1;
@@ -94,7 +94,7 @@ struct DeviceGuard {
     }
 };
 
-bool is_split(const cox_handle *h) { return h->opt.precision == COX_SPLIT_BF16; }
+bool is_split(const cox_handle *h) { return h->opt.precision == COX_SPLIT_E4M3; }
 bool is_fp64(const cox_handle *h) { return h->opt.precision == COX_FP64; }
 
 cudaEvent_t get_event(cox_handle *h)
@@ -139,12 +139,13 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
         float *b32 = static_cast<float *>(beta);
         {
             Site s_(h, 3, 2, st);
-            COX_TRY(prep_limbs_beta(h, b32, k, ws.Bb, ws.g1.NP, st));
-            COX_TRY(l1_norms32(h, b32, k, st));
+            COX_TRY(l1_norms32(h, b32, k, st, ws.bmaxp));
+            COX_TRY(prep_limbs_beta(h, b32, k, st));
         }
         EpiArgs e1;
         e1.epi = EPI_PARTIAL;
         e1.part = ws.part1;
+        e1.bscale = ws.bs1;
         {
             Site s_(h, 0, 1, st);
             COX_TRY(launch_gemm(h, ws.g1, e1, k, st));
@@ -158,8 +159,8 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
         sa.group_rows = ws.g1.T * TILE;
         sa.KC = ws.g1.KC;
         sa.L = ws.g1.L;
-        sa.v_out = V_LIMBS_BF16;
-        sa.V = ws.Vb;
+        sa.v_out = V_LIMBS_E4M3;
+        sa.V = ws.Vq;
         sa.NP = ws.g4.NP;
         sa.exp64 = false;
         sa.lam = ws.lam;
@@ -179,6 +180,7 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
         e4.mu = h->d_mu;
         e4.sumV = ws.sumV;
         e4.active = ws.active;
+        e4.bscale = ws.bs4;
         e4.rows_valid = h->p;
         e4.inv_n = 1.0 / static_cast<double>(h->n);
         {
@@ -329,14 +331,19 @@ int ensure_workspace(cox_handle *h, int k)
     A(ws.active, k);
     A(ws.Fring, static_cast<size_t>(std::max(lag, 2)) * k);
     if (is_split(h)) {
-        const int NP = (2 * k + 15) / 16 * 16 <= 16 ? 16 : (2 * k + 15) / 16 * 16 <= 32 ? 32 : (2 * k + 15) / 16 * 16 <= 64 ? 64 : 128;
-        A(ws.Bb, static_cast<size_t>(NP) * h->p_pad);
-        A(ws.Vb, static_cast<size_t>(NP) * h->n_pad);
-        cudaMemset(ws.Bb, 0, static_cast<size_t>(NP) * h->p_pad * 2);
-        cudaMemset(ws.Vb, 0, static_cast<size_t>(NP) * h->n_pad * 2);
+        const int NP = limb_cols(k);
+        A(ws.Bq, static_cast<size_t>(NP) * h->p_pad);
+        A(ws.Vq, static_cast<size_t>(NP) * h->n_pad);
+        A(ws.bs1, k);
+        A(ws.bs4, k);
+        A(ws.bmaxp, static_cast<size_t>(k) * h->l1_blocks);
+        A(ws.vmaxp, k * nch);
+        // limb rows past LIMBS k and K positions of padding stay zero
+        cudaMemset(ws.Bq, 0, static_cast<size_t>(NP) * h->p_pad);
+        cudaMemset(ws.Vq, 0, static_cast<size_t>(NP) * h->n_pad);
         ws.NP = NP;
-        if ((r = plan_gemm(h, ws.g1, h->d_A1, h->n_pad, h->p_pad, ws.Bb, k, h->opt.tile_m, h->opt.stages)) != COX_OK ||
-            (r = plan_gemm(h, ws.g4, h->d_A4, h->p_pad, h->n_pad, ws.Vb, k, h->opt.tile_m, h->opt.stages)) != COX_OK) {
+        if ((r = plan_gemm(h, ws.g1, h->d_A1, h->n_pad, h->p_pad, ws.Bq, k, h->opt.tile_m, h->opt.stages)) != COX_OK ||
+            (r = plan_gemm(h, ws.g4, h->d_A4, h->p_pad, h->n_pad, ws.Vq, k, h->opt.tile_m, h->opt.stages)) != COX_OK) {
             free_workspace(h);
             return r;
         }
@@ -371,7 +378,7 @@ extern "C" {
 void cox_default_options(cox_options *opt)
 {
     if (!opt) return;
-    opt->precision = COX_SPLIT_BF16;
+    opt->precision = COX_SPLIT_E4M3;
     opt->center = 1;
     opt->device = -1;
     opt->tile_m = 0;
@@ -418,7 +425,7 @@ int cox_setup(cox_h *out, const void *X, int64_t n, int64_t p, int x_format, con
     cox_default_options(&opt);
     if (opt_in) opt = *opt_in;
     if (!X || !time || !event || n < 1 || p < 1 || n > INT32_MAX || p > INT32_MAX) return COX_ERR_ARG;
-    if (opt.precision != COX_SPLIT_BF16 && opt.precision != COX_FP64 && opt.precision != COX_FP32_GEMV)
+    if (opt.precision != COX_SPLIT_E4M3 && opt.precision != COX_FP64 && opt.precision != COX_FP32_GEMV)
         return COX_ERR_ARG;
     if ((opt.precision == COX_FP64) != (x_format == COX_X_F64_HOST)) return COX_ERR_UNSUPPORTED;
     if (x_format < COX_X_INT8_HOST || x_format > COX_X_PACKED2_DEV) return COX_ERR_ARG;
@@ -537,7 +544,7 @@ int cox_get_info(cox_h h, cox_info *info)
 int cox_set_precision(cox_h h, int precision)
 {
     if (!h) return COX_ERR_ARG;
-    if (h->opt.precision == COX_FP64 || (precision != COX_SPLIT_BF16 && precision != COX_FP32_GEMV))
+    if (h->opt.precision == COX_FP64 || (precision != COX_SPLIT_E4M3 && precision != COX_FP32_GEMV))
         return COX_ERR_UNSUPPORTED;
     if (precision == h->opt.precision) return COX_OK;
     DeviceGuard g(h->dev);

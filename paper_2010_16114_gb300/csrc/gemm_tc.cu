@@ -6,21 +6,23 @@
 //                   soft-threshold step (Section 4.2) in the epilogue.
 //
 // A is the 2-bit genotype matrix in a tiled layout (128 x 128 blocks of 4 KB),
-// loaded by TMA into shared memory, decoded by eight warps into Tensor Memory
-// and consumed by tcgen05.mma as the A operand (kind::f16, A from TMEM,
-// B from 128B-swizzled shared memory, FP32 accumulators in TMEM).
+// loaded by TMA into shared memory, decoded by warps into Tensor Memory and
+// consumed by tcgen05.mma as the A operand (kind::f8f6f4, e4m3 A from TMEM,
+// e4m3 B from 128B-swizzled shared memory, FP32 accumulators in TMEM).
 //
-// Decode: a genotype code c in {0,1,2} placed at mantissa bits [2t, 2t+1] of
-// a zero-exponent bf16 is the subnormal c * 2^(2t-133); the matching B row is
-// pre-scaled by 2^(69-2t), so each product equals c * b * 2^-64 exactly and
-// the epilogue multiplies by 2^64.  Decoding is one AND per pair of codes.
+// Decode: a genotype code c in {0,1,2} as an e4m3 byte is the subnormal
+// c * 2^-9, exact in the tensor core; the packed layout (code_bit) makes one
+// shift and one AND produce four such bytes.
 //
-// B holds each coefficient column as two bf16 limbs, hi = RN(b), lo = RN(b-hi)
-// (columns 2c and 2c+1), so D[2c] + D[2c+1] carries ~16 significant bits of b.
+// B holds each coefficient column c as LIMBS = 4 e4m3 limbs (rows 4c .. 4c+3):
+// with r_0 = b 2^-s (s per column, |r_0| <= 256), d_l = RN_e4m3(r_l) and
+// r_(l+1) = 16 (r_l - d_l), b = 2^s sum_l d_l 2^-4l to ~16 significant bits.
+// The fold adds a column's limb accumulators with their weights 2^-4l and the
+// partial is scaled by 2^(s+9).
 //
 // Pipeline per CTA (one per SM): two TMA warps fill a ring of shared-memory
 // stages (B chunk + T A blocks); groups of four decoder warps turn a stage into
-// bf16 in a ring of TMEM slots, issuing all of a stage's tcgen05.st before one
+// e4m3 in a ring of TMEM slots, issuing all of a stage's tcgen05.st before one
 // wait; issuer warps (a tile and every Q-th stage each) issue the stage's MMAs
 // into their own accumulators and commit.  Decoders hand a slot to the issuers
 // through a hardware named barrier (tens of cycles, against a few hundred for
@@ -36,8 +38,6 @@
 // range [c L, (c+1) L).  A group cut between CTAs gets one partial per CTA
 // (slot = CTA - first CTA of the group); the last CTA to finish a group sums
 // the slots in slot order (deterministic) and applies the epilogue.
-#include <cuda_bf16.h>
-
 #include <algorithm>
 
 #include "internal.h"
@@ -48,6 +48,7 @@ namespace {
 
 struct KParams {
     int KC, F, k, stages, ring, nb_period;
+    const int *bscale;  // k: power-of-two scale of the B limbs
     int64_t units, L;
     int64_t rows_pad, slot_stride;
     float *part;
@@ -69,17 +70,13 @@ struct KParams {
 constexpr long long DRAIN_LIMIT = 4000000000LL;  // ~2 s: copies/MMAs always finish
 __device__ int g_never_set = 0;                 // abort flag for drain waits: never raised
 
+// 16 codes of a packed word -> 16 e4m3 bytes (four TMEM columns, K order)
 __device__ __forceinline__ void decode16(uint32_t P, uint32_t *o)
 {
-    const uint32_t Q = P >> 6, R = P >> 12;
-    o[0] = P & 0x00030003u;
-    o[1] = P & 0x000C000Cu;
-    o[2] = P & 0x00300030u;
-    o[3] = Q & 0x00030003u;
-    o[4] = Q & 0x000C000Cu;
-    o[5] = Q & 0x00300030u;
-    o[6] = R & 0x00030003u;
-    o[7] = R & 0x000C000Cu;
+    o[0] = P & 0x03030303u;
+    o[1] = (P >> 2) & 0x03030303u;
+    o[2] = (P >> 4) & 0x03030303u;
+    o[3] = (P >> 6) & 0x03030303u;
 }
 
 __device__ __forceinline__ void fail(volatile int *abort_sm, int *err)
@@ -88,11 +85,6 @@ __device__ __forceinline__ void fail(volatile int *abort_sm, int *err)
         *abort_sm = 1;
         atomicOr(err, DEVERR_TIMEOUT);
     }
-}
-
-__device__ __forceinline__ bool window_first(int64_t i, int kc, int64_t wstart, int F)
-{
-    return i == 0 || kc == 0 || i - wstart == F;
 }
 
 // all lanes wait; the warp agrees on the outcome
@@ -131,12 +123,12 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
                   const KParams P)
 {
     constexpr int I = T * Q;              // MMA issuers
-    constexpr int KH = NP / 2;            // lambda columns a decoder thread folds (NP/2 >= k)
-    constexpr int B_BYTES = NP * 256;
+    constexpr int KH = NP / LIMBS;        // lambda columns a decoder thread folds (>= k)
+    constexpr int B_BYTES = NP * 128;
     constexpr int X_BYTES = T * BLOCK_BYTES;
     constexpr int STAGE = B_BYTES + X_BYTES;
     constexpr int ACC_COLS = I * NP;      // one accumulator per issuer
-    constexpr int SLOT_COLS = T * 64;
+    constexpr int SLOT_COLS = T * 32;     // 128 e4m3 A values per lane and tile
     constexpr int DEC0 = 2 + I;           // first decoder warp
     constexpr int NB_COUNT = 32 * (4 + T);  // a decoder group and the stage's T issuer warps
 
@@ -216,7 +208,6 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
                 armed[s] = static_cast<int>(ph);
                 mbar_arrive_expect_tx(fb, STAGE);
                 tma_load_2d(st, &tmB, kc * TILE, 0, fb);
-                tma_load_2d(st + NP * 128, &tmB, kc * TILE + 64, 0, fb);
                 tma_load_4d(st + B_BYTES, &tmA, 0, 0, kc, g * T, fb);
                 s += 2;
                 if (s >= S) {
@@ -234,7 +225,7 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
         // ---------------- MMA issuers (whole warp; lane 0 issues) ----------------
         const int j = warp - 2;
         const int t = j / Q, c = j % Q;
-        constexpr uint32_t idesc = idesc_bf16_f32(128, NP);
+        constexpr uint32_t idesc = idesc_e4m3_f32(128, NP);
         const uint32_t d = tbase + static_cast<uint32_t>(j * NP);
         const uint64_t desc0 = smem_desc_sw128(smem_addr(smem));
         int s = 0, r = 0, kc = kc0, wlen = 0, own = 0, nbid = 0;
@@ -264,11 +255,11 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
                 if (ok && lane == 0) {
                     tc_fence_after();
                     const uint64_t dstage = desc0 + static_cast<uint64_t>((s * STAGE) >> 4);
-                    const uint32_t a = tbase + static_cast<uint32_t>(ACC_COLS + r * SLOT_COLS + t * 64);
+                    const uint32_t a = tbase + static_cast<uint32_t>(ACC_COLS + r * SLOT_COLS + t * 32);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const uint64_t bd = dstage + static_cast<uint64_t>(((q >> 2) * NP * 128 + (q & 3) * 32) >> 4);
-                        mma_ts(d, a + 8 * q, bd, idesc, (firstown && q == 0) ? 0u : 1u);
+                    for (int q = 0; q < 4; ++q) {  // K = 32 per MMA: 32 bytes of every B row, 8 TMEM columns of A
+                        const uint64_t bd = dstage + static_cast<uint64_t>((q * 32) >> 4);
+                        mma_ts_f8(d, a + 8 * q, bd, idesc, (firstown && q == 0) ? 0u : 1u);
                     }
                     mma_commit(aempty0 + 8 * r);
                 }
@@ -327,8 +318,13 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
                         tmem_ld_32x32b_x8(lane_base + static_cast<uint32_t>((tt * Q + cq) * NP + cc * 8), v);
                         tmem_wait_ld();
 #pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            acc(tt, cc * 4 + e) += __uint_as_float(v[2 * e]) + __uint_as_float(v[2 * e + 1]);
+                        for (int e = 0; e < 2; ++e) {  // two lambda columns of four limbs
+                            float x = __uint_as_float(v[4 * e + 3]);
+                            x = fmaf(x, 0.0625f, __uint_as_float(v[4 * e + 2]));
+                            x = fmaf(x, 0.0625f, __uint_as_float(v[4 * e + 1]));
+                            x = fmaf(x, 0.0625f, __uint_as_float(v[4 * e]));
+                            acc(tt, cc * 2 + e) += x;
+                        }
                     }
                 }
             }
@@ -344,7 +340,7 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
                 const int64_t row = (static_cast<int64_t>(g) * T + tt) * TILE + rit;
 #pragma unroll
                 for (int e = 0; e < KH; ++e) {
-                    if (e < P.k) P.part[slot * P.slot_stride + e * P.rows_pad + row] = acc(tt, e) * 0x1.0p64f;
+                    if (e < P.k) P.part[slot * P.slot_stride + e * P.rows_pad + row] = ldexpf(acc(tt, e), P.bscale[e] + 9);
                     acc(tt, e) = 0.f;
                 }
             }
@@ -440,16 +436,16 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
                 const uint32_t acol = lane_base + static_cast<uint32_t>(ACC_COLS + r * SLOT_COLS);
 #pragma unroll
                 for (int tt = 0; tt < T; ++tt) {
+                    uint32_t o[32];
 #pragma unroll
                     for (int hh = 0; hh < 2; ++hh) {
                         const uint4 v = *reinterpret_cast<const uint4 *>(xs + tt * BLOCK_BYTES + 16 * (hh ^ swp));
-                        uint32_t o[32];
-                        decode16(v.x, o);
-                        decode16(v.y, o + 8);
-                        decode16(v.z, o + 16);
-                        decode16(v.w, o + 24);
-                        tmem_st_32x32b_x32(acol + tt * 64 + 32 * hh, o);
+                        decode16(v.x, o + 16 * hh);
+                        decode16(v.y, o + 16 * hh + 4);
+                        decode16(v.z, o + 16 * hh + 8);
+                        decode16(v.w, o + 16 * hh + 12);
                     }
+                    tmem_st_32x32b_x32(acol + tt * 32, o);
                 }
                 tmem_wait_st();
             }
@@ -491,19 +487,32 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
     }
 }
 
-// beta (p x k fp32, column-major) -> bf16 limbs [NP][p_pad], scaled per K slot.
-__global__ void k_prep_limbs_beta(const float *__restrict__ beta, int64_t p, int k, int64_t p_pad,
-                                  uint16_t *__restrict__ Bb)
+// beta (p x k fp32, column-major) -> e4m3 limbs [NP][p_pad] with one
+// power-of-two scale per column (from the max |beta| partials of k_l1_32).
+__global__ void k_prep_limbs_beta(const float *__restrict__ beta, int64_t p, int64_t p_pad, int nb,
+                                  const float *__restrict__ maxp, uint8_t *__restrict__ Bq,
+                                  int *__restrict__ bs, int *err)
 {
+    __shared__ int s_sh;
     const int kk = blockIdx.y;
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int b = 0; b < nb; ++b) m = fmaxf(m, maxp[kk * nb + b]);
+        if (!isfinite(m)) {
+            atomicOr(err, DEVERR_NONFINITE);
+            m = 0.f;
+        }
+        s_sh = limb_scale(m);
+        if (blockIdx.x == 0) bs[kk] = s_sh;
+    }
+    __syncthreads();
+    const int s = s_sh;
     for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < p;
          j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int tsl = ((((j & 15) >> 1) % 3));
-        const float bs = ldexpf(beta[static_cast<int64_t>(kk) * p + j], 69 - 2 * tsl);
-        const __nv_bfloat16 hi = __float2bfloat16_rn(bs);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(bs - __bfloat162float(hi));
-        Bb[(2 * kk) * p_pad + j] = __bfloat16_as_ushort(hi);
-        Bb[(2 * kk + 1) * p_pad + j] = __bfloat16_as_ushort(lo);
+        uint8_t d[LIMBS];
+        split_e4m3(ldexpf(beta[static_cast<int64_t>(kk) * p + j], -s), d);
+#pragma unroll
+        for (int l = 0; l < LIMBS; ++l) Bq[(LIMBS * kk + l) * p_pad + j] = d[l];
     }
 }
 
@@ -530,23 +539,24 @@ using KernelFn = void (*)(const CUtensorMap, const CUtensorMap, const KParams);
 constexpr int DEC_GROUPS = 3;
 
 // (T row tiles per stage, Q issuers per tile) for a limb-column class NP.
-// Up to N = 32 an MMA is issue-bound (~50 cycles per instruction from one
-// thread), so two issuers per tile take alternate stages; from N = 64 on the
-// tensor pipe itself is the bound and one issuer per tile keeps up.
+// A stage of a tile is 4 MMAs (K = 32 each), which one issuer keeps up with
+// (~50-60 cycles per instruction from one thread); one issuer per tile leaves
+// the most TMEM to the A slot ring.  N = 256 fills half of TMEM per
+// accumulator, so that class takes one tile per stage.
 void shape_for(int NP, int *T, int *Q)
 {
-    if (NP <= 32) { *T = 2; *Q = 2; }
-    else if (NP == 64) { *T = 2; *Q = 1; }
-    else { *T = 1; *Q = 1; }
+    *Q = 1;
+    *T = NP <= 128 ? 2 : 1;
 }
 
 KernelFn pick_kernel(int T, int Q, int NP)
 {
     switch ((T * 10 + Q) * 1000 + NP) {
-    case 22016: return k_packed_gemm<2, 2, 16, DEC_GROUPS>;
-    case 22032: return k_packed_gemm<2, 2, 32, DEC_GROUPS>;
+    case 21016: return k_packed_gemm<2, 1, 16, DEC_GROUPS>;
+    case 21032: return k_packed_gemm<2, 1, 32, DEC_GROUPS>;
     case 21064: return k_packed_gemm<2, 1, 64, DEC_GROUPS>;
-    case 11128: return k_packed_gemm<1, 1, 128, DEC_GROUPS>;
+    case 21128: return k_packed_gemm<2, 1, 128, DEC_GROUPS>;
+    case 11256: return k_packed_gemm<1, 1, 256, DEC_GROUPS>;
     default: return nullptr;
     }
 }
@@ -559,27 +569,26 @@ int lcm_i(int a, int b) { return a / gcd_i(a, b) * b; }
 } // namespace
 
 // Plan one product: A (rows_pad x K_pad, tiled 2-bit) times B limbs (NP x K_pad).
-// TMEM budget (512 columns): 2 T NP accumulator columns + ring x T x 64 A columns.
+// TMEM budget (512 columns): T Q NP accumulator columns + ring x T x 32 A columns.
 int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, int64_t K_pad,
-              const uint16_t *B, int k, int T_req, int stages_req)
+              const uint8_t *B, int k, int T_req, int stages_req)
 {
     if (k < 1 || k > MAX_K_TC) return COX_ERR_ARG;
-    const int NP = (2 * k + 15) / 16 * 16;
-    const int np_cls = NP <= 16 ? 16 : NP <= 32 ? 32 : NP <= 64 ? 64 : 128;
+    const int np_cls = limb_cols(k);
     const int64_t m_tiles = rows_pad / TILE;
     (void)T_req;  // the row-tile count follows from the limb-column class
     int T = 2, Q = 2;
     shape_for(np_cls, &T, &Q);
     if (m_tiles % T != 0) return COX_ERR_ARG;
-    const int stage = np_cls * 256 + T * BLOCK_BYTES;
-    const int fold_bytes = T * (np_cls / 2) * 128 * 4;  // group 0's window sums
+    const int stage = np_cls * 128 + T * BLOCK_BYTES;
+    const int fold_bytes = T * (np_cls / LIMBS) * 128 * 4;  // group 0's window sums
     int S = stages_req > 0 ? stages_req : (225 * 1024 - 2048 - fold_bytes) / stage;
     if (S > 12) S = 12;
     if (S < DEC_GROUPS + 1) S = DEC_GROUPS + 1;  // decoder groups step through the stage ring by DEC_GROUPS
-    // TMEM: T Q accumulators of NP columns, the rest A slots of T x 64 columns;
+    // TMEM: T Q accumulators of NP columns, the rest A slots of T x 32 columns;
     // a slot's previous stage must still be in shared memory (ring <= S), and
     // the named-barrier period lcm(G, Q, ring) must fit barriers 1..15
-    int ring = (512 - T * Q * np_cls) / (T * 64);
+    int ring = (512 - T * Q * np_cls) / (T * 32);
     if (ring > 8) ring = 8;
     if (ring > S) ring = S;
     while (ring >= 2 && lcm_i(lcm_i(DEC_GROUPS, Q), ring) > 15) --ring;
@@ -628,11 +637,12 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
         if (r != CUDA_SUCCESS) return COX_ERR_CUDA;
     }
     {
+        // one 128-byte row (a K chunk of one limb column) per limb column
         cuuint64_t dims[2] = {static_cast<cuuint64_t>(K_pad), static_cast<cuuint64_t>(np_cls)};
-        cuuint64_t strides[1] = {static_cast<cuuint64_t>(K_pad) * 2};
-        cuuint32_t box[2] = {64, static_cast<cuuint32_t>(np_cls)};
+        cuuint64_t strides[1] = {static_cast<cuuint64_t>(K_pad)};
+        cuuint32_t box[2] = {128, static_cast<cuuint32_t>(np_cls)};
         cuuint32_t es[2] = {1, 1};
-        CUresult r = enc(&g.tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(B), dims, strides,
+        CUresult r = enc(&g.tmB, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(B), dims, strides,
                          box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return COX_ERR_CUDA;
@@ -649,6 +659,7 @@ int launch_gemm(cox_handle *h, const GemmPlan &g, const EpiArgs &e, int k, cudaS
     kp.stages = g.stages;
     kp.ring = g.ring;
     kp.nb_period = g.nb_period;
+    kp.bscale = e.bscale;
     kp.units = g.units;
     kp.L = g.L;
     kp.rows_pad = g.rows_pad;
@@ -674,11 +685,11 @@ int launch_gemm(cox_handle *h, const GemmPlan &g, const EpiArgs &e, int k, cudaS
     return COX_OK;
 }
 
-int prep_limbs_beta(cox_handle *h, const float *beta, int k, uint16_t *Bb, int NP, cudaStream_t st)
+int prep_limbs_beta(cox_handle *h, const float *beta, int k, cudaStream_t st)
 {
-    (void)NP;
     dim3 grid(static_cast<unsigned>(std::min<int64_t>((h->p + 255) / 256, 4096)), k);
-    k_prep_limbs_beta<<<grid, 256, 0, st>>>(beta, h->p, k, h->p_pad, Bb);
+    k_prep_limbs_beta<<<grid, 256, 0, st>>>(beta, h->p, h->p_pad, h->l1_blocks, h->ws.bmaxp, h->ws.Bq,
+                                            h->ws.bs1, h->d_err);
     COX_CUDA(cudaGetLastError());
     return COX_OK;
 }

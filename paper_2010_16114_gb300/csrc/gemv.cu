@@ -11,20 +11,37 @@
 namespace coxgb {
 namespace {
 
-__global__ void k_l1_32(const float *__restrict__ beta, int64_t p, int nb, double *__restrict__ l1p)
+__global__ void k_l1_32(const float *__restrict__ beta, int64_t p, int nb, double *__restrict__ l1p,
+                        float *__restrict__ maxp)
 {
     __shared__ double sh[8];
+    __shared__ float shm[8];
     const int b = blockIdx.x, kk = blockIdx.y;
     double s = 0.0;
-    for (int64_t j = static_cast<int64_t>(b) * blockDim.x + threadIdx.x; j < p; j += static_cast<int64_t>(nb) * blockDim.x)
-        s += fabs(static_cast<double>(beta[kk * p + j]));
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    float m = 0.f;
+    for (int64_t j = static_cast<int64_t>(b) * blockDim.x + threadIdx.x; j < p; j += static_cast<int64_t>(nb) * blockDim.x) {
+        const float v = fabsf(beta[kk * p + j]);
+        s += static_cast<double>(v);
+        m = fmaxf(m, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh[threadIdx.x >> 5] = s;
+        shm[threadIdx.x >> 5] = m;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < blockDim.x / 32; ++w) t += sh[w];
+        float mm = 0.f;
+        for (int w = 0; w < blockDim.x / 32; ++w) {
+            t += sh[w];
+            mm = fmaxf(mm, shm[w]);
+        }
         l1p[kk * nb + b] = t;
+        if (maxp) maxp[kk * nb + b] = mm;
     }
 }
 
@@ -70,8 +87,7 @@ __global__ void __launch_bounds__(128) k_gemv_tiles(const uint32_t *__restrict__
             if (P == 0) continue;
 #pragma unroll
             for (int kap = 0; kap < 16; ++kap) {
-                const int pos = (kap & 1) ? 15 + kap : kap;
-                const uint32_t c = (P >> pos) & 3u;
+                const uint32_t c = (P >> code_bit(kap)) & 3u;
                 const int64_t K = kb + 16 * q + kap;
                 if (c && K < K_valid) cs = fmaf(static_cast<float>(c), x[K], cs);
             }
@@ -151,9 +167,9 @@ unsigned blocks_for(int64_t n, int t) { return static_cast<unsigned>((n + t - 1)
 
 } // namespace
 
-int l1_norms32(cox_handle *h, const float *beta, int k, cudaStream_t st)
+int l1_norms32(cox_handle *h, const float *beta, int k, cudaStream_t st, float *maxp)
 {
-    k_l1_32<<<dim3(h->l1_blocks, k), 256, 0, st>>>(beta, h->p, h->l1_blocks, h->ws.l1p);
+    k_l1_32<<<dim3(h->l1_blocks, k), 256, 0, st>>>(beta, h->p, h->l1_blocks, h->ws.l1p, maxp);
     COX_CUDA(cudaGetLastError());
     return COX_OK;
 }

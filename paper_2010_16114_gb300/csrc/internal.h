@@ -1,6 +1,7 @@
 // internal.h -- handle layout and cross-file entry points of libcoxgb.
 #pragma once
 #include <cuda.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -18,6 +19,55 @@ constexpr int BLOCK_BYTES = 4096;  // one 128 x 128 block of 2-bit codes
 constexpr int PAD = 1024;          // n, p padding of the tiled layouts
 constexpr int SCAN_CH = 2048;      // subjects per scan chunk (256 threads x 8)
 constexpr int MAX_K_TC = 64;       // largest k of the tensor-core path
+constexpr int LIMBS = 4;           // e4m3 limbs per coefficient (4 significant bits each)
+
+// Limb columns of a k-column product: LIMBS k rounded up to an MMA width class.
+inline int limb_cols(int k)
+{
+    const int n = LIMBS * k;
+    return n <= 16 ? 16 : n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : 256;
+}
+
+// Position of code K (0..15) of a 16-code word: bit 8 (K mod 4) + 2 (K div 4),
+// so that (word >> 2q) & 0x03030303 is the four codes 4q..4q+3, one per byte:
+// as e4m3 bytes these are the subnormals c 2^-9, exact tensor-core operands.
+__host__ __device__ inline int code_bit(int K) { return 8 * (K & 3) + 2 * (K >> 2); }
+
+// ---- e4m3 limbs -----------------------------------------------------------------
+// A coefficient column b is held as LIMBS e4m3 numbers: with a power-of-two
+// scale 2^s putting max |b| 2^-s in [128, 256) (e4m3 reaches 448),
+// r_0 = b 2^-s, d_l = RN_e4m3(r_l), r_(l+1) = 16 (r_l - d_l); each step keeps
+// |r| <= 256, and b = 2^s sum_l d_l 2^-4l with about 4 LIMBS significant bits.
+
+__device__ inline float e4m3_value(uint8_t q)
+{
+    // sign, 4-bit exponent (bias 7), 3-bit mantissa; exponent 0: subnormal m 2^-9
+    const int e = (q >> 3) & 15, m = q & 7;
+    const float v = e ? ldexpf(1.0f + 0.125f * static_cast<float>(m), e - 7) : ldexpf(static_cast<float>(m), -9);
+    return (q & 0x80) ? -v : v;
+}
+
+__device__ inline int limb_scale(float mx) { return mx > 0.f ? ilogbf(mx) - 7 : 0; }
+
+// Limbs of r (|r| <= 256) into d[0..LIMBS); returns the value they represent.
+__device__ inline float split_e4m3(float r, uint8_t *d)
+{
+    if (!isfinite(r)) {
+        for (int l = 0; l < LIMBS; ++l) d[l] = 0x7F;  // NaN: the products flag it
+        return r;
+    }
+    float rep = 0.f, w = 1.f;
+#pragma unroll
+    for (int l = 0; l < LIMBS; ++l) {
+        const uint8_t q = static_cast<uint8_t>(__nv_cvt_float_to_fp8(r, __NV_SATFINITE, __NV_E4M3));
+        const float v = e4m3_value(q);
+        d[l] = q;
+        rep = fmaf(v, w, rep);
+        r = (r - v) * 16.f;
+        w *= 0.0625f;
+    }
+    return rep;
+}
 
 // K order of the SNP-major copy (A4).  Sorted subjects are kept in blocks of
 // 16 (one packed word), and sorted block b is stored at block (a b) mod nb,
@@ -35,7 +85,7 @@ __host__ __device__ inline int64_t a4_pos(int64_t i, int64_t a, int64_t nb)
 struct GemmPlan {
     int T = 2;         // 128-row tiles per CTA (one M group)
     int H = 2;         // MMA-issuing warps per tile (each takes every H-th stage)
-    int NP = 16;       // limb columns (2k rounded up to 16)
+    int NP = 16;       // limb columns (limb_cols(k))
     int stages = 6;    // shared-memory pipeline depth
     int ring = 4;      // TMEM A buffers
     int nb_period = 6; // named barriers in use: lcm(decoder groups, H, ring)
@@ -66,8 +116,12 @@ struct Workspace {
     int *active = nullptr;     // k
     double *Fring = nullptr;   // lag x k
     // split mode
-    uint16_t *Bb = nullptr;    // NP x p_pad bf16 limbs of beta
-    uint16_t *Vb = nullptr;    // NP x n_pad bf16 limbs of V, A4 K order
+    uint8_t *Bq = nullptr;     // NP x p_pad e4m3 limbs of beta (row LIMBS c + l: limb l of column c)
+    uint8_t *Vq = nullptr;     // NP x n_pad e4m3 limbs of V, A4 K order
+    int *bs1 = nullptr;        // k: power-of-two scale of the beta limbs
+    int *bs4 = nullptr;        // k: power-of-two scale of the V limbs
+    float *bmaxp = nullptr;    // k x l1 blocks: partial max |beta|
+    double *vmaxp = nullptr;   // k x chunks: partial max |V|
     float *part1 = nullptr;    // slots x k x rows_pad (eta partials)
     float *part4 = nullptr;    // slots x k x rows_pad (X^T V partials)
     int *cnt4 = nullptr;       // per M group of the second product
@@ -153,7 +207,7 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
 // ---- scans (scans.cu) -------------------------------------------------------------
 // Risk-set scans on eta (sorted order, k columns).  eta_src kinds:
 enum EtaSrc { ETA_PARTIAL_F32 = 0, ETA_DENSE_F64 = 1, ETA_DENSE_F32 = 2 };
-enum VOut { V_LIMBS_BF16 = 0, V_DENSE_F64 = 1, V_DENSE_F32 = 2 };
+enum VOut { V_LIMBS_E4M3 = 0, V_DENSE_F64 = 1, V_DENSE_F32 = 2 };
 struct ScanArgs {
     int k;
     int eta_src;
@@ -162,7 +216,7 @@ struct ScanArgs {
     int group_rows, KC;   // partial slot counts: group of a row, K chunks, L
     int64_t L;
     int v_out;
-    void *V;              // limbs [NP][n_pad] or dense [k][n]
+    void *V;              // e4m3 limbs [NP][n_pad] (scales in ws.bs4) or dense
     int NP;
     bool exp64;           // exp in FP64 (FP64 mode) or FP32
     const double *lam;    // k (objective); may be null
@@ -172,7 +226,7 @@ int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st);
 
 // ---- tensor-core products (gemm_tc.cu) ---------------------------------------------
 int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, int64_t K_pad,
-              const uint16_t *B, int k, int T_req, int stages_req);
+              const uint8_t *B, int k, int T_req, int stages_req);
 enum Epi { EPI_PARTIAL = 0, EPI_PROX = 1, EPI_GRAD = 2 };
 struct EpiArgs {
     int epi = EPI_PARTIAL;
@@ -185,14 +239,16 @@ struct EpiArgs {
     const double *mu = nullptr;
     const double *sumV = nullptr;
     const int *active = nullptr;
+    const int *bscale = nullptr;  // k: power-of-two scale of the B limbs
     int64_t rows_valid = 0;  // p
     double inv_n = 0;
 };
 int launch_gemm(cox_handle *h, const GemmPlan &g, const EpiArgs &e, int k, cudaStream_t st);
-int prep_limbs_beta(cox_handle *h, const float *beta, int k, uint16_t *Bb, int NP, cudaStream_t st);
+int prep_limbs_beta(cox_handle *h, const float *beta, int k, cudaStream_t st);
 
 // ---- CUDA-core paths (gemv.cu) -----------------------------------------------------
-int l1_norms32(cox_handle *h, const float *beta, int k, cudaStream_t st);
+// ||beta_c||_1 partials into ws.l1p; with maxp, max |beta_c| partials too
+int l1_norms32(cox_handle *h, const float *beta, int k, cudaStream_t st, float *maxp = nullptr);
 int l1_norms64(cox_handle *h, const double *beta, int k, cudaStream_t st);
 int gemv_tiles(cox_handle *h, const uint32_t *A, int64_t rows, int64_t KC, const float *x,
                int64_t K_valid, float *y, cudaStream_t st);

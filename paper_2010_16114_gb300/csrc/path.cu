@@ -210,7 +210,7 @@ int cox_path_fit(cox_h h, const double *lambdas, int k, int max_iter, double tol
 {
     if (!h || !beta_dev || !lambdas || max_iter < 0 || !(tol >= 0.0) || !(step > 0.0) || warm < 0 || warm > 2)
         return COX_ERR_ARG;
-    if (k < 1 || (h->opt.precision == COX_SPLIT_BF16 && k > MAX_K_TC)) return COX_ERR_ARG;
+    if (k < 1 || (h->opt.precision == COX_SPLIT_E4M3 && k > MAX_K_TC)) return COX_ERR_ARG;
     DeviceGuard g(h->dev);
     cudaStream_t user = static_cast<cudaStream_t>(stream);
     const int lag = h->opt.lag;

@@ -190,6 +190,17 @@ __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_
                  : "memory");
 }
 
+// D[tmem] (+)= A[tmem] * B[smem desc], kind::f8f6f4 (formats in the instruction
+// descriptor), fp32 accumulate; K = 32 per instruction for 8-bit operands.
+__device__ __forceinline__ void mma_ts_f8(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                          uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+                 "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+                 : "memory");
+}
+
 // Arrive on an mbarrier once all earlier tcgen05 operations of this thread complete.
 __device__ __forceinline__ void mma_commit(uint32_t bar)
 {
@@ -209,6 +220,13 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
     d |= static_cast<uint64_t>(1) << 46;          // descriptor version
     d |= static_cast<uint64_t>(2) << 61;          // 128-byte swizzle
     return d;
+}
+
+// Instruction descriptor, kind::f8f6f4: e4m3 A and B (format code 0, K-major),
+// fp32 D, M x N.
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N)
+{
+    return (1u << 4) | (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
 }
 
 // Instruction descriptor, kind::f16: bf16 A and B (K-major), fp32 D, M x N.

@@ -13,8 +13,6 @@
 // Each scan runs in fixed 2048-subject chunks (block scans with warp
 // shuffles), then an exclusive scan of the chunk totals, then a gather; the
 // summation order never depends on timing, so results are bit-reproducible.
-#include <cuda_bf16.h>
-
 #include "internal.h"
 
 namespace coxgb {
@@ -238,15 +236,17 @@ __global__ void k_fwd(SP s, bool need_loss)
 }
 
 // (4) C = F at the tie tail; u = w C; V = delta - u -> output form; sum of V.
-// The limb and FP32 forms feed products over the SNP-major copy and are
-// written at its K positions (a4_pos); the FP64 form stays in sorted order.
+// The FP32 form feeds a product over the SNP-major copy and is written at its
+// K positions (a4_pos); the FP64 form stays in sorted order.  For the e4m3
+// limbs, V goes to Rt (free after the forward scan) with chunk maxima of |V|,
+// and k_vlimbs splits it once the column's scale is known.
 template <int VO>
-__global__ void k_uv(SP s, void *Vout, int64_t n_pad)
+__global__ void k_uv(SP s, void *Vout, int64_t n_pad, double *vmaxp)
 {
     __shared__ double sh[NT / 32];
     const int c = blockIdx.x, kk = blockIdx.y;
     const int64_t i0 = static_cast<int64_t>(c) * SCAN_CH;
-    double vs = 0.0;
+    double vs = 0.0, vm = 0.0;
     for (int e = threadIdx.x; e < SCAN_CH; e += NT) {
         const int64_t i = i0 + e;
         if (i >= s.n) break;
@@ -254,29 +254,63 @@ __global__ void k_uv(SP s, void *Vout, int64_t n_pad)
         const double C = s.Ft[kk * s.n + tl] + s.pre[kk * s.nch + tl / SCAN_CH];
         const double u = s.w[kk * s.n + i] * C;
         const double V = static_cast<double>(s.delta[i]) - u;
-        const int64_t pos = a4_pos(i, s.pa, s.pnb);
         // sum V in the form the product reads: X^T V - mu sum V is then
         // exactly the centred product of that V.  (Censored subjects between
         // two event times share one V, so their rounding errors do not
         // cancel; with the exact sum, mu times their sum would remain.)
-        if (VO == V_LIMBS_BF16) {
-            const int tsl = (((i & 15) >> 1) % 3);
-            const double Vs = ldexp(V, 69 - 2 * tsl);
-            const __nv_bfloat16 hi = __float2bfloat16_rn(static_cast<float>(Vs));
-            const double hd = static_cast<double>(__bfloat162float(hi));
-            const __nv_bfloat16 lo = __float2bfloat16_rn(static_cast<float>(Vs - hd));
-            uint16_t *Vb = static_cast<uint16_t *>(Vout);
-            Vb[(2 * kk) * n_pad + pos] = __bfloat16_as_ushort(hi);
-            Vb[(2 * kk + 1) * n_pad + pos] = __bfloat16_as_ushort(lo);
-            vs += ldexp(hd + static_cast<double>(__bfloat162float(lo)), 2 * tsl - 69);
+        if (VO == V_LIMBS_E4M3) {
+            s.Rt[kk * s.n + i] = V;
+            vm = fmax(vm, fabs(V));
         } else if (VO == V_DENSE_F64) {
             static_cast<double *>(Vout)[kk * s.n + i] = V;
             vs += V;
         } else {
             const float v32 = static_cast<float>(V);
-            static_cast<float *>(Vout)[kk * n_pad + pos] = v32;
+            static_cast<float *>(Vout)[a4_pos(i, s.pa, s.pnb) + kk * n_pad] = v32;
             vs += static_cast<double>(v32);
         }
+    }
+    if (VO == V_LIMBS_E4M3) {
+        const double m = block_max(vm, sh);
+        if (threadIdx.x == 0) vmaxp[kk * s.nch + c] = m;
+    } else {
+        const double t = block_sum(vs, sh);
+        if (threadIdx.x == 0) s.vsp[kk * s.nch + c] = t;
+    }
+}
+
+// (4b) V (in Rt) -> e4m3 limbs at the A4 K positions, one power-of-two scale
+// per column (from all chunk maxima); chunk sums of the values the limbs hold.
+__global__ void k_vlimbs(SP s, uint8_t *__restrict__ Vq, int64_t n_pad, const double *__restrict__ vmaxp,
+                         int *__restrict__ bs, int *err)
+{
+    __shared__ double sh[NT / 32];
+    __shared__ int s_sh;
+    const int c = blockIdx.x, kk = blockIdx.y;
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int q = 0; q < s.nch; ++q) m = fmax(m, vmaxp[kk * s.nch + q]);
+        float mf = static_cast<float>(m);
+        if (!isfinite(mf)) {
+            atomicOr(err, DEVERR_NONFINITE);
+            mf = 0.f;
+        }
+        s_sh = limb_scale(mf);
+        if (c == 0) bs[kk] = s_sh;
+    }
+    __syncthreads();
+    const int sc = s_sh;
+    const int64_t i0 = static_cast<int64_t>(c) * SCAN_CH;
+    double vs = 0.0;
+    for (int e = threadIdx.x; e < SCAN_CH; e += NT) {
+        const int64_t i = i0 + e;
+        if (i >= s.n) break;
+        uint8_t d[LIMBS];
+        const float rep = split_e4m3(static_cast<float>(ldexp(s.Rt[kk * s.n + i], -sc)), d);
+        const int64_t pos = a4_pos(i, s.pa, s.pnb);
+#pragma unroll
+        for (int l = 0; l < LIMBS; ++l) Vq[(LIMBS * kk + l) * n_pad + pos] = d[l];
+        vs += ldexp(static_cast<double>(rep), sc);
     }
     const double t = block_sum(vs, sh);
     if (threadIdx.x == 0) s.vsp[kk * s.nch + c] = t;
@@ -348,9 +382,12 @@ int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st)
     k_fwd<<<grid, NT, 0, st>>>(s, a.need_loss);
     k_chunks<false><<<a.k, 32, 0, st>>>(s);
     switch (a.v_out) {
-    case V_LIMBS_BF16: k_uv<V_LIMBS_BF16><<<grid, NT, 0, st>>>(s, a.V, h->n_pad); break;
-    case V_DENSE_F64: k_uv<V_DENSE_F64><<<grid, NT, 0, st>>>(s, a.V, h->n_pad); break;
-    default: k_uv<V_DENSE_F32><<<grid, NT, 0, st>>>(s, a.V, h->n_pad); break;
+    case V_LIMBS_E4M3:
+        k_uv<V_LIMBS_E4M3><<<grid, NT, 0, st>>>(s, a.V, h->n_pad, ws.vmaxp);
+        k_vlimbs<<<grid, NT, 0, st>>>(s, static_cast<uint8_t *>(a.V), h->n_pad, ws.vmaxp, ws.bs4, h->d_err);
+        break;
+    case V_DENSE_F64: k_uv<V_DENSE_F64><<<grid, NT, 0, st>>>(s, a.V, h->n_pad, nullptr); break;
+    default: k_uv<V_DENSE_F32><<<grid, NT, 0, st>>>(s, a.V, h->n_pad, nullptr); break;
     }
     k_finalize<<<1, 64, 0, st>>>(s, h->l1_blocks, a.need_loss ? ws.l1p : nullptr, a.lam, ws.sumV, ws.f, ws.l1,
                                  ws.F, a.need_loss, h->d_err);

@@ -13,8 +13,8 @@
 // halves (K 0-63 and 64-127 of the chunk); the halves of rows with bit 2 of r
 // set are stored swapped, which spreads a warp's 16-byte reads over all 32
 // banks.  A half is four 32-bit words of 16 codes; inside a word, code K
-// (0..15) sits at bit K when K is even and at bit 15+K when K is odd, i.e.
-// the two codes of one bf16 pair share a bit position in the two halves.
+// (0..15) sits at bit code_bit(K) = 8 (K mod 4) + 2 (K div 4), so one shift
+// and one AND give four consecutive codes as four e4m3 bytes.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -33,8 +33,6 @@ __device__ __forceinline__ int64_t word_offset(int64_t mt, int64_t KC, int64_t k
     const int phys = hh ^ ((rit >> 2) & 1);
     return ((mt * KC + kc) * BLOCK_BYTES + rit * 32 + phys * 16 + w * 4) >> 2;
 }
-
-__device__ __forceinline__ int code_pos(int kap) { return (kap & 1) ? 15 + kap : kap; }
 
 // A1: thread per (sorted row r, 16-SNP word); validates codes.
 __global__ void k_pack_a1(const uint8_t *__restrict__ in, int64_t rb, int64_t n, int64_t p,
@@ -55,7 +53,7 @@ __global__ void k_pack_a1(const uint8_t *__restrict__ in, int64_t rb, int64_t n,
             if (j < p) {
                 const uint32_t c = (row[j >> 2] >> (2 * (j & 3))) & 3u;
                 bad |= (c == 3u);
-                P |= (c == 3u ? 0u : c) << code_pos(kap);
+                P |= (c == 3u ? 0u : c) << code_bit(kap);
             }
         }
         if (bad) atomicOr(err, DEVERR_CODE3);
@@ -82,7 +80,7 @@ __global__ void k_pack_a4(const uint8_t *__restrict__ in, int64_t rb, int64_t n,
             if (r < n) {
                 uint32_t c = (in[static_cast<int64_t>(order[r]) * rb + (j >> 2)] >> (2 * (j & 3))) & 3u;
                 if (c == 3u) c = 0u;
-                P |= c << code_pos(kap);
+                P |= c << code_bit(kap);
                 s += c;
             }
         }

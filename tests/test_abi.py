@@ -47,7 +47,7 @@ def test_strerror_and_defaults(lib):
     assert "timed out" in L.strerror(L.COX_ERR_TIMEOUT)
     assert L.strerror(12345) == "unknown error"
     o = L.cox_default_options()
-    assert o.precision == L.COX_SPLIT_BF16 and o.center == 1 and o.lag == 10 and o.wait_limit_s == 2.0
+    assert o.precision == L.COX_SPLIT_E4M3 and o.center == 1 and o.lag == 10 and o.wait_limit_s == 2.0
 
 
 def test_argument_errors_without_gpu(lib):

@@ -2,7 +2,7 @@
 
 Tolerances (stated per result; derived in the design doc):
   * FP64 path (config-0 recipe): beta and gradient relative L2 <= 1e-10.
-  * split-bf16 tensor-core path and FP32 baseline: gradient relative L2 <= 1e-5,
+  * split-e4m3 tensor-core path and FP32 baseline: gradient relative L2 <= 1e-5,
     loss relative error <= 1e-7, beta relative L2 <= 1e-4 after a fixed number
     of iterations, identical support outside a 1e-6 threshold margin.
 Sizes are chosen so the oracle finishes in seconds while n and p span several
@@ -78,7 +78,7 @@ def _random_betas(p, k, seed):
     return B
 
 
-@pytest.mark.parametrize("precision", ["split_bf16", "fp32_gemv"])
+@pytest.mark.parametrize("precision", ["split_e4m3", "fp32_gemv"])
 @pytest.mark.parametrize("k", [1, 3, 16])
 def test_loss_grad_geno(pkg, geno, precision, k):
     w, X, Xf, mu = geno
@@ -94,7 +94,7 @@ def test_loss_grad_geno(pkg, geno, precision, k):
             assert rel_l2(G[c], g_o) <= 1e-5, (c, rel_l2(G[c], g_o))
 
 
-@pytest.mark.parametrize("precision", ["split_bf16", "fp32_gemv"])
+@pytest.mark.parametrize("precision", ["split_e4m3", "fp32_gemv"])
 def test_prox_iterations_geno(pkg, geno, precision):
     """20 batched iterations for 3 penalties vs the oracle's iterates."""
     w, X, Xf, mu = geno
@@ -126,7 +126,7 @@ def test_lambda_max_and_lipschitz_geno(pkg, geno):
     v0 = synth.normal_vec(95376, 7, w.p)
     L = oracle.lipschitz(Xf, mu, v0)
     lmax = oracle.lambda_max(Xf, mu, w.y, w.delta)
-    with _problem(pkg, X, w, "split_bf16") as prob:
+    with _problem(pkg, X, w, "split_e4m3") as prob:
         assert abs(prob.lambda_max() - lmax) <= 1e-5 * lmax
         assert abs(prob.lipschitz(v0) - L) <= 1e-4 * L
 
@@ -152,7 +152,7 @@ def test_degenerate_cases(pkg, kind):
     from paper_2010_16114_gb300.cox import CoxProblem
     w, X, Xf, mu, y, d = _edge_case(kind)
     B = _random_betas(w.p, 2, 5)
-    with CoxProblem(X, y, d, precision="split_bf16") as prob:
+    with CoxProblem(X, y, d, precision="split_e4m3") as prob:
         beta = torch.tensor(B, dtype=torch.float32, device="cuda")
         loss, grad = prob.loss_grad(beta)
         G = grad.cpu().numpy()
@@ -163,7 +163,7 @@ def test_degenerate_cases(pkg, kind):
                 assert loss[c] == 0.0
             else:
                 # f = (1/n) sum_i delta_i (log W_i - eta_i): a difference of O(|eta|)
-                # terms, so its error follows the split-bf16 error of eta (~2^-17 of
+                # terms, so its error follows the limb error of eta (~2^-17 of
                 # sum_j |x_ij beta_j|), not |f| -- with one event f is nearly zero.
                 eta_o = oracle.eta(Xf, mu, beta[c].cpu().numpy().astype(np.float64))
                 eta_scale = np.abs(X.astype(np.float64)) @ np.abs(beta[c].cpu().numpy().astype(np.float64))
@@ -178,7 +178,7 @@ def test_single_predictor_and_tiny_n(pkg):
         d = w.delta.copy()
         d[0] = 1
         from paper_2010_16114_gb300.cox import CoxProblem
-        with CoxProblem(X, w.y, d, precision="split_bf16") as prob:
+        with CoxProblem(X, w.y, d, precision="split_e4m3") as prob:
             beta = torch.full((1, p), 0.3, dtype=torch.float32, device="cuda")
             loss, grad = prob.loss_grad(beta)
             f_o, g_o = oracle_loss_grad(Xf, mu, w.y, d, np.full(p, 0.3))

@@ -36,7 +36,7 @@ def _both(L, prob, v0, tol, maxiter):
     return a, b
 
 
-@pytest.mark.parametrize("precision", ["split_bf16", "fp64"])
+@pytest.mark.parametrize("precision", ["split_e4m3", "fp64"])
 def test_noalloc_matches_allocating_call_twice(L, precision):
     from paper_2010_16114_gb300.cox import CoxProblem
     if precision == "fp64":
