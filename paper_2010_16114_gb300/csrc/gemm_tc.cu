@@ -87,7 +87,8 @@ __device__ __forceinline__ void fail(volatile int *abort_sm, int *err)
     }
 }
 
-// all lanes wait; the warp agrees on the outcome
+// all lanes wait; the warp agrees on the outcome (polling from lane 0 alone,
+// with or without sleeping between polls, measured slower)
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, long long lim, volatile int *abort)
 {
     return __all_sync(0xffffffffu, mbar_wait(bar, parity, lim, abort));
@@ -117,18 +118,18 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, long lo
 // passed it (they first wait, through the TMEM slot chain, for MMAs that those
 // issuers issue after it).  Decoders arrive on every path, so an issuer's
 // (unbounded) hardware-barrier wait always ends.
-template <int T, int Q, int NP, int G>
+template <int T, int Q, int CH, int NP, int G>
 __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
     k_packed_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const KParams P)
 {
     constexpr int I = T * Q;              // MMA issuers
     constexpr int KH = NP / LIMBS;        // lambda columns a decoder thread folds (>= k)
-    constexpr int B_BYTES = NP * 128;
-    constexpr int X_BYTES = T * BLOCK_BYTES;
+    constexpr int B_BYTES = CH * NP * 128;       // CH chunk panels of NP rows x 128 bytes
+    constexpr int X_BYTES = T * CH * BLOCK_BYTES;  // [tile][chunk] 4 KB blocks
     constexpr int STAGE = B_BYTES + X_BYTES;
     constexpr int ACC_COLS = I * NP;      // one accumulator per issuer
-    constexpr int SLOT_COLS = T * 32;     // 128 e4m3 A values per lane and tile
+    constexpr int SLOT_COLS = T * CH * 32;  // 128 e4m3 A values per lane, tile and chunk
     constexpr int DEC0 = 2 + I;           // first decoder warp
     constexpr int NB_COUNT = 32 * (4 + T);  // a decoder group and the stage's T issuer warps
 
@@ -207,8 +208,9 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
                 const uint32_t fb = full0 + 8 * s;
                 armed[s] = static_cast<int>(ph);
                 mbar_arrive_expect_tx(fb, STAGE);
-                tma_load_2d(st, &tmB, kc * TILE, 0, fb);
-                tma_load_4d(st + B_BYTES, &tmA, 0, 0, kc, g * T, fb);
+#pragma unroll
+                for (int h = 0; h < CH; ++h) tma_load_2d(st + h * NP * 128, &tmB, (kc * CH + h) * TILE, 0, fb);
+                tma_load_4d(st + B_BYTES, &tmA, 0, 0, kc * CH, g * T, fb);
                 s += 2;
                 if (s >= S) {
                     s -= S;
@@ -255,10 +257,11 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
                 if (ok && lane == 0) {
                     tc_fence_after();
                     const uint64_t dstage = desc0 + static_cast<uint64_t>((s * STAGE) >> 4);
-                    const uint32_t a = tbase + static_cast<uint32_t>(ACC_COLS + r * SLOT_COLS + t * 32);
+                    const uint32_t a = tbase + static_cast<uint32_t>(ACC_COLS + r * SLOT_COLS + t * CH * 32);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {  // K = 32 per MMA: 32 bytes of every B row, 8 TMEM columns of A
-                        const uint64_t bd = dstage + static_cast<uint64_t>((q * 32) >> 4);
+                    for (int q = 0; q < 4 * CH; ++q) {
+                        // K = 32 per MMA: 32 bytes of every row of chunk panel q/4, 8 TMEM columns of A
+                        const uint64_t bd = dstage + static_cast<uint64_t>(((q >> 2) * NP * 128 + (q & 3) * 32) >> 4);
                         mma_ts_f8(d, a + 8 * q, bd, idesc, (firstown && q == 0) ? 0u : 1u);
                     }
                     mma_commit(aempty0 + 8 * r);
@@ -434,18 +437,18 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
                 tc_fence_after();
                 const uint8_t *xs = smem + s * STAGE + B_BYTES + rit * 32;
                 const uint32_t acol = lane_base + static_cast<uint32_t>(ACC_COLS + r * SLOT_COLS);
-#pragma unroll
-                for (int tt = 0; tt < T; ++tt) {
+#pragma unroll 2
+                for (int tc = 0; tc < T * CH; ++tc) {  // tile tc / CH, chunk tc % CH
                     uint32_t o[32];
 #pragma unroll
                     for (int hh = 0; hh < 2; ++hh) {
-                        const uint4 v = *reinterpret_cast<const uint4 *>(xs + tt * BLOCK_BYTES + 16 * (hh ^ swp));
+                        const uint4 v = *reinterpret_cast<const uint4 *>(xs + tc * BLOCK_BYTES + 16 * (hh ^ swp));
                         decode16(v.x, o + 16 * hh);
                         decode16(v.y, o + 16 * hh + 4);
                         decode16(v.z, o + 16 * hh + 8);
                         decode16(v.w, o + 16 * hh + 12);
                     }
-                    tmem_st_32x32b_x32(acol + tt * 32, o);
+                    tmem_st_32x32b_x32(acol + tc * 32, o);
                 }
                 tmem_wait_st();
             }
@@ -543,20 +546,24 @@ constexpr int DEC_GROUPS = 3;
 // (~50-60 cycles per instruction from one thread); one issuer per tile leaves
 // the most TMEM to the A slot ring.  N = 256 fills half of TMEM per
 // accumulator, so that class takes one tile per stage.
-void shape_for(int NP, int *T, int *Q)
+// A stage spans CH K chunks: every hand-off costs a few hundred cycles
+// whatever its size, so up to N = 64 a stage takes two chunks (16 KB of codes
+// at T = 2), which keeps the same bytes in TMEM with half the hand-offs.
+void shape_for(int NP, int *T, int *Q, int *CH)
 {
     *Q = 1;
     *T = NP <= 128 ? 2 : 1;
+    *CH = NP <= 64 ? 2 : 1;
 }
 
-KernelFn pick_kernel(int T, int Q, int NP)
+KernelFn pick_kernel(int T, int Q, int CH, int NP)
 {
-    switch ((T * 10 + Q) * 1000 + NP) {
-    case 21016: return k_packed_gemm<2, 1, 16, DEC_GROUPS>;
-    case 21032: return k_packed_gemm<2, 1, 32, DEC_GROUPS>;
-    case 21064: return k_packed_gemm<2, 1, 64, DEC_GROUPS>;
-    case 21128: return k_packed_gemm<2, 1, 128, DEC_GROUPS>;
-    case 11256: return k_packed_gemm<1, 1, 256, DEC_GROUPS>;
+    switch (((T * 10 + Q) * 10 + CH) * 1000 + NP) {
+    case 212016: return k_packed_gemm<2, 1, 2, 16, DEC_GROUPS>;
+    case 212032: return k_packed_gemm<2, 1, 2, 32, DEC_GROUPS>;
+    case 212064: return k_packed_gemm<2, 1, 2, 64, DEC_GROUPS>;
+    case 211128: return k_packed_gemm<2, 1, 1, 128, DEC_GROUPS>;
+    case 111256: return k_packed_gemm<1, 1, 1, 256, DEC_GROUPS>;
     default: return nullptr;
     }
 }
@@ -577,24 +584,25 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
     const int np_cls = limb_cols(k);
     const int64_t m_tiles = rows_pad / TILE;
     (void)T_req;  // the row-tile count follows from the limb-column class
-    int T = 2, Q = 2;
-    shape_for(np_cls, &T, &Q);
-    if (m_tiles % T != 0) return COX_ERR_ARG;
-    const int stage = np_cls * 128 + T * BLOCK_BYTES;
+    int T = 2, Q = 1, CH = 1;
+    shape_for(np_cls, &T, &Q, &CH);
+    if (m_tiles % T != 0 || (K_pad / TILE) % CH != 0) return COX_ERR_ARG;
+    const int stage = CH * (np_cls * 128 + T * BLOCK_BYTES);
     const int fold_bytes = T * (np_cls / LIMBS) * 128 * 4;  // group 0's window sums
     int S = stages_req > 0 ? stages_req : (225 * 1024 - 2048 - fold_bytes) / stage;
     if (S > 12) S = 12;
     if (S < DEC_GROUPS + 1) S = DEC_GROUPS + 1;  // decoder groups step through the stage ring by DEC_GROUPS
-    // TMEM: T Q accumulators of NP columns, the rest A slots of T x 32 columns;
+    // TMEM: T Q accumulators of NP columns, the rest A slots of T CH x 32 columns;
     // a slot's previous stage must still be in shared memory (ring <= S), and
     // the named-barrier period lcm(G, Q, ring) must fit barriers 1..15
-    int ring = (512 - T * Q * np_cls) / (T * 32);
+    int ring = (512 - T * Q * np_cls) / (T * CH * 32);
     if (ring > 8) ring = 8;
     if (ring > S) ring = S;
     while (ring >= 2 && lcm_i(lcm_i(DEC_GROUPS, Q), ring) > 15) --ring;
     if (ring < 2) return COX_ERR_ARG;
     g.H = Q;
     g.T = T;
+    g.CH = CH;
     g.NP = np_cls;
     g.ring = ring;
     g.nb_period = lcm_i(lcm_i(DEC_GROUPS, Q), ring);
@@ -602,8 +610,8 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
     g.smem = static_cast<size_t>(S) * stage + 1024 + 1024 + fold_bytes;
     if (g.smem < 120 * 1024) g.smem = 120 * 1024;  // one CTA per SM: it owns all 512 TMEM columns
     if (g.smem > 227 * 1024) return COX_ERR_ARG;    // too many stages requested
-    g.F = 64;  // K chunks per accumulation window: 64 x 8 / H MMAs into one accumulator
-    g.KC = static_cast<int>(K_pad / TILE);
+    g.F = 64 / CH;  // stages per accumulation window: 64 K chunks, 256 MMAs per accumulator
+    g.KC = static_cast<int>(K_pad / (TILE * CH));  // stages per group
     g.n_groups = static_cast<int>(m_tiles / T);
     g.units = static_cast<int64_t>(g.n_groups) * g.KC;
     int grid = h->sm_count;
@@ -618,7 +626,7 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
     g.max_slots = ms;
     g.rows_pad = rows_pad;
     {
-        KernelFn fn = pick_kernel(g.T, g.H, g.NP);
+        KernelFn fn = pick_kernel(g.T, g.H, g.CH, g.NP);
         if (!fn) return COX_ERR_ARG;
         COX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(g.smem)));
     }
@@ -626,10 +634,12 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
     EncodeTiled enc = get_encoder();
     if (!enc) return COX_ERR_CUDA;
     {
-        // a 4 KB block viewed as 4 rows of 1 KB; T consecutive row tiles per box
-        cuuint64_t dims[4] = {256, 4, static_cast<cuuint64_t>(g.KC), static_cast<cuuint64_t>(m_tiles)};
-        cuuint64_t strides[3] = {1024, BLOCK_BYTES, static_cast<cuuint64_t>(g.KC) * BLOCK_BYTES};
-        cuuint32_t box[4] = {256, 4, 1, static_cast<cuuint32_t>(T)};
+        // a 4 KB block viewed as 4 rows of 1 KB; CH consecutive chunks of T
+        // consecutive row tiles per box
+        const cuuint64_t kch = static_cast<cuuint64_t>(K_pad / TILE);
+        cuuint64_t dims[4] = {256, 4, kch, static_cast<cuuint64_t>(m_tiles)};
+        cuuint64_t strides[3] = {1024, BLOCK_BYTES, kch * BLOCK_BYTES};
+        cuuint32_t box[4] = {256, 4, static_cast<cuuint32_t>(CH), static_cast<cuuint32_t>(T)};
         cuuint32_t es[4] = {1, 1, 1, 1};
         CUresult r = enc(&g.tmA, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, const_cast<uint32_t *>(A), dims, strides,
                          box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -678,7 +688,7 @@ int launch_gemm(cox_handle *h, const GemmPlan &g, const EpiArgs &e, int k, cudaS
     kp.inv_n = e.inv_n;
     kp.wait_limit = h->wait_cycles;
     kp.err = h->d_err;
-    KernelFn fn = pick_kernel(g.T, g.H, g.NP);
+    KernelFn fn = pick_kernel(g.T, g.H, g.CH, g.NP);
     if (!fn) return COX_ERR_ARG;
     fn<<<g.grid, threads_for(g.T, g.H), g.smem, st>>>(g.tmA, g.tmB, kp);
     COX_CUDA(cudaGetLastError());

@@ -85,13 +85,14 @@ __host__ __device__ inline int64_t a4_pos(int64_t i, int64_t a, int64_t nb)
 struct GemmPlan {
     int T = 2;         // 128-row tiles per CTA (one M group)
     int H = 2;         // MMA-issuing warps per tile (each takes every H-th stage)
+    int CH = 1;        // K chunks (128 each) per stage
     int NP = 16;       // limb columns (limb_cols(k))
     int stages = 6;    // shared-memory pipeline depth
     int ring = 4;      // TMEM A buffers
     int nb_period = 6; // named barriers in use: lcm(decoder groups, H, ring)
     int F = 32;        // K chunks per TMEM accumulation window
     int grid = 0;      // CTAs
-    int KC = 0;        // K chunks
+    int KC = 0;        // stages per M group (K chunks / CH)
     int n_groups = 0;  // M groups
     int64_t units = 0, L = 0;
     int max_slots = 1;
