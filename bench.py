@@ -351,7 +351,9 @@ def run_ours(args, rank, world):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "vs_baseline": None, "dtype": "e4m3", "data": "synthetic",
+        "precision": "genotype products: codes and 4-limb split coefficients as e4m3 on tcgen05 "
+                     "(kind::f8f6f4), FP32 accumulation; risk-set scans and objective FP64",
         "config": {"workload": workload_name(r), "n": n, "p": p, "k": k,
                    "l2": "inputs larger than L2: 2 x ~50 GB of packed genotypes streamed per step",
                    "parallelism": "replicas" if world > 1 else "single GPU",

@@ -99,25 +99,27 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, long lo
 //                  warp 0 also allocates TMEM
 //   warps 2..I+1   MMA issuers: issuer j owns row tile t = j / Q and the stages
 //                  i = c (mod Q), c = j % Q, and accumulates them into its own
-//                  TMEM accumulator.  One thread issues at most one MMA per ~50
-//                  cycles and each barrier wait or commit costs it a few hundred,
-//                  so an issuer takes whole stages: 8 MMAs per wait and commit.
+//                  TMEM accumulator.  Every barrier wait or commit costs an
+//                  issuer a few hundred cycles, so it takes whole stages: 4 CH
+//                  MMAs (K = 32 each) per wait and commit.
 //   warps I+2..    G decoder groups of four warps (one per TMEM lane quarter);
 //                  group gamma decodes the stages i = gamma (mod G) into TMEM
 //                  slot i mod R.  Group 0 also adds the accumulators up at window
 //                  ends and runs the epilogue.
 // Hand-offs of stage i (shared-memory slot s = i mod S, TMEM slot r = i mod R):
 //   full[s]        mbarrier, TMA transaction bytes           producer -> decoders
-//   named 1+i%PB   hardware barrier: A slot written          decoders -> T issuers
+//   named 1+(i%PB)T+t  hardware barrier: tile t of the slot   decoders -> issuer of tile t
+//                  written (one barrier per tile, so the issuers of a stage do
+//                  not wait for one another)
 //   aempty[r]      tcgen05.commit of the T issuers           -> decoders of stage i+R
 //   empty[s]       one arrival by the decoders of stage i+R once they have seen
 //                  aempty for stage i (its MMAs, which read B and follow the
 //                  decoders' reads of X, are complete)       -> producer
 // PB = lcm(G, Q, R): each use of a named barrier has the same warps, and the
-// decoders of stage i+PB cannot arrive before the issuers of stage i have
-// passed it (they first wait, through the TMEM slot chain, for MMAs that those
-// issuers issue after it).  Decoders arrive on every path, so an issuer's
-// (unbounded) hardware-barrier wait always ends.
+// decoders of stage i+PB cannot arrive before the issuer of stage i has passed
+// it (they first wait, through the TMEM slot chain, for MMAs that this issuer
+// issues after it).  Decoders arrive on every path, so an issuer's (unbounded)
+// hardware-barrier wait always ends.
 template <int T, int Q, int CH, int NP, int G>
 __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
     k_packed_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -131,7 +133,7 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
     constexpr int ACC_COLS = I * NP;      // one accumulator per issuer
     constexpr int SLOT_COLS = T * CH * 32;  // 128 e4m3 A values per lane, tile and chunk
     constexpr int DEC0 = 2 + I;           // first decoder warp
-    constexpr int NB_COUNT = 32 * (4 + T);  // a decoder group and the stage's T issuer warps
+    constexpr int NB_COUNT = 32 * 5;      // a decoder group and the tile's issuer warp
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
             const bool last = (i == nu - 1) || (kc == KC - 1) || (wlen == F);
             if (own == c) {
                 __syncwarp();
-                named_sync(1 + nbid, NB_COUNT);
+                named_sync(1 + nbid * T + t, NB_COUNT);
                 if (ok && lane == 0) {
                     tc_fence_after();
                     const uint64_t dstage = desc0 + static_cast<uint64_t>((s * STAGE) >> 4);
@@ -449,12 +451,20 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
                         decode16(v.w, o + 16 * hh + 12);
                     }
                     tmem_st_32x32b_x32(acol + tc * 32, o);
+                    if (tc % CH == CH - 1) {
+                        // tile tc / CH is written: hand it to its issuer
+                        tmem_wait_st();
+                        tc_fence_before();
+                        __syncwarp();
+                        named_arrive(1 + nbid * T + tc / CH, NB_COUNT);
+                    }
                 }
-                tmem_wait_st();
+            } else {
+                // nothing written (error path): still arrive, so no issuer waits forever
+                __syncwarp();
+#pragma unroll
+                for (int tt = 0; tt < T; ++tt) named_arrive(1 + nbid * T + tt, NB_COUNT);
             }
-            tc_fence_before();
-            __syncwarp();
-            named_arrive(1 + nbid, NB_COUNT);
             if (!go && ok) {
                 ok = false;
                 if (lane == 0) fail(abort_sm, P.err);
@@ -594,11 +604,12 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
     if (S < DEC_GROUPS + 1) S = DEC_GROUPS + 1;  // decoder groups step through the stage ring by DEC_GROUPS
     // TMEM: T Q accumulators of NP columns, the rest A slots of T CH x 32 columns;
     // a slot's previous stage must still be in shared memory (ring <= S), and
-    // the named-barrier period lcm(G, Q, ring) must fit barriers 1..15
+    // the named barriers, one per tile for each stage of the period
+    // lcm(G, Q, ring), must fit barriers 1..15
     int ring = (512 - T * Q * np_cls) / (T * CH * 32);
     if (ring > 8) ring = 8;
     if (ring > S) ring = S;
-    while (ring >= 2 && lcm_i(lcm_i(DEC_GROUPS, Q), ring) > 15) --ring;
+    while (ring >= 2 && lcm_i(lcm_i(DEC_GROUPS, Q), ring) * T > 15) --ring;
     if (ring < 2) return COX_ERR_ARG;
     g.H = Q;
     g.T = T;
