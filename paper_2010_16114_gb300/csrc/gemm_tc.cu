@@ -376,23 +376,42 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
             epi_phase ^= 1u;
             if (!*last_sm) return;
             __threadfence();
+            // Each thread owns rows tid, tid + 128, ... of the group and walks the
+            // lambda columns; the loads of different columns are independent
+            // (restrict pointers), so they overlap.  FP32 arithmetic: the
+            // partials are FP32 and beta is stored in FP32.
             const int tid = threadIdx.x - 32 * DEC0;
-            const int64_t grows = static_cast<int64_t>(T) * TILE;
-            for (int64_t idx = tid; idx < grows * P.k; idx += 128) {
-                const int kk = static_cast<int>(idx / grows);
-                const int64_t row = static_cast<int64_t>(g) * grows + idx % grows;
-                if (row >= P.rows_valid) continue;
-                double Gs = 0.0;
-                for (int s2 = 0; s2 < cnt; ++s2) Gs += static_cast<double>(__ldcg(&P.part[s2 * P.slot_stride + kk * P.rows_pad + row]));
-                const double gv = (Gs - P.mu[row] * P.sumV[kk]) * P.inv_n;
-                const int64_t bi = static_cast<int64_t>(kk) * P.rows_valid + row;
-                if (P.epi == EPI_PROX) {
-                    if (P.active && !P.active[kk]) continue;
-                    const double z = static_cast<double>(P.beta[bi]) + P.step * gv;
-                    const double thr = P.step * P.lam[kk];
-                    P.beta[bi] = static_cast<float>(z > thr ? z - thr : (z < -thr ? z + thr : 0.0));
-                } else {
-                    P.grad[bi] = static_cast<float>(-gv);
+            constexpr int RPT = T * TILE / 128;  // rows per thread
+            const float *__restrict__ part = P.part;
+            float *__restrict__ beta = P.beta;
+            float *__restrict__ grad = P.grad;
+            const float inv_n = static_cast<float>(P.inv_n), stepf = static_cast<float>(P.step);
+            int64_t rows[RPT];
+            float muv[RPT];
+#pragma unroll
+            for (int rr = 0; rr < RPT; ++rr) {
+                rows[rr] = static_cast<int64_t>(g) * (T * TILE) + rr * 128 + tid;
+                muv[rr] = rows[rr] < P.rows_valid ? static_cast<float>(P.mu[rows[rr]]) : 0.f;
+            }
+#pragma unroll 4
+            for (int kk = 0; kk < P.k; ++kk) {
+                if (P.epi == EPI_PROX && P.active && !P.active[kk]) continue;
+                const float sv = static_cast<float>(P.sumV[kk]);
+                const float thr = static_cast<float>(P.step * P.lam[kk]);
+#pragma unroll
+                for (int rr = 0; rr < RPT; ++rr) {
+                    const int64_t row = rows[rr];
+                    if (row >= P.rows_valid) continue;
+                    float Gs = 0.f;
+                    for (int s2 = 0; s2 < cnt; ++s2) Gs += __ldcg(&part[s2 * P.slot_stride + kk * P.rows_pad + row]);
+                    const float gv = (Gs - muv[rr] * sv) * inv_n;
+                    const int64_t bi = static_cast<int64_t>(kk) * P.rows_valid + row;
+                    if (P.epi == EPI_PROX) {
+                        const float z = fmaf(stepf, gv, beta[bi]);
+                        beta[bi] = z > thr ? z - thr : (z < -thr ? z + thr : 0.f);
+                    } else {
+                        grad[bi] = -gv;
+                    }
                 }
             }
         };
