@@ -232,50 +232,63 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
         constexpr uint32_t idesc = idesc_e4m3_f32(128, NP);
         const uint32_t d = tbase + static_cast<uint32_t>(j * NP);
         const uint64_t desc0 = smem_desc_sw128(smem_addr(smem));
-        int s = 0, r = 0, kc = kc0, wlen = 0, own = 0, nbid = 0;
+        // The issuer is the critical thread of the pipeline: per stage it only
+        // waits, issues and commits.  Windows (at most F stages, never across
+        // a segment end) are sized once when they start.
+        const int bid_wrap = PB * T;
+        int s = 0, r = 0, kc = kc0, own = 0, bid = t;  // bid: named barrier id - 1
+        uint64_t dstage = desc0;
+        uint32_t aslot = tbase + static_cast<uint32_t>(ACC_COLS + t * CH * 32);
+        const uint32_t aslot0 = aslot;
         uint32_t eph = 0;
-        int64_t wi = -1;
-        bool ok = true, firstown = true;
-        for (int64_t i = 0; i < nu; ++i) {
-            if (i == 0 || kc == 0 || wlen == F) {
-                // window start: the accumulator is reused once group 0 has added
-                // up the previous window
-                ++wi;
-                wlen = 0;
-                firstown = true;
-                if (wi >= 1) {
-                    if (ok && !warp_wait(acce, eph, lim, abort_sm)) {
-                        ok = false;
-                        if (lane == 0) fail(abort_sm, P.err);
-                    }
-                    eph ^= 1u;
+        bool ok = true;
+        for (int64_t i = 0, wi = 0; i < nu; ++wi) {
+            const int wl = static_cast<int>(min(static_cast<int64_t>(min(F, KC - kc)), nu - i));
+            if (wi >= 1) {
+                // the accumulator is reused once group 0 has added up the previous window
+                if (ok && !warp_wait(acce, eph, lim, abort_sm)) {
+                    ok = false;
+                    if (lane == 0) fail(abort_sm, P.err);
                 }
+                eph ^= 1u;
             }
-            ++wlen;
-            const bool last = (i == nu - 1) || (kc == KC - 1) || (wlen == F);
-            if (own == c) {
-                __syncwarp();
-                named_sync(1 + nbid * T + t, NB_COUNT);
-                if (ok && lane == 0) {
-                    tc_fence_after();
-                    const uint64_t dstage = desc0 + static_cast<uint64_t>((s * STAGE) >> 4);
-                    const uint32_t a = tbase + static_cast<uint32_t>(ACC_COLS + r * SLOT_COLS + t * CH * 32);
+            bool first = true;
+            for (int e = 0; e < wl; ++e) {
+                if (own == c) {
+                    __syncwarp();
+                    named_sync(1 + bid, NB_COUNT);
+                    if (ok && lane == 0) {
+                        tc_fence_after();
 #pragma unroll
-                    for (int q = 0; q < 4 * CH; ++q) {
-                        // K = 32 per MMA: 32 bytes of every row of chunk panel q/4, 8 TMEM columns of A
-                        const uint64_t bd = dstage + static_cast<uint64_t>(((q >> 2) * NP * 128 + (q & 3) * 32) >> 4);
-                        mma_ts_f8(d, a + 8 * q, bd, idesc, (firstown && q == 0) ? 0u : 1u);
+                        for (int q = 0; q < 4 * CH; ++q) {
+                            // K = 32 per MMA: 32 bytes of every row of chunk panel q/4, 8 TMEM columns of A
+                            const uint64_t bd = dstage + static_cast<uint64_t>(((q >> 2) * NP * 128 + (q & 3) * 32) >> 4);
+                            mma_ts_f8(d, aslot + 8 * q, bd, idesc, (first && q == 0) ? 0u : 1u);
+                        }
+                        mma_commit(aempty0 + 8 * r);
                     }
-                    mma_commit(aempty0 + 8 * r);
+                    first = false;
                 }
-                firstown = false;
+                if (++s == S) {
+                    s = 0;
+                    dstage = desc0;
+                } else {
+                    dstage += static_cast<uint64_t>(STAGE >> 4);
+                }
+                if (++r == R) {
+                    r = 0;
+                    aslot = aslot0;
+                } else {
+                    aslot += SLOT_COLS;
+                }
+                if (++own == Q) own = 0;
+                bid += T;
+                if (bid >= bid_wrap) bid -= bid_wrap;
             }
-            if (last && ok && lane == 0) mma_commit(accf);
-            if (++s == S) s = 0;
-            if (++r == R) r = 0;
-            if (++kc == KC) kc = 0;
-            if (++own == Q) own = 0;
-            if (++nbid == PB) nbid = 0;
+            i += wl;
+            kc += wl;
+            if (kc == KC) kc = 0;
+            if (ok && lane == 0) mma_commit(accf);
         }
         __syncwarp();
         if (lane == 0) {
