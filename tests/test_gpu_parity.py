@@ -94,6 +94,23 @@ def test_loss_grad_geno(pkg, geno, precision, k):
             assert rel_l2(G[c], g_o) <= 1e-5, (c, rel_l2(G[c], g_o))
 
 
+@pytest.mark.parametrize("k", [3, 16])
+def test_loss_grad_multi_window(pkg, k):
+    """Row groups whose K range spans several accumulation windows (64 chunks
+    of 128) in both products, with ragged n and p: n = 9100, p = 8700."""
+    w, X, Xf, mu = dense_problem(1, n=9100, p=8700)
+    B = _random_betas(w.p, k, 29 + k)
+    with _problem(pkg, X, w, "split_e4m3") as prob:
+        beta = torch.tensor(B, dtype=torch.float32, device="cuda")
+        loss, grad = prob.loss_grad(beta)
+        G = grad.cpu().numpy()
+        for c in range(k):
+            bc = beta[c].cpu().numpy().astype(np.float64)
+            f_o, g_o = oracle_loss_grad(Xf, mu, w.y, w.delta, bc)
+            assert abs(loss[c] - f_o) <= 1e-7 * abs(f_o), (c, loss[c], f_o)
+            assert rel_l2(G[c], g_o) <= 1e-5, (c, rel_l2(G[c], g_o))
+
+
 @pytest.mark.parametrize("precision", ["split_e4m3", "fp32_gemv"])
 def test_prox_iterations_geno(pkg, geno, precision):
     """20 batched iterations for 3 penalties vs the oracle's iterates."""
