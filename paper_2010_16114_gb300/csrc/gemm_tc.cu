@@ -23,7 +23,7 @@
 // Pipeline per CTA (one per SM): two TMA warps fill a ring of shared-memory
 // stages (B chunk + T A blocks); groups of four decoder warps turn a stage into
 // e4m3 in a ring of TMEM slots, issuing all of a stage's tcgen05.st before one
-// wait; issuer warps (a tile and every Q-th stage each) issue the stage's MMAs
+// wait; one issuer warp per row tile issues the stage's MMAs
 // into their own accumulators and commit.  Decoders hand a slot to the issuers
 // through a hardware named barrier (tens of cycles, against a few hundred for
 // an mbarrier arrive and wait), and every wait or commit serves a whole stage.
@@ -94,12 +94,11 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, long lo
     return __all_sync(0xffffffffu, mbar_wait(bar, parity, lim, abort));
 }
 
-// Warp roles (WARPS = 2 + I + 4 G, I = T Q):
+// Warp roles (WARPS = 2 + T + 4 G):
 //   warps 0, 1     TMA producers (lane 0): warp w loads the stages i = w (mod 2);
 //                  warp 0 also allocates TMEM
-//   warps 2..I+1   MMA issuers: issuer j owns row tile t = j / Q and the stages
-//                  i = c (mod Q), c = j % Q, and accumulates them into its own
-//                  TMEM accumulator.  Every barrier wait or commit costs an
+//   warps 2..T+1   MMA issuers: issuer t owns row tile t and accumulates it
+//                  into its own TMEM accumulator.  Every barrier wait or commit costs an
 //                  issuer a few hundred cycles, so it takes whole stages: 4 CH
 //                  MMAs (K = 32 each) per wait and commit.
 //   warps I+2..    G decoder groups of four warps (one per TMEM lane quarter);
@@ -115,17 +114,17 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, long lo
 //   empty[s]       one arrival by the decoders of stage i+R once they have seen
 //                  aempty for stage i (its MMAs, which read B and follow the
 //                  decoders' reads of X, are complete)       -> producer
-// PB = lcm(G, Q, R): each use of a named barrier has the same warps, and the
+// PB = lcm(G, R): each use of a named barrier has the same warps, and the
 // decoders of stage i+PB cannot arrive before the issuer of stage i has passed
 // it (they first wait, through the TMEM slot chain, for MMAs that this issuer
 // issues after it).  Decoders arrive on every path, so an issuer's (unbounded)
 // hardware-barrier wait always ends.
-template <int T, int Q, int CH, int NP, int G>
-__global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
+template <int T, int CH, int NP, int G>
+__global__ void __launch_bounds__(32 * (2 + T + 4 * G), 1)
     k_packed_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const KParams P)
 {
-    constexpr int I = T * Q;              // MMA issuers
+    constexpr int I = T;                  // MMA issuers, one per row tile
     constexpr int KH = NP / LIMBS;        // lambda columns a decoder thread folds (>= k)
     constexpr int B_BYTES = CH * NP * 128;       // CH chunk panels of NP rows x 128 bytes
     constexpr int X_BYTES = T * CH * BLOCK_BYTES;  // [tile][chunk] 4 KB blocks
@@ -227,16 +226,15 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
         }
     } else if (warp < DEC0) {
         // ---------------- MMA issuers (whole warp; lane 0 issues) ----------------
-        const int j = warp - 2;
-        const int t = j / Q, c = j % Q;
+        const int t = warp - 2;
         constexpr uint32_t idesc = idesc_e4m3_f32(128, NP);
-        const uint32_t d = tbase + static_cast<uint32_t>(j * NP);
+        const uint32_t d = tbase + static_cast<uint32_t>(t * NP);
         const uint64_t desc0 = smem_desc_sw128(smem_addr(smem));
         // The issuer is the critical thread of the pipeline: per stage it only
         // waits, issues and commits.  Windows (at most F stages, never across
         // a segment end) are sized once when they start.
         const int bid_wrap = PB * T;
-        int s = 0, r = 0, kc = kc0, own = 0, bid = t;  // bid: named barrier id - 1
+        int s = 0, r = 0, kc = kc0, bid = t;  // bid: named barrier id - 1
         uint64_t dstage = desc0;
         uint32_t aslot = tbase + static_cast<uint32_t>(ACC_COLS + t * CH * 32);
         const uint32_t aslot0 = aslot;
@@ -252,22 +250,18 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
                 }
                 eph ^= 1u;
             }
-            bool first = true;
             for (int e = 0; e < wl; ++e) {
-                if (own == c) {
-                    __syncwarp();
-                    named_sync(1 + bid, NB_COUNT);
-                    if (ok && lane == 0) {
-                        tc_fence_after();
+                __syncwarp();
+                named_sync(1 + bid, NB_COUNT);
+                if (ok && lane == 0) {
+                    tc_fence_after();
 #pragma unroll
-                        for (int q = 0; q < 4 * CH; ++q) {
-                            // K = 32 per MMA: 32 bytes of every row of chunk panel q/4, 8 TMEM columns of A
-                            const uint64_t bd = dstage + static_cast<uint64_t>(((q >> 2) * NP * 128 + (q & 3) * 32) >> 4);
-                            mma_ts_f8(d, aslot + 8 * q, bd, idesc, (first && q == 0) ? 0u : 1u);
-                        }
-                        mma_commit(aempty0 + 8 * r);
+                    for (int q = 0; q < 4 * CH; ++q) {
+                        // K = 32 per MMA: 32 bytes of every row of chunk panel q/4, 8 TMEM columns of A
+                        const uint64_t bd = dstage + static_cast<uint64_t>(((q >> 2) * NP * 128 + (q & 3) * 32) >> 4);
+                        mma_ts_f8(d, aslot + 8 * q, bd, idesc, (e == 0 && q == 0) ? 0u : 1u);
                     }
-                    first = false;
+                    mma_commit(aempty0 + 8 * r);
                 }
                 if (++s == S) {
                     s = 0;
@@ -281,7 +275,6 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
                 } else {
                     aslot += SLOT_COLS;
                 }
-                if (++own == Q) own = 0;
                 bid += T;
                 if (bid >= bid_wrap) bid -= bid_wrap;
             }
@@ -314,9 +307,8 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
 
         // group 0: add the finished window's accumulators into registers; at a
         // segment end write this CTA's partial of group g and, for the last
-        // CTA, apply the epilogue.  Accumulator (t, c) holds the window's
-        // stages i = c (mod Q); one the window did not reach is skipped.
-        auto fold = [&](bool segend, int g, int64_t wst, int wl) {
+        // CTA, apply the epilogue.
+        auto fold = [&](bool segend, int g) {
             if (!ok) return;
             if (!warp_wait(accf, fold_phase, lim, abort_sm)) {
                 ok = false;
@@ -324,16 +316,13 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
             }
             fold_phase ^= 1u;
             tc_fence_after();
-#pragma unroll
-            for (int cq = 0; cq < Q; ++cq) {
-                const int m = (cq - static_cast<int>(wst % Q) + Q) % Q;
-                if (m >= wl) continue;
+            {
 #pragma unroll
                 for (int tt = 0; tt < T; ++tt) {
 #pragma unroll
                     for (int cc = 0; cc < NP / 8; ++cc) {
                         uint32_t v[8];
-                        tmem_ld_32x32b_x8(lane_base + static_cast<uint32_t>((tt * Q + cq) * NP + cc * 8), v);
+                        tmem_ld_32x32b_x8(lane_base + static_cast<uint32_t>(tt * NP + cc * 8), v);
                         tmem_wait_ld();
 #pragma unroll
                         for (int e = 0; e < 2; ++e) {  // two lambda columns of four limbs
@@ -432,16 +421,13 @@ __global__ void __launch_bounds__(32 * (2 + T * Q + 4 * G), 1)
         // window bookkeeping (group 0): walk every stage in order and fold each
         // window as soon as its last stage lies behind the stage being decoded
         int wkc = kc0, wg = g0, wlen = 0;
-        int64_t wnext = 0, wst = 0;
+        int64_t wnext = 0;
         auto fold_until = [&](int64_t upto) {  // stages [wnext, upto)
             for (; wnext < upto && wnext < nu && ok; ++wnext) {
-                if (wnext == 0 || wkc == 0 || wlen == F) {
-                    wlen = 0;
-                    wst = wnext;
-                }
+                if (wnext == 0 || wkc == 0 || wlen == F) wlen = 0;
                 ++wlen;
                 const bool seg = (wnext == nu - 1) || (wkc == KC - 1);
-                if (seg || wlen == F) fold(seg, wg, wst, wlen);
+                if (seg || wlen == F) fold(seg, wg);
                 if (++wkc == KC) {
                     wkc = 0;
                     ++wg;
@@ -583,34 +569,32 @@ using KernelFn = void (*)(const CUtensorMap, const CUtensorMap, const KParams);
 
 constexpr int DEC_GROUPS = 3;
 
-// (T row tiles per stage, Q issuers per tile) for a limb-column class NP.
-// A stage of a tile is 4 MMAs (K = 32 each), which one issuer keeps up with
-// (~50-60 cycles per instruction from one thread); one issuer per tile leaves
-// the most TMEM to the A slot ring.  N = 256 fills half of TMEM per
-// accumulator, so that class takes one tile per stage.
+// (T row tiles, CH K chunks) per stage for a limb-column class NP.  One issuer
+// per tile leaves the most TMEM to the A slot ring (a second issuer per tile
+// needs a second accumulator).  N = 256 fills half of TMEM per accumulator,
+// so that class takes one tile per stage.
 // A stage spans CH K chunks: every hand-off costs a few hundred cycles
 // whatever its size, so up to N = 64 a stage takes two chunks (16 KB of codes
 // at T = 2), which keeps the same bytes in TMEM with half the hand-offs.
-void shape_for(int NP, int *T, int *Q, int *CH)
+void shape_for(int NP, int *T, int *CH)
 {
-    *Q = 1;
     *T = NP <= 128 ? 2 : 1;
     *CH = NP <= 64 ? 2 : 1;
 }
 
-KernelFn pick_kernel(int T, int Q, int CH, int NP)
+KernelFn pick_kernel(int T, int CH, int NP)
 {
-    switch (((T * 10 + Q) * 10 + CH) * 1000 + NP) {
-    case 212016: return k_packed_gemm<2, 1, 2, 16, DEC_GROUPS>;
-    case 212032: return k_packed_gemm<2, 1, 2, 32, DEC_GROUPS>;
-    case 212064: return k_packed_gemm<2, 1, 2, 64, DEC_GROUPS>;
-    case 211128: return k_packed_gemm<2, 1, 1, 128, DEC_GROUPS>;
-    case 111256: return k_packed_gemm<1, 1, 1, 256, DEC_GROUPS>;
+    switch ((T * 10 + CH) * 1000 + NP) {
+    case 22016: return k_packed_gemm<2, 2, 16, DEC_GROUPS>;
+    case 22032: return k_packed_gemm<2, 2, 32, DEC_GROUPS>;
+    case 22064: return k_packed_gemm<2, 2, 64, DEC_GROUPS>;
+    case 21128: return k_packed_gemm<2, 1, 128, DEC_GROUPS>;
+    case 11256: return k_packed_gemm<1, 1, 256, DEC_GROUPS>;
     default: return nullptr;
     }
 }
 
-int threads_for(int T, int Q) { return 32 * (2 + T * Q + 4 * DEC_GROUPS); }
+int threads_for(int T) { return 32 * (2 + T + 4 * DEC_GROUPS); }
 
 int gcd_i(int a, int b) { return b ? gcd_i(b, a % b) : a; }
 int lcm_i(int a, int b) { return a / gcd_i(a, b) * b; }
@@ -618,7 +602,7 @@ int lcm_i(int a, int b) { return a / gcd_i(a, b) * b; }
 } // namespace
 
 // Plan one product: A (rows_pad x K_pad, tiled 2-bit) times B limbs (NP x K_pad).
-// TMEM budget (512 columns): T Q NP accumulator columns + ring x T x 32 A columns.
+// TMEM budget (512 columns): T NP accumulator columns + ring x T CH x 32 A columns.
 int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, int64_t K_pad,
               const uint8_t *B, int k, int T_req, int stages_req)
 {
@@ -626,29 +610,28 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
     const int np_cls = limb_cols(k);
     const int64_t m_tiles = rows_pad / TILE;
     (void)T_req;  // the row-tile count follows from the limb-column class
-    int T = 2, Q = 1, CH = 1;
-    shape_for(np_cls, &T, &Q, &CH);
+    int T = 2, CH = 1;
+    shape_for(np_cls, &T, &CH);
     if (m_tiles % T != 0 || (K_pad / TILE) % CH != 0) return COX_ERR_ARG;
     const int stage = CH * (np_cls * 128 + T * BLOCK_BYTES);
     const int fold_bytes = T * (np_cls / LIMBS) * 128 * 4;  // group 0's window sums
     int S = stages_req > 0 ? stages_req : (225 * 1024 - 2048 - fold_bytes) / stage;
     if (S > 12) S = 12;
     if (S < DEC_GROUPS + 1) S = DEC_GROUPS + 1;  // decoder groups step through the stage ring by DEC_GROUPS
-    // TMEM: T Q accumulators of NP columns, the rest A slots of T CH x 32 columns;
+    // TMEM: T accumulators of NP columns, the rest A slots of T CH x 32 columns;
     // a slot's previous stage must still be in shared memory (ring <= S), and
     // the named barriers, one per tile for each stage of the period
-    // lcm(G, Q, ring), must fit barriers 1..15
-    int ring = (512 - T * Q * np_cls) / (T * CH * 32);
+    // lcm(G, ring), must fit barriers 1..15
+    int ring = (512 - T * np_cls) / (T * CH * 32);
     if (ring > 8) ring = 8;
     if (ring > S) ring = S;
-    while (ring >= 2 && lcm_i(lcm_i(DEC_GROUPS, Q), ring) * T > 15) --ring;
+    while (ring >= 2 && lcm_i(DEC_GROUPS, ring) * T > 15) --ring;
     if (ring < 2) return COX_ERR_ARG;
-    g.H = Q;
     g.T = T;
     g.CH = CH;
     g.NP = np_cls;
     g.ring = ring;
-    g.nb_period = lcm_i(lcm_i(DEC_GROUPS, Q), ring);
+    g.nb_period = lcm_i(DEC_GROUPS, ring);
     g.stages = S;
     g.smem = static_cast<size_t>(S) * stage + 1024 + 1024 + fold_bytes;
     if (g.smem < 120 * 1024) g.smem = 120 * 1024;  // one CTA per SM: it owns all 512 TMEM columns
@@ -669,7 +652,7 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
     g.max_slots = ms;
     g.rows_pad = rows_pad;
     {
-        KernelFn fn = pick_kernel(g.T, g.H, g.CH, g.NP);
+        KernelFn fn = pick_kernel(g.T, g.CH, g.NP);
         if (!fn) return COX_ERR_ARG;
         COX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(g.smem)));
     }
@@ -731,9 +714,9 @@ int launch_gemm(cox_handle *h, const GemmPlan &g, const EpiArgs &e, int k, cudaS
     kp.inv_n = e.inv_n;
     kp.wait_limit = h->wait_cycles;
     kp.err = h->d_err;
-    KernelFn fn = pick_kernel(g.T, g.H, g.CH, g.NP);
+    KernelFn fn = pick_kernel(g.T, g.CH, g.NP);
     if (!fn) return COX_ERR_ARG;
-    fn<<<g.grid, threads_for(g.T, g.H), g.smem, st>>>(g.tmA, g.tmB, kp);
+    fn<<<g.grid, threads_for(g.T), g.smem, st>>>(g.tmA, g.tmB, kp);
     COX_CUDA(cudaGetLastError());
     return COX_OK;
 }

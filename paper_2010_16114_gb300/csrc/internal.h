@@ -84,12 +84,11 @@ __host__ __device__ inline int64_t a4_pos(int64_t i, int64_t a, int64_t nb)
 // One tensor-core product: a 2-bit A (rows x K, tiled) times limb matrix B.
 struct GemmPlan {
     int T = 2;         // 128-row tiles per CTA (one M group)
-    int H = 2;         // MMA-issuing warps per tile (each takes every H-th stage)
     int CH = 1;        // K chunks (128 each) per stage
     int NP = 16;       // limb columns (limb_cols(k))
     int stages = 6;    // shared-memory pipeline depth
     int ring = 4;      // TMEM A buffers
-    int nb_period = 6; // named barriers in use: lcm(decoder groups, H, ring)
+    int nb_period = 6; // stage period of the named barriers: lcm(decoder groups, ring)
     int F = 32;        // K chunks per TMEM accumulation window
     int grid = 0;      // CTAs
     int KC = 0;        // stages per M group (K chunks / CH)
