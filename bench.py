@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--k", type=int, default=None)
     ap.add_argument("--tile-m", type=int, default=0)
     ap.add_argument("--stages", type=int, default=0)
+    ap.add_argument("--chunks", type=int, default=0)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip cox_autotune (the pipeline shapes then come from the built-in default)")
     ap.add_argument("--gemv-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -243,13 +246,16 @@ def run_ours(args, rank, world):
     packed = torch.empty((n, (p + 3) // 4), dtype=torch.uint8, device="cuda")
     w.packed_rows_device(packed.data_ptr(), stream.cuda_stream, thr.data_ptr())
     torch.cuda.synchronize()
-    prob = CoxProblem(packed, w.y, w.delta, p=p, precision="split_e4m3", tile_m=args.tile_m, stages=args.stages)
+    prob = CoxProblem(packed, w.y, w.delta, p=p, precision="split_e4m3", tile_m=args.tile_m, stages=args.stages,
+                      chunks=args.chunks)
     del packed, thr
     torch.cuda.empty_cache()
     lmax = prob.lambda_max()
     L = prob.lipschitz(tol=1e-4, maxiter=100)
     step = 1.0 / L
     lams = lmax * r.lambda_fracs()
+    forced = args.tile_m or args.chunks or args.stages
+    tune = None if (args.no_autotune or forced) else prob.autotune(k, reps=2)
     t_setup = time.perf_counter() - t_setup0
 
     beta = prob.zeros(k)
@@ -277,7 +283,8 @@ def run_ours(args, rank, world):
     prob.profile(False)
     prob.sync()
     cls_ms, cls_n = prob.profile_read()
-    launches = prob.info()["launches"] - launches0
+    pinfo = prob.info()
+    launches = pinfo["launches"] - launches0
     F_last = prob.last_objective(k)
     ms_max = max_over_ranks(ms, world)
     ms_step = ms_max / args.steps
@@ -357,7 +364,9 @@ def run_ours(args, rank, world):
         "config": {"workload": workload_name(r), "n": n, "p": p, "k": k,
                    "l2": "inputs larger than L2: 2 x ~50 GB of packed genotypes streamed per step",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "step_size": step, "lambda_max": lmax},
+                   "step_size": step, "lambda_max": lmax,
+                   "pipeline": {"autotune": tune,
+                                "x_b_in_use": {f: pinfo[f] for f in ("tile_m", "chunks", "stages", "ring")}}},
         "lambda_iters_per_s": value * k,
         "hbm_gbs": iter_bytes / (ms_step / 1e3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -83,11 +83,15 @@ typedef struct cox_options {
     int precision;        /* COX_SPLIT_E4M3 (default), COX_FP64, COX_FP32_GEMV       */
     int center;           /* 1: X_c = X - 1 mu^T (default 1; COX_FP64 default 0)    */
     int device;           /* CUDA device ordinal (default: current device)           */
-    int tile_m;           /* 128-row tiles per CTA in the tensor-core products;
-                             0 = choose automatically (autotuned table)              */
+    int tile_m;           /* 128-row tiles per pipeline stage of the tensor-core
+                             products (1 or 2); 0 = automatic: the cox_autotune
+                             choice for the call's k if there is one, else a
+                             built-in default                                       */
     int stages;           /* shared-memory pipeline depth; 0 = automatic             */
     int lag;              /* stopping-rule lag in iterations (default 10, Section 6) */
     double wait_limit_s;  /* device-side wait limit in seconds (default 2.0)         */
+    int chunks;           /* 128-wide K chunks per pipeline stage (1 or 2);
+                             0 = automatic, as tile_m                               */
 } cox_options;
 
 /* Fill *opt with the defaults above. */
@@ -213,8 +217,27 @@ typedef struct cox_info {
     int64_t device_bytes;
     int64_t n_tie_groups;
     int64_t launches;
+    int chunks, ring;     /* K chunks per stage and TMEM slots of the X B product  */
 } cox_info;
 int cox_get_info(cox_h h, cox_info *info);
+
+/*
+ * Autotuner of the tensor-core products (COX_SPLIT_E4M3 handles).  For k
+ * coefficient columns it times every compiled pipeline shape (row tiles and
+ * K chunks per stage, and two shared-memory depths) of both products on the
+ * handle's resident genotypes: one warm-up and `reps` launches each, CUDA
+ * events on the legacy stream, partial outputs only (no coefficient
+ * changes).  The fastest shape per product is kept for k and used by later
+ * calls with k columns unless cox_options forces tile_m, chunks or stages.
+ * xb / xtv (either may be NULL) receive the choice and its mean launch time.
+ * Drops the per-k workspace.  Synchronous.  Errors: COX_ERR_UNSUPPORTED for
+ * other precisions; COX_ERR_ARG for k outside 1..64 or reps < 1.
+ */
+typedef struct cox_tune_choice {
+    int tile_m, chunks, stages, candidates;
+    double ms;
+} cox_tune_choice;
+int cox_autotune(cox_h h, int k, int reps, cox_tune_choice *xb, cox_tune_choice *xtv);
 
 /* Switch a genotype handle between COX_SPLIT_E4M3 and COX_FP32_GEMV; both
  * read the same resident tiles.  Drops the per-k workspace.  Errors:

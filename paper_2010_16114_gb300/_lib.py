@@ -36,13 +36,14 @@ EXPORTS = [
     "cox_loss_grad", "cox_prox_step", "cox_prox_step_host", "cox_sync", "cox_last_objective",
     "cox_path_fit", "cox_get_state", "cox_set_state", "cox_get_info", "cox_get_mu_order",
     "cox_strerror", "cox_set_precision", "cox_profile", "cox_profile_read", "cox_lipschitz_noalloc",
+    "cox_autotune",
 ]
 
 
 class cox_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("center", ctypes.c_int), ("device", ctypes.c_int),
                 ("tile_m", ctypes.c_int), ("stages", ctypes.c_int), ("lag", ctypes.c_int),
-                ("wait_limit_s", ctypes.c_double)]
+                ("wait_limit_s", ctypes.c_double), ("chunks", ctypes.c_int)]
 
 
 class cox_info(ctypes.Structure):
@@ -50,7 +51,12 @@ class cox_info(ctypes.Structure):
                 ("p_pad", ctypes.c_int64), ("precision", ctypes.c_int), ("center", ctypes.c_int),
                 ("tile_m", ctypes.c_int), ("stages", ctypes.c_int), ("sm_count", ctypes.c_int),
                 ("device_bytes", ctypes.c_int64), ("n_tie_groups", ctypes.c_int64),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("chunks", ctypes.c_int), ("ring", ctypes.c_int)]
+
+
+class cox_tune_choice(ctypes.Structure):
+    _fields_ = [("tile_m", ctypes.c_int), ("chunks", ctypes.c_int), ("stages", ctypes.c_int),
+                ("candidates", ctypes.c_int), ("ms", ctypes.c_double)]
 
 
 class CoxError(RuntimeError):
@@ -110,6 +116,8 @@ def load(path: str | None = None):
     lib.cox_profile.argtypes = [P, I]
     lib.cox_profile_read.restype = I
     lib.cox_profile_read.argtypes = [P, P, P]
+    lib.cox_autotune.restype = I
+    lib.cox_autotune.argtypes = [P, I, I, ctypes.POINTER(cox_tune_choice), ctypes.POINTER(cox_tune_choice)]
     lib.cox_strerror.restype = ctypes.c_char_p
     lib.cox_strerror.argtypes = [I]
     _lib = lib
@@ -219,6 +227,12 @@ def cox_profile(h, enable: int) -> int:
 
 def cox_profile_read(h, ms_ptr, launches_ptr) -> int:
     return load().cox_profile_read(h, ms_ptr, launches_ptr)
+
+
+def cox_autotune(h, k: int, reps: int):
+    xb, xtv = cox_tune_choice(), cox_tune_choice()
+    rc = load().cox_autotune(h, k, reps, ctypes.byref(xb), ctypes.byref(xtv))
+    return rc, xb, xtv
 
 
 def cox_strerror(code: int) -> str:

@@ -45,7 +45,7 @@ class CoxProblem:
 
     def __init__(self, X, time, event, precision: str = "split_e4m3", center: bool | None = None,
                  p: int | None = None, device: int | None = None, tile_m: int = 0, stages: int = 0,
-                 lag: int = 10, wait_limit_s: float = 2.0):
+                 lag: int = 10, wait_limit_s: float = 2.0, chunks: int = 0):
         lib = L.load()
         opt = L.cox_default_options()
         opt.precision = PRECISIONS[precision]
@@ -53,6 +53,7 @@ class CoxProblem:
         opt.device = -1 if device is None else int(device)
         opt.tile_m = int(tile_m)
         opt.stages = int(stages)
+        opt.chunks = int(chunks)
         opt.lag = int(lag)
         opt.wait_limit_s = float(wait_limit_s)
         time = np.ascontiguousarray(time, dtype=np.float64)
@@ -118,6 +119,14 @@ class CoxProblem:
         """Switch between "split_e4m3" and "fp32_gemv" on the same resident data."""
         L.check(L.cox_set_precision(self.h, PRECISIONS[precision]), "cox_set_precision")
         self.precision = precision
+
+    def autotune(self, k: int, reps: int = 3):
+        """Time every compiled pipeline shape of both products for k columns and
+        keep the fastest (cox_autotune); returns the choices."""
+        rc, xb, xtv = L.cox_autotune(self.h, int(k), int(reps))
+        L.check(rc, "cox_autotune")
+        f = [n for n, _ in L.cox_tune_choice._fields_]
+        return {"x_b": {n: getattr(xb, n) for n in f}, "xt_v": {n: getattr(xtv, n) for n in f}}
 
     def profile(self, enable: bool):
         L.check(L.cox_profile(self.h, int(enable)), "cox_profile")

@@ -342,8 +342,18 @@ int ensure_workspace(cox_handle *h, int k)
         cudaMemset(ws.Bq, 0, static_cast<size_t>(NP) * h->p_pad);
         cudaMemset(ws.Vq, 0, static_cast<size_t>(NP) * h->n_pad);
         ws.NP = NP;
-        if ((r = plan_gemm(h, ws.g1, h->d_A1, h->n_pad, h->p_pad, ws.Bq, k, h->opt.tile_m, h->opt.stages)) != COX_OK ||
-            (r = plan_gemm(h, ws.g4, h->d_A4, h->p_pad, h->n_pad, ws.Vq, k, h->opt.tile_m, h->opt.stages)) != COX_OK) {
+        cudaMemset(ws.bs1, 0, k * sizeof(int));
+        cudaMemset(ws.bs4, 0, k * sizeof(int));
+        // pipeline shapes: forced by the options, else autotuned for k, else default
+        int T1 = h->opt.tile_m, C1 = h->opt.chunks, S1 = h->opt.stages;
+        int T4 = T1, C4 = C1, S4 = S1;
+        const auto tc = h->tuned.find(k);
+        if (tc != h->tuned.end() && !T1 && !C1 && !S1) {
+            T1 = tc->second.T1, C1 = tc->second.CH1, S1 = tc->second.S1;
+            T4 = tc->second.T4, C4 = tc->second.CH4, S4 = tc->second.S4;
+        }
+        if ((r = plan_gemm(h, ws.g1, h->d_A1, h->n_pad, h->p_pad, ws.Bq, k, T1, C1, S1)) != COX_OK ||
+            (r = plan_gemm(h, ws.g4, h->d_A4, h->p_pad, h->n_pad, ws.Vq, k, T4, C4, S4)) != COX_OK) {
             free_workspace(h);
             return r;
         }
@@ -383,6 +393,7 @@ void cox_default_options(cox_options *opt)
     opt->device = -1;
     opt->tile_m = 0;
     opt->stages = 0;
+    opt->chunks = 0;
     opt->lag = 10;
     opt->wait_limit_s = 2.0;
 }
@@ -430,7 +441,7 @@ int cox_setup(cox_h *out, const void *X, int64_t n, int64_t p, int x_format, con
     if ((opt.precision == COX_FP64) != (x_format == COX_X_F64_HOST)) return COX_ERR_UNSUPPORTED;
     if (x_format < COX_X_INT8_HOST || x_format > COX_X_PACKED2_DEV) return COX_ERR_ARG;
     if (opt.lag < 1 || !(opt.wait_limit_s >= 0.0)) return COX_ERR_ARG;
-    if (opt.tile_m != 0 && opt.tile_m != 1 && opt.tile_m != 2 && opt.tile_m != 4 && opt.tile_m != 8) return COX_ERR_ARG;
+    if (opt.tile_m < 0 || opt.tile_m > 2 || opt.chunks < 0 || opt.chunks > 2 || opt.stages < 0) return COX_ERR_ARG;
     for (int64_t i = 0; i < n; ++i) {
         if (!std::isfinite(time[i])) return COX_ERR_ARG;
         if (event[i] > 1) return COX_ERR_ARG;
@@ -538,6 +549,82 @@ int cox_get_info(cox_h h, cox_info *info)
     info->device_bytes = h->device_bytes;
     info->n_tie_groups = h->n_groups_tie;
     info->launches = h->launches;
+    info->chunks = h->ws.k ? h->ws.g1.CH : h->opt.chunks;
+    info->ring = h->ws.k ? h->ws.g1.ring : 0;
+    return COX_OK;
+}
+
+int cox_autotune(cox_h h, int k, int reps, cox_tune_choice *xb, cox_tune_choice *xtv)
+{
+    if (!h) return COX_ERR_ARG;
+    if (!is_split(h)) return COX_ERR_UNSUPPORTED;
+    if (k < 1 || k > MAX_K_TC || reps < 1) return COX_ERR_ARG;
+    DeviceGuard guard(h->dev);
+    h->tuned.erase(k);
+    COX_TRY(ensure_workspace(h, k));  // limb buffers (zero) and scale arrays for the timing launches
+    Workspace &ws = h->ws;
+    int Ts[8], Cs[8];
+    const int nshape = gemm_shapes(k, Ts, Cs, 8);
+    const int depth_req[2] = {0, 4};  // deepest, and the shallowest the three decoder groups allow
+    cox_tune_choice best[2];
+    int cand[2] = {0, 0};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    COX_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return COX_ERR_CUDA;
+    }
+    int rc = COX_OK;
+    for (int prod = 0; prod < 2 && rc == COX_OK; ++prod) {
+        best[prod] = cox_tune_choice{0, 0, 0, 0, 1e300};
+        const uint32_t *A = prod == 0 ? h->d_A1 : h->d_A4;
+        const int64_t rows = prod == 0 ? h->n_pad : h->p_pad, K = prod == 0 ? h->p_pad : h->n_pad;
+        const uint8_t *B = prod == 0 ? ws.Bq : ws.Vq;
+        for (int j = 0; j < nshape && rc == COX_OK; ++j) {
+            int last_S = -1;
+            for (int dq = 0; dq < 2 && rc == COX_OK; ++dq) {
+                GemmPlan g;
+                if (plan_gemm(h, g, A, rows, K, B, k, Ts[j], Cs[j], depth_req[dq]) != COX_OK) continue;
+                if (g.stages == last_S) continue;  // the two depths coincide
+                last_S = g.stages;
+                float *part = nullptr;
+                if ((rc = dmalloc(nullptr, reinterpret_cast<void **>(&part),
+                                  static_cast<size_t>(g.max_slots) * k * rows * sizeof(float))) != COX_OK)
+                    break;
+                EpiArgs e;
+                e.epi = EPI_PARTIAL;
+                e.part = part;
+                e.bscale = prod == 0 ? ws.bs1 : ws.bs4;
+                float ms = 0.f;
+                bool good = launch_gemm(h, g, e, k, 0) == COX_OK;
+                good = good && cudaEventRecord(e0, 0) == cudaSuccess;
+                for (int q = 0; q < reps && good; ++q) good = launch_gemm(h, g, e, k, 0) == COX_OK;
+                good = good && cudaEventRecord(e1, 0) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                       cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+                h->launches += reps + 1;
+                dfree(part);
+                if (!good) {
+                    rc = COX_ERR_CUDA;
+                    break;
+                }
+                if ((rc = check_device_error(h, 0)) != COX_OK) break;
+                ++cand[prod];
+                const double m = static_cast<double>(ms) / reps;
+                if (m < best[prod].ms) best[prod] = cox_tune_choice{g.T, g.CH, g.stages, 0, m};
+            }
+        }
+        best[prod].candidates = cand[prod];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != COX_OK) return rc;
+    if (!cand[0] || !cand[1]) return COX_ERR_ARG;
+    h->tuned[k] = cox_handle::TuneChoice{best[0].tile_m, best[0].chunks, best[0].stages,
+                                         best[1].tile_m, best[1].chunks, best[1].stages};
+    cudaDeviceSynchronize();
+    free_workspace(h);  // the next call with k columns plans the chosen shapes
+    if (xb) *xb = best[0];
+    if (xtv) *xtv = best[1];
     return COX_OK;
 }
 

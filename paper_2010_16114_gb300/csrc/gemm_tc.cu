@@ -558,7 +558,7 @@ EncodeTiled get_encoder()
     if (!fn) {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             fn = reinterpret_cast<EncodeTiled>(p);
     }
@@ -576,6 +576,7 @@ constexpr int DEC_GROUPS = 3;
 // A stage spans CH K chunks: every hand-off costs a few hundred cycles
 // whatever its size, so up to N = 64 a stage takes two chunks (16 KB of codes
 // at T = 2), which keeps the same bytes in TMEM with half the hand-offs.
+// This is the default; the autotuner times every compiled shape instead.
 void shape_for(int NP, int *T, int *CH)
 {
     *T = NP <= 128 ? 2 : 1;
@@ -586,9 +587,17 @@ KernelFn pick_kernel(int T, int CH, int NP)
 {
     switch ((T * 10 + CH) * 1000 + NP) {
     case 22016: return k_packed_gemm<2, 2, 16, DEC_GROUPS>;
+    case 21016: return k_packed_gemm<2, 1, 16, DEC_GROUPS>;
+    case 12016: return k_packed_gemm<1, 2, 16, DEC_GROUPS>;
     case 22032: return k_packed_gemm<2, 2, 32, DEC_GROUPS>;
+    case 21032: return k_packed_gemm<2, 1, 32, DEC_GROUPS>;
+    case 12032: return k_packed_gemm<1, 2, 32, DEC_GROUPS>;
     case 22064: return k_packed_gemm<2, 2, 64, DEC_GROUPS>;
+    case 21064: return k_packed_gemm<2, 1, 64, DEC_GROUPS>;
+    case 12064: return k_packed_gemm<1, 2, 64, DEC_GROUPS>;
     case 21128: return k_packed_gemm<2, 1, 128, DEC_GROUPS>;
+    case 12128: return k_packed_gemm<1, 2, 128, DEC_GROUPS>;
+    case 11128: return k_packed_gemm<1, 1, 128, DEC_GROUPS>;
     case 11256: return k_packed_gemm<1, 1, 256, DEC_GROUPS>;
     default: return nullptr;
     }
@@ -601,17 +610,33 @@ int lcm_i(int a, int b) { return a / gcd_i(a, b) * b; }
 
 } // namespace
 
+int gemm_shapes(int k, int *T, int *CH, int max)
+{
+    const int NP = limb_cols(k);
+    int n = 0;
+    for (int t = 2; t >= 1; --t)
+        for (int c = 2; c >= 1; --c)
+            if (pick_kernel(t, c, NP) && n < max) {
+                T[n] = t;
+                CH[n] = c;
+                ++n;
+            }
+    return n;
+}
+
 // Plan one product: A (rows_pad x K_pad, tiled 2-bit) times B limbs (NP x K_pad).
 // TMEM budget (512 columns): T NP accumulator columns + ring x T CH x 32 A columns.
 int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, int64_t K_pad,
-              const uint8_t *B, int k, int T_req, int stages_req)
+              const uint8_t *B, int k, int T_req, int CH_req, int stages_req)
 {
     if (k < 1 || k > MAX_K_TC) return COX_ERR_ARG;
     const int np_cls = limb_cols(k);
     const int64_t m_tiles = rows_pad / TILE;
-    (void)T_req;  // the row-tile count follows from the limb-column class
     int T = 2, CH = 1;
     shape_for(np_cls, &T, &CH);
+    if (T_req > 0) T = T_req;
+    if (CH_req > 0) CH = CH_req;
+    if (!pick_kernel(T, CH, np_cls)) return COX_ERR_ARG;  // shape not compiled for this class
     if (m_tiles % T != 0 || (K_pad / TILE) % CH != 0) return COX_ERR_ARG;
     const int stage = CH * (np_cls * 128 + T * BLOCK_BYTES);
     const int fold_bytes = T * (np_cls / LIMBS) * 128 * 4;  // group 0's window sums
@@ -619,12 +644,14 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
     if (S > 12) S = 12;
     if (S < DEC_GROUPS + 1) S = DEC_GROUPS + 1;  // decoder groups step through the stage ring by DEC_GROUPS
     // TMEM: T accumulators of NP columns, the rest A slots of T CH x 32 columns;
-    // a slot's previous stage must still be in shared memory (ring <= S), and
+    // the decoders of stage i free the shared memory of stage i - ring, which
+    // the producer needs for stage i - ring + S: ring < S, or the producer of
+    // stage i would wait for the decoders of stage i, who wait for it; and
     // the named barriers, one per tile for each stage of the period
     // lcm(G, ring), must fit barriers 1..15
     int ring = (512 - T * np_cls) / (T * CH * 32);
     if (ring > 8) ring = 8;
-    if (ring > S) ring = S;
+    if (ring > S - 1) ring = S - 1;
     while (ring >= 2 && lcm_i(DEC_GROUPS, ring) * T > 15) --ring;
     if (ring < 2) return COX_ERR_ARG;
     g.T = T;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <vector>
 
 #include "../../include/coxgb.h"
@@ -166,6 +167,11 @@ struct cox_handle {
     std::vector<double> st_F;
     std::vector<int> st_active;
     int64_t st_step = 0;
+    // autotuned pipeline shapes per k: row tiles, K chunks, stages of each product
+    struct TuneChoice {
+        int T1, CH1, S1, T4, CH4, S4;
+    };
+    std::map<int, TuneChoice> tuned;
     // launch accounting and optional per-kernel-class event timing
     int64_t launches = 0;
     bool prof = false;
@@ -225,8 +231,11 @@ struct ScanArgs {
 int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st);
 
 // ---- tensor-core products (gemm_tc.cu) ---------------------------------------------
+// Plan one product; T_req / CH_req / stages_req of 0 take the defaults.
 int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, int64_t K_pad,
-              const uint8_t *B, int k, int T_req, int stages_req);
+              const uint8_t *B, int k, int T_req, int CH_req, int stages_req);
+// The compiled (row tiles, K chunks) shapes for k columns; returns their count.
+int gemm_shapes(int k, int *T, int *CH, int max);
 enum Epi { EPI_PARTIAL = 0, EPI_PROX = 1, EPI_GRAD = 2 };
 struct EpiArgs {
     int epi = EPI_PARTIAL;

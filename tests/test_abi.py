@@ -48,6 +48,30 @@ def test_strerror_and_defaults(lib):
     assert L.strerror(12345) == "unknown error"
     o = L.cox_default_options()
     assert o.precision == L.COX_SPLIT_E4M3 and o.center == 1 and o.lag == 10 and o.wait_limit_s == 2.0
+    assert o.tile_m == 0 and o.chunks == 0 and o.stages == 0
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the header's structs have the C sizes and offsets."""
+    import subprocess
+    from paper_2010_16114_gb300 import _lib as L
+    structs = {"cox_options": L.cox_options, "cox_info": L.cox_info, "cox_tune_choice": L.cox_tune_choice}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "coxgb.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         check=True).stdout.split("\n") if l)
+    for name, cls in structs.items():
+        assert int(out[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(out[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
 
 
 def test_argument_errors_without_gpu(lib):

@@ -94,11 +94,16 @@ def test_loss_grad_geno(pkg, geno, precision, k):
             assert rel_l2(G[c], g_o) <= 1e-5, (c, rel_l2(G[c], g_o))
 
 
+@pytest.fixture(scope="module")
+def multi_window():
+    return dense_problem(1, n=9100, p=8700)
+
+
 @pytest.mark.parametrize("k", [3, 16])
-def test_loss_grad_multi_window(pkg, k):
+def test_loss_grad_multi_window(pkg, multi_window, k):
     """Row groups whose K range spans several accumulation windows (64 chunks
     of 128) in both products, with ragged n and p: n = 9100, p = 8700."""
-    w, X, Xf, mu = dense_problem(1, n=9100, p=8700)
+    w, X, Xf, mu = multi_window
     B = _random_betas(w.p, k, 29 + k)
     with _problem(pkg, X, w, "split_e4m3") as prob:
         beta = torch.tensor(B, dtype=torch.float32, device="cuda")
@@ -109,6 +114,52 @@ def test_loss_grad_multi_window(pkg, k):
             f_o, g_o = oracle_loss_grad(Xf, mu, w.y, w.delta, bc)
             assert abs(loss[c] - f_o) <= 1e-7 * abs(f_o), (c, loss[c], f_o)
             assert rel_l2(G[c], g_o) <= 1e-5, (c, rel_l2(G[c], g_o))
+
+
+# every compiled pipeline shape (row tiles, K chunks per stage) of each limb-column class
+SHAPES = [(k, t, c) for k in (3, 16) for (t, c) in ((2, 2), (2, 1), (1, 2))] + \
+         [(32, 2, 1), (32, 1, 2), (32, 1, 1), (64, 1, 1)]
+
+
+@pytest.mark.parametrize("k,tile_m,chunks", SHAPES, ids=lambda v: str(v))
+def test_every_pipeline_shape(pkg, multi_window, k, tile_m, chunks):
+    """Each compiled shape, forced through the options, on row groups that span
+    several accumulation windows: the gradients of 4 sampled columns."""
+    w, X, Xf, mu = multi_window
+    B = _random_betas(w.p, k, 41 + k)
+    with _problem(pkg, X, w, "split_e4m3", tile_m=tile_m, chunks=chunks) as prob:
+        beta = torch.tensor(B, dtype=torch.float32, device="cuda")
+        loss, grad = prob.loss_grad(beta)
+        info = prob.info()
+        assert (info["tile_m"], info["chunks"]) == (tile_m, chunks)
+        G = grad.cpu().numpy()
+        for c in sorted({0, k // 3, (2 * k) // 3, k - 1}):
+            bc = beta[c].cpu().numpy().astype(np.float64)
+            f_o, g_o = oracle_loss_grad(Xf, mu, w.y, w.delta, bc)
+            assert abs(loss[c] - f_o) <= 1e-7 * abs(f_o), (c, loss[c], f_o)
+            assert rel_l2(G[c], g_o) <= 1e-5, (c, rel_l2(G[c], g_o))
+
+
+def test_autotune_choice_is_used_and_exact(pkg, multi_window):
+    w, X, Xf, mu = multi_window
+    k = 16
+    B = _random_betas(w.p, k, 53)
+    with _problem(pkg, X, w, "split_e4m3") as prob:
+        beta = torch.tensor(B, dtype=torch.float32, device="cuda")
+        ref_loss, ref_grad = prob.loss_grad(beta)
+        tune = prob.autotune(k, reps=2)
+        for prod in ("x_b", "xt_v"):
+            t = tune[prod]
+            assert t["candidates"] >= 3 and t["ms"] > 0 and t["tile_m"] in (1, 2) and t["chunks"] in (1, 2)
+        loss, grad = prob.loss_grad(beta)
+        info = prob.info()
+        assert (info["tile_m"], info["chunks"], info["stages"]) == \
+            (tune["x_b"]["tile_m"], tune["x_b"]["chunks"], tune["x_b"]["stages"])
+        G = grad.cpu().numpy()
+        for c in (0, 7, 15):
+            f_o, g_o = oracle_loss_grad(Xf, mu, w.y, w.delta, beta[c].cpu().numpy().astype(np.float64))
+            assert rel_l2(G[c], g_o) <= 1e-5
+            assert abs(loss[c] - f_o) <= 1e-7 * abs(f_o)
 
 
 @pytest.mark.parametrize("precision", ["split_e4m3", "fp32_gemv"])
