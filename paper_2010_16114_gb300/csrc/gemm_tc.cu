@@ -300,8 +300,19 @@ __global__ void __launch_bounds__(32 * (2 + T + 4 * G), 1)
         // registers are the scarce resource of the decoders
         float *accs = reinterpret_cast<float *>(smem + S * STAGE + 1024) + (threadIdx.x - 32 * DEC0);
         auto acc = [&](int tt, int e) -> float & { return accs[(tt * KH + e) * 128]; };
-        if (gamma == 0)
+        // per-column constants of the fused step, loaded once: sum V, step lambda, active
+        float *colc = reinterpret_cast<float *>(smem + S * STAGE + 1024) + T * KH * 128;
+        if (gamma == 0) {
             for (int e = 0; e < T * KH; ++e) accs[e * 128] = 0.f;
+            const int tid = threadIdx.x - 32 * DEC0;
+            if (P.epi != EPI_PARTIAL && tid < P.k) {
+                colc[tid] = static_cast<float>(P.sumV[tid]);
+                if (P.epi == EPI_PROX) {
+                    colc[KH + tid] = static_cast<float>(P.step * P.lam[tid]);
+                    colc[2 * KH + tid] = (P.active && !P.active[tid]) ? 0.f : 1.f;
+                }
+            }
+        }
         uint32_t epi_phase = 0, fold_phase = 0;
         bool ok = true;
 
@@ -397,9 +408,9 @@ __global__ void __launch_bounds__(32 * (2 + T + 4 * G), 1)
             }
 #pragma unroll 4
             for (int kk = 0; kk < P.k; ++kk) {
-                if (P.epi == EPI_PROX && P.active && !P.active[kk]) continue;
-                const float sv = static_cast<float>(P.sumV[kk]);
-                const float thr = static_cast<float>(P.step * P.lam[kk]);
+                if (P.epi == EPI_PROX && colc[2 * KH + kk] == 0.f) continue;
+                const float sv = colc[kk];
+                const float thr = colc[KH + kk];
 #pragma unroll
                 for (int rr = 0; rr < RPT; ++rr) {
                     const int64_t row = rows[rr];
@@ -639,7 +650,8 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
     if (!pick_kernel(T, CH, np_cls)) return COX_ERR_ARG;  // shape not compiled for this class
     if (m_tiles % T != 0 || (K_pad / TILE) % CH != 0) return COX_ERR_ARG;
     const int stage = CH * (np_cls * 128 + T * BLOCK_BYTES);
-    const int fold_bytes = T * (np_cls / LIMBS) * 128 * 4;  // group 0's window sums
+    // group 0's window sums, then three per-column constants of the fused step
+    const int fold_bytes = T * (np_cls / LIMBS) * 128 * 4 + 3 * (np_cls / LIMBS) * 4;
     int S = stages_req > 0 ? stages_req : (225 * 1024 - 2048 - fold_bytes) / stage;
     if (S > 12) S = 12;
     if (S < DEC_GROUPS + 1) S = DEC_GROUPS + 1;  // decoder groups step through the stage ring by DEC_GROUPS
