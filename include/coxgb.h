@@ -92,6 +92,8 @@ typedef struct cox_options {
     double wait_limit_s;  /* device-side wait limit in seconds (default 2.0)         */
     int chunks;           /* 128-wide K chunks per pipeline stage (1 or 2);
                              0 = automatic, as tile_m                               */
+    int window;           /* K chunks a TMEM accumulator sums in FP32 before decoder
+                             warps add it into FP32 sums (>= chunks; 0 = 256)       */
 } cox_options;
 
 /* Fill *opt with the defaults above. */

@@ -43,7 +43,7 @@ EXPORTS = [
 class cox_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("center", ctypes.c_int), ("device", ctypes.c_int),
                 ("tile_m", ctypes.c_int), ("stages", ctypes.c_int), ("lag", ctypes.c_int),
-                ("wait_limit_s", ctypes.c_double), ("chunks", ctypes.c_int)]
+                ("wait_limit_s", ctypes.c_double), ("chunks", ctypes.c_int), ("window", ctypes.c_int)]
 
 
 class cox_info(ctypes.Structure):

@@ -45,7 +45,7 @@ class CoxProblem:
 
     def __init__(self, X, time, event, precision: str = "split_e4m3", center: bool | None = None,
                  p: int | None = None, device: int | None = None, tile_m: int = 0, stages: int = 0,
-                 lag: int = 10, wait_limit_s: float = 2.0, chunks: int = 0):
+                 lag: int = 10, wait_limit_s: float = 2.0, chunks: int = 0, window: int = 0):
         lib = L.load()
         opt = L.cox_default_options()
         opt.precision = PRECISIONS[precision]
@@ -54,6 +54,7 @@ class CoxProblem:
         opt.tile_m = int(tile_m)
         opt.stages = int(stages)
         opt.chunks = int(chunks)
+        opt.window = int(window)
         opt.lag = int(lag)
         opt.wait_limit_s = float(wait_limit_s)
         time = np.ascontiguousarray(time, dtype=np.float64)

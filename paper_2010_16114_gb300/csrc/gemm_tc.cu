@@ -406,24 +406,45 @@ __global__ void __launch_bounds__(32 * (2 + T + 4 * G), 1)
                 rows[rr] = static_cast<int64_t>(g) * (T * TILE) + rr * 128 + tid;
                 muv[rr] = rows[rr] < P.rows_valid ? static_cast<float>(P.mu[rows[rr]]) : 0.f;
             }
-#pragma unroll 4
-            for (int kk = 0; kk < P.k; ++kk) {
-                if (P.epi == EPI_PROX && colc[2 * KH + kk] == 0.f) continue;
-                const float sv = colc[kk];
-                const float thr = colc[KH + kk];
+            // batches of KB columns: all loads of a batch are issued before any
+            // arithmetic, so their L2 latencies overlap
+            constexpr int KB = 4;
+            const int64_t ss = P.slot_stride;
+            for (int k0 = 0; k0 < P.k; k0 += KB) {
+                float gs[KB][RPT], bv[KB][RPT];
 #pragma unroll
-                for (int rr = 0; rr < RPT; ++rr) {
-                    const int64_t row = rows[rr];
-                    if (row >= P.rows_valid) continue;
-                    float Gs = 0.f;
-                    for (int s2 = 0; s2 < cnt; ++s2) Gs += __ldcg(&part[s2 * P.slot_stride + kk * P.rows_pad + row]);
-                    const float gv = (Gs - muv[rr] * sv) * inv_n;
-                    const int64_t bi = static_cast<int64_t>(kk) * P.rows_valid + row;
-                    if (P.epi == EPI_PROX) {
-                        const float z = fmaf(stepf, gv, beta[bi]);
-                        beta[bi] = z > thr ? z - thr : (z < -thr ? z + thr : 0.f);
-                    } else {
-                        grad[bi] = -gv;
+                for (int u = 0; u < KB; ++u) {
+                    const int kk = min(k0 + u, P.k - 1);
+#pragma unroll
+                    for (int rr = 0; rr < RPT; ++rr) {
+                        const int64_t row = rows[rr] < P.rows_valid ? rows[rr] : 0;
+                        const float *pp = part + kk * P.rows_pad + row;
+                        float g = __ldcg(pp);
+                        if (cnt > 1) g += __ldcg(pp + ss);
+                        for (int s2 = 2; s2 < cnt; ++s2) g += __ldcg(pp + s2 * ss);
+                        gs[u][rr] = g;
+                        bv[u][rr] = P.epi == EPI_PROX ? beta[static_cast<int64_t>(kk) * P.rows_valid + row] : 0.f;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < KB; ++u) {
+                    const int kk = k0 + u;
+                    if (kk >= P.k) break;
+                    const float sv = colc[kk];
+#pragma unroll
+                    for (int rr = 0; rr < RPT; ++rr) {
+                        const int64_t row = rows[rr];
+                        if (row >= P.rows_valid) continue;
+                        const float gv = (gs[u][rr] - muv[rr] * sv) * inv_n;
+                        const int64_t bi = static_cast<int64_t>(kk) * P.rows_valid + row;
+                        if (P.epi == EPI_PROX) {
+                            if (colc[2 * KH + kk] == 0.f) continue;  // converged column: frozen
+                            const float thr = colc[KH + kk];
+                            const float z = fmaf(stepf, gv, bv[u][rr]);
+                            beta[bi] = z > thr ? z - thr : (z < -thr ? z + thr : 0.f);
+                        } else {
+                            grad[bi] = -gv;
+                        }
                     }
                 }
             }
@@ -675,7 +696,9 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
     g.smem = static_cast<size_t>(S) * stage + 1024 + 1024 + fold_bytes;
     if (g.smem < 120 * 1024) g.smem = 120 * 1024;  // one CTA per SM: it owns all 512 TMEM columns
     if (g.smem > 227 * 1024) return COX_ERR_ARG;    // too many stages requested
-    g.F = 64 / CH;  // stages per accumulation window: 64 K chunks, 256 MMAs per accumulator
+    // stages per accumulation window (default 256 K chunks, 1024 MMAs per accumulator)
+    const int win = h->opt.window > 0 ? h->opt.window : 256;
+    g.F = std::max(1, win / CH);
     g.KC = static_cast<int>(K_pad / (TILE * CH));  // stages per group
     g.n_groups = static_cast<int>(m_tiles / T);
     g.units = static_cast<int64_t>(g.n_groups) * g.KC;

@@ -101,11 +101,12 @@ def multi_window():
 
 @pytest.mark.parametrize("k", [3, 16])
 def test_loss_grad_multi_window(pkg, multi_window, k):
-    """Row groups whose K range spans several accumulation windows (64 chunks
-    of 128) in both products, with ragged n and p: n = 9100, p = 8700."""
+    """Row groups whose K range spans several accumulation windows (windows of
+    16 chunks of 128 forced) in both products, with ragged n and p:
+    n = 9100, p = 8700."""
     w, X, Xf, mu = multi_window
     B = _random_betas(w.p, k, 29 + k)
-    with _problem(pkg, X, w, "split_e4m3") as prob:
+    with _problem(pkg, X, w, "split_e4m3", window=16) as prob:
         beta = torch.tensor(B, dtype=torch.float32, device="cuda")
         loss, grad = prob.loss_grad(beta)
         G = grad.cpu().numpy()
@@ -124,10 +125,10 @@ SHAPES = [(k, t, c) for k in (3, 16) for (t, c) in ((2, 2), (2, 1), (1, 2))] + \
 @pytest.mark.parametrize("k,tile_m,chunks", SHAPES, ids=lambda v: str(v))
 def test_every_pipeline_shape(pkg, multi_window, k, tile_m, chunks):
     """Each compiled shape, forced through the options, on row groups that span
-    several accumulation windows: the gradients of 4 sampled columns."""
+    several accumulation windows (16 chunks): the gradients of 4 sampled columns."""
     w, X, Xf, mu = multi_window
     B = _random_betas(w.p, k, 41 + k)
-    with _problem(pkg, X, w, "split_e4m3", tile_m=tile_m, chunks=chunks) as prob:
+    with _problem(pkg, X, w, "split_e4m3", tile_m=tile_m, chunks=chunks, window=16) as prob:
         beta = torch.tensor(B, dtype=torch.float32, device="cuda")
         loss, grad = prob.loss_grad(beta)
         info = prob.info()
