@@ -300,16 +300,20 @@ __global__ void __launch_bounds__(32 * (2 + T + 4 * G), 1)
         // registers are the scarce resource of the decoders
         float *accs = reinterpret_cast<float *>(smem + S * STAGE + 1024) + (threadIdx.x - 32 * DEC0);
         auto acc = [&](int tt, int e) -> float & { return accs[(tt * KH + e) * 128]; };
-        // per-column constants of the fused step, loaded once: sum V, step lambda, active
+        // per-column constants, loaded once: sum V, step lambda, active (fused
+        // step) and the power-of-two scale of the B limbs
         float *colc = reinterpret_cast<float *>(smem + S * STAGE + 1024) + T * KH * 128;
         if (gamma == 0) {
             for (int e = 0; e < T * KH; ++e) accs[e * 128] = 0.f;
             const int tid = threadIdx.x - 32 * DEC0;
-            if (P.epi != EPI_PARTIAL && tid < P.k) {
-                colc[tid] = static_cast<float>(P.sumV[tid]);
-                if (P.epi == EPI_PROX) {
-                    colc[KH + tid] = static_cast<float>(P.step * P.lam[tid]);
-                    colc[2 * KH + tid] = (P.active && !P.active[tid]) ? 0.f : 1.f;
+            if (tid < P.k) {
+                reinterpret_cast<int *>(colc + 3 * KH)[tid] = P.bscale[tid];
+                if (P.epi != EPI_PARTIAL) {
+                    colc[tid] = static_cast<float>(P.sumV[tid]);
+                    if (P.epi == EPI_PROX) {
+                        colc[KH + tid] = static_cast<float>(P.step * P.lam[tid]);
+                        colc[2 * KH + tid] = (P.active && !P.active[tid]) ? 0.f : 1.f;
+                    }
                 }
             }
         }
@@ -352,13 +356,54 @@ __global__ void __launch_bounds__(32 * (2 + T + 4 * G), 1)
             if (!segend) return;
 
             const int64_t first_cta = (static_cast<int64_t>(g) * KC) / P.L;
+            const int64_t last_cta = (static_cast<int64_t>(g) * KC + KC - 1) / P.L;
+            const int *bsc = reinterpret_cast<const int *>(colc + 3 * KH);
+            if (P.epi != EPI_PARTIAL && first_cta == last_cta) {
+                // the whole group ran in this CTA: apply the step straight from the
+                // sums (the same values the one partial slot would carry)
+                const float inv_n = static_cast<float>(P.inv_n), stepf = static_cast<float>(P.step);
+#pragma unroll
+                for (int tt = 0; tt < T; ++tt) {
+                    const int64_t row = (static_cast<int64_t>(g) * T + tt) * TILE + rit;
+                    const bool valid = row < P.rows_valid;
+                    const float muv = valid ? static_cast<float>(P.mu[row]) : 0.f;
+                    for (int e0 = 0; e0 < P.k; e0 += 8) {
+                        float bv[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int e = min(e0 + u, P.k - 1);
+                            bv[u] = (P.epi == EPI_PROX && valid) ? P.beta[static_cast<int64_t>(e) * P.rows_valid + row] : 0.f;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int e = e0 + u;
+                            if (e >= P.k) break;
+                            const float G = ldexpf(acc(tt, e), bsc[e] + 9);
+                            acc(tt, e) = 0.f;
+                            if (!valid) continue;
+                            const float gv = (G - muv * colc[e]) * inv_n;
+                            const int64_t bi = static_cast<int64_t>(e) * P.rows_valid + row;
+                            if (P.epi == EPI_PROX) {
+                                if (colc[2 * KH + e] == 0.f) continue;  // converged column: frozen
+                                const float thr = colc[KH + e];
+                                const float z = fmaf(stepf, gv, bv[u]);
+                                P.beta[bi] = z > thr ? z - thr : (z < -thr ? z + thr : 0.f);
+                            } else {
+                                P.grad[bi] = -gv;
+                            }
+                        }
+                    }
+                    for (int e = P.k; e < KH; ++e) acc(tt, e) = 0.f;
+                }
+                return;
+            }
             const int64_t slot = cta - first_cta;
 #pragma unroll
             for (int tt = 0; tt < T; ++tt) {
                 const int64_t row = (static_cast<int64_t>(g) * T + tt) * TILE + rit;
 #pragma unroll
                 for (int e = 0; e < KH; ++e) {
-                    if (e < P.k) P.part[slot * P.slot_stride + e * P.rows_pad + row] = ldexpf(acc(tt, e), P.bscale[e] + 9);
+                    if (e < P.k) P.part[slot * P.slot_stride + e * P.rows_pad + row] = ldexpf(acc(tt, e), bsc[e] + 9);
                     acc(tt, e) = 0.f;
                 }
             }
@@ -372,7 +417,6 @@ __global__ void __launch_bounds__(32 * (2 + T + 4 * G), 1)
                 return;
             }
             epi_phase ^= 1u;
-            const int64_t last_cta = (static_cast<int64_t>(g) * KC + KC - 1) / P.L;
             const int cnt = static_cast<int>(last_cta - first_cta + 1);
             if (threadIdx.x == 32 * DEC0) {
                 const int old = atomicAdd(&P.counters[g], 1);
@@ -671,8 +715,8 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
     if (!pick_kernel(T, CH, np_cls)) return COX_ERR_ARG;  // shape not compiled for this class
     if (m_tiles % T != 0 || (K_pad / TILE) % CH != 0) return COX_ERR_ARG;
     const int stage = CH * (np_cls * 128 + T * BLOCK_BYTES);
-    // group 0's window sums, then three per-column constants of the fused step
-    const int fold_bytes = T * (np_cls / LIMBS) * 128 * 4 + 3 * (np_cls / LIMBS) * 4;
+    // group 0's window sums, then four per-column constants
+    const int fold_bytes = T * (np_cls / LIMBS) * 128 * 4 + 4 * (np_cls / LIMBS) * 4;
     int S = stages_req > 0 ? stages_req : (225 * 1024 - 2048 - fold_bytes) / stage;
     if (S > 12) S = 12;
     if (S < DEC_GROUPS + 1) S = DEC_GROUPS + 1;  // decoder groups step through the stage ring by DEC_GROUPS

@@ -117,6 +117,33 @@ def test_loss_grad_multi_window(pkg, multi_window, k):
             assert rel_l2(G[c], g_o) <= 1e-5, (c, rel_l2(G[c], g_o))
 
 
+def test_prox_whole_and_split_row_groups(pkg):
+    """p = 40001 SNPs over n = 3000 subjects: in the X^T V product a CTA's unit
+    range holds whole row groups (the step is applied from its own sums) and
+    groups cut between CTAs (partials and the last-CTA step); both against the
+    oracle for the gradient and one step."""
+    w, X, Xf, mu = dense_problem(1, n=3000, p=40001)
+    k = 3
+    B = _random_betas(w.p, k, 61)
+    with _problem(pkg, X, w, "split_e4m3") as prob:
+        beta = torch.tensor(B, dtype=torch.float32, device="cuda")
+        loss, grad = prob.loss_grad(beta)
+        G = grad.cpu().numpy()
+        step, lam = 0.05, 1e-4
+        prob.prox_step(beta, [lam] * k, step)
+        Bn = beta.cpu().numpy().astype(np.float64)
+        for c in range(k):
+            bc = B[c].astype(np.float32).astype(np.float64)
+            f_o, g_o = oracle_loss_grad(Xf, mu, w.y, w.delta, bc)
+            assert rel_l2(G[c], g_o) <= 1e-5, (c, rel_l2(G[c], g_o))
+            z = bc - step * g_o
+            b1 = np.sign(z) * np.maximum(np.abs(z) - step * lam, 0.0)
+            dz = 1e-5 * step * np.linalg.norm(g_o)
+            amb = np.abs(np.abs(z) - step * lam) <= max(1e-6, dz)
+            assert np.all(((Bn[c] != 0) == (b1 != 0)) | amb)
+            np.testing.assert_allclose(Bn[c], b1, rtol=1e-4, atol=dz + 1e-7 * np.abs(bc).max())
+
+
 # every compiled pipeline shape (row tiles, K chunks per stage) of each limb-column class
 SHAPES = [(k, t, c) for k in (3, 16) for (t, c) in ((2, 2), (2, 1), (1, 2))] + \
          [(32, 2, 1), (32, 1, 2), (32, 1, 1), (64, 1, 1)]
