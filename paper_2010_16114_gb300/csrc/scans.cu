@@ -92,8 +92,17 @@ __global__ void k_eta(SP s, const void *src, int64_t slot_stride, int64_t col_st
                       int KC, int64_t L)
 {
     __shared__ double sh[NT / 32];
+    __shared__ int cnt_sh[SCAN_CH / 128];  // partial slots of the row groups of this chunk
     const int c = blockIdx.x, kk = blockIdx.y;
     const int64_t i0 = static_cast<int64_t>(c) * SCAN_CH;
+    if (SRC == ETA_PARTIAL_F32) {
+        // group_rows (128 or 256) divides SCAN_CH: the chunk holds whole groups
+        if (threadIdx.x < SCAN_CH / group_rows) {
+            const int64_t g = i0 / group_rows + threadIdx.x;
+            cnt_sh[threadIdx.x] = static_cast<int>((g * KC + KC - 1) / L - (g * KC) / L + 1);
+        }
+        __syncthreads();
+    }
     double mx = -INFINITY;
     for (int e = threadIdx.x; e < SCAN_CH; e += NT) {
         const int64_t i = i0 + e;
@@ -101,10 +110,9 @@ __global__ void k_eta(SP s, const void *src, int64_t slot_stride, int64_t col_st
         double v;
         if (SRC == ETA_PARTIAL_F32) {
             const float *part = static_cast<const float *>(src);
-            const int64_t g = i / group_rows;
-            const int64_t cnt = (g * KC + KC - 1) / L - (g * KC) / L + 1;
+            const int cnt = cnt_sh[e / group_rows];
             v = 0.0;
-            for (int64_t sl = 0; sl < cnt; ++sl) v += static_cast<double>(part[sl * slot_stride + kk * col_stride + i]);
+            for (int sl = 0; sl < cnt; ++sl) v += static_cast<double>(part[sl * slot_stride + kk * col_stride + i]);
         } else if (SRC == ETA_DENSE_F32) {
             v = static_cast<double>(static_cast<const float *>(src)[kk * col_stride + i]);
         } else {
@@ -192,6 +200,10 @@ __global__ void k_chunks(SP s)
 }
 
 // (3) W = R at the tie head; D = delta / W; loss terms; chunk-local forward scan of D.
+// FAST (the tensor-core and FP32 paths): 1/W in FP32, a relative error of
+// ~6e-8 per term of an FP64 sum (GB300's FP64 divide is slow).  The loss
+// keeps log W in FP64, and the FP64 path keeps both in FP64.
+template <bool FAST>
 __global__ void k_fwd(SP s, bool need_loss)
 {
     __shared__ double sh[NT / 32];
@@ -206,7 +218,7 @@ __global__ void k_fwd(SP s, bool need_loss)
         if (i < s.n && s.delta[i]) {
             const int64_t hd = s.head[i];
             const double W = s.Rt[kk * s.n + hd] + s.suf[kk * s.nch + hd / SCAN_CH];
-            d = 1.0 / W;
+            d = FAST ? static_cast<double>(1.0f / static_cast<float>(W)) : 1.0 / W;
             if (need_loss) lsum += log(W) - (s.eta[kk * s.n + i] - cmx);
         }
         buf[e] = d;
@@ -287,9 +299,10 @@ __global__ void k_vlimbs(SP s, uint8_t *__restrict__ Vq, int64_t n_pad, const do
     __shared__ double sh[NT / 32];
     __shared__ int s_sh;
     const int c = blockIdx.x, kk = blockIdx.y;
+    double m = 0.0;
+    for (int q = threadIdx.x; q < s.nch; q += NT) m = fmax(m, vmaxp[kk * s.nch + q]);
+    m = block_max(m, sh);
     if (threadIdx.x == 0) {
-        double m = 0.0;
-        for (int q = 0; q < s.nch; ++q) m = fmax(m, vmaxp[kk * s.nch + q]);
         float mf = static_cast<float>(m);
         if (!isfinite(mf)) {
             atomicOr(err, DEVERR_NONFINITE);
@@ -379,7 +392,8 @@ int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st)
     if (a.exp64) k_rev<true><<<grid, NT, 0, st>>>(s);
     else k_rev<false><<<grid, NT, 0, st>>>(s);
     k_chunks<true><<<a.k, 32, 0, st>>>(s);
-    k_fwd<<<grid, NT, 0, st>>>(s, a.need_loss);
+    if (a.exp64) k_fwd<false><<<grid, NT, 0, st>>>(s, a.need_loss);
+    else k_fwd<true><<<grid, NT, 0, st>>>(s, a.need_loss);
     k_chunks<false><<<a.k, 32, 0, st>>>(s);
     switch (a.v_out) {
     case V_LIMBS_E4M3:
