@@ -1,8 +1,8 @@
 // gemm_tc.cu -- the two genotype products of the Cox iteration on tcgen05
 // tensor cores (arXiv 2010.16114, Section 5.3: X beta, and Delta = X^T (I-P) delta):
 //
-//   first product : D = X_sorted (n x p) * Bhat (p x 2k)    -> eta partials
-//   second product: D = X_sorted^T (p x n) * Vhat (n x 2k)  -> X^T V, then the
+//   first product : D = X_sorted (n x p) * Bhat (p x 4k)    -> eta partials
+//   second product: D = X^T (p x n) * Vhat (n x 4k)         -> X^T V, then the
 //                   soft-threshold step (Section 4.2) in the epilogue.
 //
 // A is the 2-bit genotype matrix in a tiled layout (128 x 128 blocks of 4 KB),
@@ -21,22 +21,24 @@
 // partial is scaled by 2^(s+9).
 //
 // Pipeline per CTA (one per SM): two TMA warps fill a ring of shared-memory
-// stages (B chunk + T A blocks); groups of four decoder warps turn a stage into
-// e4m3 in a ring of TMEM slots, issuing all of a stage's tcgen05.st before one
-// wait; one issuer warp per row tile issues the stage's MMAs
-// into their own accumulators and commit.  Decoders hand a slot to the issuers
-// through a hardware named barrier (tens of cycles, against a few hundred for
-// an mbarrier arrive and wait), and every wait or commit serves a whole stage.
+// stages (T row tiles x CH K chunks of codes, and the matching limb panels);
+// groups of four decoder warps turn a stage into e4m3 in a ring of TMEM slots,
+// issuing all of a tile's tcgen05.st before one wait; one issuer warp per row
+// tile issues the stage's MMAs into its own accumulator and commits.  Decoders
+// hand a tile to its issuer through a hardware named barrier (tens of cycles,
+// against a few hundred for an mbarrier arrive and wait), and every wait or
+// commit serves a whole stage.
 //
-// FP32 accumulation in TMEM rounds with a bias, so each CTA accumulates at most
-// F K-chunks in TMEM, then decoder group 0 adds the window's accumulators into
-// FP32 registers (round-to-nearest).  The K order of the X^T V product spreads
-// the time order (setup.cu), so these running sums stay near the size of the
-// result instead of drifting with the time trend of V.
+// Accumulation: each accumulator sums at most one window of K chunks in FP32
+// in TMEM, then decoder group 0 adds the window into FP32 sums (round to
+// nearest).  The K order of the X^T V product spreads the time order
+// (setup.cu), so these running sums stay near the size of the result instead
+// of drifting with the time trend of V.
 //
-// Work split: units = (M group, K chunk) pairs; CTA c takes the contiguous
-// range [c L, (c+1) L).  A group cut between CTAs gets one partial per CTA
-// (slot = CTA - first CTA of the group); the last CTA to finish a group sums
+// Work split: units = (M group, stage) pairs; CTA c takes the contiguous range
+// [c L, (c+1) L).  A group that runs entirely in one CTA gets the epilogue
+// straight from its sums; a group cut between CTAs gets one partial per CTA
+// (slot = CTA - first CTA of the group), and the last CTA to finish it sums
 // the slots in slot order (deterministic) and applies the epilogue.
 #include <algorithm>
 
@@ -98,10 +100,9 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, long lo
 //   warps 0, 1     TMA producers (lane 0): warp w loads the stages i = w (mod 2);
 //                  warp 0 also allocates TMEM
 //   warps 2..T+1   MMA issuers: issuer t owns row tile t and accumulates it
-//                  into its own TMEM accumulator.  Every barrier wait or commit costs an
-//                  issuer a few hundred cycles, so it takes whole stages: 4 CH
-//                  MMAs (K = 32 each) per wait and commit.
-//   warps I+2..    G decoder groups of four warps (one per TMEM lane quarter);
+//                  into its own TMEM accumulator, 4 CH MMAs (K = 32 each) per
+//                  barrier wait and commit.
+//   warps T+2..    G decoder groups of four warps (one per TMEM lane quarter);
 //                  group gamma decodes the stages i = gamma (mod G) into TMEM
 //                  slot i mod R.  Group 0 also adds the accumulators up at window
 //                  ends and runs the epilogue.
