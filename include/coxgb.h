@@ -168,6 +168,17 @@ int cox_loss_grad(cox_h h, const void *beta_dev, int k, double *loss_host, void 
                   void *stream);
 
 /*
+ * Linear predictor eta = X_c B for k columns (Section 5.3, first step of the
+ * iteration), the quantity a column-sharded run would add up across shards:
+ * with X split by SNP columns into X_1 .. X_G, eta = sum_g (X_g)_c B_g.
+ *   beta_dev : p x k (device; float, double for COX_FP64 handles).
+ *   eta_dev  : k x n doubles (device), subjects in the handle's sorted order
+ *              (rank r = entry r of the order from cox_get_mu_order).
+ * Synchronous.  Errors: COX_ERR_UNSUPPORTED for COX_FP32_GEMV handles.
+ */
+int cox_eta(cox_h h, const void *beta_dev, int k, double *eta_dev, void *stream);
+
+/*
  * One proximal-gradient iteration for k penalties at once (Section 5.3):
  * eta = X_c B, risk-set scans, G = X_c^T V, beta <- S(beta + step g, step lambda).
  *   beta_dev : p x k in/out (device).

@@ -36,7 +36,7 @@ EXPORTS = [
     "cox_loss_grad", "cox_prox_step", "cox_prox_step_host", "cox_sync", "cox_last_objective",
     "cox_path_fit", "cox_get_state", "cox_set_state", "cox_get_info", "cox_get_mu_order",
     "cox_strerror", "cox_set_precision", "cox_profile", "cox_profile_read", "cox_lipschitz_noalloc",
-    "cox_autotune",
+    "cox_autotune", "cox_eta",
 ]
 
 
@@ -116,6 +116,8 @@ def load(path: str | None = None):
     lib.cox_profile.argtypes = [P, I]
     lib.cox_profile_read.restype = I
     lib.cox_profile_read.argtypes = [P, P, P]
+    lib.cox_eta.restype = I
+    lib.cox_eta.argtypes = [P, P, I, P, P]
     lib.cox_autotune.restype = I
     lib.cox_autotune.argtypes = [P, I, I, ctypes.POINTER(cox_tune_choice), ctypes.POINTER(cox_tune_choice)]
     lib.cox_strerror.restype = ctypes.c_char_p
@@ -227,6 +229,10 @@ def cox_profile(h, enable: int) -> int:
 
 def cox_profile_read(h, ms_ptr, launches_ptr) -> int:
     return load().cox_profile_read(h, ms_ptr, launches_ptr)
+
+
+def cox_eta(h, beta_ptr, k: int, eta_ptr, stream) -> int:
+    return load().cox_eta(h, beta_ptr, k, eta_ptr, stream)
 
 
 def cox_autotune(h, k: int, reps: int):

@@ -172,6 +172,14 @@ class CoxProblem:
         L.check(rc, "cox_loss_grad")
         return loss, grad.view_as(beta)
 
+    def eta(self, beta: torch.Tensor, stream=None) -> torch.Tensor:
+        """eta = X_c beta, shape (k, n), subjects in the handle's sorted order."""
+        b = self._beta(beta)
+        k = b.shape[0]
+        out = torch.empty((k, self.n), dtype=torch.float64, device=b.device)
+        L.check(L.cox_eta(self.h, _vp(b), k, _vp(out), _stream_ptr(stream)), "cox_eta")
+        return out
+
     def prox_step(self, beta: torch.Tensor, lambdas, step: float, stream=None):
         """One iteration in place on beta (asynchronous)."""
         b = self._beta(beta)

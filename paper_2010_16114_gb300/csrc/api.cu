@@ -55,7 +55,7 @@ void free_workspace(cox_handle *h)
 {
     Workspace &w = h->ws;
     void *ptrs[] = {w.eta, w.w, w.Rt, w.Ft, w.cmax, w.csw, w.csd, w.suf, w.pre, w.lossp, w.vsp, w.l1p,
-                    w.sumV, w.f, w.F, w.l1, w.lam, w.active, w.Fring, w.Bq, w.Vq, w.bs1, w.bs4, w.bmaxp,
+                    w.sumV, w.f, w.F, w.l1, w.mub, w.lam, w.active, w.Fring, w.Bq, w.Vq, w.bs1, w.bs4, w.bmaxp,
                     w.vmaxp, w.part1, w.part4, w.cnt4, w.V64, w.V32, w.eta32, w.G32};
     for (void *p : ptrs) dfree(p);
     const GemmPlan g1 = w.g1, g4 = w.g4;
@@ -327,6 +327,7 @@ int ensure_workspace(cox_handle *h, int k)
     A(ws.f, k);
     A(ws.F, k);
     A(ws.l1, k);
+    A(ws.mub, k);
     A(ws.lam, k);
     A(ws.active, k);
     A(ws.Fring, static_cast<size_t>(std::max(lag, 2)) * k);
@@ -717,6 +718,52 @@ int cox_loss_grad(cox_h h, const void *beta_dev, int k, double *loss_host, void 
         dfree(tmp);
     }
     return rc;
+}
+
+int cox_eta(cox_h h, const void *beta_dev, int k, double *eta_dev, void *stream)
+{
+    if (!h || !beta_dev || !eta_dev) return COX_ERR_ARG;
+    COX_TRY(validate_k(h, k));
+    if (h->opt.precision == COX_FP32_GEMV) return COX_ERR_UNSUPPORTED;
+    DeviceGuard g(h->dev);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    COX_TRY(ensure_workspace(h, k));
+    Workspace &ws = h->ws;
+    if (is_split(h)) {
+        const float *b32 = static_cast<const float *>(beta_dev);
+        COX_TRY(l1_norms32(h, b32, k, st, ws.bmaxp));
+        COX_TRY(prep_limbs_beta(h, b32, k, st));
+        EpiArgs e1;
+        e1.epi = EPI_PARTIAL;
+        e1.part = ws.part1;
+        e1.bscale = ws.bs1;
+        COX_TRY(launch_gemm(h, ws.g1, e1, k, st));
+        ScanArgs sa;
+        sa.k = k;
+        sa.eta_src = ETA_PARTIAL_F32;
+        sa.eta = ws.part1;
+        sa.slot_stride = static_cast<int64_t>(k) * h->n_pad;
+        sa.col_stride = h->n_pad;
+        sa.group_rows = ws.g1.T * TILE;
+        sa.KC = ws.g1.KC;
+        sa.L = ws.g1.L;
+        sa.v_out = V_LIMBS_E4M3;
+        sa.V = nullptr;
+        sa.NP = ws.g4.NP;
+        sa.exp64 = false;
+        sa.lam = nullptr;
+        sa.need_loss = false;
+        sa.eta_only = true;
+        COX_TRY(run_scans(h, sa, st));
+        h->launches += 4;
+    } else {
+        COX_TRY(eta64(h, static_cast<const double *>(beta_dev), k, ws.eta, st));
+        h->launches += 1;
+    }
+    COX_TRY(eta_centred_out(h, beta_dev, is_fp64(h), k, eta_dev, st));
+    h->launches += 2;
+    COX_TRY(check_device_error(h, st));
+    return COX_OK;
 }
 
 int cox_prox_step(cox_h h, void *beta_dev, const double *lambdas, int k, double step, void *stream)

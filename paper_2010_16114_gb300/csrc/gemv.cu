@@ -6,6 +6,8 @@
 //     2-bit tiles (FP32 multiply-add, FP64 across 128-wide chunks) and an
 //     unfused soft-threshold kernel;
 //   * ||beta||_1 partial sums for the penalised objective.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace coxgb {
@@ -163,6 +165,34 @@ __global__ void k_sub_scalar(const float *__restrict__ in, float *__restrict__ o
     if (i < len) out[i] = static_cast<float>(static_cast<double>(in[i]) - sub);
 }
 
+// dots[kk] = sum_j mu_j beta_jk (one block per column, fixed order)
+template <typename TB>
+__global__ void k_mu_dot(const double *__restrict__ mu, const TB *__restrict__ beta, int64_t p,
+                         double *__restrict__ dots)
+{
+    __shared__ double sh[256];
+    const int kk = blockIdx.x;
+    double s = 0.0;
+    for (int64_t j = threadIdx.x; j < p; j += 256) s += mu[j] * static_cast<double>(beta[kk * p + j]);
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) dots[kk] = sh[0];
+}
+
+__global__ void k_eta_out(const double *__restrict__ eta, const double *__restrict__ dots, int64_t n,
+                          double *__restrict__ out)
+{
+    const int kk = blockIdx.y;
+    const double d = dots[kk];
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        out[kk * n + i] = eta[kk * n + i] - d;
+}
+
 unsigned blocks_for(int64_t n, int t) { return static_cast<unsigned>((n + t - 1) / t); }
 
 } // namespace
@@ -221,6 +251,20 @@ int center_fix_vec(cox_handle *h, const float *v_in, float *a_out, int64_t len, 
 {
     (void)h;
     k_sub_scalar<<<blocks_for(len, 256), 256, 0, st>>>(v_in, a_out, len, sub);
+    COX_CUDA(cudaGetLastError());
+    return COX_OK;
+}
+
+} // namespace coxgb
+
+namespace coxgb {
+
+int eta_centred_out(cox_handle *h, const void *beta, bool f64, int k, double *out, cudaStream_t st)
+{
+    if (f64) k_mu_dot<double><<<k, 256, 0, st>>>(h->d_mu, static_cast<const double *>(beta), h->p, h->ws.mub);
+    else k_mu_dot<float><<<k, 256, 0, st>>>(h->d_mu, static_cast<const float *>(beta), h->p, h->ws.mub);
+    dim3 grid(static_cast<unsigned>(std::min<int64_t>(blocks_for(h->n, 256), 1024)), k);
+    k_eta_out<<<grid, 256, 0, st>>>(h->ws.eta, h->ws.mub, h->n, out);
     COX_CUDA(cudaGetLastError());
     return COX_OK;
 }

@@ -113,6 +113,7 @@ struct Workspace {
     double *lossp = nullptr, *vsp = nullptr;  // k x chunks
     double *l1p = nullptr;                    // k x l1 blocks
     double *sumV = nullptr, *f = nullptr, *F = nullptr, *l1 = nullptr;  // k
+    double *mub = nullptr;     // k: mu^T beta (cox_eta)
     double *lam = nullptr;     // k
     int *active = nullptr;     // k
     double *Fring = nullptr;   // lag x k
@@ -227,6 +228,7 @@ struct ScanArgs {
     bool exp64;           // exp in FP64 (FP64 mode) or FP32
     const double *lam;    // k (objective); may be null
     bool need_loss;
+    bool eta_only = false;  // stop after eta (cox_eta)
 };
 int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st);
 
@@ -268,5 +270,7 @@ int xtv64(cox_handle *h, const double *V, int k, double *beta, double *grad, con
           double step, cudaStream_t st);
 int center_fix_vec(cox_handle *h, const float *v_in, float *a_out, int64_t len, double sub,
                    cudaStream_t st);
+// out (k x n) = ws.eta - mu^T beta per column: X_c beta from the uncentred eta
+int eta_centred_out(cox_handle *h, const void *beta, bool f64, int k, double *out, cudaStream_t st);
 
 } // namespace coxgb

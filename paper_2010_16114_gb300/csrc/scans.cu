@@ -389,6 +389,10 @@ int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st)
         k_eta<ETA_DENSE_F64><<<grid, NT, 0, st>>>(s, a.eta, 0, a.col_stride, 1, 1, 1);
         break;
     }
+    if (a.eta_only) {
+        COX_CUDA(cudaGetLastError());
+        return COX_OK;
+    }
     if (a.exp64) k_rev<true><<<grid, NT, 0, st>>>(s);
     else k_rev<false><<<grid, NT, 0, st>>>(s);
     k_chunks<true><<<a.k, 32, 0, st>>>(s);
