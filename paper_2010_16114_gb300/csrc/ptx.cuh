@@ -180,16 +180,6 @@ __device__ __forceinline__ void tmem_ld_32x32b_x8(uint32_t taddr, uint32_t (&r)[
 
 // ---- tcgen05.mma ------------------------------------------------------------------
 
-// D[tmem] (+)= A[tmem] * B[smem desc], kind::f16 (bf16 inputs, fp32 accumulate).
-__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
-                                       uint32_t idesc, uint32_t accumulate)
-{
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-                 "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
-                 : "memory");
-}
-
 // D[tmem] (+)= A[tmem] * B[smem desc], kind::f8f6f4 (formats in the instruction
 // descriptor), fp32 accumulate; K = 32 per instruction for 8-bit operands.
 __device__ __forceinline__ void mma_ts_f8(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
@@ -209,7 +199,7 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
 }
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (the layout a 128B-swizzled TMA box of 64 bf16 per row
+// 1024 bytes apart (the layout a 128B-swizzled TMA box of 128-byte rows
 // writes).  addr must lie in a 1024-byte aligned swizzle atom.
 __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
 {
@@ -227,13 +217,6 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
 __host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N)
 {
     return (1u << 4) | (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
-}
-
-// Instruction descriptor, kind::f16: bf16 A and B (K-major), fp32 D, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
-           (static_cast<uint32_t>(M >> 4) << 24);
 }
 
 } // namespace coxgb
