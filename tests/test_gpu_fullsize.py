@@ -135,3 +135,45 @@ def test_config2_two_full_iterations():
             g_o, _ = oracle_grad(b_o)
     finally:
         prob.close()
+
+
+def test_config2_autograd_full_size():
+    """Config 2 at full size (n = 200,000, p = 10,000): the backward of CoxNLL
+    (the library's gradient) at 64 seeded coordinates against central
+    differences (h = 1e-3) of the FP64 oracle loss, and against the oracle
+    gradient over all columns (streamed in blocks of 500)."""
+    from paper_2010_16114_gb300.autograd import cox_nll
+    w, prob = _device_problem(2)
+    try:
+        n, p = w.n, w.p
+        r = np.random.default_rng(2)
+        b0 = np.zeros(p)
+        nz = r.choice(p, 40, replace=False)
+        b0[nz] = r.normal(0, 0.1, 40)
+        beta = torch.tensor(b0[None], dtype=torch.float32, device="cuda", requires_grad=True)
+        f = cox_nll(beta, prob)
+        f.sum().backward()
+        g = beta.grad.cpu().numpy()[0].astype(np.float64)
+        bf = beta.detach().cpu().numpy()[0].astype(np.float64)
+        nzc = np.nonzero(bf)[0]
+        Xs = w.cols(nzc)
+        eta0 = oracle.eta(Xs, Xs.mean(axis=0), bf[nzc])
+        _, u0, f0 = oracle.risk(w.y, w.delta, eta0)
+        assert abs(float(f.detach()[0]) - f0) <= 1e-7 * abs(f0)
+        g_o = np.zeros(p)
+        for j0 in range(0, p, 500):
+            blk = np.arange(j0, min(j0 + 500, p))
+            Xb = w.cols(blk)
+            g_o[blk] = -oracle.grad(Xb, Xb.mean(axis=0), w.delta, u0)
+        assert rel_l2(g, g_o) <= 1e-5
+        coords = np.unique((w.uniform_vec(11, 64) * p).astype(np.int64))
+        h, gmax = 1e-3, np.abs(g_o).max()
+        for j in coords:
+            xj = w.cols(np.array([j]))[:, 0]
+            xc = xj - xj.mean()
+            fp = oracle.risk(w.y, w.delta, eta0 + h * xc)[2]
+            fm = oracle.risk(w.y, w.delta, eta0 - h * xc)[2]
+            fd = (fp - fm) / (2 * h)
+            assert abs(g[j] - fd) <= max(1e-4 * abs(fd), 1e-4 * gmax), (j, g[j], fd)
+    finally:
+        prob.close()
