@@ -581,6 +581,10 @@ __global__ void __launch_bounds__(32 * (2 + T + 4 * G), 1)
         if (!ok && lane == 0) fail(abort_sm, P.err);
     }
 
+    // Lane 0 of the producer and issuer warps may still be loading or draining
+    // while lanes 1..31 are already here: reconverge every warp before the
+    // CTA-wide (warp-aligned) barrier that precedes the TMEM release.
+    __syncwarp();
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
