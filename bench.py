@@ -38,7 +38,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=4)
+    ap.add_argument("--workload", default="geno_400k_500k_k16",
+                    help="synthetic workload recipe (synth.WORKLOADS); --n/--p/--k rescale it")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--p", type=int, default=None)
     ap.add_argument("--k", type=int, default=None)
@@ -58,14 +59,19 @@ def parse():
 
 def recipe(args):
     import synth
-    r = synth.CONFIGS[args.config]
+    if args.workload not in synth.WORKLOADS:
+        raise SystemExit(f"unknown workload {args.workload!r}; one of {sorted(synth.WORKLOADS)}")
+    r = synth.WORKLOADS[args.workload]
     if args.n or args.p or args.k:
         r = r.scaled(n=args.n, p=args.p, k=args.k)
     return r
 
 
 def workload_name(r) -> str:
-    return (f"config {r.config}: n={r.n} subjects x p={r.p} SNPs 2-bit packed, MAF~U({r.maf_lo},{r.maf_hi}), "
+    if r.kind != "geno":
+        return (f"{r.name}: n={r.n} subjects x p={r.p} N(0,1) predictors, {r.n_causal} causal, "
+                f"{r.cens_frac:.0%} censored, no ties, k={r.k} at {r.lam_hi} lambda_max")
+    return (f"{r.name}: n={r.n} subjects x p={r.p} SNPs 2-bit packed, MAF~U({r.maf_lo},{r.maf_hi}), "
             f"{r.n_causal} causal, days 1..{r.dmax} (ties), {r.event_frac:.0%} events, k={r.k} lambdas "
             f"log-spaced lambda_max..{r.lam_lo} lambda_max")
 

@@ -5,16 +5,20 @@ arithmetic.  Both the FP64 oracle (``oracle/``) and the CUDA solver library
 consume what it produces; neither is imported here.
 
 Workload recipes (shapes of the paper's simulated Cox data, Section 5.3, and
-of its UK Biobank analysis, Section 6):
+of its UK Biobank analysis, Section 6), keyed by what they are:
 
-* config 0 -- n=1000 subjects, p=2000 predictors, x_ij ~ N(0,1), 20 causal
-  effects ~ N(0, 0.5^2), T ~ Exp(rate exp(x'beta)), C ~ Exp(r) with r set so
-  30% are censored, no ties; lambda = 0.5 lambda_max, 200 iterations, FP64.
-* configs 1-4 -- genotypes x_ij ~ Binomial(2, MAF_j), MAF_j ~ U(lo, hi),
-  causal effects on centred genotypes, T = E / (h0 exp(eta)), C ~ U(1, dmax),
-  y = ceil(min(T, C)) in whole days (ties), h0 set to hit the event rate.
+* ``normal_1k_2k`` -- n=1000 subjects, p=2000 predictors, x_ij ~ N(0,1), 20
+  causal effects ~ N(0, 0.5^2), T ~ Exp(rate exp(x'beta)), C ~ Exp(r) with r
+  set so 30% are censored, no ties; lambda = 0.5 lambda_max, 200 iterations,
+  FP64.
+* ``geno_100k_50k``, ``geno_200k_10k``, ``geno_400k_100k_k32``,
+  ``geno_400k_500k_k16`` -- n x p genotypes x_ij ~ Binomial(2, MAF_j),
+  MAF_j ~ U(lo, hi), causal effects on centred genotypes,
+  T = E / (h0 exp(eta)), C ~ U(1, dmax), y = ceil(min(T, C)) in whole days
+  (ties), h0 set to hit the event rate; k penalties (1 unless the name says).
 
-Seeds: config c uses seed 2010161140 + c.
+Each recipe carries its own seed; ``scaled`` keeps recipe and seed and
+changes only the sizes.
 """
 from __future__ import annotations
 
@@ -31,7 +35,6 @@ _LIB = os.path.join(_HERE, "libsynth.so")
 _DEV_SRC = os.path.join(_HERE, "synth_dev.cu")
 _DEV_LIB = os.path.join(_HERE, "libsynth_dev.so")
 
-SEED_BASE = 2010161140
 
 
 def build_host(force: bool = False) -> str:
@@ -94,7 +97,8 @@ def _ptr(a: np.ndarray):
 @dataclass(frozen=True)
 class Recipe:
     """One workload recipe; ``scaled`` keeps the recipe and changes sizes."""
-    config: int
+    name: str
+    seed: int
     kind: str            # "normal" or "geno"
     n: int
     p: int
@@ -111,10 +115,6 @@ class Recipe:
     iters: int = 200
     center: bool = True
 
-    @property
-    def seed(self) -> int:
-        return SEED_BASE + self.config
-
     def scaled(self, n: int | None = None, p: int | None = None, k: int | None = None,
                n_causal: int | None = None) -> "Recipe":
         n = self.n if n is None else n
@@ -129,18 +129,18 @@ class Recipe:
         return np.exp(np.linspace(np.log(self.lam_hi), np.log(self.lam_lo), self.k))
 
 
-CONFIGS = {
-    0: Recipe(0, "normal", 1000, 2000, 1, 20, 0.5, cens_frac=0.30, lam_hi=0.5, lam_lo=0.5,
-              iters=200, center=False),
-    1: Recipe(1, "geno", 100_000, 50_000, 1, 50, 0.1, 0.05, 0.5, event_frac=0.20, dmax=3650,
-              lam_hi=0.5, lam_lo=0.5, iters=50),
-    2: Recipe(2, "geno", 200_000, 10_000, 1, 50, 0.1, 0.05, 0.5, event_frac=0.20, dmax=3650,
-              lam_hi=0.5, lam_lo=0.5, iters=50),
-    3: Recipe(3, "geno", 400_000, 100_000, 32, 100, 0.1, 0.05, 0.5, event_frac=0.10, dmax=3650,
-              lam_hi=1.0, lam_lo=0.01, iters=50),
-    4: Recipe(4, "geno", 400_000, 500_000, 16, 500, 0.05, 0.01, 0.5, event_frac=0.05, dmax=5000,
-              lam_hi=1.0, lam_lo=0.01, iters=1000),
-}
+WORKLOADS = {r.name: r for r in (
+    Recipe("normal_1k_2k", 2010161140, "normal", 1000, 2000, 1, 20, 0.5, cens_frac=0.30,
+           lam_hi=0.5, lam_lo=0.5, iters=200, center=False),
+    Recipe("geno_100k_50k", 2010161141, "geno", 100_000, 50_000, 1, 50, 0.1, 0.05, 0.5,
+           event_frac=0.20, dmax=3650, lam_hi=0.5, lam_lo=0.5, iters=50),
+    Recipe("geno_200k_10k", 2010161142, "geno", 200_000, 10_000, 1, 50, 0.1, 0.05, 0.5,
+           event_frac=0.20, dmax=3650, lam_hi=0.5, lam_lo=0.5, iters=50),
+    Recipe("geno_400k_100k_k32", 2010161143, "geno", 400_000, 100_000, 32, 100, 0.1, 0.05, 0.5,
+           event_frac=0.10, dmax=3650, lam_hi=1.0, lam_lo=0.01, iters=50),
+    Recipe("geno_400k_500k_k16", 2010161144, "geno", 400_000, 500_000, 16, 500, 0.05, 0.01, 0.5,
+           event_frac=0.05, dmax=5000, lam_hi=1.0, lam_lo=0.01, iters=1000),
+)}
 
 
 class Workload:
@@ -257,9 +257,9 @@ class Workload:
         return out
 
 
-def workload(config: int, **sizes) -> Workload:
-    """Generate config ``config`` (optionally at other sizes, same recipe)."""
-    r = CONFIGS[config]
+def workload(name: str, **sizes) -> Workload:
+    """Generate recipe ``name`` (optionally at other sizes, same recipe and seed)."""
+    r = WORKLOADS[name]
     if sizes:
         r = r.scaled(**sizes)
     return Workload(r)

@@ -7,9 +7,9 @@ import oracle
 import synth
 
 
-def dense_problem(config: int, n: int | None = None, p: int | None = None):
-    """(workload, X float64 (n, p), mu or None) for a config recipe at given sizes."""
-    w = synth.workload(config, **({} if n is None and p is None else {"n": n, "p": p}))
+def dense_problem(name: str, n: int | None = None, p: int | None = None):
+    """(workload, X float64 (n, p), mu or None) for workload recipe `name` at given sizes."""
+    w = synth.workload(name, **({} if n is None and p is None else {"n": n, "p": p}))
     X = w.dense()
     Xf = X.astype(np.float64)
     mu = Xf.mean(axis=0) if w.r.center else None

@@ -55,7 +55,7 @@ def test_reference_arm_under_torchrun():
     port = _free_port()
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
-           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0", "--config", "0",
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0", "--workload", "normal_1k_2k",
            "--cpu-sample-cols", "50"]
     env = dict(os.environ, OMP_NUM_THREADS="1")
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, env=env, cwd=ROOT)

@@ -1,11 +1,12 @@
-"""Parity at the configurations' full sizes, in the launch configuration the
-benchmark uses (genotypes generated on the device, 2-bit packed, default
+"""Parity at the genotype workloads' full sizes, in the launch configuration
+the benchmark uses (genotypes generated on the device, 2-bit packed, default
 tiles).
 
-* config 2 (n=200,000, p=10,000, k=1): the oracle runs two whole iterations,
+* geno_200k_10k (n=200,000, p=10,000, k=1): the oracle runs two whole iterations,
   streaming X in column blocks; beta after each iteration and the gradient at
   beta = 0 are compared element by element.
-* configs 1, 3, 4 (up to n=400,000 x p=500,000): sampled outputs the oracle
+* geno_100k_50k, geno_400k_100k_k32, geno_400k_500k_k16 (up to n=400,000 x
+  p=500,000): sampled outputs the oracle
   computes one by one -- g_j(0) and the first iterate beta_j(1) of every
   penalty at 64 seeded columns j -- and the closed form of the loss at
   beta = 0, f(0) = (1/n) sum_i delta_i log |R_i|.
@@ -21,12 +22,12 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def _device_problem(config, **kw):
+def _device_problem(name, **kw):
     import paper_2010_16114_gb300 as P
     from paper_2010_16114_gb300.cox import CoxProblem
     P.build()
     synth.build_device()
-    w = synth.workload(config)
+    w = synth.workload(name)
     n, p = w.n, w.p
     thr = torch.from_numpy(w.thr.view(np.int32).copy()).cuda()
     packed = torch.empty((n, (p + 3) // 4), dtype=torch.uint8, device="cuda")
@@ -53,9 +54,9 @@ def _grad0_cols(w, idx):
     return oracle.grad(Xc, Xc.mean(axis=0), w.delta, u0)
 
 
-@pytest.mark.parametrize("config", [1, 3, 4])
-def test_sampled_first_iteration_full_size(config):
-    w, prob = _device_problem(config)
+@pytest.mark.parametrize("name", ["geno_100k_50k", "geno_400k_100k_k32", "geno_400k_500k_k16"])
+def test_sampled_first_iteration_full_size(name):
+    w, prob = _device_problem(name)
     try:
         r = w.r
         lmax = prob.lambda_max()
@@ -89,10 +90,10 @@ def test_sampled_first_iteration_full_size(config):
         prob.close()
 
 
-def test_config2_two_full_iterations():
-    """Config 2 at full size: two iterations from beta = 0 at lambda =
+def test_geno_200k_10k_two_full_iterations():
+    """n = 200,000 x p = 10,000 at full size: two iterations from beta = 0 at lambda =
     0.5 lambda_max, the oracle streaming X in blocks of 500 columns."""
-    w, prob = _device_problem(2)
+    w, prob = _device_problem("geno_200k_10k")
     try:
         n, p = w.n, w.p
         blocks = [np.arange(j, min(j + 500, p)) for j in range(0, p, 500)]
@@ -137,13 +138,13 @@ def test_config2_two_full_iterations():
         prob.close()
 
 
-def test_config2_autograd_full_size():
-    """Config 2 at full size (n = 200,000, p = 10,000): the backward of CoxNLL
+def test_geno_200k_10k_autograd_full_size():
+    """n = 200,000 x p = 10,000 at full size: the backward of CoxNLL
     (the library's gradient) at 64 seeded coordinates against central
     differences (h = 1e-3) of the FP64 oracle loss, and against the oracle
     gradient over all columns (streamed in blocks of 500)."""
     from paper_2010_16114_gb300.autograd import cox_nll
-    w, prob = _device_problem(2)
+    w, prob = _device_problem("geno_200k_10k")
     try:
         n, p = w.n, w.p
         r = np.random.default_rng(2)

@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
 Tolerances, stated per result:
-  * FP64 path (config-0 recipe): beta and gradient relative L2 <= 1e-10 (FP64
+  * FP64 path (normal_1k_2k recipe): beta and gradient relative L2 <= 1e-10 (FP64
     sums in a different order than the oracle's).
   * split-e4m3 tensor-core path and FP32 baseline: gradient relative L2 <= 1e-5
     (four e4m3 limbs hold each coefficient to <= 2^-16 relative; FP32
@@ -36,10 +36,10 @@ def _problem(pkg, X, w, precision, **kw):
 
 
 # ---------------------------------------------------------------- FP64 path
-def test_fp64_config0_200_iterations(pkg):
-    """Config 0 as specified: n=1000, p=2000, lambda = 0.5 lambda_max, step 1/L,
+def test_fp64_normal_1k_2k_200_iterations(pkg):
+    """The dense normal workload as specified: n=1000, p=2000, lambda = 0.5 lambda_max, step 1/L,
     200 iterations in FP64; beta and gradient within 1e-10 of the oracle."""
-    w, X, Xf, mu = dense_problem(0)
+    w, X, Xf, mu = dense_problem("normal_1k_2k")
     v0 = synth.normal_vec(95376, 7, w.p)
     L = oracle.lipschitz(Xf, mu, v0)
     lmax = oracle.lambda_max(Xf, mu, w.y, w.delta)
@@ -69,7 +69,7 @@ GENO_SIZES = [(3000, 700), (1000, 129), (4099, 1500)]
 @pytest.fixture(scope="module", params=GENO_SIZES, ids=lambda s: f"n{s[0]}_p{s[1]}")
 def geno(request):
     n, p = request.param
-    return dense_problem(1, n=n, p=p)
+    return dense_problem("geno_100k_50k", n=n, p=p)
 
 
 def _random_betas(p, k, seed):
@@ -99,7 +99,7 @@ def test_loss_grad_geno(pkg, geno, precision, k):
 
 @pytest.fixture(scope="module")
 def multi_window():
-    return dense_problem(1, n=9100, p=8700)
+    return dense_problem("geno_100k_50k", n=9100, p=8700)
 
 
 @pytest.mark.parametrize("k", [3, 16])
@@ -125,7 +125,7 @@ def test_prox_whole_and_split_row_groups(pkg):
     range holds whole row groups (the step is applied from its own sums) and
     groups cut between CTAs (partials and the last-CTA step); both against the
     oracle for the gradient and one step."""
-    w, X, Xf, mu = dense_problem(1, n=3000, p=40001)
+    w, X, Xf, mu = dense_problem("geno_100k_50k", n=3000, p=40001)
     k = 3
     B = _random_betas(w.p, k, 61)
     with _problem(pkg, X, w, "split_e4m3") as prob:
@@ -232,7 +232,7 @@ def test_lambda_max_and_lipschitz_geno(pkg, geno):
 
 # ---------------------------------------------------------------- edge cases
 def _edge_case(kind, n=700, p=300):
-    w, X, Xf, mu = dense_problem(1, n=n, p=p)
+    w, X, Xf, mu = dense_problem("geno_100k_50k", n=n, p=p)
     y, d = w.y.copy(), w.delta.copy()
     if kind == "all_censored":
         d[:] = 0
@@ -273,7 +273,7 @@ def test_degenerate_cases(pkg, kind):
 
 def test_single_predictor_and_tiny_n(pkg):
     for n, p in [(1, 1), (2, 1), (5, 3), (130, 1)]:
-        w, X, Xf, mu = dense_problem(1, n=n, p=p)
+        w, X, Xf, mu = dense_problem("geno_100k_50k", n=n, p=p)
         d = w.delta.copy()
         d[0] = 1
         from paper_2010_16114_gb300.cox import CoxProblem
@@ -288,7 +288,7 @@ def test_single_predictor_and_tiny_n(pkg):
 def test_invalid_code_rejected(pkg):
     from paper_2010_16114_gb300._lib import COX_ERR_CODE3, CoxError
     from paper_2010_16114_gb300.cox import CoxProblem
-    w, X, Xf, mu = dense_problem(1, n=200, p=50)
+    w, X, Xf, mu = dense_problem("geno_100k_50k", n=200, p=50)
     X = X.copy()
     X[17, 33] = 3
     with pytest.raises(CoxError) as ei:
@@ -299,7 +299,7 @@ def test_invalid_code_rejected(pkg):
 def test_packed_inputs_match_int8(pkg):
     """Row-major 2-bit input (host and device) gives the same handle as uint8."""
     from paper_2010_16114_gb300.cox import CoxProblem
-    w, X, Xf, mu = dense_problem(1, n=1500, p=333)
+    w, X, Xf, mu = dense_problem("geno_100k_50k", n=1500, p=333)
     pk = w.packed_rows()
     beta = torch.tensor(_random_betas(w.p, 2, 3), dtype=torch.float32, device="cuda")
     with CoxProblem(X, w.y, w.delta) as a:
@@ -320,7 +320,7 @@ def test_packed_inputs_match_int8(pkg):
 def test_repeatable_bitwise(pkg):
     """Same inputs, same launch: bit-identical loss, gradient and iterates."""
     from paper_2010_16114_gb300.cox import CoxProblem
-    w, X, Xf, mu = dense_problem(1, n=3000, p=700)
+    w, X, Xf, mu = dense_problem("geno_100k_50k", n=3000, p=700)
     with CoxProblem(X, w.y, w.delta) as prob:
         b1 = prob.zeros(4)
         b2 = prob.zeros(4)

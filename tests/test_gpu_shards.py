@@ -27,7 +27,7 @@ def test_column_shards_sum_to_eta(precision):
     import paper_2010_16114_gb300 as P
     from paper_2010_16114_gb300.cox import CoxProblem
     P.build()
-    w, X, Xf, mu = dense_problem(1, n=3000, p=2500)
+    w, X, Xf, mu = dense_problem("geno_100k_50k", n=3000, p=2500)
     k = 4
     B = _betas(w.p, k, 7)
     Xin = X if precision == "split_e4m3" else Xf

@@ -22,7 +22,7 @@ def pkg():
 
 @pytest.fixture(scope="module")
 def small():
-    w, X, Xf, mu = dense_problem(3, n=2500, p=400)
+    w, X, Xf, mu = dense_problem("geno_400k_100k_k32", n=2500, p=400)
     v0 = synth.normal_vec(95376, 7, w.p)
     L = oracle.lipschitz(Xf, mu, v0)
     lmax = oracle.lambda_max(Xf, mu, w.y, w.delta)
@@ -94,12 +94,12 @@ def test_checkpoint_resume_bit_identical(pkg, small):
 
 
 def test_autograd_matches_fd_and_oracle(pkg):
-    """Config-2 recipe (scaled): backward of CoxNLL at 64 seeded coordinates vs
+    """geno_200k_10k recipe (scaled): backward of CoxNLL at 64 seeded coordinates vs
     central differences (h = 1e-3) of the FP64 oracle loss, and vs the oracle
     gradient overall."""
     from paper_2010_16114_gb300.autograd import cox_nll
     from paper_2010_16114_gb300.cox import CoxProblem
-    w, X, Xf, mu = dense_problem(2, n=20000, p=600)
+    w, X, Xf, mu = dense_problem("geno_200k_10k", n=20000, p=600)
     r = np.random.default_rng(2)
     b0 = np.zeros(w.p)
     nz = r.choice(w.p, 40, replace=False)
@@ -113,7 +113,7 @@ def test_autograd_matches_fd_and_oracle(pkg):
     f_o, g_o = oracle_loss_grad(Xf, mu, w.y, w.delta, bf)
     assert abs(float(f[0]) - f_o) <= 1e-7 * abs(f_o)
     assert rel_l2(g, g_o) <= 1e-5
-    coords = synth.Workload(synth.CONFIGS[2].scaled(n=20000, p=600)).uniform_vec(11, 64)
+    coords = synth.Workload(synth.WORKLOADS["geno_200k_10k"].scaled(n=20000, p=600)).uniform_vec(11, 64)
     coords = np.unique((coords * w.p).astype(int))
     h = 1e-3
     gmax = np.abs(g_o).max()
@@ -129,7 +129,7 @@ def test_autograd_matches_fd_and_oracle(pkg):
 def test_nonfinite_is_reported(pkg):
     from paper_2010_16114_gb300._lib import COX_ERR_NONFINITE, CoxError
     from paper_2010_16114_gb300.cox import CoxProblem
-    w, X, Xf, mu = dense_problem(1, n=600, p=200)
+    w, X, Xf, mu = dense_problem("geno_100k_50k", n=600, p=200)
     with CoxProblem(X, w.y, w.delta) as prob:
         beta = torch.full((1, w.p), 3e37, dtype=torch.float32, device="cuda")
         beta[0, ::2] = -3e37

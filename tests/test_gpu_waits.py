@@ -20,7 +20,7 @@ def test_zero_wait_limit_reports_timeout():
     from paper_2010_16114_gb300._lib import COX_ERR_TIMEOUT, CoxError
     from paper_2010_16114_gb300.cox import CoxProblem
     P.build()
-    w, X, Xf, mu = dense_problem(1, n=8192, p=4096)
+    w, X, Xf, mu = dense_problem("geno_100k_50k", n=8192, p=4096)
     beta = torch.zeros((2, w.p), dtype=torch.float32, device="cuda")
     beta[:, ::7] = 0.01
     codes = []

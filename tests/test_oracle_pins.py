@@ -177,7 +177,7 @@ def test_logrank_score_p1(orc):
 @pytest.mark.parametrize("center", [False, True])
 def test_gradient_central_differences(orc, center):
     """g = -grad f: central differences of the FP64 loss, h = 1e-5."""
-    w = synth.workload(1, n=400, p=12)
+    w = synth.workload("geno_100k_50k", n=400, p=12)
     X = w.dense().astype(float)
     mu = X.mean(0) if center else None
     beta = _rng(5).normal(0, 0.3, w.p)
@@ -197,7 +197,7 @@ def test_gradient_central_differences(orc, center):
 
 def test_centering_leaves_loss_unchanged(orc):
     """X_c beta differs from X beta by a constant, which the loss ignores."""
-    w = synth.workload(1, n=300, p=20)
+    w = synth.workload("geno_100k_50k", n=300, p=20)
     X = w.dense().astype(float)
     beta = _rng(6).normal(0, 0.2, w.p)
     f_c = orc.risk(w.y, w.delta, orc.eta(X, X.mean(0), beta))[2]
@@ -216,7 +216,7 @@ def test_soft_threshold_cases(orc):
 
 
 def _small_problem(seed=0, n=150, p=30):
-    w = synth.workload(1, n=n, p=p)
+    w = synth.workload("geno_100k_50k", n=n, p=p)
     X = w.dense().astype(float)
     mu = X.mean(0)
     return w, X, mu

@@ -40,10 +40,10 @@ def _both(L, prob, v0, tol, maxiter):
 def test_noalloc_matches_allocating_call_twice(L, precision):
     from paper_2010_16114_gb300.cox import CoxProblem
     if precision == "fp64":
-        w, X, Xf, mu = dense_problem(0, n=700, p=300)
+        w, X, Xf, mu = dense_problem("normal_1k_2k", n=700, p=300)
         Xin = Xf
     else:
-        w, X, Xf, mu = dense_problem(1, n=3000, p=700)
+        w, X, Xf, mu = dense_problem("geno_100k_50k", n=3000, p=700)
         Xin = X
     v0 = synth.normal_vec(95376, 7, w.p)
     with CoxProblem(Xin, w.y, w.delta, precision=precision) as prob:
