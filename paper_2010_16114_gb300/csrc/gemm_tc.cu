@@ -607,15 +607,19 @@ __global__ void k_prep_limbs_beta(const float *__restrict__ beta, int64_t p, int
 {
     __shared__ int s_sh;
     const int kk = blockIdx.y;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         float m = 0.f;
-        for (int b = 0; b < nb; ++b) m = fmaxf(m, maxp[kk * nb + b]);
-        if (!isfinite(m)) {
-            atomicOr(err, DEVERR_NONFINITE);
-            m = 0.f;
+        for (int b = threadIdx.x; b < nb; b += 32) m = fmaxf(m, maxp[kk * nb + b]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) {
+            if (!isfinite(m)) {
+                atomicOr(err, DEVERR_NONFINITE);
+                m = 0.f;
+            }
+            s_sh = limb_scale(m);
+            if (blockIdx.x == 0) bs[kk] = s_sh;
         }
-        s_sh = limb_scale(m);
-        if (blockIdx.x == 0) bs[kk] = s_sh;
     }
     __syncthreads();
     const int s = s_sh;
@@ -834,7 +838,9 @@ int launch_gemm(cox_handle *h, const GemmPlan &g, const EpiArgs &e, int k, cudaS
 
 int prep_limbs_beta(cox_handle *h, const float *beta, int k, cudaStream_t st)
 {
-    dim3 grid(static_cast<unsigned>(std::min<int64_t>((h->p + 255) / 256, 4096)), k);
+    // about four blocks per SM over all columns; each block strides over p
+    const int64_t bx = std::max<int64_t>(1, (4 * static_cast<int64_t>(h->sm_count) + k - 1) / k);
+    dim3 grid(static_cast<unsigned>(std::min<int64_t>((h->p + 255) / 256, bx)), k);
     k_prep_limbs_beta<<<grid, 256, 0, st>>>(beta, h->p, h->p_pad, h->l1_blocks, h->ws.bmaxp, h->ws.Bq,
                                             h->ws.bs1, h->d_err);
     COX_CUDA(cudaGetLastError());

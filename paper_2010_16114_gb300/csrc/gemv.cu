@@ -19,13 +19,18 @@ __global__ void k_l1_32(const float *__restrict__ beta, int64_t p, int nb, doubl
     __shared__ double sh[8];
     __shared__ float shm[8];
     const int b = blockIdx.x, kk = blockIdx.y;
-    double s = 0.0;
-    float m = 0.f;
+    // compensated FP32 sum (Knuth's TwoSum per term; the error terms summed
+    // apart): ~2^-48 relative, without GB300's slow FP64 pipe in the loop
+    float hi = 0.f, lo = 0.f, m = 0.f;
     for (int64_t j = static_cast<int64_t>(b) * blockDim.x + threadIdx.x; j < p; j += static_cast<int64_t>(nb) * blockDim.x) {
         const float v = fabsf(beta[kk * p + j]);
-        s += static_cast<double>(v);
+        const float t = hi + v;
+        const float bv = t - hi;
+        lo += (hi - (t - bv)) + (v - bv);
+        hi = t;
         m = fmaxf(m, v);
     }
+    double s = static_cast<double>(hi) + static_cast<double>(lo);
     for (int o = 16; o > 0; o >>= 1) {
         s += __shfl_xor_sync(0xffffffffu, s, o);
         m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));

@@ -70,6 +70,35 @@ __device__ inline float split_e4m3(float r, uint8_t *d)
     return rep;
 }
 
+// Value of an e4m3 byte in units of 2^-9 (exact: normal values are
+// (8 + m) 2^(e - 10), subnormal ones m 2^-9).
+__device__ inline int e4m3_units(uint8_t q)
+{
+    const int e = (q >> 3) & 15, m = q & 7;
+    const int u = e ? (8 + m) << (e - 1) : m;
+    return (q & 0x80) ? -u : u;
+}
+
+// The split of split_e4m3, returning the value the limbs represent times 2^21
+// as an exact integer (limb l is a multiple of 2^-9 weighted 16^-l; below
+// 2^30 in magnitude for |r| <= 256).  Non-finite r gives NaN limbs and 0.
+__device__ inline int split_e4m3_units(float r, uint8_t *d)
+{
+    if (!isfinite(r)) {
+        for (int l = 0; l < LIMBS; ++l) d[l] = 0x7F;
+        return 0;
+    }
+    int q = 0;
+#pragma unroll
+    for (int l = 0; l < LIMBS; ++l) {
+        const uint8_t b = static_cast<uint8_t>(__nv_cvt_float_to_fp8(r, __NV_SATFINITE, __NV_E4M3));
+        d[l] = b;
+        q = 16 * q + e4m3_units(b);
+        r = (r - e4m3_value(b)) * 16.f;
+    }
+    return q;
+}
+
 // K order of the SNP-major copy (A4).  Sorted subjects are kept in blocks of
 // 16 (one packed word), and sorted block b is stored at block (a b) mod nb,
 // nb = n_pad / 16, a odd and prime to nb, near nb (sqrt 5 - 1) / 2.  Any run

@@ -77,6 +77,15 @@ __device__ __forceinline__ double block_max(double x, double *sh)
     return t;
 }
 
+// m (positive, normal) -> m 2^-e in [1, 2); returns e.  Lets a product of
+// many positive factors be carried as (mantissa, exponent) without overflow.
+__device__ __forceinline__ int renorm(double &m)
+{
+    const long long b = __double_as_longlong(m);
+    m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+    return static_cast<int>(b >> 52) - 1023;
+}
+
 struct SP {
     int64_t n, n_pad;
     int nch, k;
@@ -177,24 +186,29 @@ __global__ void k_rev(SP s)
     if (threadIdx.x == NT - 1) s.csw[kk * s.nch + c] = incl;
 }
 
-// exclusive scans of chunk totals: suffix (reverse) or prefix (forward)
+// exclusive scans of chunk totals: suffix (reverse) or prefix (forward); one
+// warp per column, lane l owning a contiguous run of chunks in scan order.
 template <bool SUFFIX>
 __global__ void k_chunks(SP s)
 {
-    const int kk = blockIdx.x;
-    if (threadIdx.x != 0) return;
-    const double *src = SUFFIX ? s.csw : s.csd;
-    double *dst = SUFFIX ? s.suf : s.pre;
-    double acc = 0.0;
-    if (SUFFIX) {
-        for (int c = s.nch - 1; c >= 0; --c) {
-            dst[kk * s.nch + c] = acc;
-            acc += src[kk * s.nch + c];
-        }
-    } else {
-        for (int c = 0; c < s.nch; ++c) {
-            dst[kk * s.nch + c] = acc;
-            acc += src[kk * s.nch + c];
+    const int kk = blockIdx.x, lane = threadIdx.x;
+    const double *src = (SUFFIX ? s.csw : s.csd) + static_cast<int64_t>(kk) * s.nch;
+    double *dst = (SUFFIX ? s.suf : s.pre) + static_cast<int64_t>(kk) * s.nch;
+    const int per = (s.nch + 31) / 32;
+    auto at = [&](int q) { return SUFFIX ? s.nch - 1 - q : q; };  // q-th chunk in scan order
+    double tot = 0.0;
+    for (int j = 0; j < per; ++j) {
+        const int q = lane * per + j;
+        if (q < s.nch) tot += src[at(q)];
+    }
+    const double incl = warp_incl_scan(tot, lane);
+    double acc = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) acc = 0.0;
+    for (int j = 0; j < per; ++j) {
+        const int q = lane * per + j;
+        if (q < s.nch) {
+            dst[at(q)] = acc;
+            acc += src[at(q)];
         }
     }
 }
@@ -211,7 +225,12 @@ __global__ void k_fwd(SP s, bool need_loss)
     const int c = blockIdx.x, kk = blockIdx.y;
     const double cmx = need_loss ? column_max(s, kk, sh) : 0.0;
     const int64_t i0 = static_cast<int64_t>(c) * SCAN_CH;
-    double lsum = 0.0;
+    // The loss terms log W are summed as the log of their product: each thread
+    // multiplies its W into pm 2^pe (pm in [1, 2)), the warp multiplies its
+    // lanes' products, and one log per warp remains (FP64 log is costly and
+    // events are sparse, so a per-event log would run in most warps anyway).
+    double lsum = 0.0, pm = 1.0;
+    int pe = 0;
     for (int e = threadIdx.x; e < SCAN_CH; e += NT) {
         const int64_t i = i0 + e;
         double d = 0.0;
@@ -219,7 +238,15 @@ __global__ void k_fwd(SP s, bool need_loss)
             const int64_t hd = s.head[i];
             const double W = s.Rt[kk * s.n + hd] + s.suf[kk * s.nch + hd / SCAN_CH];
             d = FAST ? static_cast<double>(1.0f / static_cast<float>(W)) : 1.0 / W;
-            if (need_loss) lsum += log(W) - (s.eta[kk * s.n + i] - cmx);
+            if (need_loss) {
+                lsum -= s.eta[kk * s.n + i] - cmx;
+                if (W >= 0x1p-1022 && W <= 0x1p+1000) {
+                    pm *= W;
+                    pe += renorm(pm);
+                } else {
+                    lsum += log(W);  // zero, subnormal, huge or NaN: as a plain sum of logs
+                }
+            }
         }
         buf[e] = d;
     }
@@ -242,6 +269,13 @@ __global__ void k_fwd(SP s, bool need_loss)
     }
     if (threadIdx.x == NT - 1) s.csd[kk * s.nch + c] = incl;
     if (need_loss) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {  // every lane ends with the same product
+            pm *= __shfl_xor_sync(0xffffffffu, pm, o);
+            pe += __shfl_xor_sync(0xffffffffu, pe, o);
+            pe += renorm(pm);
+        }
+        if ((threadIdx.x & 31) == 0) lsum += log(pm) + static_cast<double>(pe) * 0.6931471805599453;
         const double t = block_sum(lsum, sh);
         if (threadIdx.x == 0) s.lossp[kk * s.nch + c] = t;
     }
@@ -258,7 +292,8 @@ __global__ void k_uv(SP s, void *Vout, int64_t n_pad, double *vmaxp)
     __shared__ double sh[NT / 32];
     const int c = blockIdx.x, kk = blockIdx.y;
     const int64_t i0 = static_cast<int64_t>(c) * SCAN_CH;
-    double vs = 0.0, vm = 0.0;
+    double vs = 0.0;
+    float vm32 = 0.f;
     for (int e = threadIdx.x; e < SCAN_CH; e += NT) {
         const int64_t i = i0 + e;
         if (i >= s.n) break;
@@ -271,8 +306,11 @@ __global__ void k_uv(SP s, void *Vout, int64_t n_pad, double *vmaxp)
         // two event times share one V, so their rounding errors do not
         // cancel; with the exact sum, mu times their sum would remain.)
         if (VO == V_LIMBS_E4M3) {
-            s.Rt[kk * s.n + i] = V;
-            vm = fmax(vm, fabs(V));
+            // k_vlimbs splits the FP32 value: hand it over in FP32 (the max of
+            // the rounded values is the rounded max, so the scale is unchanged)
+            const float v32 = static_cast<float>(V);
+            reinterpret_cast<float *>(s.Rt)[kk * s.n + i] = v32;
+            vm32 = fmaxf(vm32, fabsf(v32));
         } else if (VO == V_DENSE_F64) {
             static_cast<double *>(Vout)[kk * s.n + i] = V;
             vs += V;
@@ -283,7 +321,7 @@ __global__ void k_uv(SP s, void *Vout, int64_t n_pad, double *vmaxp)
         }
     }
     if (VO == V_LIMBS_E4M3) {
-        const double m = block_max(vm, sh);
+        const double m = block_max(static_cast<double>(vm32), sh);
         if (threadIdx.x == 0) vmaxp[kk * s.nch + c] = m;
     } else {
         const double t = block_sum(vs, sh);
@@ -291,8 +329,10 @@ __global__ void k_uv(SP s, void *Vout, int64_t n_pad, double *vmaxp)
     }
 }
 
-// (4b) V (in Rt) -> e4m3 limbs at the A4 K positions, one power-of-two scale
-// per column (from all chunk maxima); chunk sums of the values the limbs hold.
+// (4b) V (FP32, in Rt) -> e4m3 limbs at the A4 K positions, one power-of-two
+// scale per column (from all chunk maxima); chunk sums of the values the limbs
+// hold, exact: each is an integer number of 2^(sc-21) units below 2^30, so
+// a chunk's sum is an integer below 2^42, exact in FP64.
 __global__ void k_vlimbs(SP s, uint8_t *__restrict__ Vq, int64_t n_pad, const double *__restrict__ vmaxp,
                          int *__restrict__ bs, int *err)
 {
@@ -314,36 +354,54 @@ __global__ void k_vlimbs(SP s, uint8_t *__restrict__ Vq, int64_t n_pad, const do
     __syncthreads();
     const int sc = s_sh;
     const int64_t i0 = static_cast<int64_t>(c) * SCAN_CH;
-    double vs = 0.0;
+    const float *V32 = reinterpret_cast<const float *>(s.Rt);
+    long long q = 0;
+    bool finite = true;
     for (int e = threadIdx.x; e < SCAN_CH; e += NT) {
         const int64_t i = i0 + e;
         if (i >= s.n) break;
         uint8_t d[LIMBS];
-        const float rep = split_e4m3(static_cast<float>(ldexp(s.Rt[kk * s.n + i], -sc)), d);
+        // ldexpf of the FP32 value equals rounding the scaled FP64 value: the
+        // scale is a power of two and |V| >= 1/n whenever V is not all zero,
+        // so nothing the limbs can hold falls into FP32's subnormal range
+        const float r = ldexpf(V32[kk * s.n + i], -sc);
+        finite = finite && isfinite(r);
+        q += split_e4m3_units(r, d);
         const int64_t pos = a4_pos(i, s.pa, s.pnb);
 #pragma unroll
         for (int l = 0; l < LIMBS; ++l) Vq[(LIMBS * kk + l) * n_pad + pos] = d[l];
-        vs += ldexp(static_cast<double>(rep), sc);
     }
-    const double t = block_sum(vs, sh);
-    if (threadIdx.x == 0) s.vsp[kk * s.nch + c] = t;
+    const double t = block_sum(finite ? static_cast<double>(q) : NAN, sh);
+    if (threadIdx.x == 0) s.vsp[kk * s.nch + c] = ldexp(t, sc - 21);
 }
 
-// (5) per column: sum V, f, ||beta||_1, F = f + lambda ||beta||_1; flag non-finite.
+// (5) per column (one warp each): sum V, f, ||beta||_1, F = f + lambda ||beta||_1;
+// flag non-finite.
+__device__ __forceinline__ double warp_sum(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
 __global__ void k_finalize(SP s, int l1_blocks, const double *l1p, const double *lam, double *sumV,
                            double *f, double *l1, double *Fobj, bool need_loss, int *err)
 {
-    const int kk = threadIdx.x;
-    if (kk >= s.k) return;
+    const int kk = blockIdx.x, lane = threadIdx.x;
     double v = 0.0, lo = 0.0, b1 = 0.0;
-    for (int c = 0; c < s.nch; ++c) v += s.vsp[kk * s.nch + c];
+    for (int c = lane; c < s.nch; c += 32) v += s.vsp[kk * s.nch + c];
+    v = warp_sum(v);
+    if (need_loss) {
+        for (int c = lane; c < s.nch; c += 32) lo += s.lossp[kk * s.nch + c];
+        if (l1p)
+            for (int c = lane; c < l1_blocks; c += 32) b1 += l1p[kk * l1_blocks + c];
+        lo = warp_sum(lo) / static_cast<double>(s.n);
+        b1 = warp_sum(b1);
+    }
+    if (lane != 0) return;
     sumV[kk] = v;
     if (need_loss) {
-        for (int c = 0; c < s.nch; ++c) lo += s.lossp[kk * s.nch + c];
-        lo /= static_cast<double>(s.n);
         f[kk] = lo;
-        if (l1p)
-            for (int c = 0; c < l1_blocks; ++c) b1 += l1p[kk * l1_blocks + c];
         l1[kk] = b1;
         Fobj[kk] = lo + (lam ? lam[kk] * b1 : 0.0);
         if (!isfinite(lo)) atomicOr(err, DEVERR_NONFINITE);
@@ -407,7 +465,7 @@ int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st)
     case V_DENSE_F64: k_uv<V_DENSE_F64><<<grid, NT, 0, st>>>(s, a.V, h->n_pad, nullptr); break;
     default: k_uv<V_DENSE_F32><<<grid, NT, 0, st>>>(s, a.V, h->n_pad, nullptr); break;
     }
-    k_finalize<<<1, 64, 0, st>>>(s, h->l1_blocks, a.need_loss ? ws.l1p : nullptr, a.lam, ws.sumV, ws.f, ws.l1,
+    k_finalize<<<a.k, 32, 0, st>>>(s, h->l1_blocks, a.need_loss ? ws.l1p : nullptr, a.lam, ws.sumV, ws.f, ws.l1,
                                  ws.F, a.need_loss, h->d_err);
     COX_CUDA(cudaGetLastError());
     return COX_OK;
