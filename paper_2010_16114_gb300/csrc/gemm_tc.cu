@@ -115,6 +115,17 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, long lo
 //   empty[s]       one arrival by the decoders of stage i+R once they have seen
 //                  aempty for stage i (its MMAs, which read B and follow the
 //                  decoders' reads of X, are complete)       -> producer
+// Parity waits must not alias (the phase before the awaited one must be
+// complete), which needs R >= G:
+//   aempty, decoders of stage i for stage i - R: their own wait at stage i - G
+//     completed stage i - G - R, so (commits complete in order) stage i - 2R;
+//   full, decoders of stage i for stage i: the load of their previous stage
+//     i - G followed the release of stage i - G - S by the decoders of stage
+//     i - G - S + R, who had waited for full at that stage, = i - S when R = G
+//     (and, through the issue order, when R > G).
+// With R < G (two slots against three groups, as three K chunks per stage
+// would leave) small cases ran exact at S = 4 while a full-size run never
+// finished; the planner refuses such rings.
 // PB = lcm(G, R): each use of a named barrier has the same warps, and the
 // decoders of stage i+PB cannot arrive before the issuer of stage i has passed
 // it (they first wait, through the TMEM slot chain, for MMAs that this issuer
@@ -739,7 +750,10 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
     if (ring > 8) ring = 8;
     if (ring > S - 1) ring = S - 1;
     while (ring >= 2 && lcm_i(DEC_GROUPS, ring) * T > 15) --ring;
-    if (ring < 2) return COX_ERR_ARG;
+    // Parity waits need the previous phase of their barrier complete, which
+    // the decoders' chains guarantee only with at least as many TMEM slots as
+    // decoder groups (see the kernel's hand-off notes)
+    if (ring < DEC_GROUPS) return COX_ERR_ARG;
     g.T = T;
     g.CH = CH;
     g.NP = np_cls;

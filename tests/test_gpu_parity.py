@@ -148,7 +148,7 @@ def test_prox_whole_and_split_row_groups(pkg):
 
 
 # every compiled pipeline shape (row tiles, K chunks per stage) of each limb-column class
-SHAPES = [(k, t, c) for k in (3, 16) for (t, c) in ((2, 2), (2, 1), (1, 2))] + \
+SHAPES = [(k, t, c) for k in (3, 8, 16) for (t, c) in ((2, 2), (2, 1), (1, 2))] + \
          [(32, 2, 1), (32, 1, 2), (32, 1, 1), (64, 1, 1)]
 
 
