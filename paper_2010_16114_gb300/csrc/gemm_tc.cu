@@ -781,9 +781,15 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
     g.max_slots = ms;
     g.rows_pad = rows_pad;
     {
+        // the two products (and the autotuner's candidates) share kernels with
+        // different depths: allow the device's largest block allocation once,
+        // and let each launch ask for its own size
         KernelFn fn = pick_kernel(g.T, g.CH, g.NP);
         if (!fn) return COX_ERR_ARG;
-        COX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(g.smem)));
+        int optin = 0;
+        COX_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
+        if (static_cast<size_t>(optin) < g.smem) return COX_ERR_ARG;
+        COX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     }
 
     EncodeTiled enc = get_encoder();
