@@ -252,6 +252,30 @@ typedef struct cox_tune_choice {
 } cox_tune_choice;
 int cox_autotune(cox_h h, int k, int reps, cox_tune_choice *xb, cox_tune_choice *xtv);
 
+/*
+ * Pipeline plan of the tensor-core products (the genotype products X beta and
+ * X^T (delta - u) of each iteration, Section 5.3), computed on the host
+ * without a device or handle: for k coefficient columns (1..64) and a shape
+ * (tile_m 128-row tiles per CTA, chunks 128-wide K chunks per stage; 0 = the
+ * built-in default) at a shared-memory depth (stages; 0 = the deepest that
+ * fits), the plan cox_setup's handles would launch.  Every plan it returns
+ * keeps the pipeline's invariants: ring >= decoder_groups, ring < stages,
+ * named_barriers <= 15, tmem_cols <= 512, smem_bytes within the device's
+ * per-block limit.  Errors: COX_ERR_ARG for a NULL out, k outside 1..64, a
+ * shape not compiled for k's limb-column class, or a depth outside those
+ * invariants.
+ */
+typedef struct cox_plan {
+    int tile_m, chunks, stages;
+    int ring;             /* TMEM slots of decoded genotype codes                  */
+    int decoder_groups;   /* decoder warp groups (each takes every G-th stage)     */
+    int named_barriers;   /* hardware barriers in use: lcm(groups, ring) x tile_m  */
+    int limb_cols;        /* e4m3 limb columns: N of every MMA                     */
+    int tmem_cols;        /* accumulators + slots, of the 512 an SM has            */
+    long long smem_bytes; /* dynamic shared memory per CTA                         */
+} cox_plan;
+int cox_plan_shape(int k, int tile_m, int chunks, int stages, cox_plan *out);
+
 /* Switch a genotype handle between COX_SPLIT_E4M3 and COX_FP32_GEMV; both
  * read the same resident tiles.  Drops the per-k workspace.  Errors:
  * COX_ERR_UNSUPPORTED for COX_FP64 handles or targets. */

@@ -36,7 +36,7 @@ EXPORTS = [
     "cox_loss_grad", "cox_prox_step", "cox_prox_step_host", "cox_sync", "cox_last_objective",
     "cox_path_fit", "cox_get_state", "cox_set_state", "cox_get_info", "cox_get_mu_order",
     "cox_strerror", "cox_set_precision", "cox_profile", "cox_profile_read", "cox_lipschitz_noalloc",
-    "cox_autotune", "cox_eta",
+    "cox_autotune", "cox_eta", "cox_plan_shape",
 ]
 
 
@@ -57,6 +57,12 @@ class cox_info(ctypes.Structure):
 class cox_tune_choice(ctypes.Structure):
     _fields_ = [("tile_m", ctypes.c_int), ("chunks", ctypes.c_int), ("stages", ctypes.c_int),
                 ("candidates", ctypes.c_int), ("ms", ctypes.c_double)]
+
+
+class cox_plan(ctypes.Structure):
+    _fields_ = [("tile_m", ctypes.c_int), ("chunks", ctypes.c_int), ("stages", ctypes.c_int),
+                ("ring", ctypes.c_int), ("decoder_groups", ctypes.c_int), ("named_barriers", ctypes.c_int),
+                ("limb_cols", ctypes.c_int), ("tmem_cols", ctypes.c_int), ("smem_bytes", ctypes.c_longlong)]
 
 
 class CoxError(RuntimeError):
@@ -120,6 +126,8 @@ def load(path: str | None = None):
     lib.cox_eta.argtypes = [P, P, I, P, P]
     lib.cox_autotune.restype = I
     lib.cox_autotune.argtypes = [P, I, I, ctypes.POINTER(cox_tune_choice), ctypes.POINTER(cox_tune_choice)]
+    lib.cox_plan_shape.restype = I
+    lib.cox_plan_shape.argtypes = [I, I, I, I, ctypes.POINTER(cox_plan)]
     lib.cox_strerror.restype = ctypes.c_char_p
     lib.cox_strerror.argtypes = [I]
     _lib = lib
@@ -239,6 +247,13 @@ def cox_autotune(h, k: int, reps: int):
     xb, xtv = cox_tune_choice(), cox_tune_choice()
     rc = load().cox_autotune(h, k, reps, ctypes.byref(xb), ctypes.byref(xtv))
     return rc, xb, xtv
+
+
+def cox_plan_shape(k: int, tile_m: int = 0, chunks: int = 0, stages: int = 0):
+    """(rc, cox_plan) of the tensor-core products for k columns; host only."""
+    out = cox_plan()
+    rc = load().cox_plan_shape(k, tile_m, chunks, stages, ctypes.byref(out))
+    return rc, out
 
 
 def cox_strerror(code: int) -> str:

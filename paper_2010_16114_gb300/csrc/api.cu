@@ -631,6 +631,23 @@ int cox_autotune(cox_h h, int k, int reps, cox_tune_choice *xb, cox_tune_choice 
     return COX_OK;
 }
 
+int cox_plan_shape(int k, int tile_m, int chunks, int stages, cox_plan *out)
+{
+    if (!out || tile_m < 0 || chunks < 0 || stages < 0) return COX_ERR_ARG;
+    GemmPlan g;
+    COX_TRY(plan_shape(g, k, tile_m, chunks, stages));
+    out->tile_m = g.T;
+    out->chunks = g.CH;
+    out->stages = g.stages;
+    out->ring = g.ring;
+    out->decoder_groups = DEC_GROUPS;
+    out->named_barriers = g.nb_period * g.T;
+    out->limb_cols = g.NP;
+    out->tmem_cols = g.T * g.NP + g.ring * g.T * g.CH * 32;
+    out->smem_bytes = static_cast<long long>(g.smem);
+    return COX_OK;
+}
+
 int cox_set_precision(cox_h h, int precision)
 {
     if (!h) return COX_ERR_ARG;

@@ -663,7 +663,6 @@ EncodeTiled get_encoder()
 
 using KernelFn = void (*)(const CUtensorMap, const CUtensorMap, const KParams);
 
-constexpr int DEC_GROUPS = 3;
 
 // (T row tiles, CH K chunks) per stage for a limb-column class NP.  One issuer
 // per tile leaves the most TMEM to the A slot ring (a second issuer per tile
@@ -722,18 +721,15 @@ int gemm_shapes(int k, int *T, int *CH, int max)
 
 // Plan one product: A (rows_pad x K_pad, tiled 2-bit) times B limbs (NP x K_pad).
 // TMEM budget (512 columns): T NP accumulator columns + ring x T CH x 32 A columns.
-int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, int64_t K_pad,
-              const uint8_t *B, int k, int T_req, int CH_req, int stages_req)
+int plan_shape(GemmPlan &g, int k, int T_req, int CH_req, int stages_req)
 {
     if (k < 1 || k > MAX_K_TC) return COX_ERR_ARG;
     const int np_cls = limb_cols(k);
-    const int64_t m_tiles = rows_pad / TILE;
     int T = 2, CH = 1;
     shape_for(np_cls, &T, &CH);
     if (T_req > 0) T = T_req;
     if (CH_req > 0) CH = CH_req;
     if (!pick_kernel(T, CH, np_cls)) return COX_ERR_ARG;  // shape not compiled for this class
-    if (m_tiles % T != 0 || (K_pad / TILE) % CH != 0) return COX_ERR_ARG;
     const int stage = CH * (np_cls * 128 + T * BLOCK_BYTES);
     // group 0's window sums, then four per-column constants
     const int fold_bytes = T * (np_cls / LIMBS) * 128 * 4 + 4 * (np_cls / LIMBS) * 4;
@@ -763,6 +759,16 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
     g.smem = static_cast<size_t>(S) * stage + 1024 + 1024 + fold_bytes;
     if (g.smem < 120 * 1024) g.smem = 120 * 1024;  // one CTA per SM: it owns all 512 TMEM columns
     if (g.smem > 227 * 1024) return COX_ERR_ARG;    // too many stages requested
+    return COX_OK;
+}
+
+int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, int64_t K_pad,
+              const uint8_t *B, int k, int T_req, int CH_req, int stages_req)
+{
+    COX_TRY(plan_shape(g, k, T_req, CH_req, stages_req));
+    const int64_t m_tiles = rows_pad / TILE;
+    const int T = g.T, CH = g.CH, np_cls = g.NP;
+    if (m_tiles % T != 0 || (K_pad / TILE) % CH != 0) return COX_ERR_ARG;
     // stages per accumulation window (default 256 K chunks, 1024 MMAs per accumulator)
     const int win = h->opt.window > 0 ? h->opt.window : 256;
     g.F = std::max(1, win / CH);

@@ -21,6 +21,7 @@ constexpr int PAD = 1024;          // n, p padding of the tiled layouts
 constexpr int SCAN_CH = 2048;      // subjects per scan chunk (256 threads x 8)
 constexpr int MAX_K_TC = 64;       // largest k of the tensor-core path
 constexpr int LIMBS = 4;           // e4m3 limbs per coefficient (4 significant bits each)
+constexpr int DEC_GROUPS = 3;      // decoder warp groups of the tensor-core products
 
 // Limb columns of a k-column product: LIMBS k rounded up to an MMA width class.
 inline int limb_cols(int k)
@@ -263,6 +264,10 @@ int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st);
 
 // ---- tensor-core products (gemm_tc.cu) ---------------------------------------------
 // Plan one product; T_req / CH_req / stages_req of 0 take the defaults.
+// The shape and depth arithmetic of a product plan (host only, no device):
+// T, CH, NP, stages, ring, nb_period and smem of g, or COX_ERR_ARG for a shape
+// not compiled for k or a depth the pipeline does not allow.
+int plan_shape(GemmPlan &g, int k, int T_req, int CH_req, int stages_req);
 int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, int64_t K_pad,
               const uint8_t *B, int k, int T_req, int CH_req, int stages_req);
 // The compiled (row tiles, K chunks) shapes for k columns; returns their count.

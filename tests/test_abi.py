@@ -55,7 +55,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     """The ctypes mirrors of the header's structs have the C sizes and offsets."""
     import subprocess
     from paper_2010_16114_gb300 import _lib as L
-    structs = {"cox_options": L.cox_options, "cox_info": L.cox_info, "cox_tune_choice": L.cox_tune_choice}
+    structs = {"cox_options": L.cox_options, "cox_info": L.cox_info, "cox_tune_choice": L.cox_tune_choice,
+               "cox_plan": L.cox_plan}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "coxgb.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')

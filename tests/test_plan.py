@@ -1,0 +1,81 @@
+"""Host-side plans of the tensor-core products (cox_plan_shape, no GPU): for
+every k and every compiled shape and depth, the plan keeps the pipeline's
+invariants, which the kernel's hand-offs rely on:
+
+* ring >= decoder groups: a decoder group's parity waits (on the TMEM slot it
+  refills and on the shared-memory stage it decodes) are unambiguous only when
+  the phase before the awaited one is known to be complete, which the hand-off
+  chains guarantee with at least as many slots as groups;
+* ring < stages: the producer of stage i waits for the decoders of stage
+  i - S + ring, who must not be waiting for that producer;
+* lcm(groups, ring) x tiles <= 15 hardware named barriers (0 is __syncthreads);
+* accumulators + slots <= 512 TMEM columns; shared memory within 227 KB and at
+  least 120 KB (one CTA per SM owns all of TMEM).
+"""
+import math
+
+import pytest
+
+from paper_2010_16114_gb300 import _lib as L
+
+SHAPES = [(t, c) for t in (2, 1) for c in (2, 1)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_2010_16114_gb300 import build
+    build()
+    return L.load()
+
+
+def _check(k, p):
+    assert p.limb_cols >= 4 * k and p.limb_cols in (16, 32, 64, 128, 256)
+    assert p.ring >= p.decoder_groups
+    assert p.ring < p.stages
+    assert p.stages >= p.decoder_groups + 1
+    assert p.named_barriers == math.lcm(p.decoder_groups, p.ring) * p.tile_m <= 15
+    assert p.tmem_cols == p.tile_m * p.limb_cols + p.ring * p.tile_m * p.chunks * 32 <= 512
+    assert 120 * 1024 <= p.smem_bytes <= 227 * 1024
+
+
+@pytest.mark.parametrize("k", range(1, 65))
+def test_every_shape_and_depth_keeps_the_invariants(k):
+    compiled = 0
+    for t, c in SHAPES:
+        rc, p = L.cox_plan_shape(k, t, c, 0)
+        if rc != 0:
+            assert rc == L.COX_ERR_ARG
+            continue
+        compiled += 1
+        assert (p.tile_m, p.chunks) == (t, c)
+        _check(k, p)
+        deepest = p.stages
+        for s in range(1, 16):
+            rc, q = L.cox_plan_shape(k, t, c, s)
+            if rc != 0:
+                # refused only beyond the shared-memory budget
+                assert rc == L.COX_ERR_ARG and s > deepest
+                continue
+            _check(k, q)
+            assert q.stages == min(max(s, q.decoder_groups + 1), 12)  # the planner caps the depth at 12
+    assert compiled >= 1
+
+
+@pytest.mark.parametrize("k", [1, 4, 5, 8, 9, 16, 17, 32, 33, 64])
+def test_default_shape(k):
+    rc, p = L.cox_plan_shape(k)
+    assert rc == 0
+    _check(k, p)
+    # the built-in default: two row tiles up to 128 limb columns, two K chunks up to 64
+    assert p.tile_m == (2 if p.limb_cols <= 128 else 1)
+    assert p.chunks == (2 if p.limb_cols <= 64 else 1)
+
+
+def test_rejections():
+    assert L.cox_plan_shape(0)[0] == L.COX_ERR_ARG
+    assert L.cox_plan_shape(65)[0] == L.COX_ERR_ARG
+    assert L.cox_plan_shape(16, 3, 0)[0] == L.COX_ERR_ARG      # three row tiles: not compiled
+    assert L.cox_plan_shape(16, 0, 3)[0] == L.COX_ERR_ARG      # three K chunks: not compiled
+    assert L.cox_plan_shape(64, 2, 2)[0] == L.COX_ERR_ARG      # 256 limb columns take one tile, one chunk
+    assert L.cox_plan_shape(16, -1, 0)[0] == L.COX_ERR_ARG
+    assert L.load().cox_plan_shape(16, 0, 0, 0, None) == L.COX_ERR_ARG
