@@ -663,7 +663,6 @@ EncodeTiled get_encoder()
 
 using KernelFn = void (*)(const CUtensorMap, const CUtensorMap, const KParams);
 
-
 // (T row tiles, CH K chunks) per stage for a limb-column class NP.  One issuer
 // per tile leaves the most TMEM to the A slot ring (a second issuer per tile
 // needs a second accumulator).  N = 256 fills half of TMEM per accumulator,
