@@ -137,7 +137,7 @@ struct Workspace {
     // split / gemv / fp64 common (sorted subject order)
     double *eta = nullptr;      // k x n
     double *w = nullptr;        // k x n
-    double *Rt = nullptr;       // k x n local reverse scans
+    double *Rt = nullptr;       // k x n local reverse scans; then V in FP32 for k_vlimbs
     double *Ft = nullptr;       // k x n local forward scans
     double *cmax = nullptr, *csw = nullptr, *csd = nullptr, *suf = nullptr, *pre = nullptr;
     double *lossp = nullptr, *vsp = nullptr;  // k x chunks
