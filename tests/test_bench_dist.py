@@ -4,7 +4,8 @@ bench.py runs one process per GPU under torch.distributed.run; ranks
 barrier around the timed region and the slowest rank's time is reported.
 These tests run that plumbing with the gloo backend on the host: the
 max-over-ranks reduction, and the reference arm launched under torchrun
-(rank 0 prints the single JSON line, the other rank exits 0)."""
+(rank 0 prints the single JSON line, the other rank exits 0); and that the
+benchmark's own arm has no CPU fallback."""
 import json
 import os
 import socket
@@ -65,3 +66,17 @@ def test_reference_arm_under_torchrun():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_our_arm_has_no_cpu_fallback():
+    """Without a GPU the benchmark's own arm fails loudly and prints no result
+    line: every step of the path runs in the CUDA library, never on the host."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--steps", "1", "--warmup", "0",
+           "--no-cpu-baseline", "--no-gemv", "--e2e-steps", "0", "--workload", "geno_100k_50k",
+           "--n", "2000", "--p", "300"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode != 0
+    assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
