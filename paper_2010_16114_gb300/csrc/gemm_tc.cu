@@ -390,10 +390,10 @@ __global__ void __launch_bounds__(32 * (2 + T + 4 * G), 1)
                         for (int u = 0; u < 8; ++u) {
                             const int e = e0 + u;
                             if (e >= P.k) break;
-                            const float G = ldexpf(acc(tt, e), bsc[e] + 9);
+                            const float xtv = ldexpf(acc(tt, e), bsc[e] + 9);  // (X^T V)_j
                             acc(tt, e) = 0.f;
                             if (!valid) continue;
-                            const float gv = (G - muv * colc[e]) * inv_n;
+                            const float gv = (xtv - muv * colc[e]) * inv_n;
                             const int64_t bi = static_cast<int64_t>(e) * P.rows_valid + row;
                             if (P.epi == EPI_PROX) {
                                 if (colc[2 * KH + e] == 0.f) continue;  // converged column: frozen
