@@ -115,17 +115,26 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, long lo
 //   empty[s]       one arrival by the decoders of stage i+R once they have seen
 //                  aempty for stage i (its MMAs, which read B and follow the
 //                  decoders' reads of X, are complete)       -> producer
-// Parity waits must not alias (the phase before the awaited one must be
-// complete), which needs R >= G:
-//   aempty, decoders of stage i for stage i - R: their own wait at stage i - G
-//     completed stage i - G - R, so (commits complete in order) stage i - 2R;
-//   full, decoders of stage i for stage i: the load of their previous stage
-//     i - G followed the release of stage i - G - S by the decoders of stage
-//     i - G - S + R, who had waited for full at that stage, = i - S when R = G
-//     (and, through the issue order, when R > G).
-// With R < G (two slots against three groups, as three K chunks per stage
-// would leave) small cases ran exact at S = 4 while a full-size run never
-// finished; the planner refuses such rings.
+// Parity waits must not alias: when a warp waits for a phase, the phase
+// before it must be complete (else the wait can return a phase early).  The
+// MMAs of a stage complete only after its decoders finished, who had waited
+// for its load and arrived on empty for stage - R; issuers go in stage order.
+// So the MMAs of stage x being complete means every stage <= x was loaded and
+// decoded.  Per barrier (G groups, R slots, S stages, 2 producer warps):
+//   aempty, decoders of stage i wait for stage i - R and need stage i - 2R:
+//     their own wait at stage i - G completed stage i - G - R: G <= R.
+//   full, decoders of stage i wait for the load of stage i and need the load
+//     of stage i - S: (a) S >= G + R (the same wait covers it), or (b) S a
+//     multiple of G (their own group loaded stage i - S), or (c) R a multiple
+//     of G (the load of stage i - G followed the release of stage i - G - S by
+//     the decoders of stage i - G - S + R, the group of stage i - S, later).
+//   empty, the producer of stage j waits for stage j - S's release and needs
+//     stage j - 2S's: S even (one producer warp owns the slot), or S >= R + 2
+//     (its load of stage j - 2 followed the release of stage j - 2 - S, so the
+//     MMAs of that stage and the releases of every stage <= j - 2 - S - R).
+// parity_safe() holds these and the planner keeps to them.  With R < G (two
+// slots against three groups, as three K chunks per stage would leave) small
+// cases ran exact at S = 4 while a full-size run never finished.
 // PB = lcm(G, R): each use of a named barrier has the same warps, and the
 // decoders of stage i+PB cannot arrive before the issuer of stage i has passed
 // it (they first wait, through the TMEM slot chain, for MMAs that this issuer
@@ -700,6 +709,17 @@ KernelFn pick_kernel(int T, int CH, int NP)
 int threads_for(int T) { return 32 * (2 + T + 4 * DEC_GROUPS); }
 
 int gcd_i(int a, int b) { return b ? gcd_i(b, a % b) : a; }
+
+// The conditions under which every parity wait of k_packed_gemm is
+// unambiguous, for G decoder groups, R TMEM slots and S shared-memory stages
+// (derived with the kernel's hand-off notes).
+bool parity_safe(int G, int R, int S)
+{
+    const bool slots = G <= R;                                 // aempty
+    const bool stages = S >= G + R || S % G == 0 || R % G == 0; // full
+    const bool release = S % 2 == 0 || S >= R + 2;             // empty
+    return slots && stages && release;
+}
 int lcm_i(int a, int b) { return a / gcd_i(a, b) * b; }
 
 } // namespace
@@ -744,10 +764,9 @@ int plan_shape(GemmPlan &g, int k, int T_req, int CH_req, int stages_req)
     int ring = (512 - T * np_cls) / (T * CH * 32);
     if (ring > 8) ring = 8;
     if (ring > S - 1) ring = S - 1;
-    while (ring >= 2 && lcm_i(DEC_GROUPS, ring) * T > 15) --ring;
-    // Parity waits need the previous phase of their barrier complete, which
-    // the decoders' chains guarantee only with at least as many TMEM slots as
-    // decoder groups (see the kernel's hand-off notes)
+    // Parity waits need the phase before the awaited one complete; the
+    // kernel's hand-off notes derive when the pipeline guarantees that
+    while (ring >= DEC_GROUPS && !(lcm_i(DEC_GROUPS, ring) * T <= 15 && parity_safe(DEC_GROUPS, ring, S))) --ring;
     if (ring < DEC_GROUPS) return COX_ERR_ARG;
     g.T = T;
     g.CH = CH;

@@ -2,10 +2,11 @@
 every k and every compiled shape and depth, the plan keeps the pipeline's
 invariants, which the kernel's hand-offs rely on:
 
-* ring >= decoder groups: a decoder group's parity waits (on the TMEM slot it
-  refills and on the shared-memory stage it decodes) are unambiguous only when
-  the phase before the awaited one is known to be complete, which the hand-off
-  chains guarantee with at least as many slots as groups;
+* parity waits are unambiguous only when the phase before the awaited one is
+  known to be complete; the hand-off chains guarantee that when ring >= decoder
+  groups (TMEM-slot waits), when stages >= groups + ring or either is a multiple
+  of the groups (shared-memory-stage waits), and when stages are even or
+  >= ring + 2 (the two producer warps' release waits);
 * ring < stages: the producer of stage i waits for the decoders of stage
   i - S + ring, who must not be waiting for that producer;
 * lcm(groups, ring) x tiles <= 15 hardware named barriers (0 is __syncthreads);
@@ -28,9 +29,18 @@ def lib():
     return L.load()
 
 
+def _parity_safe(G, R, S):
+    """The kernel's conditions for unambiguous parity waits: TMEM-slot waits
+    need G <= R; shared-memory-stage waits need S >= G + R, S a multiple of G
+    or R a multiple of G; the two producer warps' release waits need S even or
+    S >= R + 2."""
+    return G <= R and (S >= G + R or S % G == 0 or R % G == 0) and (S % 2 == 0 or S >= R + 2)
+
+
 def _check(k, p):
     assert p.limb_cols >= 4 * k and p.limb_cols in (16, 32, 64, 128, 256)
     assert p.ring >= p.decoder_groups
+    assert _parity_safe(p.decoder_groups, p.ring, p.stages)
     assert p.ring < p.stages
     assert p.stages >= p.decoder_groups + 1
     assert p.named_barriers == math.lcm(p.decoder_groups, p.ring) * p.tile_m <= 15
@@ -69,6 +79,15 @@ def test_default_shape(k):
     # the built-in default: two row tiles up to 128 limb columns, two K chunks up to 64
     assert p.tile_m == (2 if p.limb_cols <= 128 else 1)
     assert p.chunks == (2 if p.limb_cols <= 64 else 1)
+
+
+def test_widest_limb_class_keeps_a_safe_ring():
+    """256 limb columns (k > 32) fit five stages; four slots would leave the
+    shared-memory waits without a guarantee (5 < 3 + 4, neither a multiple of
+    3, 5 odd and < 4 + 2), so the planner takes three."""
+    rc, p = L.cox_plan_shape(64)
+    assert rc == 0 and (p.tile_m, p.chunks, p.stages, p.ring) == (1, 1, 5, 3)
+    assert not _parity_safe(3, 4, 5) and _parity_safe(3, 3, 5)
 
 
 def test_rejections():
