@@ -34,6 +34,15 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(int(stream))
 
 
+def plan_shape(k: int, tile_m: int = 0, chunks: int = 0, stages: int = 0) -> dict:
+    """The tensor-core products' pipeline plan for k columns (cox_plan_shape):
+    shape, shared-memory depth, TMEM slots, barriers and memory.  Host only;
+    raises CoxError for a shape or depth the pipeline does not allow."""
+    rc, p = L.cox_plan_shape(int(k), int(tile_m), int(chunks), int(stages))
+    L.check(rc, "cox_plan_shape")
+    return {f: getattr(p, f) for f, _ in L.cox_plan._fields_}
+
+
 class CoxProblem:
     """A data set (X, y, delta) laid out on the GPU (``cox_setup``).
 

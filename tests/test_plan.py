@@ -98,3 +98,11 @@ def test_rejections():
     assert L.cox_plan_shape(64, 2, 2)[0] == L.COX_ERR_ARG      # 256 limb columns take one tile, one chunk
     assert L.cox_plan_shape(16, -1, 0)[0] == L.COX_ERR_ARG
     assert L.load().cox_plan_shape(16, 0, 0, 0, None) == L.COX_ERR_ARG
+
+
+def test_front_end_wrapper():
+    from paper_2010_16114_gb300.cox import plan_shape
+    d = plan_shape(16)
+    assert (d["tile_m"], d["chunks"], d["stages"], d["ring"], d["limb_cols"]) == (2, 2, 6, 3, 64)
+    with pytest.raises(L.CoxError):
+        plan_shape(16, chunks=3)
