@@ -18,6 +18,10 @@ the passage of arXiv 2010.16114 (DistStat.jl) it follows:
 * ``opnorm2`` -- Section 4.4 power method; ``lipschitz`` = 2 ||X_c||_2^2 / n
   from the step-size remark in Section 5.3.
 * ``ista`` -- the Section 5.3 iteration repeated.
+* ``ista_unpen`` -- the iteration with an unpenalised block (Section 6: sex
+  and principal components enter unpenalised).
+* ``path`` -- the Section 6 lambda path with the lag stopping rule.
+* ``rank_by_entry`` -- the Section 6 SNP ranking by entry lambda.
 """
 from __future__ import annotations
 
@@ -75,6 +79,13 @@ def _lib(long_double: bool = False):
         lib.orc_ista.argtypes = [_i64, _i64, _p, _p, _p, _p, _f64, _f64, _i64, _p, _p, _p]
         lib.orc_opnorm2.restype = _f64
         lib.orc_opnorm2.argtypes = [_i64, _i64, _p, _p, _p, _f64, _i64, _p]
+        lib.orc_ista_unpen.restype = ctypes.c_int
+        lib.orc_ista_unpen.argtypes = [_i64, _i64, _p, _p, _i64, _p, _p, _p, _f64, _f64, _i64, _p, _p, _p]
+        lib.orc_path.restype = ctypes.c_int
+        lib.orc_path.argtypes = [_i64, _i64, _p, _p, _i64, _p, _p, _p, _f64, _i64, _p, _f64, _i64, _i64,
+                                 ctypes.c_int, _p, _p, _p]
+        lib.orc_rank_by_entry.restype = _i64
+        lib.orc_rank_by_entry.argtypes = [_i64, _i64, _p, _p, _p, _p]
         _loaded[long_double] = lib
     return _loaded[long_double]
 
@@ -212,3 +223,71 @@ def lambda_max(X, mu, y, delta) -> float:
     """Smallest lambda with beta = 0 optimal: ||g(0)||_inf."""
     W, u, _ = risk(y, delta, np.zeros(len(y)))
     return float(np.max(np.abs(grad(X, mu, delta, u))))
+
+
+def _zcols(Z, n: int) -> np.ndarray:
+    """Z (n x q, any layout) as a column-major float64 array; None -> q = 0."""
+    if Z is None:
+        return np.zeros((n, 0))
+    Z = np.asarray(Z, dtype=np.float64)
+    if Z.ndim == 1:
+        Z = Z[:, None]
+    return Z
+
+
+def ista_unpen(X, mu, Z, y, delta, sigma: float, lam: float, iters: int, beta0=None, gamma0=None):
+    """ISTA with an unpenalised block Z (Section 6: sex and principal
+    components enter unpenalised): beta thresholded, gamma a plain gradient
+    step.  Returns (beta, gamma, F_trace)."""
+    Xc = _cols(X)
+    n, p = Xc.shape
+    Zc = _cols(_zcols(Z, n))
+    q = Zc.shape[1]
+    beta = np.zeros(p) if beta0 is None else _f(beta0).copy()
+    gamma = np.zeros(max(q, 1)) if gamma0 is None else _f(gamma0).copy()
+    F = np.zeros(max(iters, 1))
+    rc = _lib().orc_ista_unpen(n, p, _ptr(Xc), _ptr(None if mu is None else _f(mu)), q, _ptr(Zc),
+                               _ptr(_f(y)), _ptr(_u8(delta)), sigma, lam, iters, _ptr(beta), _ptr(gamma),
+                               _ptr(F))
+    if rc != 0:
+        raise FloatingPointError(f"orc_ista_unpen returned {rc}")
+    return beta, gamma[:q], F[:iters]
+
+
+def path(X, mu, Z, y, delta, sigma: float, lams, tol: float = 1e-5, lag: int = 10,
+         max_iter: int = 1000, warm: bool = False):
+    """The Section 6 lambda path: each lambda solved by ISTA (with the
+    unpenalised block Z, may be None) until |F_t - F_{t-lag}| / |F_t + 1| < tol
+    or max_iter, from zero or, warm, from the previous lambda's solution.
+    Returns (B (L x p), G (L x q), iters (L))."""
+    Xc = _cols(X)
+    n, p = Xc.shape
+    Zc = _cols(_zcols(Z, n))
+    q = Zc.shape[1]
+    lams = _f(lams)
+    L = len(lams)
+    B = np.zeros((L, p))
+    G = np.zeros((L, max(q, 1)))
+    it = np.zeros(L, np.int64)
+    rc = _lib().orc_path(n, p, _ptr(Xc), _ptr(None if mu is None else _f(mu)), q, _ptr(Zc), _ptr(_f(y)),
+                         _ptr(_u8(delta)), sigma, L, _ptr(lams), tol, lag, max_iter, int(bool(warm)),
+                         _ptr(B), _ptr(G), _ptr(it))
+    if rc != 0:
+        raise FloatingPointError(f"orc_path returned {rc}")
+    return B, G[:, :q], it
+
+
+def rank_by_entry(lams, B):
+    """Section 6 SNP ranking: SNPs with a nonzero coefficient on the path,
+    ordered by the largest lambda at which they are nonzero, ties by |beta|
+    there, then by index.  B is L x p (row l = coefficients at lams[l]).
+    Returns (order, entry): entry[j] = index of SNP j's entry lambda or -1."""
+    lams = _f(lams)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    L, p = B.shape
+    order = np.zeros(max(p, 1), np.int64)
+    entry = np.zeros(max(p, 1), np.int64)
+    cnt = _lib().orc_rank_by_entry(p, L, _ptr(lams), _ptr(B), _ptr(order), _ptr(entry))
+    if cnt < 0:
+        raise MemoryError("orc_rank_by_entry")
+    return order[:cnt], entry[:p]

@@ -329,3 +329,148 @@ double orc_opnorm2(int64_t n, int64_t p, const double *X, const double *mu, cons
     free(v); free(a); free(b);
     return (double)SQRT(s);
 }
+
+/* ---- Section 6: unpenalised covariates, the lambda path, SNP ranking -- */
+
+/*
+ * ISTA with an unpenalised block (Section 6: sex and the top ten principal
+ * components enter the UK Biobank model without a penalty):
+ *   eta   = X_c beta + Z gamma,
+ *   g_X   = X_c^T (delta - u) / n,   g_Z = Z^T (delta - u) / n,
+ *   beta  <- S(beta + sigma g_X, sigma lambda),   gamma <- gamma + sigma g_Z,
+ *   F     = f(beta, gamma) + lambda ||beta||_1.
+ * Z is column-major n x q and used as given (the partial likelihood does not
+ * change when a column of Z is shifted).  q = 0 is plain ISTA.  beta and gamma
+ * are updated in place; F_trace[t] (may be NULL) is F at the iterate entering
+ * iteration t.
+ */
+int orc_ista_unpen(int64_t n, int64_t p, const double *X, const double *mu, int64_t q,
+                   const double *Z, const double *y, const uint8_t *delta, double sigma,
+                   double lam, int64_t iters, double *beta, double *gamma, double *F_trace)
+{
+    double *eta = (double *)malloc((size_t)n * sizeof(double));
+    double *etz = (double *)malloc((size_t)n * sizeof(double));
+    double *W = (double *)malloc((size_t)n * sizeof(double));
+    double *u = (double *)malloc((size_t)n * sizeof(double));
+    double *gx = (double *)malloc((size_t)(p > 0 ? p : 1) * sizeof(double));
+    double *gz = (double *)malloc((size_t)(q > 0 ? q : 1) * sizeof(double));
+    if (!eta || !etz || !W || !u || !gx || !gz) {
+        free(eta); free(etz); free(W); free(u); free(gx); free(gz);
+        return -2;
+    }
+    int rc = 0;
+    for (int64_t t = 0; t < iters; ++t) {
+        orc_eta(n, p, X, mu, beta, eta);
+        if (q > 0) {
+            orc_eta(n, q, Z, NULL, gamma, etz);
+            for (int64_t i = 0; i < n; ++i) eta[i] = (double)((real)eta[i] + (real)etz[i]);
+        }
+        double f;
+        rc = orc_risk(n, y, delta, eta, W, u, &f);
+        if (rc) break;
+        if (F_trace) {
+            real l1 = 0;
+            for (int64_t j = 0; j < p; ++j) l1 += FABS((real)beta[j]);
+            F_trace[t] = (double)((real)f + (real)lam * l1);
+        }
+        orc_grad(n, p, X, mu, delta, u, gx);
+        if (q > 0) orc_grad(n, q, Z, NULL, delta, u, gz);
+        orc_prox(p, beta, gx, sigma, lam, beta);
+        for (int64_t c = 0; c < q; ++c) gamma[c] = (double)((real)gamma[c] + (real)sigma * (real)gz[c]);
+    }
+    free(eta); free(etz); free(W); free(u); free(gx); free(gz);
+    return rc;
+}
+
+/*
+ * The lambda path of Section 6: for each lambda_l (in the order given), ISTA
+ * with the unpenalised block from beta = gamma = 0, or, when warm != 0, from
+ * the previous lambda's solution, run in blocks of `lag` iterations until
+ * the stopping rule |F_t - F_{t-lag}| / |F_t + 1| < tol holds (F_t = F at the
+ * iterate entering iteration t; tested after each block once more than lag
+ * values exist; F penalised) or max_iter iterations have run.
+ *   B: p x L (column l = beta at lambda_l), G: q x L, iters: L (may be NULL).
+ * Returns 0, -1 for bad arguments, -2 for allocation failure, -3 if a
+ * lambda's risk set degenerates (as orc_risk).
+ */
+int orc_path(int64_t n, int64_t p, const double *X, const double *mu, int64_t q, const double *Z,
+             const double *y, const uint8_t *delta, double sigma, int64_t L, const double *lams,
+             double tol, int64_t lag, int64_t max_iter, int warm, double *B, double *G,
+             int64_t *iters)
+{
+    if (lag < 1 || max_iter < 0 || L < 0) return -1;
+    double *beta = (double *)calloc((size_t)(p > 0 ? p : 1), sizeof(double));
+    double *gamma = (double *)calloc((size_t)(q > 0 ? q : 1), sizeof(double));
+    double *hist = (double *)malloc((size_t)(max_iter > 0 ? max_iter : 1) * sizeof(double));
+    if (!beta || !gamma || !hist) { free(beta); free(gamma); free(hist); return -2; }
+    int rc = 0;
+    for (int64_t l = 0; l < L && rc == 0; ++l) {
+        if (!warm) {
+            memset(beta, 0, (size_t)(p > 0 ? p : 1) * sizeof(double));
+            memset(gamma, 0, (size_t)(q > 0 ? q : 1) * sizeof(double));
+        }
+        int64_t t = 0;
+        while (t < max_iter) {
+            const int64_t steps = (max_iter - t < lag) ? (max_iter - t) : lag;
+            rc = orc_ista_unpen(n, p, X, mu, q, Z, y, delta, sigma, lams[l], steps, beta, gamma, hist + t);
+            if (rc) break;
+            t += steps;
+            if (t > lag && FABS((real)hist[t - 1] - (real)hist[t - 1 - lag]) / FABS((real)hist[t - 1] + 1) < (real)tol)
+                break;
+        }
+        memcpy(B + l * p, beta, (size_t)p * sizeof(double));
+        if (q > 0) memcpy(G + l * q, gamma, (size_t)q * sizeof(double));
+        if (iters) iters[l] = t;
+    }
+    free(beta); free(gamma); free(hist);
+    return rc;
+}
+
+/* ranking keys of one SNP: the index of its entry lambda and |beta| there */
+typedef struct { int64_t j; int64_t entry; double mag; } orc_entry;
+
+static const double *orc_rank_lams;
+
+static int cmp_entry(const void *pa, const void *pb)
+{
+    const orc_entry *a = (const orc_entry *)pa, *b = (const orc_entry *)pb;
+    const double la = orc_rank_lams[a->entry], lb = orc_rank_lams[b->entry];
+    if (la != lb) return la > lb ? -1 : 1;        /* larger entry lambda first */
+    if (a->mag != b->mag) return a->mag > b->mag ? -1 : 1;  /* then larger |beta| */
+    return (a->j > b->j) - (a->j < b->j);         /* then the SNP index */
+}
+
+/*
+ * SNP ranking of Section 6: each SNP with a nonzero coefficient somewhere on
+ * the path is ranked by the largest lambda at which its coefficient is
+ * nonzero, ties broken by the absolute value of the coefficient at that
+ * lambda (when it joins the model), then by SNP index.  B is p x L
+ * column-major, lams the L penalties (any order).  Writes the ranked SNP
+ * indices to order[0 .. count) and, per SNP, the index of its entry lambda
+ * to entry[j] (-1 if never selected); returns count, or -2 on allocation
+ * failure.
+ */
+int64_t orc_rank_by_entry(int64_t p, int64_t L, const double *lams, const double *B, int64_t *order,
+                          int64_t *entry)
+{
+    orc_entry *e = (orc_entry *)malloc((size_t)(p > 0 ? p : 1) * sizeof(orc_entry));
+    if (!e) return -2;
+    int64_t count = 0;
+    for (int64_t j = 0; j < p; ++j) {
+        int64_t best = -1;
+        for (int64_t l = 0; l < L; ++l)
+            if (B[l * p + j] != 0.0 && (best < 0 || lams[l] > lams[best])) best = l;
+        entry[j] = best;
+        if (best >= 0) {
+            e[count].j = j;
+            e[count].entry = best;
+            e[count].mag = fabs(B[best * p + j]);
+            ++count;
+        }
+    }
+    orc_rank_lams = lams;
+    qsort(e, (size_t)count, sizeof(orc_entry), cmp_entry);
+    for (int64_t c = 0; c < count; ++c) order[c] = e[c].j;
+    free(e);
+    return count;
+}

@@ -302,3 +302,140 @@ def test_long_double_twin_agrees(orc):
     g = orc.grad(X, mu, w.delta, u)
     gl = orc.grad(X, mu, w.delta, ul, long_double=True)
     np.testing.assert_allclose(g, gl, rtol=1e-10, atol=1e-13 * np.abs(gl).max())
+
+
+# --- Section 6: unpenalised covariates, the lambda path, SNP ranking ---------
+
+def _cox_newton_root(x, y, delta, iters=50):
+    """Root of the one-covariate Cox score (Breslow risk sets y_j >= y_i) by
+    Newton's method on score and information written from the partial
+    likelihood in numpy."""
+    b = 0.0
+    for _ in range(iters):
+        e = np.exp(b * x)
+        U = I = 0.0
+        for i in np.nonzero(delta)[0]:
+            R = y >= y[i]
+            s0, s1, s2 = e[R].sum(), (e[R] * x[R]).sum(), (e[R] * x[R] ** 2).sum()
+            U += x[i] - s1 / s0
+            I += s2 / s0 - (s1 / s0) ** 2
+        b += U / I
+    return b
+
+
+def _unpen_problem(q=2, seed=41, n=300, p=25):
+    w, X, mu = _small_problem(n=n, p=p)
+    r = _rng(seed)
+    Z = np.column_stack([(r.random(n) < 0.5).astype(float)] + [r.normal(0, 1, n) for _ in range(q - 1)])
+    return w, X, mu, Z
+
+
+def test_unpen_without_block_is_plain_ista(orc):
+    w, X, mu = _small_problem()
+    lam, sigma = 0.01, 0.05
+    b1, F1, _ = orc.ista(X, mu, w.y, w.delta, sigma, lam, 30)
+    b2, g2, F2 = orc.ista_unpen(X, mu, None, w.y, w.delta, sigma, lam, 30)
+    assert np.array_equal(b1, b2) and np.array_equal(F1, F2) and len(g2) == 0
+
+
+def test_unpen_block_alone_reaches_the_cox_mle(orc):
+    """With the SNPs held at zero by a penalty above lambda_max, the
+    unpenalised coefficient converges to the root of its Cox score."""
+    r = _rng(32)
+    n = 250
+    y = r.integers(1, 40, n).astype(float)
+    z = r.normal(0, 1, n) + 3.0
+    delta = (r.random(n) < 0.5).astype(np.uint8)
+    X = r.integers(0, 3, (n, 4)).astype(float)
+    b = _cox_newton_root(z, y, delta)
+    L = 2 * np.sum((z - z.mean()) ** 2) / n
+    beta, gamma, F = orc.ista_unpen(X, X.mean(0), z, y, delta, 1.0 / L, 1e6, 20000)
+    assert np.all(beta == 0)
+    assert abs(gamma[0] - b) <= 1e-9 * max(1, abs(b))
+
+
+def test_unpen_block_shift_invariance(orc):
+    """The partial likelihood does not see a shift of a covariate column, so
+    the iterates do not either (1'(delta - u) = 0)."""
+    w, X, mu, Z = _unpen_problem()
+    args = (w.y, w.delta, 0.05, 0.02, 40)
+    b1, g1, F1 = orc.ista_unpen(X, mu, Z, *args)
+    b2, g2, F2 = orc.ista_unpen(X, mu, Z + np.array([3.0, -7.0]), *args)
+    np.testing.assert_allclose(b1, b2, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(g1, g2, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(F1, F2, rtol=1e-12)
+
+
+def test_unpen_kkt_and_monotone(orc):
+    """At the fixed point the unpenalised block is stationary (Z'(delta-u)/n
+    = 0) and the SNPs satisfy the lasso KKT conditions; F never increases."""
+    w, X, mu, Z = _unpen_problem()
+    XZ = np.column_stack([X - mu, Z - Z.mean(0)])
+    L = 2 * np.linalg.norm(XZ, 2) ** 2 / w.n
+    lam = 0.3 * orc.lambda_max(X, mu, w.y, w.delta)
+    beta, gamma, F = orc.ista_unpen(X, mu, Z, w.y, w.delta, 1.0 / L, lam, 60000)
+    assert np.all(np.diff(F) <= 1e-14 * np.abs(F[1:]))
+    eta = orc.eta(X, mu, beta) + Z @ gamma
+    _, u, _ = orc.risk(w.y, w.delta, eta)
+    gz = Z.T @ (w.delta - u) / w.n
+    gx = orc.grad(X, mu, w.delta, u)
+    assert np.max(np.abs(gz)) <= 1e-9
+    zero = beta == 0
+    assert zero.any() and (~zero).any()
+    assert np.all(np.abs(gx[zero]) <= lam * (1 + 1e-6))
+    np.testing.assert_allclose(gx[~zero], lam * np.sign(beta[~zero]), rtol=0, atol=1e-6 * lam)
+
+
+def test_path_stopping_rule(orc):
+    """Section 6 rule |F_t - F_{t-lag}| / |F_t + 1| < tol, tested every lag
+    iterations once more than lag values exist: above lambda_max F never
+    moves, so the rule fires at the first test after 2 lag iterations; with
+    tol = 0 every lambda runs max_iter iterations and equals plain ISTA."""
+    w, X, mu = _small_problem()
+    lmax = orc.lambda_max(X, mu, w.y, w.delta)
+    B, G, it = orc.path(X, mu, None, w.y, w.delta, 0.05, [2 * lmax], tol=1e-5, lag=10, max_iter=500)
+    assert it[0] == 20 and np.all(B[0] == 0)
+    B, G, it = orc.path(X, mu, None, w.y, w.delta, 0.05, [0.4 * lmax, 0.2 * lmax], tol=0.0, lag=10,
+                        max_iter=57)
+    assert list(it) == [57, 57]
+    for l, lam in enumerate([0.4 * lmax, 0.2 * lmax]):
+        b, _, _ = orc.ista(X, mu, w.y, w.delta, 0.05, lam, 57)
+        assert np.array_equal(B[l], b)
+
+
+def test_path_warm_and_cold_reach_one_solution(orc):
+    """Warm starts change the route, not the (unique, p < events) minimiser:
+    run long enough, both paths agree.  (The stopping rule watches F, which
+    flattens to rounding level before slow directions of the parameters, such
+    as a binary covariate's, have settled; it is no certificate at 1e-7 in
+    beta.)  At the paper's tolerance the warm path needs fewer iterations."""
+    w, X, mu, Z = _unpen_problem(p=12)
+    XZ = np.column_stack([X - mu, Z - Z.mean(0)])
+    sigma = 1.0 / (2 * np.linalg.norm(XZ, 2) ** 2 / w.n)
+    lmax = orc.lambda_max(X, mu, w.y, w.delta)
+    lams = lmax * np.array([0.8, 0.5, 0.3, 0.15])
+    Bc, Gc, _ = orc.path(X, mu, Z, w.y, w.delta, sigma, lams, tol=0.0, lag=10, max_iter=30000)
+    Bw, Gw, _ = orc.path(X, mu, Z, w.y, w.delta, sigma, lams, tol=0.0, lag=10, max_iter=30000, warm=True)
+    np.testing.assert_allclose(Bw, Bc, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(Gw, Gc, rtol=0, atol=1e-9)
+    _, _, itc = orc.path(X, mu, Z, w.y, w.delta, sigma, lams, tol=1e-5, lag=10, max_iter=30000)
+    _, _, itw = orc.path(X, mu, Z, w.y, w.delta, sigma, lams, tol=1e-5, lag=10, max_iter=30000, warm=True)
+    assert itw[1:].sum() < itc[1:].sum() and itw[0] == itc[0]
+
+
+def test_rank_by_entry_hand_example(orc):
+    """Largest lambda with a nonzero coefficient first; ties by |beta| at entry,
+    then by index; the order of the lambdas given does not matter."""
+    lams = np.array([0.3, 0.2, 0.1])
+    B = np.array([[0.0, 0.5, 0.0, 0.0, 0.0, 0.0],
+                  [0.1, 0.7, -0.3, 0.0, 0.0, 0.1],
+                  [0.2, 0.9, -0.4, 0.0, 0.05, 0.0]])
+    order, entry = orc.rank_by_entry(lams, B)
+    # SNP 1 joins at 0.3; SNPs 2, 0, 5 at 0.2 (|beta| 0.3, then 0.1 and 0.1 by index);
+    # SNP 4 at 0.1; SNP 5 leaves again, which does not move its entry; SNP 3 never joins
+    assert list(order) == [1, 2, 0, 5, 4]
+    assert list(entry) == [1, 0, 1, -1, 2, 1]
+    perm = [2, 0, 1]
+    order2, entry2 = orc.rank_by_entry(lams[perm], B[perm])
+    assert list(order2) == [1, 2, 0, 5, 4]
+    assert [perm[e] if e >= 0 else -1 for e in entry2] == list(entry)
