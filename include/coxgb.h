@@ -276,6 +276,23 @@ typedef struct cox_plan {
 } cox_plan;
 int cox_plan_shape(int k, int tile_m, int chunks, int stages, cox_plan *out);
 
+/*
+ * SNP ranking of Section 6 on a lambda path's coefficients (host arithmetic,
+ * no device or handle): every SNP with a nonzero coefficient at some lambda
+ * is ranked by the largest lambda at which it is nonzero, ties broken by the
+ * absolute value of its coefficient at that lambda (when it joins the model),
+ * then by SNP index.
+ *   lambdas   : L penalties (host, finite, any order).
+ *   B_host    : p x L coefficients, column-major as cox_path_fit writes them
+ *               (column l at lambdas[l]); float, or double when dbl != 0.
+ *   order_host: p int64 (out): the ranked SNP indices in entries 0 .. count-1.
+ *   entry_host: p int64 (out): per SNP the index l of its entry lambda, or -1.
+ *   count_out : the number of ranked SNPs.
+ * Errors: COX_ERR_ARG for NULL pointers, p < 1, L < 1 or a non-finite lambda.
+ */
+int cox_rank_by_entry(int64_t p, int L, const double *lambdas, const void *B_host, int dbl,
+                      int64_t *order_host, int64_t *entry_host, int64_t *count_out);
+
 /* Switch a genotype handle between COX_SPLIT_E4M3 and COX_FP32_GEMV; both
  * read the same resident tiles.  Drops the per-k workspace.  Errors:
  * COX_ERR_UNSUPPORTED for COX_FP64 handles or targets. */

@@ -36,7 +36,7 @@ EXPORTS = [
     "cox_loss_grad", "cox_prox_step", "cox_prox_step_host", "cox_sync", "cox_last_objective",
     "cox_path_fit", "cox_get_state", "cox_set_state", "cox_get_info", "cox_get_mu_order",
     "cox_strerror", "cox_set_precision", "cox_profile", "cox_profile_read", "cox_lipschitz_noalloc",
-    "cox_autotune", "cox_eta", "cox_plan_shape",
+    "cox_autotune", "cox_eta", "cox_plan_shape", "cox_rank_by_entry",
 ]
 
 
@@ -128,6 +128,8 @@ def load(path: str | None = None):
     lib.cox_autotune.argtypes = [P, I, I, ctypes.POINTER(cox_tune_choice), ctypes.POINTER(cox_tune_choice)]
     lib.cox_plan_shape.restype = I
     lib.cox_plan_shape.argtypes = [I, I, I, I, ctypes.POINTER(cox_plan)]
+    lib.cox_rank_by_entry.restype = I
+    lib.cox_rank_by_entry.argtypes = [I64, I, P, P, I, P, P, ctypes.POINTER(I64)]
     lib.cox_strerror.restype = ctypes.c_char_p
     lib.cox_strerror.argtypes = [I]
     _lib = lib

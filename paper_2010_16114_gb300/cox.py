@@ -43,6 +43,32 @@ def plan_shape(k: int, tile_m: int = 0, chunks: int = 0, stages: int = 0) -> dic
     return {f: getattr(p, f) for f, _ in L.cox_plan._fields_}
 
 
+def rank_by_entry(lambdas, beta):
+    """Section 6 SNP ranking (cox_rank_by_entry, host): SNPs with a nonzero
+    coefficient on the path ordered by the largest lambda at which they are
+    nonzero, ties by |beta| there, then by index.  beta: (k, p) coefficients
+    (row c at lambdas[c]), a tensor (any device) or an array, float32 or
+    float64.  Returns (order, entry): entry[j] = index of SNP j's entry lambda
+    or -1."""
+    if isinstance(beta, torch.Tensor):
+        beta = beta.detach().cpu().numpy()
+    B = np.ascontiguousarray(beta)
+    if B.dtype not in (np.float32, np.float64):
+        B = B.astype(np.float64)
+    if B.ndim == 1:
+        B = B[None]
+    k, p = B.shape
+    lams = np.ascontiguousarray(np.atleast_1d(np.asarray(lambdas, dtype=np.float64)))
+    if len(lams) != k:
+        raise ValueError(f"{len(lams)} lambdas for {k} coefficient rows")
+    order = np.zeros(p, np.int64)
+    entry = np.zeros(p, np.int64)
+    cnt = ctypes.c_int64()
+    L.check(L.load().cox_rank_by_entry(p, k, _vp(lams), _vp(B), int(B.dtype == np.float64), _vp(order),
+                                       _vp(entry), ctypes.byref(cnt)), "cox_rank_by_entry")
+    return order[:cnt.value], entry
+
+
 class CoxProblem:
     """A data set (X, y, delta) laid out on the GPU (``cox_setup``).
 

@@ -631,6 +631,41 @@ int cox_autotune(cox_h h, int k, int reps, cox_tune_choice *xb, cox_tune_choice 
     return COX_OK;
 }
 
+int cox_rank_by_entry(int64_t p, int L, const double *lambdas, const void *B_host, int dbl,
+                      int64_t *order_host, int64_t *entry_host, int64_t *count_out)
+{
+    if (p < 1 || L < 1 || !lambdas || !B_host || !order_host || !entry_host || !count_out) return COX_ERR_ARG;
+    for (int l = 0; l < L; ++l)
+        if (!std::isfinite(lambdas[l])) return COX_ERR_ARG;
+    auto coef = [&](int l, int64_t j) -> double {
+        const int64_t at = static_cast<int64_t>(l) * p + j;
+        return dbl ? static_cast<const double *>(B_host)[at]
+                   : static_cast<double>(static_cast<const float *>(B_host)[at]);
+    };
+    struct Key {
+        int64_t j;
+        int entry;
+        double mag;
+    };
+    std::vector<Key> keys;
+    for (int64_t j = 0; j < p; ++j) {
+        int best = -1;
+        for (int l = 0; l < L; ++l)
+            if (coef(l, j) != 0.0 && (best < 0 || lambdas[l] > lambdas[best])) best = l;
+        entry_host[j] = best;
+        if (best >= 0) keys.push_back(Key{j, best, std::fabs(coef(best, j))});
+    }
+    // the largest entry lambda first; then the larger |beta| on joining; then the index
+    std::sort(keys.begin(), keys.end(), [&](const Key &a, const Key &b) {
+        if (lambdas[a.entry] != lambdas[b.entry]) return lambdas[a.entry] > lambdas[b.entry];
+        if (a.mag != b.mag) return a.mag > b.mag;
+        return a.j < b.j;
+    });
+    for (size_t c = 0; c < keys.size(); ++c) order_host[c] = keys[c].j;
+    *count_out = static_cast<int64_t>(keys.size());
+    return COX_OK;
+}
+
 int cox_plan_shape(int k, int tile_m, int chunks, int stages, cox_plan *out)
 {
     if (!out || tile_m < 0 || chunks < 0 || stages < 0) return COX_ERR_ARG;
