@@ -115,3 +115,42 @@ def test_no_device_is_reported_not_crashed(lib):
     vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     rc, h = L.cox_setup(vp(X), 4, 3, L.COX_X_INT8_HOST, vp(t), vp(e), None)
     assert rc in (L.COX_ERR_CUDA, L.COX_ERR_UNSUPPORTED) and not h.value
+
+
+def test_plain_c_program_links_and_calls(lib, tmp_path):
+    """A C11 program links libcoxgb.so through the header alone and calls the
+    entry points that need no device: defaults, error names, a pipeline plan
+    and the SNP ranking, and sees a handle-free argument error."""
+    import subprocess
+    src = tmp_path / "use.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "coxgb.h"
+int main(void) {
+    cox_options o;
+    cox_default_options(&o);
+    if (o.precision != COX_SPLIT_E4M3 || o.lag != 10) return 1;
+    if (strcmp(cox_strerror(COX_OK), "ok") != 0) return 2;
+    cox_plan pl;
+    if (cox_plan_shape(16, 0, 0, 0, &pl) != COX_OK || pl.ring < pl.decoder_groups) return 3;
+    if (cox_plan_shape(0, 0, 0, 0, &pl) != COX_ERR_ARG) return 4;
+    const double lam[3] = {0.3, 0.2, 0.1};
+    const float B[3 * 4] = {0.f, 0.5f, 0.f, 0.f,    /* lambda 0.3: SNP 1 */
+                            0.1f, 0.7f, -0.3f, 0.f, /* lambda 0.2: SNPs 0, 2 join */
+                            0.2f, 0.9f, -0.4f, 0.f};
+    int64_t order[4], entry[4], count = -1;
+    if (cox_rank_by_entry(4, 3, lam, B, 0, order, entry, &count) != COX_OK) return 5;
+    if (count != 3 || order[0] != 1 || order[1] != 2 || order[2] != 0 || entry[3] != -1) return 6;
+    if (cox_loss_grad(NULL, NULL, 1, NULL, NULL, NULL) != COX_ERR_ARG) return 7;
+    cox_destroy(NULL);
+    puts("ok");
+    return 0;
+}
+''')
+    exe = tmp_path / "use"
+    libdir = os.path.join(ROOT, "paper_2010_16114_gb300")
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                    "-L", libdir, "-lcoxgb", f"-Wl,-rpath,{libdir}"], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
