@@ -90,7 +90,7 @@ def gemm_traffic(k: int, n: int, p: int):
     """DRAM bytes per launch of the tensor-core product from the committed ncu
     summary, scaled by n*p codes; None when the kernel source changed since."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_packed_gemm_traffic.txt")
+    path = os.path.join(ROOT, "profiles", "k_packed_gemm_traffic_n65536_p65536_k16.txt")
     src = os.path.join(ROOT, "paper_2010_16114_gb300", "csrc", "gemm_tc.cu")
     try:
         kv = {}
