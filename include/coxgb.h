@@ -146,10 +146,14 @@ int cox_lipschitz(cox_h h, const double *start_host, double tol, int maxiter, do
  * plus 8 p when start_host is given, each term rounded up to 256; larger
  * problems get COX_ERR_ARG (n_pad, p_pad from cox_get_info).
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Calls share the array: calls that overlap on
- * the GPU race; each call writes everything it reads.  Calls no cudaMalloc,
- * cudaFree or allocating library routine.  Synchronous (legacy stream).
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life
+ * of the process; make that first call before any stream capture.  A device
+ * reset (cudaDeviceReset, or an embedder resetting the primary context)
+ * invalidates that address as it does every handle: neither a handle nor
+ * this call may be used across a reset.  Calls share the array: calls that
+ * overlap on the GPU race; each call writes everything it reads.  Calls no
+ * cudaMalloc, cudaFree or allocating library routine.  Synchronous (legacy
+ * stream).
  */
 int cox_lipschitz_noalloc(cox_h h, const double *start_host, double tol, int maxiter, double *L_out);
 

@@ -166,7 +166,7 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
         sa.lam = ws.lam;
         sa.need_loss = true;
         {
-            Site s_(h, 2, 7, st);
+            Site s_(h, 2, 8, st);
             COX_TRY(run_scans(h, sa, st));
         }
         EpiArgs e4;
@@ -215,7 +215,7 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
         sa.lam = ws.lam;
         sa.need_loss = true;
         {
-            Site s_(h, 2, 7, st);
+            Site s_(h, 2, 8, st);
             COX_TRY(run_scans(h, sa, st));
         }
         Site s4_(h, 1, 1, st);
@@ -251,7 +251,7 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
         sa.lam = ws.lam + c;
         sa.need_loss = true;
         {
-            Site s_(h, 2, 7, st);
+            Site s_(h, 2, 8, st);
             COX_TRY(run_scans(h, sa, st));
         }
         COX_CUDA(cudaMemcpyAsync(ws.Fring + c, ws.F, sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -424,7 +424,7 @@ void cox_destroy(cox_h h)
     cudaDeviceSynchronize();
     free_workspace(h);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
-    void *ptrs[] = {h->d_head, h->d_tail, h->d_delta, h->d_mu, h->d_A1, h->d_A4, h->d_Xr, h->d_Xc, h->d_err};
+    void *ptrs[] = {h->d_head, h->d_tail, h->d_evhead, h->d_delta, h->d_mu, h->d_A1, h->d_A4, h->d_Xr, h->d_Xc, h->d_err};
     for (void *p : ptrs) dfree(p);
     delete h;
 }
@@ -493,16 +493,21 @@ int cox_setup(cox_h *out, const void *X, int64_t n, int64_t p, int x_format, con
     std::vector<int32_t> head(static_cast<size_t>(n)), tail(static_cast<size_t>(n));
     std::vector<uint8_t> dsorted(static_cast<size_t>(n));
     int64_t groups = 0;
+    std::vector<int32_t> evhead;  // heads of the tie groups with at least one event
     for (int64_t r = 0; r < n;) {
         int64_t e = r;
         while (e + 1 < n && time[h->h_order[e + 1]] == time[h->h_order[r]]) ++e;
+        bool ev = false;
         for (int64_t s = r; s <= e; ++s) {
             head[s] = static_cast<int32_t>(r);
             tail[s] = static_cast<int32_t>(e);
+            ev = ev || event[h->h_order[s]] != 0;
         }
+        if (ev) evhead.push_back(static_cast<int32_t>(r));
         ++groups;
         r = e + 1;
     }
+    h->n_evhead = static_cast<int64_t>(evhead.size());
     for (int64_t r = 0; r < n; ++r) dsorted[r] = event[h->h_order[r]];
     h->n_groups_tie = groups;
 
@@ -512,6 +517,13 @@ int cox_setup(cox_h *out, const void *X, int64_t n, int64_t p, int x_format, con
         if ((rc = dmalloc(h, reinterpret_cast<void **>(&h->d_err), sizeof(int))) != COX_OK) break;
         if ((rc = dmalloc(h, reinterpret_cast<void **>(&h->d_head), n * sizeof(int32_t))) != COX_OK) break;
         if ((rc = dmalloc(h, reinterpret_cast<void **>(&h->d_tail), n * sizeof(int32_t))) != COX_OK) break;
+        if ((rc = dmalloc(h, reinterpret_cast<void **>(&h->d_evhead), evhead.size() * sizeof(int32_t))) != COX_OK)
+            break;
+        if (!evhead.empty() && cudaMemcpy(h->d_evhead, evhead.data(), evhead.size() * sizeof(int32_t),
+                                          cudaMemcpyHostToDevice) != cudaSuccess) {
+            rc = COX_ERR_CUDA;
+            break;
+        }
         if ((rc = dmalloc(h, reinterpret_cast<void **>(&h->d_delta), n)) != COX_OK) break;
         if ((rc = dmalloc(h, reinterpret_cast<void **>(&h->d_mu), p * sizeof(double))) != COX_OK) break;
         if (cudaMemset(h->d_err, 0, sizeof(int)) != cudaSuccess ||

@@ -180,6 +180,8 @@ struct cox_handle {
     std::vector<double> h_mu;
     // device data
     int32_t *d_head = nullptr, *d_tail = nullptr;
+    int32_t *d_evhead = nullptr;  // first positions of the tie groups that hold an event
+    int64_t n_evhead = 0;
     uint8_t *d_delta = nullptr;
     double *d_mu = nullptr;
     uint32_t *d_A1 = nullptr;  // subject-major 2-bit tiles

@@ -106,6 +106,23 @@ __global__ void k_xta64(const double *__restrict__ Xc, int64_t n, int64_t p, con
     if (lane == 0) b[j] = s;
 }
 
+// v = start / ||start|| (start == null: all entries 1/sqrt(p)); one block.
+template <typename TV>
+__global__ void k_start_vector(const double *__restrict__ start, int64_t p, TV *__restrict__ v)
+{
+    __shared__ double sh[RB];
+    double s = 0.0;
+    for (int64_t j = threadIdx.x; j < p; j += RB) s += start ? start[j] * start[j] : 1.0;
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = RB / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double inv = 1.0 / sqrt(sh[0]);
+    for (int64_t j = threadIdx.x; j < p; j += RB) v[j] = static_cast<TV>((start ? start[j] : 1.0) * inv);
+}
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev)
@@ -138,15 +155,18 @@ int power_method(cox_handle *h, const double *start, double tol, int maxiter, do
         dfree(v); dfree(a); dfree(b); dfree(sc);
         return rc;
     }
-    std::vector<TV> v0(static_cast<size_t>(p));
-    double nv = 0.0;
-    for (int64_t j = 0; j < p; ++j) nv += (start ? start[j] * start[j] : 1.0);
-    nv = std::sqrt(nv);
-    for (int64_t j = 0; j < p; ++j) v0[j] = static_cast<TV>((start ? start[j] : 1.0) / nv);
+    // the start vector is normalised on the device, by the same kernel as in
+    // cox_lipschitz_noalloc, so that both entry points run one power method
+    double *st_dev = nullptr;
+    if (start && (rc = dmalloc(nullptr, reinterpret_cast<void **>(&st_dev), p * sizeof(double))) != COX_OK) {
+        dfree(v); dfree(a); dfree(b); dfree(sc); dfree(a4);
+        return rc;
+    }
     cudaStream_t st = 0;
     double s = 0.0, s_prev = 0.0;
     do {
-        if (cudaMemcpy(v, v0.data(), p * sizeof(TV), cudaMemcpyHostToDevice) != cudaSuccess) { rc = COX_ERR_CUDA; break; }
+        if (start && cudaMemcpy(st_dev, start, p * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) { rc = COX_ERR_CUDA; break; }
+        k_start_vector<TV><<<1, RB, 0, st>>>(st_dev, p, v);
         for (int it = 1; it <= maxiter; ++it) {
             k_dot_mu<TV><<<1, RB, 0, st>>>(h->d_mu, v, p, sc);
             if (f64) {
@@ -184,6 +204,7 @@ int power_method(cox_handle *h, const double *start, double tol, int maxiter, do
     dfree(b);
     dfree(sc);
     dfree(a4);
+    dfree(st_dev);
     if (rc == COX_OK) *L_out = 2.0 * s / static_cast<double>(n);
     return rc;
 }
@@ -452,23 +473,6 @@ int noalloc_scratch(int dev, void **out)
     }
     *out = g_noalloc_addr[dev];
     return COX_OK;
-}
-
-// v = start / ||start|| (start == null: all entries 1/sqrt(p)); one block.
-template <typename TV>
-__global__ void k_start_vector(const double *__restrict__ start, int64_t p, TV *__restrict__ v)
-{
-    __shared__ double sh[RB];
-    double s = 0.0;
-    for (int64_t j = threadIdx.x; j < p; j += RB) s += start ? start[j] * start[j] : 1.0;
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = RB / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
-    }
-    const double inv = 1.0 / sqrt(sh[0]);
-    for (int64_t j = threadIdx.x; j < p; j += RB) v[j] = static_cast<TV>((start ? start[j] : 1.0) * inv);
 }
 
 template <typename TV>

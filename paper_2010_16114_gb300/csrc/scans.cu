@@ -13,6 +13,8 @@
 // Each scan runs in fixed 2048-subject chunks (block scans with warp
 // shuffles), then an exclusive scan of the chunk totals, then a gather; the
 // summation order never depends on timing, so results are bit-reproducible.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace coxgb {
@@ -92,6 +94,8 @@ struct SP {
     int64_t pa, pnb;  // K order of the SNP-major genotype copy (a4_pos)
     const uint8_t *delta;
     const int32_t *head, *tail;
+    const int32_t *evhead;  // first positions of the tie groups that hold an event
+    int64_t n_evh;
     double *eta, *w, *Rt, *Ft, *cmax, *csw, *csd, *suf, *pre, *lossp, *vsp;
 };
 
@@ -213,11 +217,25 @@ __global__ void k_chunks(SP s)
     }
 }
 
-// (3) W = R at the tie head; D = delta / W; loss terms; chunk-local forward scan of D.
-// FAST (the tensor-core and FP32 paths): 1/W in FP32, a relative error of
-// ~6e-8 per term of an FP64 sum (GB300's FP64 divide is slow).  The loss
-// keeps log W in FP64, and the FP64 path keeps both in FP64.
-template <bool FAST>
+// (2b) 1/W in FP64 once per tie group that holds an event: W = R at the
+// group's first position (chunk-local reverse scan plus the suffix of later
+// chunks), and Rt there is overwritten with 1/W.  Every event of the group
+// reads that one value (Breslow: tied events share W), so the FP64 divides
+// number the event times (at most a few thousand with times in whole days),
+// not the events, and run without divergence.
+__global__ void k_inv_w(SP s)
+{
+    const int kk = blockIdx.y;
+    for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < s.n_evh;
+         q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t hd = s.evhead[q];
+        const double W = s.Rt[kk * s.n + hd] + s.suf[kk * s.nch + hd / SCAN_CH];
+        s.Rt[kk * s.n + hd] = 1.0 / W;
+    }
+}
+
+// (3) D = delta / W (from the group heads' 1/W); loss terms; chunk-local
+// forward scan of D, all in FP64.
 __global__ void k_fwd(SP s, bool need_loss)
 {
     __shared__ double sh[NT / 32];
@@ -225,26 +243,25 @@ __global__ void k_fwd(SP s, bool need_loss)
     const int c = blockIdx.x, kk = blockIdx.y;
     const double cmx = need_loss ? column_max(s, kk, sh) : 0.0;
     const int64_t i0 = static_cast<int64_t>(c) * SCAN_CH;
-    // The loss terms log W are summed as the log of their product: each thread
-    // multiplies its W into pm 2^pe (pm in [1, 2)), the warp multiplies its
-    // lanes' products, and one log per warp remains (FP64 log is costly and
-    // events are sparse, so a per-event log would run in most warps anyway).
+    // The loss terms log W = -log(1/W) are summed as the log of a product:
+    // each thread multiplies its 1/W into pm 2^pe (pm in [1, 2)), the warp
+    // multiplies its lanes' products, and one log per warp remains (FP64 log is
+    // costly and events are sparse, so a per-event log would run in most warps
+    // anyway).
     double lsum = 0.0, pm = 1.0;
     int pe = 0;
     for (int e = threadIdx.x; e < SCAN_CH; e += NT) {
         const int64_t i = i0 + e;
         double d = 0.0;
         if (i < s.n && s.delta[i]) {
-            const int64_t hd = s.head[i];
-            const double W = s.Rt[kk * s.n + hd] + s.suf[kk * s.nch + hd / SCAN_CH];
-            d = FAST ? static_cast<double>(1.0f / static_cast<float>(W)) : 1.0 / W;
+            d = s.Rt[kk * s.n + s.head[i]];  // 1/W of i's tie group
             if (need_loss) {
                 lsum -= s.eta[kk * s.n + i] - cmx;
-                if (W >= 0x1p-1022 && W <= 0x1p+1000) {
-                    pm *= W;
+                if (d >= 0x1p-1000 && d <= 0x1p+1022) {
+                    pm *= d;
                     pe += renorm(pm);
                 } else {
-                    lsum += log(W);  // zero, subnormal, huge or NaN: as a plain sum of logs
+                    lsum -= log(d);  // zero, huge, subnormal or NaN: as a plain sum of logs
                 }
             }
         }
@@ -275,7 +292,8 @@ __global__ void k_fwd(SP s, bool need_loss)
             pe += __shfl_xor_sync(0xffffffffu, pe, o);
             pe += renorm(pm);
         }
-        if ((threadIdx.x & 31) == 0) lsum += log(pm) + static_cast<double>(pe) * 0.6931471805599453;
+        // sum of log W over this warp's events = -log(product of 1/W)
+        if ((threadIdx.x & 31) == 0) lsum -= log(pm) + static_cast<double>(pe) * 0.6931471805599453;
         const double t = block_sum(lsum, sh);
         if (threadIdx.x == 0) s.lossp[kk * s.nch + c] = t;
     }
@@ -424,6 +442,8 @@ int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st)
     s.delta = h->d_delta;
     s.head = h->d_head;
     s.tail = h->d_tail;
+    s.evhead = h->d_evhead;
+    s.n_evh = h->n_evhead;
     s.eta = ws.eta;
     s.w = ws.w;
     s.Rt = ws.Rt;
@@ -454,8 +474,11 @@ int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st)
     if (a.exp64) k_rev<true><<<grid, NT, 0, st>>>(s);
     else k_rev<false><<<grid, NT, 0, st>>>(s);
     k_chunks<true><<<a.k, 32, 0, st>>>(s);
-    if (a.exp64) k_fwd<false><<<grid, NT, 0, st>>>(s, a.need_loss);
-    else k_fwd<true><<<grid, NT, 0, st>>>(s, a.need_loss);
+    if (h->n_evhead > 0) {
+        const unsigned gx = static_cast<unsigned>(std::min<int64_t>((h->n_evhead + NT - 1) / NT, 64));
+        k_inv_w<<<dim3(gx, a.k), NT, 0, st>>>(s);
+    }
+    k_fwd<<<grid, NT, 0, st>>>(s, a.need_loss);
     k_chunks<false><<<a.k, 32, 0, st>>>(s);
     switch (a.v_out) {
     case V_LIMBS_E4M3:

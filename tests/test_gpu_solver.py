@@ -30,21 +30,30 @@ def small():
 
 
 def _oracle_path(Xf, mu, y, d, sigma, lam, max_iter, tol, lag=10):
-    """The Section 6 rule on oracle iterates, checked every `lag` iterations."""
+    """The Section 6 rule on oracle iterates, checked every `lag` iterations.
+    Returns (beta, iterations, final F, converged, {t: stopping ratio at t})."""
     beta = np.zeros(Xf.shape[1])
     hist = []
+    ratios = {}
     t = 0
     while t < max_iter:
         steps = min(lag, max_iter - t)
         beta, F, _ = oracle.ista(Xf, mu, y, d, sigma, lam, steps, beta)
         hist.extend(F)
         t += steps
-        if len(hist) > lag and abs(hist[-1] - hist[-1 - lag]) / abs(hist[-1] + 1) < tol:
-            return beta, t, hist[-1], True
-    return beta, t, hist[-1], False
+        if len(hist) > lag:
+            ratios[t] = abs(hist[-1] - hist[-1 - lag]) / abs(hist[-1] + 1)
+            if ratios[t] < tol:
+                return beta, t, hist[-1], True, ratios
+    return beta, t, hist[-1], False, ratios
 
 
 def test_path_fit_matches_oracle_rule(pkg, small):
+    """Each column stops where the oracle's rule stops, and its beta and F match
+    the oracle's there.  The rule is deterministic given F; the counts may differ
+    only where the oracle's stopping ratio lies within the F error of tol, which
+    the test then asserts before it compares beta at the oracle's count (from a
+    fixed-count run): the beta comparison is never skipped."""
     from paper_2010_16114_gb300.cox import CoxProblem
     w, X, Xf, mu, L, lmax = small
     lams = np.array([0.6, 0.25, 0.1]) * lmax
@@ -52,12 +61,22 @@ def test_path_fit_matches_oracle_rule(pkg, small):
     with CoxProblem(X, w.y, w.delta) as prob:
         beta, iters, obj, conv = prob.path_fit(lams, 1.0 / L, max_iter=max_iter, tol=tol)
         B = beta.cpu().numpy().astype(np.float64)
-    for c, lam in enumerate(lams):
-        b_o, t_o, F_o, conv_o = _oracle_path(Xf, mu, w.y, w.delta, 1.0 / L, lam, max_iter, tol)
-        assert abs(int(iters[c]) - t_o) <= 10, (c, iters[c], t_o)
-        if int(iters[c]) == t_o:
-            assert rel_l2(B[c], b_o) <= 1e-4
-            assert abs(obj[c] - F_o) <= 1e-6 * abs(F_o)
+        for c, lam in enumerate(lams):
+            b_o, t_o, F_o, conv_o, ratios = _oracle_path(Xf, mu, w.y, w.delta, 1.0 / L, lam, max_iter, tol)
+            t_g = int(iters[c])
+            if t_g == t_o:
+                assert rel_l2(B[c], b_o) <= 1e-4, (c, rel_l2(B[c], b_o))
+                assert abs(obj[c] - F_o) <= 1e-6 * abs(F_o)
+                continue
+            # a near-tie: the F values the rule compares differ by at most the
+            # objective's error (loss 1e-7 relative, as the loss gate), so the ratio
+            # moves by at most ~2e-7 |F| / |F + 1| around tol
+            t_star = min(t_g, t_o)
+            slack = 4e-7 * max(1.0, abs(F_o)) / abs(F_o + 1)
+            assert t_star in ratios and abs(ratios[t_star] - tol) <= slack, (c, t_g, t_o, ratios.get(t_star))
+            b_fix, it_fix, _, _ = prob.path_fit([lam], 1.0 / L, max_iter=t_o, tol=0.0)
+            assert int(it_fix[0]) == t_o
+            assert rel_l2(b_fix.cpu().numpy()[0].astype(np.float64), b_o) <= 1e-4
 
 
 def test_batched_columns_equal_solo_runs(pkg, small):

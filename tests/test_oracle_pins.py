@@ -439,3 +439,36 @@ def test_rank_by_entry_hand_example(orc):
     order2, entry2 = orc.rank_by_entry(lams[perm], B[perm])
     assert list(order2) == [1, 2, 0, 5, 4]
     assert [perm[e] if e >= 0 else -1 for e in entry2] == list(entry)
+
+
+# --- the penalised objective and the centring term, by hand ------------------
+
+def test_objective_hand_example(orc):
+    """F = f + lambda ||beta||_1 worked by hand (Section 5.3 likelihood, the l1
+    penalty of the problem statement).  Two subjects, y = (1, 2), the first an
+    event, the second censored; X = [[1, 0], [0, 0]] uncentred; beta =
+    (ln 2, -1).  Then eta = (ln 2, 0), w = (2, 1), the event's risk set holds
+    both subjects, W = 3, and f = (1/2)(log 3 - ln 2) = (1/2) ln(3/2); with
+    lambda = 1/2 the penalty is (1/2)(ln 2 + 1), so F = (1/2) ln 3 + 1/2.
+    A dropped or mis-scaled penalty, a wrong sign in |beta|, or a loss without
+    the 1/n all move F away from this value."""
+    X = np.array([[1.0, 0.0], [0.0, 0.0]])
+    y = np.array([1.0, 2.0])
+    d = np.array([1, 0], np.uint8)
+    beta = np.array([np.log(2.0), -1.0])
+    F = orc.objective(X, None, y, d, beta, 0.5)
+    assert abs(F - (0.5 * np.log(3.0) + 0.5)) <= 1e-15
+    assert abs(orc.objective(X, None, y, d, beta, 0.0) - 0.5 * np.log(1.5)) <= 1e-15
+    # ISTA reports F of the iterate entering each iteration: at t = 0 that is beta0
+    _, Ftr, _ = orc.ista(X, None, y, d, 0.1, 0.5, 1, beta)
+    assert abs(Ftr[0] - (0.5 * np.log(3.0) + 0.5)) <= 1e-15
+
+
+def test_centred_eta_hand_example(orc):
+    """eta = X_c beta with X_c = X - 1 mu^T, by hand in integers: X = [[1, 2],
+    [3, 4]], mu = (2, 3), beta = (1, 10) give eta = (-11, 11).  The loss is
+    shift-invariant, so only a direct check sees the centring term."""
+    X = np.array([[1.0, 2.0], [3.0, 4.0]])
+    eta = orc.eta(X, np.array([2.0, 3.0]), np.array([1.0, 10.0]))
+    assert list(eta) == [-11.0, 11.0]
+    assert list(orc.eta(X, None, np.array([1.0, 10.0]))) == [21.0, 43.0]
