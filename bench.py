@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--tile-m", type=int, default=0)
     ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--chunks", type=int, default=0)
+    ap.add_argument("--issue", type=int, default=0,
+                    help="MMA issue mode of the products: 1 one issuer per row tile, 2 two on alternate stages")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip cox_autotune (the pipeline shapes then come from the built-in default)")
     ap.add_argument("--gemv-steps", type=int, default=2)
@@ -254,14 +256,14 @@ def run_ours(args, rank, world):
     w.packed_rows_device(packed.data_ptr(), stream.cuda_stream, thr.data_ptr())
     torch.cuda.synchronize()
     prob = CoxProblem(packed, w.y, w.delta, p=p, precision="split_e4m3", tile_m=args.tile_m, stages=args.stages,
-                      chunks=args.chunks)
+                      chunks=args.chunks, issue=args.issue)
     del packed, thr
     torch.cuda.empty_cache()
     lmax = prob.lambda_max()
     L = prob.lipschitz(tol=1e-4, maxiter=100)
     step = 1.0 / L
     lams = lmax * r.lambda_fracs()
-    forced = args.tile_m or args.chunks or args.stages
+    forced = args.tile_m or args.chunks or args.stages or args.issue
     tune = None if (args.no_autotune or forced) else prob.autotune(k, reps=2)
     t_setup = time.perf_counter() - t_setup0
 
@@ -373,7 +375,8 @@ def run_ours(args, rank, world):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "step_size": step, "lambda_max": lmax,
                    "pipeline": {"autotune": tune,
-                                "x_b_in_use": {f: pinfo[f] for f in ("tile_m", "chunks", "stages", "ring")}}},
+                                "x_b_in_use": {f: pinfo[f] for f in ("tile_m", "chunks", "stages", "ring", "issue")},
+                                "xt_v_issue": pinfo["issue_xtv"]}},
         "lambda_iters_per_s": value * k,
         "hbm_gbs": iter_bytes / (ms_step / 1e3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -94,6 +94,11 @@ typedef struct cox_options {
                              0 = automatic, as tile_m                               */
     int window;           /* K chunks a TMEM accumulator sums in FP32 before decoder
                              warps add it into FP32 sums (>= chunks; 0 = 256)       */
+    int issue;            /* MMA issue of the tensor-core products: 1 = one issuer
+                             warp per row tile, every stage (4 chunks MMAs per
+                             commit); 2 = two issuer warps on alternate stages,
+                             each issuing every row tile of its stage (4 chunks
+                             tile_m MMAs per commit); 0 = automatic, as tile_m     */
 } cox_options;
 
 /* Fill *opt with the defaults above. */
@@ -235,6 +240,8 @@ typedef struct cox_info {
     int64_t n_tie_groups;
     int64_t launches;
     int chunks, ring;     /* K chunks per stage and TMEM slots of the X B product  */
+    int issue, issue_xtv; /* issue mode (cox_options.issue) of the X B and X^T V
+                             products in use                                       */
 } cox_info;
 int cox_get_info(cox_h h, cox_info *info);
 
@@ -253,6 +260,7 @@ int cox_get_info(cox_h h, cox_info *info);
 typedef struct cox_tune_choice {
     int tile_m, chunks, stages, candidates;
     double ms;
+    int issue;            /* cox_options.issue of the choice (1 or 2)               */
 } cox_tune_choice;
 int cox_autotune(cox_h h, int k, int reps, cox_tune_choice *xb, cox_tune_choice *xtv);
 
@@ -260,14 +268,15 @@ int cox_autotune(cox_h h, int k, int reps, cox_tune_choice *xb, cox_tune_choice 
  * Pipeline plan of the tensor-core products (the genotype products X beta and
  * X^T (delta - u) of each iteration, Section 5.3), computed on the host
  * without a device or handle: for k coefficient columns (1..64) and a shape
- * (tile_m 128-row tiles per CTA, chunks 128-wide K chunks per stage; 0 = the
- * built-in default) at a shared-memory depth (stages; 0 = the deepest that
- * fits), the plan cox_setup's handles would launch.  Every plan it returns
- * keeps the pipeline's invariants: ring >= decoder_groups, ring < stages,
- * named_barriers <= 15, tmem_cols <= 512, smem_bytes within the device's
- * per-block limit.  Errors: COX_ERR_ARG for a NULL out, k outside 1..64, a
- * shape not compiled for k's limb-column class, or a depth outside those
- * invariants.
+ * (tile_m 128-row tiles per CTA, chunks 128-wide K chunks per stage, issue as
+ * cox_options.issue; 0 = the built-in default) at a shared-memory depth
+ * (stages; 0 = the deepest that fits), the plan cox_setup's handles would
+ * launch.  Every plan it returns keeps the pipeline's invariants: ring >=
+ * decoder_groups, ring < stages, named_barriers <= 15, tmem_cols <= 512,
+ * smem_bytes within the device's per-block limit, and for issue 2 two decoder
+ * groups with an even ring and an even number of stages.  Errors: COX_ERR_ARG
+ * for a NULL out, k outside 1..64, a shape not compiled for k's limb-column
+ * class, or a depth outside those invariants.
  */
 typedef struct cox_plan {
     int tile_m, chunks, stages;
@@ -277,8 +286,11 @@ typedef struct cox_plan {
     int limb_cols;        /* e4m3 limb columns: N of every MMA                     */
     int tmem_cols;        /* accumulators + slots, of the 512 an SM has            */
     long long smem_bytes; /* dynamic shared memory per CTA                         */
+    int issue;            /* 1 one issuer per row tile, 2 two on alternate stages  */
+    int issuers;          /* MMA issuer warps                                      */
+    int mmas_per_commit;  /* tcgen05.mma instructions per issuer commit            */
 } cox_plan;
-int cox_plan_shape(int k, int tile_m, int chunks, int stages, cox_plan *out);
+int cox_plan_shape(int k, int tile_m, int chunks, int stages, int issue, cox_plan *out);
 
 /*
  * SNP ranking of Section 6 on a lambda path's coefficients (host arithmetic,

@@ -43,7 +43,8 @@ EXPORTS = [
 class cox_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("center", ctypes.c_int), ("device", ctypes.c_int),
                 ("tile_m", ctypes.c_int), ("stages", ctypes.c_int), ("lag", ctypes.c_int),
-                ("wait_limit_s", ctypes.c_double), ("chunks", ctypes.c_int), ("window", ctypes.c_int)]
+                ("wait_limit_s", ctypes.c_double), ("chunks", ctypes.c_int), ("window", ctypes.c_int),
+                ("issue", ctypes.c_int)]
 
 
 class cox_info(ctypes.Structure):
@@ -51,18 +52,20 @@ class cox_info(ctypes.Structure):
                 ("p_pad", ctypes.c_int64), ("precision", ctypes.c_int), ("center", ctypes.c_int),
                 ("tile_m", ctypes.c_int), ("stages", ctypes.c_int), ("sm_count", ctypes.c_int),
                 ("device_bytes", ctypes.c_int64), ("n_tie_groups", ctypes.c_int64),
-                ("launches", ctypes.c_int64), ("chunks", ctypes.c_int), ("ring", ctypes.c_int)]
+                ("launches", ctypes.c_int64), ("chunks", ctypes.c_int), ("ring", ctypes.c_int),
+                ("issue", ctypes.c_int), ("issue_xtv", ctypes.c_int)]
 
 
 class cox_tune_choice(ctypes.Structure):
     _fields_ = [("tile_m", ctypes.c_int), ("chunks", ctypes.c_int), ("stages", ctypes.c_int),
-                ("candidates", ctypes.c_int), ("ms", ctypes.c_double)]
+                ("candidates", ctypes.c_int), ("ms", ctypes.c_double), ("issue", ctypes.c_int)]
 
 
 class cox_plan(ctypes.Structure):
     _fields_ = [("tile_m", ctypes.c_int), ("chunks", ctypes.c_int), ("stages", ctypes.c_int),
                 ("ring", ctypes.c_int), ("decoder_groups", ctypes.c_int), ("named_barriers", ctypes.c_int),
-                ("limb_cols", ctypes.c_int), ("tmem_cols", ctypes.c_int), ("smem_bytes", ctypes.c_longlong)]
+                ("limb_cols", ctypes.c_int), ("tmem_cols", ctypes.c_int), ("smem_bytes", ctypes.c_longlong),
+                ("issue", ctypes.c_int), ("issuers", ctypes.c_int), ("mmas_per_commit", ctypes.c_int)]
 
 
 class CoxError(RuntimeError):
@@ -127,7 +130,7 @@ def load(path: str | None = None):
     lib.cox_autotune.restype = I
     lib.cox_autotune.argtypes = [P, I, I, ctypes.POINTER(cox_tune_choice), ctypes.POINTER(cox_tune_choice)]
     lib.cox_plan_shape.restype = I
-    lib.cox_plan_shape.argtypes = [I, I, I, I, ctypes.POINTER(cox_plan)]
+    lib.cox_plan_shape.argtypes = [I, I, I, I, I, ctypes.POINTER(cox_plan)]
     lib.cox_rank_by_entry.restype = I
     lib.cox_rank_by_entry.argtypes = [I64, I, P, P, I, P, P, ctypes.POINTER(I64)]
     lib.cox_strerror.restype = ctypes.c_char_p
@@ -251,10 +254,10 @@ def cox_autotune(h, k: int, reps: int):
     return rc, xb, xtv
 
 
-def cox_plan_shape(k: int, tile_m: int = 0, chunks: int = 0, stages: int = 0):
+def cox_plan_shape(k: int, tile_m: int = 0, chunks: int = 0, stages: int = 0, issue: int = 0):
     """(rc, cox_plan) of the tensor-core products for k columns; host only."""
     out = cox_plan()
-    rc = load().cox_plan_shape(k, tile_m, chunks, stages, ctypes.byref(out))
+    rc = load().cox_plan_shape(k, tile_m, chunks, stages, issue, ctypes.byref(out))
     return rc, out
 
 

@@ -34,11 +34,11 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(int(stream))
 
 
-def plan_shape(k: int, tile_m: int = 0, chunks: int = 0, stages: int = 0) -> dict:
+def plan_shape(k: int, tile_m: int = 0, chunks: int = 0, stages: int = 0, issue: int = 0) -> dict:
     """The tensor-core products' pipeline plan for k columns (cox_plan_shape):
-    shape, shared-memory depth, TMEM slots, barriers and memory.  Host only;
-    raises CoxError for a shape or depth the pipeline does not allow."""
-    rc, p = L.cox_plan_shape(int(k), int(tile_m), int(chunks), int(stages))
+    shape, issue mode, shared-memory depth, TMEM slots, barriers and memory.
+    Host only; raises CoxError for a shape or depth the pipeline does not allow."""
+    rc, p = L.cox_plan_shape(int(k), int(tile_m), int(chunks), int(stages), int(issue))
     L.check(rc, "cox_plan_shape")
     return {f: getattr(p, f) for f, _ in L.cox_plan._fields_}
 
@@ -80,7 +80,7 @@ class CoxProblem:
 
     def __init__(self, X, time, event, precision: str = "split_e4m3", center: bool | None = None,
                  p: int | None = None, device: int | None = None, tile_m: int = 0, stages: int = 0,
-                 lag: int = 10, wait_limit_s: float = 2.0, chunks: int = 0, window: int = 0):
+                 lag: int = 10, wait_limit_s: float = 2.0, chunks: int = 0, window: int = 0, issue: int = 0):
         lib = L.load()
         opt = L.cox_default_options()
         opt.precision = PRECISIONS[precision]
@@ -90,6 +90,7 @@ class CoxProblem:
         opt.stages = int(stages)
         opt.chunks = int(chunks)
         opt.window = int(window)
+        opt.issue = int(issue)
         opt.lag = int(lag)
         opt.wait_limit_s = float(wait_limit_s)
         time = np.ascontiguousarray(time, dtype=np.float64)

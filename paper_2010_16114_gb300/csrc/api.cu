@@ -346,15 +346,15 @@ int ensure_workspace(cox_handle *h, int k)
         cudaMemset(ws.bs1, 0, k * sizeof(int));
         cudaMemset(ws.bs4, 0, k * sizeof(int));
         // pipeline shapes: forced by the options, else autotuned for k, else default
-        int T1 = h->opt.tile_m, C1 = h->opt.chunks, S1 = h->opt.stages;
-        int T4 = T1, C4 = C1, S4 = S1;
+        int T1 = h->opt.tile_m, C1 = h->opt.chunks, S1 = h->opt.stages, A1 = h->opt.issue;
+        int T4 = T1, C4 = C1, S4 = S1, A4 = A1;
         const auto tc = h->tuned.find(k);
-        if (tc != h->tuned.end() && !T1 && !C1 && !S1) {
-            T1 = tc->second.T1, C1 = tc->second.CH1, S1 = tc->second.S1;
-            T4 = tc->second.T4, C4 = tc->second.CH4, S4 = tc->second.S4;
+        if (tc != h->tuned.end() && !T1 && !C1 && !S1 && !A1) {
+            T1 = tc->second.T1, C1 = tc->second.CH1, S1 = tc->second.S1, A1 = tc->second.A1;
+            T4 = tc->second.T4, C4 = tc->second.CH4, S4 = tc->second.S4, A4 = tc->second.A4;
         }
-        if ((r = plan_gemm(h, ws.g1, h->d_A1, h->n_pad, h->p_pad, ws.Bq, k, T1, C1, S1)) != COX_OK ||
-            (r = plan_gemm(h, ws.g4, h->d_A4, h->p_pad, h->n_pad, ws.Vq, k, T4, C4, S4)) != COX_OK) {
+        if ((r = plan_gemm(h, ws.g1, h->d_A1, h->n_pad, h->p_pad, ws.Bq, k, T1, C1, S1, A1)) != COX_OK ||
+            (r = plan_gemm(h, ws.g4, h->d_A4, h->p_pad, h->n_pad, ws.Vq, k, T4, C4, S4, A4)) != COX_OK) {
             free_workspace(h);
             return r;
         }
@@ -396,6 +396,7 @@ void cox_default_options(cox_options *opt)
     opt->stages = 0;
     opt->chunks = 0;
     opt->window = 0;
+    opt->issue = 0;
     opt->lag = 10;
     opt->wait_limit_s = 2.0;
 }
@@ -443,7 +444,8 @@ int cox_setup(cox_h *out, const void *X, int64_t n, int64_t p, int x_format, con
     if ((opt.precision == COX_FP64) != (x_format == COX_X_F64_HOST)) return COX_ERR_UNSUPPORTED;
     if (x_format < COX_X_INT8_HOST || x_format > COX_X_PACKED2_DEV) return COX_ERR_ARG;
     if (opt.lag < 1 || !(opt.wait_limit_s >= 0.0)) return COX_ERR_ARG;
-    if (opt.tile_m < 0 || opt.tile_m > 2 || opt.chunks < 0 || opt.chunks > 2 || opt.stages < 0 || opt.window < 0)
+    if (opt.tile_m < 0 || opt.tile_m > 2 || opt.chunks < 0 || opt.chunks > 2 || opt.stages < 0 || opt.window < 0 ||
+        opt.issue < 0 || opt.issue > 2)
         return COX_ERR_ARG;
     for (int64_t i = 0; i < n; ++i) {
         if (!std::isfinite(time[i])) return COX_ERR_ARG;
@@ -566,6 +568,8 @@ int cox_get_info(cox_h h, cox_info *info)
     info->launches = h->launches;
     info->chunks = h->ws.k ? h->ws.g1.CH : h->opt.chunks;
     info->ring = h->ws.k ? h->ws.g1.ring : 0;
+    info->issue = h->ws.k ? (h->ws.g1.alt ? 2 : 1) : h->opt.issue;
+    info->issue_xtv = h->ws.k ? (h->ws.g4.alt ? 2 : 1) : h->opt.issue;
     return COX_OK;
 }
 
@@ -578,9 +582,9 @@ int cox_autotune(cox_h h, int k, int reps, cox_tune_choice *xb, cox_tune_choice 
     h->tuned.erase(k);
     COX_TRY(ensure_workspace(h, k));  // limb buffers (zero) and scale arrays for the timing launches
     Workspace &ws = h->ws;
-    int Ts[8], Cs[8];
-    const int nshape = gemm_shapes(k, Ts, Cs, 8);
-    const int depth_req[2] = {0, 4};  // deepest, and the shallowest the three decoder groups allow
+    int Ts[16], Cs[16], As[16];
+    const int nshape = gemm_shapes(k, Ts, Cs, As, 16);
+    const int depth_req[2] = {0, 4};  // deepest, and the shallowest the decoder groups allow
     cox_tune_choice best[2];
     int cand[2] = {0, 0};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -591,7 +595,7 @@ int cox_autotune(cox_h h, int k, int reps, cox_tune_choice *xb, cox_tune_choice 
     }
     int rc = COX_OK;
     for (int prod = 0; prod < 2 && rc == COX_OK; ++prod) {
-        best[prod] = cox_tune_choice{0, 0, 0, 0, 1e300};
+        best[prod] = cox_tune_choice{0, 0, 0, 0, 1e300, 0};
         const uint32_t *A = prod == 0 ? h->d_A1 : h->d_A4;
         const int64_t rows = prod == 0 ? h->n_pad : h->p_pad, K = prod == 0 ? h->p_pad : h->n_pad;
         const uint8_t *B = prod == 0 ? ws.Bq : ws.Vq;
@@ -599,7 +603,7 @@ int cox_autotune(cox_h h, int k, int reps, cox_tune_choice *xb, cox_tune_choice 
             int last_S = -1;
             for (int dq = 0; dq < 2 && rc == COX_OK; ++dq) {
                 GemmPlan g;
-                if (plan_gemm(h, g, A, rows, K, B, k, Ts[j], Cs[j], depth_req[dq]) != COX_OK) continue;
+                if (plan_gemm(h, g, A, rows, K, B, k, Ts[j], Cs[j], depth_req[dq], As[j] ? 2 : 1) != COX_OK) continue;
                 if (g.stages == last_S) continue;  // the two depths coincide
                 last_S = g.stages;
                 float *part = nullptr;
@@ -625,7 +629,7 @@ int cox_autotune(cox_h h, int k, int reps, cox_tune_choice *xb, cox_tune_choice 
                 if ((rc = check_device_error(h, 0)) != COX_OK) break;
                 ++cand[prod];
                 const double m = static_cast<double>(ms) / reps;
-                if (m < best[prod].ms) best[prod] = cox_tune_choice{g.T, g.CH, g.stages, 0, m};
+                if (m < best[prod].ms) best[prod] = cox_tune_choice{g.T, g.CH, g.stages, 0, m, g.alt ? 2 : 1};
             }
         }
         best[prod].candidates = cand[prod];
@@ -634,8 +638,8 @@ int cox_autotune(cox_h h, int k, int reps, cox_tune_choice *xb, cox_tune_choice 
     cudaEventDestroy(e1);
     if (rc != COX_OK) return rc;
     if (!cand[0] || !cand[1]) return COX_ERR_ARG;
-    h->tuned[k] = cox_handle::TuneChoice{best[0].tile_m, best[0].chunks, best[0].stages,
-                                         best[1].tile_m, best[1].chunks, best[1].stages};
+    h->tuned[k] = cox_handle::TuneChoice{best[0].tile_m, best[0].chunks, best[0].stages, best[0].issue,
+                                         best[1].tile_m, best[1].chunks, best[1].stages, best[1].issue};
     cudaDeviceSynchronize();
     free_workspace(h);  // the next call with k columns plans the chosen shapes
     if (xb) *xb = best[0];
@@ -678,20 +682,23 @@ int cox_rank_by_entry(int64_t p, int L, const double *lambdas, const void *B_hos
     return COX_OK;
 }
 
-int cox_plan_shape(int k, int tile_m, int chunks, int stages, cox_plan *out)
+int cox_plan_shape(int k, int tile_m, int chunks, int stages, int issue, cox_plan *out)
 {
-    if (!out || tile_m < 0 || chunks < 0 || stages < 0) return COX_ERR_ARG;
+    if (!out || tile_m < 0 || chunks < 0 || stages < 0 || issue < 0 || issue > 2) return COX_ERR_ARG;
     GemmPlan g;
-    COX_TRY(plan_shape(g, k, tile_m, chunks, stages));
+    COX_TRY(plan_shape(g, k, tile_m, chunks, stages, issue));
     out->tile_m = g.T;
     out->chunks = g.CH;
     out->stages = g.stages;
     out->ring = g.ring;
-    out->decoder_groups = DEC_GROUPS;
+    out->decoder_groups = g.G;
     out->named_barriers = g.nb_period * g.T;
     out->limb_cols = g.NP;
-    out->tmem_cols = g.T * g.NP + g.ring * g.T * g.CH * 32;
+    out->tmem_cols = (g.alt ? 2 : 1) * g.T * g.NP + g.ring * g.T * g.CH * 32;
     out->smem_bytes = static_cast<long long>(g.smem);
+    out->issue = g.alt ? 2 : 1;
+    out->issuers = g.alt ? 2 : g.T;
+    out->mmas_per_commit = 4 * g.CH * (g.alt ? g.T : 1);
     return COX_OK;
 }
 

@@ -35,6 +35,17 @@
 // (setup.cu), so these running sums stay near the size of the result instead
 // of drifting with the time trend of V.
 //
+// Issue modes.  Per tile (ALT = false): one issuer warp per row tile issues
+// that tile's MMAs of every stage (T issuers, 4 CH MMAs per commit).
+// Alternating (ALT = true): two issuer warps take alternate stages and each
+// issues every tile of its stage into its own accumulators (4 CH T MMAs per
+// commit; a commit costs the tensor pipe a few hundred cycles, so longer
+// bursts per commit raise the MMA rate).  With two decoder groups, an even
+// number of TMEM slots and an even number of shared-memory stages, the stages
+// of one parity form a chain of their own: one producer warp, one decoder
+// group, one issuer and their own slots and stages.  The window folds add the
+// two issuers' accumulators.
+//
 // Work split: units = (M group, stage) pairs; CTA c takes the contiguous range
 // [c L, (c+1) L).  A group that runs entirely in one CTA gets the epilogue
 // straight from its sums; a group cut between CTAs gets one partial per CTA
@@ -96,7 +107,7 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, long lo
     return __all_sync(0xffffffffu, mbar_wait(bar, parity, lim, abort));
 }
 
-// Warp roles (WARPS = 2 + T + 4 G):
+// Warp roles (WARPS = 2 + I + 4 G, I = T issuers, or 2 when alternating):
 //   warps 0, 1     TMA producers (lane 0): warp w loads the stages i = w (mod 2);
 //                  warp 0 also allocates TMEM
 //   warps 2..T+1   MMA issuers: issuer t owns row tile t and accumulates it
@@ -135,22 +146,36 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, long lo
 // parity_safe() holds these and the planner keeps to them.  With R < G (two
 // slots against three groups, as three K chunks per stage would leave) small
 // cases ran exact at S = 4 while a full-size run never finished.
+// Alternating issuers (ALT): warps 2, 3 issue the stages i = 0, 1 (mod 2);
+// G = 2, and R and S are even, so stage i's producer warp, decoder group,
+// issuer, TMEM slot i mod R and shared-memory slot i mod S all belong to the
+// parity class i mod 2, and each barrier is only ever used by one class.
+// Issuers no longer go in stage order across classes, but within a class they
+// do, and every wait above is answered from inside the class: a decoder's
+// wait on aempty (stage i - R) follows its own wait for stage i - 2R, its
+// wait on full (stage i) its own wait for stage i - S, a producer's wait on
+// empty (stage j - S) its own wait for stage j - 2S; a named barrier
+// (period PB = lcm(2, R) stages, T per stage) is reused by the decoders of
+// stage i + PB only after they saw aempty for stage i + PB - R >= i, which its
+// issuer commits after passing the barrier of stage i.  The folds need both
+// classes' MMAs of a window, which the issuers commit to accf (count 2).
 // PB = lcm(G, R): each use of a named barrier has the same warps, and the
 // decoders of stage i+PB cannot arrive before the issuer of stage i has passed
 // it (they first wait, through the TMEM slot chain, for MMAs that this issuer
 // issues after it).  Decoders arrive on every path, so an issuer's (unbounded)
 // hardware-barrier wait always ends.
-template <int T, int CH, int NP, int G>
-__global__ void __launch_bounds__(32 * (2 + T + 4 * G), 1)
+template <int T, int CH, int NP, int G, bool ALT>
+__global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
     k_packed_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const KParams P)
 {
-    constexpr int I = T;                  // MMA issuers, one per row tile
+    constexpr int I = ALT ? 2 : T;        // MMA issuers: one per row tile, or two on alternate stages
+    static_assert(!ALT || G == 2, "alternating issuers pair with two decoder groups");
     constexpr int KH = NP / LIMBS;        // lambda columns a decoder thread folds (>= k)
     constexpr int B_BYTES = CH * NP * 128;       // CH chunk panels of NP rows x 128 bytes
     constexpr int X_BYTES = T * CH * BLOCK_BYTES;  // [tile][chunk] 4 KB blocks
     constexpr int STAGE = B_BYTES + X_BYTES;
-    constexpr int ACC_COLS = I * NP;      // one accumulator per issuer
+    constexpr int ACC_COLS = (ALT ? 2 * T : T) * NP;  // accumulators: per tile, or per issuer and tile
     constexpr int SLOT_COLS = T * CH * 32;  // 128 e4m3 A values per lane, tile and chunk
     constexpr int DEC0 = 2 + I;           // first decoder warp
     constexpr int NB_COUNT = 32 * 5;      // a decoder group and the tile's issuer warp
@@ -179,7 +204,7 @@ __global__ void __launch_bounds__(32 * (2 + T + 4 * G), 1)
             mbar_init(empty0 + 8 * s, 1);
             armed[s] = -1;
         }
-        for (int r = 0; r < R; ++r) mbar_init(aempty0 + 8 * r, T);
+        for (int r = 0; r < R; ++r) mbar_init(aempty0 + 8 * r, ALT ? 1 : T);  // commits per stage
         mbar_init(accf, I);
         mbar_init(acce, 4);
         mbar_init(drainb, I);
@@ -245,8 +270,81 @@ __global__ void __launch_bounds__(32 * (2 + T + 4 * G), 1)
                 }
             }
         }
+    } else if (ALT && warp < DEC0) {
+        // ------- MMA issuers on alternate stages (whole warp; lane 0 issues) -------
+        // Issuer j takes the stages i = j (mod 2) of the CTA's range and issues
+        // all T tiles of each into its own accumulators (T NP columns at
+        // j T NP), one commit per stage.  Every issuer walks every window (the
+        // fold waits for both), zeroing its accumulators with its first MMA in
+        // the window; an issuer without a stage in a window commits nothing
+        // into it, and the fold then skips its accumulators.
+        const int j = warp - 2;
+        constexpr uint32_t idesc = idesc_e4m3_f32(128, NP);
+        const uint32_t dacc = tbase + static_cast<uint32_t>(j * T * NP);
+        const uint64_t desc0 = smem_desc_sw128(smem_addr(smem));
+        int s = 0, r = 0, kc = kc0, nb = 0;
+        uint64_t dstage = desc0;
+        const uint32_t aslot0 = tbase + static_cast<uint32_t>(ACC_COLS);
+        uint32_t aslot = aslot0;
+        uint32_t eph = 0;
+        bool ok = true;
+        for (int64_t i = 0, wi = 0; i < nu; ++wi) {
+            const int wl = static_cast<int>(min(static_cast<int64_t>(min(F, KC - kc)), nu - i));
+            if (wi >= 1) {
+                if (ok && !warp_wait(acce, eph, lim, abort_sm)) {
+                    ok = false;
+                    if (lane == 0) fail(abort_sm, P.err);
+                }
+                eph ^= 1u;
+            }
+            bool first = true;
+            for (int e = 0; e < wl; ++e) {
+                if (((i + e) & 1) == j) {
+#pragma unroll
+                    for (int t = 0; t < T; ++t) {
+                        __syncwarp();
+                        named_sync(1 + nb * T + t, NB_COUNT);
+                        if (ok && lane == 0) {
+                            tc_fence_after();
+#pragma unroll
+                            for (int q = 0; q < 4 * CH; ++q) {
+                                const uint64_t bd =
+                                    dstage + static_cast<uint64_t>(((q >> 2) * NP * 128 + (q & 3) * 32) >> 4);
+                                mma_ts_f8(dacc + static_cast<uint32_t>(t * NP),
+                                          aslot + static_cast<uint32_t>(t * CH * 32 + 8 * q), bd, idesc,
+                                          (first && q == 0) ? 0u : 1u);
+                            }
+                        }
+                    }
+                    if (ok && lane == 0) mma_commit(aempty0 + 8 * r);
+                    first = false;
+                }
+                if (++s == S) {
+                    s = 0;
+                    dstage = desc0;
+                } else {
+                    dstage += static_cast<uint64_t>(STAGE >> 4);
+                }
+                if (++r == R) {
+                    r = 0;
+                    aslot = aslot0;
+                } else {
+                    aslot += SLOT_COLS;
+                }
+                if (++nb == PB) nb = 0;
+            }
+            i += wl;
+            kc += wl;
+            if (kc == KC) kc = 0;
+            if (ok && lane == 0) mma_commit(accf);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            mma_commit(drainb);
+            mbar_wait(drainb, 0, DRAIN_LIMIT, &g_never_set);
+        }
     } else if (warp < DEC0) {
-        // ---------------- MMA issuers (whole warp; lane 0 issues) ----------------
+        // ------- MMA issuers, one per row tile (whole warp; lane 0 issues) -------
         const int t = warp - 2;
         constexpr uint32_t idesc = idesc_e4m3_f32(128, NP);
         const uint32_t d = tbase + static_cast<uint32_t>(t * NP);
@@ -344,7 +442,9 @@ __global__ void __launch_bounds__(32 * (2 + T + 4 * G), 1)
         // group 0: add the finished window's accumulators into registers; at a
         // segment end write this CTA's partial of group g and, for the last
         // CTA, apply the epilogue.
-        auto fold = [&](bool segend, int g) {
+        // amask (alternating issuers): bit j set when issuer j wrote its
+        // accumulators in this window
+        auto fold = [&](bool segend, int g, int amask) {
             if (!ok) return;
             if (!warp_wait(accf, fold_phase, lim, abort_sm)) {
                 ok = false;
@@ -357,15 +457,32 @@ __global__ void __launch_bounds__(32 * (2 + T + 4 * G), 1)
                 for (int tt = 0; tt < T; ++tt) {
 #pragma unroll
                     for (int cc = 0; cc < NP / 8; ++cc) {
-                        uint32_t v[8];
-                        tmem_ld_32x32b_x8(lane_base + static_cast<uint32_t>(tt * NP + cc * 8), v);
-                        tmem_wait_ld();
+                        float v[8];
+                        if (!ALT) {
+                            uint32_t u[8];
+                            tmem_ld_32x32b_x8(lane_base + static_cast<uint32_t>(tt * NP + cc * 8), u);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int m = 0; m < 8; ++m) v[m] = __uint_as_float(u[m]);
+                        } else {
+#pragma unroll
+                            for (int m = 0; m < 8; ++m) v[m] = 0.f;
+#pragma unroll
+                            for (int jj = 0; jj < 2; ++jj) {
+                                if (!(amask >> jj & 1)) continue;  // warp-uniform
+                                uint32_t u[8];
+                                tmem_ld_32x32b_x8(lane_base + static_cast<uint32_t>((jj * T + tt) * NP + cc * 8), u);
+                                tmem_wait_ld();
+#pragma unroll
+                                for (int m = 0; m < 8; ++m) v[m] += __uint_as_float(u[m]);
+                            }
+                        }
 #pragma unroll
                         for (int e = 0; e < 2; ++e) {  // two lambda columns of four limbs
-                            float x = __uint_as_float(v[4 * e + 3]);
-                            x = fmaf(x, 0.0625f, __uint_as_float(v[4 * e + 2]));
-                            x = fmaf(x, 0.0625f, __uint_as_float(v[4 * e + 1]));
-                            x = fmaf(x, 0.0625f, __uint_as_float(v[4 * e]));
+                            float x = v[4 * e + 3];
+                            x = fmaf(x, 0.0625f, v[4 * e + 2]);
+                            x = fmaf(x, 0.0625f, v[4 * e + 1]);
+                            x = fmaf(x, 0.0625f, v[4 * e]);
                             acc(tt, cc * 2 + e) += x;
                         }
                     }
@@ -524,7 +641,9 @@ __global__ void __launch_bounds__(32 * (2 + T + 4 * G), 1)
                 if (wnext == 0 || wkc == 0 || wlen == F) wlen = 0;
                 ++wlen;
                 const bool seg = (wnext == nu - 1) || (wkc == KC - 1);
-                if (seg || wlen == F) fold(seg, wg);
+                // issuers with a stage in the window [wnext - wlen + 1, wnext]
+                const int amask = wlen >= 2 ? 3 : 1 << static_cast<int>(wnext & 1);
+                if (seg || wlen == F) fold(seg, wg, amask);
                 if (++wkc == KC) {
                     wkc = 0;
                     ++wg;
@@ -680,41 +799,53 @@ using KernelFn = void (*)(const CUtensorMap, const CUtensorMap, const KParams);
 // whatever its size, so up to N = 64 a stage takes two chunks (16 KB of codes
 // at T = 2), which keeps the same bytes in TMEM with half the hand-offs.
 // This is the default; the autotuner times every compiled shape instead.
-void shape_for(int NP, int *T, int *CH)
+void shape_for(int NP, int *T, int *CH, int *alt)
 {
     *T = NP <= 128 ? 2 : 1;
     *CH = NP <= 64 ? 2 : 1;
+    *alt = 0;
 }
 
-KernelFn pick_kernel(int T, int CH, int NP)
+constexpr int G_ALT = 2;  // decoder groups of the alternating-issuer kernels
+
+KernelFn pick_kernel(int T, int CH, int NP, int alt)
 {
-    switch ((T * 10 + CH) * 1000 + NP) {
-    case 22016: return k_packed_gemm<2, 2, 16, DEC_GROUPS>;
-    case 21016: return k_packed_gemm<2, 1, 16, DEC_GROUPS>;
-    case 12016: return k_packed_gemm<1, 2, 16, DEC_GROUPS>;
-    case 22032: return k_packed_gemm<2, 2, 32, DEC_GROUPS>;
-    case 21032: return k_packed_gemm<2, 1, 32, DEC_GROUPS>;
-    case 12032: return k_packed_gemm<1, 2, 32, DEC_GROUPS>;
-    case 22064: return k_packed_gemm<2, 2, 64, DEC_GROUPS>;
-    case 21064: return k_packed_gemm<2, 1, 64, DEC_GROUPS>;
-    case 12064: return k_packed_gemm<1, 2, 64, DEC_GROUPS>;
-    case 21128: return k_packed_gemm<2, 1, 128, DEC_GROUPS>;
-    case 12128: return k_packed_gemm<1, 2, 128, DEC_GROUPS>;
-    case 11128: return k_packed_gemm<1, 1, 128, DEC_GROUPS>;
-    case 11256: return k_packed_gemm<1, 1, 256, DEC_GROUPS>;
+    switch (((alt ? 100 : 0) + T * 10 + CH) * 1000 + NP) {
+    case 22016: return k_packed_gemm<2, 2, 16, DEC_GROUPS, false>;
+    case 21016: return k_packed_gemm<2, 1, 16, DEC_GROUPS, false>;
+    case 12016: return k_packed_gemm<1, 2, 16, DEC_GROUPS, false>;
+    case 22032: return k_packed_gemm<2, 2, 32, DEC_GROUPS, false>;
+    case 21032: return k_packed_gemm<2, 1, 32, DEC_GROUPS, false>;
+    case 12032: return k_packed_gemm<1, 2, 32, DEC_GROUPS, false>;
+    case 22064: return k_packed_gemm<2, 2, 64, DEC_GROUPS, false>;
+    case 21064: return k_packed_gemm<2, 1, 64, DEC_GROUPS, false>;
+    case 12064: return k_packed_gemm<1, 2, 64, DEC_GROUPS, false>;
+    case 21128: return k_packed_gemm<2, 1, 128, DEC_GROUPS, false>;
+    case 12128: return k_packed_gemm<1, 2, 128, DEC_GROUPS, false>;
+    case 11128: return k_packed_gemm<1, 1, 128, DEC_GROUPS, false>;
+    case 11256: return k_packed_gemm<1, 1, 256, DEC_GROUPS, false>;
+    // alternating issuers: 16 MMAs per commit up to N = 64, 8 at N = 128
+    case 122016: return k_packed_gemm<2, 2, 16, G_ALT, true>;
+    case 122032: return k_packed_gemm<2, 2, 32, G_ALT, true>;
+    case 122064: return k_packed_gemm<2, 2, 64, G_ALT, true>;
+    case 112128: return k_packed_gemm<1, 2, 128, G_ALT, true>;
     default: return nullptr;
     }
 }
 
-int threads_for(int T) { return 32 * (2 + T + 4 * DEC_GROUPS); }
+int groups_for(int alt) { return alt ? G_ALT : DEC_GROUPS; }
+int issuers_for(int T, int alt) { return alt ? 2 : T; }
+int threads_for(int T, int alt) { return 32 * (2 + issuers_for(T, alt) + 4 * groups_for(alt)); }
 
 int gcd_i(int a, int b) { return b ? gcd_i(b, a % b) : a; }
 
 // The conditions under which every parity wait of k_packed_gemm is
 // unambiguous, for G decoder groups, R TMEM slots and S shared-memory stages
-// (derived with the kernel's hand-off notes).
-bool parity_safe(int G, int R, int S)
+// (derived with the kernel's hand-off notes).  Alternating issuers need the
+// two parity classes apart instead: G = 2 and R, S even.
+bool parity_safe(int G, int R, int S, int alt)
 {
+    if (alt) return G == 2 && R >= 2 && R % 2 == 0 && S % 2 == 0;
     const bool slots = G <= R;                                 // aempty
     const bool stages = S >= G + R || S % G == 0 || R % G == 0; // full
     const bool release = S % 2 == 0 || S >= R + 2;             // empty
@@ -724,55 +855,65 @@ int lcm_i(int a, int b) { return a / gcd_i(a, b) * b; }
 
 } // namespace
 
-int gemm_shapes(int k, int *T, int *CH, int max)
+int gemm_shapes(int k, int *T, int *CH, int *alt, int max)
 {
     const int NP = limb_cols(k);
     int n = 0;
-    for (int t = 2; t >= 1; --t)
-        for (int c = 2; c >= 1; --c)
-            if (pick_kernel(t, c, NP) && n < max) {
-                T[n] = t;
-                CH[n] = c;
-                ++n;
-            }
+    for (int a = 0; a <= 1; ++a)
+        for (int t = 2; t >= 1; --t)
+            for (int c = 2; c >= 1; --c)
+                if (pick_kernel(t, c, NP, a) && n < max) {
+                    T[n] = t;
+                    CH[n] = c;
+                    alt[n] = a;
+                    ++n;
+                }
     return n;
 }
 
 // Plan one product: A (rows_pad x K_pad, tiled 2-bit) times B limbs (NP x K_pad).
-// TMEM budget (512 columns): T NP accumulator columns + ring x T CH x 32 A columns.
-int plan_shape(GemmPlan &g, int k, int T_req, int CH_req, int stages_req)
+// TMEM budget (512 columns): the accumulators (T of NP columns, twice that with
+// alternating issuers) + ring x T CH x 32 A columns.
+int plan_shape(GemmPlan &g, int k, int T_req, int CH_req, int stages_req, int issue_req)
 {
     if (k < 1 || k > MAX_K_TC) return COX_ERR_ARG;
+    if (issue_req < 0 || issue_req > 2) return COX_ERR_ARG;
     const int np_cls = limb_cols(k);
-    int T = 2, CH = 1;
-    shape_for(np_cls, &T, &CH);
+    int T = 2, CH = 1, alt = 0;
+    shape_for(np_cls, &T, &CH, &alt);
+    if (issue_req > 0) alt = issue_req == 2;
     if (T_req > 0) T = T_req;
     if (CH_req > 0) CH = CH_req;
-    if (!pick_kernel(T, CH, np_cls)) return COX_ERR_ARG;  // shape not compiled for this class
+    if (!pick_kernel(T, CH, np_cls, alt)) return COX_ERR_ARG;  // shape not compiled for this class
+    const int G = groups_for(alt);
     const int stage = CH * (np_cls * 128 + T * BLOCK_BYTES);
     // group 0's window sums, then four per-column constants
     const int fold_bytes = T * (np_cls / LIMBS) * 128 * 4 + 4 * (np_cls / LIMBS) * 4;
     int S = stages_req > 0 ? stages_req : (225 * 1024 - 2048 - fold_bytes) / stage;
     if (S > 12) S = 12;
-    if (S < DEC_GROUPS + 1) S = DEC_GROUPS + 1;  // decoder groups step through the stage ring by DEC_GROUPS
-    // TMEM: T accumulators of NP columns, the rest A slots of T CH x 32 columns;
+    if (alt && stages_req <= 0 && S % 2) --S;  // the parity classes need an even stage ring
+    if (S < G + 1) S = G + 1;  // decoder groups step through the stage ring by G
+    // TMEM: the accumulators, the rest A slots of T CH x 32 columns;
     // the decoders of stage i free the shared memory of stage i - ring, which
     // the producer needs for stage i - ring + S: ring < S, or the producer of
     // stage i would wait for the decoders of stage i, who wait for it; and
     // the named barriers, one per tile for each stage of the period
     // lcm(G, ring), must fit barriers 1..15
-    int ring = (512 - T * np_cls) / (T * CH * 32);
+    const int acc_cols = (alt ? 2 * T : T) * np_cls;
+    int ring = (512 - acc_cols) / (T * CH * 32);
     if (ring > 8) ring = 8;
     if (ring > S - 1) ring = S - 1;
     // Parity waits need the phase before the awaited one complete; the
     // kernel's hand-off notes derive when the pipeline guarantees that
-    while (ring >= DEC_GROUPS && !(lcm_i(DEC_GROUPS, ring) * T <= 15 && parity_safe(DEC_GROUPS, ring, S))) --ring;
-    if (ring < DEC_GROUPS) return COX_ERR_ARG;
+    while (ring >= G && !(lcm_i(G, ring) * T <= 15 && parity_safe(G, ring, S, alt))) --ring;
+    if (ring < G) return COX_ERR_ARG;
     g.T = T;
     g.CH = CH;
     g.NP = np_cls;
+    g.alt = alt;
+    g.G = G;
     g.ring = ring;
-    g.nb_period = lcm_i(DEC_GROUPS, ring);
+    g.nb_period = lcm_i(G, ring);
     g.stages = S;
     g.smem = static_cast<size_t>(S) * stage + 1024 + 1024 + fold_bytes;
     if (g.smem < 120 * 1024) g.smem = 120 * 1024;  // one CTA per SM: it owns all 512 TMEM columns
@@ -781,9 +922,9 @@ int plan_shape(GemmPlan &g, int k, int T_req, int CH_req, int stages_req)
 }
 
 int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, int64_t K_pad,
-              const uint8_t *B, int k, int T_req, int CH_req, int stages_req)
+              const uint8_t *B, int k, int T_req, int CH_req, int stages_req, int issue_req)
 {
-    COX_TRY(plan_shape(g, k, T_req, CH_req, stages_req));
+    COX_TRY(plan_shape(g, k, T_req, CH_req, stages_req, issue_req));
     const int64_t m_tiles = rows_pad / TILE;
     const int T = g.T, CH = g.CH, np_cls = g.NP;
     if (m_tiles % T != 0 || (K_pad / TILE) % CH != 0) return COX_ERR_ARG;
@@ -808,7 +949,7 @@ int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, i
         // the two products (and the autotuner's candidates) share kernels with
         // different depths: allow the device's largest block allocation once,
         // and let each launch ask for its own size
-        KernelFn fn = pick_kernel(g.T, g.CH, g.NP);
+        KernelFn fn = pick_kernel(g.T, g.CH, g.NP, g.alt);
         if (!fn) return COX_ERR_ARG;
         int optin = 0;
         COX_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev));
@@ -873,9 +1014,9 @@ int launch_gemm(cox_handle *h, const GemmPlan &g, const EpiArgs &e, int k, cudaS
     kp.inv_n = e.inv_n;
     kp.wait_limit = h->wait_cycles;
     kp.err = h->d_err;
-    KernelFn fn = pick_kernel(g.T, g.CH, g.NP);
+    KernelFn fn = pick_kernel(g.T, g.CH, g.NP, g.alt);
     if (!fn) return COX_ERR_ARG;
-    fn<<<g.grid, threads_for(g.T), g.smem, st>>>(g.tmA, g.tmB, kp);
+    fn<<<g.grid, threads_for(g.T, g.alt), g.smem, st>>>(g.tmA, g.tmB, kp);
     COX_CUDA(cudaGetLastError());
     return COX_OK;
 }

@@ -116,6 +116,8 @@ __host__ __device__ inline int64_t a4_pos(int64_t i, int64_t a, int64_t nb)
 struct GemmPlan {
     int T = 2;         // 128-row tiles per CTA (one M group)
     int CH = 1;        // K chunks (128 each) per stage
+    int alt = 0;       // 1: two issuers on alternate stages (else one per row tile)
+    int G = 3;         // decoder groups
     int NP = 16;       // limb columns (limb_cols(k))
     int stages = 6;    // shared-memory pipeline depth
     int ring = 4;      // TMEM A buffers
@@ -202,7 +204,7 @@ struct cox_handle {
     int64_t st_step = 0;
     // autotuned pipeline shapes per k: row tiles, K chunks, stages of each product
     struct TuneChoice {
-        int T1, CH1, S1, T4, CH4, S4;
+        int T1, CH1, S1, A1, T4, CH4, S4, A4;  // A: issue mode (1 per tile, 2 alternating)
     };
     std::map<int, TuneChoice> tuned;
     // launch accounting and optional per-kernel-class event timing
@@ -269,11 +271,13 @@ int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st);
 // The shape and depth arithmetic of a product plan (host only, no device):
 // T, CH, NP, stages, ring, nb_period and smem of g, or COX_ERR_ARG for a shape
 // not compiled for k or a depth the pipeline does not allow.
-int plan_shape(GemmPlan &g, int k, int T_req, int CH_req, int stages_req);
+// issue_req: 0 default, 1 one issuer per row tile, 2 two issuers on alternate stages.
+int plan_shape(GemmPlan &g, int k, int T_req, int CH_req, int stages_req, int issue_req);
 int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, int64_t K_pad,
-              const uint8_t *B, int k, int T_req, int CH_req, int stages_req);
-// The compiled (row tiles, K chunks) shapes for k columns; returns their count.
-int gemm_shapes(int k, int *T, int *CH, int max);
+              const uint8_t *B, int k, int T_req, int CH_req, int stages_req, int issue_req);
+// The compiled (row tiles, K chunks, alternating issuers) shapes for k columns;
+// returns their count.
+int gemm_shapes(int k, int *T, int *CH, int *alt, int max);
 enum Epi { EPI_PARTIAL = 0, EPI_PROX = 1, EPI_GRAD = 2 };
 struct EpiArgs {
     int epi = EPI_PARTIAL;

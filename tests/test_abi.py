@@ -133,8 +133,8 @@ int main(void) {
     if (o.precision != COX_SPLIT_E4M3 || o.lag != 10) return 1;
     if (strcmp(cox_strerror(COX_OK), "ok") != 0) return 2;
     cox_plan pl;
-    if (cox_plan_shape(16, 0, 0, 0, &pl) != COX_OK || pl.ring < pl.decoder_groups) return 3;
-    if (cox_plan_shape(0, 0, 0, 0, &pl) != COX_ERR_ARG) return 4;
+    if (cox_plan_shape(16, 0, 0, 0, 0, &pl) != COX_OK || pl.ring < pl.decoder_groups) return 3;
+    if (cox_plan_shape(0, 0, 0, 0, 0, &pl) != COX_ERR_ARG) return 4;
     const double lam[3] = {0.3, 0.2, 0.1};
     const float B[3 * 4] = {0.f, 0.5f, 0.f, 0.f,    /* lambda 0.3: SNP 1 */
                             0.1f, 0.7f, -0.3f, 0.f, /* lambda 0.2: SNPs 0, 2 join */

@@ -147,22 +147,25 @@ def test_prox_whole_and_split_row_groups(pkg):
             np.testing.assert_allclose(Bn[c], b1, rtol=1e-4, atol=dz + 1e-7 * np.abs(bc).max())
 
 
-# every compiled pipeline shape (row tiles, K chunks per stage) of each limb-column class
-SHAPES = [(k, t, c) for k in (3, 8, 16) for (t, c) in ((2, 2), (2, 1), (1, 2))] + \
-         [(32, 2, 1), (32, 1, 2), (32, 1, 1), (64, 1, 1)]
+# every compiled pipeline shape (row tiles, K chunks per stage, issue mode) of
+# each limb-column class: 1 = one issuer per row tile, 2 = two issuers on
+# alternate stages
+SHAPES = [(k, t, c, 1) for k in (3, 8, 16) for (t, c) in ((2, 2), (2, 1), (1, 2))] + \
+         [(32, 2, 1, 1), (32, 1, 2, 1), (32, 1, 1, 1), (64, 1, 1, 1)] + \
+         [(3, 2, 2, 2), (8, 2, 2, 2), (16, 2, 2, 2), (32, 1, 2, 2)]
 
 
-@pytest.mark.parametrize("k,tile_m,chunks", SHAPES, ids=lambda v: str(v))
-def test_every_pipeline_shape(pkg, multi_window, k, tile_m, chunks):
+@pytest.mark.parametrize("k,tile_m,chunks,issue", SHAPES, ids=lambda v: str(v))
+def test_every_pipeline_shape(pkg, multi_window, k, tile_m, chunks, issue):
     """Each compiled shape, forced through the options, on row groups that span
     several accumulation windows (16 chunks): the gradients of 4 sampled columns."""
     w, X, Xf, mu = multi_window
     B = _random_betas(w.p, k, 41 + k)
-    with _problem(pkg, X, w, "split_e4m3", tile_m=tile_m, chunks=chunks, window=16) as prob:
+    with _problem(pkg, X, w, "split_e4m3", tile_m=tile_m, chunks=chunks, window=16, issue=issue) as prob:
         beta = torch.tensor(B, dtype=torch.float32, device="cuda")
         loss, grad = prob.loss_grad(beta)
         info = prob.info()
-        assert (info["tile_m"], info["chunks"]) == (tile_m, chunks)
+        assert (info["tile_m"], info["chunks"], info["issue"], info["issue_xtv"]) == (tile_m, chunks, issue, issue)
         G = grad.cpu().numpy()
         for c in sorted({0, k // 3, (2 * k) // 3, k - 1}):
             bc = beta[c].cpu().numpy().astype(np.float64)
@@ -331,3 +334,23 @@ def test_repeatable_bitwise(pkg):
             prob.prox_step(b2, lams, 0.5)
         prob.sync()
         assert torch.equal(b1, b2)
+
+
+@pytest.mark.parametrize("window", [2, 6, 10])
+def test_alternating_issuers_odd_windows(pkg, multi_window, window):
+    """Two issuers on alternate stages with windows of 1, 3 or 5 stages (two
+    chunks each): windows where one issuer has no stage, or more stages than
+    the other, and group ends inside a window (36 stages per row group).  Gradient and one step for 16
+    columns against the oracle."""
+    w, X, Xf, mu = multi_window
+    k = 16
+    B = _random_betas(w.p, k, 71 + window)
+    with _problem(pkg, X, w, "split_e4m3", tile_m=2, chunks=2, window=window, issue=2) as prob:
+        beta = torch.tensor(B, dtype=torch.float32, device="cuda")
+        loss, grad = prob.loss_grad(beta)
+        G = grad.cpu().numpy()
+        for c in (0, 5, 15):
+            bc = beta[c].cpu().numpy().astype(np.float64)
+            f_o, g_o = oracle_loss_grad(Xf, mu, w.y, w.delta, bc)
+            assert abs(loss[c] - f_o) <= 1e-7 * abs(f_o), (c, loss[c], f_o)
+            assert rel_l2(G[c], g_o) <= 1e-5, (c, rel_l2(G[c], g_o))

@@ -12,6 +12,10 @@ invariants, which the kernel's hand-offs rely on:
 * lcm(groups, ring) x tiles <= 15 hardware named barriers (0 is __syncthreads);
 * accumulators + slots <= 512 TMEM columns; shared memory within 227 KB and at
   least 120 KB (one CTA per SM owns all of TMEM).
+
+With two issuers on alternate stages (issue 2) the stages of each parity form a
+chain of their own, which needs two decoder groups, an even ring and an even
+number of stages; each issuer holds an accumulator per row tile.
 """
 import math
 
@@ -19,7 +23,7 @@ import pytest
 
 from paper_2010_16114_gb300 import _lib as L
 
-SHAPES = [(t, c) for t in (2, 1) for c in (2, 1)]
+SHAPES = [(t, c, a) for a in (1, 2) for t in (2, 1) for c in (2, 1)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -40,34 +44,44 @@ def _parity_safe(G, R, S):
 def _check(k, p):
     assert p.limb_cols >= 4 * k and p.limb_cols in (16, 32, 64, 128, 256)
     assert p.ring >= p.decoder_groups
-    assert _parity_safe(p.decoder_groups, p.ring, p.stages)
     assert p.ring < p.stages
     assert p.stages >= p.decoder_groups + 1
     assert p.named_barriers == math.lcm(p.decoder_groups, p.ring) * p.tile_m <= 15
-    assert p.tmem_cols == p.tile_m * p.limb_cols + p.ring * p.tile_m * p.chunks * 32 <= 512
+    if p.issue == 2:
+        assert p.decoder_groups == 2 and p.ring % 2 == 0 and p.stages % 2 == 0
+        assert p.issuers == 2 and p.mmas_per_commit == 4 * p.chunks * p.tile_m
+        acc = 2 * p.tile_m * p.limb_cols
+    else:
+        assert p.issue == 1
+        assert _parity_safe(p.decoder_groups, p.ring, p.stages)
+        assert p.issuers == p.tile_m and p.mmas_per_commit == 4 * p.chunks
+        acc = p.tile_m * p.limb_cols
+    assert p.tmem_cols == acc + p.ring * p.tile_m * p.chunks * 32 <= 512
     assert 120 * 1024 <= p.smem_bytes <= 227 * 1024
 
 
 @pytest.mark.parametrize("k", range(1, 65))
 def test_every_shape_and_depth_keeps_the_invariants(k):
     compiled = 0
-    for t, c in SHAPES:
-        rc, p = L.cox_plan_shape(k, t, c, 0)
+    for t, c, a in SHAPES:
+        rc, p = L.cox_plan_shape(k, t, c, 0, a)
         if rc != 0:
             assert rc == L.COX_ERR_ARG
             continue
         compiled += 1
-        assert (p.tile_m, p.chunks) == (t, c)
+        assert (p.tile_m, p.chunks, p.issue) == (t, c, a)
         _check(k, p)
         deepest = p.stages
         for s in range(1, 16):
-            rc, q = L.cox_plan_shape(k, t, c, s)
+            rc, q = L.cox_plan_shape(k, t, c, s, a)
+            want = min(max(s, q.decoder_groups + 1 if rc == 0 else s), 12)  # the planner caps the depth at 12
             if rc != 0:
-                # refused only beyond the shared-memory budget
-                assert rc == L.COX_ERR_ARG and s > deepest
+                # refused only beyond the shared-memory budget, or (alternating
+                # issuers) at an odd depth
+                assert rc == L.COX_ERR_ARG and (s > deepest or (a == 2 and min(max(s, 3), 12) % 2 == 1))
                 continue
             _check(k, q)
-            assert q.stages == min(max(s, q.decoder_groups + 1), 12)  # the planner caps the depth at 12
+            assert q.stages == want
     assert compiled >= 1
 
 
@@ -97,7 +111,10 @@ def test_rejections():
     assert L.cox_plan_shape(16, 0, 3)[0] == L.COX_ERR_ARG      # three K chunks: not compiled
     assert L.cox_plan_shape(64, 2, 2)[0] == L.COX_ERR_ARG      # 256 limb columns take one tile, one chunk
     assert L.cox_plan_shape(16, -1, 0)[0] == L.COX_ERR_ARG
-    assert L.load().cox_plan_shape(16, 0, 0, 0, None) == L.COX_ERR_ARG
+    assert L.load().cox_plan_shape(16, 0, 0, 0, 0, None) == L.COX_ERR_ARG
+    assert L.cox_plan_shape(16, 2, 1, 0, 2)[0] == L.COX_ERR_ARG   # alternating issuers: not compiled for (2, 1)
+    assert L.cox_plan_shape(16, 2, 2, 5, 2)[0] == L.COX_ERR_ARG   # alternating issuers need an even depth
+    assert L.cox_plan_shape(16, 0, 0, 0, 3)[0] == L.COX_ERR_ARG
 
 
 def test_front_end_wrapper():
@@ -106,3 +123,14 @@ def test_front_end_wrapper():
     assert (d["tile_m"], d["chunks"], d["stages"], d["ring"], d["limb_cols"]) == (2, 2, 6, 3, 64)
     with pytest.raises(L.CoxError):
         plan_shape(16, chunks=3)
+
+
+def test_alternating_issuers_plan():
+    """k = 16 (64 limb columns) with two issuers on alternate stages: two row
+    tiles x two K chunks per stage, 16 MMAs per commit, accumulators of 2 x 2 x 64
+    columns and two 128-column slots fill TMEM, and six 32 KB stages."""
+    rc, p = L.cox_plan_shape(16, 2, 2, 0, 2)
+    assert rc == 0
+    _check(16, p)
+    assert (p.issuers, p.decoder_groups, p.ring, p.stages, p.mmas_per_commit, p.tmem_cols) == (2, 2, 2, 6, 16, 512)
+    assert p.named_barriers == 4
