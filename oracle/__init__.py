@@ -12,7 +12,8 @@ the passage of arXiv 2010.16114 (DistStat.jl) it follows:
 * ``risk`` / ``risk_bruteforce`` -- Section 5.3, W_j, pi_ij and P delta;
   Breslow ties per Section 6.
 * ``eta`` / ``grad`` -- Section 5.3, X beta and Delta = X^T (I - P) delta
-  (divided by n; the 1/n normalisation is this build's reading).
+  (divided by n; the 1/n normalisation is this build's reading);
+  ``eta_u8`` / ``grad_u8`` the same with genotype columns held as bytes.
 * ``prox`` / ``soft_threshold`` -- Section 4.2 soft threshold, applied as
   S(beta + sigma g, sigma lambda) (Section 5.3 iteration).
 * ``opnorm2`` -- Section 4.4 power method; ``lipschitz`` = 2 ||X_c||_2^2 / n
@@ -69,6 +70,10 @@ def _lib(long_double: bool = False):
         lib.orc_eta.argtypes = [_i64, _i64, _p, _p, _p, _p]
         lib.orc_grad.restype = None
         lib.orc_grad.argtypes = [_i64, _i64, _p, _p, _p, _p, _p]
+        lib.orc_eta_u8.restype = None
+        lib.orc_eta_u8.argtypes = [_i64, _i64, _p, _p, _p, _p]
+        lib.orc_grad_u8.restype = None
+        lib.orc_grad_u8.argtypes = [_i64, _i64, _p, _p, _p, _p, _p]
         lib.orc_soft_threshold.restype = _f64
         lib.orc_soft_threshold.argtypes = [_f64, _f64]
         lib.orc_prox.restype = None
@@ -159,6 +164,27 @@ def grad(Xcols, mu, delta, u, long_double: bool = False) -> np.ndarray:
     mu = None if mu is None else _f(mu)
     g = np.zeros(m)
     _lib(long_double).orc_grad(n, m, _ptr(Xc), _ptr(mu), _ptr(_u8(delta)), _ptr(_f(u)), _ptr(g))
+    return g
+
+
+def eta_u8(Xt, mu, beta) -> np.ndarray:
+    """``eta`` with the columns given as bytes: Xt is (m, n) uint8, row t =
+    column t of X (Section 5.3, X beta).  Bitwise equal to ``eta``."""
+    Xt = np.ascontiguousarray(Xt, dtype=np.uint8)
+    m, n = Xt.shape
+    out = np.zeros(n)
+    _lib().orc_eta_u8(n, m, _ptr(Xt), _ptr(None if mu is None else _f(mu)), _ptr(_f(beta)), _ptr(out))
+    return out
+
+
+def grad_u8(Xt, mu, delta, u) -> np.ndarray:
+    """``grad`` with the columns given as bytes: Xt is (m, n) uint8, row t =
+    column t of X (Section 5.3, Delta / n).  Bitwise equal to ``grad``."""
+    Xt = np.ascontiguousarray(Xt, dtype=np.uint8)
+    m, n = Xt.shape
+    g = np.zeros(m)
+    _lib().orc_grad_u8(n, m, _ptr(Xt), _ptr(None if mu is None else _f(mu)), _ptr(_u8(delta)), _ptr(_f(u)),
+                       _ptr(g))
     return g
 
 

@@ -216,6 +216,36 @@ void orc_grad(int64_t n, int64_t m, const double *Xcols, const double *mu, const
     }
 }
 
+/* The same two products with the columns given as bytes (genotype codes):
+ * each x is converted to real exactly and the loops are those of orc_eta and
+ * orc_grad, term for term, so the results are bitwise theirs.  They let a
+ * caller hold a large genotype design at one byte per code. */
+void orc_eta_u8(int64_t n, int64_t m, const uint8_t *Xcols, const double *mu, const double *beta,
+                double *eta)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        real s = 0;
+        for (int64_t t = 0; t < m; ++t) {
+            real xc = (real)Xcols[t * n + i] - (mu ? (real)mu[t] : (real)0);
+            s += xc * (real)beta[t];
+        }
+        eta[i] = (double)s;
+    }
+}
+
+void orc_grad_u8(int64_t n, int64_t m, const uint8_t *Xcols, const double *mu, const uint8_t *delta,
+                 const double *u, double *g)
+{
+    for (int64_t t = 0; t < m; ++t) {
+        real s = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            real xc = (real)Xcols[t * n + i] - (mu ? (real)mu[t] : (real)0);
+            s += xc * ((real)delta[i] - (real)u[i]);
+        }
+        g[t] = (double)(s / (real)n);
+    }
+}
+
 /* Soft threshold (Section 4.2): x - t if x > t, x + t if x < -t, else 0. */
 double orc_soft_threshold(double x, double t)
 {

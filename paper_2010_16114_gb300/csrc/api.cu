@@ -56,7 +56,7 @@ void free_workspace(cox_handle *h)
     Workspace &w = h->ws;
     void *ptrs[] = {w.eta, w.w, w.Rt, w.Ft, w.cmax, w.csw, w.csd, w.suf, w.pre, w.lossp, w.vsp, w.l1p,
                     w.sumV, w.f, w.F, w.l1, w.mub, w.lam, w.active, w.Fring, w.Bq, w.Vq, w.bs1, w.bs4, w.bmaxp,
-                    w.vmaxp, w.part1, w.part4, w.cnt4, w.V64, w.V32, w.eta32, w.G32};
+                    w.vmaxp, w.part1, w.part4, w.cnt4, w.V64, w.V32, w.eta32, w.G32, w.gpart};
     for (void *p : ptrs) dfree(p);
     const GemmPlan g1 = w.g1, g4 = w.g4;
     (void)g1;
@@ -232,8 +232,8 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
             COX_TRY(l1_norms32(h, bc, 1, st));
         }
         {
-            Site s_(h, 0, 1, st);
-            COX_TRY(gemv_tiles(h, h->d_A1, h->n_pad, h->p_pad / TILE, bc, h->p, ws.eta32, st));
+            Site s_(h, 0, 2, st);
+            COX_TRY(gemv_lut(h, h->d_A1, h->n_pad, h->p_pad / TILE, bc, h->p, ws.gpart, ws.eta32, st));
         }
         ScanArgs sa;
         sa.k = 1;
@@ -257,8 +257,8 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
         COX_CUDA(cudaMemcpyAsync(ws.Fring + c, ws.F, sizeof(double), cudaMemcpyDeviceToDevice, st));
         COX_CUDA(cudaMemcpyAsync(ws.Fring + k + c, ws.f, sizeof(double), cudaMemcpyDeviceToDevice, st));
         {
-            Site s_(h, 1, 2, st);
-            COX_TRY(gemv_tiles(h, h->d_A4, h->p_pad, h->n_pad / TILE, ws.V32, h->n_pad, ws.G32, st));
+            Site s_(h, 1, 3, st);
+            COX_TRY(gemv_lut(h, h->d_A4, h->p_pad, h->n_pad / TILE, ws.V32, h->n_pad, ws.gpart, ws.G32, st));
             float *gc = epi == EPI_GRAD ? static_cast<float *>(grad) : nullptr;
             COX_TRY(prox_or_grad32(h, ws.G32, c, epi == EPI_PROX ? b32 : nullptr, gc, ws.lam, step, st));
         }
@@ -369,6 +369,8 @@ int ensure_workspace(cox_handle *h, int k)
         cudaMemset(ws.V32, 0, h->n_pad * sizeof(float));
         A(ws.eta32, h->n_pad);
         A(ws.G32, h->p_pad);
+        A(ws.gpart, std::max(gemv_lut_part_floats(h->n_pad, h->p_pad / TILE),
+                             gemv_lut_part_floats(h->p_pad, h->n_pad / TILE)));
     }
 #undef A
     (void)p;

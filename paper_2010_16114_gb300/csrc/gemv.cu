@@ -3,10 +3,13 @@
 //   * the FP64 path: eta = X beta and X^T V on a dense FP64 design, with the
 //     soft-threshold step (Section 4.2) fused after the reduction;
 //   * the plain FP32 baseline: one matrix-vector product per penalty on the
-//     2-bit tiles (FP32 multiply-add, FP64 across 128-wide chunks) and an
+//     2-bit tiles (byte tables of partial sums of x, FP32 throughout) and an
 //     unfused soft-threshold kernel;
+//   * the power method's matrix-vector product (one thread per row, FP32
+//     multiply-add per code, FP64 across 128-wide chunks);
 //   * ||beta||_1 partial sums for the penalised objective.
 #include <algorithm>
+#include <cmath>
 
 #include "internal.h"
 
@@ -102,6 +105,92 @@ __global__ void __launch_bounds__(128) k_gemv_tiles(const uint32_t *__restrict__
         acc += static_cast<double>(cs);
     }
     y[row] = static_cast<float>(acc);
+}
+
+// ---- the FP32 baseline's matrix-vector product: byte tables of x -------------
+// In the tiled layout byte b of word q of half h of a row's 32-byte record holds
+// the codes of the four K positions base + 4m (m = 0..3), base = 128 kc + 64 h
+// + 16 q + b, two bits each.  For one K chunk a CTA tabulates, for each of those
+// 32 byte positions and each of the 256 byte values v, the FP32 sum
+//   T[v] = sum_m code_m(v) x[base + 4m],   code_m(v) = (v >> 2m) & 3,
+// after which a row's dot product with the chunk is 32 table lookups and FP32
+// adds, one per packed byte.  A CTA keeps the tables of LUT_CW chunks in
+// shared memory and streams the row tiles of its split through them with
+// 16-byte coalesced loads, two threads per row (one per 16-byte half); every
+// (range of chunks) leaves one FP32 partial per row, and k_gemv_reduce adds
+// the partials with a compensated FP32 sum.  The tables of the second half
+// start 16 words later, so the two halves' lanes index different banks.
+constexpr int LUT_CW = 6;                    // K chunks per CTA
+constexpr int LUT_THREADS = 512;             // two threads per row, two row tiles per pass
+constexpr int LUT_CHUNK = 32 * 256 + 16;     // floats per chunk's tables (+16: bank offset of half 1)
+
+__global__ void __launch_bounds__(LUT_THREADS) k_gemv_lut(const uint32_t *__restrict__ A, int64_t row_tiles,
+                                                          int64_t KC, const float *__restrict__ x,
+                                                          int64_t K_valid, float *__restrict__ part,
+                                                          int64_t rows_pad, int n_ranges, int64_t tiles_per_split)
+{
+    extern __shared__ float tab[];
+    const int range = static_cast<int>(blockIdx.x % n_ranges);
+    const int64_t split = blockIdx.x / n_ranges;
+    const int64_t kc0 = static_cast<int64_t>(range) * LUT_CW;
+    const int ncw = static_cast<int>(min(static_cast<int64_t>(LUT_CW), KC - kc0));
+    for (int e = threadIdx.x; e < ncw * 8192; e += LUT_THREADS) {
+        const int c = e >> 13, g = (e >> 8) & 31, v = e & 255;
+        const int64_t base = (kc0 + c) * TILE + 64 * (g >> 4) + 16 * ((g >> 2) & 3) + (g & 3);
+        float acc = 0.f;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int64_t K = base + 4 * m;
+            const float xv = K < K_valid ? x[K] : 0.f;
+            acc = fmaf(static_cast<float>((v >> (2 * m)) & 3), xv, acc);
+        }
+        tab[c * LUT_CHUNK + g * 256 + ((g & 16) ? 16 : 0) + v] = acc;
+    }
+    __syncthreads();
+    const int r = (threadIdx.x & 255) >> 1, hh = threadIdx.x & 1;
+    const int swp = (r >> 2) & 1;
+    const float *tb = tab + hh * (16 * 256 + 16);
+    const int64_t mt_begin = split * tiles_per_split;
+    const int64_t mt_end = min(row_tiles, mt_begin + tiles_per_split);
+    for (int64_t mt = mt_begin + (threadIdx.x >> 8); mt < mt_end; mt += 2) {
+        const uint8_t *rec = reinterpret_cast<const uint8_t *>(A) + ((mt * KC + kc0) * BLOCK_BYTES + r * 32 + 16 * (hh ^ swp));
+        uint4 w[LUT_CW];
+#pragma unroll
+        for (int c = 0; c < LUT_CW; ++c)
+            if (c < ncw) w[c] = __ldcs(reinterpret_cast<const uint4 *>(rec + static_cast<int64_t>(c) * BLOCK_BYTES));
+        float acc = 0.f;
+#pragma unroll
+        for (int c = 0; c < LUT_CW; ++c) {
+            if (c >= ncw) break;
+            const float *t = tb + c * LUT_CHUNK;
+            const uint32_t ws[4] = {w[c].x, w[c].y, w[c].z, w[c].w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc += t[(4 * q + b) * 256 + ((ws[q] >> (8 * b)) & 255u)];
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (hh == 0) part[static_cast<int64_t>(range) * rows_pad + mt * TILE + r] = acc;
+    }
+}
+
+// y[row] = sum over ranges of part[range][row] (compensated FP32: Knuth's TwoSum
+// per term, the error terms summed apart)
+__global__ void k_gemv_reduce(const float *__restrict__ part, int n_ranges, int64_t rows_pad, int64_t rows,
+                              float *__restrict__ y)
+{
+    for (int64_t row = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; row < rows;
+         row += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        float hi = 0.f, lo = 0.f;
+        for (int q = 0; q < n_ranges; ++q) {
+            const float v = part[static_cast<int64_t>(q) * rows_pad + row];
+            const float t = hi + v;
+            const float bv = t - hi;
+            lo += (hi - (t - bv)) + (v - bv);
+            hi = t;
+        }
+        y[row] = hi + lo;
+    }
 }
 
 // beta_col <- S(beta_col + step g, step lambda), g = (G - mu sum V) / n; or grad = -g.
@@ -221,6 +310,46 @@ int gemv_tiles(cox_handle *h, const uint32_t *A, int64_t rows, int64_t KC, const
 {
     (void)h;
     k_gemv_tiles<<<blocks_for(rows, 128), 128, 0, st>>>(A, rows, KC, x, K_valid, y);
+    COX_CUDA(cudaGetLastError());
+    return COX_OK;
+}
+
+int gemv_lut_plan(int64_t rows_pad, int64_t KC, int sm_count, int *n_ranges, int64_t *tiles_per_split,
+                  int *grid)
+{
+    const int64_t row_tiles = rows_pad / TILE;
+    const int64_t ranges = (KC + LUT_CW - 1) / LUT_CW;
+    // row splits: the grid nearest to whole waves of sm_count CTAs (one per SM)
+    int best_s = 1;
+    double best = 1e300;
+    for (int sp = 1; sp <= 16; ++sp) {
+        const int64_t tps = (row_tiles + sp - 1) / sp;
+        const int64_t g = ranges * ((row_tiles + tps - 1) / tps);
+        const double waves = static_cast<double>(g) / sm_count;
+        const double loss = (std::ceil(waves) - waves) / std::ceil(waves) + 0.002 * sp;  // idle share, table builds
+        if (loss < best) {
+            best = loss;
+            best_s = sp;
+        }
+    }
+    *tiles_per_split = (row_tiles + best_s - 1) / best_s;
+    *n_ranges = static_cast<int>(ranges);
+    *grid = static_cast<int>(ranges * ((row_tiles + *tiles_per_split - 1) / *tiles_per_split));
+    return COX_OK;
+}
+
+size_t gemv_lut_part_floats(int64_t rows_pad, int64_t KC) { return static_cast<size_t>((KC + LUT_CW - 1) / LUT_CW) * rows_pad; }
+
+int gemv_lut(cox_handle *h, const uint32_t *A, int64_t rows, int64_t KC, const float *x, int64_t K_valid,
+             float *part, float *y, cudaStream_t st)
+{
+    const size_t smem = static_cast<size_t>(LUT_CW) * LUT_CHUNK * sizeof(float);
+    COX_CUDA(cudaFuncSetAttribute(k_gemv_lut, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    int n_ranges = 0, grid = 0;
+    int64_t tps = 0;
+    gemv_lut_plan(rows, KC, h->sm_count, &n_ranges, &tps, &grid);
+    k_gemv_lut<<<grid, LUT_THREADS, smem, st>>>(A, rows / TILE, KC, x, K_valid, part, rows, n_ranges, tps);
+    k_gemv_reduce<<<blocks_for(rows, 256), 256, 0, st>>>(part, n_ranges, rows, rows, y);
     COX_CUDA(cudaGetLastError());
     return COX_OK;
 }

@@ -164,6 +164,7 @@ struct Workspace {
     float *V32 = nullptr;      // n_pad, A4 K order
     float *eta32 = nullptr;    // n
     float *G32 = nullptr;      // p
+    float *gpart = nullptr;    // partials of the FP32 baseline's product
     GemmPlan g1, g4;
     bool plans_ready = false;
 };
@@ -303,6 +304,12 @@ int l1_norms32(cox_handle *h, const float *beta, int k, cudaStream_t st, float *
 int l1_norms64(cox_handle *h, const double *beta, int k, cudaStream_t st);
 int gemv_tiles(cox_handle *h, const uint32_t *A, int64_t rows, int64_t KC, const float *x,
                int64_t K_valid, float *y, cudaStream_t st);
+// The FP32 baseline's product y = A x (byte tables of x; part: the partials,
+// gemv_lut_part_floats(rows, KC) floats).  Two kernels.
+int gemv_lut(cox_handle *h, const uint32_t *A, int64_t rows, int64_t KC, const float *x, int64_t K_valid,
+             float *part, float *y, cudaStream_t st);
+size_t gemv_lut_part_floats(int64_t rows_pad, int64_t KC);
+int gemv_lut_plan(int64_t rows_pad, int64_t KC, int sm_count, int *n_ranges, int64_t *tiles_per_split, int *grid);
 int prox_or_grad32(cox_handle *h, const float *G, int col, float *beta, float *grad,
                    const double *lam, double step, cudaStream_t st);
 int eta64(cox_handle *h, const double *beta, int k, double *eta, cudaStream_t st);

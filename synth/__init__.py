@@ -76,6 +76,7 @@ def _host():
         lib.syn_maf.argtypes = [_u64, _i64, _f64, _f64, _p, _p]
         lib.syn_genotypes.argtypes = [_u64, _p, _i64, _i64, _i64, _i64, _p]
         lib.syn_genotype_cols.argtypes = [_u64, _p, _i64, _p, _i64, _p]
+        lib.syn_genotype_cols_u8.argtypes = [_u64, _p, _i64, _p, _i64, _p]
         lib.syn_genotypes_packed.argtypes = [_u64, _p, _i64, _i64, _i64, _p]
         lib.syn_normals.argtypes = [_u64, _i64, _i64, _i64, _i64, _p]
         lib.syn_normal_vec.argtypes = [_u64, _u64, _i64, _p]
@@ -211,6 +212,42 @@ class Workload:
                 lib.syn_normals(self.r.seed, 0, self.r.n, int(j), 1, _ptr(tmp))
                 out[c] = tmp
         return np.ascontiguousarray(out.T)
+
+    def cols_u8(self, idx, threads: int = 1) -> np.ndarray:
+        """Genotype columns ``idx`` as uint8, shape (len(idx), n): row c is
+        column idx[c] of X (column-major X restricted to idx).  With threads > 1
+        the columns are generated in parallel blocks (the C calls release the
+        interpreter lock)."""
+        assert self.r.kind == "geno"
+        idx = np.ascontiguousarray(np.atleast_1d(idx), dtype=np.int64)
+        n, m = self.r.n, len(idx)
+        out = np.zeros((m, n), np.uint8)
+        lib = _host()
+
+        def block(c0, c1):
+            lib.syn_genotype_cols_u8(self.r.seed, _ptr(self.thr), n,
+                                     ctypes.c_void_p(idx.ctypes.data + 8 * c0), c1 - c0,
+                                     ctypes.c_void_p(out.ctypes.data + c0 * n))
+
+        if threads <= 1 or m < 2:
+            block(0, m)
+        else:
+            from concurrent.futures import ThreadPoolExecutor
+            step = max(1, -(-m // (4 * threads)))
+            with ThreadPoolExecutor(threads) as ex:
+                list(ex.map(lambda c0: block(c0, min(m, c0 + step)), range(0, m, step)))
+        return out
+
+    def rows_u8(self, rows) -> np.ndarray:
+        """Genotype rows ``rows`` as uint8, shape (len(rows), p)."""
+        assert self.r.kind == "geno"
+        rows = np.atleast_1d(np.asarray(rows, dtype=np.int64))
+        out = np.zeros((len(rows), self.r.p), np.uint8)
+        lib = _host()
+        for c, i in enumerate(rows):
+            lib.syn_genotypes(self.r.seed, _ptr(self.thr), int(i), 1, 0, self.r.p,
+                              ctypes.c_void_p(out.ctypes.data + c * self.r.p))
+        return out
 
     def dense(self) -> np.ndarray:
         """Whole X: uint8 codes (geno) or float64 (normal), row-major n x p."""

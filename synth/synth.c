@@ -101,6 +101,17 @@ void syn_genotype_cols(uint64_t seed, const uint32_t *thr, int64_t n,
 
 /* Row-major packed genotypes: ceil(p/4) bytes per row, SNP j in bits
  * 2*(j%4)..2*(j%4)+1 of byte j/4, unused tail bits zero. Rows i0..i0+ni. */
+/* Columns cols[0..m) of X as bytes, column-major: out[c * n + i] = x_{i, cols[c]}. */
+void syn_genotype_cols_u8(uint64_t seed, const uint32_t *thr, int64_t n,
+                          const int64_t *cols, int64_t m, uint8_t *out)
+{
+    for (int64_t c = 0; c < m; ++c) {
+        int64_t j = cols[c];
+        for (int64_t i = 0; i < n; ++i)
+            out[c * n + i] = geno(seed, thr[j], i, j);
+    }
+}
+
 void syn_genotypes_packed(uint64_t seed, const uint32_t *thr, int64_t p,
                           int64_t i0, int64_t ni, uint8_t *out)
 {

@@ -1,16 +1,33 @@
 """Parity at the genotype workloads' full sizes, in the launch configuration
 the benchmark uses (genotypes generated on the device, 2-bit packed, default
-tiles).
+tiles, 256-chunk accumulation windows).
 
-* geno_200k_10k (n=200,000, p=10,000, k=1): the oracle runs two whole iterations,
-  streaming X in column blocks; beta after each iteration and the gradient at
-  beta = 0 are compared element by element.
-* geno_100k_50k, geno_400k_100k_k32, geno_400k_500k_k16 (up to n=400,000 x
-  p=500,000): sampled outputs the oracle
-  computes one by one -- g_j(0) and the first iterate beta_j(1) of every
-  penalty at 64 seeded columns j -- and the closed form of the loss at
-  beta = 0, f(0) = (1/n) sum_i delta_i log |R_i|.
+Inputs the two sides share are fixed on the host, never read back from the
+GPU: the step sigma = 1 / L_bound with L_bound = (sqrt n + sqrt p)^2 / n, the
+Marchenko-Pastur edge of 2 ||X_c||_2^2 / n for near-independent genotype
+columns of variance at most 1/2 (so sigma <= 1/L and the iteration is a
+descent); the penalties are fractions of the oracle's max |g_j(0)| (over all
+columns where the oracle streams X, over 2048 seeded columns elsewhere).
+
+* geno_100k_50k (n=100,000, p=50,000, k=1): 50 whole iterations on both
+  sides, the oracle streaming X (bytes per code) in parallel column blocks:
+  beta after 50 iterations element by element (relative L2 <= 1e-4, the same
+  support outside a 1e-6 threshold margin), g(0) in full, the loss there.
+* geno_200k_10k (n=200,000, p=10,000, k=1): two whole iterations and the
+  autograd backward at full size.
+* geno_400k_100k_k32 (50 iterations, 32 penalties) and geno_400k_500k_k16
+  (3 iterations, 16 penalties): the oracle cannot run whole iterations at
+  these sizes, so the checks sit at the nonzero beta the GPU reached.  At it
+  the oracle computes eta at 64 sampled subjects for every column (the first
+  product over all p SNPs), and, for up to 4 columns whose support it can
+  regenerate, eta over all subjects, the loss, the gradient at 64 sampled SNPs
+  plus support SNPs, and the next iterate there.  At beta = 0: g_j(0) at 64
+  sampled SNPs, the first iterate there and the closed form of the loss,
+  f(0) = (1/n) sum_i delta_i log |R_i|.  geno_400k_500k_k16 also checks eta
+  for a dense random beta (every one of the 3,907 K chunks contributes).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -20,6 +37,8 @@ from helpers import rel_l2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+THREADS = max(1, min(32, os.cpu_count() or 1))
 
 
 def _device_problem(name, **kw):
@@ -39,6 +58,12 @@ def _device_problem(name, **kw):
     return w, prob
 
 
+def _step(n, p):
+    """1 / L_bound: the edge (1 + sqrt(p/n))^2 of the spectrum of X_c^T X_c / n
+    for independent columns, times 2 x the largest genotype variance 1/2."""
+    return n / (np.sqrt(n) + np.sqrt(p)) ** 2
+
+
 def _loss_at_zero(w):
     order = np.argsort(w.y, kind="stable")
     ys = w.y[order]
@@ -47,77 +72,226 @@ def _loss_at_zero(w):
     return float(np.sum(w.delta * np.log(w.n - first)) / w.n)
 
 
-def _grad0_cols(w, idx):
-    """g(0) at columns idx from the oracle: u(0) does not depend on X."""
-    _, u0, _ = oracle.risk(w.y, w.delta, np.zeros(w.n))
-    Xc = w.cols(idx)
-    return oracle.grad(Xc, Xc.mean(axis=0), w.delta, u0)
+def _par_grad(Xt, mu, delta, u, block=512):
+    """oracle.grad_u8 over the columns (rows of Xt), in parallel column blocks:
+    each column's sum is the oracle's own, so the result is the whole call's."""
+    from concurrent.futures import ThreadPoolExecutor
+    m = Xt.shape[0]
+    g = np.zeros(m)
+
+    def run(j0):
+        j1 = min(m, j0 + block)
+        g[j0:j1] = oracle.grad_u8(Xt[j0:j1], mu[j0:j1], delta, u)
+
+    with ThreadPoolExecutor(THREADS) as ex:
+        list(ex.map(run, range(0, m, block)))
+    return g
 
 
-@pytest.mark.parametrize("name", ["geno_100k_50k", "geno_400k_100k_k32", "geno_400k_500k_k16"])
-def test_sampled_first_iteration_full_size(name):
-    w, prob = _device_problem(name)
+def _cols_mu(w, idx):
+    Xt = w.cols_u8(idx, threads=THREADS)
+    return Xt, Xt.mean(axis=1, dtype=np.float64)
+
+
+def _ranks(y):
+    order = np.argsort(y, kind="stable")
+    rank = np.empty(len(y), np.int64)
+    rank[order] = np.arange(len(y))
+    return rank
+
+
+# --------------------------------------------------------------- geno_100k_50k
+def test_geno_100k_50k_fifty_iterations():
+    """n = 100,000 x p = 50,000, lambda = 0.5 lambda_max: 50 iterations on the GPU
+    against the oracle's 50 iterates (Section 5.3 iteration, run as the oracle's
+    ISTA: eta over the support, the risk-set sums, the gradient over every
+    column, the soft-threshold step)."""
+    w, prob = _device_problem("geno_100k_50k")
     try:
-        r = w.r
-        lmax = prob.lambda_max()
-        lams = lmax * r.lambda_fracs()
-        L = prob.lipschitz(tol=1e-3, maxiter=20)
-        step = 1.0 / L
-        beta = prob.zeros(r.k)
+        n, p = w.n, w.p
+        Xt, mu = _cols_mu(w, np.arange(p))  # 5 GB of codes, one byte each
+        sigma = _step(n, p)
+        _, u0, f0 = oracle.risk(w.y, w.delta, np.zeros(n))
+        g0 = _par_grad(Xt, mu, w.delta, u0)
+        lmax = float(np.abs(g0).max())
+        lam = 0.5 * lmax
+        # beta = 0: loss, gradient, lambda_max
+        beta = prob.zeros(1)
         loss, grad = prob.loss_grad(beta)
-        assert np.allclose(loss, _loss_at_zero(w), rtol=1e-12, atol=0)
-        prob.prox_step(beta, lams, step)
+        assert abs(loss[0] - f0) <= 1e-12 * abs(f0)
+        assert rel_l2(grad.cpu().numpy()[0].astype(np.float64), -g0) <= 1e-5
+        assert abs(prob.lambda_max() - lmax) <= 1e-5 * lmax
+        # 50 iterations
+        iters = 50
+        for _ in range(iters):
+            prob.prox_step(beta, [lam], sigma)
         prob.sync()
-        idx = np.unique((w.uniform_vec(13, 64) * w.p).astype(np.int64))
-        g0 = _grad0_cols(w, idx)
-        G = grad.cpu().numpy()[0, idx].astype(np.float64)
-        assert rel_l2(G, -g0) <= 1e-5
-        # lambda_max is max_j |g_j(0)|: no sampled column may exceed it
-        assert np.abs(g0).max() <= lmax * (1 + 1e-5)
-        B = beta.cpu().numpy()[:, idx].astype(np.float64)
-        z = step * g0
-        # the gradient bar bounds every |dz_j| by 1e-5 ||z||_2, and the soft
-        # threshold is 1-Lipschitz, so |dbeta_j| <= 1e-5 ||z||_2 as well
-        dz = 1e-5 * np.linalg.norm(z)
-        for c, lam in enumerate(lams):
-            b1 = np.array([oracle.soft_threshold(zj, step * lam) for zj in z])
-            amb = np.abs(np.abs(z) - step * lam) <= max(1e-6, dz)
-            assert np.all(((B[c] != 0) == (b1 != 0)) | amb)
-            nz = b1 != 0
-            if nz.any():
-                np.testing.assert_allclose(B[c][nz], b1[nz], rtol=1e-4, atol=dz)
+        Bg = beta.cpu().numpy()[0].astype(np.float64)
+        b_o = np.zeros(p)
+        for t in range(iters):
+            S = np.nonzero(b_o)[0]
+            eta = oracle.eta_u8(Xt[S], mu[S], b_o[S]) if len(S) else np.zeros(n)
+            _, u, f = oracle.risk(w.y, w.delta, eta)
+            g = g0 if t == 0 else _par_grad(Xt, mu, w.delta, u)
+            z = b_o + sigma * g
+            b_o = oracle.prox(b_o, g, sigma, lam)
+        assert np.count_nonzero(b_o) > 0
+        amb = np.abs(np.abs(z) - sigma * lam) <= 1e-6
+        assert np.all(((Bg != 0) == (b_o != 0)) | amb)
+        assert rel_l2(Bg, b_o) <= 1e-4, rel_l2(Bg, b_o)
+        # loss and gradient at the GPU's 50th iterate
+        S = np.nonzero(Bg)[0]
+        eta = oracle.eta_u8(Xt[S], mu[S], Bg[S])
+        _, u, f = oracle.risk(w.y, w.delta, eta)
+        g = _par_grad(Xt, mu, w.delta, u)
+        loss, grad = prob.loss_grad(beta)
+        assert abs(loss[0] - f) <= 1e-7 * abs(f)
+        assert rel_l2(grad.cpu().numpy()[0].astype(np.float64), -g) <= 1e-5
     finally:
         prob.close()
 
 
+# ------------------------------------------------- geno_400k_100k_k32, geno_400k_500k_k16
+def _lambda_anchor(w, idx, u0):
+    """max_j |g_j(0)| over the sampled columns idx (the oracle's): a lower bound
+    of lambda_max from which the penalty grid is laid out."""
+    Xs, mus = _cols_mu(w, idx)
+    return float(np.abs(_par_grad(Xs, mus, w.delta, u0)).max())
+
+
+def _check_eta_rows(w, prob, beta, rows, rank, gate=1e-4):
+    """eta = X_c beta at sampled subjects, up to the common shift (the loss and
+    gradient do not see one): the GPU's centred eta against the oracle's X beta
+    over all p SNPs at those subjects, each centred over the sample."""
+    B = beta.detach().cpu().numpy().astype(np.float64)
+    eg = prob.eta(beta).cpu().numpy()[:, rank[rows]]
+    Xr = np.ascontiguousarray(w.rows_u8(rows).T)  # p x 64: the "columns" are SNPs
+    for c in range(B.shape[0]):
+        eo = oracle.eta_u8(Xr, None, B[c])
+        dg, do = eg[c] - eg[c].mean(), eo - eo.mean()
+        if np.linalg.norm(do) == 0:
+            assert np.all(np.abs(dg) <= 1e-12)
+            continue
+        assert rel_l2(dg, do) <= gate, (c, rel_l2(dg, do))
+
+
+def _check_at_gpu_beta(w, prob, beta, lams, sigma, rank, max_support=4000, ncols=4):
+    """Loss, gradient and next iterate at the GPU's beta for up to `ncols`
+    columns whose support the oracle can regenerate in full."""
+    B = beta.cpu().numpy().astype(np.float64)
+    k = B.shape[0]
+    sizes = np.count_nonzero(B, axis=1)
+    cand = [c for c in np.argsort(-sizes) if 1 <= sizes[c] <= max_support][:ncols]
+    assert cand, f"no column with 1..{max_support} nonzeros: supports {sizes.tolist()}"
+    loss, grad = prob.loss_grad(beta)
+    G = grad.cpu().numpy().astype(np.float64)
+    nxt = beta.clone()
+    prob.prox_step(nxt, lams, sigma)
+    Bn = nxt.cpu().numpy().astype(np.float64)
+    samp = np.unique((w.uniform_vec(17, 64) * w.p).astype(np.int64))
+    for c in cand:
+        S = np.nonzero(B[c])[0]
+        XS, muS = _cols_mu(w, S)
+        eta = oracle.eta_u8(XS, muS, B[c, S])
+        _, u, f = oracle.risk(w.y, w.delta, eta)
+        J = np.unique(np.concatenate([samp, S[:64]]))
+        XJ, muJ = _cols_mu(w, J)
+        g = _par_grad(XJ, muJ, w.delta, u)
+        assert abs(loss[c] - f) <= 1e-7 * abs(f), (c, loss[c], f)
+        assert rel_l2(G[c, J], -g) <= 1e-5, (c, rel_l2(G[c, J], -g))
+        z = B[c, J] + sigma * g
+        b1 = oracle.prox(B[c, J], g, sigma, lams[c])
+        # the gradient bar bounds every |dz_j| by 1e-5 sigma ||g_J||; the soft
+        # threshold is 1-Lipschitz; beta is stored in FP32
+        dz = 1e-5 * sigma * np.linalg.norm(g) + 2.0 ** -22 * np.abs(B[c]).max()
+        amb = np.abs(np.abs(z) - sigma * lams[c]) <= max(1e-6, dz)
+        assert np.all(((Bn[c, J] != 0) == (b1 != 0)) | amb), c
+        assert np.all(np.abs(Bn[c, J] - b1) <= dz + 1e-6 * np.abs(b1)), (c, np.abs(Bn[c, J] - b1).max(), dz)
+    return cand
+
+
+@pytest.mark.parametrize("name,iters", [("geno_400k_100k_k32", 50), ("geno_400k_500k_k16", 3)])
+def test_full_size_sampled(name, iters):
+    w, prob = _device_problem(name)
+    try:
+        r = w.r
+        n, p = w.n, w.p
+        sigma = _step(n, p)
+        rank = _ranks(w.y)
+        _, u0, _ = oracle.risk(w.y, w.delta, np.zeros(n))
+        # beta = 0: the loss in closed form, g_j(0) at 64 sampled SNPs, lambda_max
+        idx = np.unique((w.uniform_vec(13, 64) * p).astype(np.int64))
+        Xi, mui = _cols_mu(w, idx)
+        g0 = _par_grad(Xi, mui, w.delta, u0)
+        beta = prob.zeros(r.k)
+        loss, grad = prob.loss_grad(beta)
+        assert np.allclose(loss, _loss_at_zero(w), rtol=1e-12, atol=0)
+        assert rel_l2(grad.cpu().numpy()[0, idx].astype(np.float64), -g0) <= 1e-5
+        lmax = prob.lambda_max()
+        assert np.abs(g0).max() <= lmax * (1 + 1e-5)
+        anchor = _lambda_anchor(w, np.unique((w.uniform_vec(19, 2048) * p).astype(np.int64)), u0)
+        assert anchor <= lmax * (1 + 1e-5)
+        lams = anchor * r.lambda_fracs()
+        # the first iterate at the sampled SNPs
+        prob.prox_step(beta, lams, sigma)
+        prob.sync()
+        B1 = beta.cpu().numpy()[:, idx].astype(np.float64)
+        z = sigma * g0
+        dz = 1e-5 * np.linalg.norm(z)
+        for c, lam in enumerate(lams):
+            b1 = np.array([oracle.soft_threshold(zj, sigma * lam) for zj in z])
+            amb = np.abs(np.abs(z) - sigma * lam) <= max(1e-6, dz)
+            assert np.all(((B1[c] != 0) == (b1 != 0)) | amb)
+            nz = b1 != 0
+            if nz.any():
+                np.testing.assert_allclose(B1[c][nz], b1[nz], rtol=1e-4, atol=dz)
+        # the remaining iterations, then the checks at the GPU's nonzero beta
+        for _ in range(iters - 1):
+            prob.prox_step(beta, lams, sigma)
+        prob.sync()
+        assert np.count_nonzero(beta.cpu().numpy()) > 0
+        rows = np.unique((w.uniform_vec(23, 64) * n).astype(np.int64))
+        _check_eta_rows(w, prob, beta, rows, rank)
+        _check_at_gpu_beta(w, prob, beta, lams, sigma, rank)
+        if name == "geno_400k_500k_k16":
+            # a dense beta: every K chunk of the first product contributes
+            rng = np.random.default_rng(7)
+            dense = torch.tensor(rng.normal(0, 0.01, (r.k, p)), dtype=torch.float32, device="cuda")
+            _check_eta_rows(w, prob, dense, rows, rank)
+    finally:
+        prob.close()
+
+
+# --------------------------------------------------------------- geno_200k_10k
+def _streamed_grad(w, beta, blocks):
+    """Oracle gradient and loss at beta, X streamed in column blocks."""
+    n, p = w.n, w.p
+    nzc = np.nonzero(beta)[0]
+    if len(nzc):
+        Xs, mus = _cols_mu(w, nzc)
+        eta = oracle.eta_u8(Xs, mus, beta[nzc])
+    else:
+        eta = np.zeros(n)
+    _, u, f = oracle.risk(w.y, w.delta, eta)
+    g = np.zeros(p)
+    for blk in blocks:
+        Xb, mub = _cols_mu(w, blk)
+        g[blk] = _par_grad(Xb, mub, w.delta, u)
+    return g, f, u, eta
+
+
 def test_geno_200k_10k_two_full_iterations():
     """n = 200,000 x p = 10,000 at full size: two iterations from beta = 0 at lambda =
-    0.5 lambda_max, the oracle streaming X in blocks of 500 columns."""
+    0.5 lambda_max, the oracle streaming X in blocks of 2500 columns."""
     w, prob = _device_problem("geno_200k_10k")
     try:
         n, p = w.n, w.p
-        blocks = [np.arange(j, min(j + 500, p)) for j in range(0, p, 500)]
-        # oracle gradient at beta, streaming X
-        def oracle_grad(beta):
-            nzc = np.nonzero(beta)[0]
-            if len(nzc):
-                Xs = w.cols(nzc)
-                eta = oracle.eta(Xs, Xs.mean(axis=0), beta[nzc])
-            else:
-                eta = np.zeros(n)
-            _, u, f = oracle.risk(w.y, w.delta, eta)
-            g = np.zeros(p)
-            for blk in blocks:
-                Xb = w.cols(blk)
-                g[blk] = oracle.grad(Xb, Xb.mean(axis=0), w.delta, u)
-            return g, f
-
-        g0, f0 = oracle_grad(np.zeros(p))
+        blocks = [np.arange(j, min(j + 2500, p)) for j in range(0, p, 2500)]
+        g0, f0, _, _ = _streamed_grad(w, np.zeros(p), blocks)
         lmax = float(np.abs(g0).max())
         assert abs(prob.lambda_max() - lmax) <= 1e-5 * lmax
         lam = 0.5 * lmax
-        L = prob.lipschitz(tol=1e-4, maxiter=100)
-        step = 1.0 / L
+        step = _step(n, p)
         beta = prob.zeros(1)
         loss, grad = prob.loss_grad(beta)
         assert abs(loss[0] - f0) <= 1e-12 * abs(f0)
@@ -133,7 +307,7 @@ def test_geno_200k_10k_two_full_iterations():
             amb = np.abs(np.abs(z) - step * lam) <= 1e-6
             assert np.all(((Bg != 0) == (b_o != 0)) | amb), it
             assert rel_l2(Bg, b_o) <= 1e-4, (it, rel_l2(Bg, b_o))
-            g_o, _ = oracle_grad(b_o)
+            g_o, _, _, _ = _streamed_grad(w, b_o, blocks)
     finally:
         prob.close()
 
@@ -142,7 +316,7 @@ def test_geno_200k_10k_autograd_full_size():
     """n = 200,000 x p = 10,000 at full size: the backward of CoxNLL
     (the library's gradient) at 64 seeded coordinates against central
     differences (h = 1e-3) of the FP64 oracle loss, and against the oracle
-    gradient over all columns (streamed in blocks of 500)."""
+    gradient over all columns (streamed in blocks of 2500)."""
     from paper_2010_16114_gb300.autograd import cox_nll
     w, prob = _device_problem("geno_200k_10k")
     try:
@@ -156,22 +330,16 @@ def test_geno_200k_10k_autograd_full_size():
         f.sum().backward()
         g = beta.grad.cpu().numpy()[0].astype(np.float64)
         bf = beta.detach().cpu().numpy()[0].astype(np.float64)
-        nzc = np.nonzero(bf)[0]
-        Xs = w.cols(nzc)
-        eta0 = oracle.eta(Xs, Xs.mean(axis=0), bf[nzc])
-        _, u0, f0 = oracle.risk(w.y, w.delta, eta0)
+        blocks = [np.arange(j, min(j + 2500, p)) for j in range(0, p, 2500)]
+        g_o, f0, _, eta0 = _streamed_grad(w, bf, blocks)
+        g_o = -g_o
         assert abs(float(f.detach()[0]) - f0) <= 1e-7 * abs(f0)
-        g_o = np.zeros(p)
-        for j0 in range(0, p, 500):
-            blk = np.arange(j0, min(j0 + 500, p))
-            Xb = w.cols(blk)
-            g_o[blk] = -oracle.grad(Xb, Xb.mean(axis=0), w.delta, u0)
         assert rel_l2(g, g_o) <= 1e-5
         coords = np.unique((w.uniform_vec(11, 64) * p).astype(np.int64))
         h, gmax = 1e-3, np.abs(g_o).max()
-        for j in coords:
-            xj = w.cols(np.array([j]))[:, 0]
-            xc = xj - xj.mean()
+        Xc, muc = _cols_mu(w, coords)
+        for t, j in enumerate(coords):
+            xc = Xc[t].astype(np.float64) - muc[t]
             fp = oracle.risk(w.y, w.delta, eta0 + h * xc)[2]
             fm = oracle.risk(w.y, w.delta, eta0 - h * xc)[2]
             fd = (fp - fm) / (2 * h)

@@ -24,7 +24,8 @@ def test_zero_wait_limit_reports_timeout():
     beta = torch.zeros((2, w.p), dtype=torch.float32, device="cuda")
     beta[:, ::7] = 0.01
     codes = []
-    with CoxProblem(X, w.y, w.delta, wait_limit_s=0.0) as prob:
+    # the per-tile issue mode: one issuer per row tile
+    with CoxProblem(X, w.y, w.delta, wait_limit_s=0.0, tile_m=2, chunks=2, issue=1) as prob:
         for _ in range(3):
             try:
                 prob.loss_grad(beta)

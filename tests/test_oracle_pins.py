@@ -472,3 +472,20 @@ def test_centred_eta_hand_example(orc):
     eta = orc.eta(X, np.array([2.0, 3.0]), np.array([1.0, 10.0]))
     assert list(eta) == [-11.0, 11.0]
     assert list(orc.eta(X, None, np.array([1.0, 10.0]))) == [21.0, 43.0]
+
+
+def test_byte_column_products_equal_the_float_ones(orc):
+    """eta_u8 / grad_u8 (genotype columns held as bytes) are the same loops as
+    eta / grad; on the same codes they agree bit for bit, so every pin of the
+    float64 products carries over."""
+    r = _rng(5)
+    n, m = 257, 19
+    Xt = r.integers(0, 3, size=(m, n)).astype(np.uint8)
+    X = Xt.T.astype(np.float64)
+    mu = X.mean(axis=0)
+    beta = r.normal(0, 0.3, m)
+    delta = (r.random(n) < 0.4).astype(np.uint8)
+    u = r.random(n)
+    for mm in (mu, None):
+        assert np.array_equal(orc.eta_u8(Xt, mm, beta), orc.eta(X, mm, beta))
+        assert np.array_equal(orc.grad_u8(Xt, mm, delta, u), orc.grad(X, mm, delta, u))
