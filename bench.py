@@ -54,8 +54,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gemv", action="store_true")
-    ap.add_argument("--cpu-sample-cols", type=int, default=400)
+    ap.add_argument("--cpu-sample-cols", type=int, default=1000)
     ap.add_argument("--cpu-sample-steps", type=int, default=3)
+    ap.add_argument("--path-iters", type=int, default=1000,
+                    help="iteration cap of the timed cox_path_fit run (0: skip it)")
+    ap.add_argument("--path-tol", type=float, default=1e-6)
     return ap.parse_args()
 
 
@@ -182,51 +185,93 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ CPU oracle baseline
-def oracle_sample(r, cols: int, steps: int):
+class OracleSample:
     """The FP64 oracle, as it stands, on a bounded sample of the workload: all n
-    subjects, `cols` SNP columns, one penalty; returns seconds per sample step
-    and the scale factor to one full iteration (p / cols columns, k penalties)."""
-    import oracle
-    import synth
-    w = synth.Workload(r)
-    cols = min(cols, r.p)
-    idx = np.arange(cols, dtype=np.int64)
-    Xs = w.cols(idx)
-    mu = Xs.mean(axis=0)
-    beta = np.zeros(cols)
-    lam = 0.0
-    sigma = 1e-3
-    times = []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        beta, _, _ = oracle.ista(Xs, mu, w.y, w.delta, sigma, lam, 1, beta)
-        times.append(time.perf_counter() - t0)
-    t = float(np.median(times))
-    scale = (r.p / cols) * r.k
-    return t, scale, cols
+    subjects, the first `cols` SNP columns, one penalty.  A step is one ISTA
+    iteration of the oracle (Section 5.3): eta, the risk-set sums, the
+    gradient, the soft threshold.  With one thread it is oracle.ista itself;
+    with more, the oracle's own eta and gradient routines run concurrently on
+    column blocks (each column's gradient is the oracle's; eta adds the
+    blocks' partial sums), on the host's cores."""
+
+    def __init__(self, r, cols: int):
+        import oracle
+        import synth
+        oracle.build()
+        self.oracle = oracle
+        self.r = r
+        self.w = synth.Workload(r)
+        self.cols = min(cols, r.p)
+        idx = np.arange(self.cols)
+        if r.kind == "geno":
+            X = self.w.cols_u8(idx, threads=os.cpu_count() or 1).T
+        else:
+            X = self.w.cols(idx)
+        self.X = np.asfortranarray(X, dtype=np.float64)  # n x cols, column-major
+        self.mu = self.X.mean(axis=0)
+
+    def time_step(self, cols: int, threads: int, steps: int) -> float:
+        """Median seconds of one oracle iteration on the first `cols` columns."""
+        from concurrent.futures import ThreadPoolExecutor
+        o, w = self.oracle, self.w
+        X, mu = self.X[:, :cols], self.mu[:cols]
+        sigma, lam = 1e-3, 0.0
+        beta = np.zeros(cols)
+        blocks = [b for b in np.array_split(np.arange(cols), threads) if len(b)]
+        Xb = [np.asfortranarray(X[:, b]) for b in blocks]
+        times = []
+        with ThreadPoolExecutor(max(1, threads)) as ex:
+            for _ in range(steps):
+                t0 = time.perf_counter()
+                if threads == 1:
+                    beta, _, _ = o.ista(X, mu, w.y, w.delta, sigma, lam, 1, beta)
+                else:
+                    parts = list(ex.map(lambda q: o.eta(Xb[q], mu[blocks[q]], beta[blocks[q]]), range(len(blocks))))
+                    eta = np.sum(parts, axis=0)
+                    _, u, _ = o.risk(w.y, w.delta, eta)
+                    gs = list(ex.map(lambda q: o.grad(Xb[q], mu[blocks[q]], w.delta, u), range(len(blocks))))
+                    beta = o.prox(beta, np.concatenate(gs), sigma, lam)
+                times.append(time.perf_counter() - t0)
+        return float(np.median(times))
+
+    def baseline(self, steps: int):
+        """cpu_baseline object: the threaded oracle on all host cores, the
+        1-thread figure beside it, and the per-column cost at two sample sizes
+        (the extrapolation to p columns and k penalties assumes it linear)."""
+        r = self.r
+        cores = os.cpu_count() or 1
+        half = max(1, self.cols // 2)
+        t_all = self.time_step(self.cols, cores, steps)
+        t_half = self.time_step(half, cores, steps)
+        t_one = self.time_step(self.cols, 1, max(1, steps // 2))
+        scale = (r.p / self.cols) * r.k
+        return {
+            "value": 1.0 / (t_all * scale), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one FP64 oracle iteration (eta, risk-set sums, gradient, soft threshold) on all {r.n} "
+                      f"subjects x the first {self.cols} SNP columns, one penalty, oracle routines on {cores} "
+                      f"threads over column blocks, median of {steps}; scaled by p/{self.cols} columns x {r.k} "
+                      f"penalties",
+            "one_thread": {"value": 1.0 / (t_one * scale), "unit": UNIT, "cores": 1,
+                           "sample": f"oracle.ista itself on the same sample, median of {max(1, steps // 2)}"},
+            "per_column_s": {str(self.cols): t_all / self.cols, str(half): t_half / half},
+        }
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
     r = recipe(args)
-    import oracle
-    oracle.build()
-    cols = args.cpu_sample_cols
-    # warm-up steps run inside oracle_sample's loop are not separated: run them first, untimed
+    smp = OracleSample(r, args.cpu_sample_cols)
     if args.warmup > 0:
-        oracle_sample(r, min(cols, 50), 1)
-    t_step, scale, cols = oracle_sample(r, cols, max(1, args.steps))
-    full = t_step * scale
-    value = 1.0 / full
+        smp.time_step(min(smp.cols, 50), os.cpu_count() or 1, 1)
+    cpu = smp.baseline(max(1, args.steps))
+    value = cpu["value"]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": full * 1e3, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(r)},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"one FP64 oracle iteration on all {r.n} subjects x {cols} SNP columns, one "
-                                   f"penalty, {args.steps} timed steps; scaled by p/{cols} columns x {r.k} penalties"},
+        "config": {"workload": workload_name(r), "n": r.n, "p": r.p, "k": r.k},
+        "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -346,20 +391,34 @@ def run_ours(args, rank, world):
         g1.record(stream)
         torch.cuda.synchronize()
         gms = g0.elapsed_time(g1) / args.gemv_steps
+        g_hbm = 2 * k * xb / (gms / 1e3) / 1e9
         gemv = {"iters_per_s": 1e3 / gms, "ms_per_step": gms, "steps": args.gemv_steps,
                 "lambda_iters_per_s": k * 1e3 / gms, "speedup_of_batched": (1e3 / ms_step) / (1e3 / gms),
-                "hbm_gbs": 2 * k * xb / (gms / 1e3) / 1e9,
+                "hbm_gbs": g_hbm, "hbm_frac": g_hbm / peak,
                 "rel_l2_vs_batched_one_step": diff}
         prob.set_precision("split_e4m3")
 
+    # the CUDA-graph path fit (Section 6 rule): every penalty from beta = 0 to
+    # |F_t - F_{t-10}| / |F_t + 1| < tol or the iteration cap, replays of 10 steps
+    path = None
+    if args.path_iters > 0:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, iters, obj, conv = prob.path_fit(lams, step, max_iter=args.path_iters, tol=args.path_tol)
+        torch.cuda.synchronize()
+        pt = time.perf_counter() - t0
+        steps_run = int(np.max(iters))
+        path = {"iters_per_s": steps_run / pt, "lambda_iters_per_s": k * steps_run / pt, "seconds": pt,
+                "max_iter": args.path_iters, "tol": args.path_tol, "iterations_run": steps_run,
+                "iterations_per_column": [int(x) for x in iters],
+                "converged_columns": int(np.sum(np.asarray(iters) < args.path_iters)),
+                "final_objective": [float(x) for x in obj],
+                "timing": "wall clock around cox_path_fit (graph replays of 10 iterations, host reads the "
+                          "k objectives after each replay), beta = 0 to the stopping rule or the cap"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        t_s, scale, cols = oracle_sample(r, args.cpu_sample_cols, args.cpu_sample_steps)
-        cpu = {"value": 1.0 / (t_s * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one FP64 oracle iteration on all {n} subjects x {cols} SNP columns, one penalty "
-                         f"(median of {args.cpu_sample_steps}); scaled by p/{cols} columns x {k} penalties"}
+        cpu = OracleSample(r, args.cpu_sample_cols).baseline(args.cpu_sample_steps)
 
     prob.close()
     if rank != 0:
@@ -387,6 +446,7 @@ def run_ours(args, rank, world):
         "kernel_ms_per_step": {"x_b_product": cls_ms[0] / args.steps, "xt_v_product_step": cls_ms[1] / args.steps,
                                "scans": cls_ms[2] / args.steps, "other": cls_ms[3] / args.steps},
         "cpu_baseline": cpu,
+        "path_fit": path,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": ck,
