@@ -224,10 +224,52 @@ int cox_last_objective(cox_h h, double *obj_host, int k, void *stream);
 int cox_path_fit(cox_h h, const double *lambdas, int k, int max_iter, double tol, double step,
                  int warm, void *beta_dev, int *iters_host, double *obj_host, void *stream);
 
+/*
+ * The Section 6 lambda path, one penalty after another (the UK Biobank fit
+ * ran each lambda of its grid to the stopping rule): lambdas[l] is solved
+ * from beta = 0 (warm = 0) or from the solution of lambdas[l-1] (warm = 1),
+ * with its unpenalised coefficients gamma likewise (when covariates are set),
+ * each to |F_t - F_{t-lag}| / |F_t + 1| < tol or max_iter iterations, as
+ * CUDA-graph replays of `lag` steps (the rule of cox_path_fit with k = 1).
+ *   B_dev     : p x L coefficients (device) out, column l at lambdas[l].
+ *   G_host    : q x L doubles (host) out, column l = gamma at lambdas[l]; may
+ *               be NULL (and is not written when no covariates are set).
+ *   iters_host: L ints; obj_host: L doubles (final F).  Either may be NULL.
+ * Returns COX_OK, or COX_ERR_NOT_CONVERGED if some lambda hit max_iter.
+ */
+int cox_path_seq(cox_h h, const double *lambdas, int L, int max_iter, double tol, double step, int warm,
+                 void *B_dev, double *G_host, int *iters_host, double *obj_host, void *stream);
+
+/*
+ * Unpenalised covariates (Section 6: sex and ten principal components enter
+ * the UK Biobank model without a penalty).  With Z set, every iteration works
+ * with eta = X_c beta + Z gamma: beta takes the soft-threshold step, gamma the
+ * plain gradient step gamma <- gamma + step Z^T (delta - u) / n, and the
+ * penalty covers beta only (F = f + lambda ||beta||_1).  Z is used as given
+ * (the partial likelihood does not see a shift of a column).
+ *   Z_host: n x q doubles, row-major, subjects in cox_setup's order; finite.
+ *   q     : 0 .. COX_MAX_COVARIATES (0 removes the covariates).
+ * gamma (q x k doubles, column c for lambdas[c]) belongs to the handle: it is
+ * zero after this call and whenever the number of columns k changes, and
+ * cox_path_fit with warm = 0 starts it from zero (warm = 1 keeps it, warm = 2
+ * restores the checkpoint's).  cox_lambda_max and cox_loss_grad evaluate at
+ * the handle's gamma; cox_eta returns X_c B alone.  Drops the per-k workspace.
+ */
+enum { COX_MAX_COVARIATES = 16 };
+int cox_set_covariates(cox_h h, const double *Z_host, int q);
+/* gamma of the handle for k columns (q x k doubles, host): read, or write
+ * (gamma_host NULL: zero).  No covariates: no-op.  cox_get_gamma needs the
+ * workspace for k (a call with k columns since the last change). */
+int cox_get_gamma(cox_h h, double *gamma_host, int k);
+int cox_set_gamma(cox_h h, const double *gamma_host, int k);
+/* The gradient of f with respect to gamma at the last evaluation for k
+ * columns (q x k doubles, host): -Z^T (delta - u) / n. */
+int cox_grad_gamma(cox_h h, double *grad_host, int k);
+
 /* Checkpoint: the solver state of the last path fit / step (coefficients,
- * iteration counters, objective history).  cox_get_state with buf == NULL
- * sets *size to the bytes needed.  cox_set_state restores it (same n, p, k,
- * precision) so a path fit resumes bit-identically. */
+ * gamma, iteration counters, objective history).  cox_get_state with buf ==
+ * NULL sets *size to the bytes needed.  cox_set_state restores it (same n, p,
+ * k, precision, covariate count) so a path fit resumes bit-identically. */
 int cox_get_state(cox_h h, void *buf, size_t *size);
 int cox_set_state(cox_h h, const void *buf, size_t size);
 

@@ -36,8 +36,10 @@ EXPORTS = [
     "cox_loss_grad", "cox_prox_step", "cox_prox_step_host", "cox_sync", "cox_last_objective",
     "cox_path_fit", "cox_get_state", "cox_set_state", "cox_get_info", "cox_get_mu_order",
     "cox_strerror", "cox_set_precision", "cox_profile", "cox_profile_read", "cox_lipschitz_noalloc",
-    "cox_autotune", "cox_eta", "cox_plan_shape", "cox_rank_by_entry",
+    "cox_autotune", "cox_eta", "cox_plan_shape", "cox_rank_by_entry", "cox_path_seq", "cox_set_covariates",
+    "cox_get_gamma", "cox_set_gamma", "cox_grad_gamma",
 ]
+COX_MAX_COVARIATES = 16
 
 
 class cox_options(ctypes.Structure):
@@ -133,6 +135,13 @@ def load(path: str | None = None):
     lib.cox_plan_shape.argtypes = [I, I, I, I, I, ctypes.POINTER(cox_plan)]
     lib.cox_rank_by_entry.restype = I
     lib.cox_rank_by_entry.argtypes = [I64, I, P, P, I, P, P, ctypes.POINTER(I64)]
+    lib.cox_path_seq.restype = I
+    lib.cox_path_seq.argtypes = [P, P, I, I, D, D, I, P, P, P, P, P]
+    lib.cox_set_covariates.restype = I
+    lib.cox_set_covariates.argtypes = [P, P, I]
+    for nm in ("cox_get_gamma", "cox_set_gamma", "cox_grad_gamma"):
+        getattr(lib, nm).restype = I
+        getattr(lib, nm).argtypes = [P, P, I]
     lib.cox_strerror.restype = ctypes.c_char_p
     lib.cox_strerror.argtypes = [I]
     _lib = lib
@@ -263,3 +272,24 @@ def cox_plan_shape(k: int, tile_m: int = 0, chunks: int = 0, stages: int = 0, is
 
 def cox_strerror(code: int) -> str:
     return strerror(code)
+
+
+def cox_path_seq(h, lam_ptr, L, max_iter, tol, step, warm, B_ptr, G_ptr, iters_ptr, obj_ptr, stream_ptr):
+    return load().cox_path_seq(h, lam_ptr, L, max_iter, tol, step, warm, B_ptr, G_ptr, iters_ptr, obj_ptr,
+                               stream_ptr)
+
+
+def cox_set_covariates(h, Z_ptr, q: int) -> int:
+    return load().cox_set_covariates(h, Z_ptr, q)
+
+
+def cox_get_gamma(h, out_ptr, k: int) -> int:
+    return load().cox_get_gamma(h, out_ptr, k)
+
+
+def cox_set_gamma(h, in_ptr, k: int) -> int:
+    return load().cox_set_gamma(h, in_ptr, k)
+
+
+def cox_grad_gamma(h, out_ptr, k: int) -> int:
+    return load().cox_grad_gamma(h, out_ptr, k)

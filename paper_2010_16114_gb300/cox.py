@@ -116,6 +116,7 @@ class CoxProblem:
         L.check(rc, "cox_setup")
         self.h = h
         self.n, self.p = n, p
+        self.q = 0
         self.precision = precision
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         dev = torch.cuda.current_device() if device is None else device
@@ -255,6 +256,49 @@ class CoxProblem:
                             _vp(iters), _vp(obj), _stream_ptr(stream))
         L.check(rc, "cox_path_fit", allow=(L.COX_OK, L.COX_ERR_NOT_CONVERGED))
         return beta, iters, obj, rc == L.COX_OK
+
+    def path_seq(self, lambdas, step: float, max_iter: int = 1000, tol: float = 1e-6, warm: bool = True,
+                 stream=None):
+        """The Section 6 path, one penalty after another (cox_path_seq), each from
+        the previous one's solution when warm.  Returns (B (L, p), G (L, q),
+        iterations, objectives, converged)."""
+        lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64).ravel())
+        nl = len(lam)
+        B = self.zeros(nl)
+        G = np.zeros((nl, max(self.q, 1)))
+        iters = np.zeros(nl, np.int32)
+        obj = np.zeros(nl)
+        rc = L.cox_path_seq(self.h, _vp(lam), nl, int(max_iter), float(tol), float(step), int(bool(warm)), _vp(B),
+                            _vp(G), _vp(iters), _vp(obj), _stream_ptr(stream))
+        L.check(rc, "cox_path_seq", allow=(L.COX_OK, L.COX_ERR_NOT_CONVERGED))
+        return B, G[:, :self.q], iters, obj, rc == L.COX_OK
+
+    # -- unpenalised covariates (Section 6) ---------------------------------------------
+    def set_covariates(self, Z):
+        """Covariates that enter without a penalty: Z (n, q) in subject order, or None."""
+        if Z is None:
+            L.check(L.cox_set_covariates(self.h, None, 0), "cox_set_covariates")
+            self.q = 0
+            return
+        Z = np.ascontiguousarray(np.asarray(Z, dtype=np.float64).reshape(self.n, -1))
+        L.check(L.cox_set_covariates(self.h, _vp(Z), Z.shape[1]), "cox_set_covariates")
+        self.q = Z.shape[1]
+
+    def gamma(self, k: int) -> np.ndarray:
+        """The handle's unpenalised coefficients for k columns, shape (k, q)."""
+        out = np.zeros((k, max(self.q, 1)))
+        L.check(L.cox_get_gamma(self.h, _vp(out), k), "cox_get_gamma")
+        return out[:, :self.q]
+
+    def set_gamma(self, gamma, k: int):
+        g = None if gamma is None else np.ascontiguousarray(np.asarray(gamma, dtype=np.float64).reshape(k, self.q))
+        L.check(L.cox_set_gamma(self.h, _vp(g), k), "cox_set_gamma")
+
+    def grad_gamma(self, k: int) -> np.ndarray:
+        """d f / d gamma at the last evaluation for k columns, shape (k, q)."""
+        out = np.zeros((k, max(self.q, 1)))
+        L.check(L.cox_grad_gamma(self.h, _vp(out), k), "cox_grad_gamma")
+        return out[:, :self.q]
 
     def get_state(self) -> bytes:
         size = ctypes.c_size_t()

@@ -56,7 +56,7 @@ void free_workspace(cox_handle *h)
     Workspace &w = h->ws;
     void *ptrs[] = {w.eta, w.w, w.Rt, w.Ft, w.cmax, w.csw, w.csd, w.suf, w.pre, w.lossp, w.vsp, w.l1p,
                     w.sumV, w.f, w.F, w.l1, w.mub, w.lam, w.active, w.Fring, w.Bq, w.Vq, w.bs1, w.bs4, w.bmaxp,
-                    w.vmaxp, w.part1, w.part4, w.cnt4, w.V64, w.V32, w.eta32, w.G32, w.gpart};
+                    w.vmaxp, w.part1, w.part4, w.cnt4, w.V64, w.V32, w.eta32, w.G32, w.gpart, w.gamma, w.gz, w.zvp};
     for (void *p : ptrs) dfree(p);
     const GemmPlan g1 = w.g1, g4 = w.g4;
     (void)g1;
@@ -131,6 +131,19 @@ struct Site {
 
 } // namespace
 
+// The unpenalised block of the iteration for columns from `col` on: gamma
+// enters eta, and a step (EPI_PROX) moves it by step Z^T (delta - u) / n.
+void set_covariate_args(cox_handle *h, ScanArgs &sa, int col, int epi, double step)
+{
+    Workspace &ws = h->ws;
+    if (h->q == 0) return;
+    sa.gamma = ws.gamma + static_cast<int64_t>(col) * h->q;
+    sa.gz = ws.gz + static_cast<int64_t>(col) * h->q;
+    sa.active = ws.active + col;
+    sa.step = step;
+    sa.gamma_step = epi == EPI_PROX;
+}
+
 // One iteration for k columns.  epi: EPI_PROX (update beta) or EPI_GRAD.
 int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, cudaStream_t st)
 {
@@ -165,6 +178,7 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
         sa.exp64 = false;
         sa.lam = ws.lam;
         sa.need_loss = true;
+        set_covariate_args(h, sa, 0, epi, step);
         {
             Site s_(h, 2, 8, st);
             COX_TRY(run_scans(h, sa, st));
@@ -214,6 +228,7 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
         sa.exp64 = true;
         sa.lam = ws.lam;
         sa.need_loss = true;
+        set_covariate_args(h, sa, 0, epi, step);
         {
             Site s_(h, 2, 8, st);
             COX_TRY(run_scans(h, sa, st));
@@ -250,6 +265,7 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
         sa.exp64 = false;
         sa.lam = ws.lam + c;
         sa.need_loss = true;
+        set_covariate_args(h, sa, c, epi, step);
         {
             Site s_(h, 2, 8, st);
             COX_TRY(run_scans(h, sa, st));
@@ -331,6 +347,12 @@ int ensure_workspace(cox_handle *h, int k)
     A(ws.lam, k);
     A(ws.active, k);
     A(ws.Fring, static_cast<size_t>(std::max(lag, 2)) * k);
+    if (h->q > 0) {
+        A(ws.gamma, static_cast<size_t>(k) * h->q);
+        A(ws.gz, static_cast<size_t>(k) * h->q);
+        A(ws.zvp, static_cast<size_t>(k) * h->q * nch);
+        cudaMemset(ws.gamma, 0, static_cast<size_t>(k) * h->q * sizeof(double));
+    }
     if (is_split(h)) {
         const int NP = limb_cols(k);
         A(ws.Bq, static_cast<size_t>(NP) * h->p_pad);
@@ -427,7 +449,8 @@ void cox_destroy(cox_h h)
     cudaDeviceSynchronize();
     free_workspace(h);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
-    void *ptrs[] = {h->d_head, h->d_tail, h->d_evhead, h->d_delta, h->d_mu, h->d_A1, h->d_A4, h->d_Xr, h->d_Xc, h->d_err};
+    void *ptrs[] = {h->d_head, h->d_tail, h->d_evhead, h->d_delta, h->d_mu, h->d_A1, h->d_A4, h->d_Xr, h->d_Xc, h->d_err,
+                    h->d_Z};
     for (void *p : ptrs) dfree(p);
     delete h;
 }
@@ -883,6 +906,66 @@ int cox_last_objective(cox_h h, double *obj_host, int k, void *stream)
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     COX_CUDA(cudaMemcpyAsync(obj_host, h->ws.F, k * sizeof(double), cudaMemcpyDeviceToHost, st));
     return check_device_error(h, st);
+}
+
+int cox_set_covariates(cox_h h, const double *Z_host, int q)
+{
+    if (!h || q < 0 || q > COX_MAX_COVARIATES || (q > 0 && !Z_host)) return COX_ERR_ARG;
+    const int64_t n = h->n;
+    for (int64_t i = 0; i < n * q; ++i)
+        if (!std::isfinite(Z_host[i])) return COX_ERR_ARG;
+    DeviceGuard g(h->dev);
+    cudaDeviceSynchronize();
+    free_workspace(h);  // gamma and its partials follow q
+    dfree(h->d_Z);
+    h->d_Z = nullptr;
+    h->q = 0;
+    if (q == 0) return COX_OK;
+    std::vector<double> zs(static_cast<size_t>(q) * n);  // q x n in the sorted order
+    for (int64_t r = 0; r < n; ++r)
+        for (int c = 0; c < q; ++c) zs[static_cast<size_t>(c) * n + r] = Z_host[h->h_order[r] * q + c];
+    COX_TRY(dmalloc(h, reinterpret_cast<void **>(&h->d_Z), zs.size() * sizeof(double)));
+    COX_CUDA(cudaMemcpy(h->d_Z, zs.data(), zs.size() * sizeof(double), cudaMemcpyHostToDevice));
+    h->q = q;
+    return COX_OK;
+}
+
+int cox_get_gamma(cox_h h, double *gamma_host, int k)
+{
+    if (!h || !gamma_host || k < 1) return COX_ERR_ARG;
+    if (h->q == 0) return COX_OK;
+    if (k != h->ws.k) return COX_ERR_ARG;
+    DeviceGuard g(h->dev);
+    COX_CUDA(cudaDeviceSynchronize());
+    COX_CUDA(cudaMemcpy(gamma_host, h->ws.gamma, static_cast<size_t>(k) * h->q * sizeof(double),
+                        cudaMemcpyDeviceToHost));
+    return COX_OK;
+}
+
+int cox_set_gamma(cox_h h, const double *gamma_host, int k)
+{
+    if (!h || k < 1) return COX_ERR_ARG;
+    if (h->q == 0) return COX_OK;
+    COX_TRY(validate_k(h, k));
+    DeviceGuard g(h->dev);
+    COX_TRY(ensure_workspace(h, k));
+    const size_t bytes = static_cast<size_t>(k) * h->q * sizeof(double);
+    if (gamma_host) COX_CUDA(cudaMemcpy(h->ws.gamma, gamma_host, bytes, cudaMemcpyHostToDevice));
+    else COX_CUDA(cudaMemset(h->ws.gamma, 0, bytes));
+    return COX_OK;
+}
+
+int cox_grad_gamma(cox_h h, double *gz_host, int k)
+{
+    if (!h || !gz_host || k < 1) return COX_ERR_ARG;
+    if (h->q == 0) return COX_OK;
+    if (k != h->ws.k) return COX_ERR_ARG;
+    DeviceGuard g(h->dev);
+    COX_CUDA(cudaDeviceSynchronize());
+    std::vector<double> gz(static_cast<size_t>(k) * h->q);
+    COX_CUDA(cudaMemcpy(gz.data(), h->ws.gz, gz.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < gz.size(); ++i) gz_host[i] = -gz[i];  // grad f = -Z^T (delta - u) / n
+    return COX_OK;
 }
 
 int cox_lambda_max(cox_h h, double *lmax_out)

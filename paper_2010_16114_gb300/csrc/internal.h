@@ -165,6 +165,10 @@ struct Workspace {
     float *eta32 = nullptr;    // n
     float *G32 = nullptr;      // p
     float *gpart = nullptr;    // partials of the FP32 baseline's product
+    // unpenalised covariates (q > 0)
+    double *gamma = nullptr;   // k x q coefficients (column kk at kk q)
+    double *gz = nullptr;      // k x q: Z^T (delta - u) / n at the last evaluation
+    double *zvp = nullptr;     // k x q x chunks partials
     GemmPlan g1, g4;
     bool plans_ready = false;
 };
@@ -185,6 +189,8 @@ struct cox_handle {
     int32_t *d_head = nullptr, *d_tail = nullptr;
     int32_t *d_evhead = nullptr;  // first positions of the tie groups that hold an event
     int64_t n_evhead = 0;
+    int q = 0;                    // unpenalised covariates
+    double *d_Z = nullptr;        // q x n, sorted order
     uint8_t *d_delta = nullptr;
     double *d_mu = nullptr;
     uint32_t *d_A1 = nullptr;  // subject-major 2-bit tiles
@@ -202,6 +208,7 @@ struct cox_handle {
     std::vector<int> st_iters;
     std::vector<double> st_F;
     std::vector<int> st_active;
+    std::vector<double> st_gamma;  // q x k
     int64_t st_step = 0;
     // autotuned pipeline shapes per k: row tiles, K chunks, stages of each product
     struct TuneChoice {
@@ -264,6 +271,13 @@ struct ScanArgs {
     const double *lam;    // k (objective); may be null
     bool need_loss;
     bool eta_only = false;  // stop after eta (cox_eta)
+    // unpenalised covariates (the handle's q > 0): gamma (k x q, read for eta,
+    // updated when gamma_step), gz (k x q out: Z^T (delta - u) / n), active (k)
+    double *gamma = nullptr;
+    double *gz = nullptr;
+    const int *active = nullptr;
+    double step = 0.0;
+    bool gamma_step = false;
 };
 int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st);
 

@@ -226,47 +226,21 @@ int cox_lipschitz(cox_h h, const double *start_host, double tol, int maxiter, do
     return power_method<float>(h, start_host, tol, maxiter, L_out);
 }
 
-int cox_path_fit(cox_h h, const double *lambdas, int k, int max_iter, double tol, double step, int warm,
-                 void *beta_dev, int *iters_host, double *obj_host, void *stream)
+} // extern "C"
+
+namespace coxgb {
+namespace {
+
+// The Section 6 stopping-rule loop for k columns on the handle's device
+// buffers (lambdas and active flags already set): CUDA-graph replays of `lag`
+// iterations, the host reading the k objectives after each replay; a column
+// stops when |F_t - F_{t-lag}| / |F_t + 1| < tol and is frozen.  iters,
+// active, hist and t carry the state in and out (resume).
+int path_run(cox_handle *h, int k, int max_iter, double tol, double step, void *beta_dev, std::vector<int> &iters,
+             std::vector<int> &active, std::vector<std::vector<double>> &hist, int64_t &t)
 {
-    if (!h || !beta_dev || !lambdas || max_iter < 0 || !(tol >= 0.0) || !(step > 0.0) || warm < 0 || warm > 2)
-        return COX_ERR_ARG;
-    if (k < 1 || (h->opt.precision == COX_SPLIT_E4M3 && k > MAX_K_TC)) return COX_ERR_ARG;
-    DeviceGuard g(h->dev);
-    cudaStream_t user = static_cast<cudaStream_t>(stream);
-    const int lag = h->opt.lag;
-    const size_t es = h->opt.precision == COX_FP64 ? 8 : 4;
-    const size_t bbytes = static_cast<size_t>(k) * h->p * es;
-    COX_TRY(ensure_workspace(h, k));
     Workspace &ws = h->ws;
-    for (int c = 0; c < k; ++c)
-        if (!(lambdas[c] >= 0.0)) return COX_ERR_ARG;
-    COX_CUDA(cudaMemcpy(ws.lam, lambdas, k * sizeof(double), cudaMemcpyHostToDevice));
-
-    // host-side state: iterations, active flags, objective history
-    std::vector<int> iters(static_cast<size_t>(k), 0), active(static_cast<size_t>(k), 1);
-    std::vector<std::vector<double>> hist(static_cast<size_t>(k));
-    int64_t t = 0;
-    COX_CUDA(cudaStreamSynchronize(user));
-    if (warm == 2) {
-        if (h->st_k != k) return COX_ERR_STATE;
-        const void *src = es == 8 ? static_cast<const void *>(h->st_beta64.data()) : static_cast<const void *>(h->st_beta32.data());
-        COX_CUDA(cudaMemcpy(beta_dev, src, bbytes, cudaMemcpyHostToDevice));
-        iters = h->st_iters;
-        active = h->st_active;
-        t = h->st_step;
-        hist.assign(static_cast<size_t>(k), {});
-        size_t off = 0;
-        for (int c = 0; c < k; ++c) {
-            const size_t len = static_cast<size_t>(h->st_F[off]);
-            hist[c].assign(h->st_F.begin() + off + 1, h->st_F.begin() + off + 1 + len);
-            off += 1 + len;
-        }
-    } else if (warm == 0) {
-        COX_CUDA(cudaMemset(beta_dev, 0, bbytes));
-    }
-    COX_CUDA(cudaMemcpy(ws.active, active.data(), k * sizeof(int), cudaMemcpyHostToDevice));
-
+    const int lag = h->opt.lag;
     cudaStream_t cs = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -279,6 +253,7 @@ int cox_path_fit(cox_h h, const double *lambdas, int k, int max_iter, double tol
             return COX_ERR_CUDA;
         return COX_OK;
     };
+    if (cudaMemcpy(ws.active, active.data(), k * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return COX_ERR_CUDA;
     do {
         if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) { rc = COX_ERR_CUDA; break; }
         if (max_iter - t >= lag) {
@@ -342,6 +317,62 @@ int cox_path_fit(cox_h h, const double *lambdas, int k, int max_iter, double tol
     // restore: later single steps treat every column as active
     std::vector<int> ones(static_cast<size_t>(k), 1);
     cudaMemcpy(ws.active, ones.data(), k * sizeof(int), cudaMemcpyHostToDevice);
+    return rc;
+}
+
+int check_lambdas(const double *lambdas, int k)
+{
+    for (int c = 0; c < k; ++c)
+        if (!(lambdas[c] >= 0.0) || !std::isfinite(lambdas[c])) return COX_ERR_ARG;
+    return COX_OK;
+}
+
+} // namespace
+} // namespace coxgb
+
+extern "C" {
+
+int cox_path_fit(cox_h h, const double *lambdas, int k, int max_iter, double tol, double step, int warm,
+                 void *beta_dev, int *iters_host, double *obj_host, void *stream)
+{
+    if (!h || !beta_dev || !lambdas || max_iter < 0 || !(tol >= 0.0) || !(step > 0.0) || warm < 0 || warm > 2)
+        return COX_ERR_ARG;
+    if (k < 1 || (h->opt.precision == COX_SPLIT_E4M3 && k > MAX_K_TC)) return COX_ERR_ARG;
+    COX_TRY(check_lambdas(lambdas, k));
+    DeviceGuard g(h->dev);
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    const size_t es = h->opt.precision == COX_FP64 ? 8 : 4;
+    const size_t bbytes = static_cast<size_t>(k) * h->p * es;
+    const size_t gbytes = static_cast<size_t>(k) * h->q * sizeof(double);
+    COX_TRY(ensure_workspace(h, k));
+    Workspace &ws = h->ws;
+    COX_CUDA(cudaMemcpy(ws.lam, lambdas, k * sizeof(double), cudaMemcpyHostToDevice));
+
+    // host-side state: iterations, active flags, objective history
+    std::vector<int> iters(static_cast<size_t>(k), 0), active(static_cast<size_t>(k), 1);
+    std::vector<std::vector<double>> hist(static_cast<size_t>(k));
+    int64_t t = 0;
+    COX_CUDA(cudaStreamSynchronize(user));
+    if (warm == 2) {
+        if (h->st_k != k || h->st_gamma.size() != static_cast<size_t>(k) * h->q) return COX_ERR_STATE;
+        const void *src = es == 8 ? static_cast<const void *>(h->st_beta64.data()) : static_cast<const void *>(h->st_beta32.data());
+        COX_CUDA(cudaMemcpy(beta_dev, src, bbytes, cudaMemcpyHostToDevice));
+        if (gbytes) COX_CUDA(cudaMemcpy(ws.gamma, h->st_gamma.data(), gbytes, cudaMemcpyHostToDevice));
+        iters = h->st_iters;
+        active = h->st_active;
+        t = h->st_step;
+        hist.assign(static_cast<size_t>(k), {});
+        size_t off = 0;
+        for (int c = 0; c < k; ++c) {
+            const size_t len = static_cast<size_t>(h->st_F[off]);
+            hist[c].assign(h->st_F.begin() + off + 1, h->st_F.begin() + off + 1 + len);
+            off += 1 + len;
+        }
+    } else if (warm == 0) {
+        COX_CUDA(cudaMemset(beta_dev, 0, bbytes));
+        if (gbytes) COX_CUDA(cudaMemset(ws.gamma, 0, gbytes));
+    }
+    const int rc = path_run(h, k, max_iter, tol, step, beta_dev, iters, active, hist, t);
     if (rc != COX_OK) return rc;
 
     // checkpoint state
@@ -354,6 +385,8 @@ int cox_path_fit(cox_h h, const double *lambdas, int k, int max_iter, double tol
         h->st_F.push_back(static_cast<double>(hist[c].size()));
         h->st_F.insert(h->st_F.end(), hist[c].begin(), hist[c].end());
     }
+    h->st_gamma.resize(static_cast<size_t>(k) * h->q);
+    if (gbytes) COX_CUDA(cudaMemcpy(h->st_gamma.data(), ws.gamma, gbytes, cudaMemcpyDeviceToHost));
     if (es == 8) {
         h->st_beta64.resize(static_cast<size_t>(k) * h->p);
         COX_CUDA(cudaMemcpy(h->st_beta64.data(), beta_dev, bbytes, cudaMemcpyDeviceToHost));
@@ -370,6 +403,43 @@ int cox_path_fit(cox_h h, const double *lambdas, int k, int max_iter, double tol
     return all_conv ? COX_OK : COX_ERR_NOT_CONVERGED;
 }
 
+int cox_path_seq(cox_h h, const double *lambdas, int L, int max_iter, double tol, double step, int warm,
+                 void *B_dev, double *G_host, int *iters_host, double *obj_host, void *stream)
+{
+    if (!h || !B_dev || !lambdas || L < 1 || max_iter < 0 || !(tol >= 0.0) || !(step > 0.0) || warm < 0 || warm > 1)
+        return COX_ERR_ARG;
+    COX_TRY(check_lambdas(lambdas, L));
+    DeviceGuard g(h->dev);
+    COX_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    const size_t es = h->opt.precision == COX_FP64 ? 8 : 4;
+    const size_t cb = static_cast<size_t>(h->p) * es;
+    COX_TRY(ensure_workspace(h, 1));
+    Workspace &ws = h->ws;
+    const size_t gbytes = static_cast<size_t>(h->q) * sizeof(double);
+    if (gbytes) COX_CUDA(cudaMemset(ws.gamma, 0, gbytes));
+    bool all_conv = true;
+    for (int l = 0; l < L; ++l) {
+        uint8_t *col = static_cast<uint8_t *>(B_dev) + static_cast<size_t>(l) * cb;
+        if (warm && l > 0) {
+            COX_CUDA(cudaMemcpy(col, col - cb, cb, cudaMemcpyDeviceToDevice));  // gamma stays: it carries over too
+        } else {
+            COX_CUDA(cudaMemset(col, 0, cb));
+            if (gbytes) COX_CUDA(cudaMemset(ws.gamma, 0, gbytes));
+        }
+        COX_CUDA(cudaMemcpy(ws.lam, lambdas + l, sizeof(double), cudaMemcpyHostToDevice));
+        std::vector<int> iters(1, 0), active(1, 1);
+        std::vector<std::vector<double>> hist(1);
+        int64_t t = 0;
+        COX_TRY(path_run(h, 1, max_iter, tol, step, col, iters, active, hist, t));
+        if (iters_host) iters_host[l] = iters[0];
+        if (obj_host) obj_host[l] = hist[0].empty() ? NAN : hist[0].back();
+        if (G_host && gbytes) COX_CUDA(cudaMemcpy(G_host + static_cast<size_t>(l) * h->q, ws.gamma, gbytes,
+                                                  cudaMemcpyDeviceToHost));
+        if (active[0]) all_conv = false;
+    }
+    return all_conv ? COX_OK : COX_ERR_NOT_CONVERGED;
+}
+
 int cox_get_state(cox_h h, void *buf, size_t *size)
 {
     if (!h || !size) return COX_ERR_ARG;
@@ -377,13 +447,15 @@ int cox_get_state(cox_h h, void *buf, size_t *size)
     if (k == 0) return COX_ERR_STATE;
     const bool f64 = h->opt.precision == COX_FP64;
     const size_t nb = static_cast<size_t>(k) * h->p * (f64 ? 8 : 4);
-    const size_t need = 8 * sizeof(int64_t) + nb + 2 * k * sizeof(int) + h->st_F.size() * sizeof(double);
+    const size_t ng = h->st_gamma.size() * sizeof(double);  // q x k unpenalised coefficients
+    const size_t need = 8 * sizeof(int64_t) + nb + 2 * k * sizeof(int) + h->st_F.size() * sizeof(double) +
+                        sizeof(int64_t) + ng;
     if (!buf) {
         *size = need;
         return COX_OK;
     }
     if (*size < need) return COX_ERR_ARG;
-    int64_t hdr[8] = {0x434F5853 /* "COXS" */, 1, h->n, h->p, k, h->opt.precision, h->st_step,
+    int64_t hdr[8] = {0x434F5853 /* "COXS" */, 2, h->n, h->p, k, h->opt.precision, h->st_step,
                       static_cast<int64_t>(h->st_F.size())};
     uint8_t *o = static_cast<uint8_t *>(buf);
     std::memcpy(o, hdr, sizeof(hdr));
@@ -395,6 +467,11 @@ int cox_get_state(cox_h h, void *buf, size_t *size)
     std::memcpy(o, h->st_active.data(), k * sizeof(int));
     o += k * sizeof(int);
     std::memcpy(o, h->st_F.data(), h->st_F.size() * sizeof(double));
+    o += h->st_F.size() * sizeof(double);
+    const int64_t q = static_cast<int64_t>(h->st_gamma.size() / static_cast<size_t>(k));
+    std::memcpy(o, &q, sizeof(q));
+    o += sizeof(q);
+    if (ng) std::memcpy(o, h->st_gamma.data(), ng);
     *size = need;
     return COX_OK;
 }
@@ -404,14 +481,18 @@ int cox_set_state(cox_h h, const void *buf, size_t size)
     if (!h || !buf || size < 8 * sizeof(int64_t)) return COX_ERR_ARG;
     int64_t hdr[8];
     std::memcpy(hdr, buf, sizeof(hdr));
-    if (hdr[0] != 0x434F5853 || hdr[1] != 1 || hdr[2] != h->n || hdr[3] != h->p || hdr[5] != h->opt.precision)
+    if (hdr[0] != 0x434F5853 || hdr[1] != 2 || hdr[2] != h->n || hdr[3] != h->p || hdr[5] != h->opt.precision)
         return COX_ERR_STATE;
     const int k = static_cast<int>(hdr[4]);
     if (k < 1) return COX_ERR_STATE;
     const bool f64 = h->opt.precision == COX_FP64;
     const size_t nb = static_cast<size_t>(k) * h->p * (f64 ? 8 : 4);
     const size_t nF = static_cast<size_t>(hdr[7]);
-    if (size < 8 * sizeof(int64_t) + nb + 2 * k * sizeof(int) + nF * sizeof(double)) return COX_ERR_STATE;
+    const size_t base = 8 * sizeof(int64_t) + nb + 2 * k * sizeof(int) + nF * sizeof(double);
+    if (size < base + sizeof(int64_t)) return COX_ERR_STATE;
+    int64_t q = 0;
+    std::memcpy(&q, static_cast<const uint8_t *>(buf) + base, sizeof(q));
+    if (q != h->q || size < base + sizeof(int64_t) + static_cast<size_t>(q) * k * sizeof(double)) return COX_ERR_STATE;
     const uint8_t *in = static_cast<const uint8_t *>(buf) + sizeof(hdr);
     h->st_k = k;
     h->st_step = hdr[6];
@@ -431,6 +512,9 @@ int cox_set_state(cox_h h, const void *buf, size_t size)
     in += k * sizeof(int);
     h->st_F.resize(nF);
     std::memcpy(h->st_F.data(), in, nF * sizeof(double));
+    in += nF * sizeof(double) + sizeof(int64_t);
+    h->st_gamma.resize(static_cast<size_t>(q) * k);
+    if (q) std::memcpy(h->st_gamma.data(), in, h->st_gamma.size() * sizeof(double));
     return COX_OK;
 }
 

@@ -97,7 +97,14 @@ struct SP {
     const int32_t *evhead;  // first positions of the tie groups that hold an event
     int64_t n_evh;
     double *eta, *w, *Rt, *Ft, *cmax, *csw, *csd, *suf, *pre, *lossp, *vsp;
+    // unpenalised covariates (q columns; q = 0: none): Z q x n in sorted order,
+    // gamma k x q, per-chunk partials of Z^T V (k x q x chunks)
+    int q;
+    const double *Z, *gamma;
+    double *zvp;
 };
+
+constexpr int MAXQ = 16;
 
 // (1) eta = sum of the product's partial slots (or a dense copy); chunk maxima.
 template <int SRC>
@@ -130,6 +137,11 @@ __global__ void k_eta(SP s, const void *src, int64_t slot_stride, int64_t col_st
             v = static_cast<double>(static_cast<const float *>(src)[kk * col_stride + i]);
         } else {
             v = static_cast<const double *>(src)[kk * col_stride + i];
+        }
+        if (s.q) {  // eta += Z gamma (Section 6 unpenalised covariates), in FP64
+            double zg = 0.0;
+            for (int cq = 0; cq < s.q; ++cq) zg += s.Z[cq * s.n + i] * s.gamma[kk * s.q + cq];
+            v += zg;
         }
         s.eta[kk * s.n + i] = v;
         mx = fmax(mx, v);
@@ -312,6 +324,9 @@ __global__ void k_uv(SP s, void *Vout, int64_t n_pad, double *vmaxp)
     const int64_t i0 = static_cast<int64_t>(c) * SCAN_CH;
     double vs = 0.0;
     float vm32 = 0.f;
+    double zv[MAXQ];  // Z^T V over this thread's subjects (unpenalised covariates)
+#pragma unroll
+    for (int cq = 0; cq < MAXQ; ++cq) zv[cq] = 0.0;
     for (int e = threadIdx.x; e < SCAN_CH; e += NT) {
         const int64_t i = i0 + e;
         if (i >= s.n) break;
@@ -319,6 +334,11 @@ __global__ void k_uv(SP s, void *Vout, int64_t n_pad, double *vmaxp)
         const double C = s.Ft[kk * s.n + tl] + s.pre[kk * s.nch + tl / SCAN_CH];
         const double u = s.w[kk * s.n + i] * C;
         const double V = static_cast<double>(s.delta[i]) - u;
+        if (s.q) {
+#pragma unroll
+            for (int cq = 0; cq < MAXQ; ++cq)
+                if (cq < s.q) zv[cq] += s.Z[cq * s.n + i] * V;
+        }
         // sum V in the form the product reads: X^T V - mu sum V is then
         // exactly the centred product of that V.  (Censored subjects between
         // two event times share one V, so their rounding errors do not
@@ -344,6 +364,14 @@ __global__ void k_uv(SP s, void *Vout, int64_t n_pad, double *vmaxp)
     } else {
         const double t = block_sum(vs, sh);
         if (threadIdx.x == 0) s.vsp[kk * s.nch + c] = t;
+    }
+    for (int cq = 0; cq < s.q; ++cq) {  // block-uniform trip count
+        double zc = 0.0;
+#pragma unroll
+        for (int q2 = 0; q2 < MAXQ; ++q2)
+            if (q2 == cq) zc = zv[q2];
+        const double t = block_sum(zc, sh);
+        if (threadIdx.x == 0) s.zvp[(static_cast<int64_t>(kk) * s.q + cq) * s.nch + c] = t;
     }
 }
 
@@ -402,10 +430,24 @@ __device__ __forceinline__ double warp_sum(double x)
     return x;
 }
 
+// With unpenalised covariates also g_Z = Z^T (delta - u) / n per column, and,
+// for a step, gamma <- gamma + step g_Z (Section 6: the covariates take a plain
+// gradient step; a frozen column keeps its gamma).
 __global__ void k_finalize(SP s, int l1_blocks, const double *l1p, const double *lam, double *sumV,
-                           double *f, double *l1, double *Fobj, bool need_loss, int *err)
+                           double *f, double *l1, double *Fobj, bool need_loss, int *err, double *gz,
+                           double *gamma, const int *active, double step, bool gamma_step)
 {
     const int kk = blockIdx.x, lane = threadIdx.x;
+    for (int cq = 0; cq < s.q; ++cq) {
+        double z = 0.0;
+        for (int c = lane; c < s.nch; c += 32) z += s.zvp[(static_cast<int64_t>(kk) * s.q + cq) * s.nch + c];
+        z = warp_sum(z) / static_cast<double>(s.n);
+        if (lane == 0) {
+            gz[kk * s.q + cq] = z;
+            if (gamma_step && (!active || active[kk])) gamma[kk * s.q + cq] += step * z;
+            if (!isfinite(z)) atomicOr(err, DEVERR_NONFINITE);
+        }
+    }
     double v = 0.0, lo = 0.0, b1 = 0.0;
     for (int c = lane; c < s.nch; c += 32) v += s.vsp[kk * s.nch + c];
     v = warp_sum(v);
@@ -444,6 +486,10 @@ int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st)
     s.tail = h->d_tail;
     s.evhead = h->d_evhead;
     s.n_evh = h->n_evhead;
+    s.q = a.gamma ? h->q : 0;  // no gamma: X_c beta alone (cox_eta)
+    s.Z = h->d_Z;
+    s.gamma = a.gamma;
+    s.zvp = ws.zvp;
     s.eta = ws.eta;
     s.w = ws.w;
     s.Rt = ws.Rt;
@@ -489,7 +535,7 @@ int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st)
     default: k_uv<V_DENSE_F32><<<grid, NT, 0, st>>>(s, a.V, h->n_pad, nullptr); break;
     }
     k_finalize<<<a.k, 32, 0, st>>>(s, h->l1_blocks, a.need_loss ? ws.l1p : nullptr, a.lam, ws.sumV, ws.f, ws.l1,
-                                 ws.F, a.need_loss, h->d_err);
+                                 ws.F, a.need_loss, h->d_err, a.gz, a.gamma, a.active, a.step, a.gamma_step);
     COX_CUDA(cudaGetLastError());
     return COX_OK;
 }
