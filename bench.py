@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--tile-m", type=int, default=0)
     ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--chunks", type=int, default=0)
+    ap.add_argument("--window", type=int, default=0,
+                    help="K chunks per TMEM accumulation window (0: the library default, 256)")
     ap.add_argument("--issue", type=int, default=0,
                     help="MMA issue mode of the products: 1 one issuer per row tile, 2 two on alternate stages")
     ap.add_argument("--no-autotune", action="store_true",
@@ -301,7 +303,7 @@ def run_ours(args, rank, world):
     w.packed_rows_device(packed.data_ptr(), stream.cuda_stream, thr.data_ptr())
     torch.cuda.synchronize()
     prob = CoxProblem(packed, w.y, w.delta, p=p, precision="split_e4m3", tile_m=args.tile_m, stages=args.stages,
-                      chunks=args.chunks, issue=args.issue)
+                      chunks=args.chunks, issue=args.issue, window=args.window)
     del packed, thr
     torch.cuda.empty_cache()
     lmax = prob.lambda_max()

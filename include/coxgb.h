@@ -98,7 +98,9 @@ typedef struct cox_options {
                              warp per row tile, every stage (4 chunks MMAs per
                              commit); 2 = two issuer warps on alternate stages,
                              each issuing every row tile of its stage (4 chunks
-                             tile_m MMAs per commit); 0 = automatic, as tile_m     */
+                             tile_m MMAs per commit); 3 = as 1, each issuer
+                             committing after every second stage (8 chunks MMAs
+                             per pair of commits); 0 = automatic, as tile_m      */
 } cox_options;
 
 /* Fill *opt with the defaults above. */
@@ -202,6 +204,27 @@ int cox_prox_step(cox_h h, void *beta_dev, const double *lambdas, int k, double 
  * call); synchronous.  The end-to-end form of one iteration. */
 int cox_prox_step_host(cox_h h, void *beta_host, const double *lambdas, int k, double step,
                        void *stream);
+
+/*
+ * One iteration of a column shard (Section 5.3 with X split by SNP columns
+ * over devices, as the paper's distributed matrices split it): given the
+ * linear predictor summed over all shards, eta = sum_g (X_g)_c B_g (each
+ * shard's part from cox_eta, added by the caller, e.g. by an all-reduce),
+ * run the risk-set scans (every shard computes the same ones) and this
+ * handle's X_g^T V with the soft-threshold step on its coefficients.
+ *   beta_dev: p_g x k in/out (device; this shard's columns).
+ *   eta_dev : k x n doubles (device), sorted order as cox_eta writes it.
+ * With covariates set (the same Z on every shard) the handle adds Z gamma and
+ * steps gamma, identically on every shard.  F of the entering iterate needs
+ * ||beta||_1 over all shards: cox_last_loss_l1 gives this shard's part.
+ * Asynchronous.  Errors: COX_ERR_UNSUPPORTED for COX_FP32_GEMV handles.
+ */
+int cox_prox_step_eta(cox_h h, void *beta_dev, const double *eta_dev, const double *lambdas, int k,
+                      double step, void *stream);
+/* f (the loss, k doubles) and this handle's ||beta||_1 (k doubles) at the
+ * iterate that entered the last step or evaluation; either may be NULL.
+ * Synchronous. */
+int cox_last_loss_l1(cox_h h, double *f_host, double *l1_host, int k, void *stream);
 
 /* Wait for `stream` and report any device-side error of earlier calls. */
 int cox_sync(cox_h h, void *stream);
@@ -328,7 +351,8 @@ typedef struct cox_plan {
     int limb_cols;        /* e4m3 limb columns: N of every MMA                     */
     int tmem_cols;        /* accumulators + slots, of the 512 an SM has            */
     long long smem_bytes; /* dynamic shared memory per CTA                         */
-    int issue;            /* 1 one issuer per row tile, 2 two on alternate stages  */
+    int issue;            /* 1 one issuer per row tile, 2 two on alternate stages,
+                             3 one per row tile committing every second stage      */
     int issuers;          /* MMA issuer warps                                      */
     int mmas_per_commit;  /* tcgen05.mma instructions per issuer commit            */
 } cox_plan;

@@ -37,7 +37,7 @@ EXPORTS = [
     "cox_path_fit", "cox_get_state", "cox_set_state", "cox_get_info", "cox_get_mu_order",
     "cox_strerror", "cox_set_precision", "cox_profile", "cox_profile_read", "cox_lipschitz_noalloc",
     "cox_autotune", "cox_eta", "cox_plan_shape", "cox_rank_by_entry", "cox_path_seq", "cox_set_covariates",
-    "cox_get_gamma", "cox_set_gamma", "cox_grad_gamma",
+    "cox_get_gamma", "cox_set_gamma", "cox_grad_gamma", "cox_prox_step_eta", "cox_last_loss_l1",
 ]
 COX_MAX_COVARIATES = 16
 
@@ -137,6 +137,10 @@ def load(path: str | None = None):
     lib.cox_rank_by_entry.argtypes = [I64, I, P, P, I, P, P, ctypes.POINTER(I64)]
     lib.cox_path_seq.restype = I
     lib.cox_path_seq.argtypes = [P, P, I, I, D, D, I, P, P, P, P, P]
+    lib.cox_prox_step_eta.restype = I
+    lib.cox_prox_step_eta.argtypes = [P, P, P, P, I, D, P]
+    lib.cox_last_loss_l1.restype = I
+    lib.cox_last_loss_l1.argtypes = [P, P, P, I, P]
     lib.cox_set_covariates.restype = I
     lib.cox_set_covariates.argtypes = [P, P, I]
     for nm in ("cox_get_gamma", "cox_set_gamma", "cox_grad_gamma"):
@@ -293,3 +297,11 @@ def cox_set_gamma(h, in_ptr, k: int) -> int:
 
 def cox_grad_gamma(h, out_ptr, k: int) -> int:
     return load().cox_grad_gamma(h, out_ptr, k)
+
+
+def cox_prox_step_eta(h, beta_ptr, eta_ptr, lam_ptr, k, step, stream_ptr):
+    return load().cox_prox_step_eta(h, beta_ptr, eta_ptr, lam_ptr, k, step, stream_ptr)
+
+
+def cox_last_loss_l1(h, f_ptr, l1_ptr, k, stream_ptr):
+    return load().cox_last_loss_l1(h, f_ptr, l1_ptr, k, stream_ptr)

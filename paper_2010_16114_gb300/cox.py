@@ -226,6 +226,25 @@ class CoxProblem:
         L.check(rc, "cox_prox_step")
         return beta
 
+    def prox_step_eta(self, beta: torch.Tensor, eta: torch.Tensor, lambdas, step: float, stream=None):
+        """One iteration of a column shard from the summed eta (k, n) float64 on
+        the device (cox_prox_step_eta), in place on this shard's beta."""
+        b = self._beta(beta)
+        k = b.shape[0]
+        if eta.dtype != torch.float64 or not eta.is_cuda or tuple(eta.shape) != (k, self.n) or not eta.is_contiguous():
+            raise ValueError(f"eta must be a contiguous float64 CUDA tensor of shape ({k}, {self.n})")
+        lam = np.ascontiguousarray(np.broadcast_to(np.asarray(lambdas, dtype=np.float64), (k,)))
+        L.check(L.cox_prox_step_eta(self.h, _vp(b), _vp(eta), _vp(lam), k, float(step), _stream_ptr(stream)),
+                "cox_prox_step_eta")
+        return beta
+
+    def last_loss_l1(self, k: int, stream=None):
+        """(f, ||beta||_1 of this handle's columns) at the iterate entering the last step."""
+        f = np.zeros(k)
+        l1 = np.zeros(k)
+        L.check(L.cox_last_loss_l1(self.h, _vp(f), _vp(l1), k, _stream_ptr(stream)), "cox_last_loss_l1")
+        return f, l1
+
     def prox_step_host(self, beta: np.ndarray, lambdas, step: float, stream=None):
         """One iteration on a host array (k, p), copied in and out."""
         k = beta.shape[0] if beta.ndim == 2 else 1

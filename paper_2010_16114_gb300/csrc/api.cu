@@ -285,6 +285,75 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
     return COX_OK;
 }
 
+// One iteration of a column shard from the linear predictor summed over all
+// shards (Section 5.3 with X split by columns): eta (k x n doubles, sorted
+// order, X part only; the handle adds Z gamma when covariates are set), the
+// replicated risk-set scans, then this shard's X_g^T V and the soft-threshold
+// step on its coefficients.
+int iterate_from_eta(cox_handle *h, void *beta, const double *eta, int k, double step, cudaStream_t st)
+{
+    Workspace &ws = h->ws;
+    ScanArgs sa;
+    sa.k = k;
+    sa.eta_src = ETA_DENSE_F64;
+    sa.eta = eta;
+    sa.slot_stride = 0;
+    sa.col_stride = h->n;
+    sa.group_rows = 1;
+    sa.KC = 1;
+    sa.L = 1;
+    sa.lam = ws.lam;
+    sa.need_loss = true;
+    set_covariate_args(h, sa, 0, EPI_PROX, step);
+    if (is_split(h)) {
+        float *b32 = static_cast<float *>(beta);
+        {
+            Site s_(h, 3, 1, st);
+            COX_TRY(l1_norms32(h, b32, k, st));
+        }
+        sa.v_out = V_LIMBS_E4M3;
+        sa.V = ws.Vq;
+        sa.NP = ws.g4.NP;
+        sa.exp64 = false;
+        {
+            Site s_(h, 2, 8, st);
+            COX_TRY(run_scans(h, sa, st));
+        }
+        EpiArgs e4;
+        e4.epi = EPI_PROX;
+        e4.part = ws.part4;
+        e4.counters = ws.cnt4;
+        e4.beta = b32;
+        e4.lam = ws.lam;
+        e4.step = step;
+        e4.mu = h->d_mu;
+        e4.sumV = ws.sumV;
+        e4.active = ws.active;
+        e4.bscale = ws.bs4;
+        e4.rows_valid = h->p;
+        e4.inv_n = 1.0 / static_cast<double>(h->n);
+        Site s_(h, 1, 1, st);
+        return launch_gemm(h, ws.g4, e4, k, st);
+    }
+    if (is_fp64(h)) {
+        double *b64 = static_cast<double *>(beta);
+        {
+            Site s_(h, 3, 1, st);
+            COX_TRY(l1_norms64(h, b64, k, st));
+        }
+        sa.v_out = V_DENSE_F64;
+        sa.V = ws.V64;
+        sa.exp64 = true;
+        {
+            Site s_(h, 2, 8, st);
+            COX_TRY(run_scans(h, sa, st));
+        }
+        Site s4_(h, 1, 1, st);
+        return xtv64(h, ws.V64, k, b64, nullptr, ws.lam, step, st);
+    }
+    return COX_ERR_UNSUPPORTED;
+}
+
 namespace {
 
 int validate_k(const cox_handle *h, int k)
@@ -470,7 +539,7 @@ int cox_setup(cox_h *out, const void *X, int64_t n, int64_t p, int x_format, con
     if (x_format < COX_X_INT8_HOST || x_format > COX_X_PACKED2_DEV) return COX_ERR_ARG;
     if (opt.lag < 1 || !(opt.wait_limit_s >= 0.0)) return COX_ERR_ARG;
     if (opt.tile_m < 0 || opt.tile_m > 2 || opt.chunks < 0 || opt.chunks > 2 || opt.stages < 0 || opt.window < 0 ||
-        opt.issue < 0 || opt.issue > 2)
+        opt.issue < 0 || opt.issue > 3)
         return COX_ERR_ARG;
     for (int64_t i = 0; i < n; ++i) {
         if (!std::isfinite(time[i])) return COX_ERR_ARG;
@@ -593,8 +662,8 @@ int cox_get_info(cox_h h, cox_info *info)
     info->launches = h->launches;
     info->chunks = h->ws.k ? h->ws.g1.CH : h->opt.chunks;
     info->ring = h->ws.k ? h->ws.g1.ring : 0;
-    info->issue = h->ws.k ? (h->ws.g1.alt ? 2 : 1) : h->opt.issue;
-    info->issue_xtv = h->ws.k ? (h->ws.g4.alt ? 2 : 1) : h->opt.issue;
+    info->issue = h->ws.k ? (h->ws.g1.alt ? 2 : h->ws.g1.pair ? 3 : 1) : h->opt.issue;
+    info->issue_xtv = h->ws.k ? (h->ws.g4.alt ? 2 : h->ws.g4.pair ? 3 : 1) : h->opt.issue;
     return COX_OK;
 }
 
@@ -628,7 +697,7 @@ int cox_autotune(cox_h h, int k, int reps, cox_tune_choice *xb, cox_tune_choice 
             int last_S = -1;
             for (int dq = 0; dq < 2 && rc == COX_OK; ++dq) {
                 GemmPlan g;
-                if (plan_gemm(h, g, A, rows, K, B, k, Ts[j], Cs[j], depth_req[dq], As[j] ? 2 : 1) != COX_OK) continue;
+                if (plan_gemm(h, g, A, rows, K, B, k, Ts[j], Cs[j], depth_req[dq], As[j]) != COX_OK) continue;
                 if (g.stages == last_S) continue;  // the two depths coincide
                 last_S = g.stages;
                 float *part = nullptr;
@@ -654,7 +723,7 @@ int cox_autotune(cox_h h, int k, int reps, cox_tune_choice *xb, cox_tune_choice 
                 if ((rc = check_device_error(h, 0)) != COX_OK) break;
                 ++cand[prod];
                 const double m = static_cast<double>(ms) / reps;
-                if (m < best[prod].ms) best[prod] = cox_tune_choice{g.T, g.CH, g.stages, 0, m, g.alt ? 2 : 1};
+                if (m < best[prod].ms) best[prod] = cox_tune_choice{g.T, g.CH, g.stages, 0, m, As[j]};
             }
         }
         best[prod].candidates = cand[prod];
@@ -709,7 +778,7 @@ int cox_rank_by_entry(int64_t p, int L, const double *lambdas, const void *B_hos
 
 int cox_plan_shape(int k, int tile_m, int chunks, int stages, int issue, cox_plan *out)
 {
-    if (!out || tile_m < 0 || chunks < 0 || stages < 0 || issue < 0 || issue > 2) return COX_ERR_ARG;
+    if (!out || tile_m < 0 || chunks < 0 || stages < 0 || issue < 0 || issue > 3) return COX_ERR_ARG;
     GemmPlan g;
     COX_TRY(plan_shape(g, k, tile_m, chunks, stages, issue));
     out->tile_m = g.T;
@@ -721,9 +790,9 @@ int cox_plan_shape(int k, int tile_m, int chunks, int stages, int issue, cox_pla
     out->limb_cols = g.NP;
     out->tmem_cols = (g.alt ? 2 : 1) * g.T * g.NP + g.ring * g.T * g.CH * 32;
     out->smem_bytes = static_cast<long long>(g.smem);
-    out->issue = g.alt ? 2 : 1;
+    out->issue = g.alt ? 2 : g.pair ? 3 : 1;
     out->issuers = g.alt ? 2 : g.T;
-    out->mmas_per_commit = 4 * g.CH * (g.alt ? g.T : 1);
+    out->mmas_per_commit = 4 * g.CH * (g.alt ? g.T : g.pair ? 2 : 1);
     return COX_OK;
 }
 
@@ -896,6 +965,29 @@ int cox_prox_step_host(cox_h h, void *beta_host, const double *lambdas, int k, d
     COX_TRY(set_lambdas(h, lambdas, k, st));
     COX_TRY(iterate(h, dbuf, k, EPI_PROX, nullptr, step, st));
     COX_CUDA(cudaMemcpyAsync(beta_host, dbuf, bytes, cudaMemcpyDeviceToHost, st));
+    return check_device_error(h, st);
+}
+
+int cox_prox_step_eta(cox_h h, void *beta_dev, const double *eta_dev, const double *lambdas, int k, double step,
+                      void *stream)
+{
+    if (!h || !beta_dev || !eta_dev || !(step > 0.0) || !std::isfinite(step)) return COX_ERR_ARG;
+    COX_TRY(validate_k(h, k));
+    if (h->opt.precision == COX_FP32_GEMV) return COX_ERR_UNSUPPORTED;
+    DeviceGuard g(h->dev);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    COX_TRY(ensure_workspace(h, k));
+    COX_TRY(set_lambdas(h, lambdas, k, st));
+    return iterate_from_eta(h, beta_dev, eta_dev, k, step, st);
+}
+
+int cox_last_loss_l1(cox_h h, double *f_host, double *l1_host, int k, void *stream)
+{
+    if (!h || k != h->ws.k) return COX_ERR_ARG;
+    DeviceGuard g(h->dev);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (f_host) COX_CUDA(cudaMemcpyAsync(f_host, h->ws.f, k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (l1_host) COX_CUDA(cudaMemcpyAsync(l1_host, h->ws.l1, k * sizeof(double), cudaMemcpyDeviceToHost, st));
     return check_device_error(h, st);
 }
 

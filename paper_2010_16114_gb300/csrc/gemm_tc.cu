@@ -61,6 +61,7 @@ namespace {
 
 struct KParams {
     int KC, F, k, stages, ring, nb_period;
+    int pair;           // per-tile issuers commit after every second stage of a window
     const int *bscale;  // k: power-of-two scale of the B limbs
     int64_t units, L;
     int64_t rows_pad, slot_stride;
@@ -369,6 +370,7 @@ __global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
                 }
                 eph ^= 1u;
             }
+            int pend = -1;  // pair mode: the slot of the stage whose commit waits for the next stage
             for (int e = 0; e < wl; ++e) {
                 __syncwarp();
                 named_sync(1 + bid, NB_COUNT);
@@ -380,7 +382,21 @@ __global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
                         const uint64_t bd = dstage + static_cast<uint64_t>(((q >> 2) * NP * 128 + (q & 3) * 32) >> 4);
                         mma_ts_f8(d, aslot + 8 * q, bd, idesc, (e == 0 && q == 0) ? 0u : 1u);
                     }
-                    mma_commit(aempty0 + 8 * r);
+                    // a commit arrives once all earlier MMAs of this thread are
+                    // complete: after every second stage one pair of commits
+                    // releases both stages' slots (each slot use still gets one
+                    // arrival per issuer, only later)
+                    if (!P.pair) {
+                        mma_commit(aempty0 + 8 * r);
+                    } else if (pend >= 0) {
+                        mma_commit(aempty0 + 8 * pend);
+                        mma_commit(aempty0 + 8 * r);
+                        pend = -1;
+                    } else if (e == wl - 1) {
+                        mma_commit(aempty0 + 8 * r);
+                    } else {
+                        pend = r;
+                    }
                 }
                 if (++s == S) {
                     s = 0;
@@ -855,17 +871,17 @@ int lcm_i(int a, int b) { return a / gcd_i(a, b) * b; }
 
 } // namespace
 
-int gemm_shapes(int k, int *T, int *CH, int *alt, int max)
+int gemm_shapes(int k, int *T, int *CH, int *issue, int max)
 {
     const int NP = limb_cols(k);
     int n = 0;
-    for (int a = 0; a <= 1; ++a)
+    for (int is = 1; is <= 3; ++is)
         for (int t = 2; t >= 1; --t)
             for (int c = 2; c >= 1; --c)
-                if (pick_kernel(t, c, NP, a) && n < max) {
+                if (pick_kernel(t, c, NP, is == 2) && n < max) {
                     T[n] = t;
                     CH[n] = c;
-                    alt[n] = a;
+                    issue[n] = is;
                     ++n;
                 }
     return n;
@@ -877,7 +893,7 @@ int gemm_shapes(int k, int *T, int *CH, int *alt, int max)
 int plan_shape(GemmPlan &g, int k, int T_req, int CH_req, int stages_req, int issue_req)
 {
     if (k < 1 || k > MAX_K_TC) return COX_ERR_ARG;
-    if (issue_req < 0 || issue_req > 2) return COX_ERR_ARG;
+    if (issue_req < 0 || issue_req > 3) return COX_ERR_ARG;
     const int np_cls = limb_cols(k);
     int T = 2, CH = 1, alt = 0;
     shape_for(np_cls, &T, &CH, &alt);
@@ -911,6 +927,7 @@ int plan_shape(GemmPlan &g, int k, int T_req, int CH_req, int stages_req, int is
     g.CH = CH;
     g.NP = np_cls;
     g.alt = alt;
+    g.pair = issue_req == 3;
     g.G = G;
     g.ring = ring;
     g.nb_period = lcm_i(G, ring);
@@ -995,6 +1012,7 @@ int launch_gemm(cox_handle *h, const GemmPlan &g, const EpiArgs &e, int k, cudaS
     kp.stages = g.stages;
     kp.ring = g.ring;
     kp.nb_period = g.nb_period;
+    kp.pair = g.pair;
     kp.bscale = e.bscale;
     kp.units = g.units;
     kp.L = g.L;

@@ -117,6 +117,7 @@ struct GemmPlan {
     int T = 2;         // 128-row tiles per CTA (one M group)
     int CH = 1;        // K chunks (128 each) per stage
     int alt = 0;       // 1: two issuers on alternate stages (else one per row tile)
+    int pair = 0;      // 1: per-tile issuers commit after every second stage
     int G = 3;         // decoder groups
     int NP = 16;       // limb columns (limb_cols(k))
     int stages = 6;    // shared-memory pipeline depth
@@ -252,6 +253,9 @@ int setup_dense64(cox_handle *h, const double *X, cudaStream_t st);
 // ---- workspace / plans / one iteration (api.cu) ----------------------------------
 int ensure_workspace(cox_handle *h, int k);
 int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, cudaStream_t st);
+int iterate_from_eta(cox_handle *h, void *beta, const double *eta, int k, double step, cudaStream_t st);
+struct ScanArgs;
+void set_covariate_args(cox_handle *h, ScanArgs &sa, int col, int epi, double step);
 
 // ---- scans (scans.cu) -------------------------------------------------------------
 // Risk-set scans on eta (sorted order, k columns).  eta_src kinds:
@@ -286,13 +290,14 @@ int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st);
 // The shape and depth arithmetic of a product plan (host only, no device):
 // T, CH, NP, stages, ring, nb_period and smem of g, or COX_ERR_ARG for a shape
 // not compiled for k or a depth the pipeline does not allow.
-// issue_req: 0 default, 1 one issuer per row tile, 2 two issuers on alternate stages.
+// issue_req: 0 default, 1 one issuer per row tile, 2 two issuers on alternate
+// stages, 3 one issuer per row tile committing after every second stage.
 int plan_shape(GemmPlan &g, int k, int T_req, int CH_req, int stages_req, int issue_req);
 int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, int64_t K_pad,
               const uint8_t *B, int k, int T_req, int CH_req, int stages_req, int issue_req);
-// The compiled (row tiles, K chunks, alternating issuers) shapes for k columns;
-// returns their count.
-int gemm_shapes(int k, int *T, int *CH, int *alt, int max);
+// The compiled (row tiles, K chunks, issue mode) shapes for k columns; returns
+// their count.
+int gemm_shapes(int k, int *T, int *CH, int *issue, int max);
 enum Epi { EPI_PARTIAL = 0, EPI_PROX = 1, EPI_GRAD = 2 };
 struct EpiArgs {
     int epi = EPI_PARTIAL;

@@ -23,7 +23,7 @@ import pytest
 
 from paper_2010_16114_gb300 import _lib as L
 
-SHAPES = [(t, c, a) for a in (1, 2) for t in (2, 1) for c in (2, 1)]
+SHAPES = [(t, c, a) for a in (1, 2, 3) for t in (2, 1) for c in (2, 1)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -52,9 +52,9 @@ def _check(k, p):
         assert p.issuers == 2 and p.mmas_per_commit == 4 * p.chunks * p.tile_m
         acc = 2 * p.tile_m * p.limb_cols
     else:
-        assert p.issue == 1
+        assert p.issue in (1, 3)
         assert _parity_safe(p.decoder_groups, p.ring, p.stages)
-        assert p.issuers == p.tile_m and p.mmas_per_commit == 4 * p.chunks
+        assert p.issuers == p.tile_m and p.mmas_per_commit == 4 * p.chunks * (2 if p.issue == 3 else 1)
         acc = p.tile_m * p.limb_cols
     assert p.tmem_cols == acc + p.ring * p.tile_m * p.chunks * 32 <= 512
     assert 120 * 1024 <= p.smem_bytes <= 227 * 1024
@@ -114,7 +114,7 @@ def test_rejections():
     assert L.load().cox_plan_shape(16, 0, 0, 0, 0, None) == L.COX_ERR_ARG
     assert L.cox_plan_shape(16, 2, 1, 0, 2)[0] == L.COX_ERR_ARG   # alternating issuers: not compiled for (2, 1)
     assert L.cox_plan_shape(16, 2, 2, 5, 2)[0] == L.COX_ERR_ARG   # alternating issuers need an even depth
-    assert L.cox_plan_shape(16, 0, 0, 0, 3)[0] == L.COX_ERR_ARG
+    assert L.cox_plan_shape(16, 0, 0, 0, 4)[0] == L.COX_ERR_ARG
 
 
 def test_front_end_wrapper():
