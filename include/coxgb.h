@@ -101,6 +101,13 @@ typedef struct cox_options {
                              tile_m MMAs per commit); 3 = as 1, each issuer
                              committing after every second stage (8 chunks MMAs
                              per pair of commits); 0 = automatic, as tile_m      */
+    int active_set;       /* 1: the X B product streams only the SNP columns where
+                             some coefficient is nonzero (a gathered copy of those
+                             columns, rebuilt when the support leaves it), or the
+                             dense copy when the support exceeds a quarter of the
+                             columns; each iteration then synchronises its stream
+                             once, and cox_path_fit runs plain launches instead
+                             of graph replays.  0 (default): always dense        */
 } cox_options;
 
 /* Fill *opt with the defaults above. */
@@ -307,6 +314,8 @@ typedef struct cox_info {
     int chunks, ring;     /* K chunks per stage and TMEM slots of the X B product  */
     int issue, issue_xtv; /* issue mode (cox_options.issue) of the X B and X^T V
                              products in use                                       */
+    int64_t active_cols;  /* active set: SNP columns in it (-1: off or not built)  */
+    int64_t active_rebuilds; /* times the active set was rebuilt                    */
 } cox_info;
 int cox_get_info(cox_h h, cox_info *info);
 
@@ -374,6 +383,10 @@ int cox_plan_shape(int k, int tile_m, int chunks, int stages, int issue, cox_pla
  */
 int cox_rank_by_entry(int64_t p, int L, const double *lambdas, const void *B_host, int dbl,
                       int64_t *order_host, int64_t *entry_host, int64_t *count_out);
+
+/* Turn the active-set X B product (cox_options.active_set) on or off for the
+ * following calls.  Errors: COX_ERR_ARG for on outside {0, 1}. */
+int cox_set_active_set(cox_h h, int on);
 
 /* Switch a genotype handle between COX_SPLIT_E4M3 and COX_FP32_GEMV; both
  * read the same resident tiles.  Drops the per-k workspace.  Errors:

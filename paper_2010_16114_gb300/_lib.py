@@ -38,6 +38,7 @@ EXPORTS = [
     "cox_strerror", "cox_set_precision", "cox_profile", "cox_profile_read", "cox_lipschitz_noalloc",
     "cox_autotune", "cox_eta", "cox_plan_shape", "cox_rank_by_entry", "cox_path_seq", "cox_set_covariates",
     "cox_get_gamma", "cox_set_gamma", "cox_grad_gamma", "cox_prox_step_eta", "cox_last_loss_l1",
+    "cox_set_active_set",
 ]
 COX_MAX_COVARIATES = 16
 
@@ -46,7 +47,7 @@ class cox_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("center", ctypes.c_int), ("device", ctypes.c_int),
                 ("tile_m", ctypes.c_int), ("stages", ctypes.c_int), ("lag", ctypes.c_int),
                 ("wait_limit_s", ctypes.c_double), ("chunks", ctypes.c_int), ("window", ctypes.c_int),
-                ("issue", ctypes.c_int)]
+                ("issue", ctypes.c_int), ("active_set", ctypes.c_int)]
 
 
 class cox_info(ctypes.Structure):
@@ -55,7 +56,8 @@ class cox_info(ctypes.Structure):
                 ("tile_m", ctypes.c_int), ("stages", ctypes.c_int), ("sm_count", ctypes.c_int),
                 ("device_bytes", ctypes.c_int64), ("n_tie_groups", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("chunks", ctypes.c_int), ("ring", ctypes.c_int),
-                ("issue", ctypes.c_int), ("issue_xtv", ctypes.c_int)]
+                ("issue", ctypes.c_int), ("issue_xtv", ctypes.c_int), ("active_cols", ctypes.c_int64),
+                ("active_rebuilds", ctypes.c_int64)]
 
 
 class cox_tune_choice(ctypes.Structure):
@@ -137,6 +139,8 @@ def load(path: str | None = None):
     lib.cox_rank_by_entry.argtypes = [I64, I, P, P, I, P, P, ctypes.POINTER(I64)]
     lib.cox_path_seq.restype = I
     lib.cox_path_seq.argtypes = [P, P, I, I, D, D, I, P, P, P, P, P]
+    lib.cox_set_active_set.restype = I
+    lib.cox_set_active_set.argtypes = [P, I]
     lib.cox_prox_step_eta.restype = I
     lib.cox_prox_step_eta.argtypes = [P, P, P, P, I, D, P]
     lib.cox_last_loss_l1.restype = I
@@ -305,3 +309,7 @@ def cox_prox_step_eta(h, beta_ptr, eta_ptr, lam_ptr, k, step, stream_ptr):
 
 def cox_last_loss_l1(h, f_ptr, l1_ptr, k, stream_ptr):
     return load().cox_last_loss_l1(h, f_ptr, l1_ptr, k, stream_ptr)
+
+
+def cox_set_active_set(h, on: int) -> int:
+    return load().cox_set_active_set(h, on)

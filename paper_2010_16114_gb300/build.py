@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libcoxgb.so")
-SOURCES = ["api.cu", "setup.cu", "scans.cu", "gemm_tc.cu", "gemv.cu", "path.cu"]
+SOURCES = ["api.cu", "setup.cu", "scans.cu", "gemm_tc.cu", "gemv.cu", "path.cu", "active.cu"]
 HEADERS = ["internal.h", "ptx.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing",

@@ -80,7 +80,8 @@ class CoxProblem:
 
     def __init__(self, X, time, event, precision: str = "split_e4m3", center: bool | None = None,
                  p: int | None = None, device: int | None = None, tile_m: int = 0, stages: int = 0,
-                 lag: int = 10, wait_limit_s: float = 2.0, chunks: int = 0, window: int = 0, issue: int = 0):
+                 lag: int = 10, wait_limit_s: float = 2.0, chunks: int = 0, window: int = 0, issue: int = 0,
+                 active_set: bool = False):
         lib = L.load()
         opt = L.cox_default_options()
         opt.precision = PRECISIONS[precision]
@@ -91,6 +92,7 @@ class CoxProblem:
         opt.chunks = int(chunks)
         opt.window = int(window)
         opt.issue = int(issue)
+        opt.active_set = int(bool(active_set))
         opt.lag = int(lag)
         opt.wait_limit_s = float(wait_limit_s)
         time = np.ascontiguousarray(time, dtype=np.float64)
@@ -152,6 +154,10 @@ class CoxProblem:
         order = np.zeros(self.n, np.int64)
         L.check(L.cox_get_mu_order(self.h, _vp(mu), _vp(order)), "cox_get_mu_order")
         return mu, order
+
+    def set_active_set(self, on: bool):
+        """Stream only the SNP columns with a nonzero coefficient in X B (cox_set_active_set)."""
+        L.check(L.cox_set_active_set(self.h, int(bool(on))), "cox_set_active_set")
 
     def set_precision(self, precision: str):
         """Switch between "split_e4m3" and "fp32_gemv" on the same resident data."""

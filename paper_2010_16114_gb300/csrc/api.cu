@@ -58,6 +58,7 @@ void free_workspace(cox_handle *h)
                     w.sumV, w.f, w.F, w.l1, w.mub, w.lam, w.active, w.Fring, w.Bq, w.Vq, w.bs1, w.bs4, w.bmaxp,
                     w.vmaxp, w.part1, w.part4, w.cnt4, w.V64, w.V32, w.eta32, w.G32, w.gpart, w.gamma, w.gz, w.zvp};
     for (void *p : ptrs) dfree(p);
+    dfree(w.Bqa);
     const GemmPlan g1 = w.g1, g4 = w.g4;
     (void)g1;
     (void)g4;
@@ -150,18 +151,24 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
     Workspace &ws = h->ws;
     if (is_split(h)) {
         float *b32 = static_cast<float *>(beta);
+        int use_active = 0;
         {
-            Site s_(h, 3, 2, st);
+            Site s_(h, 3, 1, st);
             COX_TRY(l1_norms32(h, b32, k, st, ws.bmaxp));
-            COX_TRY(prep_limbs_beta(h, b32, k, st));
+            if (h->opt.active_set) COX_TRY(active_prepare(h, b32, k, st, &use_active));
+            if (!use_active) {
+                COX_TRY(prep_limbs_beta(h, b32, k, st));
+                h->launches += 1;
+            }
         }
+        const GemmPlan &g1 = use_active ? ws.g1a : ws.g1;
         EpiArgs e1;
         e1.epi = EPI_PARTIAL;
         e1.part = ws.part1;
         e1.bscale = ws.bs1;
         {
             Site s_(h, 0, 1, st);
-            COX_TRY(launch_gemm(h, ws.g1, e1, k, st));
+            COX_TRY(launch_gemm(h, g1, e1, k, st));
         }
         ScanArgs sa;
         sa.k = k;
@@ -169,9 +176,9 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
         sa.eta = ws.part1;
         sa.slot_stride = static_cast<int64_t>(k) * h->n_pad;
         sa.col_stride = h->n_pad;
-        sa.group_rows = ws.g1.T * TILE;
-        sa.KC = ws.g1.KC;
-        sa.L = ws.g1.L;
+        sa.group_rows = g1.T * TILE;
+        sa.KC = g1.KC;
+        sa.L = g1.L;
         sa.v_out = V_LIMBS_E4M3;
         sa.V = ws.Vq;
         sa.NP = ws.g4.NP;
@@ -450,6 +457,7 @@ int ensure_workspace(cox_handle *h, int k)
             return r;
         }
         A(ws.part1, static_cast<size_t>(ws.g1.max_slots) * k * h->n_pad);
+        ws.part1_slots = ws.g1.max_slots;
         A(ws.part4, static_cast<size_t>(ws.g4.max_slots) * k * h->p_pad);
         A(ws.cnt4, static_cast<size_t>(ws.g4.n_groups));
         cudaMemset(ws.cnt4, 0, static_cast<size_t>(ws.g4.n_groups) * sizeof(int));
@@ -490,6 +498,7 @@ void cox_default_options(cox_options *opt)
     opt->chunks = 0;
     opt->window = 0;
     opt->issue = 0;
+    opt->active_set = 0;
     opt->lag = 10;
     opt->wait_limit_s = 2.0;
 }
@@ -517,6 +526,7 @@ void cox_destroy(cox_h h)
     DeviceGuard g(h->dev);
     cudaDeviceSynchronize();
     free_workspace(h);
+    active_free(h);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     void *ptrs[] = {h->d_head, h->d_tail, h->d_evhead, h->d_delta, h->d_mu, h->d_A1, h->d_A4, h->d_Xr, h->d_Xc, h->d_err,
                     h->d_Z};
@@ -539,7 +549,7 @@ int cox_setup(cox_h *out, const void *X, int64_t n, int64_t p, int x_format, con
     if (x_format < COX_X_INT8_HOST || x_format > COX_X_PACKED2_DEV) return COX_ERR_ARG;
     if (opt.lag < 1 || !(opt.wait_limit_s >= 0.0)) return COX_ERR_ARG;
     if (opt.tile_m < 0 || opt.tile_m > 2 || opt.chunks < 0 || opt.chunks > 2 || opt.stages < 0 || opt.window < 0 ||
-        opt.issue < 0 || opt.issue > 3)
+        opt.issue < 0 || opt.issue > 3 || opt.active_set < 0 || opt.active_set > 1)
         return COX_ERR_ARG;
     for (int64_t i = 0; i < n; ++i) {
         if (!std::isfinite(time[i])) return COX_ERR_ARG;
@@ -664,6 +674,8 @@ int cox_get_info(cox_h h, cox_info *info)
     info->ring = h->ws.k ? h->ws.g1.ring : 0;
     info->issue = h->ws.k ? (h->ws.g1.alt ? 2 : h->ws.g1.pair ? 3 : 1) : h->opt.issue;
     info->issue_xtv = h->ws.k ? (h->ws.g4.alt ? 2 : h->ws.g4.pair ? 3 : 1) : h->opt.issue;
+    info->active_cols = h->opt.active_set ? h->nA : -1;
+    info->active_rebuilds = h->act_rebuilds;
     return COX_OK;
 }
 
@@ -806,6 +818,13 @@ int cox_set_precision(cox_h h, int precision)
     cudaDeviceSynchronize();
     free_workspace(h);
     h->opt.precision = precision;
+    return COX_OK;
+}
+
+int cox_set_active_set(cox_h h, int on)
+{
+    if (!h || on < 0 || on > 1) return COX_ERR_ARG;
+    h->opt.active_set = on;
     return COX_OK;
 }
 

@@ -100,6 +100,17 @@ __device__ inline int split_e4m3_units(float r, uint8_t *d)
     return q;
 }
 
+// 32-bit word index, in a tiled 2-bit layout of KC chunks per row tile, of the
+// 16 codes of row rit (0..127) of row tile mt at K offset `within` (a multiple
+// of 16) of chunk kc: row records of 32 bytes, two 16-byte halves (K 0-63 and
+// 64-127 of the chunk), stored swapped in rows with bit 2 set.
+__host__ __device__ inline int64_t word_offset(int64_t mt, int64_t KC, int64_t kc, int rit, int within)
+{
+    const int hh = within >> 6, w = (within & 63) >> 4;
+    const int phys = hh ^ ((rit >> 2) & 1);
+    return ((mt * KC + kc) * BLOCK_BYTES + rit * 32 + phys * 16 + w * 4) >> 2;
+}
+
 // K order of the SNP-major copy (A4).  Sorted subjects are kept in blocks of
 // 16 (one packed word), and sorted block b is stored at block (a b) mod nb,
 // nb = n_pad / 16, a odd and prime to nb, near nb (sqrt 5 - 1) / 2.  Any run
@@ -172,6 +183,12 @@ struct Workspace {
     double *zvp = nullptr;     // k x q x chunks partials
     GemmPlan g1, g4;
     bool plans_ready = false;
+    int part1_slots = 0;       // partial slots part1 holds
+    // active-set first product (cox_options.active_set)
+    GemmPlan g1a;
+    bool g1a_ready = false;
+    int64_t g1a_K = 0;
+    uint8_t *Bqa = nullptr;    // NP x act_Kpad e4m3 limbs of beta at the active SNPs
 };
 
 } // namespace coxgb
@@ -192,6 +209,12 @@ struct cox_handle {
     int64_t n_evhead = 0;
     int q = 0;                    // unpenalised covariates
     double *d_Z = nullptr;        // q x n, sorted order
+    // active set of the first product (active.cu)
+    uint8_t *d_inA = nullptr, *d_flag = nullptr;  // p: in the active set; in the current support
+    int32_t *d_Aidx = nullptr;    // active SNPs, ascending
+    uint32_t *d_A1act = nullptr;  // subject-major 2-bit copy of the active columns
+    unsigned long long *d_actcnt = nullptr;
+    int64_t nA = -1, act_cap = 0, act_Kpad = 0, act_rebuilds = 0;
     uint8_t *d_delta = nullptr;
     double *d_mu = nullptr;
     uint32_t *d_A1 = nullptr;  // subject-major 2-bit tiles
@@ -316,6 +339,10 @@ struct EpiArgs {
 };
 int launch_gemm(cox_handle *h, const GemmPlan &g, const EpiArgs &e, int k, cudaStream_t st);
 int prep_limbs_beta(cox_handle *h, const float *beta, int k, cudaStream_t st);
+
+// ---- active-set first product (active.cu) -------------------------------------------
+int active_prepare(cox_handle *h, const float *beta, int k, cudaStream_t st, int *use);
+void active_free(cox_handle *h);
 
 // ---- CUDA-core paths (gemv.cu) -----------------------------------------------------
 // ||beta_c||_1 partials into ws.l1p; with maxp, max |beta_c| partials too

@@ -256,7 +256,9 @@ int path_run(cox_handle *h, int k, int max_iter, double tol, double step, void *
     if (cudaMemcpy(ws.active, active.data(), k * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return COX_ERR_CUDA;
     do {
         if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) { rc = COX_ERR_CUDA; break; }
-        if (max_iter - t >= lag) {
+        // the active-set product decides on the host before each iteration, so
+        // those iterations run as plain launches instead of graph replays
+        if (max_iter - t >= lag && !(h->opt.active_set && h->opt.precision == COX_SPLIT_E4M3)) {
             if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = COX_ERR_CUDA; break; }
             for (int s = 0; s < lag && rc == COX_OK; ++s) rc = one_step(s);
             cudaError_t ec = cudaStreamEndCapture(cs, &graph);

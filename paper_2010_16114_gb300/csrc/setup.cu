@@ -26,14 +26,6 @@
 namespace coxgb {
 namespace {
 
-__device__ __forceinline__ int64_t word_offset(int64_t mt, int64_t KC, int64_t kc, int rit, int within)
-{
-    // within = K offset inside the 128-wide chunk, a multiple of 16
-    const int hh = within >> 6, w = (within & 63) >> 4;
-    const int phys = hh ^ ((rit >> 2) & 1);
-    return ((mt * KC + kc) * BLOCK_BYTES + rit * 32 + phys * 16 + w * 4) >> 2;
-}
-
 // A1: thread per (sorted row r, 16-SNP word); validates codes.
 __global__ void k_pack_a1(const uint8_t *__restrict__ in, int64_t rb, int64_t n, int64_t p,
                           const int32_t *__restrict__ order, uint32_t *__restrict__ A1, int64_t KC1, int *err)
