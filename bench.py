@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--path-iters", type=int, default=1000,
                     help="iteration cap of the timed cox_path_fit run (0: skip it)")
     ap.add_argument("--path-tol", type=float, default=1e-6)
+    ap.add_argument("--active-steps", type=int, default=5,
+                    help="iterations timed with and without the active-set X B after the path fit (0: skip)")
     return ap.parse_args()
 
 
@@ -406,7 +408,7 @@ def run_ours(args, rank, world):
     if args.path_iters > 0:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, iters, obj, conv = prob.path_fit(lams, step, max_iter=args.path_iters, tol=args.path_tol)
+        Bpath, iters, obj, conv = prob.path_fit(lams, step, max_iter=args.path_iters, tol=args.path_tol)
         torch.cuda.synchronize()
         pt = time.perf_counter() - t0
         steps_run = int(np.max(iters))
@@ -417,6 +419,39 @@ def run_ours(args, rank, world):
                 "final_objective": [float(x) for x in obj],
                 "timing": "wall clock around cox_path_fit (graph replays of 10 iterations, host reads the "
                           "k objectives after each replay), beta = 0 to the stopping rule or the cap"}
+
+    # the active-set X B late in the path: the 8 largest penalties from the
+    # path fit's coefficients, dense then with the active set, same iterations
+    active = None
+    if path is not None and args.active_steps > 0:
+        ka = min(8, k)
+        lam_a = lams[:ka]
+
+        def timed(on):
+            b = Bpath[:ka].clone()
+            prob.set_active_set(on)
+            prob.prox_step(b, lam_a, step)  # warm: plans, the active copy
+            prob.sync()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(args.active_steps):
+                prob.prox_step(b, lam_a, step)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            return a0.elapsed_time(a1) / args.active_steps, prob.info()
+
+        d_ms, _ = timed(False)
+        a_ms, ainfo = timed(True)
+        prob.set_active_set(False)
+        cols = ainfo["active_cols"]
+        act_bytes = (-(-n // 128) * 128) * (-(-max(cols, 1) // 256) * 256) / 4.0 if cols >= 0 else xb
+        active = {"lambdas": f"the {ka} largest of the grid, from the path fit's coefficients", "k": ka,
+                  "active_cols": cols, "support_cols_limit": (-(-p // 1024) * 1024) // 4,
+                  "dense_ms_per_step": d_ms, "active_ms_per_step": a_ms,
+                  "dense_iters_per_s": 1e3 / d_ms, "active_iters_per_s": 1e3 / a_ms,
+                  "x_b_bytes_per_iteration": {"dense": xb, "active": act_bytes},
+                  "rebuilds": ainfo["active_rebuilds"], "steps": args.active_steps}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -449,6 +484,7 @@ def run_ours(args, rank, world):
                                "scans": cls_ms[2] / args.steps, "other": cls_ms[3] / args.steps},
         "cpu_baseline": cpu,
         "path_fit": path,
+        "active_set": active,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": ck,
