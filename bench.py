@@ -240,24 +240,37 @@ class OracleSample:
 
     def baseline(self, steps: int):
         """cpu_baseline object: the threaded oracle on all host cores, the
-        1-thread figure beside it, and the per-column cost at two sample sizes
-        (the extrapolation to p columns and k penalties assumes it linear)."""
+        1-thread figure beside it.  A step costs a fixed part per penalty (the
+        risk-set sums over n subjects, their sort) plus a part per column (eta
+        and the gradient), so one full iteration is extrapolated from the step
+        times at two sample sizes, t(c) = a + b c, as k (a + b p)."""
         r = self.r
         cores = os.cpu_count() or 1
         half = max(1, self.cols // 2)
         t_all = self.time_step(self.cols, cores, steps)
         t_half = self.time_step(half, cores, steps)
         t_one = self.time_step(self.cols, 1, max(1, steps // 2))
-        scale = (r.p / self.cols) * r.k
+        t_one_half = self.time_step(half, 1, max(1, steps // 2))
+
+        def full(t_c, t_h):
+            b = max((t_c - t_h) / (self.cols - half), 1e-12) if self.cols > half else t_c / self.cols
+            a = max(t_c - b * self.cols, 0.0)
+            return r.k * (a + b * r.p), a, b
+
+        T, a, b = full(t_all, t_half)
+        T1, a1, b1 = full(t_one, t_one_half)
         return {
-            "value": 1.0 / (t_all * scale), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "value": 1.0 / T, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"one FP64 oracle iteration (eta, risk-set sums, gradient, soft threshold) on all {r.n} "
-                      f"subjects x the first {self.cols} SNP columns, one penalty, oracle routines on {cores} "
-                      f"threads over column blocks, median of {steps}; scaled by p/{self.cols} columns x {r.k} "
-                      f"penalties",
-            "one_thread": {"value": 1.0 / (t_one * scale), "unit": UNIT, "cores": 1,
-                           "sample": f"oracle.ista itself on the same sample, median of {max(1, steps // 2)}"},
-            "per_column_s": {str(self.cols): t_all / self.cols, str(half): t_half / half},
+                      f"subjects x the first {self.cols} and {half} SNP columns, one penalty, oracle routines on "
+                      f"{cores} threads over column blocks, median of {steps}; a full iteration = {r.k} penalties x "
+                      f"(a + b p) from the two step times",
+            "step_s": {str(self.cols): t_all, str(half): t_half},
+            "model_s": {"a_per_penalty": a, "b_per_column": b},
+            "one_thread": {"value": 1.0 / T1, "unit": UNIT, "cores": 1,
+                           "sample": f"oracle.ista itself on the same samples, median of {max(1, steps // 2)}",
+                           "step_s": {str(self.cols): t_one, str(half): t_one_half},
+                           "model_s": {"a_per_penalty": a1, "b_per_column": b1}},
         }
 
 

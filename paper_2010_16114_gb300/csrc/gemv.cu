@@ -107,22 +107,26 @@ __global__ void __launch_bounds__(128) k_gemv_tiles(const uint32_t *__restrict__
     y[row] = static_cast<float>(acc);
 }
 
-// ---- the FP32 baseline's matrix-vector product: byte tables of x -------------
-// In the tiled layout byte b of word q of half h of a row's 32-byte record holds
-// the codes of the four K positions base + 4m (m = 0..3), base = 128 kc + 64 h
-// + 16 q + b, two bits each.  For one K chunk a CTA tabulates, for each of those
-// 32 byte positions and each of the 256 byte values v, the FP32 sum
-//   T[v] = sum_m code_m(v) x[base + 4m],   code_m(v) = (v >> 2m) & 3,
-// after which a row's dot product with the chunk is 32 table lookups and FP32
-// adds, one per packed byte.  A CTA keeps the tables of LUT_CW chunks in
-// shared memory and streams the row tiles of its split through them with
-// 16-byte coalesced loads, two threads per row (one per 16-byte half); every
-// (range of chunks) leaves one FP32 partial per row, and k_gemv_reduce adds
-// the partials with a compensated FP32 sum.  The tables of the second half
-// start 16 words later, so the two halves' lanes index different banks.
-constexpr int LUT_CW = 6;                    // K chunks per CTA
-constexpr int LUT_THREADS = 512;             // two threads per row, two row tiles per pass
-constexpr int LUT_CHUNK = 32 * 256 + 16;     // floats per chunk's tables (+16: bank offset of half 1)
+// ---- the FP32 baseline's matrix-vector product: nibble tables of x ------------
+// In the tiled layout nibble np (0, 1) of byte b of word q of half h of a row's
+// 32-byte record holds the codes of the two K positions base + 4 (2 np + m)
+// (m = 0, 1), base = 128 kc + 64 h + 16 q + b, two bits each.  For one K chunk
+// a CTA tabulates, for each of those 64 nibble positions and each of the 16
+// nibble values v, the FP32 sum
+//   T[v] = sum_m code_m(v) x[base + 4 (2 np + m)],   code_m(v) = (v >> 2m) & 3,
+// after which a row's dot product with the chunk is 64 table lookups and FP32
+// adds.  Tables are laid out [chunk][q][b][np][h][v], so at every step the 16
+// lanes of one half read one 16-entry table in banks 0-15 and the other half's
+// lanes another in banks 16-31: lanes that index different entries never
+// share a bank, lanes that index the same entry share the word.  A CTA keeps
+// the tables of LUT_CW chunks in shared memory and streams the row tiles of its
+// split through them with 16-byte coalesced loads, two threads per row (one
+// per 16-byte half); every range of chunks leaves one FP32 partial per row, and
+// k_gemv_reduce adds the partials with a compensated FP32 sum.
+constexpr int LUT_CW = 48;          // K chunks per CTA (tables: 48 x 4 KB)
+constexpr int LUT_THREADS = 512;    // two threads per row, two row tiles per pass
+constexpr int LUT_CHUNK = 1024;     // floats per chunk's tables
+constexpr int LUT_BATCH = 8;        // chunks whose codes a thread loads before it looks up
 
 __global__ void __launch_bounds__(LUT_THREADS) k_gemv_lut(const uint32_t *__restrict__ A, int64_t row_tiles,
                                                           int64_t KC, const float *__restrict__ x,
@@ -134,43 +138,53 @@ __global__ void __launch_bounds__(LUT_THREADS) k_gemv_lut(const uint32_t *__rest
     const int64_t split = blockIdx.x / n_ranges;
     const int64_t kc0 = static_cast<int64_t>(range) * LUT_CW;
     const int ncw = static_cast<int>(min(static_cast<int64_t>(LUT_CW), KC - kc0));
-    for (int e = threadIdx.x; e < ncw * 8192; e += LUT_THREADS) {
-        const int c = e >> 13, g = (e >> 8) & 31, v = e & 255;
-        const int64_t base = (kc0 + c) * TILE + 64 * (g >> 4) + 16 * ((g >> 2) & 3) + (g & 3);
+    for (int e = threadIdx.x; e < ncw * LUT_CHUNK; e += LUT_THREADS) {
+        const int c = e >> 10, q = (e >> 8) & 3, b = (e >> 6) & 3, np = (e >> 5) & 1, h = (e >> 4) & 1, v = e & 15;
+        const int64_t base = (kc0 + c) * TILE + 64 * h + 16 * q + b + 8 * np;
         float acc = 0.f;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
+        for (int m = 0; m < 2; ++m) {
             const int64_t K = base + 4 * m;
             const float xv = K < K_valid ? x[K] : 0.f;
             acc = fmaf(static_cast<float>((v >> (2 * m)) & 3), xv, acc);
         }
-        tab[c * LUT_CHUNK + g * 256 + ((g & 16) ? 16 : 0) + v] = acc;
+        tab[e] = acc;
     }
     __syncthreads();
     const int r = (threadIdx.x & 255) >> 1, hh = threadIdx.x & 1;
     const int swp = (r >> 2) & 1;
-    const float *tb = tab + hh * (16 * 256 + 16);
+    // byte address of this half's table entry 0, ORed with 4 v into each lookup
+    const uint32_t tb = static_cast<uint32_t>(__cvta_generic_to_shared(tab)) + 64u * hh;
     const int64_t mt_begin = split * tiles_per_split;
     const int64_t mt_end = min(row_tiles, mt_begin + tiles_per_split);
     for (int64_t mt = mt_begin + (threadIdx.x >> 8); mt < mt_end; mt += 2) {
         const uint8_t *rec = reinterpret_cast<const uint8_t *>(A) + ((mt * KC + kc0) * BLOCK_BYTES + r * 32 + 16 * (hh ^ swp));
-        uint4 w[LUT_CW];
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int c0 = 0; c0 < ncw; c0 += LUT_BATCH) {
+            uint4 w[LUT_BATCH];
 #pragma unroll
-        for (int c = 0; c < LUT_CW; ++c)
-            if (c < ncw) w[c] = __ldcs(reinterpret_cast<const uint4 *>(rec + static_cast<int64_t>(c) * BLOCK_BYTES));
-        float acc = 0.f;
+            for (int c = 0; c < LUT_BATCH; ++c)
+                if (c0 + c < ncw) w[c] = __ldcs(reinterpret_cast<const uint4 *>(rec + static_cast<int64_t>(c0 + c) * BLOCK_BYTES));
 #pragma unroll
-        for (int c = 0; c < LUT_CW; ++c) {
-            if (c >= ncw) break;
-            const float *t = tb + c * LUT_CHUNK;
-            const uint32_t ws[4] = {w[c].x, w[c].y, w[c].z, w[c].w};
+            for (int c = 0; c < LUT_BATCH; ++c) {
+                if (c0 + c >= ncw) break;
+                const uint32_t cb = tb + 4u * LUT_CHUNK * static_cast<uint32_t>(c0 + c);
+                const uint32_t ws[4] = {w[c].x, w[c].y, w[c].z, w[c].w};
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+                for (int q = 0; q < 4; ++q)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) acc += t[(4 * q + b) * 256 + ((ws[q] >> (8 * b)) & 255u)];
+                    for (int j = 0; j < 8; ++j) {  // nibble j = 2 b + np of word q
+                        const uint32_t off = 4u * static_cast<uint32_t>(((q * 4 + (j >> 1)) * 2 + (j & 1)) * 32);
+                        const uint32_t a = cb + off + ((ws[q] >> (4 * j)) & 15u) * 4u;
+                        float t;
+                        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(t) : "r"(a));
+                        acc[j & 3] += t;
+                    }
+            }
         }
-        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        if (hh == 0) part[static_cast<int64_t>(range) * rows_pad + mt * TILE + r] = acc;
+        float sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        if (hh == 0) part[static_cast<int64_t>(range) * rows_pad + mt * TILE + r] = sum;
     }
 }
 
