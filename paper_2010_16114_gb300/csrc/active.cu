@@ -4,10 +4,11 @@
 // penalty's coefficient is nonzero (arXiv 2010.16114, Section 6: along the UK
 // Biobank path a few hundred SNPs were selected out of 470,194).  Before each
 // X B the library marks the union support of the k coefficient columns; when
-// it holds a column outside the current active set A, the host rebuilds A as
-// that support, gathers a subject-major 2-bit copy of the columns of A (the
-// tiled layout of the full copy, K = position in A), and plans the same
-// tensor-core product on it.  A always covers the current support, so the
+// it holds a column outside the current active set A, the host rebuilds A (the
+// old set with the support added, or the support alone once that union has
+// grown past twice the support), gathers a subject-major 2-bit copy of the
+// columns of A (the tiled layout of the full copy, K = position in A), and
+// plans the same tensor-core product on it.  A always covers the current support, so the
 // product equals the dense one up to the FP32 order of the nonzero terms.
 // When the support holds more than a quarter of the (padded) columns the
 // dense product runs instead.
@@ -44,28 +45,59 @@ __global__ void k_support(const float *__restrict__ beta, int k, int64_t p, cons
     }
 }
 
-// The active copy: word (row r, active positions 16 wq .. 16 wq + 15) from the
-// codes of SNPs Aidx[t] in the full subject-major copy; positions past nA hold 0.
-__global__ void k_gather_active(const uint32_t *__restrict__ A1, int64_t KC1, const int32_t *__restrict__ Aidx,
-                                int64_t nA, int64_t n, int64_t words, int64_t KCa, uint32_t *__restrict__ out)
+// The active copy, one CTA per row tile (thread = row): for each source chunk
+// that holds active SNPs (cchunk[c], active positions cstart[c] ..
+// cstart[c+1]), the row's 32-byte record of that chunk (coalesced over the
+// tile's 128 rows, prefetched GA chunks ahead) yields the codes of all its
+// active SNPs, packed in active order into words of 16; positions past nA
+// stay 0 (the copy is cleared first).
+constexpr int GA = 4;
+__global__ void __launch_bounds__(TILE) k_gather_active(const uint32_t *__restrict__ A1, int64_t KC1,
+                                                        const int32_t *__restrict__ Aidx,
+                                                        const int32_t *__restrict__ cchunk,
+                                                        const int32_t *__restrict__ cstart, int nchunks,
+                                                        int64_t n, int64_t KCa, uint32_t *__restrict__ out)
 {
-    const int64_t total = n * words;
-    for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < total;
-         q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t wq = q / n, r = q - wq * n;  // consecutive threads: consecutive rows
-        const int64_t t0 = 16 * wq;
-        const int64_t mt = r / TILE;
-        const int rit = static_cast<int>(r % TILE);
-        uint32_t P = 0;
-        for (int kap = 0; kap < 16; ++kap) {
-            const int64_t t = t0 + kap;
-            if (t >= nA) break;
-            const int64_t K = Aidx[t];
-            const uint32_t src = A1[word_offset(mt, KC1, K / TILE, rit, static_cast<int>((K % TILE) & ~15))];
-            P |= ((src >> code_bit(static_cast<int>(K & 15))) & 3u) << code_bit(kap);
+    const int64_t mt = blockIdx.x;
+    const int rit = threadIdx.x;
+    if (mt * TILE + rit >= n) return;  // padding rows stay 0
+    const int swp = (rit >> 2) & 1;
+    int64_t cur = -1;  // word (16 active positions) being built
+    uint32_t P = 0;
+    for (int c0 = 0; c0 < nchunks; c0 += GA) {
+        uint4 rec[GA][2];
+#pragma unroll
+        for (int g = 0; g < GA; ++g) {
+            if (c0 + g >= nchunks) break;
+            const uint4 *b = reinterpret_cast<const uint4 *>(
+                reinterpret_cast<const uint8_t *>(A1) + (mt * KC1 + cchunk[c0 + g]) * BLOCK_BYTES + rit * 32);
+            rec[g][0] = __ldcs(b + swp);      // logical half 0 (K 0..63 of the chunk)
+            rec[g][1] = __ldcs(b + (swp ^ 1));  // logical half 1
         }
-        out[word_offset(mt, KCa, t0 / TILE, rit, static_cast<int>(t0 % TILE))] = P;
+#pragma unroll
+        for (int g = 0; g < GA; ++g) {
+            if (c0 + g >= nchunks) break;
+            const uint32_t wd[8] = {rec[g][0].x, rec[g][0].y, rec[g][0].z, rec[g][0].w,
+                                    rec[g][1].x, rec[g][1].y, rec[g][1].z, rec[g][1].w};
+            for (int32_t t = cstart[c0 + g]; t < cstart[c0 + g + 1]; ++t) {
+                const int within = static_cast<int>(Aidx[t] % TILE);
+                uint32_t word = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (q == (within >> 4)) word = wd[q];  // word q = 4 h + (within mod 64) / 16
+                const uint32_t code = (word >> code_bit(within & 15)) & 3u;
+                const int64_t wq = t >> 4;
+                if (wq != cur) {
+                    if (cur >= 0)
+                        out[word_offset(mt, KCa, (cur * 16) / TILE, rit, static_cast<int>((cur * 16) % TILE))] = P;
+                    P = 0;
+                    cur = wq;
+                }
+                P |= code << code_bit(t & 15);
+            }
+        }
     }
+    if (cur >= 0) out[word_offset(mt, KCa, (cur * 16) / TILE, rit, static_cast<int>((cur * 16) % TILE))] = P;
 }
 
 // e4m3 limbs of beta at the active SNPs (column t of the limb matrix = SNP
@@ -119,6 +151,7 @@ void active_free(cox_handle *h)
     h->d_actcnt = nullptr;
     h->nA = -1;
     h->act_cap = 0;
+    h->h_Aidx.clear();
 }
 
 // Decide the first product of this iteration: *use = 1 with ws.g1a planned on
@@ -148,34 +181,55 @@ int active_prepare(cox_handle *h, const float *beta, int k, cudaStream_t st, int
     if (static_cast<int64_t>(cnt[0]) > limit) return COX_OK;  // a large support: the dense product
     const bool rebuild = h->nA < 0 || cnt[1] > 0;
     if (rebuild) {
-        // the active set becomes the current support (sorted SNP indices)
+        // the new set: the old one with the current support added (SNPs that
+        // leave and re-enter then cost no rebuild), or the support alone once
+        // the union has grown past twice the support (plus 4096)
         std::vector<uint8_t> flag(static_cast<size_t>(p));
         COX_CUDA(cudaMemcpyAsync(flag.data(), h->d_flag, p, cudaMemcpyDeviceToHost, st));
         COX_CUDA(cudaStreamSynchronize(st));
+        const int64_t sup = static_cast<int64_t>(cnt[0]);
+        if (static_cast<int64_t>(h->h_Aidx.size()) + static_cast<int64_t>(cnt[1]) <= 2 * sup + 4096)
+            for (int32_t j : h->h_Aidx) flag[j] = 1;
         std::vector<int32_t> idx;
-        idx.reserve(static_cast<size_t>(cnt[0]));
         for (int64_t j = 0; j < p; ++j)
             if (flag[j]) idx.push_back(static_cast<int32_t>(j));
         const int64_t nA = static_cast<int64_t>(idx.size());
+        if (nA > limit) return COX_OK;  // the set in use stays as it was
+        // the source chunks that hold active SNPs, and each one's first active position
+        std::vector<int32_t> cchunk, cstart;
+        for (int64_t t = 0; t < nA; ++t)
+            if (cchunk.empty() || idx[t] / TILE != cchunk.back()) {
+                cchunk.push_back(idx[t] / TILE);
+                cstart.push_back(static_cast<int32_t>(t));
+            }
+        cstart.push_back(static_cast<int32_t>(nA));
         const int64_t Kpad = std::max<int64_t>(256, (nA + 255) / 256 * 256);
         if (Kpad > h->act_cap) {
             dfree(h->d_Aidx);
             dfree(h->d_A1act);
             h->d_Aidx = nullptr;
             h->d_A1act = nullptr;
-            COX_TRY(dmalloc(h, reinterpret_cast<void **>(&h->d_Aidx), Kpad * sizeof(int32_t)));
+            // Aidx then the chunk list (at most one chunk per active SNP) and its starts
+            COX_TRY(dmalloc(h, reinterpret_cast<void **>(&h->d_Aidx), (3 * Kpad + 1) * sizeof(int32_t)));
             COX_TRY(dmalloc(h, reinterpret_cast<void **>(&h->d_A1act), static_cast<size_t>(h->n_pad) * Kpad / 4));
             h->act_cap = Kpad;
         }
-        if (nA) COX_CUDA(cudaMemcpyAsync(h->d_Aidx, idx.data(), nA * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        int32_t *d_cchunk = h->d_Aidx + h->act_cap, *d_cstart = h->d_Aidx + 2 * h->act_cap;
+        const int nchunks = static_cast<int>(cchunk.size());
+        if (nA) {
+            COX_CUDA(cudaMemcpyAsync(h->d_Aidx, idx.data(), nA * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            COX_CUDA(cudaMemcpyAsync(d_cchunk, cchunk.data(), nchunks * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        }
+        COX_CUDA(cudaMemcpyAsync(d_cstart, cstart.data(), cstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         COX_CUDA(cudaMemcpyAsync(h->d_inA, flag.data(), p, cudaMemcpyHostToDevice, st));
         COX_CUDA(cudaMemsetAsync(h->d_A1act, 0, static_cast<size_t>(h->n_pad) * Kpad / 4, st));
-        const int64_t words = Kpad / 16;
-        k_gather_active<<<grid_over(h->n * words, h->sm_count), 256, 0, st>>>(
-            h->d_A1, h->p_pad / TILE, h->d_Aidx, nA, h->n, words, Kpad / TILE, h->d_A1act);
+        if (nchunks)
+            k_gather_active<<<static_cast<unsigned>(h->n_pad / TILE), TILE, 0, st>>>(
+                h->d_A1, h->p_pad / TILE, h->d_Aidx, d_cchunk, d_cstart, nchunks, h->n, Kpad / TILE, h->d_A1act);
         COX_CUDA(cudaGetLastError());
-        COX_CUDA(cudaStreamSynchronize(st));  // idx and flag leave scope
+        COX_CUDA(cudaStreamSynchronize(st));  // the host lists leave scope
         h->launches += 1;
+        h->h_Aidx.swap(idx);
         h->nA = nA;
         h->act_Kpad = Kpad;
         h->act_rebuilds += 1;

@@ -128,12 +128,37 @@ constexpr int LUT_THREADS = 512;    // two threads per row, two row tiles per pa
 constexpr int LUT_CHUNK = 1024;     // floats per chunk's tables
 constexpr int LUT_BATCH = 8;        // chunks whose codes a thread loads before it looks up
 
+// The 32 lookups of one chunk's 16 bytes of codes: nibble j of word q reads the
+// table at byte offset 4 (C LUT_CHUNK + ((4 q + j / 2) 2 + j % 2) 32 + v), v the
+// nibble, as (cb | 4 v) + offset with the offset an immediate of the load.
+#define COX_LUT_NIB(Q, J)                                                                           \
+    {                                                                                               \
+        const uint32_t a = cb | ((J) == 0 ? (ws[Q] << 2) & 0x3Cu : (ws[Q] >> (4 * (J) - 2)) & 0x3Cu);   \
+        float t;                                                                                    \
+        asm("ld.shared.f32 %0, [%1+%2];"                                                            \
+            : "=f"(t)                                                                               \
+            : "r"(a), "n"(4 * (C * LUT_CHUNK + (((Q) * 4 + ((J) >> 1)) * 2 + ((J) & 1)) * 32)));    \
+        acc[(J) & 3] += t;                                                                          \
+    }
+#define COX_LUT_WORD(Q)                                                                             \
+    COX_LUT_NIB(Q, 0) COX_LUT_NIB(Q, 1) COX_LUT_NIB(Q, 2) COX_LUT_NIB(Q, 3) COX_LUT_NIB(Q, 4)         \
+    COX_LUT_NIB(Q, 5) COX_LUT_NIB(Q, 6) COX_LUT_NIB(Q, 7)
+
+template <int C>
+__device__ __forceinline__ void lut_chunk(uint32_t cb, const uint4 &w, float (&acc)[4])
+{
+    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+    COX_LUT_WORD(0) COX_LUT_WORD(1) COX_LUT_WORD(2) COX_LUT_WORD(3)
+}
+#undef COX_LUT_WORD
+#undef COX_LUT_NIB
+
 __global__ void __launch_bounds__(LUT_THREADS) k_gemv_lut(const uint32_t *__restrict__ A, int64_t row_tiles,
                                                           int64_t KC, const float *__restrict__ x,
                                                           int64_t K_valid, float *__restrict__ part,
                                                           int64_t rows_pad, int n_ranges, int64_t tiles_per_split)
 {
-    extern __shared__ float tab[];
+    extern __shared__ __align__(1024) float tab[];
     const int range = static_cast<int>(blockIdx.x % n_ranges);
     const int64_t split = blockIdx.x / n_ranges;
     const int64_t kc0 = static_cast<int64_t>(range) * LUT_CW;
@@ -153,7 +178,10 @@ __global__ void __launch_bounds__(LUT_THREADS) k_gemv_lut(const uint32_t *__rest
     __syncthreads();
     const int r = (threadIdx.x & 255) >> 1, hh = threadIdx.x & 1;
     const int swp = (r >> 2) & 1;
-    // byte address of this half's table entry 0, ORed with 4 v into each lookup
+    // byte address of this half's table entry 0: 64-byte aligned, so that a
+    // lookup's address is this base ORed with 4 v (bits 2..5) plus the
+    // (chunk, word, byte, nibble) offset as an immediate: shift, one logic
+    // operation, the load and the add per nibble
     const uint32_t tb = static_cast<uint32_t>(__cvta_generic_to_shared(tab)) + 64u * hh;
     const int64_t mt_begin = split * tiles_per_split;
     const int64_t mt_end = min(row_tiles, mt_begin + tiles_per_split);
@@ -165,22 +193,17 @@ __global__ void __launch_bounds__(LUT_THREADS) k_gemv_lut(const uint32_t *__rest
 #pragma unroll
             for (int c = 0; c < LUT_BATCH; ++c)
                 if (c0 + c < ncw) w[c] = __ldcs(reinterpret_cast<const uint4 *>(rec + static_cast<int64_t>(c0 + c) * BLOCK_BYTES));
-#pragma unroll
-            for (int c = 0; c < LUT_BATCH; ++c) {
-                if (c0 + c >= ncw) break;
-                const uint32_t cb = tb + 4u * LUT_CHUNK * static_cast<uint32_t>(c0 + c);
-                const uint32_t ws[4] = {w[c].x, w[c].y, w[c].z, w[c].w};
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {  // nibble j = 2 b + np of word q
-                        const uint32_t off = 4u * static_cast<uint32_t>(((q * 4 + (j >> 1)) * 2 + (j & 1)) * 32);
-                        const uint32_t a = cb + off + ((ws[q] >> (4 * j)) & 15u) * 4u;
-                        float t;
-                        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(t) : "r"(a));
-                        acc[j & 3] += t;
-                    }
-            }
+            // tables of chunk c0 + c start 4 LUT_CHUNK (c0 + c) bytes in: a multiple of 4 KB
+            const uint32_t cb = tb + 4u * LUT_CHUNK * static_cast<uint32_t>(c0);
+            static_assert(LUT_BATCH == 8, "lut_chunk calls below");
+            if (c0 + 0 < ncw) lut_chunk<0>(cb, w[0], acc);
+            if (c0 + 1 < ncw) lut_chunk<1>(cb, w[1], acc);
+            if (c0 + 2 < ncw) lut_chunk<2>(cb, w[2], acc);
+            if (c0 + 3 < ncw) lut_chunk<3>(cb, w[3], acc);
+            if (c0 + 4 < ncw) lut_chunk<4>(cb, w[4], acc);
+            if (c0 + 5 < ncw) lut_chunk<5>(cb, w[5], acc);
+            if (c0 + 6 < ncw) lut_chunk<6>(cb, w[6], acc);
+            if (c0 + 7 < ncw) lut_chunk<7>(cb, w[7], acc);
         }
         float sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
         sum += __shfl_xor_sync(0xffffffffu, sum, 1);

@@ -215,6 +215,7 @@ struct cox_handle {
     uint32_t *d_A1act = nullptr;  // subject-major 2-bit copy of the active columns
     unsigned long long *d_actcnt = nullptr;
     int64_t nA = -1, act_cap = 0, act_Kpad = 0, act_rebuilds = 0;
+    std::vector<int32_t> h_Aidx;  // the active set (host copy)
     uint8_t *d_delta = nullptr;
     double *d_mu = nullptr;
     uint32_t *d_A1 = nullptr;  // subject-major 2-bit tiles
