@@ -5,10 +5,11 @@
 // Biobank path a few hundred SNPs were selected out of 470,194).  Before each
 // X B the library marks the union support of the k coefficient columns; when
 // it holds a column outside the current active set A, the host rebuilds A (the
-// old set with the support added, or the support alone once that union has
-// grown past twice the support), gathers a subject-major 2-bit copy of the
-// columns of A (the tiled layout of the full copy, K = position in A), and
-// plans the same tensor-core product on it.  A always covers the current support, so the
+// old set with the support added, and the SNPs the fused step marked as close
+// to entering, or without the old set once that union has grown past twice
+// the rest), gathers a subject-major 2-bit copy of the columns of A (the tiled
+// layout of the full copy, K = position in A), and plans the same tensor-core
+// product on it.  A always covers the current support, so the
 // product equals the dense one up to the FP32 order of the nonzero terms.
 // When the support holds more than a quarter of the (padded) columns the
 // dense product runs instead.
@@ -143,9 +144,9 @@ unsigned grid_over(int64_t total, int sms)
 
 void active_free(cox_handle *h)
 {
-    void *ptrs[] = {h->d_inA, h->d_flag, h->d_Aidx, h->d_A1act, h->d_actcnt};
+    void *ptrs[] = {h->d_inA, h->d_flag, h->d_near, h->d_Aidx, h->d_A1act, h->d_actcnt};
     for (void *p : ptrs) dfree(p);
-    h->d_inA = h->d_flag = nullptr;
+    h->d_inA = h->d_flag = h->d_near = nullptr;
     h->d_Aidx = nullptr;
     h->d_A1act = nullptr;
     h->d_actcnt = nullptr;
@@ -166,6 +167,8 @@ int active_prepare(cox_handle *h, const float *beta, int k, cudaStream_t st, int
     if (!h->d_inA) {
         COX_TRY(dmalloc(h, reinterpret_cast<void **>(&h->d_inA), p));
         COX_TRY(dmalloc(h, reinterpret_cast<void **>(&h->d_flag), p));
+        COX_TRY(dmalloc(h, reinterpret_cast<void **>(&h->d_near), p));
+        COX_CUDA(cudaMemsetAsync(h->d_near, 0, p, st));
         COX_TRY(dmalloc(h, reinterpret_cast<void **>(&h->d_actcnt), 2 * sizeof(unsigned long long)));
         COX_CUDA(cudaMemsetAsync(h->d_inA, 0, p, st));
         h->nA = -1;
@@ -184,11 +187,20 @@ int active_prepare(cox_handle *h, const float *beta, int k, cudaStream_t st, int
         // the new set: the old one with the current support added (SNPs that
         // leave and re-enter then cost no rebuild), or the support alone once
         // the union has grown past twice the support (plus 4096)
-        std::vector<uint8_t> flag(static_cast<size_t>(p));
+        std::vector<uint8_t> flag(static_cast<size_t>(p)), near(static_cast<size_t>(p));
         COX_CUDA(cudaMemcpyAsync(flag.data(), h->d_flag, p, cudaMemcpyDeviceToHost, st));
+        COX_CUDA(cudaMemcpyAsync(near.data(), h->d_near, p, cudaMemcpyDeviceToHost, st));
+        COX_CUDA(cudaMemsetAsync(h->d_near, 0, p, st));
         COX_CUDA(cudaStreamSynchronize(st));
         const int64_t sup = static_cast<int64_t>(cnt[0]);
-        if (static_cast<int64_t>(h->h_Aidx.size()) + static_cast<int64_t>(cnt[1]) <= 2 * sup + 4096)
+        // headroom: SNPs whose pre-threshold value came within a quarter of the
+        // threshold in the steps since the last rebuild (marked by the fused step)
+        // are likely to enter next, so the set takes them in now
+        int64_t nnear = 0;
+        for (int64_t j = 0; j < p; ++j) nnear += near[j] && !flag[j];
+        if (sup + nnear <= limit)
+            for (int64_t j = 0; j < p; ++j) flag[j] |= near[j];
+        if (static_cast<int64_t>(h->h_Aidx.size()) + static_cast<int64_t>(cnt[1]) <= 2 * (sup + nnear) + 4096)
             for (int32_t j : h->h_Aidx) flag[j] = 1;
         std::vector<int32_t> idx;
         for (int64_t j = 0; j < p; ++j)

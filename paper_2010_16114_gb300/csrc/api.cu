@@ -201,6 +201,7 @@ int iterate(cox_handle *h, void *beta, int k, int epi, void *grad, double step, 
         e4.mu = h->d_mu;
         e4.sumV = ws.sumV;
         e4.active = ws.active;
+        e4.near = (h->opt.active_set && epi == EPI_PROX) ? h->d_near : nullptr;
         e4.bscale = ws.bs4;
         e4.rows_valid = h->p;
         e4.inv_n = 1.0 / static_cast<double>(h->n);

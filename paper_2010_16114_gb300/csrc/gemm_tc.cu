@@ -75,6 +75,7 @@ struct KParams {
     const double *mu;
     const double *sumV;
     const int *active;
+    uint8_t *near;      // may be null: SNPs whose |z| came within a quarter of the threshold
     int64_t rows_valid;
     double inv_n;
     long long wait_limit;
@@ -542,6 +543,7 @@ __global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
                                 const float thr = colc[KH + e];
                                 const float z = fmaf(stepf, gv, bv[u]);
                                 P.beta[bi] = z > thr ? z - thr : (z < -thr ? z + thr : 0.f);
+                                if (P.near && fabsf(z) > 0.75f * thr) P.near[row] = 1;
                             } else {
                                 P.grad[bi] = -gv;
                             }
@@ -640,6 +642,7 @@ __global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
                             const float thr = colc[KH + kk];
                             const float z = fmaf(stepf, gv, bv[u][rr]);
                             beta[bi] = z > thr ? z - thr : (z < -thr ? z + thr : 0.f);
+                            if (P.near && fabsf(z) > 0.75f * thr) P.near[row] = 1;
                         } else {
                             grad[bi] = -gv;
                         }
@@ -1028,6 +1031,7 @@ int launch_gemm(cox_handle *h, const GemmPlan &g, const EpiArgs &e, int k, cudaS
     kp.mu = e.mu;
     kp.sumV = e.sumV;
     kp.active = e.active;
+    kp.near = e.near;
     kp.rows_valid = e.rows_valid;
     kp.inv_n = e.inv_n;
     kp.wait_limit = h->wait_cycles;

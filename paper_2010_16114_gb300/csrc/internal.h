@@ -211,6 +211,7 @@ struct cox_handle {
     double *d_Z = nullptr;        // q x n, sorted order
     // active set of the first product (active.cu)
     uint8_t *d_inA = nullptr, *d_flag = nullptr;  // p: in the active set; in the current support
+    uint8_t *d_near = nullptr;    // p: pre-threshold value within a quarter of the threshold
     int32_t *d_Aidx = nullptr;    // active SNPs, ascending
     uint32_t *d_A1act = nullptr;  // subject-major 2-bit copy of the active columns
     unsigned long long *d_actcnt = nullptr;
@@ -334,6 +335,7 @@ struct EpiArgs {
     const double *mu = nullptr;
     const double *sumV = nullptr;
     const int *active = nullptr;
+    uint8_t *near = nullptr;      // p: set where |z| > 3/4 of the threshold (active set's headroom)
     const int *bscale = nullptr;  // k: power-of-two scale of the B limbs
     int64_t rows_valid = 0;  // p
     double inv_n = 0;
