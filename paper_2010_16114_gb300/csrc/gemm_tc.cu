@@ -517,20 +517,24 @@ __global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
                 // the whole group ran in this CTA: apply the step straight from the
                 // sums (the same values the one partial slot would carry)
                 const float inv_n = static_cast<float>(P.inv_n), stepf = static_cast<float>(P.step);
+                // all loads of a tile (mu and a batch of up to 16 coefficients) are
+                // issued before any arithmetic, one round trip per tile and batch
+                constexpr int EB = KH < 16 ? KH : 16;
 #pragma unroll
                 for (int tt = 0; tt < T; ++tt) {
                     const int64_t row = (static_cast<int64_t>(g) * T + tt) * TILE + rit;
                     const bool valid = row < P.rows_valid;
-                    const float muv = valid ? static_cast<float>(P.mu[row]) : 0.f;
-                    for (int e0 = 0; e0 < P.k; e0 += 8) {
-                        float bv[8];
+                    const double mud = valid ? P.mu[row] : 0.0;
+                    for (int e0 = 0; e0 < P.k; e0 += EB) {
+                        float bv[EB];
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) {
+                        for (int u = 0; u < EB; ++u) {
                             const int e = min(e0 + u, P.k - 1);
                             bv[u] = (P.epi == EPI_PROX && valid) ? P.beta[static_cast<int64_t>(e) * P.rows_valid + row] : 0.f;
                         }
+                        const float muv = static_cast<float>(mud);
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) {
+                        for (int u = 0; u < EB; ++u) {
                             const int e = e0 + u;
                             if (e >= P.k) break;
                             const float xtv = ldexpf(acc(tt, e), bsc[e] + 9);  // (X^T V)_j
