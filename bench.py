@@ -445,6 +445,8 @@ def run_ours(args, rank, world):
             prob.set_active_set(on)
             prob.prox_step(b, lam_a, step)  # warm: plans, the active copy
             prob.sync()
+            r0 = prob.info()["active_rebuilds"]
+            prob.profile(True)
             a0 = torch.cuda.Event(enable_timing=True)
             a1 = torch.cuda.Event(enable_timing=True)
             a0.record(stream)
@@ -452,10 +454,16 @@ def run_ours(args, rank, world):
                 prob.prox_step(b, lam_a, step)
             a1.record(stream)
             torch.cuda.synchronize()
-            return a0.elapsed_time(a1) / args.active_steps, prob.info()
+            prob.profile(False)
+            prob.sync()
+            cms, _ = prob.profile_read()
+            inf = prob.info()
+            split = {"x_b": cms[0] / args.active_steps, "xt_v_step": cms[1] / args.active_steps,
+                     "scans": cms[2] / args.active_steps, "other_incl_active_set_work": cms[3] / args.active_steps}
+            return a0.elapsed_time(a1) / args.active_steps, inf, split, inf["active_rebuilds"] - r0
 
-        d_ms, _ = timed(False)
-        a_ms, ainfo = timed(True)
+        d_ms, _, d_split, _ = timed(False)
+        a_ms, ainfo, a_split, a_reb = timed(True)
         prob.set_active_set(False)
         cols = ainfo["active_cols"]
         act_bytes = (-(-n // 128) * 128) * (-(-max(cols, 1) // 256) * 256) / 4.0 if cols >= 0 else xb
@@ -464,7 +472,8 @@ def run_ours(args, rank, world):
                   "dense_ms_per_step": d_ms, "active_ms_per_step": a_ms,
                   "dense_iters_per_s": 1e3 / d_ms, "active_iters_per_s": 1e3 / a_ms,
                   "x_b_bytes_per_iteration": {"dense": xb, "active": act_bytes},
-                  "rebuilds": ainfo["active_rebuilds"], "steps": args.active_steps}
+                  "rebuilds": ainfo["active_rebuilds"], "rebuilds_in_timed_steps": a_reb,
+                  "kernel_ms_per_step": {"dense": d_split, "active": a_split}, "steps": args.active_steps}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
