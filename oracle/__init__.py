@@ -23,6 +23,9 @@ the passage of arXiv 2010.16114 (DistStat.jl) it follows:
   and principal components enter unpenalised).
 * ``path`` -- the Section 6 lambda path with the lag stopping rule.
 * ``rank_by_entry`` -- the Section 6 SNP ranking by entry lambda.
+* ``nmf`` / ``nmf_objective`` -- Section 5.1 nonnegative matrix factorization:
+  the multiplicative (Lee-Seung) and alternating projected gradient updates,
+  and ||X - V W||_F^2.
 """
 from __future__ import annotations
 
@@ -89,6 +92,10 @@ def _lib(long_double: bool = False):
         lib.orc_path.restype = ctypes.c_int
         lib.orc_path.argtypes = [_i64, _i64, _p, _p, _i64, _p, _p, _p, _f64, _i64, _p, _f64, _i64, _i64,
                                  ctypes.c_int, _p, _p, _p]
+        lib.orc_nmf_objective.restype = _f64
+        lib.orc_nmf_objective.argtypes = [_i64, _i64, _i64, _p, _p, _p]
+        lib.orc_nmf.restype = ctypes.c_int
+        lib.orc_nmf.argtypes = [_i64, _i64, _i64, _p, _p, _p, _i64, ctypes.c_int, _f64]
         lib.orc_rank_by_entry.restype = _i64
         lib.orc_rank_by_entry.argtypes = [_i64, _i64, _p, _p, _p, _p]
         _loaded[long_double] = lib
@@ -317,3 +324,26 @@ def rank_by_entry(lams, B):
     if cnt < 0:
         raise MemoryError("orc_rank_by_entry")
     return order[:cnt], entry[:p]
+
+
+def nmf_objective(X, V, W) -> float:
+    """||X - V W||_F^2 (Section 5.1), X (m, n), V (m, r), W (r, n)."""
+    X, V, W = _f(X), _f(V), _f(W)
+    m, n = X.shape
+    r = V.shape[1]
+    return _lib().orc_nmf_objective(m, n, r, _ptr(X), _ptr(V), _ptr(W))
+
+
+def nmf(X, V, W, iters: int, algo: str = "mult", eps: float = 1e-10):
+    """``iters`` NMF iterations (Section 5.1): V from W, then W from the new V,
+    by the multiplicative ("mult") or alternating projected gradient ("apg")
+    update.  Returns the updated (V, W)."""
+    X = _f(X)
+    V = _f(V).copy()
+    W = _f(W).copy()
+    m, n = X.shape
+    r = V.shape[1]
+    rc = _lib().orc_nmf(m, n, r, _ptr(X), _ptr(V), _ptr(W), iters, {"mult": 0, "apg": 1}[algo], eps)
+    if rc != 0:
+        raise ValueError(f"orc_nmf returned {rc}")
+    return V, W

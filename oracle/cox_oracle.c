@@ -504,3 +504,115 @@ int64_t orc_rank_by_entry(int64_t p, int64_t L, const double *lams, const double
     free(e);
     return count;
 }
+
+
+/* ---- Section 5.1: nonnegative matrix factorization ------------------------
+ * X (m x n, row-major) ~ V W with V (m x r, row-major: V[i r + c] is entry
+ * (i, c), the paper's Vt transposed) and W (r x n, row-major), both
+ * nonnegative; f(V, W) = ||X - V W||_F^2.  One iteration updates V from the
+ * current W, then W from the new V (Section 5.1 displays and listings):
+ *   multiplicative (Lee-Seung):
+ *     V <- V .* (X W^T) ./ (V (W W^T) + eps)
+ *     W <- W .* (V^T X) ./ ((V^T V) W + eps)
+ *   alternating projected gradient:
+ *     sigma = 1 / (2 ||W W^T||_F^2 + eps),  V <- max(0, V - sigma (V (W W^T) - X W^T))
+ *     tau   = 1 / (2 ||V^T V||_F^2 + eps),  W <- max(0, W - tau ((V^T V) W - V^T X))
+ */
+
+/* f = ||X - V W||_F^2 by the entries of the residual. */
+double orc_nmf_objective(int64_t m, int64_t n, int64_t r, const double *X, const double *V, const double *W)
+{
+    real f = 0;
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            real vw = 0;
+            for (int64_t c = 0; c < r; ++c) vw += (real)V[i * r + c] * (real)W[c * n + j];
+            real d = (real)X[i * n + j] - vw;
+            f += d * d;
+        }
+    return (double)f;
+}
+
+/* iters NMF iterations in place; algo 0 multiplicative, 1 APG.  Returns 0, -1
+ * on bad arguments, -2 on allocation failure. */
+int orc_nmf(int64_t m, int64_t n, int64_t r, const double *X, double *V, double *W, int64_t iters, int algo,
+            double eps)
+{
+    if (m < 1 || n < 1 || r < 1 || iters < 0 || (algo != 0 && algo != 1)) return -1;
+    real *XWt = (real *)malloc((size_t)(m * r) * sizeof(real));  /* X W^T, m x r     */
+    real *WWt = (real *)malloc((size_t)(r * r) * sizeof(real));  /* W W^T, r x r     */
+    real *VtX = (real *)malloc((size_t)(r * n) * sizeof(real));  /* V^T X, r x n     */
+    real *VtV = (real *)malloc((size_t)(r * r) * sizeof(real));  /* V^T V, r x r     */
+    real *Vold = (real *)malloc((size_t)r * sizeof(real));
+    real *Wold = (real *)malloc((size_t)r * sizeof(real));
+    if (!XWt || !WWt || !VtX || !VtV || !Vold || !Wold) {
+        free(XWt); free(WWt); free(VtX); free(VtV); free(Vold); free(Wold);
+        return -2;
+    }
+    for (int64_t t = 0; t < iters; ++t) {
+        /* V from W */
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t c = 0; c < r; ++c) {
+                real s = 0;
+                for (int64_t j = 0; j < n; ++j) s += (real)X[i * n + j] * (real)W[c * n + j];
+                XWt[i * r + c] = s;
+            }
+        real g2 = 0;
+        for (int64_t c = 0; c < r; ++c)
+            for (int64_t d = 0; d < r; ++d) {
+                real s = 0;
+                for (int64_t j = 0; j < n; ++j) s += (real)W[c * n + j] * (real)W[d * n + j];
+                WWt[c * r + d] = s;
+                g2 += s * s;
+            }
+        const real sigma = (real)1 / ((real)2 * g2 + (real)eps);
+        for (int64_t i = 0; i < m; ++i) {
+            for (int64_t c = 0; c < r; ++c) Vold[c] = (real)V[i * r + c];
+            for (int64_t c = 0; c < r; ++c) {
+                real den = 0; /* (V W W^T)_{ic} */
+                for (int64_t d = 0; d < r; ++d) den += Vold[d] * WWt[d * r + c];
+                real v;
+                if (algo == 0) {
+                    v = Vold[c] * XWt[i * r + c] / (den + (real)eps);
+                } else {
+                    v = Vold[c] - sigma * (den - XWt[i * r + c]);
+                    if (v < 0) v = 0;
+                }
+                V[i * r + c] = (double)v;
+            }
+        }
+        /* W from the new V */
+        for (int64_t c = 0; c < r; ++c)
+            for (int64_t j = 0; j < n; ++j) {
+                real s = 0;
+                for (int64_t i = 0; i < m; ++i) s += (real)V[i * r + c] * (real)X[i * n + j];
+                VtX[c * n + j] = s;
+            }
+        real h2 = 0;
+        for (int64_t c = 0; c < r; ++c)
+            for (int64_t d = 0; d < r; ++d) {
+                real s = 0;
+                for (int64_t i = 0; i < m; ++i) s += (real)V[i * r + c] * (real)V[i * r + d];
+                VtV[c * r + d] = s;
+                h2 += s * s;
+            }
+        const real tau = (real)1 / ((real)2 * h2 + (real)eps);
+        for (int64_t j = 0; j < n; ++j) {
+            for (int64_t c = 0; c < r; ++c) Wold[c] = (real)W[c * n + j];
+            for (int64_t c = 0; c < r; ++c) {
+                real den = 0; /* (V^T V W)_{cj} */
+                for (int64_t d = 0; d < r; ++d) den += VtV[c * r + d] * Wold[d];
+                real w;
+                if (algo == 0) {
+                    w = Wold[c] * VtX[c * n + j] / (den + (real)eps);
+                } else {
+                    w = Wold[c] - tau * (den - VtX[c * n + j]);
+                    if (w < 0) w = 0;
+                }
+                W[c * n + j] = (double)w;
+            }
+        }
+    }
+    free(XWt); free(WWt); free(VtX); free(VtV); free(Vold); free(Wold);
+    return 0;
+}

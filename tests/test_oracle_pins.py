@@ -489,3 +489,98 @@ def test_byte_column_products_equal_the_float_ones(orc):
     for mm in (mu, None):
         assert np.array_equal(orc.eta_u8(Xt, mm, beta), orc.eta(X, mm, beta))
         assert np.array_equal(orc.grad_u8(Xt, mm, delta, u), orc.grad(X, mm, delta, u))
+
+
+# --- Section 5.1 NMF: hand examples, theorems, fixed points ------------------
+
+def test_nmf_objective_hand_example(orc):
+    """||X - V W||_F^2 by hand: X = [[1, 2], [3, 4]], V = [[1], [1]], W = [[1, 1]]
+    leave the residual [[0, 1], [2, 3]], so f = 0 + 1 + 4 + 9 = 14."""
+    assert orc.nmf_objective([[1, 2], [3, 4]], [[1], [1]], [[1, 1]]) == 14.0
+
+
+def test_nmf_one_iteration_by_hand(orc):
+    """1 x 1, x = 6, v = 2^0, w = 2, eps = 0.  Multiplicative: v <- v x w / (v w^2)
+    = 12 / 4 = 3, then w <- w v x / (v^2 w) with the new v = 36 / 18 = 2 (so the
+    W step sees the new V: with the old one it would give 6).  APG: sigma =
+    1/(2 w^4) = 1/32, v <- 1 - (4 - 12)/32 = 1.25; tau = 1/(2 v^4) = 256/1250,
+    w <- 2 - tau (v^2 w - v x) = 2 + (256/1250)(35/8) = 2.896."""
+    V, W = orc.nmf([[6.0]], [[1.0]], [[2.0]], 1, "mult", 0.0)
+    assert V[0, 0] == 3.0 and W[0, 0] == 2.0
+    V, W = orc.nmf([[6.0]], [[1.0]], [[2.0]], 1, "apg", 0.0)
+    assert V[0, 0] == 1.25 and abs(W[0, 0] - 2.896) <= 1e-15
+
+
+def _nmf_data(m, n, r, seed, scale=1.0):
+    rng = _rng(seed)
+    return scale * rng.random((m, n)), rng.random((m, r)), rng.random((r, n))
+
+
+def test_nmf_multiplicative_is_monotone(orc):
+    """Lee and Seung's theorem: the multiplicative updates never increase
+    ||X - V W||_F^2 (Section 5.1)."""
+    X, V, W = _nmf_data(37, 29, 5, 3)
+    f = orc.nmf_objective(X, V, W)
+    for _ in range(40):
+        V, W = orc.nmf(X, V, W, 1, "mult", 1e-12)
+        f1 = orc.nmf_objective(X, V, W)
+        assert f1 <= f * (1 + 1e-13)
+        f = f1
+        assert np.all(V >= 0) and np.all(W >= 0)
+
+
+def test_nmf_apg_is_monotone_and_nonnegative(orc):
+    """APG with the Section 5.1 steps: sigma (V W W^T - X W^T) is sigma/2 times the
+    gradient in V, and with ||W W^T||_2 >= 1 the step sigma/2 <= 1/(2 ||W W^T||_2)
+    is at most the inverse Lipschitz constant, so f cannot increase (likewise for
+    W); the projection keeps both factors nonnegative."""
+    X, V, W = _nmf_data(40, 31, 4, 5, scale=3.0)
+    V, W = 2 * V, 2 * W
+    f = orc.nmf_objective(X, V, W)
+    for _ in range(30):
+        Vn, Wn = orc.nmf(X, V, W, 1, "apg", 1e-12)
+        assert np.linalg.norm(W @ W.T, 2) >= 1 and np.linalg.norm(Vn.T @ Vn, 2) >= 1
+        V, W = Vn, Wn
+        f1 = orc.nmf_objective(X, V, W)
+        assert f1 <= f * (1 + 1e-13)
+        f = f1
+        assert np.all(V >= 0) and np.all(W >= 0)
+
+
+def test_nmf_exact_factorization_is_a_fixed_point(orc):
+    """X = V0 W0 with positive factors: X W0^T = V0 (W0 W0^T) and V0^T X =
+    (V0^T V0) W0, so the multiplicative update leaves both factors unchanged
+    (eps = 0) and the APG gradients vanish."""
+    rng = _rng(7)
+    V0, W0 = rng.random((23, 3)) + 0.1, rng.random((3, 19)) + 0.1
+    X = V0 @ W0
+    for algo in ("mult", "apg"):
+        V, W = orc.nmf(X, V0, W0, 3, algo, 0.0)
+        np.testing.assert_allclose(V, V0, rtol=1e-12)
+        np.testing.assert_allclose(W, W0, rtol=1e-12)
+
+
+def test_nmf_zeros_stay_zero(orc):
+    """A zero entry of V or W is a fixed point of its multiplicative update."""
+    X, V, W = _nmf_data(20, 17, 3, 13)
+    V[4, 1] = 0.0
+    W[2, 9] = 0.0
+    V, W = orc.nmf(X, V, W, 50, "mult", 1e-12)
+    assert V[4, 1] == 0.0 and W[2, 9] == 0.0 and np.all(V[np.arange(20) != 4] > 0)
+
+
+def test_nmf_multiplicative_reaches_kkt(orc):
+    """From a strictly positive start on an exactly factorizable X the
+    multiplicative updates approach a KKT point of the nonnegative problem:
+    grad_V f >= 0 and V .* grad_V f = 0 (same for W) up to a tolerance, with the
+    gradients 2 (V W - X) W^T and 2 V^T (V W - X) computed here by numpy."""
+    rng = _rng(11)
+    V0, W0 = rng.random((30, 3)) + 0.2, rng.random((3, 25)) + 0.2
+    X = V0 @ W0
+    V, W = orc.nmf(X, rng.random((30, 3)) + 0.1, rng.random((3, 25)) + 0.1, 20000, "mult", 1e-15)
+    R = V @ W - X
+    gV, gW = 2 * R @ W.T, 2 * V.T @ R
+    assert orc.nmf_objective(X, V, W) <= 1e-6 * np.sum(X * X)
+    tol = 1e-3 * np.abs(X).max() * max(np.abs(V).max(), np.abs(W).max())
+    assert gV.min() >= -tol and gW.min() >= -tol
+    assert np.abs(V * gV).max() <= tol * np.abs(V).max() and np.abs(W * gW).max() <= tol * np.abs(W).max()
