@@ -61,6 +61,12 @@ def parse():
     ap.add_argument("--path-iters", type=int, default=1000,
                     help="iteration cap of the timed cox_path_fit run (0: skip it)")
     ap.add_argument("--path-tol", type=float, default=1e-6)
+    ap.add_argument("--nmf-iters", type=int, default=200,
+                    help="timed iterations per NMF algorithm (Section 5.1, X 10,000 x 10,000); 0 skips it")
+    ap.add_argument("--nmf-m", type=int, default=10_000)
+    ap.add_argument("--nmf-n", type=int, default=10_000)
+    ap.add_argument("--nmf-r", type=int, default=20)
+    ap.add_argument("--nmf-only", action="store_true", help="run and print only the NMF object")
     ap.add_argument("--active-steps", type=int, default=5,
                     help="iterations timed with and without the active-set X B after the path fit (0: skip)")
     return ap.parse_args()
@@ -296,6 +302,78 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ our arm
+NMF_PAPER_1GPU_S = {20: {"mult": 62, "apg": 61}, 40: {"mult": 72, "apg": 80}, 60: {"mult": 83, "apg": 85}}
+
+
+def run_nmf(args, stream):
+    """Section 5.1 NMF on one GPU: X m x n (grid k / 256, exact in bf16), rank r,
+    both algorithms; device-resident iterations timed with CUDA events, the two
+    tensor-core products timed per launch for the roofline, and an end-to-end
+    run from host factors to host factors."""
+    import torch
+
+    import synth
+    from paper_2010_16114_gb300.nmf import NMF
+
+    m, n, r = args.nmf_m, args.nmf_n, args.nmf_r
+    X, V0, W0 = synth.nmf_inputs(m, n, r)
+    h = NMF(X, r)
+    info = h.info()
+    sp = stream.cuda_stream
+    out = {"workload": f"nmf_{m // 1000}k_{n // 1000}k_r{r}", "m": m, "n": n, "r": r,
+           "data": "synthetic: X uniform on the grid k/256 (exact in bf16), V0, W0 uniform [0,1) FP32",
+           "precision": "X bf16; V, W FP32 as 3 bf16 limbs on tcgen05 (kind::f16), FP32 accumulation; "
+                        "Gram matrices FP64",
+           "limb_cols": info["limb_cols"], "stages": info["stages"]}
+    iters = args.nmf_iters
+    for algo in ("mult", "apg"):
+        h.set_factors(V0, W0, sp)
+        h.iterate(3, algo, 1e-10, sp)
+        h.sync(sp)
+        l0 = h.info()["launches"]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.iterate(iters, algo, 1e-10, sp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        h.sync(sp)
+        ms = e0.elapsed_time(e1) / iters
+        f = h.objective(sp)
+        paper = NMF_PAPER_1GPU_S.get(r, {}).get(algo)
+        out[algo] = {"iters_per_s": 1e3 / ms, "ms_per_iter": ms, "iters": iters,
+                     "seconds_per_10000_iters": 10.0 * ms,
+                     "paper_1gpu_seconds_per_10000_iters": paper,
+                     "gpu_launches": int(h.info()["launches"] - l0), "objective_after": f}
+    # roofline of the products: X (bf16) streamed once per launch, the limb panel and partial slots
+    a_ms, b_ms = h.time_products(10, sp)
+    xbytes = 2.0 * m * n
+    pa = xbytes + info["limb_cols"] * n * 2 + 4.0 * r * m
+    pb = xbytes + info["limb_cols"] * m * 2 + 4.0 * r * n
+    peak, peak_kind = measured_peak_hbm()
+    avg_ms = (a_ms + b_ms) / 2
+    achieved = (pa + pb) / 2 / (avg_ms / 1e3) / 1e9
+    flops = 2.0 * 128 * info["limb_cols"] * 64 * (info["units_xwt"] + info["units_vtx"]) / 2
+    out["roofline"] = {"bound": "hbm", "kernel": "k_nmf_gemm (both products)", "achieved": achieved,
+                       "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                       "ms_x_wt": a_ms, "ms_vt_x": b_ms, "bytes_per_launch": (pa + pb) / 2,
+                       "tensor_tflops": flops / (avg_ms / 1e3) / 1e12, "traffic": None}
+    out["product_share_of_iteration"] = (a_ms + b_ms) / out["mult"]["ms_per_iter"]
+    # end to end: host factors in, iterations, host factors out
+    e2e_it = max(1, iters // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h.set_factors(V0, W0, sp)
+    h.iterate(e2e_it, "mult", 1e-10, sp)
+    Vh, Wh = h.factors(sp)
+    e2e_s = time.perf_counter() - t0
+    out["e2e"] = {"value": e2e_it / e2e_s, "unit": "iter/s", "iters": e2e_it,
+                  "h2d_bytes": int(4 * r * (m + n)), "d2h_bytes": int(4 * r * (m + n)),
+                  "timing": "wall clock: nmf_set_factors, nmf_iterate, nmf_get_factors (host arrays)"}
+    h.close()
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -307,6 +385,10 @@ def run_ours(args, rank, world):
     synth.build_device()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.nmf_only:
+        if rank == 0:
+            print(json.dumps({"nmf": run_nmf(args, torch.cuda.current_stream())}), flush=True)
+        return 0
     r = recipe(args)
     n, p, k = r.n, r.p, r.k
     stream = torch.cuda.current_stream()
@@ -480,6 +562,9 @@ def run_ours(args, rank, world):
         cpu = OracleSample(r, args.cpu_sample_cols).baseline(args.cpu_sample_steps)
 
     prob.close()
+    del beta
+    torch.cuda.empty_cache()
+    nmf = run_nmf(args, stream) if (rank == 0 and args.nmf_iters > 0) else None
     if rank != 0:
         return 0
     line = {
@@ -511,6 +596,7 @@ def run_ours(args, rank, world):
         "gpu_launches": int(launches),
         "clocks": ck,
         "fp32_gemv": gemv,
+        "nmf": nmf,
         "objective_last": [float(x) for x in F_last[:4]],
         "setup_s": t_setup,
     }

@@ -581,13 +581,16 @@ int orc_nmf(int64_t m, int64_t n, int64_t r, const double *X, double *V, double 
                 V[i * r + c] = (double)v;
             }
         }
-        /* W from the new V */
-        for (int64_t c = 0; c < r; ++c)
-            for (int64_t j = 0; j < n; ++j) {
-                real s = 0;
-                for (int64_t i = 0; i < m; ++i) s += (real)V[i * r + c] * (real)X[i * n + j];
-                VtX[c * n + j] = s;
+        /* W from the new V.  (V^T X)_cj = sum_i V_ic X_ij, added in increasing i
+         * for every (c, j); the loop over j is innermost so that X is read
+         * along its rows. */
+        for (int64_t c = 0; c < r; ++c) {
+            for (int64_t j = 0; j < n; ++j) VtX[c * n + j] = 0;
+            for (int64_t i = 0; i < m; ++i) {
+                const real v = (real)V[i * r + c];
+                for (int64_t j = 0; j < n; ++j) VtX[c * n + j] += v * (real)X[i * n + j];
             }
+        }
         real h2 = 0;
         for (int64_t c = 0; c < r; ++c)
             for (int64_t d = 0; d < r; ++d) {

@@ -1,4 +1,4 @@
-"""ctypes binding of libcoxgb.so: the C ABI in include/coxgb.h, same names.
+"""ctypes binding of libcoxgb.so: the C ABI in include/coxgb.h and include/nmfgb.h, same names.
 
 Argument marshalling only; every step of the iteration runs in the CUDA
 library.  Loading fails loudly when the library has not been built."""
@@ -40,6 +40,14 @@ EXPORTS = [
     "cox_get_gamma", "cox_set_gamma", "cox_grad_gamma", "cox_prox_step_eta", "cox_last_loss_l1",
     "cox_set_active_set",
 ]
+# every symbol include/nmfgb.h declares
+NMF_EXPORTS = [
+    "nmf_setup", "nmf_destroy", "nmf_set_factors", "nmf_get_factors", "nmf_iterate", "nmf_objective",
+    "nmf_sync", "nmf_get_info", "nmf_time_products",
+]
+NMF_MAX_RANK = 80
+NMF_MULTIPLICATIVE = 0
+NMF_APG = 1
 COX_MAX_COVARIATES = 16
 
 
@@ -70,6 +78,13 @@ class cox_plan(ctypes.Structure):
                 ("ring", ctypes.c_int), ("decoder_groups", ctypes.c_int), ("named_barriers", ctypes.c_int),
                 ("limb_cols", ctypes.c_int), ("tmem_cols", ctypes.c_int), ("smem_bytes", ctypes.c_longlong),
                 ("issue", ctypes.c_int), ("issuers", ctypes.c_int), ("mmas_per_commit", ctypes.c_int)]
+
+
+class nmf_info(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("r", ctypes.c_int), ("limb_cols", ctypes.c_int),
+                ("stages", ctypes.c_int), ("sm_count", ctypes.c_int), ("grid_xwt", ctypes.c_int),
+                ("grid_vtx", ctypes.c_int), ("units_xwt", ctypes.c_int64), ("units_vtx", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("launches", ctypes.c_int64)]
 
 
 class CoxError(RuntimeError):
@@ -150,6 +165,24 @@ def load(path: str | None = None):
     for nm in ("cox_get_gamma", "cox_set_gamma", "cox_grad_gamma"):
         getattr(lib, nm).restype = I
         getattr(lib, nm).argtypes = [P, P, I]
+    lib.nmf_setup.restype = I
+    lib.nmf_setup.argtypes = [P, I64, I64, I, I, ctypes.POINTER(P)]
+    lib.nmf_destroy.restype = I
+    lib.nmf_destroy.argtypes = [P]
+    lib.nmf_set_factors.restype = I
+    lib.nmf_set_factors.argtypes = [P, P, P, P]
+    lib.nmf_get_factors.restype = I
+    lib.nmf_get_factors.argtypes = [P, P, P, P]
+    lib.nmf_iterate.restype = I
+    lib.nmf_iterate.argtypes = [P, I, I64, D, P]
+    lib.nmf_objective.restype = I
+    lib.nmf_objective.argtypes = [P, ctypes.POINTER(D), P]
+    lib.nmf_sync.restype = I
+    lib.nmf_sync.argtypes = [P, P]
+    lib.nmf_get_info.restype = I
+    lib.nmf_get_info.argtypes = [P, ctypes.POINTER(nmf_info)]
+    lib.nmf_time_products.restype = I
+    lib.nmf_time_products.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(D), P]
     lib.cox_strerror.restype = ctypes.c_char_p
     lib.cox_strerror.argtypes = [I]
     _lib = lib
@@ -313,3 +346,39 @@ def cox_last_loss_l1(h, f_ptr, l1_ptr, k, stream_ptr):
 
 def cox_set_active_set(h, on: int) -> int:
     return load().cox_set_active_set(h, on)
+
+
+def nmf_setup(X_ptr, m: int, n: int, r: int, device: int, out_ptr) -> int:
+    return load().nmf_setup(X_ptr, m, n, r, device, out_ptr)
+
+
+def nmf_destroy(h) -> int:
+    return load().nmf_destroy(h)
+
+
+def nmf_set_factors(h, V_ptr, W_ptr, stream_ptr) -> int:
+    return load().nmf_set_factors(h, V_ptr, W_ptr, stream_ptr)
+
+
+def nmf_get_factors(h, V_ptr, W_ptr, stream_ptr) -> int:
+    return load().nmf_get_factors(h, V_ptr, W_ptr, stream_ptr)
+
+
+def nmf_iterate(h, algo: int, iters: int, eps: float, stream_ptr) -> int:
+    return load().nmf_iterate(h, algo, iters, eps, stream_ptr)
+
+
+def nmf_objective(h, f_ptr, stream_ptr) -> int:
+    return load().nmf_objective(h, f_ptr, stream_ptr)
+
+
+def nmf_sync(h, stream_ptr) -> int:
+    return load().nmf_sync(h, stream_ptr)
+
+
+def nmf_get_info(h, info_ptr) -> int:
+    return load().nmf_get_info(h, info_ptr)
+
+
+def nmf_time_products(h, reps: int, a_ptr, b_ptr, stream_ptr) -> int:
+    return load().nmf_time_products(h, reps, a_ptr, b_ptr, stream_ptr)

@@ -1,4 +1,4 @@
-"""Build libcoxgb.so (the C-ABI solver library) in-tree for sm_103a with nvcc."""
+"""Build libcoxgb.so (the C-ABI library: the Cox solver and the NMF) in-tree for sm_103a with nvcc."""
 from __future__ import annotations
 
 import hashlib
@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libcoxgb.so")
-SOURCES = ["api.cu", "setup.cu", "scans.cu", "gemm_tc.cu", "gemv.cu", "path.cu", "active.cu"]
+SOURCES = ["api.cu", "setup.cu", "scans.cu", "gemm_tc.cu", "gemv.cu", "path.cu", "active.cu", "nmf.cu"]
 HEADERS = ["internal.h", "ptx.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing",
@@ -22,8 +22,9 @@ def _digest(extra: list[str]) -> str:
     for f in SOURCES + HEADERS:
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(fh.read())
-    with open(os.path.join(ROOT, "include", "coxgb.h"), "rb") as fh:
-        h.update(fh.read())
+    for hdr in ("coxgb.h", "nmfgb.h"):
+        with open(os.path.join(ROOT, "include", hdr), "rb") as fh:
+            h.update(fh.read())
     h.update(" ".join(ARCH + CFLAGS + extra).encode())
     return h.hexdigest()
 

@@ -1,0 +1,1033 @@
+// nmf.cu -- nonnegative matrix factorisation X ~ V W (arXiv 2010.16114,
+// Section 5.1): the multiplicative (Lee-Seung) and the alternating projected
+// gradient (APG) iterations on one GB300.
+//
+// An iteration is four kernels:
+//   k_nmf_gemm    P = X W^T   (m x r)   tcgen05 kind::f16, A = X row-major
+//   k_nmf_update  V from P and W W^T; limbs of V; Gram V^T V (FP64)
+//   k_nmf_gemm    Q = X^T V   (n x r)   A = X column-major
+//   k_nmf_update  W from Q and V^T V; limbs of W; Gram W W^T (FP64)
+// Both updates have one form.  With F a factor held r x R (V^T, or W), G the
+// Gram matrix of the other factor and P the product of X with it,
+//   (V W W^T)_ic = sum_d G_cd F_di  and  (V^T V W)_cj = sum_d G_cd F_dj
+// (G symmetric), so
+//   multiplicative: F_ci <- F_ci P_ci / (sum_d G_cd F_di + eps)
+//   APG:            F_ci <- max(0, F_ci - s (sum_d G_cd F_di - P_ci)),
+//                   s = 1 / (2 ||G||_F^2 + eps).
+//
+// Products.  X is stored in bf16 twice (row-major for X W^T, column-major for
+// X^T V), so both are K-major A operands: TMA loads 128-row x 64-column boxes
+// (128-byte rows, 128-byte swizzle), zero-filled past the matrix edges.  The
+// factor enters as the B operand in three bf16 limbs per value
+// (f = h0 + h1 + h2, h_l = RN_bf16 of the remainder; exact for FP32 f), rows
+// l rp + c of an N = 3 rp (rounded up to 16) panel, rp = r rounded up to 8 so
+// that every limb's columns start 8-aligned in TMEM, and the tensor cores
+// accumulate in FP32 in Tensor Memory.  Per CTA (one per SM): a TMA warp fills
+// a ring of shared-memory stages, one thread issues four M128 x N x K16 MMAs
+// per 64-wide K chunk into one of two TMEM accumulators, and four epilogue
+// warps (one per TMEM lane quarter) add the three limb columns of each value
+// and store the CTA's partial of the row tile.  Work split: units = (row tile,
+// K chunk) in row-tile order; CTA c takes units [c L, (c+1) L), so a row tile
+// is cut between at most a few CTAs, each leaving a partial in its own slot;
+// the update kernel adds the slots in slot order (deterministic).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+#include "ptx.cuh"
+#include "../../include/nmfgb.h"
+
+struct nmf_handle;
+
+namespace coxgb {
+namespace {
+
+constexpr int NT = 128;                 // rows per tile (MMA M)
+constexpr int NK = 64;                  // K per chunk: 64 bf16 = one 128-byte swizzled row
+constexpr int A_BYTES = NT * NK * 2;    // 16 KB A box per stage
+constexpr int GEMM_THREADS = 192;       // TMA warp, MMA warp, four epilogue warps
+constexpr int MAX_STAGES = 8;
+constexpr int UPD_THREADS = 128;        // one thread per factor column of a row tile
+constexpr long long NMF_DRAIN = 4000000000LL;  // ~2 s: copies and MMAs always finish
+__device__ int g_nmf_never = 0;                // abort flag of drain waits: never raised
+
+enum : int { NMF_ERR_TIMEOUT = 1, NMF_ERR_NONFINITE = 2, NMF_ERR_NEGATIVE = 4 };
+
+struct GemmArgs {
+    int KC;             // K chunks per row tile
+    int r, rp, NP;      // rank; r rounded up to 8; N of the MMA (3 rp rounded up to 16)
+    int S, stage;       // shared-memory stages; bytes per stage (A box + NP x 128 B panel)
+    int tcols;          // TMEM columns allocated
+    uint32_t idesc;
+    int64_t units, L;   // (row tile, chunk) units; units per CTA
+    int SL;             // partial slots per row tile
+    float *part;        // [tile][slot][r][128] FP32
+    long long wait_limit;
+    int *err;
+};
+
+__device__ __forceinline__ void nmf_fail(volatile int *abort_sm, int *err)
+{
+    if (!*abort_sm) {
+        *abort_sm = 1;
+        atomicOr(err, NMF_ERR_TIMEOUT);
+    }
+}
+
+// Pipeline hand-offs (S stages, two accumulators a = segment index mod 2):
+//   full[s]   TMA transaction bytes                    producer -> issuer
+//   empty[s]  tcgen05.commit after the stage's MMAs    issuer   -> producer
+//   accf[a]   tcgen05.commit at a segment end          issuer   -> epilogue
+//   acce[a]   four arrivals once the epilogue read a   epilogue -> issuer
+// Every waiter waits for the completions of a barrier in order, and the
+// completion before the awaited one is always one it waited for itself (the
+// producer's wait on empty[s] for unit i - S follows its wait for unit i - 2S;
+// the issuer's wait on full[s] for unit i follows the one for unit i - S; on
+// accf[a] / acce[a] for segment q, the waits for segment q - 2), so no parity
+// wait can return a phase early.  A segment is the CTA's run of units in one
+// row tile.
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+    k_nmf_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs P)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                ~static_cast<uintptr_t>(1023));
+    const int S = P.S, STAGE = P.stage;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S * STAGE);
+    const uint32_t full0 = smem_addr(bars);
+    const uint32_t empty0 = full0 + 8 * S;
+    const uint32_t accf0 = empty0 + 8 * S;
+    const uint32_t acce0 = accf0 + 16;
+    const uint32_t drainb = acce0 + 16;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 5);
+    volatile int *abort_sm = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(accf0 + 8 * a, 1);
+            mbar_init(acce0 + 8 * a, 4);
+        }
+        mbar_init(drainb, 1);
+        *abort_sm = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_addr(tmem_slot), static_cast<uint32_t>(P.tcols));
+        tmem_relinquish();
+    }
+    if (threadIdx.x == 32) {
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_slot;
+
+    const int64_t u0 = static_cast<int64_t>(blockIdx.x) * P.L;
+    const int64_t u1 = min(u0 + P.L, P.units);
+    const int64_t nu = u1 > u0 ? u1 - u0 : 0;
+    const int KC = P.KC;
+    const long long lim = P.wait_limit;
+    const int g0 = static_cast<int>(u0 / KC), kc0 = static_cast<int>(u0 - static_cast<int64_t>(g0) * KC);
+
+    if (warp == 0) {
+        // ---------------- TMA producer (lane 0) ----------------
+        if (lane == 0) {
+            int g = g0, kc = kc0, s = 0;
+            uint32_t ph = 0;
+            int64_t issued = 0;
+            for (int64_t i = 0; i < nu; ++i) {
+                if (i >= S && !mbar_wait(empty0 + 8 * s, ph ^ 1u, lim, abort_sm)) {
+                    nmf_fail(abort_sm, P.err);
+                    break;
+                }
+                const uint32_t st = smem_addr(smem + static_cast<size_t>(s) * STAGE);
+                const uint32_t fb = full0 + 8 * s;
+                mbar_arrive_expect_tx(fb, static_cast<uint32_t>(STAGE));
+                tma_load_2d(st, &tmA, kc * NK, g * NT, fb);
+                tma_load_2d(st + A_BYTES, &tmB, kc * NK, 0, fb);
+                ++issued;
+                if (++s == S) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+                if (++kc == KC) {
+                    kc = 0;
+                    ++g;
+                }
+            }
+            // every load issued has landed before the CTA may exit
+            for (int64_t i = issued > S ? issued - S : 0; i < issued; ++i)
+                mbar_wait(full0 + 8 * static_cast<uint32_t>(i % S), static_cast<uint32_t>((i / S) & 1), NMF_DRAIN,
+                          &g_nmf_never);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (lane 0) ----------------
+        if (lane == 0) {
+            const uint64_t descA = smem_desc_sw128(smem_addr(smem));
+            const uint64_t descB = smem_desc_sw128(smem_addr(smem + A_BYTES));
+            int s = 0, kc = kc0, q = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (int64_t i = 0; ok && i < nu; ++q) {
+                const int64_t len = min(static_cast<int64_t>(KC - kc), nu - i);
+                const int a = q & 1;
+                if (q >= 2 && !mbar_wait(acce0 + 8 * a, static_cast<uint32_t>(((q - 2) >> 1) & 1), lim, abort_sm)) {
+                    nmf_fail(abort_sm, P.err);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tbase + static_cast<uint32_t>(a * P.NP);
+                for (int64_t e = 0; e < len; ++e) {
+                    if (!mbar_wait(full0 + 8 * s, ph, lim, abort_sm)) {
+                        nmf_fail(abort_sm, P.err);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t off = static_cast<uint64_t>(s) * static_cast<uint64_t>(STAGE >> 4);
+#pragma unroll
+                    for (int kk = 0; kk < NK / 16; ++kk)  // K = 16 per MMA: 32 bytes of every row
+                        mma_ss_f16(d, descA + off + 2 * kk, descB + off + 2 * kk, P.idesc,
+                                   (e > 0 || kk > 0) ? 1u : 0u);
+                    mma_commit(empty0 + 8 * s);
+                    if (++s == S) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(accf0 + 8 * a);
+                i += len;
+                kc = 0;
+            }
+            mma_commit(drainb);
+            mbar_wait(drainb, 0, NMF_DRAIN, &g_nmf_never);
+        }
+    } else {
+        // ---------------- epilogue: warps 2..5, TMEM lane quarter warp % 4 ----------------
+        const int quarter = warp & 3;
+        const int row = 32 * quarter + lane;
+        const uint32_t lane_base = tbase + (static_cast<uint32_t>(32 * quarter) << 16);
+        const int r = P.r;
+        int g = g0, kc = kc0;
+        for (int64_t i = 0, q = 0; i < nu; ++q) {
+            const int64_t len = min(static_cast<int64_t>(KC - kc), nu - i);
+            const int a = static_cast<int>(q & 1);
+            if (!__all_sync(0xffffffffu, mbar_wait(accf0 + 8 * a, static_cast<uint32_t>((q >> 1) & 1), lim, abort_sm))) {
+                if (lane == 0) nmf_fail(abort_sm, P.err);
+                break;
+            }
+            tc_fence_after();
+            const int64_t slot = static_cast<int64_t>(blockIdx.x) - (static_cast<int64_t>(g) * KC) / P.L;
+            float *dst = P.part + ((static_cast<int64_t>(g) * P.SL + slot) * r) * NT + row;
+            const uint32_t acc = lane_base + static_cast<uint32_t>(a * P.NP);
+            for (int c0 = 0; c0 < r; c0 += 8) {
+                uint32_t h0[8], h1[8], h2[8];
+                tmem_ld_32x32b_x8(acc + static_cast<uint32_t>(c0), h0);
+                tmem_ld_32x32b_x8(acc + static_cast<uint32_t>(P.rp + c0), h1);
+                tmem_ld_32x32b_x8(acc + static_cast<uint32_t>(2 * P.rp + c0), h2);
+                tmem_wait_ld();
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    if (c0 + e < r)
+                        dst[static_cast<int64_t>(c0 + e) * NT] =
+                            (__uint_as_float(h0[e]) + __uint_as_float(h1[e])) + __uint_as_float(h2[e]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce0 + 8 * a);
+            i += len;
+            kc = 0;
+            ++g;
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tbase, static_cast<uint32_t>(P.tcols));
+    }
+}
+
+struct UpdArgs {
+    int r, rp, mode, algo;   // mode 1: update from the product; 0: limbs and Gram of F only
+    int64_t R;               // factor columns (m for V, n for W)
+    float *F;                // r x R, row c at c R
+    __nv_bfloat16 *limb;     // NP x ldl: row l rp + c holds limb l of F row c
+    int64_t ldl;
+    const float *part;       // product partials of this side
+    int SL, KC;
+    int64_t L;
+    const float *Gin;        // r x r Gram of the other factor
+    const double *fro_in;    // its squared Frobenius norm
+    double eps;
+    float *gpart;            // [block][pairs of 4 x 4 blocks][16]
+    int *counter;            // blocks done (reset by the last block)
+    double *G64;             // r x r Gram of the new F, FP64
+    float *G32;              // and in FP32
+    double *fro_out;
+    int *err;
+};
+
+// Split f into three bf16 limbs, f = h0 + h1 + h2 (exact for an FP32 f).
+__device__ __forceinline__ void split_bf16(float f, __nv_bfloat16 *h)
+{
+    h[0] = __float2bfloat16_rn(f);
+    const float r1 = f - __bfloat162float(h[0]);
+    h[1] = __float2bfloat16_rn(r1);
+    h[2] = __float2bfloat16_rn(r1 - __bfloat162float(h[1]));
+}
+
+// One row tile of a factor: thread t owns column i = 128 g + t of F.
+// Shared memory: the new F ([j][RP], RP = r rounded up to 4) for the Gram
+// products, G (r x r) and the old F ([c][129], conflict-free per c).
+__global__ void __launch_bounds__(UPD_THREADS) k_nmf_update(const UpdArgs A)
+{
+    extern __shared__ float4 sh4[];
+    const int r = A.r, t = threadIdx.x;
+    const int RP = (r + 3) & ~3;
+    float *Fn = reinterpret_cast<float *>(sh4);  // rows of RP floats: 16-byte aligned for float4 loads
+    float *Gs = Fn + UPD_THREADS * RP;
+    float *Fo = Gs + r * r;
+    const int64_t g = blockIdx.x;
+    const int64_t i = g * UPD_THREADS + t;
+    const bool valid = i < A.R;
+    if (A.mode)
+        for (int e = t; e < r * r; e += UPD_THREADS) Gs[e] = A.Gin[e];
+    for (int c = 0; c < r; ++c) Fo[c * (UPD_THREADS + 1) + t] = valid ? A.F[c * A.R + i] : 0.f;
+    for (int c = r; c < RP; ++c) Fn[t * RP + c] = 0.f;
+    __syncthreads();
+
+    bool bad = false;
+    if (A.mode) {
+        const float s = static_cast<float>(1.0 / (2.0 * *A.fro_in + A.eps));
+        const float eps = static_cast<float>(A.eps);
+        const int64_t first = (g * A.KC) / A.L, last = (g * A.KC + A.KC - 1) / A.L;
+        const int ns = static_cast<int>(last - first + 1);
+        const float *pp = A.part + (g * A.SL * r) * NT + t;
+        for (int c = 0; c < r; ++c) {
+            double acc = 0.0;
+            for (int sl = 0; sl < ns; ++sl) acc += static_cast<double>(pp[(static_cast<int64_t>(sl) * r + c) * NT]);
+            const float pc = static_cast<float>(acc);
+            float den = 0.f;
+            for (int d = 0; d < r; ++d) den = fmaf(Gs[c * r + d], Fo[d * (UPD_THREADS + 1) + t], den);
+            const float old = Fo[c * (UPD_THREADS + 1) + t];
+            float v = A.algo == NMF_MULTIPLICATIVE ? old * pc / (den + eps) : fmaxf(0.f, old - s * (den - pc));
+            if (!valid) v = 0.f;
+            bad |= !isfinite(v);
+            Fn[t * RP + c] = v;
+        }
+    } else {
+        for (int c = 0; c < r; ++c) Fn[t * RP + c] = Fo[c * (UPD_THREADS + 1) + t];
+    }
+    if (bad) atomicOr(A.err, NMF_ERR_NONFINITE);
+    if (valid) {
+        for (int c = 0; c < r; ++c) {
+            const float v = Fn[t * RP + c];
+            if (A.mode) A.F[c * A.R + i] = v;
+            __nv_bfloat16 h[3];
+            split_bf16(v, h);
+#pragma unroll
+            for (int l = 0; l < 3; ++l) A.limb[static_cast<int64_t>(l * A.rp + c) * A.ldl + i] = h[l];
+        }
+    }
+    __syncthreads();
+
+    // Gram partial of the new F over this tile's 128 columns, in 4 x 4 blocks
+    // (cb <= db) of the r x r matrix: 8 shared loads per 16 multiply-adds.
+    const int RB = RP / 4, NBP = RB * (RB + 1) / 2;
+    for (int bp = t; bp < NBP; bp += UPD_THREADS) {
+        int cb = 0, rem = bp;
+        while (rem >= RB - cb) {
+            rem -= RB - cb;
+            ++cb;
+        }
+        const int db = cb + rem;
+        float acc[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[e] = 0.f;
+        for (int j = 0; j < UPD_THREADS; ++j) {
+            const float4 x = *reinterpret_cast<const float4 *>(Fn + j * RP + 4 * cb);
+            const float4 y = *reinterpret_cast<const float4 *>(Fn + j * RP + 4 * db);
+            const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[4 * a + b] = fmaf(xv[a], yv[b], acc[4 * a + b]);
+        }
+        float *dst = A.gpart + (g * NBP + bp) * 16;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) dst[e] = acc[e];
+    }
+
+    // the last block adds the partials in block order (FP64) and writes G
+    __shared__ int is_last;
+    __shared__ double red[UPD_THREADS];
+    __threadfence();
+    __syncthreads();
+    if (t == 0) is_last = atomicAdd(A.counter, 1) == static_cast<int>(gridDim.x) - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double fro = 0.0;
+    for (int bp = t; bp < NBP; bp += UPD_THREADS) {
+        int cb = 0, rem = bp;
+        while (rem >= RB - cb) {
+            rem -= RB - cb;
+            ++cb;
+        }
+        const int db = cb + rem;
+        for (int e = 0; e < 16; ++e) {
+            const int c = 4 * cb + e / 4, d = 4 * db + e % 4;
+            if (c >= r || d >= r || (cb == db && d < c)) continue;
+            double s = 0.0;
+            for (unsigned b = 0; b < gridDim.x; ++b) s += static_cast<double>(__ldcg(A.gpart + (b * NBP + bp) * 16 + e));
+            A.G64[c * r + d] = s;
+            A.G64[d * r + c] = s;
+            A.G32[c * r + d] = static_cast<float>(s);
+            A.G32[d * r + c] = static_cast<float>(s);
+            fro += (c == d ? 1.0 : 2.0) * s * s;
+        }
+    }
+    red[t] = fro;
+    __syncthreads();
+    for (int w = UPD_THREADS / 2; w > 0; w >>= 1) {
+        if (t < w) red[t] += red[t + w];
+        __syncthreads();
+    }
+    if (t == 0) {
+        *A.fro_out = red[0];
+        *A.counter = 0;
+    }
+}
+
+struct FitArgs {
+    int r;
+    int64_t R;               // m
+    const float *F;          // V^T, r x m
+    const float *part;
+    int SL, KC;
+    int64_t L;
+    double *opart;           // per block
+    int *counter;
+    const double *GV, *GW;
+    double xx;
+    double *out;
+};
+
+// <V, X W^T> per row tile in FP64, then (last block) the objective by the
+// identity ||X - V W||^2 = ||X||^2 - 2 <V, X W^T> + <V^T V, W W^T>.
+__global__ void __launch_bounds__(UPD_THREADS) k_nmf_fit(const FitArgs A)
+{
+    __shared__ double red[UPD_THREADS];
+    __shared__ int is_last;
+    const int r = A.r, t = threadIdx.x;
+    const int64_t g = blockIdx.x, i = g * UPD_THREADS + t;
+    double s = 0.0;
+    if (i < A.R) {
+        const int64_t first = (g * A.KC) / A.L, last = (g * A.KC + A.KC - 1) / A.L;
+        const int ns = static_cast<int>(last - first + 1);
+        const float *pp = A.part + (g * A.SL * r) * NT + t;
+        for (int c = 0; c < r; ++c) {
+            double acc = 0.0;
+            for (int sl = 0; sl < ns; ++sl) acc += static_cast<double>(pp[(static_cast<int64_t>(sl) * r + c) * NT]);
+            s += static_cast<double>(A.F[c * A.R + i]) * acc;
+        }
+    }
+    red[t] = s;
+    __syncthreads();
+    for (int w = UPD_THREADS / 2; w > 0; w >>= 1) {
+        if (t < w) red[t] += red[t + w];
+        __syncthreads();
+    }
+    if (t == 0) A.opart[g] = red[0];
+    __threadfence();
+    __syncthreads();
+    if (t == 0) is_last = atomicAdd(A.counter, 1) == static_cast<int>(gridDim.x) - 1;
+    __syncthreads();
+    if (!is_last || t != 0) return;
+    __threadfence();
+    double vp = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) vp += __ldcg(A.opart + b);
+    double tr = 0.0;
+    for (int e = 0; e < r * r; ++e) tr += A.GV[e] * A.GW[e];
+    *A.out = A.xx - 2.0 * vp + tr;
+    *A.counter = 0;
+}
+
+// X rows [r0, r0 + nr) (FP32, nr x n) -> bf16 in both orders; 32 x 32 tiles
+// through shared memory; squares of the bf16 values summed per block (FP64).
+__global__ void k_nmf_pack(const float *__restrict__ x, int64_t r0, int64_t nr, int64_t n, __nv_bfloat16 *Xr,
+                           int64_t ldr, __nv_bfloat16 *Xc, int64_t ldc, double *sq, int *err)
+{
+    __shared__ float tile[32][33];
+    __shared__ double red[256];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t c0 = static_cast<int64_t>(blockIdx.x) * 32, rr0 = static_cast<int64_t>(blockIdx.y) * 32;
+    double s = 0.0;
+    bool bad = false;
+    for (int k = 0; k < 32; k += 8) {
+        const int64_t rr = rr0 + ty + k, c = c0 + tx;
+        float v = 0.f;
+        if (rr < nr && c < n) {
+            const float f = x[rr * n + c];
+            bad |= !(f >= 0.f) || !isfinite(f);
+            const __nv_bfloat16 b = __float2bfloat16_rn(f);
+            Xr[(r0 + rr) * ldr + c] = b;
+            v = __bfloat162float(b);
+            s += static_cast<double>(v) * static_cast<double>(v);
+        }
+        tile[ty + k][tx] = v;
+    }
+    __syncthreads();
+    for (int k = 0; k < 32; k += 8) {
+        const int64_t c = c0 + ty + k, rr = rr0 + tx;
+        if (rr < nr && c < n) Xc[c * ldc + r0 + rr] = __float2bfloat16_rn(tile[tx][ty + k]);
+    }
+    if (bad) atomicOr(err, NMF_ERR_NEGATIVE);
+    const int tid = ty * 32 + tx;
+    red[tid] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w) red[tid] += red[tid + w];
+        __syncthreads();
+    }
+    if (tid == 0) sq[static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x] = red[0];
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn nmf_encoder()
+{
+    static EncodeFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+    }
+    return fn;
+}
+
+// 2-D bf16 map: inner extent `inner` (K), `outer` rows, row pitch ld elements
+// (a multiple of 8: 16-byte strides), box 64 x box_rows, 128-byte swizzle.
+bool encode_bf16(CUtensorMap *m, const void *base, int64_t inner, int64_t outer, int64_t ld, int box_rows)
+{
+    EncodeFn enc = nmf_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(outer)};
+    const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
+    const cuuint32_t box[2] = {static_cast<cuuint32_t>(NK), static_cast<cuuint32_t>(box_rows)};
+    const cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DevGuard()
+    {
+        int cur;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int64_t rup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+} // namespace
+
+// One product: A (rows x K, bf16, K-major) times the limb panel B (NP x K).
+struct NmfSide {
+    CUtensorMap tmA, tmB;
+    GemmArgs g;
+    int grid = 0;
+    int MT = 0;         // row tiles
+    int64_t rows = 0;   // m for X W^T, n for X^T V
+    size_t smem = 0;
+};
+
+} // namespace coxgb
+
+using coxgb::NmfSide;
+
+struct nmf_handle {
+    int dev = 0, sms = 0;
+    int64_t m = 0, n = 0;
+    int r = 0, rp = 0, NP = 0;
+    cudaStream_t cap = nullptr;   // capture stream
+    __nv_bfloat16 *Xr = nullptr, *Xc = nullptr, *Vl = nullptr, *Wl = nullptr;
+    int64_t ldr = 0, ldc = 0, ldm = 0, ldn = 0;
+    float *Vt = nullptr, *W = nullptr;
+    float *part1 = nullptr, *part2 = nullptr;
+    NmfSide s1, s2;               // X W^T, X^T V
+    float *GV32 = nullptr, *GW32 = nullptr, *gpart = nullptr;
+    double *GV64 = nullptr, *GW64 = nullptr, *froV = nullptr, *froW = nullptr, *opart = nullptr, *fobj = nullptr;
+    int *counters = nullptr, *err = nullptr;
+    double xx = 0.0;
+    long long wait_cycles = 0;
+    int64_t device_bytes = 0, launches = 0;
+    cudaGraphExec_t exec = nullptr;
+    int g_algo = -1;
+    double g_eps = -1.0;
+    std::vector<void *> allocs;
+};
+
+namespace coxgb {
+namespace {
+
+int nmf_alloc(nmf_handle *h, void **p, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? COX_ERR_OOM : COX_ERR_CUDA;
+    }
+    h->allocs.push_back(*p);
+    h->device_bytes += static_cast<int64_t>(bytes);
+    return COX_OK;
+}
+
+int plan_side(nmf_handle *h, NmfSide &sd, const __nv_bfloat16 *A, int64_t rows, int64_t K, int64_t ldA,
+              const __nv_bfloat16 *B, int64_t ldB, float **part)
+{
+    sd.rows = rows;
+    sd.MT = static_cast<int>((rows + NT - 1) / NT);
+    GemmArgs &g = sd.g;
+    g.KC = static_cast<int>((K + NK - 1) / NK);
+    g.r = h->r;
+    g.rp = h->rp;
+    g.NP = h->NP;
+    g.stage = A_BYTES + h->NP * 128;
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev) != cudaSuccess) return COX_ERR_CUDA;
+    g.S = std::min(MAX_STAGES, (optin - 2048) / g.stage);
+    if (g.S < 2) return COX_ERR_UNSUPPORTED;
+    const int need = h->NP + 3 * h->rp;  // second accumulator: its last limb's columns end before NP + 3 rp
+    int tc = 32;
+    while (tc < need) tc *= 2;
+    if (tc > 512) return COX_ERR_ARG;
+    g.tcols = tc;
+    g.idesc = idesc_bf16_f32(NT, h->NP);
+    g.units = static_cast<int64_t>(sd.MT) * g.KC;
+    g.L = (g.units + h->sms - 1) / h->sms;
+    sd.grid = static_cast<int>((g.units + g.L - 1) / g.L);
+    int SL = 1;
+    for (int64_t t = 0; t < sd.MT; ++t) {
+        const int64_t f = t * g.KC / g.L, l = (t * g.KC + g.KC - 1) / g.L;
+        SL = std::max<int>(SL, static_cast<int>(l - f + 1));
+    }
+    g.SL = SL;
+    g.wait_limit = h->wait_cycles;
+    g.err = h->err;
+    COX_TRY(nmf_alloc(h, reinterpret_cast<void **>(part),
+                      static_cast<size_t>(sd.MT) * SL * h->r * NT * sizeof(float)));
+    g.part = *part;
+    sd.smem = 1024 + static_cast<size_t>(g.S) * g.stage + 256;
+    if (!encode_bf16(&sd.tmA, A, K, rows, ldA, NT)) return COX_ERR_CUDA;
+    if (!encode_bf16(&sd.tmB, B, K, h->NP, ldB, h->NP)) return COX_ERR_CUDA;
+    return COX_OK;
+}
+
+int launch_gemm(nmf_handle *h, const NmfSide &sd, cudaStream_t st)
+{
+    k_nmf_gemm<<<sd.grid, GEMM_THREADS, sd.smem, st>>>(sd.tmA, sd.tmB, sd.g);
+    ++h->launches;
+    return cudaGetLastError() == cudaSuccess ? COX_OK : COX_ERR_CUDA;
+}
+
+size_t upd_smem(int r) { return static_cast<size_t>(r * r + r * (UPD_THREADS + 1) + UPD_THREADS * ((r + 3) & ~3)) * sizeof(float); }
+
+// side 0: V from X W^T (rows m); side 1: W from X^T V (rows n)
+int launch_update(nmf_handle *h, int side, int mode, int algo, double eps, cudaStream_t st)
+{
+    UpdArgs a;
+    const NmfSide &sd = side == 0 ? h->s1 : h->s2;
+    a.r = h->r;
+    a.rp = h->rp;
+    a.mode = mode;
+    a.algo = algo;
+    a.R = side == 0 ? h->m : h->n;
+    a.F = side == 0 ? h->Vt : h->W;
+    a.limb = side == 0 ? h->Vl : h->Wl;
+    a.ldl = side == 0 ? h->ldm : h->ldn;
+    a.part = sd.g.part;
+    a.SL = sd.g.SL;
+    a.KC = sd.g.KC;
+    a.L = sd.g.L;
+    a.Gin = side == 0 ? h->GW32 : h->GV32;
+    a.fro_in = side == 0 ? h->froW : h->froV;
+    a.eps = eps;
+    a.gpart = h->gpart;
+    a.counter = h->counters + side;
+    a.G64 = side == 0 ? h->GV64 : h->GW64;
+    a.G32 = side == 0 ? h->GV32 : h->GW32;
+    a.fro_out = side == 0 ? h->froV : h->froW;
+    a.err = h->err;
+    const unsigned blocks = static_cast<unsigned>((a.R + UPD_THREADS - 1) / UPD_THREADS);
+    k_nmf_update<<<blocks, UPD_THREADS, upd_smem(h->r), st>>>(a);
+    ++h->launches;
+    return cudaGetLastError() == cudaSuccess ? COX_OK : COX_ERR_CUDA;
+}
+
+int check_err(nmf_handle *h, cudaStream_t st)
+{
+    int e = 0;
+    COX_CUDA(cudaMemcpyAsync(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    COX_CUDA(cudaStreamSynchronize(st));
+    if (e) {
+        COX_CUDA(cudaMemsetAsync(h->err, 0, sizeof(int), st));
+        COX_CUDA(cudaStreamSynchronize(st));
+    }
+    if (e & NMF_ERR_TIMEOUT) return COX_ERR_TIMEOUT;
+    if (e & NMF_ERR_NONFINITE) return COX_ERR_NONFINITE;
+    if (e & NMF_ERR_NEGATIVE) return COX_ERR_ARG;
+    return COX_OK;
+}
+
+void release(nmf_handle *h)
+{
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    for (void *p : h->allocs) cudaFree(p);
+    delete h;
+}
+
+int setup_impl(const float *X, int64_t m, int64_t n, int r, int device, nmf_handle **out)
+{
+    int dev = device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return COX_ERR_CUDA;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return COX_ERR_UNSUPPORTED;
+    }
+    if (prop.major != 10 || prop.minor != 3) return COX_ERR_UNSUPPORTED;
+    DevGuard guard(dev);
+    nmf_handle *h = new nmf_handle();
+    int rc = COX_OK;
+    do {
+        h->dev = dev;
+        h->sms = prop.multiProcessorCount;
+        h->m = m;
+        h->n = n;
+        h->r = r;
+        h->rp = static_cast<int>(rup(r, 8));
+        h->NP = static_cast<int>(rup(3 * h->rp, 16));
+        int khz = 0;
+        if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess || khz <= 0) {
+            cudaGetLastError();
+            khz = 2100000;
+        }
+        h->wait_cycles = static_cast<long long>(2.0 * static_cast<double>(khz) * 1000.0);
+        if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) { rc = COX_ERR_CUDA; break; }
+        cudaStream_t st = h->cap;
+        h->ldr = rup(n, 8);
+        h->ldc = rup(m, 8);
+        h->ldm = rup(m, 8);
+        h->ldn = rup(n, 8);
+        auto A = [&](void **p, size_t b) { return nmf_alloc(h, p, b); };
+        if ((rc = A(reinterpret_cast<void **>(&h->err), sizeof(int))) != COX_OK) break;
+        if ((rc = A(reinterpret_cast<void **>(&h->counters), 4 * sizeof(int))) != COX_OK) break;
+        if ((rc = A(reinterpret_cast<void **>(&h->Xr), static_cast<size_t>(m * h->ldr) * 2)) != COX_OK) break;
+        if ((rc = A(reinterpret_cast<void **>(&h->Xc), static_cast<size_t>(n * h->ldc) * 2)) != COX_OK) break;
+        if ((rc = A(reinterpret_cast<void **>(&h->Vl), static_cast<size_t>(h->NP * h->ldm) * 2)) != COX_OK) break;
+        if ((rc = A(reinterpret_cast<void **>(&h->Wl), static_cast<size_t>(h->NP * h->ldn) * 2)) != COX_OK) break;
+        if ((rc = A(reinterpret_cast<void **>(&h->Vt), static_cast<size_t>(r * m) * 4)) != COX_OK) break;
+        if ((rc = A(reinterpret_cast<void **>(&h->W), static_cast<size_t>(r * n) * 4)) != COX_OK) break;
+        for (float **p : {&h->GV32, &h->GW32})
+            if ((rc = A(reinterpret_cast<void **>(p), static_cast<size_t>(r * r) * 4)) != COX_OK) break;
+        if (rc) break;
+        for (double **p : {&h->GV64, &h->GW64})
+            if ((rc = A(reinterpret_cast<void **>(p), static_cast<size_t>(r * r) * 8)) != COX_OK) break;
+        if (rc) break;
+        for (double **p : {&h->froV, &h->froW, &h->fobj})
+            if ((rc = A(reinterpret_cast<void **>(p), 8)) != COX_OK) break;
+        if (rc) break;
+        const int64_t tiles = std::max((m + NT - 1) / NT, (n + NT - 1) / NT);
+        const int RB = ((r + 3) & ~3) / 4;
+        if ((rc = A(reinterpret_cast<void **>(&h->gpart), static_cast<size_t>(tiles) * RB * (RB + 1) / 2 * 16 * 4)) !=
+            COX_OK)
+            break;
+        if ((rc = A(reinterpret_cast<void **>(&h->opart), static_cast<size_t>(tiles) * 8)) != COX_OK) break;
+        if (cudaMemsetAsync(h->err, 0, sizeof(int), st) != cudaSuccess ||
+            cudaMemsetAsync(h->counters, 0, 4 * sizeof(int), st) != cudaSuccess ||
+            cudaMemsetAsync(h->Vl, 0, static_cast<size_t>(h->NP * h->ldm) * 2, st) != cudaSuccess ||
+            cudaMemsetAsync(h->Wl, 0, static_cast<size_t>(h->NP * h->ldn) * 2, st) != cudaSuccess ||
+            cudaMemsetAsync(h->Vt, 0, static_cast<size_t>(r * m) * 4, st) != cudaSuccess ||
+            cudaMemsetAsync(h->W, 0, static_cast<size_t>(r * n) * 4, st) != cudaSuccess ||
+            cudaMemsetAsync(h->GV32, 0, static_cast<size_t>(r * r) * 4, st) != cudaSuccess ||
+            cudaMemsetAsync(h->GW32, 0, static_cast<size_t>(r * r) * 4, st) != cudaSuccess ||
+            cudaMemsetAsync(h->GV64, 0, static_cast<size_t>(r * r) * 8, st) != cudaSuccess ||
+            cudaMemsetAsync(h->GW64, 0, static_cast<size_t>(r * r) * 8, st) != cudaSuccess ||
+            cudaMemsetAsync(h->froV, 0, 8, st) != cudaSuccess || cudaMemsetAsync(h->froW, 0, 8, st) != cudaSuccess) {
+            rc = COX_ERR_CUDA;
+            break;
+        }
+        // X in row blocks of about 64 MB through a staging buffer
+        const int64_t rows_blk = std::max<int64_t>(32, ((int64_t(64) << 20) / (4 * n)) / 32 * 32);
+        const int64_t nrb = std::min(rows_blk, m);
+        float *stage = nullptr;
+        if (cudaMalloc(reinterpret_cast<void **>(&stage), static_cast<size_t>(nrb * n) * 4) != cudaSuccess) {
+            cudaGetLastError();
+            rc = COX_ERR_OOM;
+            break;
+        }
+        const unsigned gx = static_cast<unsigned>((n + 31) / 32);
+        double *d_sq = nullptr;
+        const size_t nsq = static_cast<size_t>(gx) * ((nrb + 31) / 32);
+        if (cudaMalloc(reinterpret_cast<void **>(&d_sq), nsq * 8) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(stage);
+            rc = COX_ERR_OOM;
+            break;
+        }
+        std::vector<double> sq(nsq);
+        double xx = 0.0;
+        for (int64_t r0 = 0; r0 < m && rc == COX_OK; r0 += nrb) {
+            const int64_t nr = std::min(nrb, m - r0);
+            const unsigned gy = static_cast<unsigned>((nr + 31) / 32);
+            if (cudaMemcpyAsync(stage, X + r0 * n, static_cast<size_t>(nr * n) * 4, cudaMemcpyHostToDevice, st) !=
+                cudaSuccess) {
+                rc = COX_ERR_CUDA;
+                break;
+            }
+            k_nmf_pack<<<dim3(gx, gy), dim3(32, 8), 0, st>>>(stage, r0, nr, n, h->Xr, h->ldr, h->Xc, h->ldc, d_sq,
+                                                              h->err);
+            if (cudaGetLastError() != cudaSuccess ||
+                cudaMemcpyAsync(sq.data(), d_sq, static_cast<size_t>(gx) * gy * 8, cudaMemcpyDeviceToHost, st) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                rc = COX_ERR_CUDA;
+                break;
+            }
+            for (size_t b = 0; b < static_cast<size_t>(gx) * gy; ++b) xx += sq[b];
+        }
+        cudaFree(stage);
+        cudaFree(d_sq);
+        if (rc) break;
+        h->xx = xx;
+        if ((rc = check_err(h, st)) != COX_OK) break;
+        if ((rc = plan_side(h, h->s1, h->Xr, m, n, h->ldr, h->Wl, h->ldn, &h->part1)) != COX_OK) break;
+        if ((rc = plan_side(h, h->s2, h->Xc, n, m, h->ldc, h->Vl, h->ldm, &h->part2)) != COX_OK) break;
+        // the attribute is per function, not per handle: allow the device's
+        // largest block, so that handles of any rank can run side by side
+        int optin = 0;
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            std::max(h->s1.smem, h->s2.smem) > static_cast<size_t>(optin) ||
+            cudaFuncSetAttribute(k_nmf_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
+            cudaFuncSetAttribute(k_nmf_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(upd_smem(NMF_MAX_RANK))) != cudaSuccess) {
+            rc = COX_ERR_CUDA;
+            break;
+        }
+    } while (false);
+    if (rc != COX_OK) {
+        cudaGetLastError();
+        release(h);
+        return rc;
+    }
+    *out = h;
+    return COX_OK;
+}
+
+} // namespace
+} // namespace coxgb
+
+using namespace coxgb;
+
+extern "C" {
+
+int nmf_setup(const float *X_host, int64_t m, int64_t n, int r, int device, nmf_h *out)
+{
+    if (!out) return COX_ERR_ARG;
+    *out = nullptr;
+    if (!X_host || m < 1 || n < 1 || r < 1 || r > NMF_MAX_RANK) return COX_ERR_ARG;
+    if (m > (int64_t(1) << 31) - NT || n > (int64_t(1) << 31) - NT) return COX_ERR_ARG;
+    return setup_impl(X_host, m, n, r, device, out);
+}
+
+int nmf_destroy(nmf_h h)
+{
+    if (!h) return COX_OK;
+    DevGuard guard(h->dev);
+    cudaStreamSynchronize(h->cap);
+    release(h);
+    return COX_OK;
+}
+
+int nmf_set_factors(nmf_h h, const float *V, const float *W, void *stream)
+{
+    if (!h || !V || !W) return COX_ERR_ARG;
+    const int64_t m = h->m, n = h->n;
+    const int r = h->r;
+    for (int64_t e = 0; e < m * r; ++e)
+        if (!(V[e] >= 0.f) || !std::isfinite(V[e])) return COX_ERR_ARG;
+    for (int64_t e = 0; e < r * n; ++e)
+        if (!(W[e] >= 0.f) || !std::isfinite(W[e])) return COX_ERR_ARG;
+    DevGuard guard(h->dev);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<float> vt(static_cast<size_t>(r * m));
+    for (int64_t i = 0; i < m; ++i)
+        for (int c = 0; c < r; ++c) vt[c * m + i] = V[i * r + c];
+    COX_CUDA(cudaMemcpyAsync(h->Vt, vt.data(), vt.size() * 4, cudaMemcpyHostToDevice, st));
+    COX_CUDA(cudaMemcpyAsync(h->W, W, static_cast<size_t>(r * n) * 4, cudaMemcpyHostToDevice, st));
+    COX_TRY(launch_update(h, 0, 0, 0, 0.0, st));
+    COX_TRY(launch_update(h, 1, 0, 0, 0.0, st));
+    return check_err(h, st);
+}
+
+int nmf_get_factors(nmf_h h, float *V, float *W, void *stream)
+{
+    if (!h || !V || !W) return COX_ERR_ARG;
+    DevGuard guard(h->dev);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t m = h->m, n = h->n;
+    const int r = h->r;
+    std::vector<float> vt(static_cast<size_t>(r * m));
+    COX_CUDA(cudaMemcpyAsync(vt.data(), h->Vt, vt.size() * 4, cudaMemcpyDeviceToHost, st));
+    COX_CUDA(cudaMemcpyAsync(W, h->W, static_cast<size_t>(r * n) * 4, cudaMemcpyDeviceToHost, st));
+    COX_TRY(check_err(h, st));
+    for (int64_t i = 0; i < m; ++i)
+        for (int c = 0; c < r; ++c) V[i * r + c] = vt[c * m + i];
+    return COX_OK;
+}
+
+int nmf_iterate(nmf_h h, int algo, int64_t iters, double eps, void *stream)
+{
+    if (!h || iters < 0 || (algo != NMF_MULTIPLICATIVE && algo != NMF_APG) || !(eps >= 0.0) || !std::isfinite(eps))
+        return COX_ERR_ARG;
+    if (iters == 0) return COX_OK;
+    DevGuard guard(h->dev);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!h->exec || h->g_algo != algo || h->g_eps != eps) {
+        if (h->exec) {
+            cudaGraphExecDestroy(h->exec);
+            h->exec = nullptr;
+        }
+        const int64_t before = h->launches;
+        COX_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+        int rc = launch_gemm(h, h->s1, h->cap);
+        if (rc == COX_OK) rc = launch_update(h, 0, 1, algo, eps, h->cap);
+        if (rc == COX_OK) rc = launch_gemm(h, h->s2, h->cap);
+        if (rc == COX_OK) rc = launch_update(h, 1, 1, algo, eps, h->cap);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(h->cap, &graph);
+        h->launches = before;
+        if (rc == COX_OK && (ec != cudaSuccess || cudaGraphInstantiate(&h->exec, graph, 0) != cudaSuccess))
+            rc = COX_ERR_CUDA;
+        if (graph) cudaGraphDestroy(graph);
+        if (rc != COX_OK) {
+            cudaGetLastError();
+            h->exec = nullptr;
+            return rc;
+        }
+        h->g_algo = algo;
+        h->g_eps = eps;
+    }
+    for (int64_t t = 0; t < iters; ++t) COX_CUDA(cudaGraphLaunch(h->exec, st));
+    h->launches += 4 * iters;
+    return COX_OK;
+}
+
+int nmf_objective(nmf_h h, double *f, void *stream)
+{
+    if (!h || !f) return COX_ERR_ARG;
+    DevGuard guard(h->dev);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    COX_TRY(launch_gemm(h, h->s1, st));
+    FitArgs a;
+    a.r = h->r;
+    a.R = h->m;
+    a.F = h->Vt;
+    a.part = h->s1.g.part;
+    a.SL = h->s1.g.SL;
+    a.KC = h->s1.g.KC;
+    a.L = h->s1.g.L;
+    a.opart = h->opart;
+    a.counter = h->counters + 2;
+    a.GV = h->GV64;
+    a.GW = h->GW64;
+    a.xx = h->xx;
+    a.out = h->fobj;
+    k_nmf_fit<<<static_cast<unsigned>((h->m + UPD_THREADS - 1) / UPD_THREADS), UPD_THREADS, 0, st>>>(a);
+    ++h->launches;
+    COX_CUDA(cudaGetLastError());
+    COX_CUDA(cudaMemcpyAsync(f, h->fobj, sizeof(double), cudaMemcpyDeviceToHost, st));
+    return check_err(h, st);
+}
+
+int nmf_sync(nmf_h h, void *stream)
+{
+    if (!h) return COX_ERR_ARG;
+    DevGuard guard(h->dev);
+    return check_err(h, static_cast<cudaStream_t>(stream));
+}
+
+int nmf_get_info(nmf_h h, nmf_info *o)
+{
+    if (!h || !o) return COX_ERR_ARG;
+    o->m = h->m;
+    o->n = h->n;
+    o->r = h->r;
+    o->limb_cols = h->NP;
+    o->stages = h->s1.g.S;
+    o->sm_count = h->sms;
+    o->grid_xwt = h->s1.grid;
+    o->grid_vtx = h->s2.grid;
+    o->units_xwt = h->s1.g.units;
+    o->units_vtx = h->s2.g.units;
+    o->device_bytes = h->device_bytes;
+    o->launches = h->launches;
+    return COX_OK;
+}
+
+int nmf_time_products(nmf_h h, int reps, double *ms_xwt, double *ms_vtx, void *stream)
+{
+    if (!h || reps < 1 || !ms_xwt || !ms_vtx) return COX_ERR_ARG;
+    DevGuard guard(h->dev);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    int rc = COX_OK;
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) rc = COX_ERR_CUDA;
+    if (rc == COX_OK) {
+        cudaEventRecord(ev[0], st);
+        for (int i = 0; i < reps && rc == COX_OK; ++i) rc = launch_gemm(h, h->s1, st);
+        cudaEventRecord(ev[1], st);
+        for (int i = 0; i < reps && rc == COX_OK; ++i) rc = launch_gemm(h, h->s2, st);
+        cudaEventRecord(ev[2], st);
+    }
+    if (rc == COX_OK) rc = check_err(h, st);
+    float a = 0.f, b = 0.f;
+    if (rc == COX_OK &&
+        (cudaEventElapsedTime(&a, ev[0], ev[1]) != cudaSuccess || cudaEventElapsedTime(&b, ev[1], ev[2]) != cudaSuccess))
+        rc = COX_ERR_CUDA;
+    for (auto &e : ev)
+        if (e) cudaEventDestroy(e);
+    *ms_xwt = static_cast<double>(a) / reps;
+    *ms_vtx = static_cast<double>(b) / reps;
+    return rc;
+}
+
+} // extern "C"

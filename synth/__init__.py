@@ -17,6 +17,10 @@ of its UK Biobank analysis, Section 6), keyed by what they are:
   T = E / (h0 exp(eta)), C ~ U(1, dmax), y = ceil(min(T, C)) in whole days
   (ties), h0 set to hit the event rate; k penalties (1 unless the name says).
 
+NMF inputs (Section 5.1 experiments, ``nmf_inputs``): X m x n on the grid
+k / 256 (uniform, exact in bf16), V m x r and W r x n uniform on [0, 1) in FP32;
+the seed ``NMF_SEED`` stands for the paper's ``rand!`` draws.
+
 Each recipe carries its own seed; ``scaled`` keeps recipe and seed and
 changes only the sizes.
 """
@@ -85,6 +89,8 @@ def _host():
         lib.syn_causal.argtypes = [_u64, _i64, _i64, _f64, _p, _p]
         lib.syn_times_exp.restype = ctypes.c_int
         lib.syn_times_exp.argtypes = [_u64, _i64, _p, _f64, _p, _p, _p]
+        lib.syn_nmf_x.argtypes = [_u64, _i64, _i64, _i64, _p]
+        lib.syn_nmf_factor.argtypes = [_u64, ctypes.c_int, _i64, _p]
         lib.syn_times_days.restype = ctypes.c_int
         lib.syn_times_days.argtypes = [_u64, _i64, _p, _f64, _i64, _p, _p, _p]
         _lib = lib
@@ -306,3 +312,24 @@ def normal_vec(seed: int, stream: int, m: int) -> np.ndarray:
     out = np.zeros(m)
     _host().syn_normal_vec(seed, stream, m, _ptr(out))
     return out
+
+
+NMF_SEED = 2010161150
+
+
+def nmf_x(m: int, n: int, seed: int = NMF_SEED, i0: int = 0) -> np.ndarray:
+    """Rows [i0, i0 + m) of the NMF data matrix (float32, values k / 256)."""
+    out = np.empty((m, n), np.float32)
+    _host().syn_nmf_x(seed, i0, m, n, _ptr(out))
+    return out
+
+
+def nmf_inputs(m: int, n: int, r: int, seed: int = NMF_SEED):
+    """(X, V0, W0): X m x n on the grid k / 256, V0 m x r and W0 r x n uniform
+    on [0, 1), all float32."""
+    X = nmf_x(m, n, seed)
+    V = np.empty((m, r), np.float32)
+    W = np.empty((r, n), np.float32)
+    _host().syn_nmf_factor(seed, 0, m * r, _ptr(V))
+    _host().syn_nmf_factor(seed, 1, r * n, _ptr(W))
+    return X, V, W

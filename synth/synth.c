@@ -31,7 +31,10 @@ enum {
     SYN_STREAM_CAUSAL_IDX = 3,
     SYN_STREAM_CAUSAL_EFF = 4,
     SYN_STREAM_EVENT = 5,
-    SYN_STREAM_CENSOR = 6
+    SYN_STREAM_CENSOR = 6,
+    SYN_STREAM_NMF_X = 7,
+    SYN_STREAM_NMF_V = 8,
+    SYN_STREAM_NMF_W = 9
 };
 
 uint64_t syn_mix64(uint64_t z)
@@ -246,4 +249,26 @@ int syn_times_days(uint64_t seed, int64_t n, const double *eta, double event_fra
     if (h0_out) *h0_out = h0;
     free(E); free(C); free(q);
     return 0;
+}
+
+/* NMF inputs (Section 5.1 experiments: X, V and W drawn uniform on [0, 1)).
+ * X entries are drawn on the grid k / 256, k = 0..255, so that they are exact
+ * in bf16 (8 significant bits); rows [i0, i0 + ni) of an m x n row-major X. */
+void syn_nmf_x(uint64_t seed, int64_t i0, int64_t ni, int64_t n, float *out)
+{
+    for (int64_t i = 0; i < ni; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            uint64_t h = syn_draw(seed, SYN_STREAM_NMF_X, (uint64_t)(i0 + i), (uint64_t)j);
+            out[i * n + j] = (float)(h >> 56) * 0x1.0p-8f;
+        }
+}
+
+/* count uniform [0, 1) values rounded to FP32; which = 0 for V, 1 for W. */
+void syn_nmf_factor(uint64_t seed, int which, int64_t count, float *out)
+{
+    const uint64_t st = which ? SYN_STREAM_NMF_W : SYN_STREAM_NMF_V;
+    for (int64_t t = 0; t < count; ++t) {
+        float f = (float)u01(syn_draw(seed, st, (uint64_t)t, 0));
+        out[t] = f < 1.0f ? f : 0x1.fffffep-1f;
+    }
 }

@@ -9,10 +9,10 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    src = open(os.path.join(ROOT, "include", "coxgb.h")).read()
+def _declared(header: str = "coxgb.h", prefix: str = "cox"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = set(re.findall(r"\b(cox_[a-z_0-9]+)\s*\(", src))
+    names = set(re.findall(r"\b(" + prefix + r"_[a-z_0-9]+)\s*\(", src))
     return sorted(names)
 
 
@@ -41,6 +41,35 @@ def test_every_declared_symbol_is_exported(lib):
         assert n in names, f"binding exports {n} which the header does not declare"
 
 
+def test_nmf_header_symbols_are_exported(lib):
+    from paper_2010_16114_gb300 import _lib as L
+    names = _declared("nmfgb.h", "nmf")
+    assert set(names) == set(L.NMF_EXPORTS), (names, L.NMF_EXPORTS)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_nmf_argument_errors_without_gpu(lib):
+    """The NMF entry points reject bad arguments before any device work, and
+    report a missing device as an error code."""
+    import numpy as np
+    from paper_2010_16114_gb300 import _lib as L
+    X = np.ones((4, 3), np.float32)
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    h = ctypes.c_void_p()
+    assert L.nmf_setup(vp(X), 4, 3, 0, -1, ctypes.byref(h)) == L.COX_ERR_ARG and not h.value
+    assert L.nmf_setup(vp(X), 4, 3, L.NMF_MAX_RANK + 1, -1, ctypes.byref(h)) == L.COX_ERR_ARG
+    assert L.nmf_setup(None, 4, 3, 2, -1, ctypes.byref(h)) == L.COX_ERR_ARG
+    assert L.nmf_setup(vp(X), 0, 3, 2, -1, ctypes.byref(h)) == L.COX_ERR_ARG
+    assert L.nmf_iterate(None, 0, 1, 1e-10, None) == L.COX_ERR_ARG
+    assert L.nmf_objective(None, None, None) == L.COX_ERR_ARG
+    assert L.nmf_destroy(None) == L.COX_OK
+    import torch
+    if not torch.cuda.is_available():
+        rc = L.nmf_setup(vp(X), 4, 3, 2, -1, ctypes.byref(h))
+        assert rc in (L.COX_ERR_CUDA, L.COX_ERR_UNSUPPORTED) and not h.value
+
+
 def test_strerror_and_defaults(lib):
     from paper_2010_16114_gb300 import _lib as L
     assert L.strerror(0) == "ok"
@@ -56,8 +85,9 @@ def test_struct_layouts_match_the_header(tmp_path):
     import subprocess
     from paper_2010_16114_gb300 import _lib as L
     structs = {"cox_options": L.cox_options, "cox_info": L.cox_info, "cox_tune_choice": L.cox_tune_choice,
-               "cox_plan": L.cox_plan}
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "coxgb.h"', "int main(void) {"]
+               "cox_plan": L.cox_plan, "nmf_info": L.nmf_info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "coxgb.h"', '#include "nmfgb.h"',
+             "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
         for f, _ in cls._fields_:

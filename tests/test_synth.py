@@ -118,3 +118,18 @@ def test_normal_times_hit_the_censoring_fraction_without_ties():
     assert w.n - int(w.delta.sum()) == round(0.30 * w.n)
     assert len(np.unique(w.y)) == w.n and np.all(w.y > 0)
     assert len(w.causal_idx) == 20 and np.all(np.diff(w.causal_idx) > 0)
+
+
+def test_nmf_inputs_grid_range_and_determinism():
+    """NMF inputs: X on the grid k / 256 (exact in bf16), V and W in [0, 1),
+    regenerable by rows."""
+    X, V, W = synth.nmf_inputs(70, 90, 4)
+    assert X.dtype == np.float32 and X.shape == (70, 90) and V.shape == (70, 4) and W.shape == (4, 90)
+    k = X.astype(np.float64) * 256
+    assert np.array_equal(k, np.round(k)) and k.min() >= 0 and k.max() <= 255
+    assert len(np.unique(k)) > 200
+    assert 0.45 < X.mean() < 0.55
+    assert V.min() >= 0 and V.max() < 1 and W.min() >= 0 and W.max() < 1
+    X2, V2, W2 = synth.nmf_inputs(70, 90, 4)
+    assert np.array_equal(X, X2) and np.array_equal(V, V2) and np.array_equal(W, W2)
+    assert np.array_equal(synth.nmf_x(10, 90, i0=30), X[30:40])
