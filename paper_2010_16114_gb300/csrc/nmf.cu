@@ -25,8 +25,13 @@
 // accumulate in FP32 in Tensor Memory.  Per CTA (one per SM): a TMA warp fills
 // a ring of shared-memory stages, one thread issues four M128 x N x K16 MMAs
 // per 64-wide K chunk into one of two TMEM accumulators, and four epilogue
-// warps (one per TMEM lane quarter) add the three limb columns of each value
-// and store the CTA's partial of the row tile.  Work split: units = (row tile,
+// warps (one per TMEM lane quarter) add the three limb columns of each value.
+// An accumulator takes at most WINDOW chunks (512 K); the epilogue then adds
+// it into FP32 running sums in shared memory (round to nearest) while the
+// other accumulator fills: the tensor cores' own FP32 accumulation over
+// thousands of K came out about 1e-5 low at X 10,000 x 10,000, where 512 K
+// keep that bias near 1e-6.  At a row tile's end the sums are the CTA's
+// partial of the tile.  Work split: units = (row tile,
 // K chunk) in row-tile order; CTA c takes units [c L, (c+1) L), so a row tile
 // is cut between at most a few CTAs, each leaving a partial in its own slot;
 // the update kernel adds the slots in slot order (deterministic).
@@ -50,6 +55,7 @@ constexpr int NK = 64;                  // K per chunk: 64 bf16 = one 128-byte s
 constexpr int A_BYTES = NT * NK * 2;    // 16 KB A box per stage
 constexpr int GEMM_THREADS = 192;       // TMA warp, MMA warp, four epilogue warps
 constexpr int MAX_STAGES = 8;
+constexpr int WINDOW = 8;               // K chunks one TMEM accumulator sums before the epilogue folds it
 constexpr int UPD_THREADS = 128;        // one thread per factor column of a row tile
 constexpr long long NMF_DRAIN = 4000000000LL;  // ~2 s: copies and MMAs always finish
 __device__ int g_nmf_never = 0;                // abort flag of drain waits: never raised
@@ -77,18 +83,18 @@ __device__ __forceinline__ void nmf_fail(volatile int *abort_sm, int *err)
     }
 }
 
-// Pipeline hand-offs (S stages, two accumulators a = segment index mod 2):
+// Pipeline hand-offs (S stages, two accumulators a = window index mod 2):
 //   full[s]   TMA transaction bytes                    producer -> issuer
 //   empty[s]  tcgen05.commit after the stage's MMAs    issuer   -> producer
-//   accf[a]   tcgen05.commit at a segment end          issuer   -> epilogue
+//   accf[a]   tcgen05.commit at a window end           issuer   -> epilogue
 //   acce[a]   four arrivals once the epilogue read a   epilogue -> issuer
 // Every waiter waits for the completions of a barrier in order, and the
 // completion before the awaited one is always one it waited for itself (the
 // producer's wait on empty[s] for unit i - S follows its wait for unit i - 2S;
 // the issuer's wait on full[s] for unit i follows the one for unit i - S; on
-// accf[a] / acce[a] for segment q, the waits for segment q - 2), so no parity
+// accf[a] / acce[a] for window w, the waits for window w - 2), so no parity
 // wait can return a phase early.  A segment is the CTA's run of units in one
-// row tile.
+// row tile; a window is at most WINDOW units of a segment.
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     k_nmf_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs P)
 {
@@ -104,6 +110,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const uint32_t drainb = acce0 + 16;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 5);
     volatile int *abort_sm = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    float *sums = reinterpret_cast<float *>(smem + S * STAGE + 256);  // [r][128] running sums
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -175,39 +182,45 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         if (lane == 0) {
             const uint64_t descA = smem_desc_sw128(smem_addr(smem));
             const uint64_t descB = smem_desc_sw128(smem_addr(smem + A_BYTES));
-            int s = 0, kc = kc0, q = 0;
+            int s = 0, kc = kc0;
             uint32_t ph = 0;
             bool ok = true;
-            for (int64_t i = 0; ok && i < nu; ++q) {
-                const int64_t len = min(static_cast<int64_t>(KC - kc), nu - i);
-                const int a = q & 1;
-                if (q >= 2 && !mbar_wait(acce0 + 8 * a, static_cast<uint32_t>(((q - 2) >> 1) & 1), lim, abort_sm)) {
-                    nmf_fail(abort_sm, P.err);
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t d = tbase + static_cast<uint32_t>(a * P.NP);
-                for (int64_t e = 0; e < len; ++e) {
-                    if (!mbar_wait(full0 + 8 * s, ph, lim, abort_sm)) {
+            int64_t w = 0;  // windows so far
+            for (int64_t i = 0; ok && i < nu;) {
+                const int64_t seg = min(static_cast<int64_t>(KC - kc), nu - i);
+                for (int64_t e0 = 0; ok && e0 < seg; e0 += WINDOW, ++w) {
+                    const int64_t wl = min(static_cast<int64_t>(WINDOW), seg - e0);
+                    const int a = static_cast<int>(w & 1);
+                    if (w >= 2 &&
+                        !mbar_wait(acce0 + 8 * a, static_cast<uint32_t>(((w - 2) >> 1) & 1), lim, abort_sm)) {
                         nmf_fail(abort_sm, P.err);
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t off = static_cast<uint64_t>(s) * static_cast<uint64_t>(STAGE >> 4);
+                    const uint32_t d = tbase + static_cast<uint32_t>(a * P.NP);
+                    for (int64_t e = 0; e < wl; ++e) {
+                        if (!mbar_wait(full0 + 8 * s, ph, lim, abort_sm)) {
+                            nmf_fail(abort_sm, P.err);
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t off = static_cast<uint64_t>(s) * static_cast<uint64_t>(STAGE >> 4);
 #pragma unroll
-                    for (int kk = 0; kk < NK / 16; ++kk)  // K = 16 per MMA: 32 bytes of every row
-                        mma_ss_f16(d, descA + off + 2 * kk, descB + off + 2 * kk, P.idesc,
-                                   (e > 0 || kk > 0) ? 1u : 0u);
-                    mma_commit(empty0 + 8 * s);
-                    if (++s == S) {
-                        s = 0;
-                        ph ^= 1u;
+                        for (int kk = 0; kk < NK / 16; ++kk)  // K = 16 per MMA: 32 bytes of every row
+                            mma_ss_f16(d, descA + off + 2 * kk, descB + off + 2 * kk, P.idesc,
+                                       (e > 0 || kk > 0) ? 1u : 0u);
+                        mma_commit(empty0 + 8 * s);
+                        if (++s == S) {
+                            s = 0;
+                            ph ^= 1u;
+                        }
                     }
+                    if (!ok) break;
+                    mma_commit(accf0 + 8 * a);
                 }
-                if (!ok) break;
-                mma_commit(accf0 + 8 * a);
-                i += len;
+                i += seg;
                 kc = 0;
             }
             mma_commit(drainb);
@@ -219,34 +232,50 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         const int row = 32 * quarter + lane;
         const uint32_t lane_base = tbase + (static_cast<uint32_t>(32 * quarter) << 16);
         const int r = P.r;
+        float *sum = sums + row;
         int g = g0, kc = kc0;
-        for (int64_t i = 0, q = 0; i < nu; ++q) {
-            const int64_t len = min(static_cast<int64_t>(KC - kc), nu - i);
-            const int a = static_cast<int>(q & 1);
-            if (!__all_sync(0xffffffffu, mbar_wait(accf0 + 8 * a, static_cast<uint32_t>((q >> 1) & 1), lim, abort_sm))) {
-                if (lane == 0) nmf_fail(abort_sm, P.err);
-                break;
-            }
-            tc_fence_after();
+        bool ok = true;
+        int64_t w = 0;
+        for (int64_t i = 0; ok && i < nu;) {
+            const int64_t seg = min(static_cast<int64_t>(KC - kc), nu - i);
             const int64_t slot = static_cast<int64_t>(blockIdx.x) - (static_cast<int64_t>(g) * KC) / P.L;
             float *dst = P.part + ((static_cast<int64_t>(g) * P.SL + slot) * r) * NT + row;
-            const uint32_t acc = lane_base + static_cast<uint32_t>(a * P.NP);
-            for (int c0 = 0; c0 < r; c0 += 8) {
-                uint32_t h0[8], h1[8], h2[8];
-                tmem_ld_32x32b_x8(acc + static_cast<uint32_t>(c0), h0);
-                tmem_ld_32x32b_x8(acc + static_cast<uint32_t>(P.rp + c0), h1);
-                tmem_ld_32x32b_x8(acc + static_cast<uint32_t>(2 * P.rp + c0), h2);
-                tmem_wait_ld();
+            for (int64_t e0 = 0; e0 < seg; e0 += WINDOW, ++w) {
+                const bool first = e0 == 0, last = e0 + WINDOW >= seg;
+                const int a = static_cast<int>(w & 1);
+                if (!__all_sync(0xffffffffu,
+                                mbar_wait(accf0 + 8 * a, static_cast<uint32_t>((w >> 1) & 1), lim, abort_sm))) {
+                    if (lane == 0) nmf_fail(abort_sm, P.err);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acc = lane_base + static_cast<uint32_t>(a * P.NP);
+                for (int c0 = 0; c0 < r; c0 += 8) {
+                    uint32_t h0[8], h1[8], h2[8];
+                    tmem_ld_32x32b_x8(acc + static_cast<uint32_t>(c0), h0);
+                    tmem_ld_32x32b_x8(acc + static_cast<uint32_t>(P.rp + c0), h1);
+                    tmem_ld_32x32b_x8(acc + static_cast<uint32_t>(2 * P.rp + c0), h2);
+                    tmem_wait_ld();
 #pragma unroll
-                for (int e = 0; e < 8; ++e)
-                    if (c0 + e < r)
-                        dst[static_cast<int64_t>(c0 + e) * NT] =
-                            (__uint_as_float(h0[e]) + __uint_as_float(h1[e])) + __uint_as_float(h2[e]);
+                    for (int e = 0; e < 8; ++e) {
+                        const int c = c0 + e;
+                        if (c < r) {
+                            const float v =
+                                (__uint_as_float(h0[e]) + __uint_as_float(h1[e])) + __uint_as_float(h2[e]);
+                            const float t = first ? v : sum[c * NT] + v;
+                            if (last)
+                                dst[static_cast<int64_t>(c) * NT] = t;
+                            else
+                                sum[c * NT] = t;
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce0 + 8 * a);
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acce0 + 8 * a);
-            i += len;
+            i += seg;
             kc = 0;
             ++g;
         }
@@ -621,7 +650,7 @@ int plan_side(nmf_handle *h, NmfSide &sd, const __nv_bfloat16 *A, int64_t rows, 
     g.stage = A_BYTES + h->NP * 128;
     int optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev) != cudaSuccess) return COX_ERR_CUDA;
-    g.S = std::min(MAX_STAGES, (optin - 2048) / g.stage);
+    g.S = std::min(MAX_STAGES, (optin - 2048 - h->r * NT * static_cast<int>(sizeof(float))) / g.stage);
     if (g.S < 2) return COX_ERR_UNSUPPORTED;
     const int need = h->NP + 3 * h->rp;  // second accumulator: its last limb's columns end before NP + 3 rp
     int tc = 32;
@@ -643,7 +672,7 @@ int plan_side(nmf_handle *h, NmfSide &sd, const __nv_bfloat16 *A, int64_t rows, 
     COX_TRY(nmf_alloc(h, reinterpret_cast<void **>(part),
                       static_cast<size_t>(sd.MT) * SL * h->r * NT * sizeof(float)));
     g.part = *part;
-    sd.smem = 1024 + static_cast<size_t>(g.S) * g.stage + 256;
+    sd.smem = 1024 + static_cast<size_t>(g.S) * g.stage + 256 + static_cast<size_t>(h->r) * NT * sizeof(float);
     if (!encode_bf16(&sd.tmA, A, K, rows, ldA, NT)) return COX_ERR_CUDA;
     if (!encode_bf16(&sd.tmB, B, K, h->NP, ldB, h->NP)) return COX_ERR_CUDA;
     return COX_OK;

@@ -7,8 +7,8 @@ copy of X, so both sides factor the same matrix), V0 and W0 uniform on [0, 1)
 in FP32.
 
 Tolerances.  The library keeps V and W in FP32 and forms X W^T and V^T X from
-FP32-exact bf16 limbs with FP32 tensor-core accumulation (at most one segment
-of K per accumulator, partial slots added in FP64); the Gram matrices are FP64
+FP32-exact bf16 limbs with FP32 tensor-core accumulation (512 K per
+accumulator, then FP32 running sums; partial slots added in FP64); the Gram matrices are FP64
 sums of FP32 block partials.  A numpy model of that arithmetic (FP32 products
 and updates) stays within 1.1e-6 elementwise of the FP64 oracle after one
 iteration and within 1.3e-6 relative L2 after 50 at 300 x 200, r = 20.  The
@@ -47,9 +47,10 @@ def max_rel(a, b, floor):
 # (m, n, r): several row tiles with ragged tails in both products; a tall X whose
 # CTAs each run three row tiles of X W^T (both TMEM accumulators reused) and whose
 # X^T V is one row tile cut into ~130 partial slots; single ragged tiles; r = 1
-# and the largest rank (N = 240, four pipeline stages)
+# and the largest rank (N = 240, four pipeline stages); a wide X whose CTAs each sum
+# ~130 K chunks of one row tile (17 accumulator windows per segment)
 SHAPES = [(300, 200, 5), (300, 200, 20), (51200, 128, 20), (97, 45, 3), (1000, 777, 1), (640, 520, 80),
-          (1000, 3000, 60)]
+          (1000, 3000, 60), (2560, 64000, 4)]
 
 
 @pytest.mark.parametrize("m,n,r", SHAPES)
