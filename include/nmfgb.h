@@ -89,9 +89,9 @@ int nmf_set_factors(nmf_h h, const float *V_host, const float *W_host, void *str
 int nmf_get_factors(nmf_h h, float *V_host, float *W_host, void *stream);
 
 /* Run `iters` iterations of `algo` (NMF_MULTIPLICATIVE or NMF_APG) with the
- * given eps (>= 0; Section 5.1 uses 1e-10).  One iteration is four kernels
- * (X W^T, the V update, V^T X, the W update), captured once per (algo, eps)
- * as a CUDA graph and replayed.  Asynchronous on `stream`.
+ * given eps (>= 0; Section 5.1 uses 1e-10).  One iteration is six kernels
+ * (X W^T, the V update, V^T V, V^T X, the W update, W W^T), captured once
+ * per (algo, eps) as a CUDA graph and replayed.  Asynchronous on `stream`.
  * Errors: COX_ERR_ARG for iters < 0, an unknown algo or a negative or
  * non-finite eps; COX_ERR_CUDA. */
 int nmf_iterate(nmf_h h, int algo, int64_t iters, double eps, void *stream);

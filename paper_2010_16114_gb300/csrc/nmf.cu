@@ -2,11 +2,13 @@
 // Section 5.1): the multiplicative (Lee-Seung) and the alternating projected
 // gradient (APG) iterations on one GB300.
 //
-// An iteration is four kernels:
+// An iteration is six kernels:
 //   k_nmf_gemm    P = X W^T   (m x r)   tcgen05 kind::f16, A = X row-major
-//   k_nmf_update  V from P and W W^T; limbs of V; Gram V^T V (FP64)
+//   k_nmf_update  V from P and W W^T; limbs of V
+//   k_nmf_gram    V^T V (FP64) and its squared Frobenius norm
 //   k_nmf_gemm    Q = X^T V   (n x r)   A = X column-major
-//   k_nmf_update  W from Q and V^T V; limbs of W; Gram W W^T (FP64)
+//   k_nmf_update  W from Q and V^T V; limbs of W
+//   k_nmf_gram    W W^T and its norm
 // Both updates have one form.  With F a factor held r x R (V^T, or W), G the
 // Gram matrix of the other factor and P the product of X with it,
 //   (V W W^T)_ic = sum_d G_cd F_di  and  (V^T V W)_cj = sum_d G_cd F_dj
@@ -288,7 +290,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 }
 
 struct UpdArgs {
-    int r, rp, mode, algo;   // mode 1: update from the product; 0: limbs and Gram of F only
+    int r, rp, mode, algo;   // mode 1: update from the product; 0: limbs of F only
     int64_t R;               // factor columns (m for V, n for W)
     float *F;                // r x R, row c at c R
     __nv_bfloat16 *limb;     // NP x ldl: row l rp + c holds limb l of F row c
@@ -299,11 +301,6 @@ struct UpdArgs {
     const float *Gin;        // r x r Gram of the other factor
     const double *fro_in;    // its squared Frobenius norm
     double eps;
-    float *gpart;            // [block][pairs of 4 x 4 blocks][16]
-    int *counter;            // blocks done (reset by the last block)
-    double *G64;             // r x r Gram of the new F, FP64
-    float *G32;              // and in FP32
-    double *fro_out;
     int *err;
 };
 
@@ -316,16 +313,15 @@ __device__ __forceinline__ void split_bf16(float f, __nv_bfloat16 *h)
     h[2] = __float2bfloat16_rn(r1 - __bfloat162float(h[1]));
 }
 
-// One row tile of a factor: thread t owns column i = 128 g + t of F.
-// Shared memory: the new F ([j][RP], RP = r rounded up to 4) for the Gram
-// products, G (r x r) and the old F ([c][129], conflict-free per c).
+// One row tile of a factor: thread t owns column i = 128 g + t of F.  Shared
+// memory: G (r x r) and the old F ([c][129], conflict-free per c); the new
+// values go straight to F and its limbs (a thread reads only its own old
+// values, from shared memory).
 __global__ void __launch_bounds__(UPD_THREADS) k_nmf_update(const UpdArgs A)
 {
-    extern __shared__ float4 sh4[];
+    extern __shared__ float sh[];
     const int r = A.r, t = threadIdx.x;
-    const int RP = (r + 3) & ~3;
-    float *Fn = reinterpret_cast<float *>(sh4);  // rows of RP floats: 16-byte aligned for float4 loads
-    float *Gs = Fn + UPD_THREADS * RP;
+    float *Gs = sh;
     float *Fo = Gs + r * r;
     const int64_t g = blockIdx.x;
     const int64_t i = g * UPD_THREADS + t;
@@ -333,108 +329,136 @@ __global__ void __launch_bounds__(UPD_THREADS) k_nmf_update(const UpdArgs A)
     if (A.mode)
         for (int e = t; e < r * r; e += UPD_THREADS) Gs[e] = A.Gin[e];
     for (int c = 0; c < r; ++c) Fo[c * (UPD_THREADS + 1) + t] = valid ? A.F[c * A.R + i] : 0.f;
-    for (int c = r; c < RP; ++c) Fn[t * RP + c] = 0.f;
     __syncthreads();
+    if (!valid) return;
 
     bool bad = false;
-    if (A.mode) {
-        const float s = static_cast<float>(1.0 / (2.0 * *A.fro_in + A.eps));
-        const float eps = static_cast<float>(A.eps);
-        const int64_t first = (g * A.KC) / A.L, last = (g * A.KC + A.KC - 1) / A.L;
-        const int ns = static_cast<int>(last - first + 1);
-        const float *pp = A.part + (g * A.SL * r) * NT + t;
-        for (int c = 0; c < r; ++c) {
+    const float s = A.mode ? static_cast<float>(1.0 / (2.0 * *A.fro_in + A.eps)) : 0.f;
+    const float eps = static_cast<float>(A.eps);
+    const int64_t first = (g * A.KC) / A.L, last = (g * A.KC + A.KC - 1) / A.L;
+    const int ns = static_cast<int>(last - first + 1);
+    const float *pp = A.part + (g * A.SL * r) * NT + t;
+    for (int c = 0; c < r; ++c) {
+        const float old = Fo[c * (UPD_THREADS + 1) + t];
+        float v = old;
+        if (A.mode) {
             double acc = 0.0;
             for (int sl = 0; sl < ns; ++sl) acc += static_cast<double>(pp[(static_cast<int64_t>(sl) * r + c) * NT]);
             const float pc = static_cast<float>(acc);
             float den = 0.f;
             for (int d = 0; d < r; ++d) den = fmaf(Gs[c * r + d], Fo[d * (UPD_THREADS + 1) + t], den);
-            const float old = Fo[c * (UPD_THREADS + 1) + t];
-            float v = A.algo == NMF_MULTIPLICATIVE ? old * pc / (den + eps) : fmaxf(0.f, old - s * (den - pc));
-            if (!valid) v = 0.f;
+            v = A.algo == NMF_MULTIPLICATIVE ? old * pc / (den + eps) : fmaxf(0.f, old - s * (den - pc));
             bad |= !isfinite(v);
-            Fn[t * RP + c] = v;
+            A.F[c * A.R + i] = v;
         }
-    } else {
-        for (int c = 0; c < r; ++c) Fn[t * RP + c] = Fo[c * (UPD_THREADS + 1) + t];
+        __nv_bfloat16 h[3];
+        split_bf16(v, h);
+#pragma unroll
+        for (int l = 0; l < 3; ++l) A.limb[static_cast<int64_t>(l * A.rp + c) * A.ldl + i] = h[l];
     }
     if (bad) atomicOr(A.err, NMF_ERR_NONFINITE);
-    if (valid) {
-        for (int c = 0; c < r; ++c) {
-            const float v = Fn[t * RP + c];
-            if (A.mode) A.F[c * A.R + i] = v;
-            __nv_bfloat16 h[3];
-            split_bf16(v, h);
+}
+
+constexpr int GRAM_THREADS = 256;
+constexpr int GRAM_FLUSH = 32;  // FP32 runs of this many columns per thread, then added in FP64
+
+struct GramArgs {
+    int r;
+    int64_t R;
+    const float *F;          // r x R
+    double *G64;             // r x r
+    float *G32;
+    double *fro;             // ||G||_F^2
+    int *counter;            // blocks done (reset by the last block)
+};
+
+// G = F F^T.  Block b takes the 4 x 4 block (cb, db), cb <= db, of G over all
+// R columns: each thread sums its columns (stride 256) in FP32 runs of
+// GRAM_FLUSH columns added into FP64, then warp shuffles and the eight warps
+// in order give the entries (a fixed order: deterministic).  The last block
+// to finish forms ||G||_F^2.
+__global__ void __launch_bounds__(GRAM_THREADS) k_nmf_gram(const GramArgs A)
+{
+    __shared__ double red[GRAM_THREADS / 32][16];
+    __shared__ int is_last;
+    const int r = A.r, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int RB = (r + 3) / 4;
+    int cb = 0, rem = static_cast<int>(blockIdx.x);
+    while (rem >= RB - cb) {
+        rem -= RB - cb;
+        ++cb;
+    }
+    const int db = cb + rem;
+    const float *xr[4], *yr[4];
 #pragma unroll
-            for (int l = 0; l < 3; ++l) A.limb[static_cast<int64_t>(l * A.rp + c) * A.ldl + i] = h[l];
+    for (int a = 0; a < 4; ++a) {
+        xr[a] = 4 * cb + a < r ? A.F + static_cast<int64_t>(4 * cb + a) * A.R : nullptr;
+        yr[a] = 4 * db + a < r ? A.F + static_cast<int64_t>(4 * db + a) * A.R : nullptr;
+    }
+    double acc64[16];
+    float acc[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        acc64[e] = 0.0;
+        acc[e] = 0.f;
+    }
+    int run = 0;
+    for (int64_t j = t; j < A.R; j += GRAM_THREADS) {
+        float x[4], y[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            x[a] = xr[a] ? __ldg(xr[a] + j) : 0.f;
+            y[a] = yr[a] ? __ldg(yr[a] + j) : 0.f;
         }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[4 * a + b] = fmaf(x[a], y[b], acc[4 * a + b]);
+        if (++run == GRAM_FLUSH) {
+            run = 0;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                acc64[e] += static_cast<double>(acc[e]);
+                acc[e] = 0.f;
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        double v = acc64[e] + static_cast<double>(acc[e]);
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) red[wid][e] = v;
     }
     __syncthreads();
-
-    // Gram partial of the new F over this tile's 128 columns, in 4 x 4 blocks
-    // (cb <= db) of the r x r matrix: 8 shared loads per 16 multiply-adds.
-    const int RB = RP / 4, NBP = RB * (RB + 1) / 2;
-    for (int bp = t; bp < NBP; bp += UPD_THREADS) {
-        int cb = 0, rem = bp;
-        while (rem >= RB - cb) {
-            rem -= RB - cb;
-            ++cb;
+    if (t < 16) {
+        double v = 0.0;
+        for (int w = 0; w < GRAM_THREADS / 32; ++w) v += red[w][t];
+        const int c = 4 * cb + t / 4, d = 4 * db + t % 4;
+        if (c < r && d < r) {
+            A.G64[c * r + d] = v;
+            A.G64[d * r + c] = v;
+            A.G32[c * r + d] = static_cast<float>(v);
+            A.G32[d * r + c] = static_cast<float>(v);
         }
-        const int db = cb + rem;
-        float acc[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) acc[e] = 0.f;
-        for (int j = 0; j < UPD_THREADS; ++j) {
-            const float4 x = *reinterpret_cast<const float4 *>(Fn + j * RP + 4 * cb);
-            const float4 y = *reinterpret_cast<const float4 *>(Fn + j * RP + 4 * db);
-            const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[4 * a + b] = fmaf(xv[a], yv[b], acc[4 * a + b]);
-        }
-        float *dst = A.gpart + (g * NBP + bp) * 16;
-#pragma unroll
-        for (int e = 0; e < 16; ++e) dst[e] = acc[e];
     }
-
-    // the last block adds the partials in block order (FP64) and writes G
-    __shared__ int is_last;
-    __shared__ double red[UPD_THREADS];
     __threadfence();
     __syncthreads();
     if (t == 0) is_last = atomicAdd(A.counter, 1) == static_cast<int>(gridDim.x) - 1;
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    double fro = 0.0;
-    for (int bp = t; bp < NBP; bp += UPD_THREADS) {
-        int cb = 0, rem = bp;
-        while (rem >= RB - cb) {
-            rem -= RB - cb;
-            ++cb;
-        }
-        const int db = cb + rem;
-        for (int e = 0; e < 16; ++e) {
-            const int c = 4 * cb + e / 4, d = 4 * db + e % 4;
-            if (c >= r || d >= r || (cb == db && d < c)) continue;
-            double s = 0.0;
-            for (unsigned b = 0; b < gridDim.x; ++b) s += static_cast<double>(__ldcg(A.gpart + (b * NBP + bp) * 16 + e));
-            A.G64[c * r + d] = s;
-            A.G64[d * r + c] = s;
-            A.G32[c * r + d] = static_cast<float>(s);
-            A.G32[d * r + c] = static_cast<float>(s);
-            fro += (c == d ? 1.0 : 2.0) * s * s;
-        }
+    double f = 0.0;
+    for (int e = t; e < r * r; e += GRAM_THREADS) {
+        const double gv = __ldcg(A.G64 + e);
+        f += gv * gv;
     }
-    red[t] = fro;
+    for (int off = 16; off > 0; off >>= 1) f += __shfl_down_sync(0xffffffffu, f, off);
+    if (lane == 0) red[wid][0] = f;
     __syncthreads();
-    for (int w = UPD_THREADS / 2; w > 0; w >>= 1) {
-        if (t < w) red[t] += red[t + w];
-        __syncthreads();
-    }
     if (t == 0) {
-        *A.fro_out = red[0];
+        double s = 0.0;
+        for (int w = 0; w < GRAM_THREADS / 32; ++w) s += red[w][0];
+        *A.fro = s;
         *A.counter = 0;
     }
 }
@@ -608,7 +632,7 @@ struct nmf_handle {
     float *Vt = nullptr, *W = nullptr;
     float *part1 = nullptr, *part2 = nullptr;
     NmfSide s1, s2;               // X W^T, X^T V
-    float *GV32 = nullptr, *GW32 = nullptr, *gpart = nullptr;
+    float *GV32 = nullptr, *GW32 = nullptr;
     double *GV64 = nullptr, *GW64 = nullptr, *froV = nullptr, *froW = nullptr, *opart = nullptr, *fobj = nullptr;
     int *counters = nullptr, *err = nullptr;
     double xx = 0.0;
@@ -685,9 +709,10 @@ int launch_gemm(nmf_handle *h, const NmfSide &sd, cudaStream_t st)
     return cudaGetLastError() == cudaSuccess ? COX_OK : COX_ERR_CUDA;
 }
 
-size_t upd_smem(int r) { return static_cast<size_t>(r * r + r * (UPD_THREADS + 1) + UPD_THREADS * ((r + 3) & ~3)) * sizeof(float); }
+size_t upd_smem(int r) { return static_cast<size_t>(r * r + r * (UPD_THREADS + 1)) * sizeof(float); }
 
-// side 0: V from X W^T (rows m); side 1: W from X^T V (rows n)
+// side 0: V from X W^T (rows m); side 1: W from X^T V (rows n); then the Gram
+// matrix of the new factor
 int launch_update(nmf_handle *h, int side, int mode, int algo, double eps, cudaStream_t st)
 {
     UpdArgs a;
@@ -707,14 +732,21 @@ int launch_update(nmf_handle *h, int side, int mode, int algo, double eps, cudaS
     a.Gin = side == 0 ? h->GW32 : h->GV32;
     a.fro_in = side == 0 ? h->froW : h->froV;
     a.eps = eps;
-    a.gpart = h->gpart;
-    a.counter = h->counters + side;
-    a.G64 = side == 0 ? h->GV64 : h->GW64;
-    a.G32 = side == 0 ? h->GV32 : h->GW32;
-    a.fro_out = side == 0 ? h->froV : h->froW;
     a.err = h->err;
     const unsigned blocks = static_cast<unsigned>((a.R + UPD_THREADS - 1) / UPD_THREADS);
     k_nmf_update<<<blocks, UPD_THREADS, upd_smem(h->r), st>>>(a);
+    ++h->launches;
+    if (cudaGetLastError() != cudaSuccess) return COX_ERR_CUDA;
+    GramArgs gm;
+    gm.r = h->r;
+    gm.R = a.R;
+    gm.F = a.F;
+    gm.G64 = side == 0 ? h->GV64 : h->GW64;
+    gm.G32 = side == 0 ? h->GV32 : h->GW32;
+    gm.fro = side == 0 ? h->froV : h->froW;
+    gm.counter = h->counters + side;
+    const int RB = (h->r + 3) / 4;
+    k_nmf_gram<<<static_cast<unsigned>(RB * (RB + 1) / 2), GRAM_THREADS, 0, st>>>(gm);
     ++h->launches;
     return cudaGetLastError() == cudaSuccess ? COX_OK : COX_ERR_CUDA;
 }
@@ -794,10 +826,6 @@ int setup_impl(const float *X, int64_t m, int64_t n, int r, int device, nmf_hand
             if ((rc = A(reinterpret_cast<void **>(p), 8)) != COX_OK) break;
         if (rc) break;
         const int64_t tiles = std::max((m + NT - 1) / NT, (n + NT - 1) / NT);
-        const int RB = ((r + 3) & ~3) / 4;
-        if ((rc = A(reinterpret_cast<void **>(&h->gpart), static_cast<size_t>(tiles) * RB * (RB + 1) / 2 * 16 * 4)) !=
-            COX_OK)
-            break;
         if ((rc = A(reinterpret_cast<void **>(&h->opart), static_cast<size_t>(tiles) * 8)) != COX_OK) break;
         if (cudaMemsetAsync(h->err, 0, sizeof(int), st) != cudaSuccess ||
             cudaMemsetAsync(h->counters, 0, 4 * sizeof(int), st) != cudaSuccess ||
@@ -975,7 +1003,7 @@ int nmf_iterate(nmf_h h, int algo, int64_t iters, double eps, void *stream)
         h->g_eps = eps;
     }
     for (int64_t t = 0; t < iters; ++t) COX_CUDA(cudaGraphLaunch(h->exec, st));
-    h->launches += 4 * iters;
+    h->launches += 6 * iters;
     return COX_OK;
 }
 

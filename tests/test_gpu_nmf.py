@@ -129,7 +129,7 @@ def test_switching_algorithm_and_eps(N):
     Vb, Wb = oracle.nmf(X, Va, Wa, 3, "apg", 1e-3)
     assert rel_l2(V, Vb) <= 2e-5 and rel_l2(W, Wb) <= 2e-5
     info = h.info()
-    assert info["launches"] >= 4 * 5 and info["limb_cols"] == 32
+    assert info["launches"] >= 6 * 5 and info["limb_cols"] == 32
     h.close()
 
 
