@@ -58,7 +58,8 @@ constexpr int A_BYTES = NT * NK * 2;    // 16 KB A box per stage
 constexpr int GEMM_THREADS = 192;       // TMA warp, MMA warp, four epilogue warps
 constexpr int MAX_STAGES = 8;
 constexpr int WINDOW = 8;               // K chunks one TMEM accumulator sums before the epilogue folds it
-constexpr int UPD_THREADS = 128;        // one thread per factor column of a row tile
+constexpr int UPD_THREADS = 128;        // objective kernel: one thread per row of a tile
+constexpr int UPD_ROWS = 64;            // update kernel: one thread per factor column, half a row tile per block
 constexpr long long NMF_DRAIN = 4000000000LL;  // ~2 s: copies and MMAs always finish
 __device__ int g_nmf_never = 0;                // abort flag of drain waits: never raised
 
@@ -313,40 +314,51 @@ __device__ __forceinline__ void split_bf16(float f, __nv_bfloat16 *h)
     h[2] = __float2bfloat16_rn(r1 - __bfloat162float(h[1]));
 }
 
-// One row tile of a factor: thread t owns column i = 128 g + t of F.  Shared
-// memory: G (r x r) and the old F ([c][129], conflict-free per c); the new
-// values go straight to F and its limbs (a thread reads only its own old
-// values, from shared memory).
-__global__ void __launch_bounds__(UPD_THREADS) k_nmf_update(const UpdArgs A)
+// Half a row tile of a factor per block: thread t owns column
+// i = 128 g + 64 h + t of F (block 2 g + h).  Shared memory: G (r x r), the
+// old F and the summed product partials ([c][65] each, conflict-free per c).
+// The new values go straight to F and its limbs (a thread reads only its own
+// old values, from shared memory).
+__global__ void __launch_bounds__(UPD_ROWS) k_nmf_update(const UpdArgs A)
 {
     extern __shared__ float sh[];
+    constexpr int LD = UPD_ROWS + 1;
     const int r = A.r, t = threadIdx.x;
     float *Gs = sh;
     float *Fo = Gs + r * r;
-    const int64_t g = blockIdx.x;
-    const int64_t i = g * UPD_THREADS + t;
+    float *Pc = Fo + r * LD;
+    const int64_t g = blockIdx.x / (NT / UPD_ROWS);
+    const int rit = static_cast<int>(blockIdx.x % (NT / UPD_ROWS)) * UPD_ROWS + t;  // row in the tile
+    const int64_t i = g * NT + rit;
     const bool valid = i < A.R;
     if (A.mode)
-        for (int e = t; e < r * r; e += UPD_THREADS) Gs[e] = A.Gin[e];
-    for (int c = 0; c < r; ++c) Fo[c * (UPD_THREADS + 1) + t] = valid ? A.F[c * A.R + i] : 0.f;
+        for (int e = t; e < r * r; e += UPD_ROWS) Gs[e] = A.Gin[e];
+#pragma unroll 4
+    for (int c = 0; c < r; ++c) Fo[c * LD + t] = valid ? A.F[c * A.R + i] : 0.f;
+    if (A.mode) {
+        const int64_t first = (g * A.KC) / A.L, last = (g * A.KC + A.KC - 1) / A.L;
+        const int ns = static_cast<int>(last - first + 1);
+        const float *pp = A.part + (g * A.SL * r) * NT + rit;
+#pragma unroll 4
+        for (int c = 0; c < r; ++c) {
+            double acc = 0.0;
+            for (int sl = 0; sl < ns; ++sl) acc += static_cast<double>(pp[(static_cast<int64_t>(sl) * r + c) * NT]);
+            Pc[c * LD + t] = static_cast<float>(acc);
+        }
+    }
     __syncthreads();
     if (!valid) return;
 
     bool bad = false;
     const float s = A.mode ? static_cast<float>(1.0 / (2.0 * *A.fro_in + A.eps)) : 0.f;
     const float eps = static_cast<float>(A.eps);
-    const int64_t first = (g * A.KC) / A.L, last = (g * A.KC + A.KC - 1) / A.L;
-    const int ns = static_cast<int>(last - first + 1);
-    const float *pp = A.part + (g * A.SL * r) * NT + t;
     for (int c = 0; c < r; ++c) {
-        const float old = Fo[c * (UPD_THREADS + 1) + t];
+        const float old = Fo[c * LD + t];
         float v = old;
         if (A.mode) {
-            double acc = 0.0;
-            for (int sl = 0; sl < ns; ++sl) acc += static_cast<double>(pp[(static_cast<int64_t>(sl) * r + c) * NT]);
-            const float pc = static_cast<float>(acc);
+            const float pc = Pc[c * LD + t];
             float den = 0.f;
-            for (int d = 0; d < r; ++d) den = fmaf(Gs[c * r + d], Fo[d * (UPD_THREADS + 1) + t], den);
+            for (int d = 0; d < r; ++d) den = fmaf(Gs[c * r + d], Fo[d * LD + t], den);
             v = A.algo == NMF_MULTIPLICATIVE ? old * pc / (den + eps) : fmaxf(0.f, old - s * (den - pc));
             bad |= !isfinite(v);
             A.F[c * A.R + i] = v;
@@ -360,30 +372,33 @@ __global__ void __launch_bounds__(UPD_THREADS) k_nmf_update(const UpdArgs A)
 }
 
 constexpr int GRAM_THREADS = 256;
-constexpr int GRAM_FLUSH = 32;  // FP32 runs of this many columns per thread, then added in FP64
+constexpr int GRAM_UNROLL = 4;  // columns a thread loads before it multiplies
 
 struct GramArgs {
-    int r;
-    int64_t R;
+    int r, JS;               // JS column slices per 4 x 4 block of G
+    int64_t R, slice;        // columns; columns per slice
     const float *F;          // r x R
+    double *gpart;           // [block pair][slice][16]
     double *G64;             // r x r
     float *G32;
     double *fro;             // ||G||_F^2
     int *counter;            // blocks done (reset by the last block)
 };
 
-// G = F F^T.  Block b takes the 4 x 4 block (cb, db), cb <= db, of G over all
-// R columns: each thread sums its columns (stride 256) in FP32 runs of
-// GRAM_FLUSH columns added into FP64, then warp shuffles and the eight warps
-// in order give the entries (a fixed order: deterministic).  The last block
-// to finish forms ||G||_F^2.
+// G = F F^T.  Block (bp, js) takes the 4 x 4 block bp = (cb, db), cb <= db, of
+// G over the columns of slice js: each thread sums its columns (stride 256,
+// GRAM_UNROLL at a time) in FP32, then warp shuffles and the eight warps in
+// order give the slice's FP64 partial.  The last block to finish adds the
+// slices in order for every entry and forms ||G||_F^2.  Fixed orders
+// throughout: deterministic.
 __global__ void __launch_bounds__(GRAM_THREADS) k_nmf_gram(const GramArgs A)
 {
     __shared__ double red[GRAM_THREADS / 32][16];
     __shared__ int is_last;
     const int r = A.r, t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int RB = (r + 3) / 4;
-    int cb = 0, rem = static_cast<int>(blockIdx.x);
+    const int RB = (r + 3) / 4, NBP = RB * (RB + 1) / 2;
+    const int bp = static_cast<int>(blockIdx.x) / A.JS, js = static_cast<int>(blockIdx.x) % A.JS;
+    int cb = 0, rem = bp;
     while (rem >= RB - cb) {
         rem -= RB - cb;
         ++cb;
@@ -395,37 +410,31 @@ __global__ void __launch_bounds__(GRAM_THREADS) k_nmf_gram(const GramArgs A)
         xr[a] = 4 * cb + a < r ? A.F + static_cast<int64_t>(4 * cb + a) * A.R : nullptr;
         yr[a] = 4 * db + a < r ? A.F + static_cast<int64_t>(4 * db + a) * A.R : nullptr;
     }
-    double acc64[16];
     float acc[16];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        acc64[e] = 0.0;
-        acc[e] = 0.f;
-    }
-    int run = 0;
-    for (int64_t j = t; j < A.R; j += GRAM_THREADS) {
-        float x[4], y[4];
+    for (int e = 0; e < 16; ++e) acc[e] = 0.f;
+    const int64_t j0 = js * A.slice, j1 = min(j0 + A.slice, A.R);
+    for (int64_t jb = j0 + t; jb < j1; jb += GRAM_THREADS * GRAM_UNROLL) {
+        float x[GRAM_UNROLL][4], y[GRAM_UNROLL][4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            x[a] = xr[a] ? __ldg(xr[a] + j) : 0.f;
-            y[a] = yr[a] ? __ldg(yr[a] + j) : 0.f;
-        }
+        for (int u = 0; u < GRAM_UNROLL; ++u) {
+            const int64_t j = jb + u * GRAM_THREADS;
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[4 * a + b] = fmaf(x[a], y[b], acc[4 * a + b]);
-        if (++run == GRAM_FLUSH) {
-            run = 0;
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                acc64[e] += static_cast<double>(acc[e]);
-                acc[e] = 0.f;
+            for (int a = 0; a < 4; ++a) {
+                x[u][a] = (xr[a] && j < j1) ? __ldg(xr[a] + j) : 0.f;
+                y[u][a] = (yr[a] && j < j1) ? __ldg(yr[a] + j) : 0.f;
             }
         }
+#pragma unroll
+        for (int u = 0; u < GRAM_UNROLL; ++u)
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[4 * a + b] = fmaf(x[u][a], y[u][b], acc[4 * a + b]);
     }
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
-        double v = acc64[e] + static_cast<double>(acc[e]);
+        double v = static_cast<double>(acc[e]);
         for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
         if (lane == 0) red[wid][e] = v;
     }
@@ -433,13 +442,7 @@ __global__ void __launch_bounds__(GRAM_THREADS) k_nmf_gram(const GramArgs A)
     if (t < 16) {
         double v = 0.0;
         for (int w = 0; w < GRAM_THREADS / 32; ++w) v += red[w][t];
-        const int c = 4 * cb + t / 4, d = 4 * db + t % 4;
-        if (c < r && d < r) {
-            A.G64[c * r + d] = v;
-            A.G64[d * r + c] = v;
-            A.G32[c * r + d] = static_cast<float>(v);
-            A.G32[d * r + c] = static_cast<float>(v);
-        }
+        A.gpart[(static_cast<int64_t>(bp) * A.JS + js) * 16 + t] = v;
     }
     __threadfence();
     __syncthreads();
@@ -448,17 +451,31 @@ __global__ void __launch_bounds__(GRAM_THREADS) k_nmf_gram(const GramArgs A)
     if (!is_last) return;
     __threadfence();
     double f = 0.0;
-    for (int e = t; e < r * r; e += GRAM_THREADS) {
-        const double gv = __ldcg(A.G64 + e);
-        f += gv * gv;
+    for (int e = t; e < NBP * 16; e += GRAM_THREADS) {
+        const int q = e / 16, k = e % 16;
+        int qc = 0, qr = q;
+        while (qr >= RB - qc) {
+            qr -= RB - qc;
+            ++qc;
+        }
+        const int c = 4 * qc + k / 4, d = 4 * (qc + qr) + k % 4;
+        if (c >= r || d >= r || (qr == 0 && d < c)) continue;
+        double v = 0.0;
+        for (int z = 0; z < A.JS; ++z) v += __ldcg(A.gpart + (static_cast<int64_t>(q) * A.JS + z) * 16 + k);
+        A.G64[c * r + d] = v;
+        A.G64[d * r + c] = v;
+        A.G32[c * r + d] = static_cast<float>(v);
+        A.G32[d * r + c] = static_cast<float>(v);
+        f += (c == d ? 1.0 : 2.0) * v * v;
     }
     for (int off = 16; off > 0; off >>= 1) f += __shfl_down_sync(0xffffffffu, f, off);
+    __syncthreads();
     if (lane == 0) red[wid][0] = f;
     __syncthreads();
     if (t == 0) {
-        double s = 0.0;
-        for (int w = 0; w < GRAM_THREADS / 32; ++w) s += red[w][0];
-        *A.fro = s;
+        double s2 = 0.0;
+        for (int w = 0; w < GRAM_THREADS / 32; ++w) s2 += red[w][0];
+        *A.fro = s2;
         *A.counter = 0;
     }
 }
@@ -633,6 +650,7 @@ struct nmf_handle {
     float *part1 = nullptr, *part2 = nullptr;
     NmfSide s1, s2;               // X W^T, X^T V
     float *GV32 = nullptr, *GW32 = nullptr;
+    double *gpart = nullptr;   // Gram partials [block pair][slice][16]
     double *GV64 = nullptr, *GW64 = nullptr, *froV = nullptr, *froW = nullptr, *opart = nullptr, *fobj = nullptr;
     int *counters = nullptr, *err = nullptr;
     double xx = 0.0;
@@ -709,7 +727,17 @@ int launch_gemm(nmf_handle *h, const NmfSide &sd, cudaStream_t st)
     return cudaGetLastError() == cudaSuccess ? COX_OK : COX_ERR_CUDA;
 }
 
-size_t upd_smem(int r) { return static_cast<size_t>(r * r + r * (UPD_THREADS + 1)) * sizeof(float); }
+size_t upd_smem(int r) { return static_cast<size_t>(r * r + 2 * r * (UPD_ROWS + 1)) * sizeof(float); }
+
+// Column slices per 4 x 4 block of a Gram matrix: about two blocks per SM in
+// all, at least 1024 columns per slice, at most 64 slices.
+int gram_slices(const nmf_handle *h, int64_t R)
+{
+    const int RB = (h->r + 3) / 4, NBP = RB * (RB + 1) / 2;
+    int64_t js = (2 * static_cast<int64_t>(h->sms) + NBP - 1) / NBP;
+    js = std::min<int64_t>(js, std::max<int64_t>(1, R / 1024));
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(js, 64)));
+}
 
 // side 0: V from X W^T (rows m); side 1: W from X^T V (rows n); then the Gram
 // matrix of the new factor
@@ -733,20 +761,23 @@ int launch_update(nmf_handle *h, int side, int mode, int algo, double eps, cudaS
     a.fro_in = side == 0 ? h->froW : h->froV;
     a.eps = eps;
     a.err = h->err;
-    const unsigned blocks = static_cast<unsigned>((a.R + UPD_THREADS - 1) / UPD_THREADS);
-    k_nmf_update<<<blocks, UPD_THREADS, upd_smem(h->r), st>>>(a);
+    const unsigned blocks = static_cast<unsigned>((a.R + NT - 1) / NT * (NT / UPD_ROWS));
+    k_nmf_update<<<blocks, UPD_ROWS, upd_smem(h->r), st>>>(a);
     ++h->launches;
     if (cudaGetLastError() != cudaSuccess) return COX_ERR_CUDA;
     GramArgs gm;
     gm.r = h->r;
     gm.R = a.R;
     gm.F = a.F;
+    const int RB = (h->r + 3) / 4, NBP = RB * (RB + 1) / 2;
+    gm.JS = gram_slices(h, a.R);
+    gm.slice = (a.R + gm.JS - 1) / gm.JS;
+    gm.gpart = h->gpart;
     gm.G64 = side == 0 ? h->GV64 : h->GW64;
     gm.G32 = side == 0 ? h->GV32 : h->GW32;
     gm.fro = side == 0 ? h->froV : h->froW;
     gm.counter = h->counters + side;
-    const int RB = (h->r + 3) / 4;
-    k_nmf_gram<<<static_cast<unsigned>(RB * (RB + 1) / 2), GRAM_THREADS, 0, st>>>(gm);
+    k_nmf_gram<<<static_cast<unsigned>(NBP * gm.JS), GRAM_THREADS, 0, st>>>(gm);
     ++h->launches;
     return cudaGetLastError() == cudaSuccess ? COX_OK : COX_ERR_CUDA;
 }
@@ -827,6 +858,12 @@ int setup_impl(const float *X, int64_t m, int64_t n, int r, int device, nmf_hand
         if (rc) break;
         const int64_t tiles = std::max((m + NT - 1) / NT, (n + NT - 1) / NT);
         if ((rc = A(reinterpret_cast<void **>(&h->opart), static_cast<size_t>(tiles) * 8)) != COX_OK) break;
+        {
+            const int RB = (r + 3) / 4;
+            if ((rc = A(reinterpret_cast<void **>(&h->gpart), static_cast<size_t>(RB * (RB + 1) / 2) * 64 * 16 * 8)) !=
+                COX_OK)
+                break;
+        }
         if (cudaMemsetAsync(h->err, 0, sizeof(int), st) != cudaSuccess ||
             cudaMemsetAsync(h->counters, 0, 4 * sizeof(int), st) != cudaSuccess ||
             cudaMemsetAsync(h->Vl, 0, static_cast<size_t>(h->NP * h->ldm) * 2, st) != cudaSuccess ||
