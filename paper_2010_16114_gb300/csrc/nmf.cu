@@ -4,11 +4,11 @@
 //
 // An iteration is six kernels:
 //   k_nmf_gemm    P = X W^T   (m x r)   tcgen05 kind::f16, A = X row-major
-//   k_nmf_update  V from P and W W^T; limbs of V
-//   k_nmf_gram    V^T V (FP64) and its squared Frobenius norm
+//   k_nmf_update  V from P and W W^T; limbs of V; per-block partials of V^T V
+//   k_nmf_gram    V^T V (FP64) from the partials
 //   k_nmf_gemm    Q = X^T V   (n x r)   A = X column-major
-//   k_nmf_update  W from Q and V^T V; limbs of W
-//   k_nmf_gram    W W^T and its norm
+//   k_nmf_update  W from Q and V^T V; limbs of W; partials of W W^T
+//   k_nmf_gram    W W^T
 // Both updates have one form.  With F a factor held r x R (V^T, or W), G the
 // Gram matrix of the other factor and P the product of X with it,
 //   (V W W^T)_ic = sum_d G_cd F_di  and  (V^T V W)_cj = sum_d G_cd F_dj
@@ -59,7 +59,6 @@ constexpr int GEMM_THREADS = 192;       // TMA warp, MMA warp, four epilogue war
 constexpr int MAX_STAGES = 8;
 constexpr int WINDOW = 8;               // K chunks one TMEM accumulator sums before the epilogue folds it
 constexpr int UPD_THREADS = 128;        // objective kernel: one thread per row of a tile
-constexpr int UPD_ROWS = 64;            // update kernel: one thread per factor column, half a row tile per block
 constexpr long long NMF_DRAIN = 4000000000LL;  // ~2 s: copies and MMAs always finish
 __device__ int g_nmf_never = 0;                // abort flag of drain waits: never raised
 
@@ -291,7 +290,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 }
 
 struct UpdArgs {
-    int r, rp, mode, algo;   // mode 1: update from the product; 0: limbs of F only
+    int r, rp, mode, algo;   // mode 1: update from the product; 0: limbs and Gram partials of F only
     int64_t R;               // factor columns (m for V, n for W)
     float *F;                // r x R, row c at c R
     __nv_bfloat16 *limb;     // NP x ldl: row l rp + c holds limb l of F row c
@@ -299,184 +298,145 @@ struct UpdArgs {
     const float *part;       // product partials of this side
     int SL, KC;
     int64_t L;
-    const float *Gin;        // r x r Gram of the other factor
-    const double *fro_in;    // its squared Frobenius norm
+    const float *Gin;        // r x r Gram of the other factor, FP32
+    const double *Gin64;     // and FP64 (its squared Frobenius norm sets the APG step)
     double eps;
+    float *gpart;            // Gram partials of the new F: [pair][block], pairs c <= d
+    int nblk;                // blocks of this launch
     int *err;
 };
 
 // Split f into three bf16 limbs, f = h0 + h1 + h2 (exact for an FP32 f).
-__device__ __forceinline__ void split_bf16(float f, __nv_bfloat16 *h)
+__device__ __forceinline__ void split_bf16(float f, __nv_bfloat16 &h0, __nv_bfloat16 &h1, __nv_bfloat16 &h2)
 {
-    h[0] = __float2bfloat16_rn(f);
-    const float r1 = f - __bfloat162float(h[0]);
-    h[1] = __float2bfloat16_rn(r1);
-    h[2] = __float2bfloat16_rn(r1 - __bfloat162float(h[1]));
+    h0 = __float2bfloat16_rn(f);
+    const float r1 = f - __bfloat162float(h0);
+    h1 = __float2bfloat16_rn(r1);
+    h2 = __float2bfloat16_rn(r1 - __bfloat162float(h1));
 }
 
-// Half a row tile of a factor per block: thread t owns column
-// i = 128 g + 64 h + t of F (block 2 g + h).  Shared memory: G (r x r), the
-// old F and the summed product partials ([c][65] each, conflict-free per c).
-// The new values go straight to F and its limbs (a thread reads only its own
-// old values, from shared memory).
-__global__ void __launch_bounds__(UPD_ROWS) k_nmf_update(const UpdArgs A)
+// Pair p of the upper triangle (c <= d, row by row) of an r x r matrix.
+__device__ __forceinline__ void pair_cd(int p, int r, int &c, int &d)
+{
+    c = 0;
+    while (p >= r - c) {
+        p -= r - c;
+        ++c;
+    }
+    d = c + p;
+}
+
+constexpr int UPD_ROWS = 32;                   // factor columns per block (one per lane)
+constexpr int UPD_LANES = 8;                   // warps per block: rank rows c = warp, warp + 8, ...
+constexpr int UPD_BLOCK = UPD_ROWS * UPD_LANES;
+
+// A quarter row tile of a factor per block: lane x of every warp owns column
+// i = 128 g + 32 q + x of F (block 4 g + q); warp y takes the rank rows
+// c = y, y + 8, ...  Shared memory: G (r x r), the old and the new F and the
+// summed product partials ([c][33] each).  The block also leaves its partial
+// of the new F's Gram matrix over its 32 columns (FP32), one per pair c <= d.
+__global__ void __launch_bounds__(UPD_BLOCK) k_nmf_update(const UpdArgs A)
 {
     extern __shared__ float sh[];
+    __shared__ double red[UPD_BLOCK];
     constexpr int LD = UPD_ROWS + 1;
-    const int r = A.r, t = threadIdx.x;
+    const int r = A.r, t = threadIdx.x, x = t % UPD_ROWS, y = t / UPD_ROWS;
     float *Gs = sh;
     float *Fo = Gs + r * r;
-    float *Pc = Fo + r * LD;
+    float *Fn = Fo + r * LD;
+    float *Pc = Fn + r * LD;
     const int64_t g = blockIdx.x / (NT / UPD_ROWS);
-    const int rit = static_cast<int>(blockIdx.x % (NT / UPD_ROWS)) * UPD_ROWS + t;  // row in the tile
+    const int rit = static_cast<int>(blockIdx.x % (NT / UPD_ROWS)) * UPD_ROWS + x;  // row in the tile
     const int64_t i = g * NT + rit;
     const bool valid = i < A.R;
-    if (A.mode)
-        for (int e = t; e < r * r; e += UPD_ROWS) Gs[e] = A.Gin[e];
-#pragma unroll 4
-    for (int c = 0; c < r; ++c) Fo[c * LD + t] = valid ? A.F[c * A.R + i] : 0.f;
+    double fro = 0.0;
     if (A.mode) {
+        for (int e = t; e < r * r; e += UPD_BLOCK) {
+            Gs[e] = A.Gin[e];
+            const double gv = A.Gin64[e];
+            fro += gv * gv;
+        }
         const int64_t first = (g * A.KC) / A.L, last = (g * A.KC + A.KC - 1) / A.L;
         const int ns = static_cast<int>(last - first + 1);
         const float *pp = A.part + (g * A.SL * r) * NT + rit;
-#pragma unroll 4
-        for (int c = 0; c < r; ++c) {
+        for (int c = y; c < r; c += UPD_LANES) {
             double acc = 0.0;
             for (int sl = 0; sl < ns; ++sl) acc += static_cast<double>(pp[(static_cast<int64_t>(sl) * r + c) * NT]);
-            Pc[c * LD + t] = static_cast<float>(acc);
+            Pc[c * LD + x] = static_cast<float>(acc);
         }
     }
+    for (int c = y; c < r; c += UPD_LANES) Fo[c * LD + x] = valid ? A.F[c * A.R + i] : 0.f;
+    red[t] = fro;
     __syncthreads();
-    if (!valid) return;
-
-    bool bad = false;
-    const float s = A.mode ? static_cast<float>(1.0 / (2.0 * *A.fro_in + A.eps)) : 0.f;
+    for (int w = UPD_BLOCK / 2; w > 0; w >>= 1) {  // ||G||_F^2 in a fixed order (the same in every block)
+        if (t < w) red[t] += red[t + w];
+        __syncthreads();
+    }
+    const float s = A.mode ? static_cast<float>(1.0 / (2.0 * red[0] + A.eps)) : 0.f;
     const float eps = static_cast<float>(A.eps);
-    for (int c = 0; c < r; ++c) {
-        const float old = Fo[c * LD + t];
+    bool bad = false;
+    for (int c = y; c < r; c += UPD_LANES) {
+        const float old = Fo[c * LD + x];
         float v = old;
-        if (A.mode) {
-            const float pc = Pc[c * LD + t];
+        if (A.mode && valid) {
+            const float pc = Pc[c * LD + x];
             float den = 0.f;
-            for (int d = 0; d < r; ++d) den = fmaf(Gs[c * r + d], Fo[d * LD + t], den);
+            for (int d = 0; d < r; ++d) den = fmaf(Gs[c * r + d], Fo[d * LD + x], den);
             v = A.algo == NMF_MULTIPLICATIVE ? old * pc / (den + eps) : fmaxf(0.f, old - s * (den - pc));
             bad |= !isfinite(v);
             A.F[c * A.R + i] = v;
         }
-        __nv_bfloat16 h[3];
-        split_bf16(v, h);
-#pragma unroll
-        for (int l = 0; l < 3; ++l) A.limb[static_cast<int64_t>(l * A.rp + c) * A.ldl + i] = h[l];
+        if (!valid) v = 0.f;
+        Fn[c * LD + x] = v;
+        if (valid) {
+            __nv_bfloat16 h0, h1, h2;
+            split_bf16(v, h0, h1, h2);
+            A.limb[static_cast<int64_t>(c) * A.ldl + i] = h0;
+            A.limb[static_cast<int64_t>(A.rp + c) * A.ldl + i] = h1;
+            A.limb[static_cast<int64_t>(2 * A.rp + c) * A.ldl + i] = h2;
+        }
     }
     if (bad) atomicOr(A.err, NMF_ERR_NONFINITE);
+    __syncthreads();
+    // Gram partial over the block's 32 columns (zero for columns past R)
+    const int npair = r * (r + 1) / 2;
+    for (int p = t; p < npair; p += UPD_BLOCK) {
+        int c, d;
+        pair_cd(p, r, c, d);
+        float acc = 0.f;
+#pragma unroll 8
+        for (int j = 0; j < UPD_ROWS; ++j) acc = fmaf(Fn[c * LD + j], Fn[d * LD + j], acc);
+        A.gpart[static_cast<int64_t>(p) * A.nblk + blockIdx.x] = acc;
+    }
 }
 
-constexpr int GRAM_THREADS = 256;
-constexpr int GRAM_UNROLL = 4;  // columns a thread loads before it multiplies
-
 struct GramArgs {
-    int r, JS;               // JS column slices per 4 x 4 block of G
-    int64_t R, slice;        // columns; columns per slice
-    const float *F;          // r x R
-    double *gpart;           // [block pair][slice][16]
+    int r, nblk;
+    const float *gpart;      // [pair][block]
     double *G64;             // r x r
     float *G32;
-    double *fro;             // ||G||_F^2
-    int *counter;            // blocks done (reset by the last block)
 };
 
-// G = F F^T.  Block (bp, js) takes the 4 x 4 block bp = (cb, db), cb <= db, of
-// G over the columns of slice js: each thread sums its columns (stride 256,
-// GRAM_UNROLL at a time) in FP32, then warp shuffles and the eight warps in
-// order give the slice's FP64 partial.  The last block to finish adds the
-// slices in order for every entry and forms ||G||_F^2.  Fixed orders
-// throughout: deterministic.
-__global__ void __launch_bounds__(GRAM_THREADS) k_nmf_gram(const GramArgs A)
+// G = F F^T from the update blocks' partials: one warp per pair c <= d, lane
+// sums of the blocks b = lane, lane + 32, ... in FP64 and a shuffle tree (a
+// fixed order: deterministic).
+__global__ void __launch_bounds__(256) k_nmf_gram(const GramArgs A)
 {
-    __shared__ double red[GRAM_THREADS / 32][16];
-    __shared__ int is_last;
-    const int r = A.r, t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int RB = (r + 3) / 4, NBP = RB * (RB + 1) / 2;
-    const int bp = static_cast<int>(blockIdx.x) / A.JS, js = static_cast<int>(blockIdx.x) % A.JS;
-    int cb = 0, rem = bp;
-    while (rem >= RB - cb) {
-        rem -= RB - cb;
-        ++cb;
-    }
-    const int db = cb + rem;
-    const float *xr[4], *yr[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        xr[a] = 4 * cb + a < r ? A.F + static_cast<int64_t>(4 * cb + a) * A.R : nullptr;
-        yr[a] = 4 * db + a < r ? A.F + static_cast<int64_t>(4 * db + a) * A.R : nullptr;
-    }
-    float acc[16];
-#pragma unroll
-    for (int e = 0; e < 16; ++e) acc[e] = 0.f;
-    const int64_t j0 = js * A.slice, j1 = min(j0 + A.slice, A.R);
-    for (int64_t jb = j0 + t; jb < j1; jb += GRAM_THREADS * GRAM_UNROLL) {
-        float x[GRAM_UNROLL][4], y[GRAM_UNROLL][4];
-#pragma unroll
-        for (int u = 0; u < GRAM_UNROLL; ++u) {
-            const int64_t j = jb + u * GRAM_THREADS;
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                x[u][a] = (xr[a] && j < j1) ? __ldg(xr[a] + j) : 0.f;
-                y[u][a] = (yr[a] && j < j1) ? __ldg(yr[a] + j) : 0.f;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < GRAM_UNROLL; ++u)
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[4 * a + b] = fmaf(x[u][a], y[u][b], acc[4 * a + b]);
-    }
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        double v = static_cast<double>(acc[e]);
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        if (lane == 0) red[wid][e] = v;
-    }
-    __syncthreads();
-    if (t < 16) {
-        double v = 0.0;
-        for (int w = 0; w < GRAM_THREADS / 32; ++w) v += red[w][t];
-        A.gpart[(static_cast<int64_t>(bp) * A.JS + js) * 16 + t] = v;
-    }
-    __threadfence();
-    __syncthreads();
-    if (t == 0) is_last = atomicAdd(A.counter, 1) == static_cast<int>(gridDim.x) - 1;
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    double f = 0.0;
-    for (int e = t; e < NBP * 16; e += GRAM_THREADS) {
-        const int q = e / 16, k = e % 16;
-        int qc = 0, qr = q;
-        while (qr >= RB - qc) {
-            qr -= RB - qc;
-            ++qc;
-        }
-        const int c = 4 * qc + k / 4, d = 4 * (qc + qr) + k % 4;
-        if (c >= r || d >= r || (qr == 0 && d < c)) continue;
-        double v = 0.0;
-        for (int z = 0; z < A.JS; ++z) v += __ldcg(A.gpart + (static_cast<int64_t>(q) * A.JS + z) * 16 + k);
+    const int lane = threadIdx.x & 31;
+    const int p = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int r = A.r;
+    if (p >= r * (r + 1) / 2) return;
+    const float *src = A.gpart + static_cast<int64_t>(p) * A.nblk;
+    double v = 0.0;
+    for (int b = lane; b < A.nblk; b += 32) v += static_cast<double>(src[b]);
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) {
+        int c, d;
+        pair_cd(p, r, c, d);
         A.G64[c * r + d] = v;
         A.G64[d * r + c] = v;
         A.G32[c * r + d] = static_cast<float>(v);
         A.G32[d * r + c] = static_cast<float>(v);
-        f += (c == d ? 1.0 : 2.0) * v * v;
-    }
-    for (int off = 16; off > 0; off >>= 1) f += __shfl_down_sync(0xffffffffu, f, off);
-    __syncthreads();
-    if (lane == 0) red[wid][0] = f;
-    __syncthreads();
-    if (t == 0) {
-        double s2 = 0.0;
-        for (int w = 0; w < GRAM_THREADS / 32; ++w) s2 += red[w][0];
-        *A.fro = s2;
-        *A.counter = 0;
     }
 }
 
@@ -650,8 +610,8 @@ struct nmf_handle {
     float *part1 = nullptr, *part2 = nullptr;
     NmfSide s1, s2;               // X W^T, X^T V
     float *GV32 = nullptr, *GW32 = nullptr;
-    double *gpart = nullptr;   // Gram partials [block pair][slice][16]
-    double *GV64 = nullptr, *GW64 = nullptr, *froV = nullptr, *froW = nullptr, *opart = nullptr, *fobj = nullptr;
+    float *gpart = nullptr;    // Gram partials [pair][update block]
+    double *GV64 = nullptr, *GW64 = nullptr, *opart = nullptr, *fobj = nullptr;
     int *counters = nullptr, *err = nullptr;
     double xx = 0.0;
     long long wait_cycles = 0;
@@ -727,20 +687,12 @@ int launch_gemm(nmf_handle *h, const NmfSide &sd, cudaStream_t st)
     return cudaGetLastError() == cudaSuccess ? COX_OK : COX_ERR_CUDA;
 }
 
-size_t upd_smem(int r) { return static_cast<size_t>(r * r + 2 * r * (UPD_ROWS + 1)) * sizeof(float); }
+size_t upd_smem(int r) { return static_cast<size_t>(r * r + 3 * r * (UPD_ROWS + 1)) * sizeof(float); }
 
-// Column slices per 4 x 4 block of a Gram matrix: about two blocks per SM in
-// all, at least 1024 columns per slice, at most 64 slices.
-int gram_slices(const nmf_handle *h, int64_t R)
-{
-    const int RB = (h->r + 3) / 4, NBP = RB * (RB + 1) / 2;
-    int64_t js = (2 * static_cast<int64_t>(h->sms) + NBP - 1) / NBP;
-    js = std::min<int64_t>(js, std::max<int64_t>(1, R / 1024));
-    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(js, 64)));
-}
+int upd_blocks(int64_t R) { return static_cast<int>((R + NT - 1) / NT * (NT / UPD_ROWS)); }
 
 // side 0: V from X W^T (rows m); side 1: W from X^T V (rows n); then the Gram
-// matrix of the new factor
+// matrix of the new factor from the blocks' partials
 int launch_update(nmf_handle *h, int side, int mode, int algo, double eps, cudaStream_t st)
 {
     UpdArgs a;
@@ -758,26 +710,22 @@ int launch_update(nmf_handle *h, int side, int mode, int algo, double eps, cudaS
     a.KC = sd.g.KC;
     a.L = sd.g.L;
     a.Gin = side == 0 ? h->GW32 : h->GV32;
-    a.fro_in = side == 0 ? h->froW : h->froV;
+    a.Gin64 = side == 0 ? h->GW64 : h->GV64;
     a.eps = eps;
+    a.gpart = h->gpart;
+    a.nblk = upd_blocks(a.R);
     a.err = h->err;
-    const unsigned blocks = static_cast<unsigned>((a.R + NT - 1) / NT * (NT / UPD_ROWS));
-    k_nmf_update<<<blocks, UPD_ROWS, upd_smem(h->r), st>>>(a);
+    k_nmf_update<<<a.nblk, UPD_BLOCK, upd_smem(h->r), st>>>(a);
     ++h->launches;
     if (cudaGetLastError() != cudaSuccess) return COX_ERR_CUDA;
     GramArgs gm;
     gm.r = h->r;
-    gm.R = a.R;
-    gm.F = a.F;
-    const int RB = (h->r + 3) / 4, NBP = RB * (RB + 1) / 2;
-    gm.JS = gram_slices(h, a.R);
-    gm.slice = (a.R + gm.JS - 1) / gm.JS;
+    gm.nblk = a.nblk;
     gm.gpart = h->gpart;
     gm.G64 = side == 0 ? h->GV64 : h->GW64;
     gm.G32 = side == 0 ? h->GV32 : h->GW32;
-    gm.fro = side == 0 ? h->froV : h->froW;
-    gm.counter = h->counters + side;
-    k_nmf_gram<<<static_cast<unsigned>(NBP * gm.JS), GRAM_THREADS, 0, st>>>(gm);
+    const int npair = h->r * (h->r + 1) / 2;
+    k_nmf_gram<<<(npair + 7) / 8, 256, 0, st>>>(gm);
     ++h->launches;
     return cudaGetLastError() == cudaSuccess ? COX_OK : COX_ERR_CUDA;
 }
@@ -853,17 +801,12 @@ int setup_impl(const float *X, int64_t m, int64_t n, int r, int device, nmf_hand
         for (double **p : {&h->GV64, &h->GW64})
             if ((rc = A(reinterpret_cast<void **>(p), static_cast<size_t>(r * r) * 8)) != COX_OK) break;
         if (rc) break;
-        for (double **p : {&h->froV, &h->froW, &h->fobj})
-            if ((rc = A(reinterpret_cast<void **>(p), 8)) != COX_OK) break;
-        if (rc) break;
+        if ((rc = A(reinterpret_cast<void **>(&h->fobj), 8)) != COX_OK) break;
         const int64_t tiles = std::max((m + NT - 1) / NT, (n + NT - 1) / NT);
         if ((rc = A(reinterpret_cast<void **>(&h->opart), static_cast<size_t>(tiles) * 8)) != COX_OK) break;
-        {
-            const int RB = (r + 3) / 4;
-            if ((rc = A(reinterpret_cast<void **>(&h->gpart), static_cast<size_t>(RB * (RB + 1) / 2) * 64 * 16 * 8)) !=
-                COX_OK)
-                break;
-        }
+        if ((rc = A(reinterpret_cast<void **>(&h->gpart), static_cast<size_t>(r * (r + 1) / 2) *
+                                                                  upd_blocks(std::max(m, n)) * sizeof(float))) != COX_OK)
+            break;
         if (cudaMemsetAsync(h->err, 0, sizeof(int), st) != cudaSuccess ||
             cudaMemsetAsync(h->counters, 0, 4 * sizeof(int), st) != cudaSuccess ||
             cudaMemsetAsync(h->Vl, 0, static_cast<size_t>(h->NP * h->ldm) * 2, st) != cudaSuccess ||
@@ -873,8 +816,7 @@ int setup_impl(const float *X, int64_t m, int64_t n, int r, int device, nmf_hand
             cudaMemsetAsync(h->GV32, 0, static_cast<size_t>(r * r) * 4, st) != cudaSuccess ||
             cudaMemsetAsync(h->GW32, 0, static_cast<size_t>(r * r) * 4, st) != cudaSuccess ||
             cudaMemsetAsync(h->GV64, 0, static_cast<size_t>(r * r) * 8, st) != cudaSuccess ||
-            cudaMemsetAsync(h->GW64, 0, static_cast<size_t>(r * r) * 8, st) != cudaSuccess ||
-            cudaMemsetAsync(h->froV, 0, 8, st) != cudaSuccess || cudaMemsetAsync(h->froW, 0, 8, st) != cudaSuccess) {
+            cudaMemsetAsync(h->GW64, 0, static_cast<size_t>(r * r) * 8, st) != cudaSuccess) {
             rc = COX_ERR_CUDA;
             break;
         }
