@@ -123,6 +123,29 @@ def gemm_traffic(k: int, n: int, p: int):
         return None
 
 
+def nmf_traffic(m: int, n: int, r: int):
+    """DRAM bytes per launch of the NMF product from the committed ncu summary
+    (taken at this workload's full size); None for another workload or when the
+    kernel source changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_nmf_gemm_traffic_m10000_n10000_r20.txt")
+    src = os.path.join(ROOT, "paper_2010_16114_gb300", "csrc", "nmf_gemm.cuh")
+    try:
+        kv = {}
+        with open(path) as fh:
+            for line in fh:
+                if ":" in line:
+                    a, b = line.split(":", 1)
+                    kv[a.strip()] = b.strip()
+        with open(src, "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()
+        if kv.get("source_sha256") != sha or (m, n, r) != (int(kv["m"]), int(kv["n"]), int(kv["r"])):
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 # ------------------------------------------------------------------ distributed plumbing
 def dist_init(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -305,7 +328,7 @@ def run_reference(args, rank, world):
 NMF_PAPER_1GPU_S = {20: {"mult": 62, "apg": 61}, 40: {"mult": 72, "apg": 80}, 60: {"mult": 83, "apg": 85}}
 
 
-def run_nmf(args, stream):
+def run_nmf(args, stream, cpu_baseline: bool = False):
     """Section 5.1 NMF on one GPU: X m x n (grid k / 256, exact in bf16), rank r,
     both algorithms; device-resident iterations timed with CUDA events, the two
     tensor-core products timed per launch for the roofline, and an end-to-end
@@ -357,7 +380,7 @@ def run_nmf(args, stream):
     out["roofline"] = {"bound": "hbm", "kernel": "k_nmf_gemm (both products)", "achieved": achieved,
                        "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
                        "ms_x_wt": a_ms, "ms_vt_x": b_ms, "bytes_per_launch": (pa + pb) / 2,
-                       "tensor_tflops": flops / (avg_ms / 1e3) / 1e12, "traffic": None}
+                       "tensor_tflops": flops / (avg_ms / 1e3) / 1e12, "traffic": nmf_traffic(m, n, r)}
     out["product_share_of_iteration"] = (a_ms + b_ms) / out["mult"]["ms_per_iter"]
     # end to end: host factors in, iterations, host factors out
     e2e_it = max(1, iters // 2)
@@ -371,6 +394,17 @@ def run_nmf(args, stream):
                   "h2d_bytes": int(4 * r * (m + n)), "d2h_bytes": int(4 * r * (m + n)),
                   "timing": "wall clock: nmf_set_factors, nmf_iterate, nmf_get_factors (host arrays)"}
     h.close()
+    if cpu_baseline:
+        # the FP64 oracle as it stands (one thread), one multiplicative iteration
+        # of the same workload
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        oracle.nmf(X, V0, W0, 1, "mult", 1e-10)
+        cs = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": 1.0 / cs, "unit": "iter/s", "cores": 1, "kind": "oracle",
+                               "sample": f"one multiplicative iteration of the full {m} x {n}, r = {r} workload "
+                                         "(orc_nmf, FP64, one thread)"}
     return out
 
 
@@ -387,7 +421,8 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(local)
     if args.nmf_only:
         if rank == 0:
-            print(json.dumps({"nmf": run_nmf(args, torch.cuda.current_stream())}), flush=True)
+            print(json.dumps({"nmf": run_nmf(args, torch.cuda.current_stream(),
+                                             cpu_baseline=world == 1 and not args.no_cpu_baseline)}), flush=True)
         return 0
     r = recipe(args)
     n, p, k = r.n, r.p, r.k
@@ -564,7 +599,8 @@ def run_ours(args, rank, world):
     prob.close()
     del beta
     torch.cuda.empty_cache()
-    nmf = run_nmf(args, stream) if (rank == 0 and args.nmf_iters > 0) else None
+    nmf = (run_nmf(args, stream, cpu_baseline=world == 1 and not args.no_cpu_baseline)
+           if (rank == 0 and args.nmf_iters > 0) else None)
     if rank != 0:
         return 0
     line = {
