@@ -77,21 +77,25 @@ __device__ __forceinline__ void pair_cd(int p, int r, int &c, int &d)
     d = c + p;
 }
 
-constexpr int UPD_ROWS = 32;                   // factor columns per block (one per lane)
-constexpr int UPD_LANES = 8;                   // warps per block: rank rows c = warp, warp + 8, ...
-constexpr int UPD_BLOCK = UPD_ROWS * UPD_LANES;
+constexpr int UPD_ROWS = 32;    // factor columns per block (one per lane)
+constexpr int UPD_MAXW = 32;    // warps per block: min(r, 32); warp y takes rank rows c = y, y + W, ...
+
+int upd_warps(int r) { return r < UPD_MAXW ? r : UPD_MAXW; }
 
 // A quarter row tile of a factor per block: lane x of every warp owns column
-// i = 128 g + 32 q + x of F (block 4 g + q); warp y takes the rank rows
-// c = y, y + 8, ...  Shared memory: G (r x r), the old and the new F and the
-// summed product partials ([c][33] each).  The block also leaves its partial
-// of the new F's Gram matrix over its 32 columns (FP32), one per pair c <= d.
-__global__ void __launch_bounds__(UPD_BLOCK) k_nmf_update(const UpdArgs A)
+// i = 128 g + 32 q + x of F (block 4 g + q); warp y of W = min(r, 32) takes
+// the rank rows c = y, y + W, ...  Shared memory: G (r x r), the old and the
+// new F and the summed product partials ([c][33] each).  The block also
+// leaves its partial of the new F's Gram matrix over its 32 columns (FP32),
+// one per pair c <= d.  Dot products run in four interleaved FP32 sums (a
+// fixed order) to shorten the dependent chains.
+__global__ void __launch_bounds__(UPD_ROWS * UPD_MAXW) k_nmf_update(const UpdArgs A)
 {
     extern __shared__ float sh[];
-    __shared__ double red[UPD_BLOCK];
+    __shared__ double fro_s;
     constexpr int LD = UPD_ROWS + 1;
     const int r = A.r, t = threadIdx.x, x = t % UPD_ROWS, y = t / UPD_ROWS;
+    const int W = blockDim.x / UPD_ROWS, nthr = blockDim.x;
     float *Gs = sh;
     float *Fo = Gs + r * r;
     float *Fn = Fo + r * LD;
@@ -100,39 +104,45 @@ __global__ void __launch_bounds__(UPD_BLOCK) k_nmf_update(const UpdArgs A)
     const int rit = static_cast<int>(blockIdx.x % (NT / UPD_ROWS)) * UPD_ROWS + x;  // row in the tile
     const int64_t i = g * NT + rit;
     const bool valid = i < A.R;
-    double fro = 0.0;
     if (A.mode) {
-        for (int e = t; e < r * r; e += UPD_BLOCK) {
-            Gs[e] = A.Gin[e];
-            const double gv = A.Gin64[e];
-            fro += gv * gv;
+        for (int e = t; e < r * r; e += nthr) Gs[e] = A.Gin[e];
+        if (y == 0) {  // ||G||_F^2 in one fixed order (the same in every block)
+            double f = 0.0;
+            for (int e = x; e < r * r; e += 32) {
+                const double gv = A.Gin64[e];
+                f += gv * gv;
+            }
+            for (int off = 16; off > 0; off >>= 1) f += __shfl_down_sync(0xffffffffu, f, off);
+            if (x == 0) fro_s = f;
         }
         const int64_t first = (g * A.KC) / A.L, last = (g * A.KC + A.KC - 1) / A.L;
         const int ns = static_cast<int>(last - first + 1);
         const float *pp = A.part + (g * A.SL * r) * NT + rit;
-        for (int c = y; c < r; c += UPD_LANES) {
+        for (int c = y; c < r; c += W) {
             double acc = 0.0;
             for (int sl = 0; sl < ns; ++sl) acc += static_cast<double>(pp[(static_cast<int64_t>(sl) * r + c) * NT]);
             Pc[c * LD + x] = static_cast<float>(acc);
         }
     }
-    for (int c = y; c < r; c += UPD_LANES) Fo[c * LD + x] = valid ? A.F[c * A.R + i] : 0.f;
-    red[t] = fro;
+    for (int c = y; c < r; c += W) Fo[c * LD + x] = valid ? A.F[c * A.R + i] : 0.f;
     __syncthreads();
-    for (int w = UPD_BLOCK / 2; w > 0; w >>= 1) {  // ||G||_F^2 in a fixed order (the same in every block)
-        if (t < w) red[t] += red[t + w];
-        __syncthreads();
-    }
-    const float s = A.mode ? static_cast<float>(1.0 / (2.0 * red[0] + A.eps)) : 0.f;
+    const float s = A.mode ? static_cast<float>(1.0 / (2.0 * fro_s + A.eps)) : 0.f;
     const float eps = static_cast<float>(A.eps);
     bool bad = false;
-    for (int c = y; c < r; c += UPD_LANES) {
+    for (int c = y; c < r; c += W) {
         const float old = Fo[c * LD + x];
         float v = old;
         if (A.mode && valid) {
             const float pc = Pc[c * LD + x];
-            float den = 0.f;
-            for (int d = 0; d < r; ++d) den = fmaf(Gs[c * r + d], Fo[d * LD + x], den);
+            float d4[4] = {0.f, 0.f, 0.f, 0.f};
+            const float *gr = Gs + c * r;
+            int d = 0;
+            for (; d + 4 <= r; d += 4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) d4[q] = fmaf(gr[d + q], Fo[(d + q) * LD + x], d4[q]);
+            }
+            for (; d < r; ++d) d4[0] = fmaf(gr[d], Fo[d * LD + x], d4[0]);
+            const float den = (d4[0] + d4[1]) + (d4[2] + d4[3]);
             v = A.algo == NMF_MULTIPLICATIVE ? old * pc / (den + eps) : fmaxf(0.f, old - s * (den - pc));
             bad |= !isfinite(v);
             A.F[c * A.R + i] = v;
@@ -151,13 +161,17 @@ __global__ void __launch_bounds__(UPD_BLOCK) k_nmf_update(const UpdArgs A)
     __syncthreads();
     // Gram partial over the block's 32 columns (zero for columns past R)
     const int npair = r * (r + 1) / 2;
-    for (int p = t; p < npair; p += UPD_BLOCK) {
+    for (int p = t; p < npair; p += nthr) {
         int c, d;
         pair_cd(p, r, c, d);
-        float acc = 0.f;
-#pragma unroll 8
-        for (int j = 0; j < UPD_ROWS; ++j) acc = fmaf(Fn[c * LD + j], Fn[d * LD + j], acc);
-        A.gpart[static_cast<int64_t>(p) * A.nblk + blockIdx.x] = acc;
+        const float *fc = Fn + c * LD, *fd = Fn + d * LD;
+        float a4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < UPD_ROWS; j += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a4[q] = fmaf(fc[j + q], fd[j + q], a4[q]);
+        }
+        A.gpart[static_cast<int64_t>(p) * A.nblk + blockIdx.x] = (a4[0] + a4[1]) + (a4[2] + a4[3]);
     }
 }
 
@@ -178,8 +192,14 @@ __global__ void __launch_bounds__(256) k_nmf_gram(const GramArgs A)
     const int r = A.r;
     if (p >= r * (r + 1) / 2) return;
     const float *src = A.gpart + static_cast<int64_t>(p) * A.nblk;
-    double v = 0.0;
-    for (int b = lane; b < A.nblk; b += 32) v += static_cast<double>(src[b]);
+    double v0 = 0.0, v1 = 0.0;  // blocks lane + 64 j and lane + 32 + 64 j
+    int b = lane;
+    for (; b + 32 < A.nblk; b += 64) {
+        v0 += static_cast<double>(src[b]);
+        v1 += static_cast<double>(src[b + 32]);
+    }
+    if (b < A.nblk) v0 += static_cast<double>(src[b]);
+    double v = v0 + v1;
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     if (lane == 0) {
         int c, d;
@@ -466,7 +486,7 @@ int launch_update(nmf_handle *h, int side, int mode, int algo, double eps, cudaS
     a.gpart = h->gpart;
     a.nblk = upd_blocks(a.R);
     a.err = h->err;
-    k_nmf_update<<<a.nblk, UPD_BLOCK, upd_smem(h->r), st>>>(a);
+    k_nmf_update<<<a.nblk, UPD_ROWS * upd_warps(h->r), upd_smem(h->r), st>>>(a);
     ++h->launches;
     if (cudaGetLastError() != cudaSuccess) return COX_ERR_CUDA;
     GramArgs gm;
