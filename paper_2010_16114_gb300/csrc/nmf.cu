@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <utility>
 #include <vector>
 
 #include "internal.h"
@@ -92,10 +93,13 @@ int upd_warps(int r) { return r < UPD_MAXW ? r : UPD_MAXW; }
 __global__ void __launch_bounds__(UPD_ROWS * UPD_MAXW) k_nmf_update(const UpdArgs A)
 {
     extern __shared__ float sh[];
+    __shared__ double fro_w[UPD_MAXW];
     __shared__ double fro_s;
     constexpr int LD = UPD_ROWS + 1;
     const int r = A.r, t = threadIdx.x, x = t % UPD_ROWS, y = t / UPD_ROWS;
     const int W = blockDim.x / UPD_ROWS, nthr = blockDim.x;
+    pdl_trigger();
+    pdl_wait();  // the product ahead (and everything before it) is complete
     float *Gs = sh;
     float *Fo = Gs + r * r;
     float *Fn = Fo + r * LD;
@@ -104,29 +108,39 @@ __global__ void __launch_bounds__(UPD_ROWS * UPD_MAXW) k_nmf_update(const UpdArg
     const int rit = static_cast<int>(blockIdx.x % (NT / UPD_ROWS)) * UPD_ROWS + x;  // row in the tile
     const int64_t i = g * NT + rit;
     const bool valid = i < A.R;
+    const bool apg = A.mode && A.algo == NMF_APG;
     if (A.mode) {
-        for (int e = t; e < r * r; e += nthr) Gs[e] = A.Gin[e];
-        if (y == 0) {  // ||G||_F^2 in one fixed order (the same in every block)
-            double f = 0.0;
-            for (int e = x; e < r * r; e += 32) {
+        double f = 0.0;  // ||G||_F^2 (APG step): every thread a few entries, then a fixed-order reduction
+        for (int e = t; e < r * r; e += nthr) {
+            Gs[e] = A.Gin[e];
+            if (apg) {
                 const double gv = A.Gin64[e];
                 f += gv * gv;
             }
+        }
+        if (apg) {
             for (int off = 16; off > 0; off >>= 1) f += __shfl_down_sync(0xffffffffu, f, off);
-            if (x == 0) fro_s = f;
+            if (x == 0) fro_w[y] = f;
         }
         const int64_t first = (g * A.KC) / A.L, last = (g * A.KC + A.KC - 1) / A.L;
         const int ns = static_cast<int>(last - first + 1);
         const float *pp = A.part + (g * A.SL * r) * NT + rit;
         for (int c = y; c < r; c += W) {
             double acc = 0.0;
+#pragma unroll 4
             for (int sl = 0; sl < ns; ++sl) acc += static_cast<double>(pp[(static_cast<int64_t>(sl) * r + c) * NT]);
             Pc[c * LD + x] = static_cast<float>(acc);
         }
     }
     for (int c = y; c < r; c += W) Fo[c * LD + x] = valid ? A.F[c * A.R + i] : 0.f;
     __syncthreads();
-    const float s = A.mode ? static_cast<float>(1.0 / (2.0 * fro_s + A.eps)) : 0.f;
+    if (apg && t == 0) {
+        double f2 = 0.0;
+        for (int w = 0; w < W; ++w) f2 += fro_w[w];
+        fro_s = f2;
+    }
+    if (apg) __syncthreads();
+    const float s = apg ? static_cast<float>(1.0 / (2.0 * fro_s + A.eps)) : 0.f;
     const float eps = static_cast<float>(A.eps);
     bool bad = false;
     for (int c = y; c < r; c += W) {
@@ -190,16 +204,21 @@ __global__ void __launch_bounds__(256) k_nmf_gram(const GramArgs A)
     const int lane = threadIdx.x & 31;
     const int p = blockIdx.x * 8 + (threadIdx.x >> 5);
     const int r = A.r;
+    pdl_trigger();
+    pdl_wait();  // the update ahead is complete
     if (p >= r * (r + 1) / 2) return;
     const float *src = A.gpart + static_cast<int64_t>(p) * A.nblk;
-    double v0 = 0.0, v1 = 0.0;  // blocks lane + 64 j and lane + 32 + 64 j
+    double v4[4] = {0.0, 0.0, 0.0, 0.0};  // blocks lane + 32 (4 j + q)
     int b = lane;
-    for (; b + 32 < A.nblk; b += 64) {
-        v0 += static_cast<double>(src[b]);
-        v1 += static_cast<double>(src[b + 32]);
+    for (; b + 96 < A.nblk; b += 128) {
+        float u[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) u[q] = src[b + 32 * q];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v4[q] += static_cast<double>(u[q]);
     }
-    if (b < A.nblk) v0 += static_cast<double>(src[b]);
-    double v = v0 + v1;
+    for (; b < A.nblk; b += 32) v4[0] += static_cast<double>(src[b]);
+    double v = (v4[0] + v4[1]) + (v4[2] + v4[3]);
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     if (lane == 0) {
         int c, d;
@@ -451,11 +470,32 @@ int plan_side(nmf_handle *h, NmfSide &sd, const __nv_bfloat16 *A, int64_t rows, 
     return COX_OK;
 }
 
+// Launch with programmatic stream serialisation: the kernel may be scheduled
+// while the one ahead of it in the stream finishes (each NMF kernel waits for
+// its predecessor with pdl_wait before touching global memory).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                       Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 int launch_gemm(nmf_handle *h, const NmfSide &sd, cudaStream_t st)
 {
-    k_nmf_gemm<<<sd.grid, GEMM_THREADS, sd.smem, st>>>(sd.tmA, sd.tmB, sd.g);
     ++h->launches;
-    return cudaGetLastError() == cudaSuccess ? COX_OK : COX_ERR_CUDA;
+    return launch_pdl(k_nmf_gemm, sd.grid, GEMM_THREADS, sd.smem, st, sd.tmA, sd.tmB, sd.g) == cudaSuccess
+               ? COX_OK
+               : COX_ERR_CUDA;
 }
 
 size_t upd_smem(int r) { return static_cast<size_t>(r * r + 3 * r * (UPD_ROWS + 1)) * sizeof(float); }
@@ -486,9 +526,9 @@ int launch_update(nmf_handle *h, int side, int mode, int algo, double eps, cudaS
     a.gpart = h->gpart;
     a.nblk = upd_blocks(a.R);
     a.err = h->err;
-    k_nmf_update<<<a.nblk, UPD_ROWS * upd_warps(h->r), upd_smem(h->r), st>>>(a);
     ++h->launches;
-    if (cudaGetLastError() != cudaSuccess) return COX_ERR_CUDA;
+    if (launch_pdl(k_nmf_update, a.nblk, UPD_ROWS * upd_warps(h->r), upd_smem(h->r), st, a) != cudaSuccess)
+        return COX_ERR_CUDA;
     GramArgs gm;
     gm.r = h->r;
     gm.nblk = a.nblk;
@@ -496,9 +536,8 @@ int launch_update(nmf_handle *h, int side, int mode, int algo, double eps, cudaS
     gm.G64 = side == 0 ? h->GV64 : h->GW64;
     gm.G32 = side == 0 ? h->GV32 : h->GW32;
     const int npair = h->r * (h->r + 1) / 2;
-    k_nmf_gram<<<(npair + 7) / 8, 256, 0, st>>>(gm);
     ++h->launches;
-    return cudaGetLastError() == cudaSuccess ? COX_OK : COX_ERR_CUDA;
+    return launch_pdl(k_nmf_gram, (npair + 7) / 8, 256, 0, st, gm) == cudaSuccess ? COX_OK : COX_ERR_CUDA;
 }
 
 int check_err(nmf_handle *h, cudaStream_t st)

@@ -9,6 +9,9 @@
 // 128-row x 64-column boxes (zero-filled past the matrix edges), the panel
 // in NP x 64 boxes.
 //
+// Launched with programmatic stream serialisation, a CTA sets up its barriers
+// and TMEM while the kernel ahead finishes, then waits for it (pdl_wait).
+//
 // Per CTA (one per SM): a TMA warp fills a ring of shared-memory stages, one
 // thread issues four M128 x N x K16 MMAs per 64-wide K chunk into one of two
 // TMEM accumulators, and four epilogue warps (one per TMEM lane quarter) add
@@ -92,6 +95,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     float *sums = reinterpret_cast<float *>(smem + S * STAGE + 256);  // [r][128] running sums
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    pdl_trigger();
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full0 + 8 * s, 1);
@@ -117,6 +121,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tmem_slot;
+    // everything above touches only this CTA's shared memory, TMEM and the
+    // kernel parameters; the kernel ahead (the factor update that wrote the
+    // limb panel) must be complete before any global access
+    pdl_wait();
 
     const int64_t u0 = static_cast<int64_t>(blockIdx.x) * P.L;
     const int64_t u1 = min(u0 + P.L, P.units);

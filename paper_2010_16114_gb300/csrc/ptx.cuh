@@ -95,6 +95,15 @@ __device__ __forceinline__ void named_sync(int id, int count)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// ---- programmatic dependent launch -----------------------------------------------
+// A kernel launched with programmatic stream serialisation may start before
+// the kernel ahead of it in the stream has finished.  pdl_trigger lets the
+// next such kernel be scheduled once every block of this one has issued it;
+// pdl_wait returns once the kernel ahead has completed and its memory is
+// visible.  Without that launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---- TMA (bulk tensor copies, global -> shared) ------------------------------
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1,

@@ -48,9 +48,10 @@ def max_rel(a, b, floor):
 # CTAs each run three row tiles of X W^T (both TMEM accumulators reused) and whose
 # X^T V is one row tile cut into ~130 partial slots; single ragged tiles; r = 1
 # and the largest rank (N = 240, four pipeline stages); a wide X whose CTAs each sum
-# ~130 K chunks of one row tile (17 accumulator windows per segment)
+# ~130 K chunks of one row tile (17 accumulator windows per segment); degenerate
+# X of one entry, one row and one column
 SHAPES = [(300, 200, 5), (300, 200, 20), (51200, 128, 20), (97, 45, 3), (1000, 777, 1), (640, 520, 80),
-          (1000, 3000, 60), (2560, 64000, 4)]
+          (1000, 3000, 60), (2560, 64000, 4), (1, 1, 1), (1, 300, 3), (130, 1, 2)]
 
 
 @pytest.mark.parametrize("m,n,r", SHAPES)
