@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(UPD_ROWS * UPD_MAXW) k_nmf_update(const UpdArg
 {
     extern __shared__ float sh[];
     __shared__ double fro_w[UPD_MAXW];
-    __shared__ double fro_s;
+    __shared__ float step_s;
     constexpr int LD = UPD_ROWS + 1;
     const int r = A.r, t = threadIdx.x, x = t % UPD_ROWS, y = t / UPD_ROWS;
     const int W = blockDim.x / UPD_ROWS, nthr = blockDim.x;
@@ -134,13 +134,13 @@ __global__ void __launch_bounds__(UPD_ROWS * UPD_MAXW) k_nmf_update(const UpdArg
     }
     for (int c = y; c < r; c += W) Fo[c * LD + x] = valid ? A.F[c * A.R + i] : 0.f;
     __syncthreads();
-    if (apg && t == 0) {
+    if (apg && t == 0) {  // the step, formed once per block (FP64 division is slow on this part)
         double f2 = 0.0;
         for (int w = 0; w < W; ++w) f2 += fro_w[w];
-        fro_s = f2;
+        step_s = static_cast<float>(1.0 / (2.0 * f2 + A.eps));
     }
     if (apg) __syncthreads();
-    const float s = apg ? static_cast<float>(1.0 / (2.0 * fro_s + A.eps)) : 0.f;
+    const float s = apg ? step_s : 0.f;
     const float eps = static_cast<float>(A.eps);
     bool bad = false;
     for (int c = y; c < r; c += W) {
