@@ -39,8 +39,6 @@ struct nmf_handle;
 namespace coxgb {
 namespace {
 
-constexpr int UPD_THREADS = 128;        // objective kernel: one thread per row of a tile
-
 struct UpdArgs {
     int r, rp, mode, algo;   // mode 1: update from the product; 0: limbs and Gram partials of F only
     int64_t R;               // factor columns (m for V, n for W)
@@ -244,44 +242,63 @@ struct FitArgs {
     double *out;
 };
 
-// <V, X W^T> per row tile in FP64, then (last block) the objective by the
-// identity ||X - V W||^2 = ||X||^2 - 2 <V, X W^T> + <V^T V, W W^T>.
-__global__ void __launch_bounds__(UPD_THREADS) k_nmf_fit(const FitArgs A)
+// Block sum of one FP64 value per thread in a fixed order: warp shuffles, then
+// the warps' sums in warp order by thread 0 (valid there only).
+__device__ __forceinline__ double block_sum(double v, double *wsum)
 {
-    __shared__ double red[UPD_THREADS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) wsum[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < nw; ++k) s += wsum[k];
+    return s;
+}
+
+// <V, X W^T> over a quarter row tile per block (lane x: column i of V^T, warp
+// y: rank rows c = y, y + W, ...) in FP64, then (last block, all threads) the
+// objective by the identity ||X - V W||^2 = ||X||^2 - 2 <V, X W^T> +
+// <V^T V, W W^T>.  Fixed orders throughout.
+__global__ void __launch_bounds__(UPD_ROWS * UPD_MAXW) k_nmf_fit(const FitArgs A)
+{
+    __shared__ double wsum[UPD_MAXW];
     __shared__ int is_last;
-    const int r = A.r, t = threadIdx.x;
-    const int64_t g = blockIdx.x, i = g * UPD_THREADS + t;
+    const int r = A.r, t = threadIdx.x, x = t % UPD_ROWS, y = t / UPD_ROWS;
+    const int W = blockDim.x / UPD_ROWS, nthr = blockDim.x;
+    const int64_t g = blockIdx.x / (NT / UPD_ROWS);
+    const int rit = static_cast<int>(blockIdx.x % (NT / UPD_ROWS)) * UPD_ROWS + x;
+    const int64_t i = g * NT + rit;
     double s = 0.0;
     if (i < A.R) {
         const int64_t first = (g * A.KC) / A.L, last = (g * A.KC + A.KC - 1) / A.L;
         const int ns = static_cast<int>(last - first + 1);
-        const float *pp = A.part + (g * A.SL * r) * NT + t;
-        for (int c = 0; c < r; ++c) {
+        const float *pp = A.part + (g * A.SL * r) * NT + rit;
+        for (int c = y; c < r; c += W) {
             double acc = 0.0;
+#pragma unroll 4
             for (int sl = 0; sl < ns; ++sl) acc += static_cast<double>(pp[(static_cast<int64_t>(sl) * r + c) * NT]);
             s += static_cast<double>(A.F[c * A.R + i]) * acc;
         }
     }
-    red[t] = s;
-    __syncthreads();
-    for (int w = UPD_THREADS / 2; w > 0; w >>= 1) {
-        if (t < w) red[t] += red[t + w];
-        __syncthreads();
-    }
-    if (t == 0) A.opart[g] = red[0];
+    const double bs = block_sum(s, wsum);
+    if (t == 0) A.opart[blockIdx.x] = bs;
     __threadfence();
     __syncthreads();
     if (t == 0) is_last = atomicAdd(A.counter, 1) == static_cast<int>(gridDim.x) - 1;
     __syncthreads();
-    if (!is_last || t != 0) return;
+    if (!is_last) return;
     __threadfence();
-    double vp = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) vp += __ldcg(A.opart + b);
-    double tr = 0.0;
-    for (int e = 0; e < r * r; ++e) tr += A.GV[e] * A.GW[e];
-    *A.out = A.xx - 2.0 * vp + tr;
-    *A.counter = 0;
+    double v = 0.0, tr = 0.0;
+    for (int b2 = t; b2 < static_cast<int>(gridDim.x); b2 += nthr) v += __ldcg(A.opart + b2);
+    for (int e = t; e < r * r; e += nthr) tr += A.GV[e] * A.GW[e];
+    const double vp = block_sum(v, wsum);
+    __syncthreads();
+    const double trs = block_sum(tr, wsum);
+    if (t == 0) {
+        *A.out = A.xx - 2.0 * vp + trs;
+        *A.counter = 0;
+    }
 }
 
 // X rows [r0, r0 + nr) (FP32, nr x n) -> bf16 in both orders; 32 x 32 tiles
@@ -612,8 +629,9 @@ int setup_impl(const float *X, int64_t m, int64_t n, int r, int device, nmf_hand
             if ((rc = A(reinterpret_cast<void **>(p), static_cast<size_t>(r * r) * 8)) != COX_OK) break;
         if (rc) break;
         if ((rc = A(reinterpret_cast<void **>(&h->fobj), 8)) != COX_OK) break;
-        const int64_t tiles = std::max((m + NT - 1) / NT, (n + NT - 1) / NT);
-        if ((rc = A(reinterpret_cast<void **>(&h->opart), static_cast<size_t>(tiles) * 8)) != COX_OK) break;
+        if ((rc = A(reinterpret_cast<void **>(&h->opart), static_cast<size_t>(upd_blocks(std::max(m, n))) * 8)) !=
+            COX_OK)
+            break;
         if ((rc = A(reinterpret_cast<void **>(&h->gpart), static_cast<size_t>(r * (r + 1) / 2) *
                                                                   upd_blocks(std::max(m, n)) * sizeof(float))) != COX_OK)
             break;
@@ -816,7 +834,7 @@ int nmf_objective(nmf_h h, double *f, void *stream)
     a.GW = h->GW64;
     a.xx = h->xx;
     a.out = h->fobj;
-    k_nmf_fit<<<static_cast<unsigned>((h->m + UPD_THREADS - 1) / UPD_THREADS), UPD_THREADS, 0, st>>>(a);
+    k_nmf_fit<<<upd_blocks(h->m), UPD_ROWS * upd_warps(h->r), 0, st>>>(a);
     ++h->launches;
     COX_CUDA(cudaGetLastError());
     COX_CUDA(cudaMemcpyAsync(f, h->fobj, sizeof(double), cudaMemcpyDeviceToHost, st));
