@@ -123,9 +123,9 @@ __global__ void __launch_bounds__(128) k_gemv_tiles(const uint32_t *__restrict__
 // split through them with 16-byte coalesced loads, two threads per row (one
 // per 16-byte half); every range of chunks leaves one FP32 partial per row, and
 // k_gemv_reduce adds the partials with a compensated FP32 sum.
-// 16 chunks (64 KB of tables) leave room for three CTAs per SM; measured at
-// full size against 48 (one CTA per SM) and 24 (two): 0.546, 0.477 and 0.529 of
-// the HBM copy bandwidth.
+// 16 chunks (64 KB of tables) let two CTAs share an SM (registers allow two of
+// 512 threads); measured at full size against 48 (one CTA per SM) and 24:
+// 0.546, 0.477 and 0.529 of the HBM copy bandwidth.
 constexpr int LUT_CW = 16;          // K chunks per CTA (tables: 16 x 4 KB)
 constexpr int LUT_THREADS = 512;    // two threads per row, two row tiles per pass
 constexpr int LUT_CHUNK = 1024;     // floats per chunk's tables
