@@ -8,8 +8,8 @@
 // old set with the support added, and the SNPs the fused step marked as close
 // to entering, or without the old set once that union has grown past twice
 // the rest), gathers a subject-major 2-bit copy of the columns of A (the tiled
-// layout of the full copy, K = position in A), and plans the same tensor-core
-// product on it.  A always covers the current support, so the
+// layout of the full copy, K = position in A) from the rows of A in the
+// SNP-major copy, and plans the same tensor-core product on it.  A always covers the current support, so the
 // product equals the dense one up to the FP32 order of the nonzero terms.
 // When the support holds more than a quarter of the (padded) columns the
 // dense product runs instead.
@@ -46,59 +46,49 @@ __global__ void k_support(const float *__restrict__ beta, int k, int64_t p, cons
     }
 }
 
-// The active copy, one CTA per row tile (thread = row): for each source chunk
-// that holds active SNPs (cchunk[c], active positions cstart[c] ..
-// cstart[c+1]), the row's 32-byte record of that chunk (coalesced over the
-// tile's 128 rows, prefetched GA chunks ahead) yields the codes of all its
-// active SNPs, packed in active order into words of 16; positions past nA
-// stay 0 (the copy is cleared first).
-constexpr int GA = 4;
-__global__ void __launch_bounds__(TILE) k_gather_active(const uint32_t *__restrict__ A1, int64_t KC1,
-                                                        const int32_t *__restrict__ Aidx,
-                                                        const int32_t *__restrict__ cchunk,
-                                                        const int32_t *__restrict__ cstart, int nchunks,
-                                                        int64_t n, int64_t KCa, uint32_t *__restrict__ out)
+// The active copy from the SNP-major copy A4, one CTA of 128 threads per
+// (active chunk ca of 128 active positions, A4 K chunk kc of 128 K positions).
+// Thread s reads the 32-byte record of active SNP Aidx[128 ca + s] in chunk kc:
+// eight words, word u holding the codes of the 16 subjects of K block
+// B = 8 kc + u (A4 stores sorted subject block b at block B = (a b) mod nb, so
+// b = a^-1 B mod nb).  Per u the 16 threads of a group g (active positions
+// 16 g .. 16 g + 15) transpose their 16 words by shuffles into one word per
+// subject (the codes of the group's 16 SNPs) and write it to that subject's
+// row of the subject-major copy, at active position 16 g of chunk ca: the CTA
+// writes whole 32-byte records of 16 rows per u.  Positions past nA read 0.
+// Reads are whole 32-byte sectors of the active SNPs' rows only (|A| n / 4
+// bytes); every word of the copy is written (no clearing needed).
+__global__ void __launch_bounds__(TILE) k_gather_active(const uint32_t *__restrict__ A4, int64_t KC4,
+                                                        const int32_t *__restrict__ Aidx, int64_t nA, int64_t KCa,
+                                                        int64_t ainv, int64_t nb, uint32_t *__restrict__ out)
 {
-    const int64_t mt = blockIdx.x;
-    const int rit = threadIdx.x;
-    if (mt * TILE + rit >= n) return;  // padding rows stay 0
-    const int swp = (rit >> 2) & 1;
-    int64_t cur = -1;  // word (16 active positions) being built
-    uint32_t P = 0;
-    for (int c0 = 0; c0 < nchunks; c0 += GA) {
-        uint4 rec[GA][2];
-#pragma unroll
-        for (int g = 0; g < GA; ++g) {
-            if (c0 + g >= nchunks) break;
-            const uint4 *b = reinterpret_cast<const uint4 *>(
-                reinterpret_cast<const uint8_t *>(A1) + (mt * KC1 + cchunk[c0 + g]) * BLOCK_BYTES + rit * 32);
-            rec[g][0] = __ldcs(b + swp);      // logical half 0 (K 0..63 of the chunk)
-            rec[g][1] = __ldcs(b + (swp ^ 1));  // logical half 1
-        }
-#pragma unroll
-        for (int g = 0; g < GA; ++g) {
-            if (c0 + g >= nchunks) break;
-            const uint32_t wd[8] = {rec[g][0].x, rec[g][0].y, rec[g][0].z, rec[g][0].w,
-                                    rec[g][1].x, rec[g][1].y, rec[g][1].z, rec[g][1].w};
-            for (int32_t t = cstart[c0 + g]; t < cstart[c0 + g + 1]; ++t) {
-                const int within = static_cast<int>(Aidx[t] % TILE);
-                uint32_t word = 0;
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (q == (within >> 4)) word = wd[q];  // word q = 4 h + (within mod 64) / 16
-                const uint32_t code = (word >> code_bit(within & 15)) & 3u;
-                const int64_t wq = t >> 4;
-                if (wq != cur) {
-                    if (cur >= 0)
-                        out[word_offset(mt, KCa, (cur * 16) / TILE, rit, static_cast<int>((cur * 16) % TILE))] = P;
-                    P = 0;
-                    cur = wq;
-                }
-                P |= code << code_bit(t & 15);
-            }
-        }
+    const int64_t ca = static_cast<int64_t>(blockIdx.x) % KCa;
+    const int64_t kc = static_cast<int64_t>(blockIdx.x) / KCa;
+    const int s = threadIdx.x, lane = s & 31, i = s & 15, g = s >> 4;
+    const int64_t t = ca * TILE + s;
+    uint32_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (t < nA) {
+        const int64_t j = Aidx[t];
+        const int row = static_cast<int>(j % TILE);
+        const int swp = (row >> 2) & 1;
+        const uint4 *rec = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(A4) +
+                                                           ((j / TILE) * KC4 + kc) * BLOCK_BYTES + row * 32);
+        const uint4 h0 = __ldcs(rec + swp), h1 = __ldcs(rec + (swp ^ 1));  // logical halves 0, 1
+        w[0] = h0.x; w[1] = h0.y; w[2] = h0.z; w[3] = h0.w;
+        w[4] = h1.x; w[5] = h1.y; w[6] = h1.z; w[7] = h1.w;
     }
-    if (cur >= 0) out[word_offset(mt, KCa, (cur * 16) / TILE, rit, static_cast<int>((cur * 16) % TILE))] = P;
+    const int src0 = lane & 16;  // first lane of this thread's group in the warp
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        uint32_t o = 0;  // subject i of the block: the group's 16 SNP codes
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const uint32_t wk = __shfl_sync(0xffffffffu, w[u], src0 + k);
+            o |= ((wk >> code_bit(i)) & 3u) << code_bit(k);
+        }
+        const int64_t b = (ainv * (8 * kc + u)) % nb;  // sorted subject block
+        out[word_offset(b >> 3, KCa, ca, static_cast<int>((b & 7) * 16 + i), 16 * g)] = o;
+    }
 }
 
 // e4m3 limbs of beta at the active SNPs (column t of the limb matrix = SNP
@@ -207,37 +197,23 @@ int active_prepare(cox_handle *h, const float *beta, int k, cudaStream_t st, int
             if (flag[j]) idx.push_back(static_cast<int32_t>(j));
         const int64_t nA = static_cast<int64_t>(idx.size());
         if (nA > limit) return COX_OK;  // the set in use stays as it was
-        // the source chunks that hold active SNPs, and each one's first active position
-        std::vector<int32_t> cchunk, cstart;
-        for (int64_t t = 0; t < nA; ++t)
-            if (cchunk.empty() || idx[t] / TILE != cchunk.back()) {
-                cchunk.push_back(idx[t] / TILE);
-                cstart.push_back(static_cast<int32_t>(t));
-            }
-        cstart.push_back(static_cast<int32_t>(nA));
         const int64_t Kpad = std::max<int64_t>(256, (nA + 255) / 256 * 256);
         if (Kpad > h->act_cap) {
             dfree(h->d_Aidx);
             dfree(h->d_A1act);
             h->d_Aidx = nullptr;
             h->d_A1act = nullptr;
-            // Aidx then the chunk list (at most one chunk per active SNP) and its starts
-            COX_TRY(dmalloc(h, reinterpret_cast<void **>(&h->d_Aidx), (3 * Kpad + 1) * sizeof(int32_t)));
+            COX_TRY(dmalloc(h, reinterpret_cast<void **>(&h->d_Aidx), Kpad * sizeof(int32_t)));
             COX_TRY(dmalloc(h, reinterpret_cast<void **>(&h->d_A1act), static_cast<size_t>(h->n_pad) * Kpad / 4));
             h->act_cap = Kpad;
         }
-        int32_t *d_cchunk = h->d_Aidx + h->act_cap, *d_cstart = h->d_Aidx + 2 * h->act_cap;
-        const int nchunks = static_cast<int>(cchunk.size());
-        if (nA) {
-            COX_CUDA(cudaMemcpyAsync(h->d_Aidx, idx.data(), nA * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-            COX_CUDA(cudaMemcpyAsync(d_cchunk, cchunk.data(), nchunks * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        }
-        COX_CUDA(cudaMemcpyAsync(d_cstart, cstart.data(), cstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        if (nA) COX_CUDA(cudaMemcpyAsync(h->d_Aidx, idx.data(), nA * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         COX_CUDA(cudaMemcpyAsync(h->d_inA, flag.data(), p, cudaMemcpyHostToDevice, st));
-        COX_CUDA(cudaMemsetAsync(h->d_A1act, 0, static_cast<size_t>(h->n_pad) * Kpad / 4, st));
-        if (nchunks)
-            k_gather_active<<<static_cast<unsigned>(h->n_pad / TILE), TILE, 0, st>>>(
-                h->d_A1, h->p_pad / TILE, h->d_Aidx, d_cchunk, d_cstart, nchunks, h->n, Kpad / TILE, h->d_A1act);
+        {
+            const int64_t KC4 = h->n_pad / TILE, KCa = Kpad / TILE;
+            k_gather_active<<<static_cast<unsigned>(KCa * KC4), TILE, 0, st>>>(
+                h->d_A4, KC4, h->d_Aidx, nA, KCa, h->kperm_ainv, h->kperm_nb, h->d_A1act);
+        }
         COX_CUDA(cudaGetLastError());
         COX_CUDA(cudaStreamSynchronize(st));  // the host lists leave scope
         h->launches += 1;

@@ -582,6 +582,16 @@ int cox_setup(cox_h *out, const void *X, int64_t n, int64_t p, int x_format, con
         while (std::gcd(a, nb) != 1) a += 2;
         h->kperm_nb = nb;
         h->kperm_a = a % nb;
+        // inverse of a modulo nb (extended Euclid; a is prime to nb)
+        int64_t r0 = nb, r1 = h->kperm_a, t0 = 0, t1 = 1;
+        while (r1 != 0) {
+            const int64_t q = r0 / r1, r2 = r0 - q * r1, t2 = t0 - q * t1;
+            r0 = r1;
+            r1 = r2;
+            t0 = t1;
+            t1 = t2;
+        }
+        h->kperm_ainv = ((t0 % nb) + nb) % nb;
     }
     h->l1_blocks = static_cast<int>(std::min<int64_t>(64, (p + 4095) / 4096));
     {

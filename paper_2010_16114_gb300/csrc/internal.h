@@ -197,6 +197,7 @@ struct cox_handle {
     int dev = 0, sm_count = 0;
     int64_t n = 0, p = 0, n_pad = 0, p_pad = 0;
     int64_t kperm_a = 1, kperm_nb = 1;  // K order of A4 (a4_pos)
+    int64_t kperm_ainv = 1;             // a^-1 mod nb: A4 block B holds sorted block ainv B mod nb
     int n_chunks = 0, l1_blocks = 0;
     cox_options opt;
     int64_t n_groups_tie = 0;
