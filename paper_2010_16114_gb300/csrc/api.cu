@@ -54,7 +54,7 @@ int alloc(cox_handle *h, T *&p, size_t count)
 void free_workspace(cox_handle *h)
 {
     Workspace &w = h->ws;
-    void *ptrs[] = {w.eta, w.w, w.Rt, w.Ft, w.cmax, w.csw, w.csd, w.suf, w.pre, w.lossp, w.vsp, w.l1p,
+    void *ptrs[] = {w.eta, w.w, w.Rt, w.Fg, w.lossg, w.cmax, w.csw, w.suf, w.lossp, w.vsp, w.l1p,
                     w.sumV, w.f, w.F, w.l1, w.mub, w.lam, w.active, w.Fring, w.Bq, w.Vq, w.bs1, w.bs4, w.bmaxp,
                     w.vmaxp, w.part1, w.part4, w.cnt4, w.V64, w.V32, w.eta32, w.G32, w.gpart, w.gamma, w.gz, w.zvp};
     for (void *p : ptrs) dfree(p);
@@ -407,12 +407,11 @@ int ensure_workspace(cox_handle *h, int k)
     A(ws.eta, k * n);
     A(ws.w, k * n);
     A(ws.Rt, k * n);
-    A(ws.Ft, k * n);
+    A(ws.Fg, k * std::max<int64_t>(1, h->n_evhead));
+    A(ws.lossg, k);
     A(ws.cmax, k * nch);
     A(ws.csw, k * nch);
-    A(ws.csd, k * nch);
     A(ws.suf, k * nch);
-    A(ws.pre, k * nch);
     A(ws.lossp, k * nch);
     A(ws.vsp, k * nch);
     A(ws.l1p, static_cast<size_t>(k) * h->l1_blocks);
@@ -529,8 +528,8 @@ void cox_destroy(cox_h h)
     free_workspace(h);
     active_free(h);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
-    void *ptrs[] = {h->d_head, h->d_tail, h->d_evhead, h->d_delta, h->d_mu, h->d_A1, h->d_A4, h->d_Xr, h->d_Xc, h->d_err,
-                    h->d_Z};
+    void *ptrs[] = {h->d_head, h->d_tail, h->d_evhead, h->d_evcnt, h->d_evidx, h->d_evflag, h->d_delta,
+                    h->d_mu, h->d_A1, h->d_A4, h->d_Xr, h->d_Xc, h->d_err, h->d_Z};
     for (void *p : ptrs) dfree(p);
     delete h;
 }
@@ -611,16 +610,24 @@ int cox_setup(cox_h *out, const void *X, int64_t n, int64_t p, int x_format, con
     std::vector<uint8_t> dsorted(static_cast<size_t>(n));
     int64_t groups = 0;
     std::vector<int32_t> evhead;  // heads of the tie groups with at least one event
+    std::vector<int32_t> evcnt;   // and their event counts
+    std::vector<int32_t> evidx(static_cast<size_t>(n));  // event groups with head <= the subject's tail
+    std::vector<uint8_t> evflag(static_cast<size_t>(n), 0);
     for (int64_t r = 0; r < n;) {
         int64_t e = r;
         while (e + 1 < n && time[h->h_order[e + 1]] == time[h->h_order[r]]) ++e;
-        bool ev = false;
+        int32_t nev = 0;
         for (int64_t s = r; s <= e; ++s) {
             head[s] = static_cast<int32_t>(r);
             tail[s] = static_cast<int32_t>(e);
-            ev = ev || event[h->h_order[s]] != 0;
+            nev += event[h->h_order[s]] != 0;
         }
-        if (ev) evhead.push_back(static_cast<int32_t>(r));
+        if (nev) {
+            evhead.push_back(static_cast<int32_t>(r));
+            evcnt.push_back(nev);
+            evflag[r] = 1;
+        }
+        for (int64_t s = r; s <= e; ++s) evidx[s] = static_cast<int32_t>(evhead.size());
         ++groups;
         r = e + 1;
     }
@@ -636,8 +643,17 @@ int cox_setup(cox_h *out, const void *X, int64_t n, int64_t p, int x_format, con
         if ((rc = dmalloc(h, reinterpret_cast<void **>(&h->d_tail), n * sizeof(int32_t))) != COX_OK) break;
         if ((rc = dmalloc(h, reinterpret_cast<void **>(&h->d_evhead), evhead.size() * sizeof(int32_t))) != COX_OK)
             break;
-        if (!evhead.empty() && cudaMemcpy(h->d_evhead, evhead.data(), evhead.size() * sizeof(int32_t),
-                                          cudaMemcpyHostToDevice) != cudaSuccess) {
+        if ((rc = dmalloc(h, reinterpret_cast<void **>(&h->d_evcnt), evcnt.size() * sizeof(int32_t))) != COX_OK)
+            break;
+        if ((rc = dmalloc(h, reinterpret_cast<void **>(&h->d_evidx), n * sizeof(int32_t))) != COX_OK) break;
+        if ((rc = dmalloc(h, reinterpret_cast<void **>(&h->d_evflag), n)) != COX_OK) break;
+        if ((!evhead.empty() &&
+             (cudaMemcpy(h->d_evhead, evhead.data(), evhead.size() * sizeof(int32_t), cudaMemcpyHostToDevice) !=
+                  cudaSuccess ||
+              cudaMemcpy(h->d_evcnt, evcnt.data(), evcnt.size() * sizeof(int32_t), cudaMemcpyHostToDevice) !=
+                  cudaSuccess)) ||
+            cudaMemcpy(h->d_evidx, evidx.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(h->d_evflag, evflag.data(), n, cudaMemcpyHostToDevice) != cudaSuccess) {
             rc = COX_ERR_CUDA;
             break;
         }

@@ -151,10 +151,11 @@ struct Workspace {
     // split / gemv / fp64 common (sorted subject order)
     double *eta = nullptr;      // k x n
     double *w = nullptr;        // k x n
-    double *Rt = nullptr;       // k x n local reverse scans; then V in FP32 for k_vlimbs
-    double *Ft = nullptr;       // k x n local forward scans
-    double *cmax = nullptr, *csw = nullptr, *csd = nullptr, *suf = nullptr, *pre = nullptr;
-    double *lossp = nullptr, *vsp = nullptr;  // k x chunks
+    double *Rt = nullptr;       // k x n local reverse scans (at event-group heads); then V in FP32 for k_vlimbs
+    double *Fg = nullptr;       // k x event groups: cumulative sum of (events / W) over event groups
+    double *lossg = nullptr;    // k: sum over event groups of (events) log W, plus (events) c
+    double *cmax = nullptr, *csw = nullptr, *suf = nullptr;
+    double *lossp = nullptr, *vsp = nullptr;  // k x chunks (lossp: sum of delta eta per chunk)
     double *l1p = nullptr;                    // k x l1 blocks
     double *sumV = nullptr, *f = nullptr, *F = nullptr, *l1 = nullptr;  // k
     double *mub = nullptr;     // k: mu^T beta (cox_eta)
@@ -207,6 +208,9 @@ struct cox_handle {
     // device data
     int32_t *d_head = nullptr, *d_tail = nullptr;
     int32_t *d_evhead = nullptr;  // first positions of the tie groups that hold an event
+    int32_t *d_evcnt = nullptr;   // events in each of those groups
+    int32_t *d_evidx = nullptr;   // n: event groups whose head is at or before the subject's tie tail
+    uint8_t *d_evflag = nullptr;  // n: 1 at the head of a tie group that holds an event
     int64_t n_evhead = 0;
     int q = 0;                    // unpenalised covariates
     double *d_Z = nullptr;        // q x n, sorted order

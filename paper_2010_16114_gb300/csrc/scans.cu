@@ -4,15 +4,21 @@
 // cumulative sum; Section 6: Breslow ties).
 //
 // Subjects are stored in ascending time order, so with R_r = sum_{s >= r} w_s
-// (a reverse inclusive scan) and F_r = sum_{s <= r} delta_s / W_s (a forward
-// inclusive scan):
-//   W_r = R_{head(r)}            head = first position of r's tie group
-//   u_r = w_r F_{tail(r)}        tail = last position of r's tie group
-//   V_r = delta_r - u_r          (the vector X^T multiplies)
-//   f   = (1/n) sum_r delta_r (log W_r - (eta_r - c)),  c = max eta.
-// Each scan runs in fixed 2048-subject chunks (block scans with warp
-// shuffles), then an exclusive scan of the chunk totals, then a gather; the
-// summation order never depends on timing, so results are bit-reproducible.
+// (a reverse inclusive scan), and the tie groups that hold events numbered
+// g = 0, 1, ... in time order (head h_g, e_g events):
+//   W_g = R_{h_g}                       the risk-set sum of group g
+//   F_g = sum_{g' <= g} e_g' / W_g'     a forward scan over event groups
+//   u_r = w_r F_{G(r) - 1}              G(r) = event groups with head <= r's
+//                                       tie tail (u_r = 0 when G(r) = 0)
+//   V_r = delta_r - u_r                 (the vector X^T multiplies)
+//   f   = (1/n) [sum_g e_g log W_g - sum_r delta_r (eta_r - c)],  c = max eta.
+// delta / W is nonzero only at events, and tied events share W, so the
+// forward scan runs over the event groups (a few thousand with times in whole
+// days) instead of the n subjects; the FP64 work that remains per subject is
+// the reverse scan of w.  The reverse scan runs in fixed 2048-subject chunks
+// (block scans with warp shuffles), then an exclusive scan of the chunk
+// totals; the summation order never depends on timing, so results are
+// bit-reproducible.
 #include <algorithm>
 
 #include "internal.h"
@@ -95,8 +101,11 @@ struct SP {
     const uint8_t *delta;
     const int32_t *head, *tail;
     const int32_t *evhead;  // first positions of the tie groups that hold an event
+    const int32_t *evcnt;   // their event counts
+    const int32_t *evidx;   // n: event groups with head <= the subject's tie tail
+    const uint8_t *evflag;  // n: 1 at an event group's head
     int64_t n_evh;
-    double *eta, *w, *Rt, *Ft, *cmax, *csw, *csd, *suf, *pre, *lossp, *vsp;
+    double *eta, *w, *Rt, *Fg, *lossg, *cmax, *csw, *suf, *lossp, *vsp;
     // unpenalised covariates (q columns; q = 0: none): Z q x n in sorted order,
     // gamma k x q, per-chunk partials of Z^T V (k x q x chunks)
     int q;
@@ -106,7 +115,8 @@ struct SP {
 
 constexpr int MAXQ = 16;
 
-// (1) eta = sum of the product's partial slots (or a dense copy); chunk maxima.
+// (1) eta = sum of the product's partial slots (or a dense copy); chunk maxima;
+// chunk sums of delta eta (the events' part of the loss).
 template <int SRC>
 __global__ void k_eta(SP s, const void *src, int64_t slot_stride, int64_t col_stride, int group_rows,
                       int KC, int64_t L)
@@ -123,7 +133,7 @@ __global__ void k_eta(SP s, const void *src, int64_t slot_stride, int64_t col_st
         }
         __syncthreads();
     }
-    double mx = -INFINITY;
+    double mx = -INFINITY, de = 0.0;
     for (int e = threadIdx.x; e < SCAN_CH; e += NT) {
         const int64_t i = i0 + e;
         if (i >= s.n) break;
@@ -145,9 +155,12 @@ __global__ void k_eta(SP s, const void *src, int64_t slot_stride, int64_t col_st
         }
         s.eta[kk * s.n + i] = v;
         mx = fmax(mx, v);
+        if (s.delta[i]) de += v;
     }
     const double m = block_max(mx, sh);
     if (threadIdx.x == 0) s.cmax[kk * s.nch + c] = m;
+    const double t = block_sum(de, sh);
+    if (threadIdx.x == 0) s.lossp[kk * s.nch + c] = t;
 }
 
 __device__ __forceinline__ double column_max(const SP &s, int kk, double *sh)
@@ -162,7 +175,9 @@ __device__ __forceinline__ double column_max(const SP &s, int kk, double *sh)
     return m;
 }
 
-// (2) w = exp(eta - c); chunk-local reverse inclusive scan of w; chunk totals.
+// (2) w = exp(eta - c); chunk-local reverse inclusive scan of w, kept at the
+// heads of the tie groups that hold events (the only places W is read);
+// chunk totals.
 template <bool EXP64>
 __global__ void k_rev(SP s)
 {
@@ -193,25 +208,22 @@ __global__ void k_rev(SP s)
     const double incl = block_incl_scan(run, sh);
     const double excl = incl - run;
 #pragma unroll
-    for (int j = 0; j < PER; ++j) buf[SCAN_CH - 1 - (PER * threadIdx.x + j)] = loc[j] + excl;
-    __syncthreads();
-    for (int e = threadIdx.x; e < SCAN_CH; e += NT) {
-        const int64_t i = i0 + e;
-        if (i < s.n) s.Rt[kk * s.n + i] = buf[e];
+    for (int j = 0; j < PER; ++j) {
+        const int64_t i = i0 + SCAN_CH - 1 - (PER * threadIdx.x + j);
+        if (i < s.n && s.evflag[i]) s.Rt[kk * s.n + i] = loc[j] + excl;
     }
     if (threadIdx.x == NT - 1) s.csw[kk * s.nch + c] = incl;
 }
 
-// exclusive scans of chunk totals: suffix (reverse) or prefix (forward); one
-// warp per column, lane l owning a contiguous run of chunks in scan order.
-template <bool SUFFIX>
+// exclusive suffix scans of the chunk totals of w; one warp per column, lane
+// l owning a contiguous run of chunks in scan order.
 __global__ void k_chunks(SP s)
 {
     const int kk = blockIdx.x, lane = threadIdx.x;
-    const double *src = (SUFFIX ? s.csw : s.csd) + static_cast<int64_t>(kk) * s.nch;
-    double *dst = (SUFFIX ? s.suf : s.pre) + static_cast<int64_t>(kk) * s.nch;
+    const double *src = s.csw + static_cast<int64_t>(kk) * s.nch;
+    double *dst = s.suf + static_cast<int64_t>(kk) * s.nch;
     const int per = (s.nch + 31) / 32;
-    auto at = [&](int q) { return SUFFIX ? s.nch - 1 - q : q; };  // q-th chunk in scan order
+    auto at = [&](int q) { return s.nch - 1 - q; };  // q-th chunk in scan order
     double tot = 0.0;
     for (int j = 0; j < per; ++j) {
         const int q = lane * per + j;
@@ -229,92 +241,58 @@ __global__ void k_chunks(SP s)
     }
 }
 
-// (2b) 1/W in FP64 once per tie group that holds an event: W = R at the
-// group's first position (chunk-local reverse scan plus the suffix of later
-// chunks), and Rt there is overwritten with 1/W.  Every event of the group
-// reads that one value (Breslow: tied events share W), so the FP64 divides
-// number the event times (at most a few thousand with times in whole days),
-// not the events, and run without divergence.
-__global__ void k_inv_w(SP s)
-{
-    const int kk = blockIdx.y;
-    for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < s.n_evh;
-         q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t hd = s.evhead[q];
-        const double W = s.Rt[kk * s.n + hd] + s.suf[kk * s.nch + hd / SCAN_CH];
-        s.Rt[kk * s.n + hd] = 1.0 / W;
-    }
-}
-
-// (3) D = delta / W (from the group heads' 1/W); loss terms; chunk-local
-// forward scan of D, all in FP64.
-__global__ void k_fwd(SP s, bool need_loss)
+// (3) One block per column, over the tie groups that hold events: W_g = the
+// chunk-local reverse sum at the group's head plus the suffix of later chunks,
+// D_g = e_g / W_g (one FP64 division per event time: tied events share W,
+// Breslow), F = the inclusive scan of D over the groups, and the loss term
+// sum_g e_g log W_g + (events) c.  Thread t takes a contiguous run of groups;
+// the logs are taken of products carried as (mantissa, exponent), one log per
+// thread (FP64 log is costly).
+__global__ void k_group(SP s, bool need_loss)
 {
     __shared__ double sh[NT / 32];
-    __shared__ double buf[SCAN_CH];
-    const int c = blockIdx.x, kk = blockIdx.y;
+    const int kk = blockIdx.x;
+    const int64_t G = s.n_evh;
+    const int64_t per = (G + NT - 1) / NT;
+    const int64_t g0 = min(G, per * threadIdx.x), g1 = min(G, g0 + per);
     const double cmx = need_loss ? column_max(s, kk, sh) : 0.0;
-    const int64_t i0 = static_cast<int64_t>(c) * SCAN_CH;
-    // The loss terms log W = -log(1/W) are summed as the log of a product:
-    // each thread multiplies its 1/W into pm 2^pe (pm in [1, 2)), the warp
-    // multiplies its lanes' products, and one log per warp remains (FP64 log is
-    // costly and events are sparse, so a per-event log would run in most warps
-    // anyway).
-    double lsum = 0.0, pm = 1.0;
+    double run = 0.0, pm = 1.0, lsum = 0.0;
     int pe = 0;
-    for (int e = threadIdx.x; e < SCAN_CH; e += NT) {
-        const int64_t i = i0 + e;
-        double d = 0.0;
-        if (i < s.n && s.delta[i]) {
-            d = s.Rt[kk * s.n + s.head[i]];  // 1/W of i's tie group
-            if (need_loss) {
-                lsum -= s.eta[kk * s.n + i] - cmx;
-                if (d >= 0x1p-1000 && d <= 0x1p+1022) {
-                    pm *= d;
+    long long nev = 0;
+    for (int64_t g = g0; g < g1; ++g) {
+        const int64_t hd = s.evhead[g];
+        const double W = s.Rt[kk * s.n + hd] + s.suf[kk * s.nch + hd / SCAN_CH];
+        const int e = s.evcnt[g];
+        run += static_cast<double>(e) / W;
+        s.Fg[kk * G + g] = run;  // local; the block offset is added below
+        if (need_loss) {
+            nev += e;
+            if (e <= 8 && W >= 0x1p-1000 && W <= 0x1p+1000) {
+                for (int q = 0; q < e; ++q) {
+                    pm *= W;
                     pe += renorm(pm);
-                } else {
-                    lsum -= log(d);  // zero, huge, subnormal or NaN: as a plain sum of logs
                 }
+            } else {
+                lsum += static_cast<double>(e) * log(W);  // many tied events, or W zero, huge, subnormal, NaN
             }
         }
-        buf[e] = d;
-    }
-    __syncthreads();
-    double loc[PER];
-    double run = 0.0;
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        run += buf[PER * threadIdx.x + j];
-        loc[j] = run;
     }
     const double incl = block_incl_scan(run, sh);
     const double excl = incl - run;
-#pragma unroll
-    for (int j = 0; j < PER; ++j) buf[PER * threadIdx.x + j] = loc[j] + excl;
-    __syncthreads();
-    for (int e = threadIdx.x; e < SCAN_CH; e += NT) {
-        const int64_t i = i0 + e;
-        if (i < s.n) s.Ft[kk * s.n + i] = buf[e];
-    }
-    if (threadIdx.x == NT - 1) s.csd[kk * s.nch + c] = incl;
+    if (excl != 0.0)
+        for (int64_t g = g0; g < g1; ++g) s.Fg[kk * G + g] += excl;
     if (need_loss) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {  // every lane ends with the same product
-            pm *= __shfl_xor_sync(0xffffffffu, pm, o);
-            pe += __shfl_xor_sync(0xffffffffu, pe, o);
-            pe += renorm(pm);
-        }
-        // sum of log W over this warp's events = -log(product of 1/W)
-        if ((threadIdx.x & 31) == 0) lsum -= log(pm) + static_cast<double>(pe) * 0.6931471805599453;
+        lsum += log(pm) + static_cast<double>(pe) * 0.6931471805599453 + static_cast<double>(nev) * cmx;
         const double t = block_sum(lsum, sh);
-        if (threadIdx.x == 0) s.lossp[kk * s.nch + c] = t;
+        if (threadIdx.x == 0) s.lossg[kk] = t;
     }
 }
 
-// (4) C = F at the tie tail; u = w C; V = delta - u -> output form; sum of V.
+// (4) C = F of the last event group at or before the tie tail; u = w C;
+// V = delta - u -> output form; sum of V.
 // The FP32 form feeds a product over the SNP-major copy and is written at its
 // K positions (a4_pos); the FP64 form stays in sorted order.  For the e4m3
-// limbs, V goes to Rt (free after the forward scan) with chunk maxima of |V|,
+// limbs, V goes to Rt (free once the group kernel read it) with chunk maxima of |V|,
 // and k_vlimbs splits it once the column's scale is known.
 template <int VO>
 __global__ void k_uv(SP s, void *Vout, int64_t n_pad, double *vmaxp)
@@ -330,8 +308,8 @@ __global__ void k_uv(SP s, void *Vout, int64_t n_pad, double *vmaxp)
     for (int e = threadIdx.x; e < SCAN_CH; e += NT) {
         const int64_t i = i0 + e;
         if (i >= s.n) break;
-        const int64_t tl = s.tail[i];
-        const double C = s.Ft[kk * s.n + tl] + s.pre[kk * s.nch + tl / SCAN_CH];
+        const int32_t gi = s.evidx[i];
+        const double C = gi > 0 ? s.Fg[kk * s.n_evh + gi - 1] : 0.0;
         const double u = s.w[kk * s.n + i] * C;
         const double V = static_cast<double>(s.delta[i]) - u;
         if (s.q) {
@@ -452,10 +430,11 @@ __global__ void k_finalize(SP s, int l1_blocks, const double *l1p, const double 
     for (int c = lane; c < s.nch; c += 32) v += s.vsp[kk * s.nch + c];
     v = warp_sum(v);
     if (need_loss) {
+        // f = (sum_g e_g log W_g + (events) c - sum_r delta_r eta_r) / n
         for (int c = lane; c < s.nch; c += 32) lo += s.lossp[kk * s.nch + c];
         if (l1p)
             for (int c = lane; c < l1_blocks; c += 32) b1 += l1p[kk * l1_blocks + c];
-        lo = warp_sum(lo) / static_cast<double>(s.n);
+        lo = (s.lossg[kk] - warp_sum(lo)) / static_cast<double>(s.n);
         b1 = warp_sum(b1);
     }
     if (lane != 0) return;
@@ -485,6 +464,9 @@ int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st)
     s.head = h->d_head;
     s.tail = h->d_tail;
     s.evhead = h->d_evhead;
+    s.evcnt = h->d_evcnt;
+    s.evidx = h->d_evidx;
+    s.evflag = h->d_evflag;
     s.n_evh = h->n_evhead;
     s.q = a.gamma ? h->q : 0;  // no gamma: X_c beta alone (cox_eta)
     s.Z = h->d_Z;
@@ -493,12 +475,11 @@ int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st)
     s.eta = ws.eta;
     s.w = ws.w;
     s.Rt = ws.Rt;
-    s.Ft = ws.Ft;
+    s.Fg = ws.Fg;
+    s.lossg = ws.lossg;
     s.cmax = ws.cmax;
     s.csw = ws.csw;
-    s.csd = ws.csd;
     s.suf = ws.suf;
-    s.pre = ws.pre;
     s.lossp = ws.lossp;
     s.vsp = ws.vsp;
     dim3 grid(h->n_chunks, a.k);
@@ -519,13 +500,8 @@ int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st)
     }
     if (a.exp64) k_rev<true><<<grid, NT, 0, st>>>(s);
     else k_rev<false><<<grid, NT, 0, st>>>(s);
-    k_chunks<true><<<a.k, 32, 0, st>>>(s);
-    if (h->n_evhead > 0) {
-        const unsigned gx = static_cast<unsigned>(std::min<int64_t>((h->n_evhead + NT - 1) / NT, 64));
-        k_inv_w<<<dim3(gx, a.k), NT, 0, st>>>(s);
-    }
-    k_fwd<<<grid, NT, 0, st>>>(s, a.need_loss);
-    k_chunks<false><<<a.k, 32, 0, st>>>(s);
+    k_chunks<<<a.k, 32, 0, st>>>(s);
+    k_group<<<a.k, NT, 0, st>>>(s, a.need_loss);
     switch (a.v_out) {
     case V_LIMBS_E4M3:
         k_uv<V_LIMBS_E4M3><<<grid, NT, 0, st>>>(s, a.V, h->n_pad, ws.vmaxp);
