@@ -829,7 +829,8 @@ void shape_for(int NP, int *T, int *CH, int *alt)
     *alt = 0;
 }
 
-constexpr int G_ALT = 2;  // decoder groups of the alternating-issuer kernels
+constexpr int G_ALT = 2;   // decoder groups of the alternating-issuer kernels
+constexpr int G_WIDE = 2;  // decoder groups of the 2 x 2 shape at 128 limb columns
 
 KernelFn pick_kernel(int T, int CH, int NP, int alt)
 {
@@ -846,6 +847,9 @@ KernelFn pick_kernel(int T, int CH, int NP, int alt)
     case 21128: return k_packed_gemm<2, 1, 128, DEC_GROUPS, false>;
     case 12128: return k_packed_gemm<1, 2, 128, DEC_GROUPS, false>;
     case 11128: return k_packed_gemm<1, 1, 128, DEC_GROUPS, false>;
+    // two decoder groups: 2 tiles x 2 chunks at 128 limb columns, whose two
+    // 128-column TMEM slots beside 256 accumulator columns leave no third slot
+    case 22128: return k_packed_gemm<2, 2, 128, G_WIDE, false>;
     case 11256: return k_packed_gemm<1, 1, 256, DEC_GROUPS, false>;
     // alternating issuers: 16 MMAs per commit up to N = 64, 8 at N = 128
     case 122016: return k_packed_gemm<2, 2, 16, G_ALT, true>;
@@ -856,9 +860,13 @@ KernelFn pick_kernel(int T, int CH, int NP, int alt)
     }
 }
 
-int groups_for(int alt) { return alt ? G_ALT : DEC_GROUPS; }
+int groups_for(int T, int CH, int NP, int alt)
+{
+    if (alt) return G_ALT;
+    return (T == 2 && CH == 2 && NP == 128) ? G_WIDE : DEC_GROUPS;
+}
 int issuers_for(int T, int alt) { return alt ? 2 : T; }
-int threads_for(int T, int alt) { return 32 * (2 + issuers_for(T, alt) + 4 * groups_for(alt)); }
+int threads_for(int T, int G, int alt) { return 32 * (2 + issuers_for(T, alt) + 4 * G); }
 
 int gcd_i(int a, int b) { return b ? gcd_i(b, a % b) : a; }
 
@@ -885,7 +893,8 @@ int gemm_shapes(int k, int *T, int *CH, int *issue, int max)
     for (int is = 1; is <= 3; ++is)
         for (int t = 2; t >= 1; --t)
             for (int c = 2; c >= 1; --c)
-                if (pick_kernel(t, c, NP, is == 2) && n < max) {
+                if (pick_kernel(t, c, NP, is == 2) && n < max &&
+                    !(is == 3 && groups_for(t, c, NP, 0) == G_WIDE)) {
                     T[n] = t;
                     CH[n] = c;
                     issue[n] = is;
@@ -908,7 +917,8 @@ int plan_shape(GemmPlan &g, int k, int T_req, int CH_req, int stages_req, int is
     if (T_req > 0) T = T_req;
     if (CH_req > 0) CH = CH_req;
     if (!pick_kernel(T, CH, np_cls, alt)) return COX_ERR_ARG;  // shape not compiled for this class
-    const int G = groups_for(alt);
+    const int G = groups_for(T, CH, np_cls, alt);
+    if (G == G_WIDE && !alt && issue_req == 3) return COX_ERR_ARG;  // pair commits: not planned for it
     const int stage = CH * (np_cls * 128 + T * BLOCK_BYTES);
     // group 0's window sums, then four per-column constants
     const int fold_bytes = T * (np_cls / LIMBS) * 128 * 4 + 4 * (np_cls / LIMBS) * 4;
@@ -923,12 +933,21 @@ int plan_shape(GemmPlan &g, int k, int T_req, int CH_req, int stages_req, int is
     // the named barriers, one per tile for each stage of the period
     // lcm(G, ring), must fit barriers 1..15
     const int acc_cols = (alt ? 2 * T : T) * np_cls;
-    int ring = (512 - acc_cols) / (T * CH * 32);
-    if (ring > 8) ring = 8;
-    if (ring > S - 1) ring = S - 1;
+    const int ring_max = std::min(8, (512 - acc_cols) / (T * CH * 32));
     // Parity waits need the phase before the awaited one complete; the
-    // kernel's hand-off notes derive when the pipeline guarantees that
-    while (ring >= G && !(lcm_i(G, ring) * T <= 15 && parity_safe(G, ring, S, alt))) --ring;
+    // kernel's hand-off notes derive when the pipeline guarantees that.  With
+    // the default depth, one stage more is tried when the rule holds for no
+    // ring at the budget's depth and the deeper ring still fits 227 KB (the
+    // two-group shape: three stages allow no safe ring of two, four do).
+    int ring = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        ring = std::min(ring_max, S - 1);
+        while (ring >= G && !(lcm_i(G, ring) * T <= 15 && parity_safe(G, ring, S, alt))) --ring;
+        if (ring >= G || stages_req > 0 || S >= 12 ||
+            static_cast<size_t>(S + 1) * stage + 1024 + 1024 + fold_bytes > 227 * 1024)
+            break;
+        ++S;
+    }
     if (ring < G) return COX_ERR_ARG;
     g.T = T;
     g.CH = CH;
@@ -1042,7 +1061,7 @@ int launch_gemm(cox_handle *h, const GemmPlan &g, const EpiArgs &e, int k, cudaS
     kp.err = h->d_err;
     KernelFn fn = pick_kernel(g.T, g.CH, g.NP, g.alt);
     if (!fn) return COX_ERR_ARG;
-    fn<<<g.grid, threads_for(g.T, g.alt), g.smem, st>>>(g.tmA, g.tmB, kp);
+    fn<<<g.grid, threads_for(g.T, g.G, g.alt), g.smem, st>>>(g.tmA, g.tmB, kp);
     COX_CUDA(cudaGetLastError());
     return COX_OK;
 }

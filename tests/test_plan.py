@@ -41,6 +41,31 @@ def _parity_safe(G, R, S):
     return G <= R and (S >= G + R or S % G == 0 or R % G == 0) and (S % 2 == 0 or S >= R + 2)
 
 
+def _limb_cols(k):
+    n = 4 * k
+    return next(c for c in (16, 32, 64, 128, 256) if n <= c)
+
+
+def _groups(t, c, a, np_cls):
+    """Decoder groups: two for alternating issuers and for 2 tiles x 2 chunks at
+    128 limb columns (no room for a third TMEM slot), else three."""
+    return 2 if a == 2 or (t, c, np_cls) == (2, 2, 128) else 3
+
+
+def _some_safe_ring(t, c, a, np_cls, S):
+    """Whether any TMEM ring the plan could take meets the parity rule at depth S."""
+    G = _groups(t, c, a, np_cls)
+    acc = (2 * t if a == 2 else t) * np_cls
+    rmax = min(8, (512 - acc) // (t * c * 32), S - 1)
+    for R in range(G, rmax + 1):
+        if math.lcm(G, R) * t > 15:
+            continue
+        ok = (R % 2 == 0 and S % 2 == 0) if a == 2 else _parity_safe(G, R, S)
+        if ok:
+            return True
+    return False
+
+
 def _check(k, p):
     assert p.limb_cols >= 4 * k and p.limb_cols in (16, 32, 64, 128, 256)
     assert p.ring >= p.decoder_groups
@@ -76,9 +101,10 @@ def test_every_shape_and_depth_keeps_the_invariants(k):
             rc, q = L.cox_plan_shape(k, t, c, s, a)
             want = min(max(s, q.decoder_groups + 1 if rc == 0 else s), 12)  # the planner caps the depth at 12
             if rc != 0:
-                # refused only beyond the shared-memory budget, or (alternating
-                # issuers) at an odd depth
-                assert rc == L.COX_ERR_ARG and (s > deepest or (a == 2 and min(max(s, 3), 12) % 2 == 1))
+                # refused only beyond the shared-memory budget, or at a depth where no
+                # ring meets the parity rule (an odd depth for alternating issuers)
+                S = min(max(s, _groups(t, c, a, _limb_cols(k)) + 1), 12)
+                assert rc == L.COX_ERR_ARG and (s > deepest or not _some_safe_ring(t, c, a, _limb_cols(k), S))
                 continue
             _check(k, q)
             assert q.stages == want
@@ -134,3 +160,21 @@ def test_alternating_issuers_plan():
     _check(16, p)
     assert (p.issuers, p.decoder_groups, p.ring, p.stages, p.mmas_per_commit, p.tmem_cols) == (2, 2, 2, 6, 16, 512)
     assert p.named_barriers == 4
+
+
+def test_two_group_shape_at_128_limb_columns():
+    """k = 17..32 (128 limb columns) with 2 row tiles x 2 K chunks: 256
+    accumulator columns leave room for two 128-column slots only, so the shape
+    runs two decoder groups (R = G = 2); at three stages no ring meets the
+    shared-memory waits' rule (3 < 2 + 2, 3 odd), so the planner takes four
+    stages (227 KB); 8 MMAs per commit per issuer.  Pair commits are not planned
+    for it."""
+    for k in (17, 32):
+        rc, p = L.cox_plan_shape(k, 2, 2, 0, 1)
+        assert rc == 0
+        _check(k, p)
+        assert (p.decoder_groups, p.ring, p.stages, p.named_barriers, p.tmem_cols, p.mmas_per_commit) == \
+            (2, 2, 4, 4, 512, 8)
+        assert not _parity_safe(2, 2, 3) and _parity_safe(2, 2, 4)
+        assert L.cox_plan_shape(k, 2, 2, 3, 1)[0] == L.COX_ERR_ARG
+        assert L.cox_plan_shape(k, 2, 2, 0, 3)[0] == L.COX_ERR_ARG
