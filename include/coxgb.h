@@ -322,9 +322,10 @@ int cox_get_info(cox_h h, cox_info *info);
 /*
  * Autotuner of the tensor-core products (COX_SPLIT_E4M3 handles).  For k
  * coefficient columns it times every compiled pipeline shape (row tiles and
- * K chunks per stage, and two shared-memory depths) of both products on the
- * handle's resident genotypes: one warm-up and `reps` launches each, CUDA
- * events on the legacy stream, partial outputs only (no coefficient
+ * K chunks per stage; per-tile and alternating issuers) of both products at
+ * the planner's shared-memory depth on the handle's resident genotypes: one
+ * warm-up and `reps` launches each, CUDA events on the legacy stream, the
+ * device synchronised after each shape, partial outputs only (no coefficient
  * changes).  The fastest shape per product is kept for k and used by later
  * calls with k columns unless cox_options forces tile_m, chunks or stages.
  * xb / xtv (either may be NULL) receive the choice and its mean launch time.
