@@ -830,7 +830,7 @@ void shape_for(int NP, int *T, int *CH, int *alt)
 }
 
 constexpr int G_ALT = 2;   // decoder groups of the alternating-issuer kernels
-constexpr int G_WIDE = 2;  // decoder groups of the 2 x 2 shape at 128 limb columns
+constexpr int G_WIDE = 2;  // decoder groups of the 2 x 2 shape at 128 limb columns and 2 x 3 at 64
 
 KernelFn pick_kernel(int T, int CH, int NP, int alt)
 {
@@ -850,6 +850,9 @@ KernelFn pick_kernel(int T, int CH, int NP, int alt)
     // two decoder groups: 2 tiles x 2 chunks at 128 limb columns, whose two
     // 128-column TMEM slots beside 256 accumulator columns leave no third slot
     case 22128: return k_packed_gemm<2, 2, 128, G_WIDE, false>;
+    // two decoder groups: 2 tiles x 3 chunks at 64 limb columns (12 MMAs per
+    // commit per issuer; two 192-column slots beside 128 accumulator columns)
+    case 23064: return k_packed_gemm<2, 3, 64, G_WIDE, false>;
     case 11256: return k_packed_gemm<1, 1, 256, DEC_GROUPS, false>;
     // alternating issuers: 16 MMAs per commit up to N = 64, 8 at N = 128
     case 122016: return k_packed_gemm<2, 2, 16, G_ALT, true>;
@@ -863,7 +866,7 @@ KernelFn pick_kernel(int T, int CH, int NP, int alt)
 int groups_for(int T, int CH, int NP, int alt)
 {
     if (alt) return G_ALT;
-    return (T == 2 && CH == 2 && NP == 128) ? G_WIDE : DEC_GROUPS;
+    return ((T == 2 && CH == 2 && NP == 128) || (T == 2 && CH == 3 && NP == 64)) ? G_WIDE : DEC_GROUPS;
 }
 int issuers_for(int T, int alt) { return alt ? 2 : T; }
 int threads_for(int T, int G, int alt) { return 32 * (2 + issuers_for(T, alt) + 4 * G); }
@@ -892,7 +895,7 @@ int gemm_shapes(int k, int *T, int *CH, int *issue, int max)
     int n = 0;
     for (int is = 1; is <= 3; ++is)
         for (int t = 2; t >= 1; --t)
-            for (int c = 2; c >= 1; --c)
+            for (int c = 3; c >= 1; --c)
                 if (pick_kernel(t, c, NP, is == 2) && n < max &&
                     !(is == 3 && groups_for(t, c, NP, 0) == G_WIDE)) {
                     T[n] = t;

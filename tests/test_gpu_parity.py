@@ -152,6 +152,7 @@ def test_prox_whole_and_split_row_groups(pkg):
 # alternate stages, 3 = one per row tile committing after every second stage
 SHAPES = [(k, t, c, 1) for k in (3, 8, 16) for (t, c) in ((2, 2), (2, 1), (1, 2))] + \
          [(32, 2, 1, 1), (32, 1, 2, 1), (32, 1, 1, 1), (32, 2, 2, 1), (20, 2, 2, 1), (64, 1, 1, 1)] + \
+         [(16, 2, 3, 1), (10, 2, 3, 1)] + \
          [(3, 2, 2, 2), (8, 2, 2, 2), (16, 2, 2, 2), (32, 1, 2, 2)] + \
          [(3, 2, 2, 3), (16, 2, 2, 3), (16, 2, 1, 3), (32, 2, 1, 3), (64, 1, 1, 3)]
 

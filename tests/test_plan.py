@@ -23,7 +23,7 @@ import pytest
 
 from paper_2010_16114_gb300 import _lib as L
 
-SHAPES = [(t, c, a) for a in (1, 2, 3) for t in (2, 1) for c in (2, 1)]
+SHAPES = [(t, c, a) for a in (1, 2, 3) for t in (2, 1) for c in (3, 2, 1)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -47,9 +47,10 @@ def _limb_cols(k):
 
 
 def _groups(t, c, a, np_cls):
-    """Decoder groups: two for alternating issuers and for 2 tiles x 2 chunks at
-    128 limb columns (no room for a third TMEM slot), else three."""
-    return 2 if a == 2 or (t, c, np_cls) == (2, 2, 128) else 3
+    """Decoder groups: two for alternating issuers, for 2 tiles x 2 chunks at
+    128 limb columns and 2 tiles x 3 chunks at 64 (no room for a third TMEM
+    slot), else three."""
+    return 2 if a == 2 or (t, c, np_cls) in ((2, 2, 128), (2, 3, 64)) else 3
 
 
 def _some_safe_ring(t, c, a, np_cls, S):
@@ -134,7 +135,8 @@ def test_rejections():
     assert L.cox_plan_shape(0)[0] == L.COX_ERR_ARG
     assert L.cox_plan_shape(65)[0] == L.COX_ERR_ARG
     assert L.cox_plan_shape(16, 3, 0)[0] == L.COX_ERR_ARG      # three row tiles: not compiled
-    assert L.cox_plan_shape(16, 0, 3)[0] == L.COX_ERR_ARG      # three K chunks: not compiled
+    assert L.cox_plan_shape(32, 0, 3)[0] == L.COX_ERR_ARG      # three K chunks: only at 64 limb columns
+    assert L.cox_plan_shape(16, 1, 3)[0] == L.COX_ERR_ARG      # three K chunks: only with two row tiles
     assert L.cox_plan_shape(64, 2, 2)[0] == L.COX_ERR_ARG      # 256 limb columns take one tile, one chunk
     assert L.cox_plan_shape(16, -1, 0)[0] == L.COX_ERR_ARG
     assert L.load().cox_plan_shape(16, 0, 0, 0, 0, None) == L.COX_ERR_ARG
@@ -148,7 +150,7 @@ def test_front_end_wrapper():
     d = plan_shape(16)
     assert (d["tile_m"], d["chunks"], d["stages"], d["ring"], d["limb_cols"]) == (2, 2, 6, 3, 64)
     with pytest.raises(L.CoxError):
-        plan_shape(16, chunks=3)
+        plan_shape(32, chunks=3)
 
 
 def test_alternating_issuers_plan():
@@ -178,3 +180,16 @@ def test_two_group_shape_at_128_limb_columns():
         assert not _parity_safe(2, 2, 3) and _parity_safe(2, 2, 4)
         assert L.cox_plan_shape(k, 2, 2, 3, 1)[0] == L.COX_ERR_ARG
         assert L.cox_plan_shape(k, 2, 2, 0, 3)[0] == L.COX_ERR_ARG
+
+
+def test_two_group_shape_with_three_chunks():
+    """k = 9..16 (64 limb columns) with 2 row tiles x 3 K chunks: 128
+    accumulator columns and two 192-column slots fill TMEM, so two decoder
+    groups (R = G = 2); 12 MMAs per commit per issuer; four 48 KB stages."""
+    for k in (9, 16):
+        rc, p = L.cox_plan_shape(k, 2, 3, 0, 1)
+        assert rc == 0
+        _check(k, p)
+        assert (p.decoder_groups, p.ring, p.stages, p.named_barriers, p.tmem_cols, p.mmas_per_commit) == \
+            (2, 2, 4, 4, 512, 12)
+        assert L.cox_plan_shape(k, 2, 3, 0, 3)[0] == L.COX_ERR_ARG
