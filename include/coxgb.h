@@ -90,7 +90,9 @@ typedef struct cox_options {
     int stages;           /* shared-memory pipeline depth; 0 = automatic             */
     int lag;              /* stopping-rule lag in iterations (default 10, Section 6) */
     double wait_limit_s;  /* device-side wait limit in seconds (default 2.0)         */
-    int chunks;           /* 128-wide K chunks per pipeline stage (1 or 2);
+    int chunks;           /* 128-wide K chunks per pipeline stage (1 or 2; 3 with
+                             two row tiles at 64 limb columns, k = 9..16, where
+                             the product's chunk count divides by 3);
                              0 = automatic, as tile_m                               */
     int window;           /* K chunks a TMEM accumulator sums in FP32 before decoder
                              warps add it into FP32 sums (>= chunks; 0 = 256)       */
