@@ -124,8 +124,9 @@ __global__ void __launch_bounds__(128) k_gemv_tiles(const uint32_t *__restrict__
 // per 16-byte half); every range of chunks leaves one FP32 partial per row, and
 // k_gemv_reduce adds the partials with a compensated FP32 sum.
 // 16 chunks (64 KB of tables) let two CTAs share an SM (registers allow two of
-// 512 threads); measured at full size against 48 (one CTA per SM) and 24:
-// 0.546, 0.477 and 0.529 of the HBM copy bandwidth.
+// 512 threads); measured at full size against 48 (one CTA per SM) and 24 with a
+// shift and a mask per lookup: 0.546, 0.477 and 0.529 of the HBM copy bandwidth;
+// with the byte-permute lookup below, 0.610.
 constexpr int LUT_CW = 16;          // K chunks per CTA (tables: 16 x 4 KB)
 constexpr int LUT_THREADS = 512;    // two threads per row, two row tiles per pass
 constexpr int LUT_CHUNK = 1024;     // floats per chunk's tables
@@ -133,10 +134,14 @@ constexpr int LUT_BATCH = 8;        // chunks whose codes a thread loads before 
 
 // The 32 lookups of one chunk's 16 bytes of codes: nibble j of word q reads the
 // table at byte offset 4 (C LUT_CHUNK + ((4 q + j / 2) 2 + j % 2) 32 + v), v the
-// nibble, as (cb | 4 v) + offset with the offset an immediate of the load.
+// nibble, from a 256-byte aligned base.  Per word, lo and hi hold in each byte b
+// the low or high nibble of byte b times 4, ORed with this half's 64-byte table
+// offset (hm); a lookup's address is then one byte permute, byte 0 from lo or hi
+// and bytes 1-3 from the base, with the offset an immediate of the load: a
+// permute, the load and the add per nibble, plus four logic operations a word.
 #define COX_LUT_NIB(Q, J)                                                                           \
     {                                                                                               \
-        const uint32_t a = cb | ((J) == 0 ? (ws[Q] << 2) & 0x3Cu : (ws[Q] >> (4 * (J) - 2)) & 0x3Cu);   \
+        const uint32_t a = __byte_perm((J) & 1 ? hi : lo, cb, 0x7650u | ((J) >> 1));                 \
         float t;                                                                                    \
         asm("ld.shared.f32 %0, [%1+%2];"                                                            \
             : "=f"(t)                                                                               \
@@ -144,11 +149,15 @@ constexpr int LUT_BATCH = 8;        // chunks whose codes a thread loads before 
         acc[(J) & 3] += t;                                                                          \
     }
 #define COX_LUT_WORD(Q)                                                                             \
-    COX_LUT_NIB(Q, 0) COX_LUT_NIB(Q, 1) COX_LUT_NIB(Q, 2) COX_LUT_NIB(Q, 3) COX_LUT_NIB(Q, 4)         \
-    COX_LUT_NIB(Q, 5) COX_LUT_NIB(Q, 6) COX_LUT_NIB(Q, 7)
+    {                                                                                               \
+        const uint32_t lo = ((ws[Q] << 2) & 0x3C3C3C3Cu) | hm;                                      \
+        const uint32_t hi = ((ws[Q] >> 2) & 0x3C3C3C3Cu) | hm;                                      \
+        COX_LUT_NIB(Q, 0) COX_LUT_NIB(Q, 1) COX_LUT_NIB(Q, 2) COX_LUT_NIB(Q, 3) COX_LUT_NIB(Q, 4)     \
+        COX_LUT_NIB(Q, 5) COX_LUT_NIB(Q, 6) COX_LUT_NIB(Q, 7)                                       \
+    }
 
 template <int C>
-__device__ __forceinline__ void lut_chunk(uint32_t cb, const uint4 &w, float (&acc)[4])
+__device__ __forceinline__ void lut_chunk(uint32_t cb, uint32_t hm, const uint4 &w, float (&acc)[4])
 {
     const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
     COX_LUT_WORD(0) COX_LUT_WORD(1) COX_LUT_WORD(2) COX_LUT_WORD(3)
@@ -161,7 +170,10 @@ __global__ void __launch_bounds__(LUT_THREADS) k_gemv_lut(const uint32_t *__rest
                                                           int64_t K_valid, float *__restrict__ part,
                                                           int64_t rows_pad, int n_ranges, int64_t tiles_per_split)
 {
-    extern __shared__ __align__(1024) float tab[];
+    extern __shared__ __align__(1024) float smem_lut[];
+    // tables from the first 256-byte boundary (the launch adds 256 bytes)
+    float *tab = reinterpret_cast<float *>(
+        smem_lut + ((256u - (static_cast<uint32_t>(__cvta_generic_to_shared(smem_lut)) & 255u)) & 255u) / 4);
     const int range = static_cast<int>(blockIdx.x % n_ranges);
     const int64_t split = blockIdx.x / n_ranges;
     const int64_t kc0 = static_cast<int64_t>(range) * LUT_CW;
@@ -181,11 +193,10 @@ __global__ void __launch_bounds__(LUT_THREADS) k_gemv_lut(const uint32_t *__rest
     __syncthreads();
     const int r = (threadIdx.x & 255) >> 1, hh = threadIdx.x & 1;
     const int swp = (r >> 2) & 1;
-    // byte address of this half's table entry 0: 64-byte aligned, so that a
-    // lookup's address is this base ORed with 4 v (bits 2..5) plus the
-    // (chunk, word, byte, nibble) offset as an immediate: shift, one logic
-    // operation, the load and the add per nibble
-    const uint32_t tb = static_cast<uint32_t>(__cvta_generic_to_shared(tab)) + 64u * hh;
+    // byte address of the tables (256-byte aligned); this half's tables sit 64 bytes
+    // in, which hm carries into byte 0 of every lookup's address
+    const uint32_t tb = static_cast<uint32_t>(__cvta_generic_to_shared(tab));
+    const uint32_t hm = hh ? 0x40404040u : 0u;
     const int64_t mt_begin = split * tiles_per_split;
     const int64_t mt_end = min(row_tiles, mt_begin + tiles_per_split);
     for (int64_t mt = mt_begin + (threadIdx.x >> 8); mt < mt_end; mt += 2) {
@@ -199,14 +210,14 @@ __global__ void __launch_bounds__(LUT_THREADS) k_gemv_lut(const uint32_t *__rest
             // tables of chunk c0 + c start 4 LUT_CHUNK (c0 + c) bytes in: a multiple of 4 KB
             const uint32_t cb = tb + 4u * LUT_CHUNK * static_cast<uint32_t>(c0);
             static_assert(LUT_BATCH == 8, "lut_chunk calls below");
-            if (c0 + 0 < ncw) lut_chunk<0>(cb, w[0], acc);
-            if (c0 + 1 < ncw) lut_chunk<1>(cb, w[1], acc);
-            if (c0 + 2 < ncw) lut_chunk<2>(cb, w[2], acc);
-            if (c0 + 3 < ncw) lut_chunk<3>(cb, w[3], acc);
-            if (c0 + 4 < ncw) lut_chunk<4>(cb, w[4], acc);
-            if (c0 + 5 < ncw) lut_chunk<5>(cb, w[5], acc);
-            if (c0 + 6 < ncw) lut_chunk<6>(cb, w[6], acc);
-            if (c0 + 7 < ncw) lut_chunk<7>(cb, w[7], acc);
+            if (c0 + 0 < ncw) lut_chunk<0>(cb, hm, w[0], acc);
+            if (c0 + 1 < ncw) lut_chunk<1>(cb, hm, w[1], acc);
+            if (c0 + 2 < ncw) lut_chunk<2>(cb, hm, w[2], acc);
+            if (c0 + 3 < ncw) lut_chunk<3>(cb, hm, w[3], acc);
+            if (c0 + 4 < ncw) lut_chunk<4>(cb, hm, w[4], acc);
+            if (c0 + 5 < ncw) lut_chunk<5>(cb, hm, w[5], acc);
+            if (c0 + 6 < ncw) lut_chunk<6>(cb, hm, w[6], acc);
+            if (c0 + 7 < ncw) lut_chunk<7>(cb, hm, w[7], acc);
         }
         float sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
         sum += __shfl_xor_sync(0xffffffffu, sum, 1);
@@ -383,7 +394,7 @@ size_t gemv_lut_part_floats(int64_t rows_pad, int64_t KC) { return static_cast<s
 int gemv_lut(cox_handle *h, const uint32_t *A, int64_t rows, int64_t KC, const float *x, int64_t K_valid,
              float *part, float *y, cudaStream_t st)
 {
-    const size_t smem = static_cast<size_t>(LUT_CW) * LUT_CHUNK * sizeof(float);
+    const size_t smem = static_cast<size_t>(LUT_CW) * LUT_CHUNK * sizeof(float) + 256;
     COX_CUDA(cudaFuncSetAttribute(k_gemv_lut, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     int n_ranges = 0, grid = 0;
     int64_t tps = 0;
