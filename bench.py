@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--p", type=int, default=None)
     ap.add_argument("--k", type=int, default=None)
+    ap.add_argument("--precision", default="split_e2m1", choices=["split_e4m3", "split_e2m1"],
+                    help="operand form of the tensor-core products: e2m1 (kind::mxf4, six limbs) or e4m3 "
+                         "(kind::f8f6f4, four limbs)")
     ap.add_argument("--tile-m", type=int, default=0)
     ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--chunks", type=int, default=0)
@@ -101,12 +104,14 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def gemm_traffic(k: int, n: int, p: int):
+def gemm_traffic(k: int, n: int, p: int, precision: str):
     """DRAM bytes per launch of the tensor-core product from the committed ncu
-    summary, scaled by n*p codes; None when the kernel source changed since."""
+    summary of its operand form, scaled by n*p codes; None when the kernel
+    source changed since."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_packed_gemm_traffic_n65536_p65536_k16.txt")
-    src = os.path.join(ROOT, "paper_2010_16114_gb300", "csrc", "gemm_tc.cu")
+    form = "e2m1" if precision == "split_e2m1" else "e4m3"
+    path = os.path.join(ROOT, "profiles", f"k_packed_gemm_{form}_traffic_n65536_p65536_k16.txt")
+    src = os.path.join(ROOT, "paper_2010_16114_gb300", "csrc", "gemm_kernel.cuh")
     try:
         kv = {}
         with open(path) as fh:
@@ -434,7 +439,7 @@ def run_ours(args, rank, world):
     packed = torch.empty((n, (p + 3) // 4), dtype=torch.uint8, device="cuda")
     w.packed_rows_device(packed.data_ptr(), stream.cuda_stream, thr.data_ptr())
     torch.cuda.synchronize()
-    prob = CoxProblem(packed, w.y, w.delta, p=p, precision="split_e4m3", tile_m=args.tile_m, stages=args.stages,
+    prob = CoxProblem(packed, w.y, w.delta, p=p, precision=args.precision, tile_m=args.tile_m, stages=args.stages,
                       chunks=args.chunks, issue=args.issue, window=args.window)
     del packed, thr
     torch.cuda.empty_cache()
@@ -480,8 +485,9 @@ def run_ours(args, rank, world):
 
     # algorithmic bytes (packed X padded to 128 per dimension, as streamed by each product)
     xb = (-(-n // 128) * 128) * (-(-p // 128) * 128) / 4.0
-    b1 = xb + p * 2 * k * 2 + k * n * 4           # X, beta limbs, eta partials
-    b4 = xb + n * 2 * k * 2 + 8 * k * p           # X, V limbs, beta read+write
+    lb = 3 if args.precision == "split_e2m1" else 4  # limb bytes per coefficient: 6 e2m1 or 4 e4m3
+    b1 = xb + p * lb * k + k * n * 4              # X, beta limbs, eta partials
+    b4 = xb + n * lb * k + 8 * k * p              # X, V limbs, beta read+write
     scan_bytes = k * n * 8 * 12                     # FP64 scan passes (eta, w, R, F, gathers, V)
     iter_bytes = b1 + b4 + scan_bytes + 12 * k * p  # + beta limbs / l1 pass
     gemm_ms = cls_ms[0] + cls_ms[1]
@@ -489,7 +495,7 @@ def run_ours(args, rank, world):
     avg_launch_s = (gemm_ms / max(gemm_n, 1)) / 1e3
     achieved = ((b1 + b4) / 2.0) / avg_launch_s / 1e9
     peak, peak_kind = measured_peak_hbm()
-    traffic = gemm_traffic(k, n, p)
+    traffic = gemm_traffic(k, n, p, args.precision)
 
     # end to end: host buffers through the C ABI, copies inside the timed region
     e2e = None
@@ -530,7 +536,7 @@ def run_ours(args, rank, world):
                 "lambda_iters_per_s": k * 1e3 / gms, "speedup_of_batched": (1e3 / ms_step) / (1e3 / gms),
                 "hbm_gbs": g_hbm, "hbm_frac": g_hbm / peak,
                 "rel_l2_vs_batched_one_step": diff}
-        prob.set_precision("split_e4m3")
+        prob.set_precision(args.precision)
 
     # the CUDA-graph path fit (Section 6 rule): every penalty from beta = 0 to
     # |F_t - F_{t-10}| / |F_t + 1| < tol or the iteration cap, replays of 10 steps
@@ -606,9 +612,12 @@ def run_ours(args, rank, world):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "e4m3", "data": "synthetic",
-        "precision": "genotype products: codes and 4-limb split coefficients as e4m3 on tcgen05 "
-                     "(kind::f8f6f4), FP32 accumulation; risk-set scans and objective FP64",
+        "vs_baseline": None, "dtype": "e2m1" if args.precision == "split_e2m1" else "e4m3", "data": "synthetic",
+        "precision": ("genotype products: codes and 6-limb split coefficients as e2m1 on tcgen05 "
+                      "(kind::mxf4, unit block scales), FP32 accumulation; risk-set scans and objective FP64"
+                      if args.precision == "split_e2m1" else
+                      "genotype products: codes and 4-limb split coefficients as e4m3 on tcgen05 "
+                      "(kind::f8f6f4), FP32 accumulation; risk-set scans and objective FP64"),
         "config": {"workload": workload_name(r), "n": n, "p": p, "k": k,
                    "l2": "inputs larger than L2: 2 x ~50 GB of packed genotypes streamed per step",
                    "parallelism": "replicas" if world > 1 else "single GPU",

@@ -75,8 +75,14 @@ enum {
                            power-of-two column scale, FP32 accumulation; FP64
                            risk-set scans (default)                            */
     COX_FP64 = 1,       /* FP64 everywhere, dense X (COX_X_F64_HOST)          */
-    COX_FP32_GEMV = 2   /* baseline: one lambda at a time, FP32 CUDA-core GEMV
+    COX_FP32_GEMV = 2,  /* baseline: one lambda at a time, FP32 CUDA-core GEMV
                            on the packed genotypes, unfused soft threshold    */
+    COX_SPLIT_E2M1 = 3  /* tcgen05 tensor cores (kind::mxf4, unit block scales):
+                           genotype codes as e2m1 (two per byte, K = 64 per
+                           MMA), coefficients split into 6 e2m1 limbs on the
+                           grid of halves under a power-of-two column scale
+                           (within 2^-17 of the column's largest magnitude),
+                           FP32 accumulation; FP64 risk-set scans; k <= 16  */
 };
 
 typedef struct cox_options {
@@ -369,6 +375,11 @@ typedef struct cox_plan {
     int mmas_per_commit;  /* tcgen05.mma instructions per issuer commit            */
 } cox_plan;
 int cox_plan_shape(int k, int tile_m, int chunks, int stages, int issue, cox_plan *out);
+/* The same plan for either operand form: precision COX_SPLIT_E4M3 (as
+ * cox_plan_shape) or COX_SPLIT_E2M1 (k <= 16; issue 0 or 1 only; limb_cols
+ * counts e2m1 limb columns, tmem_cols includes the 8 scale-factor columns).
+ * COX_ERR_ARG for any other precision or a shape that is not compiled. */
+int cox_plan_shape_prec(int precision, int k, int tile_m, int chunks, int stages, int issue, cox_plan *out);
 
 /*
  * SNP ranking of Section 6 on a lambda path's coefficients (host arithmetic,

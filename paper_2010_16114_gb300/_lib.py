@@ -29,6 +29,7 @@ COX_X_PACKED2_DEV = 3
 COX_SPLIT_E4M3 = 0
 COX_FP64 = 1
 COX_FP32_GEMV = 2
+COX_SPLIT_E2M1 = 3
 
 # every symbol include/coxgb.h declares
 EXPORTS = [
@@ -38,7 +39,7 @@ EXPORTS = [
     "cox_strerror", "cox_set_precision", "cox_profile", "cox_profile_read", "cox_lipschitz_noalloc",
     "cox_autotune", "cox_eta", "cox_plan_shape", "cox_rank_by_entry", "cox_path_seq", "cox_set_covariates",
     "cox_get_gamma", "cox_set_gamma", "cox_grad_gamma", "cox_prox_step_eta", "cox_last_loss_l1",
-    "cox_set_active_set",
+    "cox_set_active_set", "cox_plan_shape_prec",
 ]
 # every symbol include/nmfgb.h declares
 NMF_EXPORTS = [
@@ -150,6 +151,8 @@ def load(path: str | None = None):
     lib.cox_autotune.argtypes = [P, I, I, ctypes.POINTER(cox_tune_choice), ctypes.POINTER(cox_tune_choice)]
     lib.cox_plan_shape.restype = I
     lib.cox_plan_shape.argtypes = [I, I, I, I, I, ctypes.POINTER(cox_plan)]
+    lib.cox_plan_shape_prec.restype = I
+    lib.cox_plan_shape_prec.argtypes = [I, I, I, I, I, I, ctypes.POINTER(cox_plan)]
     lib.cox_rank_by_entry.restype = I
     lib.cox_rank_by_entry.argtypes = [I64, I, P, P, I, P, P, ctypes.POINTER(I64)]
     lib.cox_path_seq.restype = I
@@ -308,6 +311,14 @@ def cox_plan_shape(k: int, tile_m: int = 0, chunks: int = 0, stages: int = 0, is
     """(rc, cox_plan) of the tensor-core products for k columns; host only."""
     out = cox_plan()
     rc = load().cox_plan_shape(k, tile_m, chunks, stages, issue, ctypes.byref(out))
+    return rc, out
+
+
+def cox_plan_shape_prec(precision: int, k: int, tile_m: int = 0, chunks: int = 0, stages: int = 0,
+                        issue: int = 0):
+    """(rc, cox_plan) of either operand form of the tensor-core products; host only."""
+    out = cox_plan()
+    rc = load().cox_plan_shape_prec(precision, k, tile_m, chunks, stages, issue, ctypes.byref(out))
     return rc, out
 
 

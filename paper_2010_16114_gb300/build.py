@@ -10,8 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libcoxgb.so")
-SOURCES = ["api.cu", "setup.cu", "scans.cu", "gemm_tc.cu", "gemv.cu", "path.cu", "active.cu", "nmf.cu"]
-HEADERS = ["internal.h", "ptx.cuh", "nmf_gemm.cuh"]
+SOURCES = ["api.cu", "setup.cu", "scans.cu", "gemm_tc.cu", "gemm_f4.cu", "gemv.cu", "path.cu", "active.cu", "nmf.cu"]
+HEADERS = ["internal.h", "ptx.cuh", "nmf_gemm.cuh", "gemm_kernel.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing",
           f"-I{os.path.join(ROOT, 'include')}"]

@@ -13,7 +13,8 @@ import torch
 
 from . import _lib as L
 
-PRECISIONS = {"split_e4m3": L.COX_SPLIT_E4M3, "fp64": L.COX_FP64, "fp32_gemv": L.COX_FP32_GEMV}
+PRECISIONS = {"split_e4m3": L.COX_SPLIT_E4M3, "fp64": L.COX_FP64, "fp32_gemv": L.COX_FP32_GEMV,
+              "split_e2m1": L.COX_SPLIT_E2M1}
 
 
 def _vp(x):
@@ -34,12 +35,15 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(int(stream))
 
 
-def plan_shape(k: int, tile_m: int = 0, chunks: int = 0, stages: int = 0, issue: int = 0) -> dict:
-    """The tensor-core products' pipeline plan for k columns (cox_plan_shape):
-    shape, issue mode, shared-memory depth, TMEM slots, barriers and memory.
-    Host only; raises CoxError for a shape or depth the pipeline does not allow."""
-    rc, p = L.cox_plan_shape(int(k), int(tile_m), int(chunks), int(stages), int(issue))
-    L.check(rc, "cox_plan_shape")
+def plan_shape(k: int, tile_m: int = 0, chunks: int = 0, stages: int = 0, issue: int = 0,
+               precision: str = "split_e4m3") -> dict:
+    """The tensor-core products' pipeline plan for k columns (cox_plan_shape_prec):
+    shape, issue mode, shared-memory depth, TMEM slots, barriers and memory, for
+    the e4m3 or the e2m1 operand form.  Host only; raises CoxError for a shape or
+    depth the pipeline does not allow."""
+    rc, p = L.cox_plan_shape_prec(PRECISIONS[precision], int(k), int(tile_m), int(chunks), int(stages),
+                                  int(issue))
+    L.check(rc, "cox_plan_shape_prec")
     return {f: getattr(p, f) for f, _ in L.cox_plan._fields_}
 
 

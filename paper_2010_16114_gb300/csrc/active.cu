@@ -125,6 +125,42 @@ __global__ void k_prep_limbs_active(const float *__restrict__ beta, int64_t p, c
     }
 }
 
+// e2m1 limbs of beta at the active SNPs: byte t of a limb row holds active
+// positions 16 (t / 8) + t mod 8 (low nibble) and that + 8 (e2m1_byte).
+__global__ void k_prep_limbs_active4(const float *__restrict__ beta, int64_t p, const int32_t *__restrict__ Aidx,
+                                     int64_t nA, int64_t Kpad, int nb, const float *__restrict__ maxp,
+                                     uint8_t *__restrict__ Bq, int *__restrict__ bs, int *err)
+{
+    __shared__ int s_sh;
+    const int kk = blockIdx.y;
+    if (threadIdx.x < 32) {
+        float m = 0.f;
+        for (int b = threadIdx.x; b < nb; b += 32) m = fmaxf(m, maxp[kk * nb + b]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) {
+            if (!isfinite(m)) {
+                atomicOr(err, DEVERR_NONFINITE);
+                m = 0.f;
+            }
+            s_sh = limb_scale4(m);
+            if (blockIdx.x == 0) bs[kk] = s_sh;
+        }
+    }
+    __syncthreads();
+    const int s = s_sh;
+    const int64_t rb = Kpad / 2;
+    for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < rb;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t t0 = ((t >> 3) << 4) + (t & 7);
+        uint8_t d0[LIMBS4] = {0, 0, 0, 0, 0, 0}, d1[LIMBS4] = {0, 0, 0, 0, 0, 0};
+        if (t0 < nA) split_e2m1_units(ldexpf(beta[static_cast<int64_t>(kk) * p + Aidx[t0]], -s), d0);
+        if (t0 + 8 < nA) split_e2m1_units(ldexpf(beta[static_cast<int64_t>(kk) * p + Aidx[t0 + 8]], -s), d1);
+#pragma unroll
+        for (int l = 0; l < LIMBS4; ++l) Bq[(LIMBS4 * kk + l) * rb + t] = static_cast<uint8_t>(d0[l] | (d1[l] << 4));
+    }
+}
+
 unsigned grid_over(int64_t total, int sms)
 {
     return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 16LL * sms)));
@@ -197,7 +233,9 @@ int active_prepare(cox_handle *h, const float *beta, int k, cudaStream_t st, int
             if (flag[j]) idx.push_back(static_cast<int32_t>(j));
         const int64_t nA = static_cast<int64_t>(idx.size());
         if (nA > limit) return COX_OK;  // the set in use stays as it was
-        const int64_t Kpad = std::max<int64_t>(256, (nA + 255) / 256 * 256);
+        // K chunk pairs; groups of four chunks for the e2m1 stages of four chunks
+        const int64_t ku = ws.g1.CH == 4 ? 512 : 256;
+        const int64_t Kpad = std::max<int64_t>(ku, (nA + ku - 1) / ku * ku);
         if (Kpad > h->act_cap) {
             dfree(h->d_Aidx);
             dfree(h->d_A1act);
@@ -227,8 +265,9 @@ int active_prepare(cox_handle *h, const float *beta, int k, cudaStream_t st, int
         // limbs and plan for this active width (the shape of the dense plan)
         dfree(ws.Bqa);
         ws.Bqa = nullptr;
-        COX_TRY(dmalloc(h, reinterpret_cast<void **>(&ws.Bqa), static_cast<size_t>(ws.NP) * h->act_Kpad));
-        COX_CUDA(cudaMemsetAsync(ws.Bqa, 0, static_cast<size_t>(ws.NP) * h->act_Kpad, st));
+        const int64_t bpk = ws.g1.f4 ? 2 : 1;  // K positions per limb byte
+        COX_TRY(dmalloc(h, reinterpret_cast<void **>(&ws.Bqa), static_cast<size_t>(ws.NP) * h->act_Kpad / bpk));
+        COX_CUDA(cudaMemsetAsync(ws.Bqa, 0, static_cast<size_t>(ws.NP) * h->act_Kpad / bpk, st));
         const int issue = ws.g1.alt ? 2 : ws.g1.pair ? 3 : 1;
         COX_TRY(plan_gemm(h, ws.g1a, h->d_A1act, h->n_pad, h->act_Kpad, ws.Bqa, k, ws.g1.T, ws.g1.CH, ws.g1.stages,
                           issue));
@@ -243,8 +282,12 @@ int active_prepare(cox_handle *h, const float *beta, int k, cudaStream_t st, int
         ws.g1a_K = h->act_Kpad;
     }
     const int64_t gx = std::min<int64_t>((h->act_Kpad + 255) / 256, std::max<int64_t>(1, 4LL * h->sm_count / k));
-    k_prep_limbs_active<<<dim3(static_cast<unsigned>(gx), k), 256, 0, st>>>(
-        beta, p, h->d_Aidx, h->nA, h->act_Kpad, h->l1_blocks, ws.bmaxp, ws.Bqa, ws.bs1, h->d_err);
+    if (ws.g1.f4)
+        k_prep_limbs_active4<<<dim3(static_cast<unsigned>(gx), k), 256, 0, st>>>(
+            beta, p, h->d_Aidx, h->nA, h->act_Kpad, h->l1_blocks, ws.bmaxp, ws.Bqa, ws.bs1, h->d_err);
+    else
+        k_prep_limbs_active<<<dim3(static_cast<unsigned>(gx), k), 256, 0, st>>>(
+            beta, p, h->d_Aidx, h->nA, h->act_Kpad, h->l1_blocks, ws.bmaxp, ws.Bqa, ws.bs1, h->d_err);
     COX_CUDA(cudaGetLastError());
     h->launches += 1;
     *use = 1;

@@ -95,8 +95,10 @@ struct DeviceGuard {
     }
 };
 
-bool is_split(const cox_handle *h) { return h->opt.precision == COX_SPLIT_E4M3; }
+bool is_split(const cox_handle *h) { return h->opt.precision == COX_SPLIT_E4M3 || is_e2m1(h); }
 bool is_fp64(const cox_handle *h) { return h->opt.precision == COX_FP64; }
+// largest k of the tensor-core products: 96 e2m1 limb columns hold 16 coefficients
+int max_k_tc(const cox_handle *h) { return is_e2m1(h) ? MAX_K_E2M1 : MAX_K_TC; }
 
 cudaEvent_t get_event(cox_handle *h)
 {
@@ -367,7 +369,7 @@ namespace {
 int validate_k(const cox_handle *h, int k)
 {
     if (k < 1) return COX_ERR_ARG;
-    if (is_split(h) && k > MAX_K_TC) return COX_ERR_ARG;
+    if (is_split(h) && k > max_k_tc(h)) return COX_ERR_ARG;
     if (k > 1024) return COX_ERR_ARG;
     return COX_OK;
 }
@@ -430,16 +432,18 @@ int ensure_workspace(cox_handle *h, int k)
         cudaMemset(ws.gamma, 0, static_cast<size_t>(k) * h->q * sizeof(double));
     }
     if (is_split(h)) {
-        const int NP = limb_cols(k);
-        A(ws.Bq, static_cast<size_t>(NP) * h->p_pad);
-        A(ws.Vq, static_cast<size_t>(NP) * h->n_pad);
+        // limb rows of K_pad e4m3 bytes, or K_pad / 2 bytes of e2m1 pairs
+        const int NP = is_e2m1(h) ? limb_cols4(k) : limb_cols(k);
+        const int64_t bpk = is_e2m1(h) ? 2 : 1;  // K positions per byte
+        A(ws.Bq, static_cast<size_t>(NP) * h->p_pad / bpk);
+        A(ws.Vq, static_cast<size_t>(NP) * h->n_pad / bpk);
         A(ws.bs1, k);
         A(ws.bs4, k);
         A(ws.bmaxp, static_cast<size_t>(k) * h->l1_blocks);
         A(ws.vmaxp, k * nch);
         // limb rows past LIMBS k and K positions of padding stay zero
-        cudaMemset(ws.Bq, 0, static_cast<size_t>(NP) * h->p_pad);
-        cudaMemset(ws.Vq, 0, static_cast<size_t>(NP) * h->n_pad);
+        cudaMemset(ws.Bq, 0, static_cast<size_t>(NP) * h->p_pad / bpk);
+        cudaMemset(ws.Vq, 0, static_cast<size_t>(NP) * h->n_pad / bpk);
         ws.NP = NP;
         cudaMemset(ws.bs1, 0, k * sizeof(int));
         cudaMemset(ws.bs4, 0, k * sizeof(int));
@@ -543,7 +547,8 @@ int cox_setup(cox_h *out, const void *X, int64_t n, int64_t p, int x_format, con
     cox_default_options(&opt);
     if (opt_in) opt = *opt_in;
     if (!X || !time || !event || n < 1 || p < 1 || n > INT32_MAX || p > INT32_MAX) return COX_ERR_ARG;
-    if (opt.precision != COX_SPLIT_E4M3 && opt.precision != COX_FP64 && opt.precision != COX_FP32_GEMV)
+    if (opt.precision != COX_SPLIT_E4M3 && opt.precision != COX_FP64 && opt.precision != COX_FP32_GEMV &&
+        opt.precision != COX_SPLIT_E2M1)
         return COX_ERR_ARG;
     if ((opt.precision == COX_FP64) != (x_format == COX_X_F64_HOST)) return COX_ERR_UNSUPPORTED;
     if (x_format < COX_X_INT8_HOST || x_format > COX_X_PACKED2_DEV) return COX_ERR_ARG;
@@ -710,13 +715,13 @@ int cox_autotune(cox_h h, int k, int reps, cox_tune_choice *xb, cox_tune_choice 
 {
     if (!h) return COX_ERR_ARG;
     if (!is_split(h)) return COX_ERR_UNSUPPORTED;
-    if (k < 1 || k > MAX_K_TC || reps < 1) return COX_ERR_ARG;
+    if (k < 1 || k > max_k_tc(h) || reps < 1) return COX_ERR_ARG;
     DeviceGuard guard(h->dev);
     h->tuned.erase(k);
     COX_TRY(ensure_workspace(h, k));  // limb buffers (zero) and scale arrays for the timing launches
     Workspace &ws = h->ws;
     int Ts[16], Cs[16], As[16];
-    const int nshape = gemm_shapes(k, Ts, Cs, As, 16);
+    const int nshape = gemm_shapes(k, Ts, Cs, As, 16, is_e2m1(h));
     // the planner's depth only: four-stage plans measured 2-3x slower for every
     // shape at full size (the bench's workloads), so they are not timed
     const int depth_req[1] = {0};
@@ -822,9 +827,16 @@ int cox_rank_by_entry(int64_t p, int L, const double *lambdas, const void *B_hos
 
 int cox_plan_shape(int k, int tile_m, int chunks, int stages, int issue, cox_plan *out)
 {
+    return cox_plan_shape_prec(COX_SPLIT_E4M3, k, tile_m, chunks, stages, issue, out);
+}
+
+int cox_plan_shape_prec(int precision, int k, int tile_m, int chunks, int stages, int issue, cox_plan *out)
+{
     if (!out || tile_m < 0 || chunks < 0 || stages < 0 || issue < 0 || issue > 3) return COX_ERR_ARG;
+    if (precision != COX_SPLIT_E4M3 && precision != COX_SPLIT_E2M1) return COX_ERR_ARG;
+    const int f4 = precision == COX_SPLIT_E2M1;
     GemmPlan g;
-    COX_TRY(plan_shape(g, k, tile_m, chunks, stages, issue));
+    COX_TRY(plan_shape(g, k, tile_m, chunks, stages, issue, f4));
     out->tile_m = g.T;
     out->chunks = g.CH;
     out->stages = g.stages;
@@ -832,23 +844,25 @@ int cox_plan_shape(int k, int tile_m, int chunks, int stages, int issue, cox_pla
     out->decoder_groups = g.G;
     out->named_barriers = g.nb_period * g.T;
     out->limb_cols = g.NP;
-    out->tmem_cols = (g.alt ? 2 : 1) * g.T * g.NP + g.ring * g.T * g.CH * 32;
+    out->tmem_cols = (g.alt ? 2 : 1) * g.T * g.NP + g.ring * g.T * g.CH * (f4 ? 16 : 32) + (f4 ? 8 : 0);
     out->smem_bytes = static_cast<long long>(g.smem);
     out->issue = g.alt ? 2 : g.pair ? 3 : 1;
     out->issuers = g.alt ? 2 : g.T;
-    out->mmas_per_commit = 4 * g.CH * (g.alt ? g.T : g.pair ? 2 : 1);
+    out->mmas_per_commit = (f4 ? 2 : 4) * g.CH * (g.alt ? g.T : g.pair ? 2 : 1);
     return COX_OK;
 }
 
 int cox_set_precision(cox_h h, int precision)
 {
     if (!h) return COX_ERR_ARG;
-    if (h->opt.precision == COX_FP64 || (precision != COX_SPLIT_E4M3 && precision != COX_FP32_GEMV))
+    if (h->opt.precision == COX_FP64 ||
+        (precision != COX_SPLIT_E4M3 && precision != COX_FP32_GEMV && precision != COX_SPLIT_E2M1))
         return COX_ERR_UNSUPPORTED;
     if (precision == h->opt.precision) return COX_OK;
     DeviceGuard g(h->dev);
     cudaDeviceSynchronize();
     free_workspace(h);
+    h->tuned.clear();  // tuned shapes belong to one operand form
     h->opt.precision = precision;
     return COX_OK;
 }

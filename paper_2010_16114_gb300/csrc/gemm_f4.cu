@@ -1,0 +1,26 @@
+// gemm_f4.cu -- the e2m1 instantiations of the genotype-product kernel
+// (gemm_kernel.cuh): codes as e2m1 nibbles, coefficients as LIMBS4 e2m1 limbs,
+// tcgen05.mma kind::mxf4 with unit block scales (K = 64 per instruction).  In a
+// translation unit of their own so that the two forms compile in parallel.
+#include "gemm_kernel.cuh"
+
+namespace coxgb {
+
+// (T row tiles, CH K chunks, NP limb columns) -> kernel, or null when that
+// shape is not compiled.  TMEM (504 columns beside the scale factors): T NP
+// accumulator columns and at least G slots of T CH 16 columns.  The limb
+// classes stop at 96 columns (k <= 16): MMAs of N <= 128 read B scale factors
+// that lie inside the eight scale-factor columns; a 192-column class faulted
+// on the GPU in its first parity test, and is not compiled.
+GemmKernelFn pick_kernel_f4(int T, int CH, int NP)
+{
+    switch ((T * 10 + CH) * 1000 + NP) {
+    case 22048: return k_packed_gemm<2, 2, 48, DEC_GROUPS, false, true>;
+    case 24048: return k_packed_gemm<2, 4, 48, DEC_GROUPS, false, true>;
+    case 22096: return k_packed_gemm<2, 2, 96, DEC_GROUPS, false, true>;
+    case 14096: return k_packed_gemm<1, 4, 96, DEC_GROUPS, false, true>;
+    default: return nullptr;
+    }
+}
+
+} // namespace coxgb

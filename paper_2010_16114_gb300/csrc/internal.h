@@ -22,12 +22,23 @@ constexpr int SCAN_CH = 2048;      // subjects per scan chunk (256 threads x 8)
 constexpr int MAX_K_TC = 64;       // largest k of the tensor-core path
 constexpr int LIMBS = 4;           // e4m3 limbs per coefficient (4 significant bits each)
 constexpr int DEC_GROUPS = 3;      // decoder warp groups of the tensor-core products
+constexpr int LIMBS4 = 6;          // e2m1 limbs per coefficient (3 significant bits each)
+constexpr int SF_COL = 504;        // TMEM columns 504..511: unit block scales of the e2m1 products
 
 // Limb columns of a k-column product: LIMBS k rounded up to an MMA width class.
 inline int limb_cols(int k)
 {
     const int n = LIMBS * k;
     return n <= 16 ? 16 : n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : 256;
+}
+
+// Limb columns of the e2m1 form: LIMBS4 k rounded up to 48 or 96 (k <= MAX_K_E2M1),
+// multiples of 24 (four coefficient columns per fold step); 0 beyond.
+constexpr int MAX_K_E2M1 = 16;
+inline int limb_cols4(int k)
+{
+    const int n = LIMBS4 * k;
+    return n <= 48 ? 48 : n <= 96 ? 96 : 0;
 }
 
 // Position of code K (0..15) of a 16-code word: bit 8 (K mod 4) + 2 (K div 4),
@@ -100,6 +111,39 @@ __device__ inline int split_e4m3_units(float r, uint8_t *d)
     return q;
 }
 
+// ---- e2m1 limbs -----------------------------------------------------------------
+// A coefficient column b is held as LIMBS4 e2m1 numbers on the grid of halves in
+// [-2, 2]: with a power-of-two scale 2^s putting max |b| 2^-s in [1, 2),
+// r_0 = b 2^-s, d_l = RN(2 r_l) / 2, r_(l+1) = 8 (r_l - d_l) (exact; |r| <= 2),
+// and b = 2^s sum_l d_l 8^-l to within 2^(1 - 3 LIMBS4) of max |b|.
+// Limb rows hold two K positions per byte, in the order the decoders give the
+// codes (decode16_e2m1): positions K and K + 8 of a 16-code group w share byte
+// 8 w + (K mod 8), K in the low nibble.
+__host__ __device__ inline int64_t e2m1_byte(int64_t K) { return ((K >> 4) << 3) + (K & 7); }
+
+__device__ inline int limb_scale4(float mx) { return mx > 0.f ? ilogbf(mx) : 0; }
+
+// Limbs of r (|r| < 2) as e2m1 nibbles; returns the value they represent in
+// units of 2^(-1 - 3 (LIMBS4 - 1)), an exact integer.  Non-finite r gives zero
+// limbs (its caller flags it).
+__device__ inline int split_e2m1_units(float r, uint8_t *nib)
+{
+    if (!isfinite(r)) {
+        for (int l = 0; l < LIMBS4; ++l) nib[l] = 0;
+        return 0;
+    }
+    int q = 0;
+#pragma unroll
+    for (int l = 0; l < LIMBS4; ++l) {
+        const float t = rintf(2.f * r);  // -4 .. 4
+        const int ti = static_cast<int>(t);
+        nib[l] = static_cast<uint8_t>((ti < 0 ? 8 : 0) | (ti < 0 ? -ti : ti));
+        q = 8 * q + ti;
+        r = fmaf(-4.f, t, 8.f * r);  // 8 (r - t / 2), exact
+    }
+    return q;
+}
+
 // 32-bit word index, in a tiled 2-bit layout of KC chunks per row tile, of the
 // 16 codes of row rit (0..127) of row tile mt at K offset `within` (a multiple
 // of 16) of chunk kc: row records of 32 bytes, two 16-byte halves (K 0-63 and
@@ -130,7 +174,8 @@ struct GemmPlan {
     int alt = 0;       // 1: two issuers on alternate stages (else one per row tile)
     int pair = 0;      // 1: per-tile issuers commit after every second stage
     int G = 3;         // decoder groups
-    int NP = 16;       // limb columns (limb_cols(k))
+    int NP = 16;       // limb columns (limb_cols(k), or limb_cols4(k) in the e2m1 form)
+    int f4 = 0;        // 1: e2m1 operands (kind::mxf4), else e4m3 (kind::f8f6f4)
     int stages = 6;    // shared-memory pipeline depth
     int ring = 4;      // TMEM A buffers
     int nb_period = 6; // stage period of the named barriers: lcm(decoder groups, ring)
@@ -258,6 +303,9 @@ struct cox_handle {
     size_t ev_used = 0;
 };
 
+// The e2m1 form of the tensor-core products (COX_SPLIT_E2M1).
+inline bool is_e2m1(const cox_handle *h) { return h->opt.precision == COX_SPLIT_E2M1; }
+
 namespace coxgb {
 
 // ---- error helpers ----------------------------------------------------------
@@ -322,12 +370,12 @@ int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st);
 // not compiled for k or a depth the pipeline does not allow.
 // issue_req: 0 default, 1 one issuer per row tile, 2 two issuers on alternate
 // stages, 3 one issuer per row tile committing after every second stage.
-int plan_shape(GemmPlan &g, int k, int T_req, int CH_req, int stages_req, int issue_req);
+int plan_shape(GemmPlan &g, int k, int T_req, int CH_req, int stages_req, int issue_req, int f4);
 int plan_gemm(cox_handle *h, GemmPlan &g, const uint32_t *A, int64_t rows_pad, int64_t K_pad,
               const uint8_t *B, int k, int T_req, int CH_req, int stages_req, int issue_req);
 // The compiled (row tiles, K chunks, issue mode) shapes for k columns; returns
 // their count.
-int gemm_shapes(int k, int *T, int *CH, int *issue, int max);
+int gemm_shapes(int k, int *T, int *CH, int *issue, int max, int f4);
 enum Epi { EPI_PARTIAL = 0, EPI_PROX = 1, EPI_GRAD = 2 };
 struct EpiArgs {
     int epi = EPI_PARTIAL;

@@ -258,7 +258,7 @@ int path_run(cox_handle *h, int k, int max_iter, double tol, double step, void *
         if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) { rc = COX_ERR_CUDA; break; }
         // the active-set product decides on the host before each iteration, so
         // those iterations run as plain launches instead of graph replays
-        if (max_iter - t >= lag && !(h->opt.active_set && h->opt.precision == COX_SPLIT_E4M3)) {
+        if (max_iter - t >= lag && !(h->opt.active_set && (h->opt.precision == COX_SPLIT_E4M3 || is_e2m1(h)))) {
             if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = COX_ERR_CUDA; break; }
             for (int s = 0; s < lag && rc == COX_OK; ++s) rc = one_step(s);
             cudaError_t ec = cudaStreamEndCapture(cs, &graph);
@@ -339,7 +339,7 @@ int cox_path_fit(cox_h h, const double *lambdas, int k, int max_iter, double tol
 {
     if (!h || !beta_dev || !lambdas || max_iter < 0 || !(tol >= 0.0) || !(step > 0.0) || warm < 0 || warm > 2)
         return COX_ERR_ARG;
-    if (k < 1 || (h->opt.precision == COX_SPLIT_E4M3 && k > MAX_K_TC)) return COX_ERR_ARG;
+    if (k < 1 || (h->opt.precision == COX_SPLIT_E4M3 && k > MAX_K_TC) || (is_e2m1(h) && k > MAX_K_E2M1)) return COX_ERR_ARG;
     COX_TRY(check_lambdas(lambdas, k));
     DeviceGuard g(h->dev);
     cudaStream_t user = static_cast<cudaStream_t>(stream);

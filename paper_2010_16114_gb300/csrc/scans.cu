@@ -399,6 +399,58 @@ __global__ void k_vlimbs(SP s, uint8_t *__restrict__ Vq, int64_t n_pad, const do
     if (threadIdx.x == 0) s.vsp[kk * s.nch + c] = ldexp(t, sc - 21);
 }
 
+// (4b, e2m1 form) V -> e2m1 limbs at the A4 K positions: thread e of a chunk
+// takes subjects 16 (e / 8) + e mod 8 and that + 8 of the chunk, which share
+// one byte per limb row (e2m1_byte); chunk sums of the values the limbs hold,
+// exact (integers of 2^(sc-16) units, below 2^29 per chunk).
+__global__ void k_vlimbs4(SP s, uint8_t *__restrict__ Vq, int64_t n_pad, const double *__restrict__ vmaxp,
+                          int *__restrict__ bs, int *err)
+{
+    __shared__ double sh[NT / 32];
+    __shared__ int s_sh;
+    const int c = blockIdx.x, kk = blockIdx.y;
+    double m = 0.0;
+    for (int q = threadIdx.x; q < s.nch; q += NT) m = fmax(m, vmaxp[kk * s.nch + q]);
+    m = block_max(m, sh);
+    if (threadIdx.x == 0) {
+        float mf = static_cast<float>(m);
+        if (!isfinite(mf)) {
+            atomicOr(err, DEVERR_NONFINITE);
+            mf = 0.f;
+        }
+        s_sh = limb_scale4(mf);
+        if (c == 0) bs[kk] = s_sh;
+    }
+    __syncthreads();
+    const int sc = s_sh;
+    const int64_t i0 = static_cast<int64_t>(c) * SCAN_CH;
+    const float *V32 = reinterpret_cast<const float *>(s.Rt);
+    const int64_t rb = n_pad / 2;
+    long long q = 0;
+    bool finite = true;
+    for (int e = threadIdx.x; e < SCAN_CH / 2; e += NT) {
+        const int64_t ia = i0 + ((e >> 3) << 4) + (e & 7);
+        if (ia >= s.n) break;
+        uint8_t d0[LIMBS4], d1[LIMBS4];
+        const float ra = ldexpf(V32[kk * s.n + ia], -sc);
+        finite = finite && isfinite(ra);
+        q += split_e2m1_units(ra, d0);
+        if (ia + 8 < s.n) {
+            const float rb8 = ldexpf(V32[kk * s.n + ia + 8], -sc);
+            finite = finite && isfinite(rb8);
+            q += split_e2m1_units(rb8, d1);
+        } else {
+#pragma unroll
+            for (int l = 0; l < LIMBS4; ++l) d1[l] = 0;
+        }
+        const int64_t byte = e2m1_byte(a4_pos(ia, s.pa, s.pnb));
+#pragma unroll
+        for (int l = 0; l < LIMBS4; ++l) Vq[(LIMBS4 * kk + l) * rb + byte] = static_cast<uint8_t>(d0[l] | (d1[l] << 4));
+    }
+    const double t = block_sum(finite ? static_cast<double>(q) : NAN, sh);
+    if (threadIdx.x == 0) s.vsp[kk * s.nch + c] = ldexp(t, sc - 16);
+}
+
 // (5) per column (one warp each): sum V, f, ||beta||_1, F = f + lambda ||beta||_1;
 // flag non-finite.
 __device__ __forceinline__ double warp_sum(double x)
@@ -505,7 +557,10 @@ int run_scans(cox_handle *h, const ScanArgs &a, cudaStream_t st)
     switch (a.v_out) {
     case V_LIMBS_E4M3:
         k_uv<V_LIMBS_E4M3><<<grid, NT, 0, st>>>(s, a.V, h->n_pad, ws.vmaxp);
-        k_vlimbs<<<grid, NT, 0, st>>>(s, static_cast<uint8_t *>(a.V), h->n_pad, ws.vmaxp, ws.bs4, h->d_err);
+        if (ws.g4.f4)
+            k_vlimbs4<<<grid, NT, 0, st>>>(s, static_cast<uint8_t *>(a.V), h->n_pad, ws.vmaxp, ws.bs4, h->d_err);
+        else
+            k_vlimbs<<<grid, NT, 0, st>>>(s, static_cast<uint8_t *>(a.V), h->n_pad, ws.vmaxp, ws.bs4, h->d_err);
         break;
     case V_DENSE_F64: k_uv<V_DENSE_F64><<<grid, NT, 0, st>>>(s, a.V, h->n_pad, nullptr); break;
     default: k_uv<V_DENSE_F32><<<grid, NT, 0, st>>>(s, a.V, h->n_pad, nullptr); break;

@@ -17,7 +17,8 @@ columns where the oracle streams X, over 2048 seeded columns elsewhere).
 * geno_200k_10k (n=200,000, p=10,000, k=1): two whole iterations and the
   autograd backward at full size.
 * geno_400k_100k_k32 (50 iterations, 32 penalties) and geno_400k_500k_k16
-  (3 iterations, 16 penalties): the oracle cannot run whole iterations at
+  (3 iterations, 16 penalties; in both operand forms of the tensor-core
+  products, e4m3 and e2m1): the oracle cannot run whole iterations at
   these sizes, so the checks sit at the nonzero beta the GPU reached.  At it
   the oracle computes eta at 64 sampled subjects for every column (the first
   product over all p SNPs), and, for up to 4 columns whose support it can
@@ -211,14 +212,17 @@ def _check_at_gpu_beta(w, prob, beta, lams, sigma, rank, max_support=4000, ncols
     return cand
 
 
-@pytest.mark.parametrize("name,iters", [("geno_400k_100k_k32", 50), ("geno_400k_500k_k16", 3)])
-def test_full_size_sampled(name, iters):
-    w, prob = _device_problem(name)
+@pytest.mark.parametrize("name,iters,precision", [("geno_400k_100k_k32", 50, "split_e4m3"),
+                                                   ("geno_400k_500k_k16", 3, "split_e4m3"),
+                                                   ("geno_400k_500k_k16", 3, "split_e2m1")])
+def test_full_size_sampled(name, iters, precision):
+    w, prob = _device_problem(name, precision=precision)
     try:
         r = w.r
         # the launch configuration bench.py times: the autotuner's shapes for k columns
         tune = prob.autotune(r.k, reps=1)
-        assert tune["x_b"]["candidates"] >= 3 and tune["xt_v"]["candidates"] >= 3
+        want = 3 if precision == "split_e4m3" else 2  # compiled shapes of the k-column class
+        assert tune["x_b"]["candidates"] >= want and tune["xt_v"]["candidates"] >= want
         n, p = w.n, w.p
         sigma = _step(n, p)
         rank = _ranks(w.y)
