@@ -153,7 +153,7 @@ __global__ void k_prep_limbs_active4(const float *__restrict__ beta, int64_t p, 
     for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < rb;
          t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int64_t t0 = ((t >> 3) << 4) + (t & 7);
-        uint8_t d0[LIMBS4] = {0, 0, 0, 0, 0, 0}, d1[LIMBS4] = {0, 0, 0, 0, 0, 0};
+        uint8_t d0[LIMBS4] = {}, d1[LIMBS4] = {};
         if (t0 < nA) split_e2m1_units(ldexpf(beta[static_cast<int64_t>(kk) * p + Aidx[t0]], -s), d0);
         if (t0 + 8 < nA) split_e2m1_units(ldexpf(beta[static_cast<int64_t>(kk) * p + Aidx[t0 + 8]], -s), d1);
 #pragma unroll

@@ -9,16 +9,16 @@ namespace coxgb {
 // (T row tiles, CH K chunks, NP limb columns) -> kernel, or null when that
 // shape is not compiled.  TMEM (504 columns beside the scale factors): T NP
 // accumulator columns and at least G slots of T CH 16 columns.  The limb
-// classes stop at 96 columns (k <= 16): MMAs of N <= 128 read B scale factors
-// that lie inside the eight scale-factor columns; a 192-column class faulted
-// on the GPU in its first parity test, and is not compiled.
+// classes stop at 128 columns (k <= 16): a class of N = 192 (six limbs at
+// k = 32) faulted on the GPU in its first parity test, and no MMA of N > 128
+// is compiled.
 GemmKernelFn pick_kernel_f4(int T, int CH, int NP)
 {
     switch ((T * 10 + CH) * 1000 + NP) {
-    case 22048: return k_packed_gemm<2, 2, 48, DEC_GROUPS, false, true>;
-    case 24048: return k_packed_gemm<2, 4, 48, DEC_GROUPS, false, true>;
-    case 22096: return k_packed_gemm<2, 2, 96, DEC_GROUPS, false, true>;
-    case 14096: return k_packed_gemm<1, 4, 96, DEC_GROUPS, false, true>;
+    case 22064: return k_packed_gemm<2, 2, 64, DEC_GROUPS, false, true>;
+    case 14064: return k_packed_gemm<1, 4, 64, DEC_GROUPS, false, true>;
+    case 22128: return k_packed_gemm<2, 2, 128, DEC_GROUPS, false, true>;
+    case 14128: return k_packed_gemm<1, 4, 128, DEC_GROUPS, false, true>;
     default: return nullptr;
     }
 }

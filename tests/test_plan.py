@@ -201,16 +201,16 @@ SHAPES4 = [(2, 2), (2, 4), (1, 2), (1, 4)]
 
 
 def _limb_cols4(k):
-    n = 6 * k
-    return next(c for c in (48, 96) if n <= c)
+    n = 8 * k
+    return next(c for c in (64, 128) if n <= c)
 
 
 def _check4(k, p):
-    """e2m1 plans: six limbs per coefficient in 48 or 96 columns (four
-    coefficient columns per 24-column fold step); per-tile issuers, two MMAs (K =
-    64) per K chunk; 16 TMEM columns per tile and chunk beside 8 columns of scale
-    factors; the parity rule as for the e4m3 form."""
-    assert p.limb_cols == _limb_cols4(k) and p.limb_cols % 24 == 0
+    """e2m1 plans: eight limbs per coefficient in 64 or 128 columns;
+    per-tile issuers, two MMAs (K = 64) per K chunk; 16 TMEM columns per tile
+    and chunk beside 8 columns of scale factors; the parity rule as for the e4m3
+    form."""
+    assert p.limb_cols == _limb_cols4(k)
     assert p.issue == 1 and p.issuers == p.tile_m and p.mmas_per_commit == 2 * p.chunks
     assert p.decoder_groups == 3 and p.chunks % 2 == 0
     assert p.ring >= p.decoder_groups and p.ring < p.stages
@@ -243,19 +243,19 @@ def test_e2m1_every_shape_and_depth_keeps_the_invariants(k):
 
 def test_e2m1_default_shapes_and_rejections():
     # two row tiles x two K chunks (k <= 16)
-    for k, want in ((1, (2, 2, 48)), (8, (2, 2, 48)), (9, (2, 2, 96)), (16, (2, 2, 96))):
+    for k, want in ((1, (2, 2, 64)), (8, (2, 2, 64)), (9, (2, 2, 128)), (16, (2, 2, 128))):
         rc, p = L.cox_plan_shape_prec(L.COX_SPLIT_E2M1, k, 0, 0, 0, 0)
         assert rc == 0
         _check4(k, p)
         assert (p.tile_m, p.chunks, p.limb_cols) == want
     E = L.COX_SPLIT_E2M1
-    assert L.cox_plan_shape_prec(E, 17)[0] == L.COX_ERR_ARG          # 96 columns hold 16 coefficients
+    assert L.cox_plan_shape_prec(E, 17)[0] == L.COX_ERR_ARG          # 128 columns hold 16 coefficients
     assert L.cox_plan_shape_prec(E, 32)[0] == L.COX_ERR_ARG
     assert L.cox_plan_shape_prec(E, 16, 2, 1)[0] == L.COX_ERR_ARG    # chunk pairs only
     assert L.cox_plan_shape_prec(E, 16, 2, 3)[0] == L.COX_ERR_ARG
     assert L.cox_plan_shape_prec(E, 16, 2, 2, 0, 2)[0] == L.COX_ERR_ARG  # per-tile issuers only
     assert L.cox_plan_shape_prec(E, 16, 2, 2, 0, 3)[0] == L.COX_ERR_ARG
-    assert L.cox_plan_shape_prec(E, 16, 2, 4)[0] == L.COX_ERR_ARG    # 2 x 4 at 96 columns: no safe ring fits
+    assert L.cox_plan_shape_prec(E, 16, 2, 4)[0] == L.COX_ERR_ARG    # 2 x 4: not compiled
     assert L.cox_plan_shape_prec(7, 16)[0] == L.COX_ERR_ARG          # not a tensor-core form
     # the e4m3 entry point is the e4m3 form of the general one
     for k in (1, 16, 64):
