@@ -98,7 +98,8 @@ typedef struct cox_options {
     double wait_limit_s;  /* device-side wait limit in seconds (default 2.0)         */
     int chunks;           /* 128-wide K chunks per pipeline stage (1 or 2; 3 with
                              two row tiles at 64 limb columns, k = 9..16, where
-                             the product's chunk count divides by 3);
+                             the product's chunk count divides by 3; COX_SPLIT_E2M1:
+                             2, or 4 with one row tile);
                              0 = automatic, as tile_m                               */
     int window;           /* K chunks a TMEM accumulator sums in FP32 before decoder
                              warps add it into FP32 sums (>= chunks; 0 = 256)       */

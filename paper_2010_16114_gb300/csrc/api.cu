@@ -553,7 +553,7 @@ int cox_setup(cox_h *out, const void *X, int64_t n, int64_t p, int x_format, con
     if ((opt.precision == COX_FP64) != (x_format == COX_X_F64_HOST)) return COX_ERR_UNSUPPORTED;
     if (x_format < COX_X_INT8_HOST || x_format > COX_X_PACKED2_DEV) return COX_ERR_ARG;
     if (opt.lag < 1 || !(opt.wait_limit_s >= 0.0)) return COX_ERR_ARG;
-    if (opt.tile_m < 0 || opt.tile_m > 2 || opt.chunks < 0 || opt.chunks > 3 || opt.stages < 0 || opt.window < 0 ||
+    if (opt.tile_m < 0 || opt.tile_m > 2 || opt.chunks < 0 || opt.chunks > 4 || opt.stages < 0 || opt.window < 0 ||
         opt.issue < 0 || opt.issue > 3 || opt.active_set < 0 || opt.active_set > 1)
         return COX_ERR_ARG;
     for (int64_t i = 0; i < n; ++i) {
