@@ -97,7 +97,9 @@ struct DeviceGuard {
 
 bool is_split(const cox_handle *h) { return h->opt.precision == COX_SPLIT_E4M3 || is_e2m1(h); }
 bool is_fp64(const cox_handle *h) { return h->opt.precision == COX_FP64; }
-// largest k of the tensor-core products: 96 e2m1 limb columns hold 16 coefficients
+// tuned shapes are kept per operand form and k (switching forms keeps both)
+int tune_key(const cox_handle *h, int k) { return is_e2m1(h) ? k + 4096 : k; }
+// largest k of the tensor-core products: 128 e2m1 limb columns hold 16 coefficients
 int max_k_tc(const cox_handle *h) { return is_e2m1(h) ? MAX_K_E2M1 : MAX_K_TC; }
 
 cudaEvent_t get_event(cox_handle *h)
@@ -450,7 +452,7 @@ int ensure_workspace(cox_handle *h, int k)
         // pipeline shapes: forced by the options, else autotuned for k, else default
         int T1 = h->opt.tile_m, C1 = h->opt.chunks, S1 = h->opt.stages, A1 = h->opt.issue;
         int T4 = T1, C4 = C1, S4 = S1, A4 = A1;
-        const auto tc = h->tuned.find(k);
+        const auto tc = h->tuned.find(tune_key(h, k));
         if (tc != h->tuned.end() && !T1 && !C1 && !S1 && !A1) {
             T1 = tc->second.T1, C1 = tc->second.CH1, S1 = tc->second.S1, A1 = tc->second.A1;
             T4 = tc->second.T4, C4 = tc->second.CH4, S4 = tc->second.S4, A4 = tc->second.A4;
@@ -717,7 +719,7 @@ int cox_autotune(cox_h h, int k, int reps, cox_tune_choice *xb, cox_tune_choice 
     if (!is_split(h)) return COX_ERR_UNSUPPORTED;
     if (k < 1 || k > max_k_tc(h) || reps < 1) return COX_ERR_ARG;
     DeviceGuard guard(h->dev);
-    h->tuned.erase(k);
+    h->tuned.erase(tune_key(h, k));
     COX_TRY(ensure_workspace(h, k));  // limb buffers (zero) and scale arrays for the timing launches
     Workspace &ws = h->ws;
     int Ts[16], Cs[16], As[16];
@@ -781,7 +783,7 @@ int cox_autotune(cox_h h, int k, int reps, cox_tune_choice *xb, cox_tune_choice 
     cudaEventDestroy(e1);
     if (rc != COX_OK) return rc;
     if (!cand[0] || !cand[1]) return COX_ERR_ARG;
-    h->tuned[k] = cox_handle::TuneChoice{best[0].tile_m, best[0].chunks, best[0].stages, best[0].issue,
+    h->tuned[tune_key(h, k)] = cox_handle::TuneChoice{best[0].tile_m, best[0].chunks, best[0].stages, best[0].issue,
                                          best[1].tile_m, best[1].chunks, best[1].stages, best[1].issue};
     cudaDeviceSynchronize();
     free_workspace(h);  // the next call with k columns plans the chosen shapes
@@ -862,7 +864,6 @@ int cox_set_precision(cox_h h, int precision)
     DeviceGuard g(h->dev);
     cudaDeviceSynchronize();
     free_workspace(h);
-    h->tuned.clear();  // tuned shapes belong to one operand form
     h->opt.precision = precision;
     return COX_OK;
 }
