@@ -485,7 +485,7 @@ def run_ours(args, rank, world):
 
     # algorithmic bytes (packed X padded to 128 per dimension, as streamed by each product)
     xb = (-(-n // 128) * 128) * (-(-p // 128) * 128) / 4.0
-    lb = 3.5 if args.precision == "split_e2m1" else 4  # limb bytes per coefficient: 7 e2m1 nibbles or 4 e4m3
+    lb = 4  # limb bytes per coefficient: 8 e2m1 nibbles or 4 e4m3 bytes
     b1 = xb + p * lb * k + k * n * 4              # X, beta limbs, eta partials
     b4 = xb + n * lb * k + 8 * k * p              # X, V limbs, beta read+write
     scan_bytes = k * n * 8 * 12                     # FP64 scan passes (eta, w, R, F, gathers, V)
@@ -613,7 +613,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "e2m1" if args.precision == "split_e2m1" else "e4m3", "data": "synthetic",
-        "precision": ("genotype products: codes and 7-limb split coefficients as e2m1 on tcgen05 "
+        "precision": ("genotype products: codes and 8-limb split coefficients as e2m1 on tcgen05 "
                       "(kind::mxf4, unit block scales), FP32 accumulation; risk-set scans and objective FP64"
                       if args.precision == "split_e2m1" else
                       "genotype products: codes and 4-limb split coefficients as e4m3 on tcgen05 "

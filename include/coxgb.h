@@ -79,9 +79,9 @@ enum {
                            on the packed genotypes, unfused soft threshold    */
     COX_SPLIT_E2M1 = 3  /* tcgen05 tensor cores (kind::mxf4, unit block scales):
                            genotype codes as e2m1 (two per byte, K = 64 per
-                           MMA), coefficients split into 7 e2m1 limbs on the
+                           MMA), coefficients split into 8 e2m1 limbs on the
                            grid of halves under a power-of-two column scale
-                           (within 2^-20 of the column's largest magnitude),
+                           (within 2^-23 of the column's largest magnitude),
                            FP32 accumulation; FP64 risk-set scans; k <= 16  */
 };
 

@@ -157,7 +157,7 @@ __global__ void k_prep_limbs_active4(const float *__restrict__ beta, int64_t p, 
         if (t0 < nA) split_e2m1_units(ldexpf(beta[static_cast<int64_t>(kk) * p + Aidx[t0]], -s), d0);
         if (t0 + 8 < nA) split_e2m1_units(ldexpf(beta[static_cast<int64_t>(kk) * p + Aidx[t0 + 8]], -s), d1);
 #pragma unroll
-        for (int l = 0; l < LIMBS4; ++l) Bq[e2m1_row(kk, l) * rb + t] = static_cast<uint8_t>(d0[l] | (d1[l] << 4));
+        for (int l = 0; l < LIMBS4; ++l) Bq[(LIMBS4 * kk + l) * rb + t] = static_cast<uint8_t>(d0[l] | (d1[l] << 4));
     }
 }
 

@@ -8,15 +8,17 @@ namespace coxgb {
 
 // (T row tiles, CH K chunks, NP limb columns) -> kernel, or null when that
 // shape is not compiled.  TMEM (504 columns beside the scale factors): T NP
-// accumulator columns and at least G slots of T CH 16 columns.  One limb
-// class, 112 columns (k <= 16): a class of N = 192 (six limbs at k = 32)
-// faulted on the GPU in its first parity test, and no MMA of N > 128 is
-// compiled.
+// accumulator columns and at least G slots of T CH 16 columns.  The limb
+// classes stop at 128 columns (k <= 16): a class of N = 192 (six limbs at
+// k = 32) faulted on the GPU in its first parity test, and no MMA of N > 128
+// is compiled.
 GemmKernelFn pick_kernel_f4(int T, int CH, int NP)
 {
     switch ((T * 10 + CH) * 1000 + NP) {
-    case 22112: return k_packed_gemm<2, 2, 112, DEC_GROUPS, false, true>;
-    case 14112: return k_packed_gemm<1, 4, 112, DEC_GROUPS, false, true>;
+    case 22064: return k_packed_gemm<2, 2, 64, DEC_GROUPS, false, true>;
+    case 14064: return k_packed_gemm<1, 4, 64, DEC_GROUPS, false, true>;
+    case 22128: return k_packed_gemm<2, 2, 128, DEC_GROUPS, false, true>;
+    case 14128: return k_packed_gemm<1, 4, 128, DEC_GROUPS, false, true>;
     default: return nullptr;
     }
 }

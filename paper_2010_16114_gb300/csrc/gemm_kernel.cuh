@@ -28,11 +28,10 @@
 // covers twice the K of an e4m3 one at the same issue cost and a K chunk
 // takes 16 TMEM columns per lane instead of 32.  decode16_e2m1 turns a packed
 // word into two TMEM words with one shift and one AND each; the limb rows hold
-// their K positions in the same order (e2m1_byte).  Coefficients are LIMBS4 = 7
+// their K positions in the same order (e2m1_byte).  Coefficients are LIMBS4 = 8
 // e2m1 limbs on the grid of halves (r_0 = b 2^-s in [-2, 2), d_l = RN(2 r_l)/2,
-// r_(l+1) = 8 (r_l - d_l)), b = 2^s sum_l d_l 8^-l to within 2^-20 of the
-// column's largest |b|, in limb-major rows (limb l of column c in row
-// 16 l + c, N = 112); the fold weights are 8^-l and the scale 2^s.  The
+// r_(l+1) = 8 (r_l - d_l)), b = 2^s sum_l d_l 8^-l to within 2^-23 of the
+// column's largest |b|; the fold weights are 8^-l and the scale 2^s.  The
 // block scales are all 1 (ue8m0 127 in every byte of TMEM columns SF_COL ..
 // SF_COL + 7, written once per launch), so the scale-factor layout never
 // matters.  A limb panel of 128-byte rows covers two K chunks, so the e2m1
@@ -208,9 +207,10 @@ __global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
 {
     constexpr int I = ALT ? 2 : T;        // MMA issuers: one per row tile, or two on alternate stages
     static_assert(!ALT || G == 2, "alternating issuers pair with two decoder groups");
-    static_assert(!F4 || (!ALT && CH % 2 == 0 && NP == LIMBS4 * KH4 && KH4 % 8 == 0),
-                  "e2m1 operands: per-tile issuers, chunk pairs, limb-major columns");
-    constexpr int KH = F4 ? KH4 : NP / LIMBS;  // lambda columns a decoder thread folds (>= k)
+    static_assert(!F4 || (!ALT && CH % 2 == 0 && NP % 8 == 0 && LIMBS4 == 8),
+                  "e2m1 operands: per-tile issuers, chunk pairs, one coefficient per 8 columns");
+    constexpr int NL = F4 ? LIMBS4 : LIMBS;  // limbs per coefficient column
+    constexpr int KH = NP / NL;           // lambda columns a decoder thread folds (>= k)
     // B: one panel of NP rows x 128 bytes per K chunk (e4m3), or per two K
     // chunks (e2m1, two values per byte)
     constexpr int B_BYTES = (F4 ? CH / 2 : CH) * NP * 128;
@@ -531,24 +531,18 @@ __global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
             fold_phase ^= 1u;
             tc_fence_after();
             if constexpr (F4) {
-                // eight lambda columns at a time, their limbs (weights 8^-l) from the
-                // last to the first: limb l of columns c0 .. c0+7 is one 8-column load
+                // one lambda column of eight e2m1 limbs (weights 8^-l) per 8 columns
 #pragma unroll
                 for (int tt = 0; tt < T; ++tt) {
 #pragma unroll
-                    for (int c0 = 0; c0 < KH4; c0 += 8) {
-                        float x[8];
+                    for (int cc = 0; cc < NP / 8; ++cc) {
+                        uint32_t u[8];
+                        tmem_ld_32x32b_x8(lane_base + static_cast<uint32_t>(tt * NP + cc * 8), u);
+                        tmem_wait_ld();
+                        float x = __uint_as_float(u[7]);
 #pragma unroll
-                        for (int l = LIMBS4 - 1; l >= 0; --l) {
-                            uint32_t u[8];
-                            tmem_ld_32x32b_x8(lane_base + static_cast<uint32_t>(tt * NP + e2m1_row(c0, l)), u);
-                            tmem_wait_ld();
-#pragma unroll
-                            for (int j = 0; j < 8; ++j)
-                                x[j] = l == LIMBS4 - 1 ? __uint_as_float(u[j]) : fmaf(x[j], 0.125f, __uint_as_float(u[j]));
-                        }
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) acc(tt, c0 + j) += x[j];
+                        for (int l = 6; l >= 0; --l) x = fmaf(x, 0.125f, __uint_as_float(u[l]));
+                        acc(tt, cc) += x;
                     }
                 }
             } else {

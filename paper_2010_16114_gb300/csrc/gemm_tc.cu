@@ -76,7 +76,7 @@ __global__ void k_prep_limbs_beta4(const float *__restrict__ beta, int64_t p, in
         else
             for (int l = 0; l < LIMBS4; ++l) d1[l] = 0;
 #pragma unroll
-        for (int l = 0; l < LIMBS4; ++l) Bq[e2m1_row(kk, l) * rb + j] = static_cast<uint8_t>(d0[l] | (d1[l] << 4));
+        for (int l = 0; l < LIMBS4; ++l) Bq[(LIMBS4 * kk + l) * rb + j] = static_cast<uint8_t>(d0[l] | (d1[l] << 4));
     }
 }
 
@@ -216,7 +216,7 @@ int plan_shape(GemmPlan &g, int k, int T_req, int CH_req, int stages_req, int is
     if (G == G_WIDE && !alt && issue_req == 3) return COX_ERR_ARG;  // pair commits: not planned for it
     // limb panels of 128-byte rows: one per K chunk (e4m3), one per chunk pair (e2m1)
     const int stage = (f4 ? CH / 2 : CH) * np_cls * 128 + CH * T * BLOCK_BYTES;
-    const int kh = f4 ? KH4 : np_cls / LIMBS;  // coefficient columns the fold holds
+    const int kh = np_cls / (f4 ? LIMBS4 : LIMBS);  // coefficient columns the fold holds
     // group 0's window sums, then four per-column constants
     const int fold_bytes = T * kh * 128 * 4 + 4 * kh * 4;
     int S = stages_req > 0 ? stages_req : (225 * 1024 - 2048 - fold_bytes) / stage;

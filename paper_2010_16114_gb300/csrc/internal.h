@@ -22,8 +22,7 @@ constexpr int SCAN_CH = 2048;      // subjects per scan chunk (256 threads x 8)
 constexpr int MAX_K_TC = 64;       // largest k of the tensor-core path
 constexpr int LIMBS = 4;           // e4m3 limbs per coefficient (4 significant bits each)
 constexpr int DEC_GROUPS = 3;      // decoder warp groups of the tensor-core products
-constexpr int LIMBS4 = 7;          // e2m1 limbs per coefficient (3 significant bits each)
-constexpr int KH4 = 16;            // coefficient columns of the e2m1 form (limb-major: row l KH4 + c)
+constexpr int LIMBS4 = 8;          // e2m1 limbs per coefficient (3 significant bits each)
 constexpr int SF_COL = 504;        // TMEM columns 504..511: unit block scales of the e2m1 products
 
 // Limb columns of a k-column product: LIMBS k rounded up to an MMA width class.
@@ -33,12 +32,14 @@ inline int limb_cols(int k)
     return n <= 16 ? 16 : n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : 256;
 }
 
-// Limb columns of the e2m1 form: LIMBS4 KH4 = 112 for every k <= MAX_K_E2M1, limb
-// l of coefficient column c in row l KH4 + c (limb-major, so that eight columns of
-// one limb are one aligned TMEM load in the fold); 0 beyond.
-constexpr int MAX_K_E2M1 = KH4;
-inline int limb_cols4(int k) { return k >= 1 && k <= MAX_K_E2M1 ? LIMBS4 * KH4 : 0; }
-__host__ __device__ inline int e2m1_row(int c, int l) { return l * KH4 + c; }
+// Limb columns of the e2m1 form: LIMBS4 k rounded up to 64 or 128 (k <= MAX_K_E2M1);
+// 0 beyond.
+constexpr int MAX_K_E2M1 = 16;
+inline int limb_cols4(int k)
+{
+    const int n = LIMBS4 * k;
+    return n <= 64 ? 64 : n <= 128 ? 128 : 0;
+}
 
 // Position of code K (0..15) of a 16-code word: bit 8 (K mod 4) + 2 (K div 4),
 // so that (word >> 2q) & 0x03030303 is the four codes 4q..4q+3, one per byte:
@@ -114,7 +115,7 @@ __device__ inline int split_e4m3_units(float r, uint8_t *d)
 // A coefficient column b is held as LIMBS4 e2m1 numbers on the grid of halves in
 // [-2, 2]: with a power-of-two scale 2^s putting max |b| 2^-s in [1, 2),
 // r_0 = b 2^-s, d_l = RN(2 r_l) / 2, r_(l+1) = 8 (r_l - d_l) (exact; |r| <= 2),
-// and b = 2^s sum_l d_l 8^-l to within 2^(1 - 3 LIMBS4) = 2^-20 of max |b|.
+// and b = 2^s sum_l d_l 8^-l to within 2^(1 - 3 LIMBS4) = 2^-23 of max |b|.
 // Limb rows hold two K positions per byte, in the order the decoders give the
 // codes (decode16_e2m1): positions K and K + 8 of a 16-code group w share byte
 // 8 w + (K mod 8), K in the low nibble.

@@ -402,7 +402,7 @@ __global__ void k_vlimbs(SP s, uint8_t *__restrict__ Vq, int64_t n_pad, const do
 // (4b, e2m1 form) V -> e2m1 limbs at the A4 K positions: thread e of a chunk
 // takes subjects 16 (e / 8) + e mod 8 and that + 8 of the chunk, which share
 // one byte per limb row (e2m1_byte); chunk sums of the values the limbs hold,
-// exact (integers of 2^(sc-19) units, below 2^32 per chunk).
+// exact (integers of 2^(sc-22) units, below 2^35 per chunk).
 __global__ void k_vlimbs4(SP s, uint8_t *__restrict__ Vq, int64_t n_pad, const double *__restrict__ vmaxp,
                           int *__restrict__ bs, int *err)
 {
@@ -445,7 +445,7 @@ __global__ void k_vlimbs4(SP s, uint8_t *__restrict__ Vq, int64_t n_pad, const d
         }
         const int64_t byte = e2m1_byte(a4_pos(ia, s.pa, s.pnb));
 #pragma unroll
-        for (int l = 0; l < LIMBS4; ++l) Vq[e2m1_row(kk, l) * rb + byte] = static_cast<uint8_t>(d0[l] | (d1[l] << 4));
+        for (int l = 0; l < LIMBS4; ++l) Vq[(LIMBS4 * kk + l) * rb + byte] = static_cast<uint8_t>(d0[l] | (d1[l] << 4));
     }
     const double t = block_sum(finite ? static_cast<double>(q) : NAN, sh);
     if (threadIdx.x == 0) s.vsp[kk * s.nch + c] = ldexp(t, sc - (1 + 3 * (LIMBS4 - 1)));

@@ -201,11 +201,12 @@ SHAPES4 = [(2, 2), (2, 4), (1, 2), (1, 4)]
 
 
 def _limb_cols4(k):
-    return 112  # seven limbs of 16 coefficient columns, limb-major
+    n = 8 * k
+    return next(c for c in (64, 128) if n <= c)
 
 
 def _check4(k, p):
-    """e2m1 plans: seven limbs of 16 coefficient columns (112 columns);
+    """e2m1 plans: eight limbs per coefficient in 64 or 128 columns;
     per-tile issuers, two MMAs (K = 64) per K chunk; 16 TMEM columns per tile
     and chunk beside 8 columns of scale factors; the parity rule as for the e4m3
     form."""
@@ -242,13 +243,13 @@ def test_e2m1_every_shape_and_depth_keeps_the_invariants(k):
 
 def test_e2m1_default_shapes_and_rejections():
     # two row tiles x two K chunks (k <= 16)
-    for k, want in ((1, (2, 2, 112)), (8, (2, 2, 112)), (9, (2, 2, 112)), (16, (2, 2, 112))):
+    for k, want in ((1, (2, 2, 64)), (8, (2, 2, 64)), (9, (2, 2, 128)), (16, (2, 2, 128))):
         rc, p = L.cox_plan_shape_prec(L.COX_SPLIT_E2M1, k, 0, 0, 0, 0)
         assert rc == 0
         _check4(k, p)
         assert (p.tile_m, p.chunks, p.limb_cols) == want
     E = L.COX_SPLIT_E2M1
-    assert L.cox_plan_shape_prec(E, 17)[0] == L.COX_ERR_ARG          # 112 columns hold 16 coefficients
+    assert L.cox_plan_shape_prec(E, 17)[0] == L.COX_ERR_ARG          # 128 columns hold 16 coefficients
     assert L.cox_plan_shape_prec(E, 32)[0] == L.COX_ERR_ARG
     assert L.cox_plan_shape_prec(E, 16, 2, 1)[0] == L.COX_ERR_ARG    # chunk pairs only
     assert L.cox_plan_shape_prec(E, 16, 2, 3)[0] == L.COX_ERR_ARG
