@@ -50,7 +50,7 @@ def _problem(X, w, Z, **kw):
     return prob
 
 
-@pytest.mark.parametrize("precision", ["split_e4m3", "fp32_gemv"])
+@pytest.mark.parametrize("precision", ["split_e4m3", "split_e2m1", "fp32_gemv"])
 def test_loss_and_gradients_with_covariates(pkg, data, precision):
     w, X, Xf, mu, Z, L, lmax = data
     r = np.random.default_rng(4)
@@ -76,7 +76,7 @@ def test_loss_and_gradients_with_covariates(pkg, data, precision):
             assert rel_l2(gg[c], -oracle.grad(Z, None, w.delta, u)) <= 1e-5
 
 
-@pytest.mark.parametrize("precision", ["split_e4m3", "fp32_gemv"])
+@pytest.mark.parametrize("precision", ["split_e4m3", "split_e2m1", "fp32_gemv"])
 def test_iterations_with_covariates_match_oracle(pkg, data, precision):
     """20 batched iterations for 3 penalties: beta thresholded, gamma a plain
     gradient step (orc_ista_unpen)."""

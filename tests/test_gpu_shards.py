@@ -22,7 +22,7 @@ def _betas(p, k, seed):
     return B
 
 
-@pytest.mark.parametrize("precision", ["split_e4m3", "fp64"])
+@pytest.mark.parametrize("precision", ["split_e4m3", "split_e2m1", "fp64"])
 def test_column_shards_sum_to_eta(precision):
     import paper_2010_16114_gb300 as P
     from paper_2010_16114_gb300.cox import CoxProblem
@@ -30,9 +30,10 @@ def test_column_shards_sum_to_eta(precision):
     w, X, Xf, mu = dense_problem("geno_100k_50k", n=3000, p=2500)
     k = 4
     B = _betas(w.p, k, 7)
-    Xin = X if precision == "split_e4m3" else Xf
-    dt = torch.float32 if precision == "split_e4m3" else torch.float64
-    kw = {} if precision == "split_e4m3" else {"center": True}
+    split = precision.startswith("split")
+    Xin = X if split else Xf
+    dt = torch.float32 if split else torch.float64
+    kw = {} if split else {"center": True}
     with CoxProblem(Xin, w.y, w.delta, precision=precision, **kw) as full:
         eta_full = full.eta(torch.tensor(B, dtype=dt, device="cuda")).cpu().numpy()
         _, order = full.mu_order()
@@ -44,7 +45,7 @@ def test_column_shards_sum_to_eta(precision):
             _, og = prob.mu_order()
             assert np.array_equal(og, order)  # same subjects, same (stable) time order
     scale = (np.abs(Xf) @ np.abs(B.astype(np.float64)).T).max()
-    tol = (2.0 ** -15 if precision == "split_e4m3" else 1e-12) * scale
+    tol = (2.0 ** -15 if split else 1e-12) * scale
     assert np.abs(eta_sum - eta_full).max() <= tol
     for c in range(k):
         eta_o = oracle.eta(Xf, mu, B[c].astype(np.float64))[order]

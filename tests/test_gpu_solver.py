@@ -48,7 +48,8 @@ def _oracle_path(Xf, mu, y, d, sigma, lam, max_iter, tol, lag=10):
     return beta, t, hist[-1], False, ratios
 
 
-def test_path_fit_matches_oracle_rule(pkg, small):
+@pytest.mark.parametrize("precision", ["split_e4m3", "split_e2m1"])
+def test_path_fit_matches_oracle_rule(pkg, small, precision):
     """Each column stops where the oracle's rule stops, and its beta and F match
     the oracle's there.  The rule is deterministic given F; the counts may differ
     only where the oracle's stopping ratio lies within the F error of tol, which
@@ -58,7 +59,7 @@ def test_path_fit_matches_oracle_rule(pkg, small):
     w, X, Xf, mu, L, lmax = small
     lams = np.array([0.6, 0.25, 0.1]) * lmax
     tol, max_iter = 1e-5, 400
-    with CoxProblem(X, w.y, w.delta) as prob:
+    with CoxProblem(X, w.y, w.delta, precision=precision) as prob:
         beta, iters, obj, conv = prob.path_fit(lams, 1.0 / L, max_iter=max_iter, tol=tol)
         B = beta.cpu().numpy().astype(np.float64)
         for c, lam in enumerate(lams):
@@ -79,13 +80,14 @@ def test_path_fit_matches_oracle_rule(pkg, small):
             assert rel_l2(b_fix.cpu().numpy()[0].astype(np.float64), b_o) <= 1e-4
 
 
-def test_batched_columns_equal_solo_runs(pkg, small):
+@pytest.mark.parametrize("precision", ["split_e4m3", "split_e2m1"])
+def test_batched_columns_equal_solo_runs(pkg, small, precision):
     """A frozen column stops changing, so each column of a batched path fit is
     bit-identical to fitting that penalty alone."""
     from paper_2010_16114_gb300.cox import CoxProblem
     w, X, Xf, mu, L, lmax = small
     lams = np.array([0.6, 0.25, 0.1]) * lmax
-    with CoxProblem(X, w.y, w.delta) as prob:
+    with CoxProblem(X, w.y, w.delta, precision=precision) as prob:
         beta, iters, obj, _ = prob.path_fit(lams, 1.0 / L, max_iter=200, tol=1e-5)
         for c, lam in enumerate(lams):
             b1, it1, ob1, _ = prob.path_fit([lam], 1.0 / L, max_iter=200, tol=1e-5)
@@ -94,16 +96,17 @@ def test_batched_columns_equal_solo_runs(pkg, small):
             assert ob1[0] == obj[c]
 
 
-def test_checkpoint_resume_bit_identical(pkg, small):
+@pytest.mark.parametrize("precision", ["split_e4m3", "split_e2m1"])
+def test_checkpoint_resume_bit_identical(pkg, small, precision):
     from paper_2010_16114_gb300.cox import CoxProblem
     w, X, Xf, mu, L, lmax = small
     lams = np.array([0.3, 0.05]) * lmax
-    with CoxProblem(X, w.y, w.delta) as prob:
+    with CoxProblem(X, w.y, w.delta, precision=precision) as prob:
         full, it_full, ob_full, _ = prob.path_fit(lams, 1.0 / L, max_iter=80, tol=0.0)
         part, it_part, _, _ = prob.path_fit(lams, 1.0 / L, max_iter=40, tol=0.0)
         assert list(it_part) == [40, 40]
         blob = prob.get_state()
-    with CoxProblem(X, w.y, w.delta) as prob2:
+    with CoxProblem(X, w.y, w.delta, precision=precision) as prob2:
         prob2.set_state(blob)
         beta = prob2.zeros(2)
         res, it_res, ob_res, _ = prob2.path_fit(lams, 1.0 / L, max_iter=80, tol=0.0, beta=beta, warm=2)
