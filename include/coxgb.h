@@ -374,6 +374,9 @@ typedef struct cox_plan {
                              3 one per row tile committing every second stage      */
     int issuers;          /* MMA issuer warps                                      */
     int mmas_per_commit;  /* tcgen05.mma instructions per issuer commit            */
+    int limb_stages;      /* COX_SPLIT_E2M1: slots of the limb ring, ring + 2 (the
+                             codes then have a ring of their own, `stages` deep,
+                             freed as soon as they are decoded); 0 otherwise      */
 } cox_plan;
 int cox_plan_shape(int k, int tile_m, int chunks, int stages, int issue, cox_plan *out);
 /* The same plan for either operand form: precision COX_SPLIT_E4M3 (as

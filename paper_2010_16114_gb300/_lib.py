@@ -78,7 +78,8 @@ class cox_plan(ctypes.Structure):
     _fields_ = [("tile_m", ctypes.c_int), ("chunks", ctypes.c_int), ("stages", ctypes.c_int),
                 ("ring", ctypes.c_int), ("decoder_groups", ctypes.c_int), ("named_barriers", ctypes.c_int),
                 ("limb_cols", ctypes.c_int), ("tmem_cols", ctypes.c_int), ("smem_bytes", ctypes.c_longlong),
-                ("issue", ctypes.c_int), ("issuers", ctypes.c_int), ("mmas_per_commit", ctypes.c_int)]
+                ("issue", ctypes.c_int), ("issuers", ctypes.c_int), ("mmas_per_commit", ctypes.c_int),
+                ("limb_stages", ctypes.c_int)]
 
 
 class nmf_info(ctypes.Structure):

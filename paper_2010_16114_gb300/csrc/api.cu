@@ -851,6 +851,7 @@ int cox_plan_shape_prec(int precision, int k, int tile_m, int chunks, int stages
     out->issue = g.alt ? 2 : g.pair ? 3 : 1;
     out->issuers = g.alt ? 2 : g.T;
     out->mmas_per_commit = (f4 ? 2 : 4) * g.CH * (g.alt ? g.T : g.pair ? 2 : 1);
+    out->limb_stages = f4 ? g.stages2 : 0;
     return COX_OK;
 }
 

@@ -78,6 +78,7 @@ namespace coxgb {
 
 struct KParams {
     int KC, F, k, stages, ring, nb_period;
+    int stages2;        // e2m1 form: depth of the limb ring (stages is the code ring's)
     int pair;           // per-tile issuers commit after every second stage of a window
     const int *bscale;  // k: power-of-two scale of the B limbs
     int64_t units, L;
@@ -228,7 +229,15 @@ __global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                 ~static_cast<uintptr_t>(1023));
     const int S = P.stages, R = P.ring, PB = P.nb_period;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S * STAGE);
+    // e2m1 form: two rings, S code slots (released by the decoders once they have
+    // read them) and S2 limb slots (released once the stage's MMAs are complete),
+    // so the codes, streamed from HBM, are fetched further ahead than the limbs,
+    // which come from L2.  e4m3 form: one ring of S stages of limbs and codes.
+    const int S2 = F4 ? P.stages2 : S;
+    uint8_t *const lring = smem + static_cast<size_t>(S) * X_BYTES;  // e2m1 limb ring
+    const size_t ring_bytes = F4 ? static_cast<size_t>(S) * X_BYTES + static_cast<size_t>(S2) * B_BYTES
+                                 : static_cast<size_t>(S) * STAGE;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + ring_bytes);
     const uint32_t full0 = smem_addr(bars);
     const uint32_t empty0 = full0 + 8 * S;
     const uint32_t aempty0 = empty0 + 8 * S;
@@ -236,18 +245,27 @@ __global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
     const uint32_t acce = accf + 8;
     const uint32_t drainb = acce + 8;
     const uint32_t epib = drainb + 8;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + R + 4);
+    const uint32_t lfull0 = epib + 8;          // e2m1: limb slots loaded
+    const uint32_t lempty0 = lfull0 + 8 * S2;  // e2m1: limb slots free
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + R + 4 + (F4 ? 2 * S2 : 0));
     volatile int *abort_sm = reinterpret_cast<volatile int *>(tmem_slot + 1);
     volatile int *last_sm = reinterpret_cast<volatile int *>(tmem_slot + 2);
     volatile int *armed = reinterpret_cast<volatile int *>(tmem_slot + 4);  // [S] parity of the last TMA into a slot
+    volatile int *armed2 = armed + S;                                      // [S2] the same for the limb slots
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, F4 ? 4 : 1);  // e2m1: each warp of the decoding group
             armed[s] = -1;
         }
+        if (F4)
+            for (int s = 0; s < S2; ++s) {
+                mbar_init(lfull0 + 8 * s, 1);
+                mbar_init(lempty0 + 8 * s, 1);
+                armed2[s] = -1;
+            }
         for (int r = 0; r < R; ++r) mbar_init(aempty0 + 8 * r, ALT ? 1 : T);  // commits per stage
         mbar_init(accf, I);
         mbar_init(acce, 4);
@@ -294,7 +312,45 @@ __global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
     // increments only (no division on the per-stage path)
     const int g0 = static_cast<int>(u0 / KC), kc0 = static_cast<int>(u0 - static_cast<int64_t>(g0) * KC);
 
-    if (warp < 2) {
+    if (F4 && warp < 2) {
+        // ------- TMA producers of the e2m1 form: warp 0 the codes, warp 1 the limbs -------
+        // One thread per ring loads every stage in order, each slot only after its
+        // release, so a slot's phases alternate and no wait can see an older one.
+        if (lane == 0) {
+            const bool codes = warp == 0;
+            const int SR = codes ? S : S2;
+            int s = 0, kc = kc0, g = g0;
+            uint32_t ph = 0;
+            for (int64_t i = 0; i < nu; ++i) {
+                const uint32_t eb = (codes ? empty0 : lempty0) + 8 * s;
+                if (i >= SR && !mbar_wait(eb, ph ^ 1u, lim, abort_sm)) {
+                    fail(abort_sm, P.err);
+                    break;
+                }
+                if (codes) {
+                    const uint32_t fb = full0 + 8 * s;
+                    armed[s] = static_cast<int>(ph);
+                    mbar_arrive_expect_tx(fb, X_BYTES);
+                    tma_load_4d(smem_addr(smem + static_cast<size_t>(s) * X_BYTES), &tmA, 0, 0, kc * CH, g * T, fb);
+                } else {
+                    const uint32_t fb = lfull0 + 8 * s;
+                    const uint32_t st = smem_addr(lring + static_cast<size_t>(s) * B_BYTES);
+                    armed2[s] = static_cast<int>(ph);
+                    mbar_arrive_expect_tx(fb, B_BYTES);
+#pragma unroll
+                    for (int h = 0; h < CH / 2; ++h) tma_load_2d(st + h * NP * 128, &tmB, (kc * (CH / 2) + h) * 128, 0, fb);
+                }
+                if (++s == SR) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+                if (++kc == KC) {
+                    kc = 0;
+                    ++g;
+                }
+            }
+        }
+    } else if (warp < 2) {
         // ---------------- TMA producers ----------------
         if (lane == 0) {
             const int w = warp;
@@ -407,7 +463,9 @@ __global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
         const int t = warp - 2;
         constexpr uint32_t idesc = F4 ? idesc_mxf4_f32(128, NP) : idesc_e4m3_f32(128, NP);
         const uint32_t d = tbase + static_cast<uint32_t>(t * NP);
-        const uint64_t desc0 = smem_desc_sw128(smem_addr(smem));
+        // B of stage i: the limb panels at the head of stage slot i mod S, or limb slot i mod S2
+        const uint64_t desc0 = smem_desc_sw128(smem_addr(F4 ? lring : smem));
+        constexpr uint32_t DSTEP = (F4 ? B_BYTES : STAGE) >> 4;
         // The issuer is the critical thread of the pipeline: per stage it only
         // waits, issues and commits.  Windows (at most F stages, never across
         // a segment end) are sized once when they start.
@@ -460,11 +518,11 @@ __global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
                         pend = r;
                     }
                 }
-                if (++s == S) {
+                if (++s == S2) {
                     s = 0;
                     dstage = desc0;
                 } else {
-                    dstage += static_cast<uint64_t>(STAGE >> 4);
+                    dstage += static_cast<uint64_t>(DSTEP);
                 }
                 if (++r == R) {
                     r = 0;
@@ -495,11 +553,11 @@ __global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
         const uint32_t lane_base = tbase + (static_cast<uint32_t>(32 * q) << 16);
         // group 0's running sums of the windows, in shared memory ([column][thread]):
         // registers are the scarce resource of the decoders
-        float *accs = reinterpret_cast<float *>(smem + S * STAGE + 1024) + (threadIdx.x - 32 * DEC0);
+        float *accs = reinterpret_cast<float *>(smem + ring_bytes + 1024) + (threadIdx.x - 32 * DEC0);
         auto acc = [&](int tt, int e) -> float & { return accs[(tt * KH + e) * 128]; };
         // per-column constants, loaded once: sum V, step lambda, active (fused
         // step) and the power-of-two scale of the B limbs
-        float *colc = reinterpret_cast<float *>(smem + S * STAGE + 1024) + T * KH * 128;
+        float *colc = reinterpret_cast<float *>(smem + ring_bytes + 1024) + T * KH * 128;
         if (gamma == 0) {
             for (int e = 0; e < T * KH; ++e) accs[e * 128] = 0.f;
             const int tid = threadIdx.x - 32 * DEC0;
@@ -750,8 +808,9 @@ __global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
             }
         };
 
-        int s = gamma % S, r = gamma % R, nbid = gamma % PB;
+        int s = gamma % S, r = gamma % R, nbid = gamma % PB, s2 = gamma % S2;
         uint32_t fph = static_cast<uint32_t>((gamma / S) & 1), aph = static_cast<uint32_t>((gamma / R) & 1);
+        uint32_t lph = static_cast<uint32_t>((gamma / S2) & 1);
         for (int64_t i = gamma; i < nu; i += G) {
             bool go = ok;
             if (go && gamma == 0) {
@@ -761,16 +820,27 @@ __global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
                 go = ok;
             }
             if (go && !warp_wait(full0 + 8 * s, fph, lim, abort_sm)) go = false;
+            // e2m1: the stage's limbs too, so that the issuers find them in place
+            if (F4 && go && !warp_wait(lfull0 + 8 * s2, lph, lim, abort_sm)) go = false;
             // TMEM slot r is free once the MMAs of stage i - R are complete
             if (go && i >= R && !warp_wait(aempty0 + 8 * r, aph ^ 1u, lim, abort_sm)) go = false;
             if (go) {
                 if (i >= R && q == (DEC0 & 3) && lane == 0) {
-                    int se = s - R;
-                    if (se < 0) se += S;
-                    mbar_arrive(empty0 + 8 * se);
+                    // the MMAs of stage i - R, which read its limbs (and in the
+                    // e4m3 form follow the decoders' reads of its codes), are complete
+                    if (F4) {
+                        int se = s2 - R;
+                        if (se < 0) se += S2;
+                        mbar_arrive(lempty0 + 8 * se);
+                    } else {
+                        int se = s - R;
+                        if (se < 0) se += S;
+                        mbar_arrive(empty0 + 8 * se);
+                    }
                 }
                 tc_fence_after();
-                const uint8_t *xs = smem + s * STAGE + B_BYTES + rit * 32;
+                const uint8_t *xs = F4 ? smem + static_cast<size_t>(s) * X_BYTES + rit * 32
+                                       : smem + s * STAGE + B_BYTES + rit * 32;
                 const uint32_t acol = lane_base + static_cast<uint32_t>(ACC_COLS + r * SLOT_COLS);
                 if constexpr (F4) {
                     // two chunks of one tile per store: 16 TMEM columns each
@@ -798,6 +868,10 @@ __global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
                             named_arrive(1 + nbid * T + (2 * tp) / CH, NB_COUNT);
                         }
                     }
+                    // every code of the slot has been read into registers (the
+                    // stores consumed them): the code slot goes back to its producer
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(empty0 + 8 * s);
                 } else {
 #pragma unroll 2
                 for (int tc = 0; tc < T * CH; ++tc) {  // tile tc / CH, chunk tc % CH
@@ -835,6 +909,11 @@ __global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
                 s -= S;
                 fph ^= 1u;
             }
+            s2 += G;
+            while (s2 >= S2) {
+                s2 -= S2;
+                lph ^= 1u;
+            }
             r += G;
             while (r >= R) {
                 r -= R;
@@ -856,9 +935,14 @@ __global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
     if (warp == 0) {
         // never leave a copy in flight into shared memory we are about to give
         // up (after an abort, stages may have been loaded that nobody waited for)
-        if (lane == 0)
+        if (lane == 0) {
             for (int s = 0; s < S; ++s)
                 if (armed[s] >= 0) mbar_wait(full0 + 8 * s, static_cast<uint32_t>(armed[s]), DRAIN_LIMIT, &g_never_set);
+            if (F4)
+                for (int s = 0; s < S2; ++s)
+                    if (armed2[s] >= 0)
+                        mbar_wait(lfull0 + 8 * s, static_cast<uint32_t>(armed2[s]), DRAIN_LIMIT, &g_never_set);
+        }
         __syncwarp();
         tc_fence_after();
         tmem_dealloc(tbase, 512);

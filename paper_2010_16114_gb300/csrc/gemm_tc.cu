@@ -177,6 +177,49 @@ bool parity_safe(int G, int R, int S, int alt)
 }
 int lcm_i(int a, int b) { return a / gcd_i(a, b) * b; }
 
+// The e2m1 form's plan: a ring of S code slots (T CH 4 KB blocks, released by
+// the decoders once they have read them) and one of S2 = R + 2 (else R + 1)
+// limb slots (CH/2 panels of NP 128-byte rows, released once the stage's MMAs
+// are complete).  Each ring has one producer thread that loads every stage in
+// order and reuses a slot only after its release, which followed the wait on
+// its previous phase, so no wait can return a phase early: only the TMEM slot
+// waits need G <= R.  S2 > R keeps the limb producer of stage i from waiting on
+// the decoders of stage i.  The code ring takes the rest of the shared memory
+// (at most 12, at least G + 1: the decoder groups step through it by G); the
+// largest TMEM ring that leaves that much is taken.
+int plan_e2m1(GemmPlan &g, int T, int CH, int NP, int G, int stages_req, int fold_bytes)
+{
+    const int xb = T * CH * BLOCK_BYTES, bb = (CH / 2) * NP * 128;
+    const int acc_cols = T * NP;
+    int ring = std::min(8, (SF_COL - acc_cols) / (T * CH * 16)), S2 = 0, S = 0;
+    for (; ring >= G; --ring) {
+        if (lcm_i(G, ring) * T > 15) continue;
+        for (S2 = ring + 2; S2 >= ring + 1; --S2) {
+            S = stages_req > 0 ? std::max(stages_req, G + 1) : (225 * 1024 - (S2 * bb + 2048 + fold_bytes)) / xb;
+            if (S >= G + 1) break;
+        }
+        if (S >= G + 1) break;
+    }
+    if (ring < G) return COX_ERR_ARG;
+    if (S > 12) S = 12;
+    const int fixed = S2 * bb + 2048 + fold_bytes;
+    g.T = T;
+    g.CH = CH;
+    g.NP = NP;
+    g.f4 = 1;
+    g.alt = 0;
+    g.pair = 0;
+    g.G = G;
+    g.ring = ring;
+    g.nb_period = lcm_i(G, ring);
+    g.stages = S;
+    g.stages2 = S2;
+    g.smem = static_cast<size_t>(S) * xb + static_cast<size_t>(fixed);
+    if (g.smem < 120 * 1024) g.smem = 120 * 1024;  // one CTA per SM: it owns all 512 TMEM columns
+    if (g.smem > 227 * 1024) return COX_ERR_ARG;    // too many stages requested
+    return COX_OK;
+}
+
 } // namespace
 
 int gemm_shapes(int k, int *T, int *CH, int *issue, int max, int f4)
@@ -219,6 +262,7 @@ int plan_shape(GemmPlan &g, int k, int T_req, int CH_req, int stages_req, int is
     const int kh = np_cls / (f4 ? LIMBS4 : LIMBS);  // coefficient columns the fold holds
     // group 0's window sums, then four per-column constants
     const int fold_bytes = T * kh * 128 * 4 + 4 * kh * 4;
+    if (f4) return plan_e2m1(g, T, CH, np_cls, G, stages_req, fold_bytes);
     int S = stages_req > 0 ? stages_req : (225 * 1024 - 2048 - fold_bytes) / stage;
     if (S > 12) S = 12;
     if (alt && stages_req <= 0 && S % 2) --S;  // the parity classes need an even stage ring
@@ -338,6 +382,7 @@ int launch_gemm(cox_handle *h, const GemmPlan &g, const EpiArgs &e, int k, cudaS
     kp.F = g.F;
     kp.k = k;
     kp.stages = g.stages;
+    kp.stages2 = g.stages2;
     kp.ring = g.ring;
     kp.nb_period = g.nb_period;
     kp.pair = g.pair;

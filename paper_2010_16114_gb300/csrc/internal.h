@@ -176,7 +176,8 @@ struct GemmPlan {
     int G = 3;         // decoder groups
     int NP = 16;       // limb columns (limb_cols(k), or limb_cols4(k) in the e2m1 form)
     int f4 = 0;        // 1: e2m1 operands (kind::mxf4), else e4m3 (kind::f8f6f4)
-    int stages = 6;    // shared-memory pipeline depth
+    int stages = 6;    // shared-memory pipeline depth (e2m1 form: code slots)
+    int stages2 = 0;   // e2m1 form: limb slots
     int ring = 4;      // TMEM A buffers
     int nb_period = 6; // stage period of the named barriers: lcm(decoder groups, ring)
     int F = 32;        // K chunks per TMEM accumulation window

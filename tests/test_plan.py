@@ -208,16 +208,21 @@ def _limb_cols4(k):
 def _check4(k, p):
     """e2m1 plans: eight limbs per coefficient in 64 or 128 columns;
     per-tile issuers, two MMAs (K = 64) per K chunk; 16 TMEM columns per tile
-    and chunk beside 8 columns of scale factors; the parity rule as for the e4m3
-    form."""
+    and chunk beside 8 columns of scale factors.  Two shared-memory rings, each
+    with one producer that reuses a slot only after its release: code slots
+    (`stages`, at least G + 1) and limb slots (`limb_stages`, ring + 1 or ring +
+    2), so only the TMEM slot waits need G <= ring."""
     assert p.limb_cols == _limb_cols4(k)
     assert p.issue == 1 and p.issuers == p.tile_m and p.mmas_per_commit == 2 * p.chunks
     assert p.decoder_groups == 3 and p.chunks % 2 == 0
-    assert p.ring >= p.decoder_groups and p.ring < p.stages
-    assert _parity_safe(p.decoder_groups, p.ring, p.stages)
+    assert p.ring >= p.decoder_groups and p.ring + 1 <= p.limb_stages <= p.ring + 2
+    assert p.stages >= p.decoder_groups + 1
     assert p.named_barriers == math.lcm(p.decoder_groups, p.ring) * p.tile_m <= 15
     assert p.tmem_cols == p.tile_m * p.limb_cols + p.ring * p.tile_m * p.chunks * 16 + 8 <= 512
-    assert 120 * 1024 <= p.smem_bytes <= 227 * 1024
+    fold = p.tile_m * (p.limb_cols // 8) * 128 * 4 + 4 * (p.limb_cols // 8) * 4
+    code_slot, limb_slot = p.tile_m * p.chunks * 4096, (p.chunks // 2) * p.limb_cols * 128
+    assert p.smem_bytes == max(120 * 1024, p.stages * code_slot + p.limb_stages * limb_slot + 2048 + fold)
+    assert p.smem_bytes <= 227 * 1024
 
 
 @pytest.mark.parametrize("k", range(1, 17))
