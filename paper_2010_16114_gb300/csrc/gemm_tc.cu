@@ -194,7 +194,7 @@ int plan_e2m1(GemmPlan &g, int T, int CH, int NP, int G, int stages_req, int fol
     int ring = std::min(8, (SF_COL - acc_cols) / (T * CH * 16)), S2 = 0, S = 0;
     for (; ring >= G; --ring) {
         if (lcm_i(G, ring) * T > 15) continue;
-        for (S2 = ring + 2; S2 >= ring + 1; --S2) {
+        for (S2 = ring + 3; S2 >= ring + 1; --S2) {
             S = stages_req > 0 ? std::max(stages_req, G + 1) : (225 * 1024 - (S2 * bb + 2048 + fold_bytes)) / xb;
             if (S >= G + 1) break;
         }

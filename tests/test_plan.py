@@ -215,7 +215,7 @@ def _check4(k, p):
     assert p.limb_cols == _limb_cols4(k)
     assert p.issue == 1 and p.issuers == p.tile_m and p.mmas_per_commit == 2 * p.chunks
     assert p.decoder_groups == 3 and p.chunks % 2 == 0
-    assert p.ring >= p.decoder_groups and p.ring + 1 <= p.limb_stages <= p.ring + 2
+    assert p.ring >= p.decoder_groups and p.ring + 1 <= p.limb_stages <= p.ring + 3
     assert p.stages >= p.decoder_groups + 1
     assert p.named_barriers == math.lcm(p.decoder_groups, p.ring) * p.tile_m <= 15
     assert p.tmem_cols == p.tile_m * p.limb_cols + p.ring * p.tile_m * p.chunks * 16 + 8 <= 512
