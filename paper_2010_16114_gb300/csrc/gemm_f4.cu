@@ -11,14 +11,15 @@ namespace coxgb {
 // accumulator columns and at least G slots of T CH 16 columns.  The limb
 // classes stop at 128 columns (k <= 16): a class of N = 192 (six limbs at
 // k = 32) faulted on the GPU in its first parity test, and no MMA of N > 128
-// is compiled.
+// is compiled.  One tile x four chunks is compiled at 64 columns only: at 128
+// its 32 KB limb slots leave no ring depths that keep every parity wait
+// unambiguous (the planner's ring_safe) within 227 KB.
 GemmKernelFn pick_kernel_f4(int T, int CH, int NP)
 {
     switch ((T * 10 + CH) * 1000 + NP) {
     case 22064: return k_packed_gemm<2, 2, 64, DEC_GROUPS, false, true>;
     case 14064: return k_packed_gemm<1, 4, 64, DEC_GROUPS, false, true>;
     case 22128: return k_packed_gemm<2, 2, 128, DEC_GROUPS, false, true>;
-    case 14128: return k_packed_gemm<1, 4, 128, DEC_GROUPS, false, true>;
     default: return nullptr;
     }
 }

@@ -315,7 +315,9 @@ __global__ void __launch_bounds__(32 * (2 + (ALT ? 2 : T) + 4 * G), 1)
     if (F4 && warp < 2) {
         // ------- TMA producers of the e2m1 form: warp 0 the codes, warp 1 the limbs -------
         // One thread per ring loads every stage in order, each slot only after its
-        // release, so a slot's phases alternate and no wait can see an older one.
+        // release, so the producers' own waits never see an older phase.  The
+        // decoders' waits on the full barriers need the ring depths the planner
+        // keeps (at least G + R, or a multiple of G: ring_safe).
         if (lane == 0) {
             const bool codes = warp == 0;
             const int SR = codes ? S : S2;

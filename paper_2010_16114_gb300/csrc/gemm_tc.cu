@@ -177,31 +177,52 @@ bool parity_safe(int G, int R, int S, int alt)
 }
 int lcm_i(int a, int b) { return a / gcd_i(a, b) * b; }
 
+// A decoder group's parity wait on a slot of a ring of n slots, for stage i,
+// is unambiguous once the load of stage i - n is complete.  The group's own
+// previous wait was for stage i - G, after the MMAs of stage i - G - R, so
+// every load up to stage i - G - R is complete: n >= G + R suffices, and so
+// does n a multiple of G (the group itself waited for stage i - n).
+bool ring_safe(int G, int R, int n) { return n >= G + R || n % G == 0; }
+
 // The e2m1 form's plan: a ring of S code slots (T CH 4 KB blocks, released by
-// the decoders once they have read them) and one of S2 = R + 2 (else R + 1)
-// limb slots (CH/2 panels of NP 128-byte rows, released once the stage's MMAs
-// are complete).  Each ring has one producer thread that loads every stage in
-// order and reuses a slot only after its release, which followed the wait on
-// its previous phase, so no wait can return a phase early: only the TMEM slot
-// waits need G <= R.  S2 > R keeps the limb producer of stage i from waiting on
-// the decoders of stage i.  The code ring takes the rest of the shared memory
-// (at most 12, at least G + 1: the decoder groups step through it by G); the
-// largest TMEM ring that leaves that much is taken.
+// the decoders once they have read them) and one of S2 limb slots (CH/2 panels
+// of NP 128-byte rows, released once the stage's MMAs are complete), each with
+// one producer thread that loads every stage in order and reuses a slot only
+// after its release.  Both depths keep ring_safe; S2 > R keeps the limb
+// producer of stage i from waiting on the decoders of stage i, and S2 = R + 3
+// when it fits gives the limbs (from L2) three stages of look-ahead (R + 2
+// measured 0.65 of HBM against 0.84).  The code ring takes the rest of the
+// shared memory (at most 12, at least G + 1), the deepest safe depth.  The
+// largest TMEM ring for which such depths exist is taken.
 int plan_e2m1(GemmPlan &g, int T, int CH, int NP, int G, int stages_req, int fold_bytes)
 {
     const int xb = T * CH * BLOCK_BYTES, bb = (CH / 2) * NP * 128;
     const int acc_cols = T * NP;
-    int ring = std::min(8, (SF_COL - acc_cols) / (T * CH * 16)), S2 = 0, S = 0;
-    for (; ring >= G; --ring) {
-        if (lcm_i(G, ring) * T > 15) continue;
-        for (S2 = ring + 3; S2 >= ring + 1; --S2) {
-            S = stages_req > 0 ? std::max(stages_req, G + 1) : (225 * 1024 - (S2 * bb + 2048 + fold_bytes)) / xb;
-            if (S >= G + 1) break;
+    // depth of the code ring beside S2 limb slots at TMEM ring R, or 0
+    auto code_depth = [&](int R, int S2) {
+        if (stages_req > 0) {
+            const int S = std::max(stages_req, G + 1);
+            const bool fits = S * xb + S2 * bb + 2048 + fold_bytes <= 227 * 1024;
+            return ring_safe(G, R, S) && fits ? S : 0;
         }
-        if (S >= G + 1) break;
+        int S = std::min(12, (225 * 1024 - (S2 * bb + 2048 + fold_bytes)) / xb);
+        while (S >= G + 1 && !ring_safe(G, R, S)) --S;
+        return S >= G + 1 ? S : 0;
+    };
+    int ring = 0, S2 = 0, S = 0;
+    for (int R = std::min(8, (SF_COL - acc_cols) / (T * CH * 16)); R >= G && !S; --R) {
+        if (lcm_i(G, R) * T > 15) continue;
+        for (int L = R + 3; L >= R + 1 && !S; --L) {
+            if (!ring_safe(G, R, L)) continue;
+            const int d = code_depth(R, L);
+            if (d) {
+                ring = R;
+                S2 = L;
+                S = d;
+            }
+        }
     }
-    if (ring < G) return COX_ERR_ARG;
-    if (S > 12) S = 12;
+    if (!S) return COX_ERR_ARG;
     const int fixed = S2 * bb + 2048 + fold_bytes;
     g.T = T;
     g.CH = CH;

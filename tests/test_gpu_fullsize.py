@@ -221,7 +221,7 @@ def test_full_size_sampled(name, iters, precision):
         r = w.r
         # the launch configuration bench.py times: the autotuner's shapes for k columns
         tune = prob.autotune(r.k, reps=1)
-        want = 3 if precision == "split_e4m3" else 2  # compiled shapes of the k-column class
+        want = 3 if precision == "split_e4m3" else 1  # plannable shapes of the k-column class
         assert tune["x_b"]["candidates"] >= want and tune["xt_v"]["candidates"] >= want
         n, p = w.n, w.p
         sigma = _step(n, p)

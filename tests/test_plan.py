@@ -210,12 +210,16 @@ def _check4(k, p):
     per-tile issuers, two MMAs (K = 64) per K chunk; 16 TMEM columns per tile
     and chunk beside 8 columns of scale factors.  Two shared-memory rings, each
     with one producer that reuses a slot only after its release: code slots
-    (`stages`, at least G + 1) and limb slots (`limb_stages`, ring + 1 or ring +
-    2), so only the TMEM slot waits need G <= ring."""
+    (`stages`, at least G + 1) and limb slots (`limb_stages`, ring + 1 .. ring +
+    3); a decoder group's parity wait on either ring is unambiguous when the
+    ring's depth is at least G + ring or a multiple of G."""
     assert p.limb_cols == _limb_cols4(k)
     assert p.issue == 1 and p.issuers == p.tile_m and p.mmas_per_commit == 2 * p.chunks
     assert p.decoder_groups == 3 and p.chunks % 2 == 0
-    assert p.ring >= p.decoder_groups and p.ring + 1 <= p.limb_stages <= p.ring + 3
+    G, R = p.decoder_groups, p.ring
+    assert R >= G and R + 1 <= p.limb_stages <= R + 3
+    for depth in (p.stages, p.limb_stages):
+        assert depth >= G + R or depth % G == 0, (depth, G, R)
     assert p.stages >= p.decoder_groups + 1
     assert p.named_barriers == math.lcm(p.decoder_groups, p.ring) * p.tile_m <= 15
     assert p.tmem_cols == p.tile_m * p.limb_cols + p.ring * p.tile_m * p.chunks * 16 + 8 <= 512
@@ -238,11 +242,15 @@ def test_e2m1_every_shape_and_depth_keeps_the_invariants(k):
         _check4(k, p)
         for s in range(1, 16):
             rc, q = L.cox_plan_shape_prec(L.COX_SPLIT_E2M1, k, t, c, s, 1)
+            want = max(s, p.decoder_groups + 1)
             if rc != 0:
+                # refused only at a depth the parity rule forbids, or beyond 227 KB
                 assert rc == L.COX_ERR_ARG
+                unsafe = not (want >= p.decoder_groups + p.ring or want % p.decoder_groups == 0)
+                assert unsafe or want > p.stages, (k, t, c, s)
                 continue
             _check4(k, q)
-            assert q.stages == min(max(s, 4), 12)
+            assert q.stages == want
     assert compiled >= 1
 
 
@@ -261,6 +269,8 @@ def test_e2m1_default_shapes_and_rejections():
     assert L.cox_plan_shape_prec(E, 16, 2, 2, 0, 2)[0] == L.COX_ERR_ARG  # per-tile issuers only
     assert L.cox_plan_shape_prec(E, 16, 2, 2, 0, 3)[0] == L.COX_ERR_ARG
     assert L.cox_plan_shape_prec(E, 16, 2, 4)[0] == L.COX_ERR_ARG    # 2 x 4: not compiled
+    assert L.cox_plan_shape_prec(E, 16, 1, 4)[0] == L.COX_ERR_ARG    # 1 x 4 at 128 columns: no safe depths fit
+    assert L.cox_plan_shape_prec(E, 8, 1, 4)[0] == 0
     assert L.cox_plan_shape_prec(7, 16)[0] == L.COX_ERR_ARG          # not a tensor-core form
     # the e4m3 entry point is the e4m3 form of the general one
     for k in (1, 16, 64):
