@@ -205,14 +205,14 @@ int plan_e2m1(GemmPlan &g, int T, int CH, int NP, int G, int stages_req, int fol
             const bool fits = S * xb + S2 * bb + 2048 + fold_bytes <= 227 * 1024;
             return ring_safe(G, R, S) && fits ? S : 0;
         }
-        int S = std::min(12, (225 * 1024 - (S2 * bb + 2048 + fold_bytes)) / xb);
+        int S = std::min(12, (227 * 1024 - (S2 * bb + 2048 + fold_bytes)) / xb);
         while (S >= G + 1 && !ring_safe(G, R, S)) --S;
         return S >= G + 1 ? S : 0;
     };
     int ring = 0, S2 = 0, S = 0;
     for (int R = std::min(8, (SF_COL - acc_cols) / (T * CH * 16)); R >= G && !S; --R) {
         if (lcm_i(G, R) * T > 15) continue;
-        for (int L = R + 3; L >= R + 1 && !S; --L) {
+        for (int L = R + 4; L >= R + 1 && !S; --L) {
             if (!ring_safe(G, R, L)) continue;
             const int d = code_depth(R, L);
             if (d) {

@@ -217,7 +217,7 @@ def _check4(k, p):
     assert p.issue == 1 and p.issuers == p.tile_m and p.mmas_per_commit == 2 * p.chunks
     assert p.decoder_groups == 3 and p.chunks % 2 == 0
     G, R = p.decoder_groups, p.ring
-    assert R >= G and R + 1 <= p.limb_stages <= R + 3
+    assert R >= G and R + 1 <= p.limb_stages <= R + 4
     for depth in (p.stages, p.limb_stages):
         assert depth >= G + R or depth % G == 0, (depth, G, R)
     assert p.stages >= p.decoder_groups + 1
