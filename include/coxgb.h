@@ -86,7 +86,8 @@ enum {
 };
 
 typedef struct cox_options {
-    int precision;        /* COX_SPLIT_E4M3 (default), COX_FP64, COX_FP32_GEMV       */
+    int precision;        /* COX_SPLIT_E4M3 (default), COX_SPLIT_E2M1, COX_FP64,
+                             COX_FP32_GEMV                                         */
     int center;           /* 1: X_c = X - 1 mu^T (default 1; COX_FP64 default 0)    */
     int device;           /* CUDA device ordinal (default: current device)           */
     int tile_m;           /* 128-row tiles per pipeline stage of the tensor-core
@@ -329,9 +330,10 @@ typedef struct cox_info {
 int cox_get_info(cox_h h, cox_info *info);
 
 /*
- * Autotuner of the tensor-core products (COX_SPLIT_E4M3 handles).  For k
- * coefficient columns it times every compiled pipeline shape (row tiles and
- * K chunks per stage; per-tile and alternating issuers) of both products at
+ * Autotuner of the tensor-core products (COX_SPLIT_E4M3 and COX_SPLIT_E2M1
+ * handles; the choice is kept per operand form and k).  For k coefficient
+ * columns it times every plannable pipeline shape of the handle's operand form
+ * (row tiles and K chunks per stage; per-tile and alternating issuers) of both products at
  * the planner's shared-memory depth on the handle's resident genotypes: one
  * warm-up and `reps` launches each, CUDA events on the legacy stream, the
  * device synchronised after each shape, partial outputs only (no coefficient
@@ -339,7 +341,8 @@ int cox_get_info(cox_h h, cox_info *info);
  * calls with k columns unless cox_options forces tile_m, chunks or stages.
  * xb / xtv (either may be NULL) receive the choice and its mean launch time.
  * Drops the per-k workspace.  Synchronous.  Errors: COX_ERR_UNSUPPORTED for
- * other precisions; COX_ERR_ARG for k outside 1..64 or reps < 1.
+ * other precisions; COX_ERR_ARG for k outside 1..64 (1..16 for COX_SPLIT_E2M1)
+ * or reps < 1.
  */
 typedef struct cox_tune_choice {
     int tile_m, chunks, stages, candidates;
@@ -356,7 +359,7 @@ int cox_autotune(cox_h h, int k, int reps, cox_tune_choice *xb, cox_tune_choice 
  * cox_options.issue; 0 = the built-in default) at a shared-memory depth
  * (stages; 0 = the deepest that fits), the plan cox_setup's handles would
  * launch.  Every plan it returns keeps the pipeline's invariants: ring >=
- * decoder_groups, ring < stages, named_barriers <= 15, tmem_cols <= 512,
+ * decoder_groups, ring < stages (e2m1: ring < limb_stages), named_barriers <= 15, tmem_cols <= 512,
  * smem_bytes within the device's per-block limit, and for issue 2 two decoder
  * groups with an even ring and an even number of stages.  Errors: COX_ERR_ARG
  * for a NULL out, k outside 1..64, a shape not compiled for k's limb-column
