@@ -8,7 +8,9 @@
  * Section 6 (Breslow ties, lag-10 stopping rule).
  *
  * Notation: n subjects, p predictors (SNPs), k penalty values solved
- * together.  y = observed times, delta = event indicators.  The library
+ * together (k <= 64 on the tensor cores in the e4m3 form, k <= 16 in the e2m1
+ * form; calls with more return COX_ERR_ARG).  y = observed times, delta =
+ * event indicators.  The library
  * centres the design, X_c = X - 1 mu^T with mu_j the column mean, when
  * cox_options.center is 1, and works with
  *     f(beta)  = -(1/n) sum_i delta_i [ eta_i - log sum_{j: y_j >= y_i} exp(eta_j) ],
