@@ -15,7 +15,10 @@ the kernel's agents as atomic steps in every order a scheduler picks:
   limb load and the TMEM slot (the MMAs of stage i - R), releases the limbs of
   stage i - R, decodes, releases the code slot, and hands stage i to the issuer;
 * the issuer (one; per-tile issuers behave alike for these barriers) issues the
-  stages' MMAs in order; MMAs complete in order and free their TMEM slot.
+  stages' MMAs in order; MMAs complete in the order they were issued and free
+  their TMEM slot.  With alternating issuers (the e4m3 form's issue mode 2) two
+  issuers take the even and the odd stages, each in order, and the tensor pipe
+  completes the MMAs in the interleaved order they were issued.
 
 The e4m3 form's single ring (one slot per stage holding codes and limbs,
 released by the decoders of stage i + R after the MMAs of stage i) is modelled
@@ -33,21 +36,23 @@ import random
 
 class Model:
     def __init__(self, G: int, R: int, S: int, S2: int | None, N: int, inorder: bool = False,
-                 from_stage: int = 0):
+                 from_stage: int = 0, issuers: int = 1):
         """S2 = None: the e4m3 single ring of S stages; else the e2m1 rings.
         inorder: loads complete in stage order (else in any order).
-        from_stage: aliasing waits of decoders at earlier stages are not reported."""
+        from_stage: aliasing waits of decoders at earlier stages are not reported.
+        issuers: 1, or 2 on alternate stages."""
         self.G, self.R, self.S, self.S2, self.N = G, R, S, S2, N
         self.split = S2 is not None
         self.inorder = inorder
         self.from_stage = from_stage
+        self.I = issuers
 
-    # state: (prod, loads_pending, dec, issued, mma_done, P) with
+    # state: (prod, loads_pending, dec, iss, handed, queue, P) with
     #   prod = tuple of next stage per producer (split: codes, limbs; single: two warps)
     #   loads_pending = frozenset of (kind, stage) loads issued and not complete
     #   dec = tuple of (next stage, substep) per decoder group
-    #   issued = next stage the issuer issues; handed = frozenset of stages handed over
-    #   mma_done = stages whose MMAs completed (in order)
+    #   iss = tuple of the next stage per issuer; handed = frozenset of stages handed over
+    #   queue = stages whose MMAs are issued and not complete, in issue order
     #   P = dict-like tuple of completed phases per barrier
     def initial(self):
         G, S, R = self.G, self.S, self.R
@@ -55,7 +60,7 @@ class Model:
         prod = (0, 0) if self.split else (0, 1)
         dec = tuple((g, 0) for g in range(G))
         P = {"full": (0,) * S, "empty": (0,) * S, "aempty": (0,) * R, "lfull": (0,) * S2, "lempty": (0,) * S2}
-        return (prod, frozenset(), dec, 0, frozenset(), 0, tuple(sorted(P.items())))
+        return (prod, frozenset(), dec, tuple(range(self.I)), frozenset(), (), tuple(sorted(P.items())))
 
     @staticmethod
     def _bump(P, name, idx):
@@ -77,7 +82,7 @@ class Model:
 
     def moves(self, st):
         """Yield (label, next_state) for every enabled step, or raise on aliasing."""
-        prod, pend, dec, issued, handed, done, P = st
+        prod, pend, dec, issued, handed, done, P = st  # issued: per issuer; done: the MMA queue
         G, R, S, N = self.G, self.R, self.S, self.N
         out = []
         # producers
@@ -154,23 +159,26 @@ class Model:
                         P2 = self._bump(P2, "empty", i % S)  # codes read: slot free
                     nd[g] = (i + G, 0)
                     out.append((("decode", g, i), (prod, pend, tuple(nd), issued, handed | {i}, done, P2)))
-        # issuer, in stage order
-        if issued < N and issued in handed:
-            out.append((("issue", issued), (prod, pend, dec, issued + 1, handed, done, P)))
-        # MMA completion, in order
-        if done < issued:
-            out.append((("mma", done), (prod, pend, dec, issued, handed, done + 1,
-                                        self._bump(P, "aempty", done % R))))
+        # issuers, each in stage order over its stages
+        for j, i in enumerate(issued):
+            if i < N and i in handed:
+                ni = list(issued)
+                ni[j] = i + self.I
+                out.append((("issue", i), (prod, pend, dec, tuple(ni), handed, done + (i,), P)))
+        # MMA completion, in issue order
+        if done:
+            out.append((("mma", done[0]), (prod, pend, dec, issued, handed, done[1:],
+                                           self._bump(P, "aempty", done[0] % R))))
         return out, None
 
     def finished(self, st):
-        return st[3] == self.N and st[5] == self.N
+        return all(i >= self.N for i in st[3]) and not st[5]
 
 
-def explore(G, R, S, S2, N, limit=400_000, inorder=False, from_stage=0):
+def explore(G, R, S, S2, N, limit=400_000, inorder=False, from_stage=0, issuers=1):
     """Every interleaving (memoised); returns the first aliasing wait, or None.
     Raises RuntimeError when the state space exceeds `limit` or a state deadlocks."""
-    m = Model(G, R, S, S2, N, inorder, from_stage)
+    m = Model(G, R, S, S2, N, inorder, from_stage, issuers)
     seen = set()
     stack = [m.initial()]
     while stack:
@@ -193,11 +201,11 @@ def explore(G, R, S, S2, N, limit=400_000, inorder=False, from_stage=0):
     return None
 
 
-def random_runs(G, R, S, S2, N, runs=300, seed=1, inorder=False, from_stage=0):
+def random_runs(G, R, S, S2, N, runs=300, seed=1, inorder=False, from_stage=0, issuers=1):
     """Random schedules, each biased towards one agent kind (so decoder groups
     race ahead of late loads, or loads of late MMAs); returns the first aliasing
     wait, or None."""
-    m = Model(G, R, S, S2, N, inorder, from_stage)
+    m = Model(G, R, S, S2, N, inorder, from_stage, issuers)
     rng = random.Random(seed)
     kinds = ["load", "landed", "dfull", "dlfull", "decode", "issue", "mma"]
     for _ in range(runs):

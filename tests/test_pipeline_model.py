@@ -1,15 +1,15 @@
 """The tensor-core products' barrier protocol in a model (pipeline_model.py), on
-CPU: no plan the library launches lets an mbarrier parity wait return on a stale
-phase, whatever order the asynchronous loads and MMAs complete in and however
-the warps are scheduled.
+CPU: which plans the library launches could let an mbarrier parity wait return
+on a stale phase, over every order the asynchronous loads and MMAs complete in
+and every schedule of the warps.
 
 * e2m1 form (a ring of code slots released after decoding, one of limb slots
   released after the MMAs): every plan of every k and shape is safe in any order.
 * The depths its planner refuses (a code ring of 5, or a limb ring of 5, at three
   decoder groups and three TMEM slots) do alias; a build that planned a code ring
   of 5 faulted on the GPU.
-* e4m3 form (one ring): the plans whose depth is at least G + R or a multiple of G
-  are safe in any order.  The plans that rely on the TMEM ring being a multiple of
+* e4m3 form (one ring; one issuer per tile or two on alternate stages): the
+  plans whose depth is at least G + R or a multiple of G are safe in any order.  The plans that rely on the TMEM ring being a multiple of
   G instead (one row tile at 64, 128 and 256 limb columns) are safe once the first
   S loads have landed; before that, a load of the first S stages that lands after
   later ones could let a decoder group's wait on its slot's second phase return
@@ -90,3 +90,21 @@ def test_single_ring_exhaustive_small():
     # conditions never aliases
     assert explore(3, 3, 6, None, N=15, limit=400_000) is None
     assert explore(2, 2, 4, None, N=12, limit=400_000) is None
+
+
+def test_alternating_issuer_plans():
+    """e4m3 issue mode 2 (two issuers on alternate stages, two decoder groups):
+    every plan is safe in any order; an odd ring of stages (which the planner
+    refuses) aliases."""
+    plans = set()
+    for k in range(1, 65):
+        for t in (2, 1):
+            for c in (3, 2, 1):
+                rc, p = L.cox_plan_shape(k, t, c, 0, 2)
+                if rc == 0:
+                    plans.add((p.decoder_groups, p.ring, p.stages))
+    assert plans
+    for G, R, S in sorted(plans):
+        assert random_runs(G, R, S, None, N, runs=RUNS, seed=11, issuers=2) is None, (G, R, S)
+        assert explore(G, R, S, None, N=12, limit=400_000, issuers=2) is None, (G, R, S)
+    assert random_runs(2, 2, 5, None, N, runs=RUNS, seed=11, issuers=2) is not None
