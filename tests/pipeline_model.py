@@ -36,16 +36,19 @@ import random
 
 class Model:
     def __init__(self, G: int, R: int, S: int, S2: int | None, N: int, inorder: bool = False,
-                 from_stage: int = 0, issuers: int = 1):
+                 from_stage: int = 0, issuers: int = 1, ordered_start: bool = False):
         """S2 = None: the e4m3 single ring of S stages; else the e2m1 rings.
         inorder: loads complete in stage order (else in any order).
         from_stage: aliasing waits of decoders at earlier stages are not reported.
-        issuers: 1, or 2 on alternate stages."""
+        issuers: 1, or 2 on alternate stages.
+        ordered_start: (single ring) each of the first S loads is issued only
+        once the load before it has landed."""
         self.G, self.R, self.S, self.S2, self.N = G, R, S, S2, N
         self.split = S2 is not None
         self.inorder = inorder
         self.from_stage = from_stage
         self.I = issuers
+        self.ordered_start = ordered_start
 
     # state: (prod, loads_pending, dec, iss, handed, queue, P) with
     #   prod = tuple of next stage per producer (split: codes, limbs; single: two warps)
@@ -105,6 +108,10 @@ class Model:
                     ok, alias = (True, False) if j < S else self._wait(P, "empty", j % S, j // S - 1)
                     if alias:
                         return None, ("producer", w, j)
+                    if ok and self.ordered_start and 1 <= j < S:
+                        ok, alias = self._wait(P, "full", j - 1, 0)
+                        if alias:
+                            return None, ("producer start", w, j)
                     if ok:
                         np_ = list(prod)
                         np_[w] = j + 2
@@ -175,10 +182,10 @@ class Model:
         return all(i >= self.N for i in st[3]) and not st[5]
 
 
-def explore(G, R, S, S2, N, limit=400_000, inorder=False, from_stage=0, issuers=1):
+def explore(G, R, S, S2, N, limit=400_000, inorder=False, from_stage=0, issuers=1, ordered_start=False):
     """Every interleaving (memoised); returns the first aliasing wait, or None.
     Raises RuntimeError when the state space exceeds `limit` or a state deadlocks."""
-    m = Model(G, R, S, S2, N, inorder, from_stage, issuers)
+    m = Model(G, R, S, S2, N, inorder, from_stage, issuers, ordered_start)
     seen = set()
     stack = [m.initial()]
     while stack:
@@ -201,11 +208,12 @@ def explore(G, R, S, S2, N, limit=400_000, inorder=False, from_stage=0, issuers=
     return None
 
 
-def random_runs(G, R, S, S2, N, runs=300, seed=1, inorder=False, from_stage=0, issuers=1):
+def random_runs(G, R, S, S2, N, runs=300, seed=1, inorder=False, from_stage=0, issuers=1,
+                ordered_start=False):
     """Random schedules, each biased towards one agent kind (so decoder groups
     race ahead of late loads, or loads of late MMAs); returns the first aliasing
     wait, or None."""
-    m = Model(G, R, S, S2, N, inorder, from_stage, issuers)
+    m = Model(G, R, S, S2, N, inorder, from_stage, issuers, ordered_start)
     rng = random.Random(seed)
     kinds = ["load", "landed", "dfull", "dlfull", "decode", "issue", "mma"]
     for _ in range(runs):

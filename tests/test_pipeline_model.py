@@ -108,3 +108,18 @@ def test_alternating_issuer_plans():
         assert random_runs(G, R, S, None, N, runs=RUNS, seed=11, issuers=2) is None, (G, R, S)
         assert explore(G, R, S, None, N=12, limit=400_000, issuers=2) is None, (G, R, S)
     assert random_runs(2, 2, 5, None, N, runs=RUNS, seed=11, issuers=2) is not None
+
+
+def test_ordered_start_closes_the_window_where_it_is_needed():
+    """The fix for the start-up window of the third condition: each of the first S
+    loads issued only once the load before it has landed.  For the plans that
+    need it the model finds neither an aliasing wait nor a deadlock, in any load
+    order; applied to a two-group ring of 4 it can deadlock (a producer warp that
+    is late to look at the previous slot finds it already refilled by the other
+    warp), so the fix belongs to those plans only."""
+    for G, R, S in ((3, 3, 5), (3, 6, 8)):
+        assert random_runs(G, R, S, None, N, runs=RUNS, seed=11, ordered_start=True) is None, (G, R, S)
+        assert explore(G, R, S, None, N=2 * S + 3, limit=600_000, ordered_start=True) is None, (G, R, S)
+    with pytest.raises(RuntimeError, match="deadlock"):
+        for seed in range(1, 6):
+            random_runs(2, 2, 4, None, N, runs=RUNS, seed=seed, ordered_start=True)
